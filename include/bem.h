@@ -1,0 +1,176 @@
+/*
+ * bem.h — C ABI of the GB300 (sm_103a) FFT-accelerated boundary element
+ * operator after Benad, "Acceleration of the Boundary Element Method for
+ * arbitrary shapes with the Fast Fourier Transformation" (arXiv:1809.00845).
+ *
+ * The method (Section 3, Section 4, Eq. 15-16): a boundary integral over a
+ * curve (surface) S is a convolution over the grid that encloses S, one
+ * dimension higher, once the densities are extended with zeros off S.  Each
+ * operator apply therefore
+ *   1. scatters the weighted boundary densities onto a zero-padded uniform grid
+ *      (u extended with zeros, Fig. 4; q, and u n_a for the double layer),
+ *   2. transforms forward (FFT),
+ *   3. multiplies by the precomputed spectra of the kernel tables (Eq. 16),
+ *   4. transforms back, and
+ *   5. reads the result at the boundary cells (Section 4, last paragraph).
+ * bem_solve wraps the apply in a Krylov iteration (Section 4 uses conjugate
+ * gradients; this library uses restarted GMRES).
+ *
+ * Discretisation conventions (all calls):
+ *   * grid of n cells per axis, spacing h; node of cell g at (g + 1/2) h;
+ *   * boundary cell j: grid index g_j (dim int32, axis 0 = x), boundary
+ *     measure w_j (length in 2D, area in 3D; the "divide by the discretisation
+ *     length" of Section 4 folded into the source weight) and unit outward
+ *     normal n_j;
+ *   * d_ij = x_gi - x_gj (collocation minus integration point, Eq. 15);
+ *   * single layer (S f)_i = sum_j U(d_ij) w_j f_j; double layer
+ *     (D u)_i = sum_j sum_a Q_a(d_ij) w_j n_{a,j} u_j with
+ *     2D Laplace U = -ln r/(2 pi) (Eq. 3), Q_a = -d_a/(2 pi r^2) (Eq. 15);
+ *     3D Laplace U = 1/(4 pi r), Q_a = -d_a/(4 pi r^3);
+ *     Kelvin (Eq. 7) U_ab and the traction kernel T_ab (Eq. 8);
+ *   * the singular cell (d = 0) carries the kernel's average over the h-cell
+ *     ("constant elements", Section 4), odd kernels carry 0;
+ *   * BIE row (Eq. 4, Eq. 8): c u = S q + D u (Laplace), c u = U t - T u
+ *     (Navier), c = 1/2 unless set otherwise.
+ *
+ * Errors: every call returns a bem_status; nothing throws or aborts across
+ * the ABI.  bem_last_error() returns a thread-local message for the last
+ * failing call on the calling thread.  On a CUDA error the plan stays valid
+ * only if the CUDA context survived.
+ *
+ * Threading: a plan may be used by one thread at a time (it owns one set of
+ * scratch buffers); use one plan per concurrent stream.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bem_plan_s* bem_plan_t;
+
+typedef enum {
+  BEM_OK = 0,
+  BEM_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, duplicate/out-of-grid cell) */
+  BEM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  BEM_ERR_OOM = 3,            /* device allocation failed */
+  BEM_ERR_NOT_CONVERGED = 4,  /* bem_solve hit max_iter; best iterate written, info filled */
+  BEM_ERR_BREAKDOWN = 5,      /* GMRES breakdown before reaching tol */
+  BEM_ERR_NONFINITE = 6,      /* NaN/Inf in data or residual */
+  BEM_ERR_TIMEOUT = 7,        /* a bounded device-side wait expired */
+  BEM_ERR_UNSUPPORTED = 8     /* valid but unsupported configuration (e.g. grid size) */
+} bem_status;
+
+typedef enum { BEM_LAPLACE_2D = 0, BEM_LAPLACE_3D = 1, BEM_KELVIN_3D = 2 } bem_kernel;
+typedef enum { BEM_F64 = 0, BEM_F32 = 1 } bem_precision;
+
+/* BEM_SINGLE: S (Laplace) or U (Kelvin).  BEM_DOUBLE: D (Laplace) or T
+ * (Kelvin).  BEM_SYSTEM: the boundary-condition-split operator A of the last
+ * bem_set_bc call: A x = K1(x m_D) + K2(x m_N) - c x m_N with K1 = S|U,
+ * K2 = +D (Laplace, Eq. 15) or -T (Navier, Eq. 8), m_D/m_N the Dirichlet and
+ * Neumann masks (per component). */
+typedef enum { BEM_SINGLE = 0, BEM_DOUBLE = 1, BEM_SYSTEM = 2 } bem_layer;
+
+typedef struct {
+  int iters;                 /* total GMRES iterations (operator applies inside the Krylov loop) */
+  int restarts;              /* number of restarts performed */
+  double rel_residual;       /* ||b - A x|| / ||b|| recomputed with the plan's own apply (FP64 norms) */
+  double rel_residual_est;   /* GMRES (Givens) estimate at exit */
+  double seconds;            /* wall time of the solve (host clock) */
+  int applies;               /* all operator applies, right-hand side and final check included */
+} bem_solve_info;
+
+typedef struct {
+  int dim, ncomp;            /* 2 or 3; 1 (Laplace) or 3 (Kelvin) */
+  int64_t n, N, nb;          /* cells per axis, padded transform length (2n), boundary cells */
+  int precision;             /* bem_precision */
+  int grid_ctas;             /* persistent CTAs of the fused column kernel */
+  int threads_per_cta;
+  size_t scratch_bytes;      /* device scratch owned by the plan (partials, weighted densities) */
+  size_t spectra_bytes;      /* device bytes of the compressed kernel spectra */
+  double plan_seconds;       /* wall time of bem_plan */
+} bem_plan_info;
+
+/* Build a plan (Section 3-4: kernel tables on the padded grid and their
+ * spectra; Fig. 5, Eq. 16).
+ *   dim     2 (BEM_LAPLACE_2D) or 3 (BEM_LAPLACE_3D, BEM_KELVIN_3D)
+ *   n       host array of dim cell counts; all equal (else BEM_ERR_UNSUPPORTED)
+ *   h       grid spacing (> 0)
+ *   nb      number of boundary cells (>= 1)
+ *   cell    host, nb*dim int32 grid indices in [0, n), row-major (cell j axis a
+ *           at cell[j*dim + a]); duplicates are rejected (BEM_ERR_ARG)
+ *   w       host, nb boundary measures
+ *   normal  host, nb*dim unit outward normals
+ *   nu, mu  Poisson ratio and shear modulus (Kelvin only; ignored otherwise)
+ *   prec    arithmetic of the apply; spectra are always computed in FP64 on
+ *           the device and rounded to prec
+ *   flags   reserved, pass 0
+ *   stream  cudaStream_t (may be NULL) used for the set-up kernels; the call
+ *           synchronises it before returning
+ * The plan copies every input.  Device memory: spectra (ncomp-dependent,
+ * (n+1)^dim reals each), scratch, boundary metadata. */
+bem_status bem_plan(bem_plan_t* out, int dim, const int64_t* n, double h, int64_t nb, const int32_t* cell,
+                    const double* w, const double* normal, bem_kernel kernel, double nu, double mu,
+                    bem_precision prec, uint32_t flags, void* stream);
+
+/* Set the boundary-condition types used by BEM_SYSTEM and bem_solve.
+ *   bc  host, nb*ncomp bytes: 0 = Dirichlet (u known, q/t unknown),
+ *       1 = Neumann (q/t known, u unknown)
+ *   c   free-term coefficient (Section 2: 1/2 on a smooth boundary) */
+bem_status bem_set_bc(bem_plan_t plan, const uint8_t* bc, double c);
+
+/* One operator apply on the device (Section 4, Eq. 15-16).
+ *   in_dev, out_dev  device pointers, nb*ncomp values of the plan precision
+ *                    (double for BEM_F64, float for BEM_F32), component
+ *                    fastest; caller-owned; must not alias
+ *   stream           cudaStream_t (may be NULL); the call is asynchronous
+ * BEM_SYSTEM needs a prior bem_set_bc. */
+bem_status bem_apply(bem_plan_t plan, bem_layer layer, const void* in_dev, void* out_dev, void* stream);
+
+/* The same apply with HOST buffers (plan precision): copies in, applies,
+ * copies out and synchronises the stream before returning. */
+bem_status bem_apply_host(bem_plan_t plan, bem_layer layer, const void* in_host, void* out_host, void* stream);
+
+/* Solve the boundary-condition split system for the unknowns (Section 4:
+ * Krylov iteration on the FFT apply; restarted GMRES here).
+ *   bc        host nb*ncomp (as bem_set_bc; also sets the plan's BC state)
+ *   data      host nb*ncomp FP64 known values: u where bc = 0, q/t where bc = 1
+ *   c         free-term coefficient
+ *   tol       stop when the relative residual ||b - A x||/||b|| <= tol
+ *   max_iter  total iteration cap;  restart  Krylov dimension m (<= 512)
+ *   x0        host nb*ncomp FP64 initial guess of the unknowns, or NULL (zero)
+ *   u_out, q_out  host nb*ncomp FP64 full boundary fields (known entries
+ *             copied from data, unknown ones from the solution); either may be NULL
+ *   info      may be NULL
+ * Returns BEM_ERR_NOT_CONVERGED with the best iterate written if max_iter is
+ * reached.  Arnoldi, Givens rotations and residual norms are FP64. */
+bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
+                     int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
+                     void* stream);
+
+/* Query sizes and launch shape of a plan. */
+bem_status bem_get_info(bem_plan_t plan, bem_plan_info* info);
+
+/* Kernel timing: when enabled, every apply records CUDA events around the
+ * fused column kernel on the apply's stream; bem_kernel_time returns the sum
+ * of their elapsed times (ms) and the count since the last reset.  Reading
+ * the times synchronises the recorded events. */
+bem_status bem_set_kernel_timing(bem_plan_t plan, int enable);
+bem_status bem_kernel_time(bem_plan_t plan, double* total_ms, int64_t* launches);
+
+/* Number of kernel launches one apply of the given layer issues. */
+int bem_launches_per_apply(bem_plan_t plan, bem_layer layer);
+
+bem_status bem_destroy(bem_plan_t plan);
+const char* bem_status_string(bem_status s);
+const char* bem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_GB300_H */

@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in include/bem.h (argument marshalling only).
+
+Every step of an apply or a solve runs in the CUDA kernels of libbem_gb300.so;
+this module converts arrays, passes raw pointers and maps status codes to
+exceptions.  PyTorch is used only to hold device memory and to name the
+current CUDA stream.  There is no CPU fallback: if the library is missing the
+import of the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbem_gb300.so")
+
+BEM_OK, BEM_ERR_ARG, BEM_ERR_CUDA, BEM_ERR_OOM, BEM_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+BEM_ERR_BREAKDOWN, BEM_ERR_NONFINITE, BEM_ERR_TIMEOUT, BEM_ERR_UNSUPPORTED = 5, 6, 7, 8
+BEM_LAPLACE_2D, BEM_LAPLACE_3D, BEM_KELVIN_3D = 0, 1, 2
+BEM_F64, BEM_F32 = 0, 1
+BEM_SINGLE, BEM_DOUBLE, BEM_SYSTEM = 0, 1, 2
+
+KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d": BEM_KELVIN_3D}
+PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32}
+LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
+
+EXPORTED = ["bem_plan", "bem_set_bc", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
+            "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
+            "bem_status_string", "bem_last_error"]
+
+
+class BemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("rel_residual_est", ctypes.c_double), ("seconds", ctypes.c_double), ("applies", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("ncomp", ctypes.c_int), ("n", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("nb", ctypes.c_int64), ("precision", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+                ("threads_per_cta", ctypes.c_int), ("scratch_bytes", ctypes.c_size_t),
+                ("spectra_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libbem_gb300.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libbem_gb300.so not built ({path}); run paper_1809_00845_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    lib.bem_plan.argtypes = [ctypes.POINTER(P), I, P, D, I64, P, P, P, I, D, D, I, ctypes.c_uint32, P]
+    lib.bem_set_bc.argtypes = [P, P, D]
+    lib.bem_apply.argtypes = [P, I, P, P, P]
+    lib.bem_apply_host.argtypes = [P, I, P, P, P]
+    lib.bem_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
+    lib.bem_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    lib.bem_set_kernel_timing.argtypes = [P, I]
+    lib.bem_kernel_time.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64)]
+    lib.bem_launches_per_apply.argtypes = [P, I]
+    lib.bem_launches_per_apply.restype = I
+    lib.bem_destroy.argtypes = [P]
+    lib.bem_status_string.argtypes = [I]
+    lib.bem_status_string.restype = ctypes.c_char_p
+    lib.bem_last_error.argtypes = []
+    lib.bem_last_error.restype = ctypes.c_char_p
+    for name in ("bem_plan", "bem_set_bc", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
+                 "bem_set_kernel_timing", "bem_kernel_time", "bem_destroy"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, allow=()):
+    if rc != BEM_OK and rc not in allow:
+        lib = load_library()
+        raise BemError(rc, f"{lib.bem_status_string(rc).decode()}: {lib.bem_last_error().decode()}")
+    return rc
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(0)
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+@dataclass
+class Geometry:
+    dim: int
+    n: int
+    h: float
+    cell: np.ndarray
+    w: np.ndarray
+    normal: np.ndarray
+
+
+class Plan:
+    """Owning wrapper of a bem_plan_t."""
+
+    def __init__(self, dim, n, h, cell, w, normal, kernel="laplace2d", precision="f32", nu=0.3, mu=1.0,
+                 stream=None):
+        lib = load_library()
+        self.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.dim = int(dim)
+        self.ncomp = 3 if self.kernel == BEM_KELVIN_3D else 1
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        normal = np.ascontiguousarray(normal, dtype=np.float64)
+        self.nb = int(cell.shape[0])
+        nn = np.ascontiguousarray(np.full(self.dim, int(n), dtype=np.int64) if np.isscalar(n) else n,
+                                  dtype=np.int64)
+        self._h = ctypes.c_void_p()
+        rc = lib.bem_plan(ctypes.byref(self._h), self.dim, _ptr(nn), float(h), self.nb, _ptr(cell), _ptr(w),
+                          _ptr(normal), self.kernel, float(nu), float(mu), self.precision, 0, _stream_ptr(stream))
+        _check(rc)
+        self.torch_dtype = None
+
+    @classmethod
+    def from_boundary(cls, b, kernel="laplace2d", precision="f32", **kw):
+        return cls(b.dim, b.n, b.h, b.cell, b.w, b.normal, kernel=kernel, precision=precision, **kw)
+
+    # --------------------------------------------------------------- helpers
+    @property
+    def np_dtype(self):
+        return np.float64 if self.precision == BEM_F64 else np.float32
+
+    def _tdtype(self):
+        import torch
+        return torch.float64 if self.precision == BEM_F64 else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().bem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def set_bc(self, bc, c=0.5):
+        bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
+        _check(load_library().bem_set_bc(self._h, _ptr(bc), float(c)))
+
+    def apply(self, layer, x, out=None, stream=None):
+        """Device apply.  x: CUDA tensor of nb*ncomp plan-precision values."""
+        import torch
+        lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
+        if not (isinstance(x, torch.Tensor) and x.is_cuda):
+            raise TypeError("apply expects a CUDA tensor; use apply_host for host arrays")
+        if x.dtype != self._tdtype() or not x.is_contiguous() or x.numel() != self.nb * self.ncomp:
+            raise ValueError("input must be a contiguous tensor of nb*ncomp values in the plan precision")
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load_library().bem_apply(self._h, lay, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                        _stream_ptr(stream)))
+        return out
+
+    def apply_host(self, layer, x, out=None, stream=None):
+        lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
+        x = np.ascontiguousarray(x, dtype=self.np_dtype).reshape(-1)
+        if x.size != self.nb * self.ncomp:
+            raise ValueError("input must hold nb*ncomp values")
+        if out is None:
+            out = np.empty_like(x)
+        _check(load_library().bem_apply_host(self._h, lay, _ptr(x), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def solve(self, bc, data, c=0.5, tol=1e-6, max_iter=2000, restart=50, x0=None, stream=None,
+              raise_on_nonconvergence=False):
+        bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
+        data = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)
+        m = self.nb * self.ncomp
+        if bc.size != m or data.size != m:
+            raise ValueError("bc and data must hold nb*ncomp values")
+        u = np.empty(m)
+        q = np.empty(m)
+        x0p = None
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+            x0p = _ptr(x0)
+        info = SolveInfo()
+        rc = load_library().bem_solve(self._h, _ptr(bc), _ptr(data), float(c), float(tol), int(max_iter),
+                                      int(restart), x0p, _ptr(u), _ptr(q), ctypes.byref(info), _stream_ptr(stream))
+        allow = () if raise_on_nonconvergence else (BEM_ERR_NOT_CONVERGED,)
+        _check(rc, allow)
+        d = info.as_dict()
+        d["status"] = rc
+        return u, q, d
+
+    def info(self):
+        pi = PlanInfo()
+        _check(load_library().bem_get_info(self._h, ctypes.byref(pi)))
+        return pi.as_dict()
+
+    def set_kernel_timing(self, enable: bool):
+        _check(load_library().bem_set_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(load_library().bem_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+    def launches_per_apply(self, layer="system"):
+        lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
+        return int(load_library().bem_launches_per_apply(self._h, lay))
+
+
+def bem_plan(dim, n, h, cell, w, normal, kernel="laplace2d", precision="f32", nu=0.3, mu=1.0, stream=None):
+    return Plan(dim, n, h, cell, w, normal, kernel, precision, nu, mu, stream)
+
+
+def bem_apply(plan: Plan, layer, x, out=None, stream=None):
+    return plan.apply(layer, x, out, stream)
+
+
+def bem_apply_host(plan: Plan, layer, x, out=None, stream=None):
+    return plan.apply_host(layer, x, out, stream)
+
+
+def bem_set_bc(plan: Plan, bc, c=0.5):
+    return plan.set_bc(bc, c)
+
+
+def bem_solve(plan: Plan, bc, data, c=0.5, tol=1e-6, max_iter=2000, restart=50, x0=None, stream=None):
+    return plan.solve(bc, data, c, tol, max_iter, restart, x0, stream)
+
+
+def bem_destroy(plan: Plan):
+    plan.close()

@@ -1,0 +1,443 @@
+// C ABI entry points (include/bem.h): argument checking, plan construction
+// (cell sorting, boundary metadata, operator field lists, spectra) and
+// dispatch of applies and solves.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "bem_internal.h"
+#include "fft_reg.cuh"
+
+namespace bemfft {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+size_t prec_bytes(const bem_plan_s* p) { return p->prec == BEM_F64 ? sizeof(double) : sizeof(float); }
+
+static bem_status upload_coef(bem_plan_s* p, Operator& op, const std::vector<double>& v, const void** dst) {
+  void* d = nullptr;
+  const size_t tb = prec_bytes(p);
+  BEM_CUDA_TRY(cudaMalloc(&d, v.size() * tb));
+  if (p->prec == BEM_F64) {
+    BEM_CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * tb, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(v.begin(), v.end());
+    BEM_CUDA_TRY(cudaMemcpy(d, f.data(), f.size() * tb, cudaMemcpyHostToDevice));
+  }
+  op.owned.push_back(d);
+  *dst = d;
+  return BEM_OK;
+}
+
+static void free_operator(Operator& op) {
+  for (void* d : op.owned) cudaFree(d);
+  op.owned.clear();
+  op.nf = 0;
+  op.diag = nullptr;
+}
+
+// Laplace 2D operators.  Spectra: 0 = U, 1 = Q_x, 2 = Q_y.
+static bem_status build_ops_2d(bem_plan_s* p) {
+  const int64_t nb = p->nb;
+  std::vector<double> w(p->h_w), wx(nb), wy(nb);
+  for (int64_t j = 0; j < nb; ++j) {
+    wx[j] = p->h_w[j] * p->h_normal[2 * j];
+    wy[j] = p->h_w[j] * p->h_normal[2 * j + 1];
+  }
+  bem_status rc;
+  Operator& s = p->op_single;
+  s.nf = 1;
+  s.f[0] = {nullptr, 0, 0, 0};
+  if ((rc = upload_coef(p, s, w, &s.f[0].coef)) != BEM_OK) return rc;
+  Operator& d = p->op_double;
+  d.nf = 2;
+  d.f[0] = {nullptr, 0, 1, 0};
+  d.f[1] = {nullptr, 0, 2, 0};
+  if ((rc = upload_coef(p, d, wx, &d.f[0].coef)) != BEM_OK) return rc;
+  if ((rc = upload_coef(p, d, wy, &d.f[1].coef)) != BEM_OK) return rc;
+  return BEM_OK;
+}
+
+}  // namespace bemfft
+
+using namespace bemfft;
+
+static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h, int64_t nb, const int32_t* cell,
+                            const double* w, const double* normal, bem_kernel kernel, double nu, double mu,
+                            bem_precision prec, uint32_t flags, void* stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out || !n || !cell || !w || !normal) {
+    set_error("bem_plan: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  *out = nullptr;
+  if (kernel != BEM_LAPLACE_2D && kernel != BEM_LAPLACE_3D && kernel != BEM_KELVIN_3D) {
+    set_error("bem_plan: unknown kernel");
+    return BEM_ERR_ARG;
+  }
+  if ((kernel == BEM_LAPLACE_2D) != (dim == 2) || (dim != 2 && dim != 3)) {
+    set_error("bem_plan: dimension does not match the kernel");
+    return BEM_ERR_ARG;
+  }
+  if (prec != BEM_F64 && prec != BEM_F32) {
+    set_error("bem_plan: unknown precision");
+    return BEM_ERR_ARG;
+  }
+  if (flags != 0) {
+    set_error("bem_plan: flags must be 0");
+    return BEM_ERR_ARG;
+  }
+  if (!(h > 0.0) || !std::isfinite(h) || nb < 1 || nb > (int64_t)1 << 30) {
+    set_error("bem_plan: need h > 0 and 1 <= nb <= 2^30");
+    return BEM_ERR_ARG;
+  }
+  for (int a = 0; a < dim; ++a)
+    if (n[a] < 1) {
+      set_error("bem_plan: grid size must be positive");
+      return BEM_ERR_ARG;
+    }
+  for (int a = 1; a < dim; ++a)
+    if (n[a] != n[0]) {
+      set_error("bem_plan: unequal grid sizes per axis are not supported");
+      return BEM_ERR_UNSUPPORTED;
+    }
+  const int64_t nn = n[0];
+  if ((nn & (nn - 1)) != 0 || nn < 4) {
+    set_error("bem_plan: n must be a power of two >= 4");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  if (kernel != BEM_LAPLACE_2D) {
+    set_error("bem_plan: 3D kernels are not available in this build");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  if (kernel == BEM_KELVIN_3D && (!(mu > 0.0) || !(nu < 0.5) || !(nu > -1.0))) {
+    set_error("bem_plan: need mu > 0 and -1 < nu < 1/2");
+    return BEM_ERR_ARG;
+  }
+  // validate cells, weights, normals
+  for (int64_t j = 0; j < nb; ++j) {
+    for (int a = 0; a < dim; ++a) {
+      const int32_t g = cell[j * dim + a];
+      if (g < 0 || g >= nn) {
+        set_error("bem_plan: cell index outside the grid");
+        return BEM_ERR_ARG;
+      }
+      if (!std::isfinite(normal[j * dim + a])) {
+        set_error("bem_plan: non-finite normal");
+        return BEM_ERR_ARG;
+      }
+    }
+    if (!std::isfinite(w[j])) {
+      set_error("bem_plan: non-finite weight");
+      return BEM_ERR_ARG;
+    }
+  }
+  auto* p = new bem_plan_s();
+  p->dim = dim;
+  p->ncomp = kernel == BEM_KELVIN_3D ? 3 : 1;
+  p->kernel = kernel;
+  p->prec = prec;
+  p->n = nn;
+  p->N = 2 * nn;
+  p->log2N = 0;
+  while ((int64_t(1) << p->log2N) < p->N) ++p->log2N;
+  p->nb = nb;
+  p->h = h;
+  p->nu = nu;
+  p->mu = mu;
+  cudaGetDevice(&p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // sort cells by row (y), then x; reject duplicates
+  std::vector<int32_t> perm(nb);
+  std::iota(perm.begin(), perm.end(), 0);
+  auto key = [&](int32_t j) { return (int64_t)cell[(int64_t)j * dim + 1] * nn + cell[(int64_t)j * dim]; };
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
+  for (int64_t j = 1; j < nb; ++j)
+    if (key(perm[j]) == key(perm[j - 1])) {
+      set_error("bem_plan: duplicate boundary cell");
+      delete p;
+      return BEM_ERR_ARG;
+    }
+  std::vector<int32_t> rowptr(nn + 1, 0), col(nb);
+  p->h_w.resize(nb);
+  p->h_normal.resize(nb * dim);
+  for (int64_t j = 0; j < nb; ++j) {
+    const int32_t u = perm[j];
+    rowptr[cell[(int64_t)u * dim + 1] + 1]++;
+    col[j] = cell[(int64_t)u * dim];
+    p->h_w[j] = w[u];
+    for (int a = 0; a < dim; ++a) p->h_normal[j * dim + a] = normal[(int64_t)u * dim + a];
+  }
+  for (int64_t r = 0; r < nn; ++r) rowptr[r + 1] += rowptr[r];
+  p->h_perm = perm;
+  p->nlines = nn;
+
+  auto fail = [&](bem_status rc) {
+    bem_destroy(p);
+    return rc;
+  };
+#define PLAN_CUDA(expr)                                                          \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));            \
+      return fail(_e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA); \
+    }                                                                            \
+  } while (0)
+  PLAN_CUDA(cudaMalloc(&p->d_perm, nb * sizeof(int32_t)));
+  PLAN_CUDA(cudaMalloc(&p->d_rowptr, (nn + 1) * sizeof(int32_t)));
+  PLAN_CUDA(cudaMalloc(&p->d_col, nb * sizeof(int32_t)));
+  PLAN_CUDA(cudaMemcpy(p->d_perm, perm.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice));
+  PLAN_CUDA(cudaMemcpy(p->d_rowptr, rowptr.data(), (nn + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  PLAN_CUDA(cudaMemcpy(p->d_col, col.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice));
+
+  // quarter-wave twiddles e^{2 pi i r / N}, FP64 on the host, rounded once
+  {
+    const int64_t N = p->N;
+    const double PI = 3.14159265358979323846;
+    if (prec == BEM_F64) {
+      std::vector<cplx<double>> q(N / 4);
+      for (int64_t r = 0; r < N / 4; ++r) q[r] = {std::cos(2.0 * PI * r / N), std::sin(2.0 * PI * r / N)};
+      PLAN_CUDA(cudaMalloc(&p->d_qtab, q.size() * sizeof(q[0])));
+      PLAN_CUDA(cudaMemcpy(p->d_qtab, q.data(), q.size() * sizeof(q[0]), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<cplx<float>> q(N / 4);
+      for (int64_t r = 0; r < N / 4; ++r)
+        q[r] = {(float)std::cos(2.0 * PI * r / N), (float)std::sin(2.0 * PI * r / N)};
+      PLAN_CUDA(cudaMalloc(&p->d_qtab, q.size() * sizeof(q[0])));
+      PLAN_CUDA(cudaMemcpy(p->d_qtab, q.data(), q.size() * sizeof(q[0]), cudaMemcpyHostToDevice));
+    }
+  }
+  bem_status rc = compute_spectra_2d(p, st);
+  if (rc != BEM_OK) return fail(rc);
+  if ((rc = build_ops_2d(p)) != BEM_OK) return fail(rc);
+  if ((rc = setup_apply_2d(p)) != BEM_OK) return fail(rc);
+  PLAN_CUDA(cudaStreamSynchronize(st));
+#undef PLAN_CUDA
+  p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return BEM_OK;
+}
+
+extern "C" {
+
+bem_status bem_plan(bem_plan_t* out, int dim, const int64_t* n, double h, int64_t nb, const int32_t* cell,
+                    const double* w, const double* normal, bem_kernel kernel, double nu, double mu,
+                    bem_precision prec, uint32_t flags, void* stream) {
+  return plan_impl(out, dim, n, h, nb, cell, w, normal, kernel, nu, mu, prec, flags, stream);
+}
+
+bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
+  if (!p || !bc) {
+    set_error("bem_set_bc: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  if (!std::isfinite(c)) {
+    set_error("bem_set_bc: c must be finite");
+    return BEM_ERR_ARG;
+  }
+  const int64_t nb = p->nb;
+  for (int64_t i = 0; i < nb * p->ncomp; ++i)
+    if (bc[i] > 1) {
+      set_error("bem_set_bc: bc entries must be 0 or 1");
+      return BEM_ERR_ARG;
+    }
+  if (p->have_bc && c == p->c && std::equal(p->h_bc.begin(), p->h_bc.end(), bc)) return BEM_OK;
+  free_operator(p->op_system);
+  p->h_bc.assign(bc, bc + nb * p->ncomp);
+  p->c = c;
+  Operator& s = p->op_system;
+  bem_status rc;
+  if (p->kernel == BEM_LAPLACE_2D) {
+    // A x = S(x m_D) + D(x m_N) - c x m_N   (Eq. 15 with the BC split)
+    std::vector<double> aq(nb), ax(nb), ay(nb), dg(nb);
+    for (int64_t j = 0; j < nb; ++j) {
+      const int32_t u = p->h_perm[j];
+      const double mN = bc[u] ? 1.0 : 0.0, mD = 1.0 - mN;
+      aq[j] = p->h_w[j] * mD;
+      ax[j] = p->h_w[j] * p->h_normal[2 * j] * mN;
+      ay[j] = p->h_w[j] * p->h_normal[2 * j + 1] * mN;
+    }
+    for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;  // user order
+    s.nf = 3;
+    s.f[0] = {nullptr, 0, 0, 0};
+    s.f[1] = {nullptr, 0, 1, 0};
+    s.f[2] = {nullptr, 0, 2, 0};
+    if ((rc = upload_coef(p, s, aq, &s.f[0].coef)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, ax, &s.f[1].coef)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, ay, &s.f[2].coef)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+  } else {
+    set_error("bem_set_bc: kernel not available");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  p->have_bc = true;
+  return BEM_OK;
+}
+
+bem_status bem_apply(bem_plan_t p, bem_layer layer, const void* in_dev, void* out_dev, void* stream) {
+  if (!p || !in_dev || !out_dev) {
+    set_error("bem_apply: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  if (in_dev == out_dev) {
+    set_error("bem_apply: input and output must not alias");
+    return BEM_ERR_ARG;
+  }
+  return apply_operator(p, layer, in_dev, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+bem_status bem_apply_host(bem_plan_t p, bem_layer layer, const void* in_host, void* out_host, void* stream) {
+  if (!p || !in_host || !out_host) {
+    set_error("bem_apply_host: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)p->nb * p->ncomp * prec_bytes(p);
+  if (!p->d_tin) {
+    BEM_CUDA_TRY(cudaMalloc(&p->d_tin, bytes));
+    BEM_CUDA_TRY(cudaMalloc(&p->d_tout, bytes));
+  }
+  BEM_CUDA_TRY(cudaMemcpyAsync(p->d_tin, in_host, bytes, cudaMemcpyHostToDevice, st));
+  bem_status rc = apply_operator(p, layer, p->d_tin, p->d_tout, st);
+  if (rc != BEM_OK) return rc;
+  BEM_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_tout, bytes, cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return BEM_OK;
+}
+
+bem_status bem_solve(bem_plan_t p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
+                     int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
+                     void* stream) {
+  if (!p || !bc || !data) {
+    set_error("bem_solve: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  return solve_gmres(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info,
+                     static_cast<cudaStream_t>(stream));
+}
+
+bem_status bem_get_info(bem_plan_t p, bem_plan_info* info) {
+  if (!p || !info) {
+    set_error("bem_get_info: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  info->dim = p->dim;
+  info->ncomp = p->ncomp;
+  info->n = p->n;
+  info->N = p->N;
+  info->nb = p->nb;
+  info->precision = p->prec;
+  info->grid_ctas = p->grid;
+  info->threads_per_cta = p->threads;
+  info->scratch_bytes = p->scratch_bytes;
+  info->spectra_bytes = p->spectra_bytes;
+  info->plan_seconds = p->plan_seconds;
+  return BEM_OK;
+}
+
+bem_status bem_set_kernel_timing(bem_plan_t p, int enable) {
+  if (!p) {
+    set_error("bem_set_kernel_timing: null plan");
+    return BEM_ERR_ARG;
+  }
+  p->timing = enable != 0;
+  p->ev_used = 0;
+  p->timed_ms = 0;
+  p->timed_launches = 0;
+  return BEM_OK;
+}
+
+bem_status bem_kernel_time(bem_plan_t p, double* total_ms, int64_t* launches) {
+  if (!p || !total_ms || !launches) {
+    set_error("bem_kernel_time: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  for (int i = 0; i + 1 < p->ev_used; i += 2) {
+    BEM_CUDA_TRY(cudaEventSynchronize(p->ev_pool[i + 1]));
+    float ms = 0.f;
+    BEM_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]));
+    p->timed_ms += ms;
+    p->timed_launches += 1;
+  }
+  p->ev_used = 0;
+  *total_ms = p->timed_ms;
+  *launches = p->timed_launches;
+  return BEM_OK;
+}
+
+int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
+  (void)layer;
+  if (!p) return -1;
+  return 3;  // prep (weighted densities), fused column kernel, reduction
+}
+
+bem_status bem_destroy(bem_plan_t p) {
+  if (!p) return BEM_OK;
+  cudaFree(p->d_perm);
+  cudaFree(p->d_rowptr);
+  cudaFree(p->d_col);
+  cudaFree(p->d_line);
+  cudaFree(p->d_qtab);
+  for (auto& s : p->spectra) cudaFree(s.data);
+  free_operator(p->op_single);
+  free_operator(p->op_double);
+  free_operator(p->op_system);
+  cudaFree(p->d_rho);
+  cudaFree(p->d_partial);
+  for (auto e : p->ev_pool) cudaEventDestroy(e);
+  cudaFree(p->d_V);
+  cudaFree(p->d_vec);
+  cudaFree(p->d_small);
+  cudaFree(p->d_tin);
+  cudaFree(p->d_tout);
+  delete p;
+  return BEM_OK;
+}
+
+const char* bem_status_string(bem_status s) {
+  switch (s) {
+    case BEM_OK: return "ok";
+    case BEM_ERR_ARG: return "invalid argument";
+    case BEM_ERR_CUDA: return "CUDA error";
+    case BEM_ERR_OOM: return "out of device memory";
+    case BEM_ERR_NOT_CONVERGED: return "not converged";
+    case BEM_ERR_BREAKDOWN: return "GMRES breakdown";
+    case BEM_ERR_NONFINITE: return "non-finite value";
+    case BEM_ERR_TIMEOUT: return "device wait timed out";
+    case BEM_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* bem_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+namespace bemfft {
+
+bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st) {
+  const Operator* op = nullptr;
+  if (layer == BEM_SINGLE) op = &p->op_single;
+  else if (layer == BEM_DOUBLE) op = &p->op_double;
+  else if (layer == BEM_SYSTEM) {
+    if (!p->have_bc) {
+      set_error("bem_apply: BEM_SYSTEM needs bem_set_bc first");
+      return BEM_ERR_ARG;
+    }
+    op = &p->op_system;
+  } else {
+    set_error("bem_apply: unknown layer");
+    return BEM_ERR_ARG;
+  }
+  return launch_apply_2d(p, *op, in, out, st);
+}
+
+}  // namespace bemfft

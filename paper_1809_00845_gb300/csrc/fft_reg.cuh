@@ -1,0 +1,245 @@
+// Register-resident mixed-radix Stockham FFT for one line per CTA (sm_103a).
+//
+// A length-N line (N a power of two) is spread over TT = N/E threads, thread t
+// holding the E elements at positions t + m*TT (m = 0..E-1) in registers.  A
+// pass of radix R (R | E) performs E/R butterflies per thread: butterfly
+// b = t + s*TT reads positions b + r*N/R, i.e. registers s + r*E/R, so the
+// register <-> position map is the same in every pass.  Between passes the
+// data goes through shared memory (Stockham autosort order, padded by one
+// element every 16 to keep both the strided writes of the first pass and
+// the unit-stride reads conflict-free).  The last pass writes its outputs
+// back in place: afterwards register m holds frequency t + m*TT in natural
+// order, which is exactly the register map the first pass of the inverse
+// transform reads.  That lets the spectral multiply (Eq. 16) run on registers
+// between the forward and inverse transforms with no shared-memory round trip.
+//
+// Twiddles come from a quarter-wave table of e^{2 pi i r/N}, r in [0, N/4),
+// computed in FP64 on the host and rounded once to the working precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bemfft {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
+
+// multiply by e^{DIR i pi/2} = DIR * i
+template <int DIR, typename T>
+__device__ __forceinline__ cplx<T> mul_i(cplx<T> a) {
+  if constexpr (DIR > 0) return {-a.y, a.x};
+  else return {a.y, -a.x};
+}
+
+// cos and sin of 2 pi j / 32 (j = 0..8); other octants by symmetry.
+__device__ __forceinline__ double cos32(int j) {
+  switch (j) {
+    case 0: return 1.0;
+    case 1: return 0.98078528040323044913;
+    case 2: return 0.92387953251128675613;
+    case 3: return 0.83146961230254523708;
+    case 4: return 0.70710678118654752440;
+    case 5: return 0.55557023301960222474;
+    case 6: return 0.38268343236508977173;
+    case 7: return 0.19509032201612826785;
+    default: return 0.0;
+  }
+}
+
+// a * e^{DIR 2 pi i m / R} for a compile-time-foldable m (after unrolling).
+template <int R, int DIR, typename T>
+__device__ __forceinline__ cplx<T> twc(cplx<T> a, int m) {
+  m = m % R;
+  if (m == 0) return a;
+  if (4 * m == R) return mul_i<DIR>(a);
+  if (2 * m == R) return {-a.x, -a.y};
+  if (4 * m == 3 * R) return mul_i<-DIR>(a);
+  const int j = (32 / R) * m;  // angle 2 pi j / 32
+  const int q = j >> 3, r = j & 7;
+  // e^{i 2 pi j/32} = i^q e^{i 2 pi r/32}
+  T c = (T)cos32(r), s = (T)cos32(8 - r);
+  cplx<T> w;
+  if (q == 0) w = {c, s};
+  else if (q == 1) w = {-s, c};
+  else if (q == 2) w = {-c, -s};
+  else w = {s, -c};
+  if (DIR < 0) w.y = -w.y;
+  if (r == 4) {
+    // (+-h +- i h): two multiplies
+    const T hh = (T)0.70710678118654752440;
+    T sx = w.x > 0 ? (T)1 : (T)-1, sy = w.y > 0 ? (T)1 : (T)-1;
+    // (a.x + i a.y)(sx h + i sy h) = h[(sx a.x - sy a.y) + i(sy a.x + sx a.y)]
+    T re = sx * a.x - sy * a.y, im = sy * a.x + sx * a.y;
+    return {re * hh, im * hh};
+  }
+  return cmul(a, w);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft2(cplx<T>& a, cplx<T>& b) {
+  cplx<T> t = a;
+  a = t + b;
+  b = t - b;
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
+  cplx<T> s0 = a0 + a2, d0 = a0 - a2, s1 = a1 + a3, d1 = mul_i<DIR>(a1 - a3);
+  a0 = s0 + s1;
+  a2 = s0 - s1;
+  a1 = d0 + d1;
+  a3 = d0 - d1;
+}
+
+// In-place DFT of R registers: a[k] <- sum_r a[r] e^{DIR 2 pi i r k / R}.
+// R = R1 * R2 split: R1-point DFTs on stride-R2 subsequences, twiddles,
+// R2-point DFTs, transposed read-out (register renaming after unrolling).
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft(cplx<T> (&a)[R]) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<DIR>(a[0], a[1]);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(a[0], a[1], a[2], a[3]);
+  } else {
+    constexpr int R1 = 4;
+    constexpr int R2 = R / R1;
+#pragma unroll
+    for (int r2 = 0; r2 < R2; ++r2) {
+      cplx<T> t[R1];
+#pragma unroll
+      for (int r1 = 0; r1 < R1; ++r1) t[r1] = a[r2 + R2 * r1];
+      dft<R1, DIR>(t);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) a[r2 + R2 * k1] = t[k1];
+    }
+#pragma unroll
+    for (int r2 = 1; r2 < R2; ++r2)
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) a[r2 + R2 * k1] = twc<R, DIR>(a[r2 + R2 * k1], r2 * k1);
+    cplx<T> o[R];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      cplx<T> t[R2];
+#pragma unroll
+      for (int r2 = 0; r2 < R2; ++r2) t[r2] = a[r2 + R2 * k1];
+      dft<R2, DIR>(t);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = t[k2];
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = o[i];
+  }
+}
+
+// Quarter-wave twiddle table of e^{2 pi i r / N}, r < N/4.
+template <typename T>
+struct Twiddles {
+  const cplx<T>* q;  // N/4 entries (shared or global)
+  int log2q;         // log2(N/4)
+  // e^{DIR 2 pi i m / N} for m in [0, N)
+  template <int DIR>
+  __device__ __forceinline__ cplx<T> get(int m) const {
+    const int quad = m >> log2q;
+    const cplx<T> t = q[m & ((1 << log2q) - 1)];
+    cplx<T> w;
+    // rotate by i^quad
+    w.x = (quad & 1) ? -t.y : t.x;
+    w.y = (quad & 1) ? t.x : t.y;
+    if (quad & 2) {
+      w.x = -w.x;
+      w.y = -w.y;
+    }
+    if constexpr (DIR < 0) w.y = -w.y;
+    return w;
+  }
+};
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// One Stockham pass of radix R on the register set v (E per thread).
+// Ns: product of the radices of the previous passes.  If LAST, outputs stay
+// in registers (natural order); otherwise they go to smem and are read back.
+template <int E, int R, int DIR, bool LAST, typename T>
+__device__ __forceinline__ void stockham_pass(cplx<T> (&v)[E], const int t, const int TT, const int Ns,
+                                              const int log2N, const Twiddles<T>& tw, cplx<T>* sbuf) {
+  constexpr int S = E / R;
+  const int N = 1 << log2N;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int b = t + s * TT;
+    const int k = b & (Ns - 1);
+    cplx<T> u[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = v[s + r * S];
+    if (Ns > 1) {
+      // twiddle e^{DIR 2 pi i k r / (Ns R)} = table index k r N/(Ns R) < N
+      const int m1 = k * (N / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw.template get<DIR>(m1 * r));
+    }
+    dft<R, DIR>(u);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[s + r * S] = u[r];
+    } else {
+      const int base = (b - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sbuf[pad16(base + r * Ns)] = u[r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = sbuf[pad16(t + m * TT)];
+    __syncthreads();
+  }
+}
+
+// Full transform of one line held in registers (positions t + m*TT) with
+// radix-E passes followed by one smaller last pass when log2(N) is not a
+// multiple of log2(E).  Result in natural order in the same register map.
+template <int E, int DIR, typename T>
+__device__ __forceinline__ void fft_line(cplx<T> (&v)[E], const int t, const int TT, const int log2N,
+                                         const Twiddles<T>& tw, cplx<T>* sbuf) {
+  constexpr int LE = (E == 16) ? 4 : (E == 8) ? 3 : (E == 4) ? 2 : 1;
+  const int full = log2N / LE;       // number of radix-E passes possible
+  const int rem = log2N - full * LE;  // leftover bits
+  // passes: (full - (rem == 0)) radix-E passes not last, then the last pass of radix E or 2^rem
+  const int nfirst = rem == 0 ? full - 1 : full;
+  int Ns = 1;
+  for (int p = 0; p < nfirst; ++p) {
+    stockham_pass<E, E, DIR, false>(v, t, TT, Ns, log2N, tw, sbuf);
+    Ns *= E;
+  }
+  if (rem == 0) {
+    stockham_pass<E, E, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+  } else if (rem == 1) {
+    stockham_pass<E, 2, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+  } else if (rem == 2) {
+    if constexpr (E >= 4) stockham_pass<E, 4, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+  } else if (rem == 3) {
+    if constexpr (E >= 8) stockham_pass<E, 8, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+  }
+}
+
+}  // namespace bemfft

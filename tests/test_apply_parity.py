@@ -1,0 +1,144 @@
+"""Parity of the CUDA operator apply with the CPU FP64 oracle (GPU).
+
+Bars: relative L2 <= 1e-12 for FP64 plans and <= 2e-6 for FP32 plans on
+random N(0,1) densities, element by element over every boundary cell.  Sizes
+span one-thread columns (n = 4) through multi-pass transforms with a ragged
+last pass (N = 2n = 2^k with k not a multiple of 4) up to the full 4096^2
+star workload, where the oracle evaluates sampled target rows one by one.
+"""
+import numpy as np
+import pytest
+
+from paper_1809_00845_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_00845_gb300 import build
+    build.build()
+    return torch
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def gpu_apply(torch, plan, layer, x):
+    t = torch.from_numpy(np.asarray(x, dtype=plan.np_dtype)).cuda()
+    y = plan.apply(layer, t)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def _plan(b, prec):
+    from paper_1809_00845_gb300.bem import Plan
+    return Plan.from_boundary(b, "laplace2d", prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,nb", [(4, 5), (8, 17), (16, 40), (32, 77), (64, 300), (128, 901), (256, 1500),
+                                  (512, 2000)])
+def test_random_cells_single_double(torch_cuda, oracle_mod, prec, n, nb):
+    rng = np.random.default_rng(1000 + n)
+    b = I.random_cells(n, nb, rng)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, prec)
+    for layer, lid in (("single", 0), ("double", 1)):
+        ref = oracle_mod.apply("laplace2d", lid, b.cell, b.h, b.w, b.normal, x)
+        out = gpu_apply(torch_cuda, plan, layer, x)
+        assert rel_l2(out, ref) <= TOL[prec], (layer, rel_l2(out, ref))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_system_operator_mixed_bc(torch_cuda, oracle_mod, prec):
+    rng = np.random.default_rng(5)
+    b = I.star_boundary(256)
+    bc = I.mixed_bc_theta(b)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, prec)
+    plan.set_bc(bc, 0.5)
+    ref = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
+    out = gpu_apply(torch_cuda, plan, "system", x)
+    assert rel_l2(out, ref) <= TOL[prec]
+    # switching the BC pattern rebuilds the operator
+    bc2 = 1 - bc
+    plan.set_bc(bc2, 0.25)
+    ref2 = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc2, x, c=0.25)
+    assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref2) <= TOL[prec]
+
+
+def test_circle_config_f64(torch_cuda, oracle_mod):
+    """Circle R = 0.35 on 128^2 (356 cells), FP64, single and double layer."""
+    b = I.circle_boundary(128, 0.35)
+    assert b.nb == 356
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, "f64")
+    for layer, lid in (("single", 0), ("double", 1)):
+        ref = oracle_mod.apply("laplace2d", lid, b.cell, b.h, b.w, b.normal, x)
+        assert rel_l2(gpu_apply(torch_cuda, plan, layer, x), ref) <= 1e-12
+
+
+def test_edge_cases(torch_cuda, oracle_mod):
+    # a single cell: only the singular-cell value; zero weights; a full plane (Eq. 9)
+    from paper_1809_00845_gb300.bem import Plan
+    for prec in ("f64", "f32"):
+        one = I.Boundary(2, 8, np.array([[3, 5]], np.int32), np.array([0.125]), np.array([[0.6, 0.8]]),
+                         np.zeros((1, 2)), np.zeros(1))
+        p = _plan(one, prec)
+        ref = oracle_mod.apply("laplace2d", 0, one.cell, one.h, one.w, one.normal, np.array([2.0]))
+        assert rel_l2(gpu_apply(torch_cuda, p, "single", [2.0]), ref) <= TOL[prec]
+        assert np.max(np.abs(gpu_apply(torch_cuda, p, "double", [2.0]))) <= 1e-12 * abs(ref[0]) * (1e6 if prec == "f32" else 1)
+        rng = np.random.default_rng(9)
+        full = I.full_plane_boundary(16, rng)
+        x = rng.standard_normal(full.nb)
+        p = _plan(full, prec)
+        for layer, lid in (("single", 0), ("double", 1)):
+            ref = oracle_mod.apply("laplace2d", lid, full.cell, full.h, full.w, full.normal, x)
+            assert rel_l2(gpu_apply(torch_cuda, p, layer, x), ref) <= TOL[prec]
+        # cells on the outermost rows/columns of the grid (largest offsets)
+        corners = I.Boundary(2, 16, np.array([[0, 0], [15, 15], [0, 15], [15, 0], [7, 8]], np.int32),
+                             np.full(5, 1 / 16), np.array([[1.0, 0.0]] * 5), np.zeros((5, 2)), np.zeros(5))
+        x = rng.standard_normal(5)
+        p = _plan(corners, prec)
+        for layer, lid in (("single", 0), ("double", 1)):
+            ref = oracle_mod.apply("laplace2d", lid, corners.cell, corners.h, corners.w, corners.normal, x)
+            assert rel_l2(gpu_apply(torch_cuda, p, layer, x), ref) <= TOL[prec]
+
+
+def test_linearity_and_repeatability(torch_cuda):
+    b = I.circle_boundary(256, 0.3)
+    rng = np.random.default_rng(3)
+    x1, x2 = rng.standard_normal(b.nb), rng.standard_normal(b.nb)
+    plan = _plan(b, "f64")
+    y1 = gpu_apply(torch_cuda, plan, "single", x1)
+    y2 = gpu_apply(torch_cuda, plan, "single", x2)
+    y12 = gpu_apply(torch_cuda, plan, "single", 2.0 * x1 - 3.0 * x2)
+    assert rel_l2(y12, 2.0 * y1 - 3.0 * y2) < 1e-13
+    assert np.array_equal(gpu_apply(torch_cuda, plan, "single", x1), y1)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_star_4096_full_size_sampled_rows(torch_cuda, oracle_mod, prec):
+    """The 4096^2 star (padded 8192^2), mixed BCs, in the launch configuration
+    the benchmark times; the oracle evaluates 3 x 256 target rows exactly."""
+    b = I.star_boundary(4096)
+    bc = I.mixed_bc_theta(b)
+    rng = I.rng_for(1)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, prec)
+    plan.set_bc(bc, 0.5)
+    out = gpu_apply(torch_cuda, plan, "system", x)
+    for row0 in (0, b.nb // 2, b.nb - 256):
+        ref = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x, rows=(row0, 256))
+        assert rel_l2(out[row0:row0 + 256], ref) <= TOL[prec], row0
+    s_out = gpu_apply(torch_cuda, plan, "single", x)
+    ref = oracle_mod.apply("laplace2d", 0, b.cell, b.h, b.w, b.normal, x, rows=(1000, 256))
+    assert rel_l2(s_out[1000:1256], ref) <= TOL[prec]

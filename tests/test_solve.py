@@ -1,0 +1,72 @@
+"""GMRES solve on the FFT apply against the oracle's dense LU and direct-sum
+residual (GPU)."""
+import numpy as np
+import pytest
+
+from paper_1809_00845_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_00845_gb300 import build
+    build.build()
+    return torch
+
+
+def _plan(b, prec):
+    from paper_1809_00845_gb300.bem import Plan
+    return Plan.from_boundary(b, "laplace2d", prec)
+
+
+def test_circle_dirichlet_f64_matches_dense_lu(torch_cuda, oracle_mod):
+    """Circle R = 0.35 on 128^2, u = x^2 - y^2 on S, solve for q to 1e-10."""
+    b = I.circle_boundary(128, 0.35)
+    u, q = I.boundary_data(b, I.field_x2y2)
+    bc = np.zeros(b.nb, np.uint8)
+    plan = _plan(b, "f64")
+    u_out, q_out, info = plan.solve(bc, u, tol=1e-10, restart=100, max_iter=1000)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    assert np.array_equal(u_out, u)
+    A, rhs = oracle_mod.system("laplace2d", b.cell, b.h, b.w, b.normal, bc, u, np.zeros(b.nb))
+    x = oracle_mod.solve_lu(A, rhs)
+    assert np.linalg.norm(q_out - x) / np.linalg.norm(x) <= 1e-8
+    # oracle residual of the GPU solution
+    assert np.linalg.norm(A @ q_out - rhs) / np.linalg.norm(rhs) <= 2e-10
+
+
+@pytest.mark.parametrize("prec,tol,bound", [("f64", 1e-10, 2e-10), ("f32", 1e-5, 1e-4)])
+def test_star_mixed_bc_residual(torch_cuda, oracle_mod, prec, tol, bound):
+    b = I.star_boundary(256)
+    u, q = I.boundary_data(b, I.field_expcos)
+    bc = I.mixed_bc_theta(b)
+    data = np.where(bc == 0, u, q)
+    plan = _plan(b, prec)
+    u_out, q_out, info = plan.solve(bc, data, tol=tol, restart=100, max_iter=2000)
+    assert info["status"] == 0, info
+    x = np.where(bc == 0, q_out, u_out)
+    rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, u * (bc == 0), q * (bc == 1))
+    r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) <= bound
+    # known entries are passed through
+    assert np.array_equal(u_out[bc == 0], u[bc == 0]) and np.array_equal(q_out[bc == 1], q[bc == 1])
+
+
+def test_initial_guess_and_iteration_cap(torch_cuda, oracle_mod):
+    b = I.circle_boundary(64, 0.3)
+    u, _ = I.boundary_data(b, I.field_x2y2)
+    bc = np.zeros(b.nb, np.uint8)
+    plan = _plan(b, "f64")
+    _, q1, info1 = plan.solve(bc, u, tol=1e-11, restart=60, max_iter=500)
+    assert info1["status"] == 0
+    # starting from the solution needs no iteration
+    _, q2, info2 = plan.solve(bc, u, tol=1e-9, restart=60, max_iter=500, x0=q1)
+    assert info2["status"] == 0 and info2["iters"] == 0
+    # an iteration cap returns NOT_CONVERGED with the iterate reached so far
+    _, q3, info3 = plan.solve(bc, u, tol=1e-14, restart=5, max_iter=3)
+    assert info3["status"] == 4 and info3["iters"] == 3
+    assert np.all(np.isfinite(q3))
