@@ -27,7 +27,7 @@ KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d":
 PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32}
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
-EXPORTED = ["bem_plan", "bem_set_bc", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
+EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
             "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
             "bem_status_string", "bem_last_error"]
 
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
     P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
     lib.bem_plan.argtypes = [ctypes.POINTER(P), I, P, D, I64, P, P, P, I, D, D, I, ctypes.c_uint32, P]
     lib.bem_set_bc.argtypes = [P, P, D]
+    lib.bem_set_preconditioner.argtypes = [P, I, I]
     lib.bem_apply.argtypes = [P, I, P, P, P]
     lib.bem_apply_host.argtypes = [P, I, P, P, P]
     lib.bem_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
@@ -83,7 +84,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_status_string.restype = ctypes.c_char_p
     lib.bem_last_error.argtypes = []
     lib.bem_last_error.restype = ctypes.c_char_p
-    for name in ("bem_plan", "bem_set_bc", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
+    for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
                  "bem_set_kernel_timing", "bem_kernel_time", "bem_destroy"):
         getattr(lib, name).restype = I
     _lib = lib
@@ -170,6 +171,10 @@ class Plan:
     def set_bc(self, bc, c=0.5):
         bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
         _check(load_library().bem_set_bc(self._h, _ptr(bc), float(c)))
+
+    def set_preconditioner(self, kind="block", block_size=64):
+        k = {"none": 0, "block": 1}[kind] if isinstance(kind, str) else int(kind)
+        _check(load_library().bem_set_preconditioner(self._h, k, int(block_size)))
 
     def apply(self, layer, x, out=None, stream=None):
         """Device apply.  x: CUDA tensor of nb*ncomp plan-precision values."""

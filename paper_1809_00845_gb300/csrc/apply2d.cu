@@ -15,10 +15,15 @@
 // gather).  The padded grid never exists in global memory; the only large
 // stream from HBM is the spectrum ((n+1)^2 reals per kernel table).
 //
-// Each CTA accumulates the contributions of its columns to every boundary
-// cell (one owner thread per grid row, so no atomics), and a small reduction
-// kernel sums the per-CTA partials in FP64 and writes the result in the
-// caller's cell order.
+// Thread t of a CTA owns grid rows t + m*TT (m < E/2): these are exactly the
+// positions its registers hold in the first pass of the forward transform
+// and after the last pass of the inverse one, so the scatter writes and the
+// gather reads registers directly.  Cells are read through a warp-coalesced
+// slot layout (see SlotSet) so each load of the sparse loops is contiguous
+// across a warp and every loop has a warp-uniform trip count.  Each CTA
+// accumulates the contributions of its columns per cell slot (shared memory
+// when it fits, else its own slice of the partial buffer), and a reduction
+// kernel sums the per-CTA partials in FP64 in the caller's cell order.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -30,31 +35,39 @@ namespace bemfft {
 
 template <typename T>
 struct Col2DParams {
-  int n, log2N, nb;
-  const int32_t* rowptr;  // n + 1
-  const int32_t* col;     // nb
-  const T* rho;           // NF * nb
+  int n, log2N, G, H;
   const T* spec[kMaxFields];
   int imag[kMaxFields];
   int oddy[kMaxFields];
+  const int32_t* cnt[kMaxFields];
+  const int32_t* off[kMaxFields];
+  const uint16_t* xs[kMaxFields];
+  const T* rho[kMaxFields];
+  const int32_t* gcnt;
+  const int32_t* goff;
+  const uint16_t* gx;
+  int64_t gnelem;
   const cplx<T>* qtab;  // N/4
-  T* partial;           // gridDim.x * nb
+  T* partial;           // gridDim.x * gnelem
   int acc_in_smem;
 };
 
 template <typename T, int E>
-__device__ __forceinline__ void gather_rows(const cplx<T> (&y)[E], const Col2DParams<T>& p, const int t, const int TT,
-                                            const int kx, const Twiddles<T>& tw, T* acc) {
+__device__ __forceinline__ void gather_rows(const cplx<T> (&y)[E], const Col2DParams<T>& p, const int grp,
+                                            const int lane, const int kx, const Twiddles<T>& tw, T* acc) {
   constexpr int H = E / 2;
   const int N = 1 << p.log2N;
   const T ckx = (kx == 0 || kx == p.n) ? T(1) : T(2);
 #pragma unroll
   for (int m = 0; m < H; ++m) {
-    const int row = t + m * TT;
-    const int j0 = __ldg(p.rowptr + row), j1 = __ldg(p.rowptr + row + 1);
-    for (int j = j0; j < j1; ++j) {
-      const cplx<T> w = tw.template get<+1>((kx * __ldg(p.col + j)) & (N - 1));
-      acc[j] += ckx * (y[m].x * w.x - y[m].y * w.y);
+    const int c = __ldg(p.gcnt + grp * H + m);
+    const int64_t base = (int64_t)__ldg(p.goff + grp * H + m) * p.G + lane;
+    const T yr = ckx * y[m].x, yi = ckx * y[m].y;
+#pragma unroll 4
+    for (int i = 0; i < c; ++i) {
+      const int64_t e = base + (int64_t)i * p.G;
+      const cplx<T> w = tw.template get<+1>((kx * (int)__ldg(p.gx + e)) & (N - 1));
+      acc[e] += yr * w.x - yi * w.y;
     }
   }
 }
@@ -63,12 +76,13 @@ template <typename T, int E, int NF, bool ACCREG>
 __global__ void __launch_bounds__(512) k_col2d(const Col2DParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int t = threadIdx.x, TT = blockDim.x;
-  const int log2N = p.log2N, N = 1 << log2N, n = p.n, nb = p.nb;
+  const int log2N = p.log2N, N = 1 << log2N, n = p.n;
+  const int grp = t / p.G, lane = t - grp * p.G;
   cplx<T>* sbuf = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* sq = sbuf + (N + (N >> 4));
-  T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sq + (N >> 2)) : p.partial + (size_t)blockIdx.x * nb;
+  T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sq + (N >> 2)) : p.partial + (size_t)blockIdx.x * p.gnelem;
   for (int i = t; i < (N >> 2); i += TT) sq[i] = p.qtab[i];
-  for (int j = t; j < nb; j += TT) acc[j] = T(0);
+  for (int64_t e = t; e < p.gnelem; e += TT) acc[e] = T(0);
   __syncthreads();
   const Twiddles<T> tw{sq, log2N - 2};
   constexpr int H = E / 2;
@@ -78,16 +92,19 @@ __global__ void __launch_bounds__(512) k_col2d(const Col2DParams<T> p) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       cplx<T> v[E];
-      const T* rho = p.rho + (size_t)f * nb;
       // scatter fused with the input-pruned forward DFT along x
+      const T* rho = p.rho[f];
+      const uint16_t* xs = p.xs[f];
 #pragma unroll
       for (int m = 0; m < H; ++m) {
-        const int row = t + m * TT;
-        const int j0 = __ldg(p.rowptr + row), j1 = __ldg(p.rowptr + row + 1);
+        const int c = __ldg(p.cnt[f] + grp * H + m);
+        const int64_t base = (int64_t)__ldg(p.off[f] + grp * H + m) * p.G + lane;
         cplx<T> s = {T(0), T(0)};
-        for (int j = j0; j < j1; ++j) {
-          const T r = __ldg(rho + j);
-          const cplx<T> w = tw.template get<-1>((kx * __ldg(p.col + j)) & (N - 1));
+#pragma unroll 4
+        for (int i = 0; i < c; ++i) {
+          const int64_t e = base + (int64_t)i * p.G;
+          const T r = __ldg(rho + e);
+          const cplx<T> w = tw.template get<-1>((kx * (int)__ldg(xs + e)) & (N - 1));
           s.x += r * w.x;
           s.y += r * w.y;
         }
@@ -115,63 +132,152 @@ __global__ void __launch_bounds__(512) k_col2d(const Col2DParams<T> p) {
       }
       if constexpr (!ACCREG) {
         fft_line<E, +1>(v, t, TT, log2N, tw, sbuf);
-        gather_rows<T, E>(v, p, t, TT, kx, tw, acc);
+        gather_rows<T, E>(v, p, grp, lane, kx, tw, acc);
       }
     }
     if constexpr (ACCREG) {
       fft_line<E, +1>(y, t, TT, log2N, tw, sbuf);
-      gather_rows<T, E>(y, p, t, TT, kx, tw, acc);
+      gather_rows<T, E>(y, p, grp, lane, kx, tw, acc);
     }
   }
   if (p.acc_in_smem) {
     __syncthreads();
-    for (int j = t; j < nb; j += TT) p.partial[(size_t)blockIdx.x * nb + j] = acc[j];
+    for (int64_t e = t; e < p.gnelem; e += TT) p.partial[(size_t)blockIdx.x * p.gnelem + e] = acc[e];
   }
 }
 
-// rho_f[j] = coef_f[j] * in[perm[j]*ncomp + comp_f]
+// rho_f[e] = coef_f[cidx[e]] * in[perm[cidx[e]]*ncomp + comp_f]  (0 on padding)
 template <typename T>
 struct PrepParams {
-  int nb, ncomp, nf;
+  int ncomp, nf;
   const int32_t* perm;
   const T* in;
   const T* coef[kMaxFields];
+  const int32_t* cidx[kMaxFields];
+  int64_t nelem[kMaxFields];
   int comp[kMaxFields];
-  T* rho;
+  T* rho[kMaxFields];
 };
 
 template <typename T>
 __global__ void k_prep(const PrepParams<T> p) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.nb) return;
-  const int u = p.perm[j];
-  for (int f = 0; f < p.nf; ++f) p.rho[(size_t)f * p.nb + j] = p.coef[f][j] * p.in[(size_t)u * p.ncomp + p.comp[f]];
+  const int f = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.nelem[f]) return;
+  const int c = p.cidx[f][e];
+  p.rho[f][e] = c >= 0 ? p.coef[f][c] * p.in[(int64_t)p.perm[c] * p.ncomp + p.comp[f]] : T(0);
 }
 
-// out[perm[j]*ncomp + c] = sum_b partial[(b*ncomp + c)*nb + j] + diag * in
+// out[perm[cidx[e]]] = sum_b partial[b][e] + diag * in  over valid slots e
 template <typename T>
-__global__ void k_reduce(const T* __restrict__ partial, int grid, int nb, int ncomp, const int32_t* __restrict__ perm,
-                         const T* __restrict__ diag, const T* __restrict__ in, T* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nb) return;
-  const int u = perm[j];
-  for (int c = 0; c < ncomp; ++c) {
-    double s = 0.0;
-    for (int b = 0; b < grid; ++b) s += (double)partial[((size_t)b * ncomp + c) * nb + j];
-    const size_t o = (size_t)u * ncomp + c;
-    if (diag) s += (double)diag[o] * (double)in[o];
-    out[o] = (T)s;
-  }
+__global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem, const int32_t* __restrict__ cidx,
+                         const int32_t* __restrict__ perm, const T* __restrict__ diag, const T* __restrict__ in,
+                         T* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nelem) return;
+  const int c = cidx[e];
+  if (c < 0) return;
+  double s = 0.0;
+  for (int b = 0; b < grid; ++b) s += (double)partial[(size_t)b * nelem + e];
+  const int u = perm[c];
+  if (diag) s += (double)diag[u] * (double)in[u];
+  out[u] = (T)s;
 }
 
 // ------------------------------------------------------------------ host side
 
 static int elems_per_thread(int log2N) { return log2N >= 8 ? 16 : 8; }
 
+void free_slot_set(SlotSet* s) {
+  cudaFree(s->d_cnt);
+  cudaFree(s->d_off);
+  cudaFree(s->d_x);
+  cudaFree(s->d_cidx);
+  *s = SlotSet();
+}
+
+bem_status build_slot_set(bem_plan_s* p, const std::vector<uint8_t>& member, SlotSet* s) {
+  const int E = elems_per_thread(p->log2N);
+  const int TT = (int)(p->N / E), H = E / 2;
+  const int G = TT < 32 ? TT : 32;
+  const int ngroups = TT / G;
+  // cells per row (rows sorted, x ascending within a row)
+  const int64_t n = p->n;
+  std::vector<int32_t> rowbeg(n + 1, 0);
+  for (int64_t j = 0; j < p->nb; ++j)
+    if (member[j]) rowbeg[p->h_row[j] + 1]++;
+  for (int64_t r = 0; r < n; ++r) rowbeg[r + 1] += rowbeg[r];
+  std::vector<int32_t> rowcells(rowbeg[n]);
+  {
+    std::vector<int32_t> fill(rowbeg.begin(), rowbeg.end() - 1);
+    for (int64_t j = 0; j < p->nb; ++j)
+      if (member[j]) rowcells[fill[p->h_row[j]]++] = (int32_t)j;
+  }
+  std::vector<int32_t> cnt((size_t)ngroups * H), off((size_t)ngroups * H);
+  int64_t total = 0;
+  for (int g = 0; g < ngroups; ++g)
+    for (int m = 0; m < H; ++m) {
+      int mx = 0;
+      for (int l = 0; l < G; ++l) {
+        const int64_t row = (int64_t)(g * G + l) + (int64_t)m * TT;
+        mx = std::max(mx, rowbeg[row + 1] - rowbeg[row]);
+      }
+      cnt[(size_t)g * H + m] = mx;
+      off[(size_t)g * H + m] = (int32_t)total;
+      total += mx;
+    }
+  if (total * G >= ((int64_t)1 << 31)) {
+    set_error("slot layout too large");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  const int64_t nelem = std::max<int64_t>(1, total * G);
+  std::vector<uint16_t> xs(nelem, 0);
+  std::vector<int32_t> cidx(nelem, -1);
+  for (int g = 0; g < ngroups; ++g)
+    for (int m = 0; m < H; ++m)
+      for (int l = 0; l < G; ++l) {
+        const int64_t row = (int64_t)(g * G + l) + (int64_t)m * TT;
+        const int64_t base = (int64_t)off[(size_t)g * H + m] * G + l;
+        for (int i = 0; i < rowbeg[row + 1] - rowbeg[row]; ++i) {
+          const int32_t j = rowcells[rowbeg[row] + i];
+          xs[base + (int64_t)i * G] = (uint16_t)p->h_col[j];
+          cidx[base + (int64_t)i * G] = j;
+        }
+      }
+  free_slot_set(s);
+  s->ngroups = ngroups;
+  s->G = G;
+  s->H = H;
+  s->nelem = nelem;
+  BEM_CUDA_TRY(cudaMalloc(&s->d_cnt, cnt.size() * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMalloc(&s->d_off, off.size() * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMalloc(&s->d_x, nelem * sizeof(uint16_t)));
+  BEM_CUDA_TRY(cudaMalloc(&s->d_cidx, nelem * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMemcpy(s->d_cnt, cnt.data(), cnt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMemcpy(s->d_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMemcpy(s->d_x, xs.data(), nelem * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMemcpy(s->d_cidx, cidx.data(), nelem * sizeof(int32_t), cudaMemcpyHostToDevice));
+  s->h_cidx = std::move(cidx);
+  return BEM_OK;
+}
+
+bem_status alloc_field_rho(bem_plan_s* p, Operator& op) {
+  for (int f = 0; f < op.nf; ++f) {
+    void* d = nullptr;
+    const size_t bytes = (size_t)op.f[f].set->nelem * prec_bytes(p);
+    BEM_CUDA_TRY(cudaMalloc(&d, bytes));
+    BEM_CUDA_TRY(cudaMemset(d, 0, bytes));
+    op.owned.push_back(d);
+    op.f[f].rho = d;
+    p->scratch_bytes += bytes;
+  }
+  return BEM_OK;
+}
+
 template <typename T>
-static size_t smem_2d(int64_t N, int64_t nb, bool acc) {
+static size_t smem_2d(int64_t N, int64_t nelem, bool acc) {
   size_t s = (size_t)(N + N / 16) * sizeof(cplx<T>) + (size_t)(N / 4) * sizeof(cplx<T>);
-  if (acc) s += (size_t)nb * sizeof(T);
+  if (acc) s += (size_t)nelem * sizeof(T);
   return s;
 }
 
@@ -197,15 +303,19 @@ static cudaError_t configure_all(size_t smem, int threads, int* bps) {
 
 template <typename T>
 static bem_status setup_t(bem_plan_s* p) {
-  const int64_t N = p->N, nb = p->nb;
+  const int64_t N = p->N;
   const int E = elems_per_thread(p->log2N);
   p->threads = (int)(N / E);
+  std::vector<uint8_t> all(p->nb, 1);
+  bem_status rc = build_slot_set(p, all, &p->all_set);
+  if (rc != BEM_OK) return rc;
+  const int64_t nelem = p->all_set.nelem;
   int dev = 0, nsm = 0, smem_optin = 0;
   BEM_CUDA_TRY(cudaGetDevice(&dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  p->acc_in_smem = smem_2d<T>(N, nb, true) <= (size_t)smem_optin;
-  p->smem_bytes = smem_2d<T>(N, nb, p->acc_in_smem);
+  p->acc_in_smem = smem_2d<T>(N, nelem, true) <= (size_t)smem_optin;
+  p->smem_bytes = smem_2d<T>(N, nelem, p->acc_in_smem);
   if (p->smem_bytes > (size_t)smem_optin) {
     set_error("grid too large for the shared-memory column buffer");
     return BEM_ERR_UNSUPPORTED;
@@ -221,9 +331,8 @@ static bem_status setup_t(bem_plan_s* p) {
   }
   p->grid = (int)std::min<int64_t>((int64_t)bps * nsm, p->n + 1);
   const size_t tb = sizeof(T);
-  BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * nb * p->ncomp * tb));
-  BEM_CUDA_TRY(cudaMalloc(&p->d_rho, (size_t)kMaxFields * nb * tb));
-  p->scratch_bytes = (size_t)p->grid * nb * p->ncomp * tb + (size_t)kMaxFields * nb * tb;
+  BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * nelem * p->ncomp * tb));
+  p->scratch_bytes += (size_t)p->grid * nelem * p->ncomp * tb;
   return BEM_OK;
 }
 
@@ -250,34 +359,43 @@ static void launch_col_nf(const bem_plan_s* p, int nf, const Col2DParams<T>& cp,
 
 template <typename T>
 static bem_status launch_t(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st) {
-  const int nb = (int)p->nb;
   PrepParams<T> pp{};
-  pp.nb = nb;
   pp.ncomp = p->ncomp;
   pp.nf = op.nf;
   pp.perm = p->d_perm;
   pp.in = static_cast<const T*>(in);
-  pp.rho = static_cast<T*>(p->d_rho);
+  int64_t maxe = 1;
   for (int f = 0; f < op.nf; ++f) {
     pp.coef[f] = static_cast<const T*>(op.f[f].coef);
+    pp.cidx[f] = op.f[f].set->d_cidx;
+    pp.nelem[f] = op.f[f].set->nelem;
     pp.comp[f] = op.f[f].comp;
+    pp.rho[f] = static_cast<T*>(op.f[f].rho);
+    maxe = std::max(maxe, op.f[f].set->nelem);
   }
   const int tb = 256;
-  k_prep<T><<<(nb + tb - 1) / tb, tb, 0, st>>>(pp);
+  k_prep<T><<<dim3((unsigned)((maxe + tb - 1) / tb), op.nf), tb, 0, st>>>(pp);
 
+  const SlotSet& ga = p->all_set;
   Col2DParams<T> cp{};
   cp.n = (int)p->n;
   cp.log2N = p->log2N;
-  cp.nb = nb;
-  cp.rowptr = p->d_rowptr;
-  cp.col = p->d_col;
-  cp.rho = static_cast<const T*>(p->d_rho);
+  cp.G = ga.G;
+  cp.H = ga.H;
   for (int f = 0; f < op.nf; ++f) {
     const Spectrum& s = p->spectra[op.f[f].spec];
     cp.spec[f] = static_cast<const T*>(s.data);
     cp.imag[f] = s.imag;
     cp.oddy[f] = s.odd[1];
+    cp.cnt[f] = op.f[f].set->d_cnt;
+    cp.off[f] = op.f[f].set->d_off;
+    cp.xs[f] = op.f[f].set->d_x;
+    cp.rho[f] = static_cast<const T*>(op.f[f].rho);
   }
+  cp.gcnt = ga.d_cnt;
+  cp.goff = ga.d_off;
+  cp.gx = ga.d_x;
+  cp.gnelem = ga.nelem;
   cp.qtab = static_cast<const cplx<T>*>(p->d_qtab);
   cp.partial = static_cast<T*>(p->d_partial);
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
@@ -300,9 +418,9 @@ static bem_status launch_t(bem_plan_s* p, const Operator& op, const void* in, vo
   else
     launch_col_nf<T, 8>(p, op.nf, cp, st);
   if (p->timing) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k_reduce<T><<<(nb + tb - 1) / tb, tb, 0, st>>>(static_cast<const T*>(p->d_partial), p->grid, nb, p->ncomp,
-                                                 p->d_perm, static_cast<const T*>(op.diag), static_cast<const T*>(in),
-                                                 static_cast<T*>(out));
+  k_reduce<T><<<(unsigned)((ga.nelem + tb - 1) / tb), tb, 0, st>>>(
+      static_cast<const T*>(p->d_partial), p->grid, ga.nelem, ga.d_cidx, p->d_perm, static_cast<const T*>(op.diag),
+      static_cast<const T*>(in), static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }

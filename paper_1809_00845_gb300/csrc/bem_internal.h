@@ -24,14 +24,33 @@ void set_error(const std::string& msg);
     }                                                                                             \
   } while (0)
 
-// One scattered field of an operator: rho_f[j] = coef_f[j] * in[perm[j]*ncomp + comp_f],
-// transformed, multiplied by the compressed spectrum spec_f (parity flags) and
-// accumulated into output component out_f.
+// Warp-coalesced "slot" layout of a set of boundary cells for the fused
+// column kernel.  Thread t of the CTA owns grid rows t + m*TT (m < H).  Lanes
+// are grouped by G (32, or TT when TT < 32); for group g and row slot m all
+// lanes loop over cnt[g*H + m] cells (the maximum over the group, padding
+// entries have x = 0, cidx = -1 and a zero density), so every load of the
+// loop is one contiguous G-element access.  Element (g, m, i, lane) sits at
+// (off[g*H + m] + i) * G + lane.
+struct SlotSet {
+  int ngroups = 0, G = 0, H = 0;
+  int64_t nelem = 0;            // total elements (slot rows * G)
+  int32_t* d_cnt = nullptr;     // ngroups * H
+  int32_t* d_off = nullptr;     // ngroups * H
+  uint16_t* d_x = nullptr;      // nelem: x grid index (0 on padding)
+  int32_t* d_cidx = nullptr;    // nelem: sorted cell index, -1 on padding
+  std::vector<int32_t> h_cidx;  // host copy of d_cidx
+};
+
+// One scattered field of an operator: rho_f[e] = coef_f[cidx[e]] * in[perm[cidx[e]]*ncomp + comp_f]
+// over the slot layout of its cell set, transformed, multiplied by the
+// compressed spectrum spec_f (parity flags) and accumulated into output out_f.
 struct FieldDesc {
   const void* coef;   // nb, sorted order, plan precision
   int comp;           // input component
   int spec;           // index into plan spectra
   int out;            // output component
+  const SlotSet* set = nullptr;
+  void* rho = nullptr;  // set->nelem values, plan precision (operator-owned scratch)
 };
 
 // Compressed spectrum of one kernel table: K^(k) = i^imag * S(k) with S real,
@@ -46,7 +65,18 @@ struct Operator {
   int nf = 0;
   FieldDesc f[kMaxFields];
   const void* diag = nullptr;  // nb*ncomp diagonal term (plan precision) or null
-  std::vector<void*> owned;    // coefficient arrays owned by this operator
+  std::vector<void*> owned;    // device arrays owned by this operator
+  SlotSet sets[2];             // operator-specific cell sets (BC-split operator)
+};
+
+// Block-Jacobi near-field preconditioner: dense inverses of the operator's
+// diagonal blocks of consecutive cells (caller order).
+struct BlockPrecond {
+  int kind = 1;     // 0 none, 1 block Jacobi
+  int bs = 64;      // block size (cells)
+  int nblocks = 0;
+  double* d_inv = nullptr;  // nblocks * (bs*ncomp)^2, row-major per block
+  bool valid = false;
 };
 
 }  // namespace bemfft
@@ -63,15 +93,20 @@ struct bem_plan_s {
   int32_t* d_line = nullptr;    // line index per sorted cell (3D)
   int64_t nlines = 0;
   void* d_qtab = nullptr;       // quarter twiddle table, plan precision
+  bemfft::SlotSet all_set;      // every cell (gather layout, single/double layer fields)
   std::vector<bemfft::Spectrum> spectra;
   std::vector<double> h_w, h_normal;  // host copies in sorted order
   std::vector<int32_t> h_perm;
+  std::vector<int32_t> h_row, h_col;  // sorted order: grid row (y) and column (x)
+  std::vector<int32_t> h_cell_user;   // caller order copies of the geometry
+  std::vector<double> h_w_user, h_normal_user;
   bemfft::Operator op_single, op_double, op_system;
   bool have_bc = false;
   std::vector<uint8_t> h_bc;
+  bemfft::BlockPrecond pc;
   // scratch
-  void* d_rho = nullptr;       // kMaxFields * nb
-  void* d_partial = nullptr;   // grid * nb * ncomp
+  void* d_rho = nullptr;       // unused (densities live with the operators)
+  void* d_partial = nullptr;   // grid * all_set.nelem * ncomp
   int grid = 0, threads = 0;
   size_t smem_bytes = 0;
   bool acc_in_smem = false;
@@ -98,6 +133,9 @@ namespace bemfft {
 bem_status compute_spectra_2d(bem_plan_s* p, cudaStream_t st);
 // apply2d.cu
 bem_status setup_apply_2d(bem_plan_s* p);
+bem_status build_slot_set(bem_plan_s* p, const std::vector<uint8_t>& member, SlotSet* s);
+void free_slot_set(SlotSet* s);
+bem_status alloc_field_rho(bem_plan_s* p, Operator& op);
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st);
 // gmres.cu
 bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
@@ -105,5 +143,7 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
                        cudaStream_t st);
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);
 size_t prec_bytes(const bem_plan_s* p);
+bem_status build_preconditioner(bem_plan_s* p);
+double kernel2d_point(int kind, int dx, int dy, double h);
 
 }  // namespace bemfft

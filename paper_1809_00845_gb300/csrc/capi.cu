@@ -38,6 +38,7 @@ static bem_status upload_coef(bem_plan_s* p, Operator& op, const std::vector<dou
 static void free_operator(Operator& op) {
   for (void* d : op.owned) cudaFree(d);
   op.owned.clear();
+  for (auto& st : op.sets) free_slot_set(&st);
   op.nf = 0;
   op.diag = nullptr;
 }
@@ -53,14 +54,16 @@ static bem_status build_ops_2d(bem_plan_s* p) {
   bem_status rc;
   Operator& s = p->op_single;
   s.nf = 1;
-  s.f[0] = {nullptr, 0, 0, 0};
+  s.f[0] = {nullptr, 0, 0, 0, &p->all_set, nullptr};
   if ((rc = upload_coef(p, s, w, &s.f[0].coef)) != BEM_OK) return rc;
+  if ((rc = alloc_field_rho(p, s)) != BEM_OK) return rc;
   Operator& d = p->op_double;
   d.nf = 2;
-  d.f[0] = {nullptr, 0, 1, 0};
-  d.f[1] = {nullptr, 0, 2, 0};
+  d.f[0] = {nullptr, 0, 1, 0, &p->all_set, nullptr};
+  d.f[1] = {nullptr, 0, 2, 0, &p->all_set, nullptr};
   if ((rc = upload_coef(p, d, wx, &d.f[0].coef)) != BEM_OK) return rc;
   if ((rc = upload_coef(p, d, wy, &d.f[1].coef)) != BEM_OK) return rc;
+  if ((rc = alloc_field_rho(p, d)) != BEM_OK) return rc;
   return BEM_OK;
 }
 
@@ -168,10 +171,17 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   std::vector<int32_t> rowptr(nn + 1, 0), col(nb);
   p->h_w.resize(nb);
   p->h_normal.resize(nb * dim);
+  p->h_row.resize(nb);
+  p->h_col.resize(nb);
+  p->h_cell_user.assign(cell, cell + nb * dim);
+  p->h_w_user.assign(w, w + nb);
+  p->h_normal_user.assign(normal, normal + nb * dim);
   for (int64_t j = 0; j < nb; ++j) {
     const int32_t u = perm[j];
     rowptr[cell[(int64_t)u * dim + 1] + 1]++;
     col[j] = cell[(int64_t)u * dim];
+    p->h_row[j] = cell[(int64_t)u * dim + 1];
+    p->h_col[j] = col[j];
     p->h_w[j] = w[u];
     for (int a = 0; a < dim; ++a) p->h_normal[j * dim + a] = normal[(int64_t)u * dim + a];
   }
@@ -217,8 +227,8 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   }
   bem_status rc = compute_spectra_2d(p, st);
   if (rc != BEM_OK) return fail(rc);
-  if ((rc = build_ops_2d(p)) != BEM_OK) return fail(rc);
   if ((rc = setup_apply_2d(p)) != BEM_OK) return fail(rc);
+  if ((rc = build_ops_2d(p)) != BEM_OK) return fail(rc);
   PLAN_CUDA(cudaStreamSynchronize(st));
 #undef PLAN_CUDA
   p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -266,19 +276,43 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       ay[j] = p->h_w[j] * p->h_normal[2 * j + 1] * mN;
     }
     for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;  // user order
+    std::vector<uint8_t> memD(nb), memN(nb);
+    for (int64_t j = 0; j < nb; ++j) {
+      memN[j] = bc[p->h_perm[j]] ? 1 : 0;
+      memD[j] = 1 - memN[j];
+    }
+    if ((rc = build_slot_set(p, memD, &s.sets[0])) != BEM_OK) return rc;
+    if ((rc = build_slot_set(p, memN, &s.sets[1])) != BEM_OK) return rc;
     s.nf = 3;
-    s.f[0] = {nullptr, 0, 0, 0};
-    s.f[1] = {nullptr, 0, 1, 0};
-    s.f[2] = {nullptr, 0, 2, 0};
+    s.f[0] = {nullptr, 0, 0, 0, &s.sets[0], nullptr};
+    s.f[1] = {nullptr, 0, 1, 0, &s.sets[1], nullptr};
+    s.f[2] = {nullptr, 0, 2, 0, &s.sets[1], nullptr};
     if ((rc = upload_coef(p, s, aq, &s.f[0].coef)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, ax, &s.f[1].coef)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, ay, &s.f[2].coef)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+    if ((rc = alloc_field_rho(p, s)) != BEM_OK) return rc;
   } else {
     set_error("bem_set_bc: kernel not available");
     return BEM_ERR_UNSUPPORTED;
   }
   p->have_bc = true;
+  p->pc.valid = false;
+  return BEM_OK;
+}
+
+bem_status bem_set_preconditioner(bem_plan_t p, int kind, int block_size) {
+  if (!p) {
+    set_error("bem_set_preconditioner: null plan");
+    return BEM_ERR_ARG;
+  }
+  if (kind < 0 || kind > 1 || (kind == 1 && (block_size < 1 || block_size * p->ncomp > 1024))) {
+    set_error("bem_set_preconditioner: kind 0 or 1, 1 <= block_size*ncomp <= 1024");
+    return BEM_ERR_ARG;
+  }
+  p->pc.kind = kind;
+  if (kind == 1) p->pc.bs = block_size;
+  p->pc.valid = false;
   return BEM_OK;
 }
 
@@ -390,6 +424,8 @@ bem_status bem_destroy(bem_plan_t p) {
   free_operator(p->op_single);
   free_operator(p->op_double);
   free_operator(p->op_system);
+  free_slot_set(&p->all_set);
+  cudaFree(p->pc.d_inv);
   cudaFree(p->d_rho);
   cudaFree(p->d_partial);
   for (auto e : p->ev_pool) cudaEventDestroy(e);

@@ -180,10 +180,11 @@ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 // Ns: product of the radices of the previous passes.  If LAST, outputs stay
 // in registers (natural order); otherwise they go to smem and are read back.
 template <int E, int R, int DIR, bool LAST, typename T>
-__device__ __forceinline__ void stockham_pass(cplx<T> (&v)[E], const int t, const int TT, const int Ns,
+__device__ __forceinline__ void stockham_pass(cplx<T> (&v)[E], const int t, const int TT, const int log2Ns,
                                               const int log2N, const Twiddles<T>& tw, cplx<T>* sbuf) {
   constexpr int S = E / R;
-  const int N = 1 << log2N;
+  constexpr int LR = (R == 32) ? 5 : (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : (R == 2) ? 1 : 0;
+  const int Ns = 1 << log2Ns;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int b = t + s * TT;
@@ -193,7 +194,7 @@ __device__ __forceinline__ void stockham_pass(cplx<T> (&v)[E], const int t, cons
     for (int r = 0; r < R; ++r) u[r] = v[s + r * S];
     if (Ns > 1) {
       // twiddle e^{DIR 2 pi i k r / (Ns R)} = table index k r N/(Ns R) < N
-      const int m1 = k * (N / (Ns * R));
+      const int m1 = k << (log2N - log2Ns - LR);
 #pragma unroll
       for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw.template get<DIR>(m1 * r));
     }
@@ -226,19 +227,19 @@ __device__ __forceinline__ void fft_line(cplx<T> (&v)[E], const int t, const int
   const int rem = log2N - full * LE;  // leftover bits
   // passes: (full - (rem == 0)) radix-E passes not last, then the last pass of radix E or 2^rem
   const int nfirst = rem == 0 ? full - 1 : full;
-  int Ns = 1;
+  int lNs = 0;
   for (int p = 0; p < nfirst; ++p) {
-    stockham_pass<E, E, DIR, false>(v, t, TT, Ns, log2N, tw, sbuf);
-    Ns *= E;
+    stockham_pass<E, E, DIR, false>(v, t, TT, lNs, log2N, tw, sbuf);
+    lNs += LE;
   }
   if (rem == 0) {
-    stockham_pass<E, E, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+    stockham_pass<E, E, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
   } else if (rem == 1) {
-    stockham_pass<E, 2, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+    stockham_pass<E, 2, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
   } else if (rem == 2) {
-    if constexpr (E >= 4) stockham_pass<E, 4, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+    if constexpr (E >= 4) stockham_pass<E, 4, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
   } else if (rem == 3) {
-    if constexpr (E >= 8) stockham_pass<E, 8, DIR, true>(v, t, TT, Ns, log2N, tw, sbuf);
+    if constexpr (E >= 8) stockham_pass<E, 8, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
   }
 }
 

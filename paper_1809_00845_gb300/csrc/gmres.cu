@@ -93,6 +93,22 @@ __global__ void k_axpby(double a, const double* __restrict__ x, double b, double
   if (i < M) y[i] = a * x[i] + b * y[i];
 }
 
+// out[b*bs + i] = sum_j inv_b[i][j] in[b*bs + j]   (block-Jacobi M^-1)
+__global__ void k_block_apply(const double* __restrict__ inv, int bs, int64_t M, const double* __restrict__ in,
+                              double* __restrict__ out) {
+  extern __shared__ double xin[];
+  const int b = blockIdx.x, i = threadIdx.x;
+  const int64_t i0 = (int64_t)b * bs;
+  const int sz = (int)(M - i0 < bs ? M - i0 : bs);
+  if (i < sz) xin[i] = in[i0 + i];
+  __syncthreads();
+  if (i >= sz) return;
+  const double* row = inv + ((size_t)b * bs + i) * bs;
+  double s = 0.0;
+  for (int j = 0; j < sz; ++j) s += row[j] * xin[j];
+  out[i0 + i] = s;
+}
+
 // masked copies: um = data * (1 - bc), qm = data * bc
 __global__ void k_split_known(const double* __restrict__ data, const uint8_t* __restrict__ bc, double* __restrict__ um,
                               double* __restrict__ qm, int64_t M) {
@@ -123,6 +139,14 @@ struct Gm {
     k_convert<float, double><<<blocks_for(M, 256), 256, 0, st>>>(static_cast<const float*>(p->d_tout), w, M);
     return BEM_OK;
   }
+  // z = M^-1 v (or a copy when unpreconditioned)
+  void precond(const double* v, double* z) {
+    if (p->pc.kind == 0) {
+      cudaMemcpyAsync(z, v, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    } else {
+      k_block_apply<<<p->pc.nblocks, p->pc.bs, p->pc.bs * sizeof(double), st>>>(p->pc.d_inv, p->pc.bs, M, v, z);
+    }
+  }
   // out[0..nvec) = V[0..nvec) . w   (device)
   void dots(const double* V, int64_t ldv, int nvec, const double* w, double* out, bool accumulate) {
     dim3 g(nchunk, nvec);
@@ -150,7 +174,8 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     BEM_CUDA_TRY(cudaMalloc(&p->d_V, (size_t)(m + 1) * M * sizeof(double)));
     p->gm_m = m;
   }
-  if (!p->d_vec) BEM_CUDA_TRY(cudaMalloc(&p->d_vec, (size_t)6 * M * sizeof(double) + (size_t)M));
+  if ((rc = build_preconditioner(p)) != BEM_OK) return rc;
+  if (!p->d_vec) BEM_CUDA_TRY(cudaMalloc(&p->d_vec, (size_t)7 * M * sizeof(double) + (size_t)M));
   const int nchunk = (int)((M + kDotChunk - 1) / kDotChunk);
   if (!p->d_small) BEM_CUDA_TRY(cudaMalloc(&p->d_small, (size_t)(3 * 520 + 520 * 64 + 8) * sizeof(double)));
   if (nchunk > 64) {
@@ -168,7 +193,8 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
   double* d_um = d_w + M;
   double* d_qm = d_um + M;
   double* d_data = d_qm + M;
-  uint8_t* d_bc = reinterpret_cast<uint8_t*>(d_data + M);
+  double* d_z = d_data + M;
+  uint8_t* d_bc = reinterpret_cast<uint8_t*>(d_z + M);
   double* d_h = p->d_small;              // 520: first CGS sweep (accumulated), then norm^2 at [m+1]
   double* d_h2 = d_h + 520;              // 520: second sweep
   double* d_y = d_h2 + 520;              // 520
@@ -247,7 +273,8 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     for (; j < m && iters < max_iter; ++j) {
       double* vj = V + (int64_t)j * M;
       double* vn = V + (int64_t)(j + 1) * M;
-      if ((rc = g.apply(BEM_SYSTEM, vj, d_w)) != BEM_OK) return rc;
+      g.precond(vj, d_z);
+      if ((rc = g.apply(BEM_SYSTEM, d_z, d_w)) != BEM_OK) return rc;
       ++applies;
       ++iters;
       // CGS2
@@ -298,8 +325,12 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
       y[i] = s / H[(size_t)i * (m + 1) + i];
     }
     if (j > 0) {
+      // x += M^-1 (V y)
       BEM_CUDA_TRY(cudaMemcpyAsync(d_y, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, st));
-      k_add_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j, d_y, d_x, M);
+      BEM_CUDA_TRY(cudaMemsetAsync(d_w, 0, M * sizeof(double), st));
+      k_add_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j, d_y, d_w, M);
+      g.precond(d_w, d_z);
+      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(1.0, d_z, 1.0, d_x, M);
     }
     ++restarts;
     (void)breakdown;

@@ -56,6 +56,23 @@ def test_star_mixed_bc_residual(torch_cuda, oracle_mod, prec, tol, bound):
     assert np.array_equal(u_out[bc == 0], u[bc == 0]) and np.array_equal(q_out[bc == 1], q[bc == 1])
 
 
+def test_block_preconditioner_cuts_iterations(torch_cuda):
+    """Mixed BC on a star: block-Jacobi (default) against no preconditioner."""
+    b = I.star_boundary(256)
+    u, q = I.boundary_data(b, I.field_expcos)
+    bc = I.mixed_bc_theta(b)
+    data = np.where(bc == 0, u, q)
+    plan = _plan(b, "f64")
+    _, _, pre = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=3000)
+    plan.set_preconditioner("none")
+    _, _, plain = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=400)
+    assert pre["status"] == 0
+    assert pre["iters"] * 5 < max(plain["iters"], 1) or plain["status"] != 0
+    plan.set_preconditioner("block", 32)
+    _, _, pre32 = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=3000)
+    assert pre32["status"] == 0
+
+
 def test_initial_guess_and_iteration_cap(torch_cuda, oracle_mod):
     b = I.circle_boundary(64, 0.3)
     u, _ = I.boundary_data(b, I.field_x2y2)
