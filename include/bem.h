@@ -135,6 +135,23 @@ bem_status bem_apply(bem_plan_t plan, bem_layer layer, const void* in_dev, void*
  * copies out and synchronises the stream before returning. */
 bem_status bem_apply_host(bem_plan_t plan, bem_layer layer, const void* in_host, void* out_host, void* stream);
 
+/* bem_apply without touching the CUDA allocator, for callers that cannot
+ * allocate device memory at the point where they apply the operator (device
+ * memory fully reserved by another framework's pool, latency-critical loops
+ * that must not enter the allocator, hosts that forbid device allocation after
+ * start-up).  The paper has no counterpart: this is a deployment variant of
+ * the apply above, same arguments, same results.
+ * The densities and per-CTA partial sums go to one static 16 MiB device
+ * buffer linked into the library (held on every GPU that uses this call until
+ * the process exits) instead of the plan's scratch.  The first call on a
+ * device looks up the buffer's address (make it before any stream capture).
+ * Plans whose scratch does not fit return BEM_ERR_UNSUPPORTED with the needed
+ * size in bem_last_error().  All calls share the buffer: calls that overlap on
+ * the GPU (unordered streams, concurrent threads) race.  No cudaMalloc, no
+ * cudaFree, no allocating library call. */
+bem_status bem_apply_static_scratch(bem_plan_t plan, bem_layer layer, const void* in_dev, void* out_dev,
+                                    void* stream);
+
 /* Solve the boundary-condition split system for the unknowns (Section 4:
  * Krylov iteration on the FFT apply; restarted GMRES here).
  *   bc        host nb*ncomp (as bem_set_bc; also sets the plan's BC state)

@@ -27,8 +27,8 @@ KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d":
 PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32}
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
-EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
-            "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
+EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
+            "bem_get_info", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
             "bem_status_string", "bem_last_error"]
 
 
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_set_preconditioner.argtypes = [P, I, I]
     lib.bem_apply.argtypes = [P, I, P, P, P]
     lib.bem_apply_host.argtypes = [P, I, P, P, P]
+    lib.bem_apply_static_scratch.argtypes = [P, I, P, P, P]
     lib.bem_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
     lib.bem_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.bem_set_kernel_timing.argtypes = [P, I]
@@ -84,7 +85,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_status_string.restype = ctypes.c_char_p
     lib.bem_last_error.argtypes = []
     lib.bem_last_error.restype = ctypes.c_char_p
-    for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_solve", "bem_get_info",
+    for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_static_scratch", "bem_apply_host", "bem_solve", "bem_get_info",
                  "bem_set_kernel_timing", "bem_kernel_time", "bem_destroy"):
         getattr(lib, name).restype = I
     _lib = lib

@@ -425,6 +425,72 @@ static bem_status launch_t(bem_plan_s* p, const Operator& op, const void* in, vo
   return BEM_OK;
 }
 
+// Same launch sequence as launch_t, with the weighted densities and the
+// per-CTA partials placed in caller-provided device scratch (rho[f] holds
+// op.f[f].set->nelem values, partial holds grid * nelem * ncomp values).
+template <typename T>
+static bem_status launch_t_scratch(bem_plan_s* p, const Operator& op, const void* in, void* out, void* const* rho,
+                                   void* partial, cudaStream_t st) {
+  PrepParams<T> pp{};
+  pp.ncomp = p->ncomp;
+  pp.nf = op.nf;
+  pp.perm = p->d_perm;
+  pp.in = static_cast<const T*>(in);
+  int64_t maxe = 1;
+  for (int f = 0; f < op.nf; ++f) {
+    pp.coef[f] = static_cast<const T*>(op.f[f].coef);
+    pp.cidx[f] = op.f[f].set->d_cidx;
+    pp.nelem[f] = op.f[f].set->nelem;
+    pp.comp[f] = op.f[f].comp;
+    pp.rho[f] = static_cast<T*>(rho[f]);
+    maxe = std::max(maxe, op.f[f].set->nelem);
+  }
+  const int tb = 256;
+  k_prep<T><<<dim3((unsigned)((maxe + tb - 1) / tb), op.nf), tb, 0, st>>>(pp);
+  const SlotSet& ga = p->all_set;
+  Col2DParams<T> cp{};
+  cp.n = (int)p->n;
+  cp.log2N = p->log2N;
+  cp.G = ga.G;
+  cp.H = ga.H;
+  for (int f = 0; f < op.nf; ++f) {
+    const Spectrum& s = p->spectra[op.f[f].spec];
+    cp.spec[f] = static_cast<const T*>(s.data);
+    cp.imag[f] = s.imag;
+    cp.oddy[f] = s.odd[1];
+    cp.cnt[f] = op.f[f].set->d_cnt;
+    cp.off[f] = op.f[f].set->d_off;
+    cp.xs[f] = op.f[f].set->d_x;
+    cp.rho[f] = static_cast<const T*>(rho[f]);
+  }
+  cp.gcnt = ga.d_cnt;
+  cp.goff = ga.d_off;
+  cp.gx = ga.d_x;
+  cp.gnelem = ga.nelem;
+  cp.qtab = static_cast<const cplx<T>*>(p->d_qtab);
+  cp.partial = static_cast<T*>(partial);
+  cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
+  if (elems_per_thread(p->log2N) == 16)
+    launch_col_nf<T, 16>(p, op.nf, cp, st);
+  else
+    launch_col_nf<T, 8>(p, op.nf, cp, st);
+  k_reduce<T><<<(unsigned)((ga.nelem + tb - 1) / tb), tb, 0, st>>>(
+      static_cast<const T*>(partial), p->grid, ga.nelem, ga.d_cidx, p->d_perm, static_cast<const T*>(op.diag),
+      static_cast<const T*>(in), static_cast<T*>(out));
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status launch_apply_2d_scratch(bem_plan_s* p, const Operator& op, const void* in, void* out, void* const* rho,
+                                   void* partial, cudaStream_t st) {
+  if (op.nf < 1 || op.nf > 3) {
+    set_error("2D operator with unsupported field count");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  return p->prec == BEM_F64 ? launch_t_scratch<double>(p, op, in, out, rho, partial, st)
+                            : launch_t_scratch<float>(p, op, in, out, rho, partial, st);
+}
+
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st) {
   if (op.nf < 1 || op.nf > 3) {
     set_error("2D operator with unsupported field count");

@@ -137,6 +137,8 @@ bem_status build_slot_set(bem_plan_s* p, const std::vector<uint8_t>& member, Slo
 void free_slot_set(SlotSet* s);
 bem_status alloc_field_rho(bem_plan_s* p, Operator& op);
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st);
+bem_status launch_apply_2d_scratch(bem_plan_s* p, const Operator& op, const void* in, void* out, void* const* rho,
+                                   void* partial, cudaStream_t st);
 // gmres.cu
 bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
                        int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,

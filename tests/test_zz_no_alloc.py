@@ -1,0 +1,78 @@
+"""bem_apply_static_scratch: the apply for callers that cannot allocate device
+memory when they apply the operator (for example because another framework's
+pool has reserved the device, or because the call sits in a loop that must
+not enter the allocator).  It must give the same result as bem_apply, call
+after call, while its scratch lives in the library's static device buffer.
+
+This file is collected last so that a failure here never hides the other GPU
+tests; it also passes when run alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1809_00845_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_00845_gb300 import build
+    build.build()
+    return torch
+
+
+def _rel(a, b):
+    a = a.double().cpu().numpy()
+    b = b.double().cpu().numpy()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec,n", [("f32", 512), ("f32", 4096), ("f64", 256)])
+def test_static_scratch_matches_bem_apply_twice(torch_cuda, prec, n):
+    torch = torch_cuda
+    from paper_1809_00845_gb300 import bem
+    lib = bem.load_library()
+    b = I.star_boundary(n)
+    bc = I.mixed_bc_theta(b)
+    plan = bem.Plan.from_boundary(b, "laplace2d", prec)
+    plan.set_bc(bc, 0.5)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    stream = ctypes.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+    rng = np.random.default_rng(17)
+    for layer in (bem.BEM_SINGLE, bem.BEM_DOUBLE, bem.BEM_SYSTEM):
+        x = torch.from_numpy(rng.standard_normal(b.nb)).to(dt).cuda()
+        ref = torch.empty_like(x)
+        assert lib.bem_apply(plan._h, layer, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(ref.data_ptr()),
+                             stream) == 0
+        for _ in range(2):
+            out = torch.full_like(x, float("nan"))
+            rc = lib.bem_apply_static_scratch(plan._h, layer, ctypes.c_void_p(x.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr()), stream)
+            assert rc == 0, lib.bem_last_error().decode()
+            torch.cuda.synchronize()
+            assert _rel(out, ref) <= TOL[prec]
+    plan.close()
+
+
+def test_static_scratch_rejects_plans_that_do_not_fit(torch_cuda):
+    torch = torch_cuda
+    from paper_1809_00845_gb300 import bem
+    lib = bem.load_library()
+    b = I.star_boundary(4096)
+    plan = bem.Plan.from_boundary(b, "laplace2d", "f64")  # ~27 MB of partial sums
+    x = torch.zeros(b.nb, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    stream = ctypes.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+    rc = lib.bem_apply_static_scratch(plan._h, bem.BEM_SINGLE, ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(y.data_ptr()), stream)
+    assert rc == bem.BEM_ERR_UNSUPPORTED
+    assert b"static buffer" in lib.bem_last_error()
+    plan.close()
