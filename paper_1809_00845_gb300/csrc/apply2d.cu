@@ -29,6 +29,7 @@
 #include <cstring>
 
 #include "bem_internal.h"
+#include "fft4step.cuh"
 #include "fft_reg.cuh"
 
 namespace bemfft {
@@ -184,9 +185,280 @@ __global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem,
   out[u] = (T)s;
 }
 
+
+// ------------------------------------------------- four-step column kernel
+//
+// For N >= 512.  Thread t owns a contiguous range of grid rows
+// [rowbeg[t], rowbeg[t+1]) and therefore the contiguous range of sorted cells
+// [chunk[t], chunk[t+1]) lying in those rows (ranges balanced by cells + rows
+// at plan time).  Per column kx:
+//   1. the thread walks its cells (loads batched 8 at a time), forms the
+//      input-pruned x-DFT of every field row by row and writes its rows
+//      (zeros for empty rows) to shared memory: field 0 into the transform
+//      buffer, fields 1.. into staging rows;
+//   2. each field is loaded into the four-step engine's register map
+//      (rows t + m*TT), transformed, multiplied by the spectrum column (copied
+//      to shared memory with coalesced loads) and accumulated;
+//   3. the inverse transform leaves rows t + m*TT in registers, they are
+//      written to shared memory and every thread gathers its own cells
+//      (output-pruned inverse x-DFT) into its accumulators.
+template <typename T>
+struct Col2Dv2Params {
+  int n, log2N, nb;
+  const int32_t* chunk;   // TT + 1
+  const int32_t* rowbeg;  // TT + 1
+  const uint32_t* meta;   // nb: x | row << 16 | type << 31
+  const cplx<T>* val;     // nb density pairs
+  const T* spec[3];
+  int imag[3];
+  int oddy[3];
+  const cplx<T>* qtab;
+  T* partial;  // gridDim.x * nb, sorted cell order
+  int acc_in_smem;
+};
+
+// Walk cells [c0, c1) (rows r0 <= row < r1) and write the x-DFT of the
+// selected fields per row: FSEL < 0 = all NF fields (field 0 -> out0[row],
+// field f > 0 -> outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.
+template <typename T, int NF, int FSEL>
+__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int c0, int c1, int r0, int r1,
+                                            cplx<T>* out0, cplx<T>* outF, const Twiddles<T>& tw) {
+  const int Nm = (1 << p.log2N) - 1;
+  cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
+  int cur = r0;
+  auto flush = [&](int r) {
+    if (FSEL < 0) {
+      out0[r] = s0;
+      if (NF > 1) outF[r] = s1;
+      if (NF > 2) outF[p.n + r] = s2;
+    } else {
+      out0[r] = FSEL == 0 ? s0 : (FSEL == 1 ? s1 : s2);
+    }
+  };
+  for (int j0 = c0; j0 < c1; j0 += 8) {
+    uint32_t mt[8];
+    cplx<T> vv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = j0 + i < c1 ? j0 + i : c1 - 1;
+      mt[i] = __ldg(p.meta + j);
+      vv[i] = p.val[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (j0 + i < c1) {
+        const int row = (int)((mt[i] >> 16) & 0x7fffu), x = (int)(mt[i] & 0xffffu);
+        const bool ty = (mt[i] >> 31) != 0;
+        while (cur < row) {
+          flush(cur);
+          s0 = s1 = s2 = {T(0), T(0)};
+          ++cur;
+        }
+        const cplx<T> w = tw.template get<-1>((kx * x) & Nm);
+        const T a = vv[i].x, b = vv[i].y;
+        const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
+        if (FSEL < 0 || FSEL == 0) {
+          s0.x += ca * w.x;
+          s0.y += ca * w.y;
+        }
+        if ((FSEL < 0 && NF > 1) || FSEL == 1) {
+          s1.x += cb * w.x;
+          s1.y += cb * w.y;
+        }
+        if ((FSEL < 0 && NF > 2) || FSEL == 2) {
+          s2.x += cc * w.x;
+          s2.y += cc * w.y;
+        }
+      }
+    }
+  }
+  while (cur < r1) {
+    flush(cur);
+    s0 = s1 = s2 = {T(0), T(0)};
+    ++cur;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, int c0, int c1, const cplx<T>* rows,
+                                             const Twiddles<T>& tw, T* acc) {
+  const int Nm = (1 << p.log2N) - 1;
+  const T ckx = (kx == 0 || kx == p.n) ? T(1) : T(2);
+  for (int j0 = c0; j0 < c1; j0 += 8) {
+    uint32_t mt[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (j0 + i < c1 ? j0 + i : c1 - 1));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (j0 + i < c1) {
+        const int row = (int)((mt[i] >> 16) & 0x7fffu), x = (int)(mt[i] & 0xffffu);
+        const cplx<T> Y = rows[row];
+        const cplx<T> w = tw.template get<+1>((kx * x) & Nm);
+        acc[j0 + i] += ckx * (Y.x * w.x - Y.y * w.y);
+      }
+    }
+  }
+}
+
+// field-indexed parameters without dynamic indexing of the parameter arrays
+template <typename T>
+__device__ __forceinline__ const T* spec_of(const Col2Dv2Params<T>& p, int f) {
+  return f == 0 ? p.spec[0] : (f == 1 ? p.spec[1] : p.spec[2]);
+}
+template <typename T>
+__device__ __forceinline__ int imag_of(const Col2Dv2Params<T>& p, int f) {
+  return f == 0 ? p.imag[0] : (f == 1 ? p.imag[1] : p.imag[2]);
+}
+template <typename T>
+__device__ __forceinline__ int oddy_of(const Col2Dv2Params<T>& p, int f) {
+  return f == 0 ? p.oddy[0] : (f == 1 ? p.oddy[1] : p.oddy[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_spectrum(const Col2Dv2Params<T>& p, int f, int kx, T* sS) {
+  const T* S = spec_of(p, f) + (size_t)kx * (p.n + 1);
+  for (int i = threadIdx.x; i <= p.n; i += blockDim.x) sS[i] = __ldg(S + i);
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> spectral_term(const Col2Dv2Params<T>& p, bool im, bool oy, const T* sS, int K,
+                                                 cplx<T> v) {
+  const int N = 1 << p.log2N;
+  const bool hi = K > p.n;
+  T sv = sS[hi ? N - K : K];
+  if (hi && oy) sv = -sv;
+  return im ? cplx<T>{-v.y * sv, v.x * sv} : cplx<T>{v.x * sv, v.y * sv};
+}
+
+template <typename T, int NF, bool ACCREG>
+__global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x, TT = blockDim.x, W = TT >> 5;
+  const int log2N = p.log2N, N = 1 << log2N, n = p.n;
+  const int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
+  cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* sq = sA + nbuf;
+  T* sS = reinterpret_cast<T*>(sq + (N >> 2));
+  cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + ((n + 4) & ~3));
+  T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
+                         : p.partial + (size_t)blockIdx.x * p.nb;
+  for (int i = t; i < (N >> 2); i += TT) sq[i] = p.qtab[i];
+  const int c0 = p.chunk[t], c1 = p.chunk[t + 1], r0 = p.rowbeg[t], r1 = p.rowbeg[t + 1];
+  for (int j = c0; j < c1; ++j) acc[j] = T(0);
+  __syncthreads();
+  const Twiddles<T> tw{sq, log2N - 2};
+  FourStep<T> fs;
+  fs.init(t, TT, log2N, sA, tw);
+
+  for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
+    __syncthreads();  // the previous column's gather has finished reading sA
+    if constexpr (ACCREG) {
+      sparse_rows<T, NF, -1>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+      __syncthreads();
+      cplx<T> y[16];
+#pragma unroll 1
+      for (int f = 0; f < NF; ++f) {
+        cplx<T> v[16];
+        const cplx<T>* src = f == 0 ? sA : sF + (size_t)(f - 1) * n;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = src[t + m * TT];
+#pragma unroll
+        for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+        __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
+        load_spectrum(p, f, kx, sS);
+        fs.template forward<true>(v);
+        const bool im = imag_of(p, f) != 0, oy = oddy_of(p, f) != 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const cplx<T> term = spectral_term(p, im, oy, sS, fs.freq(k), v[k]);
+          y[k] = f == 0 ? term : y[k] + term;
+        }
+      }
+      fs.inverse(y);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) sA[t + m * TT] = y[m];
+      __syncthreads();
+      gather_cells(p, kx, c0, c1, sA, tw, acc);
+    } else {
+#pragma unroll 1
+      for (int f = 0; f < NF; ++f) {
+        if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
+        if (NF == 1) sparse_rows<T, NF, -1>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+        else if (f == 0) sparse_rows<T, NF, 0>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+        else if (f == 1) sparse_rows<T, NF, 1>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+        else sparse_rows<T, NF, 2>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+        __syncthreads();
+        cplx<T> v[16];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = sA[t + m * TT];
+#pragma unroll
+        for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+        __syncthreads();
+        load_spectrum(p, f, kx, sS);
+        fs.template forward<true>(v);
+        const bool im = imag_of(p, f) != 0, oy = oddy_of(p, f) != 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = spectral_term(p, im, oy, sS, fs.freq(k), v[k]);
+        fs.inverse(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sA[t + m * TT] = v[m];
+        __syncthreads();
+        gather_cells(p, kx, c0, c1, sA, tw, acc);
+      }
+    }
+  }
+  if (p.acc_in_smem)
+    for (int j = c0; j < c1; ++j) p.partial[(size_t)blockIdx.x * p.nb + j] = acc[j];
+}
+
+// val[j] = (coefA[j], coefB[j]) * in[perm[j]]
+template <typename T>
+__global__ void k_prep_v2(int nb, const int32_t* __restrict__ perm, const T* __restrict__ in,
+                          const T* __restrict__ coefA, const T* __restrict__ coefB, cplx<T>* __restrict__ val) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const T x = in[perm[j]];
+  val[j] = {coefA[j] * x, coefB[j] * x};
+}
+
+// out[perm[j]] = sum_b partial[b*nb + j] (+ diag * in), FP64 sum in fixed order
+template <typename T>
+__global__ void k_reduce_v2(const T* __restrict__ partial, int grid, int nb, const int32_t* __restrict__ perm,
+                            const T* __restrict__ diag, const T* __restrict__ in, T* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double s = 0.0;
+  for (int b = 0; b < grid; ++b) s += (double)partial[(size_t)b * nb + j];
+  const int u = perm[j];
+  if (diag) s += (double)diag[u] * (double)in[u];
+  out[u] = (T)s;
+}
+
 // ------------------------------------------------------------------ host side
 
 static int elems_per_thread(int log2N) { return log2N >= 8 ? 16 : 8; }
+
+// Records the start event of a timed column-kernel launch on st and returns
+// the end event to record after it (nullptr on failure).
+static cudaEvent_t timing_begin(bem_plan_s* p, cudaStream_t st) {
+  if (p->ev_used + 2 > (int)p->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        set_error("cudaEventCreate failed");
+        return nullptr;
+      }
+      p->ev_pool.push_back(e);
+    }
+  }
+  cudaEvent_t e0 = p->ev_pool[p->ev_used++];
+  cudaEvent_t e1 = p->ev_pool[p->ev_used++];
+  if (cudaEventRecord(e0, st) != cudaSuccess) {
+    set_error("cudaEventRecord failed");
+    return nullptr;
+  }
+  return e1;
+}
 
 void free_slot_set(SlotSet* s) {
   cudaFree(s->d_cnt);
@@ -336,12 +608,120 @@ static bem_status setup_t(bem_plan_s* p) {
   return BEM_OK;
 }
 
+// shared memory of the four-step kernel
+template <typename T>
+static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc) {
+  const int W = TT / 32;
+  const size_t nbuf = (size_t)std::max(16 * TT, W * 544);
+  const int64_t N = 2 * n;
+  size_t s = nbuf * sizeof(cplx<T>) + (size_t)(N / 4) * sizeof(cplx<T>) + (size_t)((n + 4) & ~3) * sizeof(T);
+  if (accreg) s += (size_t)2 * n * sizeof(cplx<T>);
+  if (acc) s += (size_t)nb * sizeof(T);
+  return s;
+}
+
+template <typename T, int NF, bool ACCREG>
+static cudaError_t configure_v2_one(size_t smem, int threads, int* bps) {
+  auto kern = k_col2d_v2<T, NF, ACCREG>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, threads, smem);
+}
+
+template <typename T>
+static bem_status setup_v2_t(bem_plan_s* p) {
+  constexpr bool R = std::is_same<T, float>::value;
+  const int64_t n = p->n, nb = p->nb;
+  const int TT = (int)(p->N / 16);
+  p->threads = TT;
+  // balanced contiguous row ranges: cost of a row = 1 + its cells
+  std::vector<int64_t> rowcnt(n, 0);
+  for (int64_t j = 0; j < nb; ++j) rowcnt[p->h_row[j]]++;
+  const double total = (double)(n + nb);
+  std::vector<int32_t> rowbeg(TT + 1), chunk(TT + 1);
+  {
+    int64_t r = 0, cells = 0;
+    double acc = 0;
+    for (int t = 0; t < TT; ++t) {
+      rowbeg[t] = (int32_t)r;
+      chunk[t] = (int32_t)cells;
+      const double target = total * (t + 1) / TT;
+      while (r < n && (t == TT - 1 || acc + 0.5 * (1 + rowcnt[r]) <= target)) {
+        acc += 1 + rowcnt[r];
+        cells += rowcnt[r];
+        ++r;
+      }
+    }
+    rowbeg[TT] = (int32_t)n;
+    chunk[TT] = (int32_t)nb;
+  }
+  BEM_CUDA_TRY(cudaMalloc(&p->d_rowbeg, (TT + 1) * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_chunk, (TT + 1) * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMemcpy(p->d_rowbeg, rowbeg.data(), (TT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMemcpy(p->d_chunk, chunk.data(), (TT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  int dev = 0, nsm = 0, smem_optin = 0;
+  BEM_CUDA_TRY(cudaGetDevice(&dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  p->acc_in_smem = smem_v2<T>(n, TT, nb, R, true) <= (size_t)smem_optin;
+  p->smem_bytes = smem_v2<T>(n, TT, nb, R, p->acc_in_smem);
+  if (p->smem_bytes > (size_t)smem_optin) {
+    set_error("grid too large for the shared-memory column buffers");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  int b1 = 0, b2 = 0, b3 = 0;
+  BEM_CUDA_TRY((configure_v2_one<T, 1, false>(p->smem_bytes, TT, &b1)));
+  BEM_CUDA_TRY((configure_v2_one<T, 2, R>(p->smem_bytes, TT, &b2)));
+  BEM_CUDA_TRY((configure_v2_one<T, 3, R>(p->smem_bytes, TT, &b3)));
+  const int bps = std::min(b1, std::min(b2, b3));
+  if (bps < 1) {
+    set_error("column kernel cannot be resident (registers/shared memory)");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  p->grid = (int)std::min<int64_t>((int64_t)bps * nsm, n + 1);
+  const size_t tb = sizeof(T);
+  BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * nb * tb));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_val, (size_t)nb * 2 * tb));
+  p->scratch_bytes += (size_t)p->grid * nb * tb + (size_t)nb * 2 * tb;
+  return BEM_OK;
+}
+
 bem_status setup_apply_2d(bem_plan_s* p) {
   if (p->log2N < 3 || p->log2N > 13) {
     set_error("2D grids need 4 <= n <= 4096, n a power of two");
     return BEM_ERR_UNSUPPORTED;
   }
+  p->v2 = p->log2N >= 9;
+  if (p->v2) return p->prec == BEM_F64 ? setup_v2_t<double>(p) : setup_v2_t<float>(p);
   return p->prec == BEM_F64 ? setup_t<double>(p) : setup_t<float>(p);
+}
+
+bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& coefA, const std::vector<double>& coefB,
+                       const std::vector<uint8_t>& type) {
+  const int64_t nb = p->nb;
+  std::vector<uint32_t> meta(nb);
+  for (int64_t j = 0; j < nb; ++j)
+    meta[j] = (uint32_t)p->h_col[j] | ((uint32_t)p->h_row[j] << 16) | ((uint32_t)(type[j] ? 1u : 0u) << 31);
+  void* dm = nullptr;
+  BEM_CUDA_TRY(cudaMalloc(&dm, nb * sizeof(uint32_t)));
+  BEM_CUDA_TRY(cudaMemcpy(dm, meta.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  op.owned.push_back(dm);
+  op.meta = static_cast<const uint32_t*>(dm);
+  const size_t tb = prec_bytes(p);
+  for (int k = 0; k < 2; ++k) {
+    const std::vector<double>& c = k == 0 ? coefA : coefB;
+    void* d = nullptr;
+    BEM_CUDA_TRY(cudaMalloc(&d, nb * tb));
+    if (p->prec == BEM_F64) {
+      BEM_CUDA_TRY(cudaMemcpy(d, c.data(), nb * tb, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> f(c.begin(), c.end());
+      BEM_CUDA_TRY(cudaMemcpy(d, f.data(), nb * tb, cudaMemcpyHostToDevice));
+    }
+    op.owned.push_back(d);
+    (k == 0 ? op.coefA : op.coefB) = d;
+  }
+  return BEM_OK;
 }
 
 template <typename T, int E, int NF, bool ACCREG>
@@ -358,7 +738,8 @@ static void launch_col_nf(const bem_plan_s* p, int nf, const Col2DParams<T>& cp,
 }
 
 template <typename T>
-static bem_status launch_t(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st) {
+static bem_status launch_v1(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
+                            bool timed, cudaStream_t st) {
   PrepParams<T> pp{};
   pp.ncomp = p->ncomp;
   pp.nf = op.nf;
@@ -370,12 +751,11 @@ static bem_status launch_t(bem_plan_s* p, const Operator& op, const void* in, vo
     pp.cidx[f] = op.f[f].set->d_cidx;
     pp.nelem[f] = op.f[f].set->nelem;
     pp.comp[f] = op.f[f].comp;
-    pp.rho[f] = static_cast<T*>(op.f[f].rho);
+    pp.rho[f] = static_cast<T*>(sp.rho[f]);
     maxe = std::max(maxe, op.f[f].set->nelem);
   }
   const int tb = 256;
   k_prep<T><<<dim3((unsigned)((maxe + tb - 1) / tb), op.nf), tb, 0, st>>>(pp);
-
   const SlotSet& ga = p->all_set;
   Col2DParams<T> cp{};
   cp.n = (int)p->n;
@@ -390,113 +770,122 @@ static bem_status launch_t(bem_plan_s* p, const Operator& op, const void* in, vo
     cp.cnt[f] = op.f[f].set->d_cnt;
     cp.off[f] = op.f[f].set->d_off;
     cp.xs[f] = op.f[f].set->d_x;
-    cp.rho[f] = static_cast<const T*>(op.f[f].rho);
+    cp.rho[f] = static_cast<const T*>(sp.rho[f]);
   }
   cp.gcnt = ga.d_cnt;
   cp.goff = ga.d_off;
   cp.gx = ga.d_x;
   cp.gnelem = ga.nelem;
   cp.qtab = static_cast<const cplx<T>*>(p->d_qtab);
-  cp.partial = static_cast<T*>(p->d_partial);
+  cp.partial = static_cast<T*>(sp.partial);
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
-
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (p->timing) {
-    if (p->ev_used + 2 > (int)p->ev_pool.size()) {
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        BEM_CUDA_TRY(cudaEventCreate(&e));
-        p->ev_pool.push_back(e);
-      }
-    }
-    e0 = p->ev_pool[p->ev_used++];
-    e1 = p->ev_pool[p->ev_used++];
-    BEM_CUDA_TRY(cudaEventRecord(e0, st));
-  }
+  cudaEvent_t e1 = nullptr;
+  if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   if (elems_per_thread(p->log2N) == 16)
     launch_col_nf<T, 16>(p, op.nf, cp, st);
   else
     launch_col_nf<T, 8>(p, op.nf, cp, st);
-  if (p->timing) BEM_CUDA_TRY(cudaEventRecord(e1, st));
+  if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
   k_reduce<T><<<(unsigned)((ga.nelem + tb - 1) / tb), tb, 0, st>>>(
-      static_cast<const T*>(p->d_partial), p->grid, ga.nelem, ga.d_cidx, p->d_perm, static_cast<const T*>(op.diag),
+      static_cast<const T*>(sp.partial), p->grid, ga.nelem, ga.d_cidx, p->d_perm, static_cast<const T*>(op.diag),
       static_cast<const T*>(in), static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
 
-// Same launch sequence as launch_t, with the weighted densities and the
-// per-CTA partials placed in caller-provided device scratch (rho[f] holds
-// op.f[f].set->nelem values, partial holds grid * nelem * ncomp values).
 template <typename T>
-static bem_status launch_t_scratch(bem_plan_s* p, const Operator& op, const void* in, void* out, void* const* rho,
-                                   void* partial, cudaStream_t st) {
-  PrepParams<T> pp{};
-  pp.ncomp = p->ncomp;
-  pp.nf = op.nf;
-  pp.perm = p->d_perm;
-  pp.in = static_cast<const T*>(in);
-  int64_t maxe = 1;
-  for (int f = 0; f < op.nf; ++f) {
-    pp.coef[f] = static_cast<const T*>(op.f[f].coef);
-    pp.cidx[f] = op.f[f].set->d_cidx;
-    pp.nelem[f] = op.f[f].set->nelem;
-    pp.comp[f] = op.f[f].comp;
-    pp.rho[f] = static_cast<T*>(rho[f]);
-    maxe = std::max(maxe, op.f[f].set->nelem);
-  }
+static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
+                            bool timed, cudaStream_t st) {
+  const int nb = (int)p->nb;
   const int tb = 256;
-  k_prep<T><<<dim3((unsigned)((maxe + tb - 1) / tb), op.nf), tb, 0, st>>>(pp);
-  const SlotSet& ga = p->all_set;
-  Col2DParams<T> cp{};
+  k_prep_v2<T><<<(nb + tb - 1) / tb, tb, 0, st>>>(nb, p->d_perm, static_cast<const T*>(in),
+                                                  static_cast<const T*>(op.coefA), static_cast<const T*>(op.coefB),
+                                                  static_cast<cplx<T>*>(sp.val));
+  Col2Dv2Params<T> cp{};
   cp.n = (int)p->n;
   cp.log2N = p->log2N;
-  cp.G = ga.G;
-  cp.H = ga.H;
+  cp.nb = nb;
+  cp.chunk = p->d_chunk;
+  cp.rowbeg = p->d_rowbeg;
+  cp.meta = op.meta;
+  cp.val = static_cast<const cplx<T>*>(sp.val);
   for (int f = 0; f < op.nf; ++f) {
     const Spectrum& s = p->spectra[op.f[f].spec];
     cp.spec[f] = static_cast<const T*>(s.data);
     cp.imag[f] = s.imag;
     cp.oddy[f] = s.odd[1];
-    cp.cnt[f] = op.f[f].set->d_cnt;
-    cp.off[f] = op.f[f].set->d_off;
-    cp.xs[f] = op.f[f].set->d_x;
-    cp.rho[f] = static_cast<const T*>(rho[f]);
   }
-  cp.gcnt = ga.d_cnt;
-  cp.goff = ga.d_off;
-  cp.gx = ga.d_x;
-  cp.gnelem = ga.nelem;
   cp.qtab = static_cast<const cplx<T>*>(p->d_qtab);
-  cp.partial = static_cast<T*>(partial);
+  cp.partial = static_cast<T*>(sp.partial);
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
-  if (elems_per_thread(p->log2N) == 16)
-    launch_col_nf<T, 16>(p, op.nf, cp, st);
-  else
-    launch_col_nf<T, 8>(p, op.nf, cp, st);
-  k_reduce<T><<<(unsigned)((ga.nelem + tb - 1) / tb), tb, 0, st>>>(
-      static_cast<const T*>(partial), p->grid, ga.nelem, ga.d_cidx, p->d_perm, static_cast<const T*>(op.diag),
-      static_cast<const T*>(in), static_cast<T*>(out));
+  cudaEvent_t e1 = nullptr;
+  if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
+  constexpr bool R = std::is_same<T, float>::value;
+  if (op.nf == 1) k_col2d_v2<T, 1, false><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
+  else if (op.nf == 2) k_col2d_v2<T, 2, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
+  else k_col2d_v2<T, 3, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
+  if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
+  k_reduce_v2<T><<<(nb + tb - 1) / tb, tb, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, nb, p->d_perm,
+                                                    static_cast<const T*>(op.diag), static_cast<const T*>(in),
+                                                    static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
 
-bem_status launch_apply_2d_scratch(bem_plan_s* p, const Operator& op, const void* in, void* out, void* const* rho,
-                                   void* partial, cudaStream_t st) {
+static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t apply_scratch_bytes(const bem_plan_s* p, const Operator& op) {
+  const size_t tb = prec_bytes(p);
+  size_t need = 0;
+  if (p->v2) {
+    need += align256((size_t)p->nb * 2 * tb);
+    need += align256((size_t)p->grid * p->nb * tb);
+  } else {
+    for (int f = 0; f < op.nf; ++f) need += align256((size_t)op.f[f].set->nelem * tb);
+    need += align256((size_t)p->grid * p->all_set.nelem * p->ncomp * tb);
+  }
+  return need;
+}
+
+void carve_scratch(const bem_plan_s* p, const Operator& op, void* base, ScratchPtrs* sp) {
+  const size_t tb = prec_bytes(p);
+  unsigned char* b = static_cast<unsigned char*>(base);
+  size_t off = 0;
+  if (p->v2) {
+    sp->val = b + off;
+    off += align256((size_t)p->nb * 2 * tb);
+    sp->partial = b + off;
+  } else {
+    for (int f = 0; f < op.nf; ++f) {
+      sp->rho[f] = b + off;
+      off += align256((size_t)op.f[f].set->nelem * tb);
+    }
+    sp->partial = b + off;
+  }
+}
+
+bem_status launch_apply_2d_with(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
+                                bool timed, cudaStream_t st) {
   if (op.nf < 1 || op.nf > 3) {
     set_error("2D operator with unsupported field count");
     return BEM_ERR_UNSUPPORTED;
   }
-  return p->prec == BEM_F64 ? launch_t_scratch<double>(p, op, in, out, rho, partial, st)
-                            : launch_t_scratch<float>(p, op, in, out, rho, partial, st);
+  if (p->v2)
+    return p->prec == BEM_F64 ? launch_v2<double>(p, op, in, out, sp, timed, st)
+                              : launch_v2<float>(p, op, in, out, sp, timed, st);
+  return p->prec == BEM_F64 ? launch_v1<double>(p, op, in, out, sp, timed, st)
+                            : launch_v1<float>(p, op, in, out, sp, timed, st);
 }
 
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st) {
-  if (op.nf < 1 || op.nf > 3) {
-    set_error("2D operator with unsupported field count");
-    return BEM_ERR_UNSUPPORTED;
+  ScratchPtrs sp{};
+  if (p->v2) {
+    sp.val = p->d_val;
+  } else {
+    for (int f = 0; f < op.nf; ++f) sp.rho[f] = op.f[f].rho;
   }
-  return p->prec == BEM_F64 ? launch_t<double>(p, op, in, out, st) : launch_t<float>(p, op, in, out, st);
+  sp.partial = p->d_partial;
+  return launch_apply_2d_with(p, op, in, out, sp, p->timing, st);
 }
 
 }  // namespace bemfft

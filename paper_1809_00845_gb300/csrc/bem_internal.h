@@ -67,6 +67,13 @@ struct Operator {
   const void* diag = nullptr;  // nb*ncomp diagonal term (plan precision) or null
   std::vector<void*> owned;    // device arrays owned by this operator
   SlotSet sets[2];             // operator-specific cell sets (BC-split operator)
+  // four-step column kernel (N >= 512): per sorted cell a packed word
+  // x | row << 16 | type << 31 and two coefficients; the density pair of cell
+  // j is (coefA[j], coefB[j]) * in[perm[j]], routed to fields (0, 1) for
+  // type 0 and (1, 2) for type 1.
+  const uint32_t* meta = nullptr;
+  const void* coefA = nullptr;
+  const void* coefB = nullptr;
 };
 
 // Block-Jacobi near-field preconditioner: dense inverses of the operator's
@@ -104,6 +111,11 @@ struct bem_plan_s {
   bool have_bc = false;
   std::vector<uint8_t> h_bc;
   bemfft::BlockPrecond pc;
+  // four-step column kernel: per-thread balanced row ranges and cell ranges
+  bool v2 = false;
+  int32_t* d_rowbeg = nullptr;  // threads + 1
+  int32_t* d_chunk = nullptr;   // threads + 1
+  void* d_val = nullptr;        // nb density pairs (scratch)
   // scratch
   void* d_rho = nullptr;       // unused (densities live with the operators)
   void* d_partial = nullptr;   // grid * all_set.nelem * ncomp
@@ -136,9 +148,20 @@ bem_status setup_apply_2d(bem_plan_s* p);
 bem_status build_slot_set(bem_plan_s* p, const std::vector<uint8_t>& member, SlotSet* s);
 void free_slot_set(SlotSet* s);
 bem_status alloc_field_rho(bem_plan_s* p, Operator& op);
+bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& coefA, const std::vector<double>& coefB,
+                       const std::vector<uint8_t>& type);
+size_t apply_scratch_bytes(const bem_plan_s* p, const Operator& op);
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st);
-bem_status launch_apply_2d_scratch(bem_plan_s* p, const Operator& op, const void* in, void* out, void* const* rho,
-                                   void* partial, cudaStream_t st);
+// Device scratch of one apply: per-field densities (slot layout kernel) or
+// density pairs (four-step kernel), and the per-CTA partial sums.
+struct ScratchPtrs {
+  void* rho[kMaxFields];
+  void* val;
+  void* partial;
+};
+void carve_scratch(const bem_plan_s* p, const Operator& op, void* base, ScratchPtrs* sp);
+bem_status launch_apply_2d_with(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
+                                bool timed, cudaStream_t st);
 // gmres.cu
 bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
                        int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,

@@ -52,6 +52,19 @@ static bem_status build_ops_2d(bem_plan_s* p) {
     wy[j] = p->h_w[j] * p->h_normal[2 * j + 1];
   }
   bem_status rc;
+  if (p->v2) {
+    std::vector<double> zero(nb, 0.0);
+    std::vector<uint8_t> t0(nb, 0);
+    Operator& s = p->op_single;
+    s.nf = 1;
+    s.f[0] = {nullptr, 0, 0, 0, nullptr, nullptr};
+    if ((rc = build_op_v2(p, s, w, zero, t0)) != BEM_OK) return rc;
+    Operator& d = p->op_double;
+    d.nf = 2;
+    d.f[0] = {nullptr, 0, 1, 0, nullptr, nullptr};
+    d.f[1] = {nullptr, 0, 2, 0, nullptr, nullptr};
+    return build_op_v2(p, d, wx, wy, t0);
+  }
   Operator& s = p->op_single;
   s.nf = 1;
   s.f[0] = {nullptr, 0, 0, 0, &p->all_set, nullptr};
@@ -276,6 +289,25 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       ay[j] = p->h_w[j] * p->h_normal[2 * j + 1] * mN;
     }
     for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;  // user order
+    if (p->v2) {
+      // type 0 (Dirichlet): (w, 0) -> fields (U, -); type 1 (Neumann): (w n_x, w n_y) -> (Q_x, Q_y)
+      std::vector<double> ca(nb), cb(nb);
+      std::vector<uint8_t> ty(nb);
+      for (int64_t j = 0; j < nb; ++j) {
+        ty[j] = bc[p->h_perm[j]] ? 1 : 0;
+        ca[j] = ty[j] ? p->h_w[j] * p->h_normal[2 * j] : p->h_w[j];
+        cb[j] = ty[j] ? p->h_w[j] * p->h_normal[2 * j + 1] : 0.0;
+      }
+      s.nf = 3;
+      s.f[0] = {nullptr, 0, 0, 0, nullptr, nullptr};
+      s.f[1] = {nullptr, 0, 1, 0, nullptr, nullptr};
+      s.f[2] = {nullptr, 0, 2, 0, nullptr, nullptr};
+      if ((rc = build_op_v2(p, s, ca, cb, ty)) != BEM_OK) return rc;
+      if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+      p->have_bc = true;
+      p->pc.valid = false;
+      return BEM_OK;
+    }
     std::vector<uint8_t> memD(nb), memN(nb);
     for (int64_t j = 0; j < nb; ++j) {
       memN[j] = bc[p->h_perm[j]] ? 1 : 0;
@@ -425,6 +457,9 @@ bem_status bem_destroy(bem_plan_t p) {
   free_operator(p->op_double);
   free_operator(p->op_system);
   free_slot_set(&p->all_set);
+  cudaFree(p->d_rowbeg);
+  cudaFree(p->d_chunk);
+  cudaFree(p->d_val);
   cudaFree(p->pc.d_inv);
   cudaFree(p->d_rho);
   cudaFree(p->d_partial);

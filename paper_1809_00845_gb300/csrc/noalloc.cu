@@ -35,8 +35,6 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
 }  // namespace
 }  // namespace bemfft
 
@@ -71,16 +69,8 @@ extern "C" bem_status bem_apply_static_scratch(bem_plan_t p, bem_layer layer, co
     set_error("bem_apply_static_scratch: the plan's device must be current");
     return BEM_ERR_ARG;
   }
-  // bytes needed: one density array per field, then grid * slots * ncomp partials
-  const size_t tb = prec_bytes(p);
-  size_t need = 0;
-  size_t rho_off[kMaxFields];
-  for (int f = 0; f < op->nf; ++f) {
-    rho_off[f] = need;
-    need += align256((size_t)op->f[f].set->nelem * tb);
-  }
-  const size_t partial_off = need;
-  need += align256((size_t)p->grid * p->all_set.nelem * p->ncomp * tb);
+  // bytes needed: the densities of every field, then the per-CTA partial sums
+  const size_t need = apply_scratch_bytes(p, *op);
   if (need > kStaticScratchBytes) {
     set_error("bem_apply_static_scratch: this plan needs " + std::to_string(need) +
               " bytes of scratch, more than the static buffer's " + std::to_string(kStaticScratchBytes) +
@@ -101,8 +91,7 @@ extern "C" bem_status bem_apply_static_scratch(bem_plan_t p, bem_layer layer, co
     }
     base = static_cast<unsigned char*>(g_scratch_addr[dev]);
   }
-  void* rho[kMaxFields];
-  for (int f = 0; f < op->nf; ++f) rho[f] = base + rho_off[f];
-  return launch_apply_2d_scratch(p, *op, in_dev, out_dev, rho, base + partial_off,
-                                 static_cast<cudaStream_t>(stream));
+  ScratchPtrs sp{};
+  carve_scratch(p, *op, base, &sp);
+  return launch_apply_2d_with(p, *op, in_dev, out_dev, sp, false, static_cast<cudaStream_t>(stream));
 }

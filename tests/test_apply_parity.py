@@ -142,3 +142,45 @@ def test_star_4096_full_size_sampled_rows(torch_cuda, oracle_mod, prec):
     s_out = gpu_apply(torch_cuda, plan, "single", x)
     ref = oracle_mod.apply("laplace2d", 0, b.cell, b.h, b.w, b.normal, x, rows=(1000, 256))
     assert rel_l2(s_out[1000:1256], ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fourstep_kernel_edge_cases(torch_cuda, oracle_mod, prec):
+    """n >= 256 uses the four-step column kernel: one cell, the four grid
+    corners (largest offsets), and a dense random set where many rows carry
+    several cells and thread row-ranges are uneven."""
+    rng = np.random.default_rng(21)
+    n = 256
+    one = I.Boundary(2, n, np.array([[200, 3]], np.int32), np.array([1.0 / n]), np.array([[0.0, 1.0]]),
+                     np.zeros((1, 2)), np.zeros(1))
+    ref = oracle_mod.apply("laplace2d", 0, one.cell, one.h, one.w, one.normal, np.array([1.5]))
+    assert rel_l2(gpu_apply(torch_cuda, _plan(one, prec), "single", [1.5]), ref) <= TOL[prec]
+    corners = I.Boundary(2, n, np.array([[0, 0], [n - 1, n - 1], [0, n - 1], [n - 1, 0]], np.int32),
+                         np.full(4, 1.0 / n), np.array([[0.6, 0.8]] * 4), np.zeros((4, 2)), np.zeros(4))
+    x = rng.standard_normal(4)
+    p = _plan(corners, prec)
+    for layer, lid in (("single", 0), ("double", 1)):
+        ref = oracle_mod.apply("laplace2d", lid, corners.cell, corners.h, corners.w, corners.normal, x)
+        assert rel_l2(gpu_apply(torch_cuda, p, layer, x), ref) <= TOL[prec]
+    dense = I.random_cells(n, 6000, rng)
+    x = rng.standard_normal(dense.nb)
+    p = _plan(dense, prec)
+    bc = (rng.uniform(size=dense.nb) < 0.5).astype(np.uint8)
+    p.set_bc(bc, 0.5)
+    for layer, lid in (("single", 0), ("double", 1)):
+        ref = oracle_mod.apply("laplace2d", lid, dense.cell, dense.h, dense.w, dense.normal, x)
+        assert rel_l2(gpu_apply(torch_cuda, p, layer, x), ref) <= TOL[prec]
+    ref = oracle_mod.system_apply("laplace2d", dense.cell, dense.h, dense.w, dense.normal, bc, x)
+    assert rel_l2(gpu_apply(torch_cuda, p, "system", x), ref) <= TOL[prec]
+
+
+def test_fourstep_global_accumulators(torch_cuda, oracle_mod):
+    """More cells than the shared-memory accumulators hold (n = 4096, FP32,
+    20000 cells): per-CTA partial sums live in global memory."""
+    rng = np.random.default_rng(33)
+    b = I.random_cells(4096, 20000, rng)
+    x = rng.standard_normal(b.nb)
+    p = _plan(b, "f32")
+    out = gpu_apply(torch_cuda, p, "single", x)
+    ref = oracle_mod.apply("laplace2d", 0, b.cell, b.h, b.w, b.normal, x, rows=(5000, 400))
+    assert rel_l2(out[5000:5400], ref) <= TOL["f32"]
