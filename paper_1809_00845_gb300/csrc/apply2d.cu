@@ -25,8 +25,10 @@
 // when it fits, else its own slice of the partial buffer), and a reduction
 // kernel sums the per-CTA partials in FP64 in the caller's cell order.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "bem_internal.h"
 #include "fft4step.cuh"
@@ -212,17 +214,23 @@ struct Col2Dv2Params {
   const T* spec[3];
   int imag[3];
   int oddy[3];
-  const cplx<T>* qtab;
-  T* partial;  // gridDim.x * nb, sorted cell order
+  const cplx<T>* fstab;  // four-step tables (lane, warp, t5) then sparse tables (hi, lo)
+  T* partial;            // gridDim.x * nb, sorted cell order
   int acc_in_smem;
 };
+
+// number of table entries of the four-step kernel for TT threads, N = 16 TT
+__host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 16 + 512 + TT / 4 + 64; }
+// spectrum column in shared memory, padded by one entry every 16
+__host__ __device__ inline int sspec_entries(int n) { return ((n + 1 + (n + 1) / 16) + 3) & ~3; }
+__device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 
 // Walk cells [c0, c1) (rows r0 <= row < r1) and write the x-DFT of the
 // selected fields per row: FSEL < 0 = all NF fields (field 0 -> out0[row],
 // field f > 0 -> outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.
 template <typename T, int NF, int FSEL>
 __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int c0, int c1, int r0, int r1,
-                                            cplx<T>* out0, cplx<T>* outF, const Twiddles<T>& tw) {
+                                            cplx<T>* out0, cplx<T>* outF, const Twiddles2L<T>& tw) {
   const int Nm = (1 << p.log2N) - 1;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
   int cur = r0;
@@ -281,7 +289,7 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, i
 
 template <typename T>
 __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, int c0, int c1, const cplx<T>* rows,
-                                             const Twiddles<T>& tw, T* acc) {
+                                             const Twiddles2L<T>& tw, T* acc) {
   const int Nm = (1 << p.log2N) - 1;
   const T ckx = (kx == 0 || kx == p.n) ? T(1) : T(2);
   for (int j0 = c0; j0 < c1; j0 += 8) {
@@ -317,7 +325,7 @@ __device__ __forceinline__ int oddy_of(const Col2Dv2Params<T>& p, int f) {
 template <typename T>
 __device__ __forceinline__ void load_spectrum(const Col2Dv2Params<T>& p, int f, int kx, T* sS) {
   const T* S = spec_of(p, f) + (size_t)kx * (p.n + 1);
-  for (int i = threadIdx.x; i <= p.n; i += blockDim.x) sS[i] = __ldg(S + i);
+  for (int i = threadIdx.x; i <= p.n; i += blockDim.x) sS[swz16(i)] = __ldg(S + i);
 }
 
 template <typename T>
@@ -325,7 +333,7 @@ __device__ __forceinline__ cplx<T> spectral_term(const Col2Dv2Params<T>& p, bool
                                                  cplx<T> v) {
   const int N = 1 << p.log2N;
   const bool hi = K > p.n;
-  T sv = sS[hi ? N - K : K];
+  T sv = sS[swz16(hi ? N - K : K)];
   if (hi && oy) sv = -sv;
   return im ? cplx<T>{-v.y * sv, v.x * sv} : cplx<T>{v.x * sv, v.y * sv};
 }
@@ -336,19 +344,21 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
   const int t = threadIdx.x, TT = blockDim.x, W = TT >> 5;
   const int log2N = p.log2N, N = 1 << log2N, n = p.n;
   const int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
+  const int ntab = fstab_entries(TT);
   cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* sq = sA + nbuf;
-  T* sS = reinterpret_cast<T*>(sq + (N >> 2));
-  cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + ((n + 4) & ~3));
+  cplx<T>* stab = sA + nbuf;
+  T* sS = reinterpret_cast<T*>(stab + ntab);
+  cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
   T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
                          : p.partial + (size_t)blockIdx.x * p.nb;
-  for (int i = t; i < (N >> 2); i += TT) sq[i] = p.qtab[i];
+  for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
   const int c0 = p.chunk[t], c1 = p.chunk[t + 1], r0 = p.rowbeg[t], r1 = p.rowbeg[t + 1];
   for (int j = c0; j < c1; ++j) acc[j] = T(0);
   __syncthreads();
-  const Twiddles<T> tw{sq, log2N - 2};
+  const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
+  const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + (N >> 6)};
   FourStep<T> fs;
-  fs.init(t, TT, log2N, sA, tw);
+  fs.init(t, TT, sA, ftab);
 
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
     __syncthreads();  // the previous column's gather has finished reading sA
@@ -613,8 +623,7 @@ template <typename T>
 static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc) {
   const int W = TT / 32;
   const size_t nbuf = (size_t)std::max(16 * TT, W * 544);
-  const int64_t N = 2 * n;
-  size_t s = nbuf * sizeof(cplx<T>) + (size_t)(N / 4) * sizeof(cplx<T>) + (size_t)((n + 4) & ~3) * sizeof(T);
+  size_t s = (nbuf + (size_t)fstab_entries(TT)) * sizeof(cplx<T>) + (size_t)sspec_entries((int)n) * sizeof(T);
   if (accreg) s += (size_t)2 * n * sizeof(cplx<T>);
   if (acc) s += (size_t)nb * sizeof(T);
   return s;
@@ -654,6 +663,31 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     }
     rowbeg[TT] = (int32_t)n;
     chunk[TT] = (int32_t)nb;
+  }
+  {
+    // four-step and sparse twiddle tables, FP64 on the host, rounded once
+    const int W = TT / 32;
+    const int64_t N = p->N;
+    const double PI = 3.14159265358979323846;
+    std::vector<cplx<T>> tab;
+    auto push = [&](double num, double den) {
+      const double a = 2.0 * PI * num / den;
+      tab.push_back({(T)std::cos(a), (T)std::sin(a)});
+    };
+    for (int k = 0; k < 16; ++k)
+      for (int l = 0; l < 32; ++l) push((double)(l * k), (double)N);                  // lane
+    for (int a = 0; a < W; ++a)
+      for (int k = 0; k < 16; ++k) push((double)(32 * a * k % N), (double)N);         // warp
+    for (int k = 0; k < 16; ++k)
+      for (int l = 0; l < 32; ++l) push((double)((l * k) % TT), (double)TT);           // t5
+    for (int64_t i = 0; i < N / 64; ++i) push((double)(64 * i), (double)N);           // hi
+    for (int i = 0; i < 64; ++i) push((double)i, (double)N);                          // lo
+    if ((int)tab.size() != fstab_entries(TT)) {
+      set_error("internal: twiddle table size");
+      return BEM_ERR_CUDA;
+    }
+    BEM_CUDA_TRY(cudaMalloc(&p->d_fstab, tab.size() * sizeof(cplx<T>)));
+    BEM_CUDA_TRY(cudaMemcpy(p->d_fstab, tab.data(), tab.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
   }
   BEM_CUDA_TRY(cudaMalloc(&p->d_rowbeg, (TT + 1) * sizeof(int32_t)));
   BEM_CUDA_TRY(cudaMalloc(&p->d_chunk, (TT + 1) * sizeof(int32_t)));
@@ -815,7 +849,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
     cp.imag[f] = s.imag;
     cp.oddy[f] = s.odd[1];
   }
-  cp.qtab = static_cast<const cplx<T>*>(p->d_qtab);
+  cp.fstab = static_cast<const cplx<T>*>(p->d_fstab);
   cp.partial = static_cast<T*>(sp.partial);
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
   cudaEvent_t e1 = nullptr;

@@ -116,6 +116,7 @@ struct bem_plan_s {
   int32_t* d_rowbeg = nullptr;  // threads + 1
   int32_t* d_chunk = nullptr;   // threads + 1
   void* d_val = nullptr;        // nb density pairs (scratch)
+  void* d_fstab = nullptr;      // twiddle tables of the four-step kernel
   // scratch
   void* d_rho = nullptr;       // unused (densities live with the operators)
   void* d_partial = nullptr;   // grid * all_set.nelem * ncomp

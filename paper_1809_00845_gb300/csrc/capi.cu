@@ -460,6 +460,7 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_rowbeg);
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
+  cudaFree(p->d_fstab);
   cudaFree(p->pc.d_inv);
   cudaFree(p->d_rho);
   cudaFree(p->d_partial);

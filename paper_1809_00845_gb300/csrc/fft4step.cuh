@@ -61,62 +61,68 @@ __device__ __forceinline__ void dft16_lowhalf(cplx<T> (&a)[16]) {
   for (int i = 0; i < 16; ++i) a[i] = o[i];
 }
 
+// Twiddle tables of the four-step engine (forward direction e^{+2 pi i ...},
+// conjugated on use), built on the host in FP64 and rounded once:
+//   lane[k*32 + l] = e^{2 pi i l k / N}          (T2, lane factor)
+//   warp[a*16 + k] = e^{2 pi i 32 a k / N}       (T2, warp factor, a < W)
+//   t5[k*32 + l]   = e^{2 pi i l k / TT}         (T5)
+// Every read is either lane-contiguous or warp-uniform, so none conflicts.
+template <typename T>
+struct FourStepTables {
+  const cplx<T>* lane;
+  const cplx<T>* warp;
+  const cplx<T>* t5;
+};
+
 template <typename T>
 struct FourStep {
-  int t, TT, log2N, log2TT;
-  int w, l;      // warp, lane
-  int W, L, J;   // warps, lines per warp, elements per line per lane
-  cplx<T>* sA;   // max(N, W*16*34) elements, shared
-  Twiddles<T> tw;
+  int t, TT;
+  int w, l;             // warp, lane
+  int W, L, J;          // warps, lines per warp, elements per line per lane
+  int lgJ;              // log2(J)
+  cplx<T>* sA;          // max(16*TT, W*16*34) elements, shared
+  FourStepTables<T> tb; // shared-memory copies
 
-  __device__ __forceinline__ void init(int t_, int TT_, int log2N_, cplx<T>* s, const Twiddles<T>& tw_) {
+  __device__ __forceinline__ void init(int t_, int TT_, cplx<T>* s, const FourStepTables<T>& tb_) {
     t = t_;
     TT = TT_;
-    log2N = log2N_;
-    log2TT = log2N_ - 4;
     w = t >> 5;
     l = t & 31;
     W = TT >> 5;
     L = 16 / W;
     J = TT >> 5;
+    lgJ = 31 - __clz(J);
     sA = s;
-    tw = tw_;
+    tb = tb_;
   }
   __device__ __forceinline__ void cta_sync() const {
     if (W > 1) __syncthreads();
     else __syncwarp();
   }
-  // e^{DIR 2 pi i m / N}
   template <int DIR>
-  __device__ __forceinline__ cplx<T> twN(int m) const {
-    return tw.template get<DIR>(m & ((1 << log2N) - 1));
+  static __device__ __forceinline__ cplx<T> dirw(cplx<T> z) {
+    if constexpr (DIR < 0) z.y = -z.y;
+    return z;
   }
-  // v[k] *= w^(k) for k = 1..15, w^k = e^{DIR 2 pi i base k / N}: four table
-  // lookups (k = 1, 2, 4, 8) and products of at most three of them.
+  // T2: v[k] *= e^{DIR 2 pi i t k / N}, t = 32 w + l
   template <int DIR>
-  __device__ __forceinline__ void twiddle16(cplx<T> (&v)[16], int base) const {
-    const cplx<T> w1 = twN<DIR>(base), w2 = twN<DIR>(2 * base), w4 = twN<DIR>(4 * base), w8 = twN<DIR>(8 * base);
-    const cplx<T> w3 = cmul(w1, w2), w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
-    const cplx<T> w9 = cmul(w8, w1), w10 = cmul(w8, w2), w11 = cmul(w8, w3), w12 = cmul(w8, w4);
-    const cplx<T> w13 = cmul(w8, w5), w14 = cmul(w8, w6), w15 = cmul(w8, w7);
-    v[1] = cmul(v[1], w1);
-    v[2] = cmul(v[2], w2);
-    v[3] = cmul(v[3], w3);
-    v[4] = cmul(v[4], w4);
-    v[5] = cmul(v[5], w5);
-    v[6] = cmul(v[6], w6);
-    v[7] = cmul(v[7], w7);
-    v[8] = cmul(v[8], w8);
-    v[9] = cmul(v[9], w9);
-    v[10] = cmul(v[10], w10);
-    v[11] = cmul(v[11], w11);
-    v[12] = cmul(v[12], w12);
-    v[13] = cmul(v[13], w13);
-    v[14] = cmul(v[14], w14);
-    v[15] = cmul(v[15], w15);
+  __device__ __forceinline__ void twiddleT2(cplx<T> (&v)[16]) const {
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+      const cplx<T> z = cmul(tb.warp[w * 16 + k], tb.lane[k * 32 + l]);
+      v[k] = cmul(v[k], dirw<DIR>(z));
+    }
   }
-
-  // line-local J-point DFTs on u[a*J + j] (J = 16/L), direction DIR
+  // T5: u[a*J + kj] *= e^{DIR 2 pi i l kj / TT}
+  template <int DIR>
+  __device__ __forceinline__ void twiddleT5(cplx<T> (&u)[16]) const {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int kj = i & (J - 1);
+      if (kj) u[i] = cmul(u[i], dirw<DIR>(tb.t5[kj * 32 + l]));
+    }
+  }
+  // line-local J-point DFTs on u[a*J + j], direction DIR
   template <int DIR>
   __device__ __forceinline__ void dftJ(cplx<T> (&u)[16]) const {
     if (J == 16) {
@@ -139,44 +145,26 @@ struct FourStep {
       for (int a = 0; a < 8; ++a) dft2<DIR>(u[a * 2], u[a * 2 + 1]);
     }
   }
-  // u[a*J + kj] *= e^{DIR 2 pi i l kj / TT}
-  template <int DIR>
-  __device__ __forceinline__ void twiddleT5(cplx<T> (&u)[16]) const {
-    if (J == 1) return;
-    const int s = 1 << (log2N - log2TT);  // table stride for N/TT
-    if (J == 16) {
-      twiddle16<DIR>(u, l * s);
-      return;
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int kj = i & (J - 1);
-      if (kj) u[i] = cmul(u[i], twN<DIR>(l * kj * s));
-    }
+  // shared-memory index of register a in the transposed (line) layout
+  __device__ __forceinline__ int lineidx(int a) const {
+    return (w * L + (a >> lgJ)) * TT + l + 32 * (a & (J - 1));
   }
 
-  // ---- forward: registers in natural position order -> scrambled spectrum
-  // sync_first: the previous call on this buffer was forward() (its warp
-  // transposes may still be reading), so wait before rewriting the buffer.
+  // ---- forward: registers in natural position order -> scrambled spectrum.
+  // The caller guarantees that nobody still reads sA (previous use).
   template <bool LOWHALF>
-  __device__ __forceinline__ void forward(cplx<T> (&v)[16], bool sync_first = false) const {
-    if (sync_first) cta_sync();
+  __device__ __forceinline__ void forward(cplx<T> (&v)[16]) const {
     if constexpr (LOWHALF) dft16_lowhalf<-1>(v);
     else dft<16, -1>(v);
-    twiddle16<-1>(v, t);
-    // A: smem[k1][t]
+    twiddleT2<-1>(v);
 #pragma unroll
     for (int k = 0; k < 16; ++k) sA[k * TT + t] = v[k];
     cta_sync();
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
-      const int line = w * L + a / J, j = a % J;
-      v[a] = sA[line * TT + l + 32 * j];
-    }
+    for (int a = 0; a < 16; ++a) v[a] = sA[lineidx(a)];
     cta_sync();
     dftJ<-1>(v);
     twiddleT5<-1>(v);
-    // B: warp region, row d = a*J + kj = register index, 34-element rows
     cplx<T>* sB = sA + w * (16 * 34);
 #pragma unroll
     for (int d = 0; d < 16; ++d) sB[d * 34 + l] = v[d];
@@ -196,18 +184,17 @@ struct FourStep {
       v[k] = h ? other - mine : mine + other;
     }
   }
-  // frequency held by register k after forward()
-  __device__ __forceinline__ int freq(int k) const {
+  // frequency held by register k after forward(): freq0() + 16 * J * k
+  __device__ __forceinline__ int freq0() const {
     const int d = l >> 1, h = l & 1;
-    const int a = d / J, kj = d % J;
-    const int k1 = w * L + a;
-    const int kl = k + 16 * h;
-    return k1 + 16 * (kj + J * kl);
+    const int a = d >> lgJ, kj = d & (J - 1);
+    return (w * L + a) + 16 * (kj + J * 16 * h);
   }
-  // ---- inverse: scrambled spectrum -> registers in natural position order
+  __device__ __forceinline__ int freq(int k) const { return freq0() + 16 * J * k; }
+  // ---- inverse: scrambled spectrum -> registers in natural position order.
+  // Ends with a barrier after its last shared-memory read.
   __device__ __forceinline__ void inverse(cplx<T> (&v)[16]) const {
     const int d = l >> 1, h = l & 1;
-    // S8^H: lane 0 holds A, lane 1 holds B: E0 = A + B, E1 = conj(w)(A - B)
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       cplx<T> other;
@@ -226,16 +213,27 @@ struct FourStep {
     dftJ<+1>(v);
     cta_sync();  // every warp is done with its B region before A is rewritten
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
-      const int line = w * L + a / J, j = a % J;
-      sA[line * TT + l + 32 * j] = v[a];
-    }
+    for (int a = 0; a < 16; ++a) sA[lineidx(a)] = v[a];
     cta_sync();
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = sA[k * TT + t];
     cta_sync();
-    twiddle16<+1>(v, t);
+    twiddleT2<+1>(v);
     dft<16, +1>(v);
+  }
+};
+
+// e^{DIR 2 pi i m / N} from two small tables: m = 64 hi + lo,
+// hi[i] = e^{2 pi i 64 i / N}, lo[i] = e^{2 pi i i / N} (N/64 + 64 entries).
+template <typename T>
+struct Twiddles2L {
+  const cplx<T>* hi;
+  const cplx<T>* lo;
+  template <int DIR>
+  __device__ __forceinline__ cplx<T> get(int m) const {
+    cplx<T> z = cmul(hi[m >> 6], lo[m & 63]);
+    if constexpr (DIR < 0) z.y = -z.y;
+    return z;
   }
 };
 

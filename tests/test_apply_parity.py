@@ -30,6 +30,22 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+def fp32_abs_bound(b, x, layer):
+    """Absolute error bound of an FP32 FFT apply: its rounding error is
+    relative to the whole convolution, about eps32 * log2(N^2) * max|K| *
+    sum_j |w_j x_j|, not to the (possibly much smaller) values at the targets.
+    Used for degenerate cell sets whose outputs cancel far below the kernel's
+    near-field scale; random dense inputs are held to the relative bar."""
+    import math
+    h = b.h
+    L2 = math.pi / 4 - 1.5 - 0.5 * math.log(2)
+    if layer == "single":
+        kmax = max(abs(-(math.log(h) + L2) / (2 * math.pi)), abs(math.log(h * b.n * 2 ** 0.5)) / (2 * math.pi))
+    else:
+        kmax = 1.0 / (2 * math.pi * h)
+    return 6e-8 * math.log2((2 * b.n) ** 2) * kmax * float(np.sum(np.abs(b.w * np.asarray(x))))
+
+
 def gpu_apply(torch, plan, layer, x):
     t = torch.from_numpy(np.asarray(x, dtype=plan.np_dtype)).cuda()
     y = plan.apply(layer, t)
@@ -161,7 +177,11 @@ def test_fourstep_kernel_edge_cases(torch_cuda, oracle_mod, prec):
     p = _plan(corners, prec)
     for layer, lid in (("single", 0), ("double", 1)):
         ref = oracle_mod.apply("laplace2d", lid, corners.cell, corners.h, corners.w, corners.normal, x)
-        assert rel_l2(gpu_apply(torch_cuda, p, layer, x), ref) <= TOL[prec]
+        out = gpu_apply(torch_cuda, p, layer, x)
+        if prec == "f64":
+            assert rel_l2(out, ref) <= TOL[prec]
+        else:  # four far-apart cells: outputs ~1e-4 of the near-field scale
+            assert np.max(np.abs(out - ref)) <= fp32_abs_bound(corners, x, layer)
     dense = I.random_cells(n, 6000, rng)
     x = rng.standard_normal(dense.nb)
     p = _plan(dense, prec)
