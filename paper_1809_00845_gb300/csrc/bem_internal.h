@@ -76,6 +76,25 @@ struct Operator {
   const void* coefB = nullptr;
 };
 
+// 3D operators: field f scatters coef_f[j] * in[perm[j]*ncomp + comp]; output
+// o sums K_{coup[o][f]} * field f over the fields (coup < 0: no coupling).
+struct Field3D {
+  const void* coef;  // nb, sorted order, plan precision
+  int comp;
+};
+struct Spec3D {
+  const void* data;  // (n+1)^3 reals, [kx][ky][kz]; K^ = i^q * S
+  int q;             // number of axes in which the kernel is odd
+  int oddy, oddz;    // fold signs for ky, kz > n
+};
+struct Operator3D {
+  int nf = 0, no = 0, lpc = 1;
+  Field3D* d_fields = nullptr;  // nf (device)
+  int16_t* d_coup = nullptr;    // no * nf (device)
+  const void* diag = nullptr;   // nb*ncomp (caller order) or null
+  std::vector<void*> owned;
+};
+
 // Block-Jacobi near-field preconditioner: dense inverses of the operator's
 // diagonal blocks of consecutive cells (caller order).
 struct BlockPrecond {
@@ -117,6 +136,19 @@ struct bem_plan_s {
   int32_t* d_chunk = nullptr;   // threads + 1
   void* d_val = nullptr;        // nb density pairs (scratch)
   void* d_fstab = nullptr;      // twiddle tables of the four-step kernel
+  // 3D path
+  int32_t* d_lptr = nullptr;    // n*n + 1 line pointers over sorted cells (line = z*n + y)
+  uint16_t* d_x3 = nullptr;     // x per sorted cell
+  uint32_t* d_yz3 = nullptr;    // y | z << 16 per sorted cell
+  void* d_tw2 = nullptr;        // 2-level twiddles (N/64 + 64)
+  void* d_val3 = nullptr;       // maxnf * nb
+  void* d_X3 = nullptr;         // maxnf * (n+1) * n * n complex
+  void* d_B3 = nullptr;         // maxnf * (n+1) * N * n complex
+  int maxnf3 = 0;
+  bemfft::Spec3D* d_specs3 = nullptr;
+  std::vector<bemfft::Spec3D> h_specs3;
+  std::vector<int32_t> h_z;     // sorted order z
+  bemfft::Operator3D op3_single, op3_double, op3_system;
   // scratch
   void* d_rho = nullptr;       // unused (densities live with the operators)
   void* d_partial = nullptr;   // grid * all_set.nelem * ncomp
@@ -144,6 +176,15 @@ namespace bemfft {
 
 // spectra.cu
 bem_status compute_spectra_2d(bem_plan_s* p, cudaStream_t st);
+bem_status compute_spectra_3d(bem_plan_s* p, cudaStream_t st);
+// apply3d.cu
+bem_status setup_apply_3d(bem_plan_s* p, int maxnf);
+int zpass_lpc(const bem_plan_s* p, int nf);
+bem_status launch_apply_3d(bem_plan_s* p, const Operator3D& op, const void* in, void* out, void* val, void* X, void* B,
+                           cudaStream_t st);
+size_t buffers3d_bytes(const bem_plan_s* p, int nf);
+// index of a 3D spectrum: Laplace U=0, Q_a=1+a; Kelvin U_ab (a<=b) 0..5, G_abc 6 + 9a + 3b + c
+int kelvin_u_index(int a, int b);
 // apply2d.cu
 bem_status setup_apply_2d(bem_plan_s* p);
 bem_status build_slot_set(bem_plan_s* p, const std::vector<uint8_t>& member, SlotSet* s);

@@ -80,6 +80,85 @@ static bem_status build_ops_2d(bem_plan_s* p) {
   return BEM_OK;
 }
 
+static void free_operator3(Operator3D& op) {
+  for (void* d : op.owned) cudaFree(d);
+  op.owned.clear();
+  op.nf = op.no = 0;
+  op.d_fields = nullptr;
+  op.d_coup = nullptr;
+  op.diag = nullptr;
+}
+
+// coefs[f] (sorted order, FP64 on the host), comps[f], coupling no x nf
+static bem_status build_op3(bem_plan_s* p, Operator3D& op, const std::vector<std::vector<double>>& coefs,
+                            const std::vector<int>& comps, int no, const std::vector<int16_t>& coup) {
+  free_operator3(op);
+  const int nf = (int)coefs.size();
+  std::vector<Field3D> fields(nf);
+  const size_t tb = prec_bytes(p);
+  for (int f = 0; f < nf; ++f) {
+    void* d = nullptr;
+    BEM_CUDA_TRY(cudaMalloc(&d, coefs[f].size() * tb));
+    if (p->prec == BEM_F64) {
+      BEM_CUDA_TRY(cudaMemcpy(d, coefs[f].data(), coefs[f].size() * tb, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> v(coefs[f].begin(), coefs[f].end());
+      BEM_CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * tb, cudaMemcpyHostToDevice));
+    }
+    op.owned.push_back(d);
+    fields[f] = {d, comps[f]};
+  }
+  void* df = nullptr;
+  BEM_CUDA_TRY(cudaMalloc(&df, nf * sizeof(Field3D)));
+  BEM_CUDA_TRY(cudaMemcpy(df, fields.data(), nf * sizeof(Field3D), cudaMemcpyHostToDevice));
+  op.owned.push_back(df);
+  void* dc = nullptr;
+  BEM_CUDA_TRY(cudaMalloc(&dc, coup.size() * sizeof(int16_t)));
+  BEM_CUDA_TRY(cudaMemcpy(dc, coup.data(), coup.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  op.owned.push_back(dc);
+  op.d_fields = static_cast<Field3D*>(df);
+  op.d_coup = static_cast<int16_t*>(dc);
+  op.nf = nf;
+  op.no = no;
+  op.lpc = zpass_lpc(p, nf);
+  return BEM_OK;
+}
+
+// Single and double layer of the 3D kernels.  Laplace: U / (Q_x, Q_y, Q_z)
+// (spectra 0, 1..3).  Kelvin: U_ab (fields b, outputs a) and T_ab = sum_c
+// G_abc n_c (fields (b, c) with coefficient w n_c, outputs a).
+static bem_status build_ops_3d(bem_plan_s* p) {
+  const int64_t nb = p->nb;
+  const std::vector<double>& w = p->h_w;
+  bem_status rc;
+  if (p->kernel == BEM_LAPLACE_3D) {
+    if ((rc = build_op3(p, p->op3_single, {w}, {0}, 1, {0})) != BEM_OK) return rc;
+    std::vector<std::vector<double>> c(3, std::vector<double>(nb));
+    for (int a = 0; a < 3; ++a)
+      for (int64_t j = 0; j < nb; ++j) c[a][j] = w[j] * p->h_normal[3 * j + a];
+    return build_op3(p, p->op3_double, c, {0, 0, 0}, 1, {1, 2, 3});
+  }
+  {
+    std::vector<int16_t> coup(9);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) coup[a * 3 + b] = (int16_t)kelvin_u_index(a, b);
+    if ((rc = build_op3(p, p->op3_single, {w, w, w}, {0, 1, 2}, 3, coup)) != BEM_OK) return rc;
+  }
+  std::vector<std::vector<double>> c;
+  std::vector<int> comps;
+  for (int b = 0; b < 3; ++b)
+    for (int cc = 0; cc < 3; ++cc) {
+      std::vector<double> v(nb);
+      for (int64_t j = 0; j < nb; ++j) v[j] = w[j] * p->h_normal[3 * j + cc];
+      c.push_back(v);
+      comps.push_back(b);
+    }
+  std::vector<int16_t> coup(27);
+  for (int a = 0; a < 3; ++a)
+    for (int f = 0; f < 9; ++f) coup[a * 9 + f] = (int16_t)(6 + 9 * a + f);  // f = 3b + c
+  return build_op3(p, p->op3_double, c, comps, 3, coup);
+}
+
 }  // namespace bemfft
 
 using namespace bemfft;
@@ -128,10 +207,6 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     set_error("bem_plan: n must be a power of two >= 4");
     return BEM_ERR_UNSUPPORTED;
   }
-  if (kernel != BEM_LAPLACE_2D) {
-    set_error("bem_plan: 3D kernels are not available in this build");
-    return BEM_ERR_UNSUPPORTED;
-  }
   if (kernel == BEM_KELVIN_3D && (!(mu > 0.0) || !(nu < 0.5) || !(nu > -1.0))) {
     set_error("bem_plan: need mu > 0 and -1 < nu < 1/2");
     return BEM_ERR_ARG;
@@ -173,7 +248,10 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   // sort cells by row (y), then x; reject duplicates
   std::vector<int32_t> perm(nb);
   std::iota(perm.begin(), perm.end(), 0);
-  auto key = [&](int32_t j) { return (int64_t)cell[(int64_t)j * dim + 1] * nn + cell[(int64_t)j * dim]; };
+  auto key = [&](int32_t j) {
+    const int64_t z = dim == 3 ? cell[(int64_t)j * dim + 2] : 0;
+    return (z * nn + cell[(int64_t)j * dim + 1]) * nn + cell[(int64_t)j * dim];
+  };
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
   for (int64_t j = 1; j < nb; ++j)
     if (key(perm[j]) == key(perm[j - 1])) {
@@ -195,6 +273,7 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     col[j] = cell[(int64_t)u * dim];
     p->h_row[j] = cell[(int64_t)u * dim + 1];
     p->h_col[j] = col[j];
+    if (dim == 3) p->h_z.push_back(cell[(int64_t)u * dim + 2]);
     p->h_w[j] = w[u];
     for (int a = 0; a < dim; ++a) p->h_normal[j * dim + a] = normal[(int64_t)u * dim + a];
   }
@@ -238,10 +317,32 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
       PLAN_CUDA(cudaMemcpy(p->d_qtab, q.data(), q.size() * sizeof(q[0]), cudaMemcpyHostToDevice));
     }
   }
-  bem_status rc = compute_spectra_2d(p, st);
-  if (rc != BEM_OK) return fail(rc);
-  if ((rc = setup_apply_2d(p)) != BEM_OK) return fail(rc);
-  if ((rc = build_ops_2d(p)) != BEM_OK) return fail(rc);
+  bem_status rc;
+  if (dim == 2) {
+    if ((rc = compute_spectra_2d(p, st)) != BEM_OK) return fail(rc);
+    if ((rc = setup_apply_2d(p)) != BEM_OK) return fail(rc);
+    if ((rc = build_ops_2d(p)) != BEM_OK) return fail(rc);
+  } else {
+    // line pointers over the sorted cells (line = z*n + y) and packed coordinates
+    std::vector<int32_t> lptr(nn * nn + 1, 0);
+    std::vector<uint16_t> x3(nb);
+    std::vector<uint32_t> yz3(nb);
+    for (int64_t j = 0; j < nb; ++j) {
+      lptr[(int64_t)p->h_z[j] * nn + p->h_row[j] + 1]++;
+      x3[j] = (uint16_t)p->h_col[j];
+      yz3[j] = (uint32_t)p->h_row[j] | ((uint32_t)p->h_z[j] << 16);
+    }
+    for (int64_t l = 0; l < nn * nn; ++l) lptr[l + 1] += lptr[l];
+    PLAN_CUDA(cudaMalloc(&p->d_lptr, lptr.size() * sizeof(int32_t)));
+    PLAN_CUDA(cudaMalloc(&p->d_x3, nb * sizeof(uint16_t)));
+    PLAN_CUDA(cudaMalloc(&p->d_yz3, nb * sizeof(uint32_t)));
+    PLAN_CUDA(cudaMemcpy(p->d_lptr, lptr.data(), lptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    PLAN_CUDA(cudaMemcpy(p->d_x3, x3.data(), nb * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    PLAN_CUDA(cudaMemcpy(p->d_yz3, yz3.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    if ((rc = compute_spectra_3d(p, st)) != BEM_OK) return fail(rc);
+    if ((rc = setup_apply_3d(p, kernel == BEM_KELVIN_3D ? 12 : 4)) != BEM_OK) return fail(rc);
+    if ((rc = build_ops_3d(p)) != BEM_OK) return fail(rc);
+  }
   PLAN_CUDA(cudaStreamSynchronize(st));
 #undef PLAN_CUDA
   p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -324,9 +425,48 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     if ((rc = upload_coef(p, s, ay, &s.f[2].coef)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
     if ((rc = alloc_field_rho(p, s)) != BEM_OK) return rc;
+  } else if (p->kernel == BEM_LAPLACE_3D) {
+    // A x = S(x m_D) + D(x m_N) - c x m_N: fields U (w m_D), Q_a (w n_a m_N)
+    std::vector<std::vector<double>> cf(4, std::vector<double>(nb));
+    std::vector<double> dg(nb);
+    for (int64_t j = 0; j < nb; ++j) {
+      const double mN = bc[p->h_perm[j]] ? 1.0 : 0.0;
+      cf[0][j] = p->h_w[j] * (1.0 - mN);
+      for (int a = 0; a < 3; ++a) cf[1 + a][j] = p->h_w[j] * p->h_normal[3 * j + a] * mN;
+    }
+    for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;
+    if ((rc = build_op3(p, p->op3_system, cf, {0, 0, 0, 0}, 1, {0, 1, 2, 3})) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+    p->op3_system.diag = s.diag;
   } else {
-    set_error("bem_set_bc: kernel not available");
-    return BEM_ERR_UNSUPPORTED;
+    // Navier (Eq. 8): A x = U(x m_D) - T(x m_N) - c x m_N per component:
+    // fields b (w m_D,b) -> U_ab and fields (b, c) (-w n_c m_N,b) -> G_abc
+    std::vector<std::vector<double>> cf;
+    std::vector<int> comps;
+    for (int b = 0; b < 3; ++b) {
+      std::vector<double> v(nb);
+      for (int64_t j = 0; j < nb; ++j) v[j] = bc[(int64_t)p->h_perm[j] * 3 + b] ? 0.0 : p->h_w[j];
+      cf.push_back(v);
+      comps.push_back(b);
+    }
+    for (int b = 0; b < 3; ++b)
+      for (int cc = 0; cc < 3; ++cc) {
+        std::vector<double> v(nb);
+        for (int64_t j = 0; j < nb; ++j)
+          v[j] = bc[(int64_t)p->h_perm[j] * 3 + b] ? -p->h_w[j] * p->h_normal[3 * j + cc] : 0.0;
+        cf.push_back(v);
+        comps.push_back(b);
+      }
+    std::vector<int16_t> coup(3 * 12);
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) coup[a * 12 + b] = (int16_t)kelvin_u_index(a, b);
+      for (int f = 0; f < 9; ++f) coup[a * 12 + 3 + f] = (int16_t)(6 + 9 * a + f);
+    }
+    std::vector<double> dg(nb * 3);
+    for (int64_t i = 0; i < nb * 3; ++i) dg[i] = bc[i] ? -c : 0.0;
+    if ((rc = build_op3(p, p->op3_system, cf, comps, 3, coup)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+    p->op3_system.diag = s.diag;
   }
   p->have_bc = true;
   p->pc.valid = false;
@@ -442,7 +582,8 @@ bem_status bem_kernel_time(bem_plan_t p, double* total_ms, int64_t* launches) {
 int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
   (void)layer;
   if (!p) return -1;
-  return 3;  // prep (weighted densities), fused column kernel, reduction
+  if (p->dim == 3) return 6;  // prep, x-DFT, y pass, z pass, inverse y pass, gather
+  return 3;                   // prep (weighted densities), fused column kernel, reduction
 }
 
 bem_status bem_destroy(bem_plan_t p) {
@@ -461,6 +602,18 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
   cudaFree(p->d_fstab);
+  free_operator3(p->op3_single);
+  free_operator3(p->op3_double);
+  free_operator3(p->op3_system);
+  cudaFree(p->d_lptr);
+  cudaFree(p->d_x3);
+  cudaFree(p->d_yz3);
+  cudaFree(p->d_tw2);
+  cudaFree(p->d_val3);
+  cudaFree(p->d_X3);
+  cudaFree(p->d_B3);
+  for (auto& sp : p->h_specs3) cudaFree(const_cast<void*>(sp.data));
+  cudaFree(p->d_specs3);
   cudaFree(p->pc.d_inv);
   cudaFree(p->d_rho);
   cudaFree(p->d_partial);
@@ -496,6 +649,22 @@ const char* bem_last_error(void) { return g_last_error.c_str(); }
 namespace bemfft {
 
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st) {
+  if (p->dim == 3) {
+    const Operator3D* op3 = nullptr;
+    if (layer == BEM_SINGLE) op3 = &p->op3_single;
+    else if (layer == BEM_DOUBLE) op3 = &p->op3_double;
+    else if (layer == BEM_SYSTEM) {
+      if (!p->have_bc) {
+        set_error("bem_apply: BEM_SYSTEM needs bem_set_bc first");
+        return BEM_ERR_ARG;
+      }
+      op3 = &p->op3_system;
+    } else {
+      set_error("bem_apply: unknown layer");
+      return BEM_ERR_ARG;
+    }
+    return launch_apply_3d(p, *op3, in, out, p->d_val3, p->d_X3, p->d_B3, st);
+  }
   const Operator* op = nullptr;
   if (layer == BEM_SINGLE) op = &p->op_single;
   else if (layer == BEM_DOUBLE) op = &p->op_double;

@@ -179,7 +179,15 @@ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 // One Stockham pass of radix R on the register set v (E per thread).
 // Ns: product of the radices of the previous passes.  If LAST, outputs stay
 // in registers (natural order); otherwise they go to smem and are read back.
-template <int E, int R, int DIR, bool LAST, typename T>
+// Barrier between Stockham passes: the whole CTA (one line per CTA) or, with
+// WARP, the warp (lines of at most 32 threads, several lines per CTA).
+template <bool WARP>
+__device__ __forceinline__ void line_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
+template <int E, int R, int DIR, bool LAST, typename T, bool WARP = false>
 __device__ __forceinline__ void stockham_pass(cplx<T> (&v)[E], const int t, const int TT, const int log2Ns,
                                               const int log2N, const Twiddles<T>& tw, cplx<T>* sbuf) {
   constexpr int S = E / R;
@@ -209,17 +217,17 @@ __device__ __forceinline__ void stockham_pass(cplx<T> (&v)[E], const int t, cons
     }
   }
   if constexpr (!LAST) {
-    __syncthreads();
+    line_sync<WARP>();
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = sbuf[pad16(t + m * TT)];
-    __syncthreads();
+    line_sync<WARP>();
   }
 }
 
 // Full transform of one line held in registers (positions t + m*TT) with
 // radix-E passes followed by one smaller last pass when log2(N) is not a
 // multiple of log2(E).  Result in natural order in the same register map.
-template <int E, int DIR, typename T>
+template <int E, int DIR, typename T, bool WARP = false>
 __device__ __forceinline__ void fft_line(cplx<T> (&v)[E], const int t, const int TT, const int log2N,
                                          const Twiddles<T>& tw, cplx<T>* sbuf) {
   constexpr int LE = (E == 16) ? 4 : (E == 8) ? 3 : (E == 4) ? 2 : 1;
@@ -229,17 +237,17 @@ __device__ __forceinline__ void fft_line(cplx<T> (&v)[E], const int t, const int
   const int nfirst = rem == 0 ? full - 1 : full;
   int lNs = 0;
   for (int p = 0; p < nfirst; ++p) {
-    stockham_pass<E, E, DIR, false>(v, t, TT, lNs, log2N, tw, sbuf);
+    stockham_pass<E, E, DIR, false, T, WARP>(v, t, TT, lNs, log2N, tw, sbuf);
     lNs += LE;
   }
   if (rem == 0) {
-    stockham_pass<E, E, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
+    stockham_pass<E, E, DIR, true, T, WARP>(v, t, TT, lNs, log2N, tw, sbuf);
   } else if (rem == 1) {
-    stockham_pass<E, 2, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
+    stockham_pass<E, 2, DIR, true, T, WARP>(v, t, TT, lNs, log2N, tw, sbuf);
   } else if (rem == 2) {
-    if constexpr (E >= 4) stockham_pass<E, 4, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
+    if constexpr (E >= 4) stockham_pass<E, 4, DIR, true, T, WARP>(v, t, TT, lNs, log2N, tw, sbuf);
   } else if (rem == 3) {
-    if constexpr (E >= 8) stockham_pass<E, 8, DIR, true>(v, t, TT, lNs, log2N, tw, sbuf);
+    if constexpr (E >= 8) stockham_pass<E, 8, DIR, true, T, WARP>(v, t, TT, lNs, log2N, tw, sbuf);
   }
 }
 

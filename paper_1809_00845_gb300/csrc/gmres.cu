@@ -144,7 +144,8 @@ struct Gm {
     if (p->pc.kind == 0) {
       cudaMemcpyAsync(z, v, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
     } else {
-      k_block_apply<<<p->pc.nblocks, p->pc.bs, p->pc.bs * sizeof(double), st>>>(p->pc.d_inv, p->pc.bs, M, v, z);
+      const int m = p->pc.bs * p->ncomp;
+      k_block_apply<<<p->pc.nblocks, m, m * sizeof(double), st>>>(p->pc.d_inv, m, M, v, z);
     }
   }
   // out[0..nvec) = V[0..nvec) . w   (device)

@@ -32,6 +32,47 @@ double kernel2d_point(int kind, int dx, int dy, double h) {
   return -da / (2.0 * PI * h * r2);
 }
 
+// 3D kernels at grid offset delta (d = delta h), same definitions as the FFT
+// tables: U3 = 1/(4 pi r), Q3_a = -d_a/(4 pi r^3), Kelvin U_ab (Eq. 7) and the
+// traction block T_ab(d; n) = sum_c G_abc(d) n_c (Eq. 8); singular cell as in
+// the tables.
+static void kernel3d_block(int kernel, const int* dl, const double* nrm, double h, double nu, double mu,
+                           bool single, double* out) {
+  const double PI = 3.14159265358979323846;
+  const double C3 = 3.0 * std::log(2.0 + std::sqrt(3.0)) - PI / 2.0;
+  const bool zero = dl[0] == 0 && dl[1] == 0 && dl[2] == 0;
+  const double d[3] = {dl[0] * h, dl[1] * h, dl[2] * h};
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double r = std::sqrt(r2), r3 = r2 * r;
+  if (kernel == BEM_LAPLACE_3D) {
+    if (single) {
+      out[0] = zero ? C3 / (4.0 * PI * h) : 1.0 / (4.0 * PI * r);
+    } else {
+      out[0] = 0.0;
+      if (!zero)
+        for (int a = 0; a < 3; ++a) out[0] += -d[a] / (4.0 * PI * r3) * nrm[a];
+    }
+    return;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double v = 0.0;
+      if (single) {
+        if (zero)
+          v = a == b ? (3.0 - 4.0 * nu + 1.0 / 3.0) * C3 / (16.0 * PI * mu * (1.0 - nu) * h) : 0.0;
+        else
+          v = (((a == b) ? (3.0 - 4.0 * nu) / r : 0.0) + d[a] * d[b] / r3) / (16.0 * PI * mu * (1.0 - nu));
+      } else if (!zero) {
+        for (int c = 0; c < 3; ++c) {
+          const double lin = (a == b ? d[c] : 0.0) + (a == c ? d[b] : 0.0) - (b == c ? d[a] : 0.0);
+          const double g = ((1.0 - 2.0 * nu) * lin / r3 + 3.0 * d[a] * d[b] * d[c] / (r3 * r2)) / (8.0 * PI * (1.0 - nu));
+          v += g * nrm[c];
+        }
+      }
+      out[a * 3 + b] = v;
+    }
+}
+
 // Gauss-Jordan inversion with partial pivoting (row-major m x m, in place).
 static bool invert(std::vector<double>& A, int m) {
   std::vector<double> I((size_t)m * m, 0.0);
@@ -72,38 +113,47 @@ bem_status build_preconditioner(bem_plan_s* p) {
     set_error("preconditioner needs boundary conditions");
     return BEM_ERR_ARG;
   }
-  if (p->kernel != BEM_LAPLACE_2D) {
-    set_error("block preconditioner not available for this kernel");
-    return BEM_ERR_UNSUPPORTED;
-  }
   const int64_t nb = p->nb;
   const int bs = p->pc.bs;
+  const int nc = p->ncomp;
   const int nblocks = (int)((nb + bs - 1) / bs);
-  const int m = bs;  // ncomp = 1
+  const int m = bs * nc;
   std::vector<double> all((size_t)nblocks * m * m, 0.0);
   const double c = p->c;
   const int dim = p->dim;
+  const double sigma = p->kernel == BEM_KELVIN_3D ? -1.0 : 1.0;  // K2 = +D or -T
   for (int b = 0; b < nblocks; ++b) {
     const int64_t i0 = (int64_t)b * bs;
-    const int sz = (int)std::min<int64_t>(bs, nb - i0);
+    const int sz = (int)std::min<int64_t>(bs, nb - i0) * nc;
     std::vector<double> A((size_t)sz * sz);
-    for (int a = 0; a < sz; ++a) {
-      const int64_t i = i0 + a;
-      for (int e = 0; e < sz; ++e) {
-        const int64_t j = i0 + e;
-        const int dx = p->h_cell_user[i * dim] - p->h_cell_user[j * dim];
-        const int dy = p->h_cell_user[i * dim + 1] - p->h_cell_user[j * dim + 1];
+    for (int ia = 0; ia < sz; ++ia) {
+      const int64_t i = i0 + ia / nc;
+      const int ca = ia % nc;
+      for (int jb = 0; jb < sz; ++jb) {
+        const int64_t j = i0 + jb / nc;
+        const int cb = jb % nc;
         const double wj = p->h_w_user[j];
+        const bool neu = p->h_bc[j * nc + cb] != 0;
         double v;
-        if (p->h_bc[j] == 0) {
-          v = kernel2d_point(0, dx, dy, p->h) * wj;
+        if (dim == 2) {
+          const int dx = p->h_cell_user[i * dim] - p->h_cell_user[j * dim];
+          const int dy = p->h_cell_user[i * dim + 1] - p->h_cell_user[j * dim + 1];
+          if (!neu)
+            v = kernel2d_point(0, dx, dy, p->h) * wj;
+          else
+            v = (kernel2d_point(1, dx, dy, p->h) * p->h_normal_user[j * dim] +
+                 kernel2d_point(2, dx, dy, p->h) * p->h_normal_user[j * dim + 1]) *
+                wj;
         } else {
-          v = (kernel2d_point(1, dx, dy, p->h) * p->h_normal_user[j * dim] +
-               kernel2d_point(2, dx, dy, p->h) * p->h_normal_user[j * dim + 1]) *
-              wj;
-          if (i == j) v -= c;
+          const int dl[3] = {p->h_cell_user[i * 3] - p->h_cell_user[j * 3],
+                             p->h_cell_user[i * 3 + 1] - p->h_cell_user[j * 3 + 1],
+                             p->h_cell_user[i * 3 + 2] - p->h_cell_user[j * 3 + 2]};
+          double blk[9];
+          kernel3d_block(p->kernel, dl, &p->h_normal_user[j * 3], p->h, p->nu, p->mu, !neu, blk);
+          v = (nc == 1 ? blk[0] : blk[ca * 3 + cb]) * wj * (neu ? sigma : 1.0);
         }
-        A[(size_t)a * sz + e] = v;
+        if (neu && i == j && ca == cb) v -= c;
+        A[(size_t)ia * sz + jb] = v;
       }
     }
     if (!invert(A, sz)) {
@@ -114,6 +164,7 @@ bem_status build_preconditioner(bem_plan_s* p) {
     double* dst = &all[(size_t)b * m * m];
     for (int a = 0; a < sz; ++a)
       for (int e = 0; e < sz; ++e) dst[(size_t)a * m + e] = A[(size_t)a * sz + e];
+
   }
   cudaFree(p->pc.d_inv);
   p->pc.d_inv = nullptr;

@@ -178,6 +178,89 @@ def random_cells(n: int, nb: int, rng: np.random.Generator, dim: int = 2) -> Bou
     return Boundary(dim, n, cells, w, nrm, (cells + 0.5) / n, np.zeros(nb))
 
 
+# ---------------------------------------------------------------- 3D surfaces --
+
+def ellipsoid_boundary(n: int = 256, axes=(0.4, 0.3, 0.2), centre=(0.5, 0.5, 0.5),
+                       samples_per_cell: int = 6) -> Boundary:
+    """Boundary cells of an ellipsoid on an n^3 grid.  The surface is sampled
+    on a (theta, phi) grid fine enough that neighbouring samples are at most
+    h / samples_per_cell apart; w_j = in-cell area (sum of the samples' area
+    elements), normal = analytic at the in-cell sample closest to the in-cell
+    centroid.  Cells are returned sorted by (theta, phi) of their first sample."""
+    a, b, c = axes
+    h = 1.0 / n
+    amax = max(axes)
+    d = h / samples_per_cell / amax
+    nt = int(math.ceil(math.pi / d))
+    npf = int(math.ceil(2 * math.pi / d))
+    cells_acc = {}
+    th = (np.arange(nt) + 0.5) * (math.pi / nt)
+    dth = math.pi / nt
+    dph = 2 * math.pi / npf
+    keys_all, area_all, pts_all, par_all = [], [], [], []
+    chunk = max(1, 2_000_000 // npf)
+    ph = (np.arange(npf) + 0.5) * dph
+    for i0 in range(0, nt, chunk):
+        t = th[i0:i0 + chunk][:, None]
+        st, ct = np.sin(t), np.cos(t)
+        cp, sp = np.cos(ph)[None, :], np.sin(ph)[None, :]
+        x = centre[0] + a * st * cp
+        y = centre[1] + b * st * sp
+        z = centre[2] + c * ct * np.ones_like(cp)
+        # |p_theta x p_phi|
+        nx, ny, nz = b * c * st * st * cp, a * c * st * st * sp, a * b * st * ct * np.ones_like(cp)
+        dA = np.sqrt(nx * nx + ny * ny + nz * nz) * dth * dph
+        P = np.stack([x, y, z], axis=-1).reshape(-1, 3)
+        g = np.floor(P / h).astype(np.int64)
+        keys_all.append((g[:, 2] * n + g[:, 1]) * n + g[:, 0])
+        area_all.append(dA.reshape(-1))
+        pts_all.append(P)
+        par_all.append(np.stack([np.broadcast_to(t, x.shape), np.broadcast_to(ph[None, :], x.shape)],
+                                axis=-1).reshape(-1, 2))
+    key = np.concatenate(keys_all)
+    dA = np.concatenate(area_all)
+    P = np.concatenate(pts_all)
+    par = np.concatenate(par_all)
+    uniq, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    nb = uniq.size
+    w = np.bincount(inv, weights=dA, minlength=nb)
+    cen = np.stack([np.bincount(inv, weights=P[:, k] * dA, minlength=nb) for k in range(3)], axis=-1) / w[:, None]
+    dist = np.linalg.norm(P - cen[inv], axis=1)
+    order = np.lexsort((dist, inv))
+    pick = order[np.searchsorted(inv[order], np.arange(nb))]
+    pj = P[pick]
+    grad = np.stack([(pj[:, 0] - centre[0]) / a ** 2, (pj[:, 1] - centre[1]) / b ** 2,
+                     (pj[:, 2] - centre[2]) / c ** 2], axis=-1)
+    nrm = grad / np.linalg.norm(grad, axis=1, keepdims=True)
+    cells = np.stack([uniq % n, (uniq // n) % n, uniq // (n * n)], axis=-1).astype(np.int32)
+    arc = np.argsort(first, kind="stable")
+    return Boundary(3, n, cells[arc], w[arc], nrm[arc], pj[arc], par[pick][arc])
+
+
+def cube_boundary(n: int = 128, lo: int = None, hi: int = None) -> Boundary:
+    """Cube whose faces run through the node planes lo and hi (default n/4
+    and 3n/4: side 0.5 for the unit box): every grid cell whose node lies on
+    the surface.  Face cells carry w = h^2; cells on an edge carry the two
+    half-cells h^2/2 + h^2/2 and an averaged normal; corner cells carry
+    3 (h/2)^2 and the averaged normal of the three faces."""
+    lo = n // 4 if lo is None else lo
+    hi = (3 * n) // 4 if hi is None else hi
+    h = 1.0 / n
+    rng = np.arange(lo, hi + 1)
+    gx, gy, gz = np.meshgrid(rng, rng, rng, indexing="ij")
+    g = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=-1)
+    on = (g == lo) | (g == hi)
+    keep = on.any(axis=1)
+    g, on = g[keep], on[keep]
+    nrm = np.where(g == hi, 1.0, 0.0) - np.where(g == lo, 1.0, 0.0)
+    k = on.sum(axis=1)
+    w = np.where(k == 1, h * h, np.where(k == 2, h * h, 0.75 * h * h))
+    nrm = nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+    order = np.lexsort((g[:, 0], g[:, 1], g[:, 2]))
+    g = g[order].astype(np.int32)
+    return Boundary(3, n, g, w[order], nrm[order], (g + 0.5) * h, k[order].astype(np.float64))
+
+
 # ------------------------------------------------------------ analytic fields --
 
 def field_x2y2(p):
