@@ -310,15 +310,22 @@ static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in
 }
 
 template <typename T>
-static bem_status configure3d_t(bem_plan_s* p, int maxnf, int maxlpc) {
+static bem_status configure3d_t(bem_plan_s* p) {
   const int n = (int)p->n, N = (int)p->N;
   const int ZB = pick_zb(n);
   const size_t sm_y = (size_t)(N / 4) * sizeof(cplx<T>) +
                       std::max((size_t)ZB * (N + N / 16), (size_t)N * (ZB + 1)) * sizeof(cplx<T>);
-  const size_t sm_z = (size_t)(N / 4) * sizeof(cplx<T>) + (size_t)maxlpc * ((N + N / 16) + (size_t)maxnf * N) * sizeof(cplx<T>);
+  int dev = 0, optin = 0;
+  BEM_CUDA_TRY(cudaGetDevice(&dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (sm_y > (size_t)optin) {
+    set_error("3D grid too large for the shared-memory line buffers");
+    return BEM_ERR_UNSUPPORTED;
+  }
   BEM_CUDA_TRY(cudaFuncSetAttribute(k3_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_y));
   BEM_CUDA_TRY(cudaFuncSetAttribute(k3_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_y));
-  BEM_CUDA_TRY(cudaFuncSetAttribute(k3_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_z));
+  // every operator's z pass stays within zpass_lpc's budget (<= 200 KB)
+  BEM_CUDA_TRY(cudaFuncSetAttribute(k3_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   return BEM_OK;
 }
 
@@ -339,8 +346,7 @@ bem_status setup_apply_3d(bem_plan_s* p, int maxnf) {
     set_error("3D grids need 16 <= n <= 512, n a power of two");
     return BEM_ERR_UNSUPPORTED;
   }
-  const int lpc = zpass_lpc(p, maxnf);
-  bem_status rc = p->prec == BEM_F64 ? configure3d_t<double>(p, maxnf, lpc) : configure3d_t<float>(p, maxnf, lpc);
+  bem_status rc = p->prec == BEM_F64 ? configure3d_t<double>(p) : configure3d_t<float>(p);
   if (rc != BEM_OK) return rc;
   // 2-level twiddles e^{2 pi i m / N}
   const int64_t N = p->N;
