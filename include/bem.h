@@ -82,6 +82,7 @@ typedef struct {
   double rel_residual_est;   /* GMRES (Givens) estimate at exit */
   double seconds;            /* wall time of the solve (host clock) */
   int applies;               /* all operator applies, right-hand side and final check included */
+  int refine_steps;          /* outer steps of mixed-precision refinement (0 without it) */
 } bem_solve_info;
 
 typedef struct {
@@ -180,6 +181,15 @@ bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, dou
  * a first-kind operator whose condition number grows with n, so unpreconditioned
  * restarted GMRES stalls on mixed problems. */
 bem_status bem_set_preconditioner(bem_plan_t plan, int kind, int block_size);
+
+/* Mixed-precision iterative refinement for BEM_F32 plans: with enable != 0
+ * the plan builds an FP64 plan of the same geometry; bem_solve then forms
+ * the right-hand side and every residual with the FP64 operator and solves
+ * for the corrections with the preconditioned FP32 GMRES, so that tolerances
+ * below the FP32 operator's own accuracy (a relative residual of ~3e-6 for
+ * the 4096^2 star) are reached.  rel_residual then is the FP64 residual.
+ * No effect on BEM_F64 plans. */
+bem_status bem_enable_refinement(bem_plan_t plan, int enable);
 
 /* Query sizes and launch shape of a plan. */
 bem_status bem_get_info(bem_plan_t plan, bem_plan_info* info);

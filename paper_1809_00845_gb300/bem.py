@@ -28,7 +28,7 @@ PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32}
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
-            "bem_get_info", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
+            "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
             "bem_status_string", "bem_last_error"]
 
 
@@ -40,7 +40,8 @@ class BemError(RuntimeError):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("rel_residual_est", ctypes.c_double), ("seconds", ctypes.c_double), ("applies", ctypes.c_int)]
+                ("rel_residual_est", ctypes.c_double), ("seconds", ctypes.c_double), ("applies", ctypes.c_int),
+                ("refine_steps", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +72,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_plan.argtypes = [ctypes.POINTER(P), I, P, D, I64, P, P, P, I, D, D, I, ctypes.c_uint32, P]
     lib.bem_set_bc.argtypes = [P, P, D]
     lib.bem_set_preconditioner.argtypes = [P, I, I]
+    lib.bem_enable_refinement.argtypes = [P, I]
     lib.bem_apply.argtypes = [P, I, P, P, P]
     lib.bem_apply_host.argtypes = [P, I, P, P, P]
     lib.bem_apply_static_scratch.argtypes = [P, I, P, P, P]
@@ -85,7 +87,8 @@ def load_library(path: str = LIB_PATH):
     lib.bem_status_string.restype = ctypes.c_char_p
     lib.bem_last_error.argtypes = []
     lib.bem_last_error.restype = ctypes.c_char_p
-    for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_static_scratch", "bem_apply_host", "bem_solve", "bem_get_info",
+    for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
+                 "bem_apply_static_scratch", "bem_apply_host", "bem_solve", "bem_get_info",
                  "bem_set_kernel_timing", "bem_kernel_time", "bem_destroy"):
         getattr(lib, name).restype = I
     _lib = lib
@@ -176,6 +179,9 @@ class Plan:
     def set_preconditioner(self, kind="block", block_size=64):
         k = {"none": 0, "block": 1}[kind] if isinstance(kind, str) else int(kind)
         _check(load_library().bem_set_preconditioner(self._h, k, int(block_size)))
+
+    def enable_refinement(self, enable=True):
+        _check(load_library().bem_enable_refinement(self._h, 1 if enable else 0))
 
     def apply(self, layer, x, out=None, stream=None):
         """Device apply.  x: CUDA tensor of nb*ncomp plan-precision values."""

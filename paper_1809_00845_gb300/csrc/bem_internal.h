@@ -168,6 +168,8 @@ struct bem_plan_s {
   double* d_V = nullptr;
   double* d_vec = nullptr;  // several nb*ncomp FP64 vectors
   double* d_small = nullptr;
+  size_t small_len = 0;
+  bem_plan_s* companion = nullptr;  // FP64 plan of the same geometry for refinement residuals
   void* d_tin = nullptr;    // plan-precision in/out buffers for the apply
   void* d_tout = nullptr;
 };

@@ -530,6 +530,27 @@ bem_status bem_solve(bem_plan_t p, const uint8_t* bc, const double* data, double
                      static_cast<cudaStream_t>(stream));
 }
 
+bem_status bem_enable_refinement(bem_plan_t p, int enable) {
+  if (!p) {
+    set_error("bem_enable_refinement: null plan");
+    return BEM_ERR_ARG;
+  }
+  if (!enable || p->prec == BEM_F64) {
+    if (p->companion) bem_destroy(p->companion);
+    p->companion = nullptr;
+    return BEM_OK;
+  }
+  if (p->companion) return BEM_OK;
+  const int64_t n[3] = {p->n, p->n, p->n};
+  bem_plan_t c = nullptr;
+  bem_status rc = plan_impl(&c, p->dim, n, p->h, p->nb, p->h_cell_user.data(), p->h_w_user.data(),
+                            p->h_normal_user.data(), (bem_kernel)p->kernel, p->nu, p->mu, BEM_F64, 0, nullptr);
+  if (rc != BEM_OK) return rc;
+  c->pc.kind = 0;
+  p->companion = c;
+  return BEM_OK;
+}
+
 bem_status bem_get_info(bem_plan_t p, bem_plan_info* info) {
   if (!p || !info) {
     set_error("bem_get_info: null pointer argument");
@@ -588,6 +609,7 @@ int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
 
 bem_status bem_destroy(bem_plan_t p) {
   if (!p) return BEM_OK;
+  if (p->companion) bem_destroy(p->companion);
   cudaFree(p->d_perm);
   cudaFree(p->d_rowptr);
   cudaFree(p->d_col);

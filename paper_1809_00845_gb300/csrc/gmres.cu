@@ -156,144 +156,97 @@ struct Gm {
   }
 };
 
-bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
-                       int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
-                       cudaStream_t st) {
-  auto t0 = std::chrono::steady_clock::now();
-  const int64_t M = p->nb * p->ncomp;
-  if (restart < 1 || restart > 512 || max_iter < 0 || !(tol > 0.0)) {
-    set_error("bem_solve: need 1 <= restart <= 512, max_iter >= 0, tol > 0");
-    return BEM_ERR_ARG;
-  }
-  bem_status rc = bem_set_bc(p, bc, c);
-  if (rc != BEM_OK) return rc;
-  const int m = restart;
-  // workspace
-  if (p->gm_m < m) {
-    cudaFree(p->d_V);
-    p->d_V = nullptr;
-    BEM_CUDA_TRY(cudaMalloc(&p->d_V, (size_t)(m + 1) * M * sizeof(double)));
-    p->gm_m = m;
-  }
-  if ((rc = build_preconditioner(p)) != BEM_OK) return rc;
-  if (!p->d_vec) BEM_CUDA_TRY(cudaMalloc(&p->d_vec, (size_t)7 * M * sizeof(double) + (size_t)M));
-  const int nchunk = (int)((M + kDotChunk - 1) / kDotChunk);
-  if (!p->d_small) BEM_CUDA_TRY(cudaMalloc(&p->d_small, (size_t)(3 * 520 + 520 * 64 + 8) * sizeof(double)));
-  if (nchunk > 64) {
-    set_error("bem_solve: vector too long for the dot-product scratch");
-    return BEM_ERR_UNSUPPORTED;
-  }
-  if (!p->d_tin) {
-    BEM_CUDA_TRY(cudaMalloc(&p->d_tin, (size_t)M * prec_bytes(p)));
-    BEM_CUDA_TRY(cudaMalloc(&p->d_tout, (size_t)M * prec_bytes(p)));
-  }
-  double* V = p->d_V;
-  double* d_b = p->d_vec;
-  double* d_x = d_b + M;
-  double* d_w = d_x + M;
-  double* d_um = d_w + M;
-  double* d_qm = d_um + M;
-  double* d_data = d_qm + M;
-  double* d_z = d_data + M;
-  uint8_t* d_bc = reinterpret_cast<uint8_t*>(d_z + M);
-  double* d_h = p->d_small;              // 520: first CGS sweep (accumulated), then norm^2 at [m+1]
-  double* d_h2 = d_h + 520;              // 520: second sweep
-  double* d_y = d_h2 + 520;              // 520
-  double* d_partial = d_y + 520;         // 520 * 64
-  Gm g{p, st, M, d_partial, nchunk, p->prec == BEM_F64};
-  int applies = 0;
+struct GmresWs {
+  double* V;
+  double* w;
+  double* z;
+  double* h;
+  double* h2;
+  double* y;
+  int m;
+};
 
-  BEM_CUDA_TRY(cudaMemcpyAsync(d_data, data, M * sizeof(double), cudaMemcpyHostToDevice, st));
-  BEM_CUDA_TRY(cudaMemcpyAsync(d_bc, bc, M, cudaMemcpyHostToDevice, st));
-  k_split_known<<<blocks_for(M, 256), 256, 0, st>>>(d_data, d_bc, d_um, d_qm, M);
-  // b = c um - sigma K2 um - K1 qm,  sigma K2 = +D (Laplace) or -T (Kelvin)
-  const double sigma = p->kernel == BEM_KELVIN_3D ? -1.0 : 1.0;
-  if ((rc = g.apply(BEM_DOUBLE, d_um, d_b)) != BEM_OK) return rc;
-  if ((rc = g.apply(BEM_SINGLE, d_qm, d_w)) != BEM_OK) return rc;
-  applies += 2;
-  k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, -sigma, d_b, M);  // b = -sigma K2 um - K1 qm
-  k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(c, d_um, 1.0, d_b, M);       // b += c um
-  if (x0)
-    BEM_CUDA_TRY(cudaMemcpyAsync(d_x, x0, M * sizeof(double), cudaMemcpyHostToDevice, st));
-  else
-    BEM_CUDA_TRY(cudaMemsetAsync(d_x, 0, M * sizeof(double), st));
-
-  // ||b||
-  double bnorm2 = 0.0;
-  g.dots(d_b, M, 1, d_b, d_h, false);
-  BEM_CUDA_TRY(cudaMemcpyAsync(&bnorm2, d_h, sizeof(double), cudaMemcpyDeviceToHost, st));
-  BEM_CUDA_TRY(cudaStreamSynchronize(st));
-  const double bnorm = std::sqrt(bnorm2);
-  if (!std::isfinite(bnorm)) {
-    set_error("bem_solve: right-hand side is not finite");
-    return BEM_ERR_NONFINITE;
-  }
-
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (m + 1) + 1), y(m);
-  int iters = 0, restarts = 0;
+struct GmresOut {
+  int iters = 0, restarts = 0, applies = 0;
   double rel = 1.0, rel_est = 1.0;
-  bem_status result = BEM_ERR_NOT_CONVERGED;
+  bem_status status = BEM_ERR_NOT_CONVERGED;
+};
+
+// Restarted right-preconditioned GMRES on A x = b with the plan-precision
+// apply of g.p; stops when ||b - A x|| <= tol * bnorm (recomputed at every
+// restart with the same apply), after max_iter iterations, or when the
+// recomputed residual stagnates for three restarts.  x is updated in place.
+static bem_status gmres_core(Gm& g, const GmresWs& ws, const double* d_b, double bnorm, double* d_x, double tol,
+                             int max_iter, GmresOut* out) {
+  const int64_t M = g.M;
+  const int m = ws.m;
+  cudaStream_t st = g.st;
+  bem_status rc;
+  double* V = ws.V;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (m + 1) + 1), y(m);
   double best_rel = INFINITY;
   int stagnant = 0;
-
+  out->status = BEM_ERR_NOT_CONVERGED;
   while (true) {
     // r = b - A x  -> V[0]
-    if ((rc = g.apply(BEM_SYSTEM, d_x, d_w)) != BEM_OK) return rc;
-    ++applies;
+    if ((rc = g.apply(BEM_SYSTEM, d_x, ws.w)) != BEM_OK) return rc;
+    ++out->applies;
     BEM_CUDA_TRY(cudaMemcpyAsync(V, d_b, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, 1.0, V, M);
+    k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, ws.w, 1.0, V, M);
     double beta2 = 0.0;
-    g.dots(V, M, 1, V, d_h, false);
-    BEM_CUDA_TRY(cudaMemcpyAsync(&beta2, d_h, sizeof(double), cudaMemcpyDeviceToHost, st));
+    g.dots(V, M, 1, V, ws.h, false);
+    BEM_CUDA_TRY(cudaMemcpyAsync(&beta2, ws.h, sizeof(double), cudaMemcpyDeviceToHost, st));
     BEM_CUDA_TRY(cudaStreamSynchronize(st));
     const double beta = std::sqrt(beta2);
     if (!std::isfinite(beta)) {
       set_error("bem_solve: residual is not finite");
-      result = BEM_ERR_NONFINITE;
-      break;
+      out->status = BEM_ERR_NONFINITE;
+      return BEM_OK;
     }
-    rel = bnorm > 0 ? beta / bnorm : 0.0;
-    if (rel <= tol) {
-      result = BEM_OK;
-      break;
+    out->rel = bnorm > 0 ? beta / bnorm : 0.0;
+    if (out->rel <= tol) {
+      out->status = BEM_OK;
+      return BEM_OK;
     }
-    if (rel < best_rel * 0.999) {
-      best_rel = rel;
+    if (out->rel < best_rel * 0.999) {
+      best_rel = out->rel;
       stagnant = 0;
     } else if (++stagnant >= 3) {
-      result = BEM_ERR_NOT_CONVERGED;
       set_error("bem_solve: residual stagnates (precision floor of the apply reached)");
-      break;
+      return BEM_OK;
     }
-    if (iters >= max_iter) break;
-    k_normalize<<<blocks_for(M, 256), 256, 0, st>>>(V, d_h, V, M);
+    if (out->iters >= max_iter) {
+      set_error("bem_solve: max_iter reached");
+      return BEM_OK;
+    }
+    k_normalize<<<blocks_for(M, 256), 256, 0, st>>>(V, ws.h, V, M);
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int j = 0;
-    bool breakdown = false;
-    for (; j < m && iters < max_iter; ++j) {
+    for (; j < m && out->iters < max_iter; ++j) {
       double* vj = V + (int64_t)j * M;
       double* vn = V + (int64_t)(j + 1) * M;
-      g.precond(vj, d_z);
-      if ((rc = g.apply(BEM_SYSTEM, d_z, d_w)) != BEM_OK) return rc;
-      ++applies;
-      ++iters;
-      // CGS2
-      g.dots(V, M, j + 1, d_w, d_h, false);
-      k_sub_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j + 1, d_h, d_w, M);
-      g.dots(V, M, j + 1, d_w, d_h2, false);
-      k_sub_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j + 1, d_h2, d_w, M);
-      g.dots(d_w, M, 1, d_w, d_h + (j + 1), false);
-      k_normalize<<<blocks_for(M, 256), 256, 0, st>>>(d_w, d_h + (j + 1), vn, M);
-      BEM_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), d_h, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      BEM_CUDA_TRY(cudaMemcpyAsync(hbuf.data() + (m + 1), d_h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      g.precond(vj, ws.z);
+      if ((rc = g.apply(BEM_SYSTEM, ws.z, ws.w)) != BEM_OK) return rc;
+      ++out->applies;
+      ++out->iters;
+      // classical Gram-Schmidt with one re-orthogonalisation (FP64)
+      g.dots(V, M, j + 1, ws.w, ws.h, false);
+      k_sub_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j + 1, ws.h, ws.w, M);
+      g.dots(V, M, j + 1, ws.w, ws.h2, false);
+      k_sub_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j + 1, ws.h2, ws.w, M);
+      g.dots(ws.w, M, 1, ws.w, ws.h + (j + 1), false);
+      k_normalize<<<blocks_for(M, 256), 256, 0, st>>>(ws.w, ws.h + (j + 1), vn, M);
+      BEM_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), ws.h, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      BEM_CUDA_TRY(cudaMemcpyAsync(hbuf.data() + (m + 1), ws.h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       BEM_CUDA_TRY(cudaStreamSynchronize(st));
       double* col = &H[(size_t)j * (m + 1)];
       for (int i = 0; i <= j; ++i) col[i] = hbuf[i] + hbuf[m + 1 + i];
       col[j + 1] = std::sqrt(hbuf[j + 1]);
       if (!std::isfinite(col[j + 1])) {
         set_error("bem_solve: Arnoldi vector is not finite");
-        return BEM_ERR_NONFINITE;
+        out->status = BEM_ERR_NONFINITE;
+        return BEM_OK;
       }
       for (int i = 0; i < j; ++i) {
         const double a = col[i], b = col[i + 1];
@@ -308,34 +261,169 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
       col[j + 1] = 0.0;
       gv[j + 1] = -sn[j] * gv[j];
       gv[j] = cs[j] * gv[j];
-      rel_est = bnorm > 0 ? std::fabs(gv[j + 1]) / bnorm : 0.0;
-      if (rel_est <= tol) {
-        ++j;
-        break;
-      }
-      if (std::sqrt(hbuf[j + 1]) <= 1e-14 * bnorm) {
-        breakdown = true;
+      out->rel_est = bnorm > 0 ? std::fabs(gv[j + 1]) / bnorm : 0.0;
+      if (out->rel_est <= tol || std::sqrt(hbuf[j + 1]) <= 1e-14 * bnorm) {
         ++j;
         break;
       }
     }
-    // y = H^-1 g (upper triangular j x j), x += V y
+    // y = H^-1 g (upper triangular j x j), x += M^-1 (V y)
     for (int i = j - 1; i >= 0; --i) {
       double s = gv[i];
       for (int k = i + 1; k < j; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
       y[i] = s / H[(size_t)i * (m + 1) + i];
     }
     if (j > 0) {
-      // x += M^-1 (V y)
-      BEM_CUDA_TRY(cudaMemcpyAsync(d_y, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, st));
-      BEM_CUDA_TRY(cudaMemsetAsync(d_w, 0, M * sizeof(double), st));
-      k_add_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j, d_y, d_w, M);
-      g.precond(d_w, d_z);
-      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(1.0, d_z, 1.0, d_x, M);
+      BEM_CUDA_TRY(cudaMemcpyAsync(ws.y, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, st));
+      BEM_CUDA_TRY(cudaMemsetAsync(ws.w, 0, M * sizeof(double), st));
+      k_add_basis<<<blocks_for(M, 256), 256, 0, st>>>(V, M, j, ws.y, ws.w, M);
+      g.precond(ws.w, ws.z);
+      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(1.0, ws.z, 1.0, d_x, M);
     }
-    ++restarts;
-    (void)breakdown;
+    ++out->restarts;
   }
+}
+
+bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
+                       int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
+                       cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t M = p->nb * p->ncomp;
+  if (restart < 1 || restart > 512 || max_iter < 0 || !(tol > 0.0)) {
+    set_error("bem_solve: need 1 <= restart <= 512, max_iter >= 0, tol > 0");
+    return BEM_ERR_ARG;
+  }
+  bem_status rc = bem_set_bc(p, bc, c);
+  if (rc != BEM_OK) return rc;
+  bem_plan_s* R = p->companion ? p->companion : p;  // residual (outer) operator
+  if (R != p && (rc = bem_set_bc(R, bc, c)) != BEM_OK) return rc;
+  const int m = restart;
+  // workspace
+  if (p->gm_m < m) {
+    cudaFree(p->d_V);
+    p->d_V = nullptr;
+    BEM_CUDA_TRY(cudaMalloc(&p->d_V, (size_t)(m + 1) * M * sizeof(double)));
+    p->gm_m = m;
+  }
+  if ((rc = build_preconditioner(p)) != BEM_OK) return rc;
+  if (!p->d_vec) BEM_CUDA_TRY(cudaMalloc(&p->d_vec, (size_t)9 * M * sizeof(double) + (size_t)M));
+  const int nchunk = (int)((M + kDotChunk - 1) / kDotChunk);
+  const size_t small = (size_t)3 * 520 + (size_t)520 * nchunk + 8;
+  if (p->small_len < small) {
+    cudaFree(p->d_small);
+    p->d_small = nullptr;
+    BEM_CUDA_TRY(cudaMalloc(&p->d_small, small * sizeof(double)));
+    p->small_len = small;
+  }
+  for (bem_plan_s* q : {p, R})
+    if (!q->d_tin) {
+      BEM_CUDA_TRY(cudaMalloc(&q->d_tin, (size_t)M * prec_bytes(q)));
+      BEM_CUDA_TRY(cudaMalloc(&q->d_tout, (size_t)M * prec_bytes(q)));
+    }
+  double* d_b = p->d_vec;
+  double* d_x = d_b + M;
+  double* d_w = d_x + M;
+  double* d_um = d_w + M;
+  double* d_qm = d_um + M;
+  double* d_data = d_qm + M;
+  double* d_z = d_data + M;
+  double* d_r = d_z + M;
+  double* d_d = d_r + M;
+  uint8_t* d_bc = reinterpret_cast<uint8_t*>(d_d + M);
+  double* d_h = p->d_small;   // 520: first CGS sweep, then norm^2 at [j+1]
+  double* d_h2 = d_h + 520;   // 520: second sweep
+  double* d_y = d_h2 + 520;   // 520
+  double* d_partial = d_y + 520;
+  Gm g{p, st, M, d_partial, nchunk, p->prec == BEM_F64};
+  Gm gr{R, st, M, d_partial, nchunk, R->prec == BEM_F64};
+  GmresWs ws{p->d_V, d_w, d_z, d_h, d_h2, d_y, m};
+  int applies = 0;
+
+  BEM_CUDA_TRY(cudaMemcpyAsync(d_data, data, M * sizeof(double), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(d_bc, bc, M, cudaMemcpyHostToDevice, st));
+  k_split_known<<<blocks_for(M, 256), 256, 0, st>>>(d_data, d_bc, d_um, d_qm, M);
+  // b = c um - sigma K2 um - K1 qm,  sigma K2 = +D (Laplace) or -T (Kelvin)
+  const double sigma = p->kernel == BEM_KELVIN_3D ? -1.0 : 1.0;
+  if ((rc = gr.apply(BEM_DOUBLE, d_um, d_b)) != BEM_OK) return rc;
+  if ((rc = gr.apply(BEM_SINGLE, d_qm, d_w)) != BEM_OK) return rc;
+  applies += 2;
+  k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, -sigma, d_b, M);  // b = -sigma K2 um - K1 qm
+  k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(c, d_um, 1.0, d_b, M);       // b += c um
+  if (x0)
+    BEM_CUDA_TRY(cudaMemcpyAsync(d_x, x0, M * sizeof(double), cudaMemcpyHostToDevice, st));
+  else
+    BEM_CUDA_TRY(cudaMemsetAsync(d_x, 0, M * sizeof(double), st));
+
+  double bnorm2 = 0.0;
+  g.dots(d_b, M, 1, d_b, d_h, false);
+  BEM_CUDA_TRY(cudaMemcpyAsync(&bnorm2, d_h, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(bnorm2);
+  if (!std::isfinite(bnorm)) {
+    set_error("bem_solve: right-hand side is not finite");
+    return BEM_ERR_NONFINITE;
+  }
+
+  GmresOut tot;
+  int refine_steps = 0;
+  bem_status result = BEM_ERR_NOT_CONVERGED;
+  double rel = 1.0, rel_est = 1.0;
+  if (R == p) {
+    if ((rc = gmres_core(g, ws, d_b, bnorm, d_x, tol, max_iter, &tot)) != BEM_OK) return rc;
+    result = tot.status;
+    rel = tot.rel;
+    rel_est = tot.rel_est;
+  } else {
+    // Mixed-precision iterative refinement: residuals with the FP64 operator,
+    // corrections from the preconditioned low-precision GMRES.
+    double best = INFINITY;
+    int stagnant = 0;
+    for (;;) {
+      if ((rc = gr.apply(BEM_SYSTEM, d_x, d_w)) != BEM_OK) return rc;
+      ++applies;
+      BEM_CUDA_TRY(cudaMemcpyAsync(d_r, d_b, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, 1.0, d_r, M);
+      double r2 = 0.0;
+      g.dots(d_r, M, 1, d_r, d_h, false);
+      BEM_CUDA_TRY(cudaMemcpyAsync(&r2, d_h, sizeof(double), cudaMemcpyDeviceToHost, st));
+      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+      const double rn = std::sqrt(r2);
+      if (!std::isfinite(rn)) {
+        set_error("bem_solve: residual is not finite");
+        result = BEM_ERR_NONFINITE;
+        break;
+      }
+      rel = bnorm > 0 ? rn / bnorm : 0.0;
+      if (rel <= tol) {
+        result = BEM_OK;
+        break;
+      }
+      if (rel < best * 0.5) {
+        best = rel;
+        stagnant = 0;
+      } else if (++stagnant >= 2) {
+        set_error("bem_solve: refinement stagnates");
+        break;
+      }
+      if (tot.iters >= max_iter) {
+        set_error("bem_solve: max_iter reached");
+        break;
+      }
+      // inner solve A d = r to a modest relative accuracy
+      BEM_CUDA_TRY(cudaMemsetAsync(d_d, 0, M * sizeof(double), st));
+      GmresOut in;
+      const double eta = std::max(1e-4, 0.1 * tol / std::max(rel, 1e-300));
+      if ((rc = gmres_core(g, ws, d_r, rn, d_d, std::min(eta, 1e-2), max_iter - tot.iters, &in)) != BEM_OK)
+        return rc;
+      tot.iters += in.iters;
+      tot.restarts += in.restarts;
+      tot.applies += in.applies;
+      rel_est = in.rel_est * rn / std::max(bnorm, 1e-300);
+      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(1.0, d_d, 1.0, d_x, M);
+      ++refine_steps;
+    }
+  }
+  applies += tot.applies;
 
   // outputs
   std::vector<double> x(M);
@@ -347,14 +435,14 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     if (q_out) q_out[i] = neu ? data[i] : x[i];
   }
   if (info) {
-    info->iters = iters;
-    info->restarts = restarts;
+    info->iters = tot.iters;
+    info->restarts = tot.restarts;
     info->rel_residual = rel;
     info->rel_residual_est = rel_est;
     info->applies = applies;
+    info->refine_steps = refine_steps;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
-  if (result == BEM_ERR_NOT_CONVERGED && iters >= max_iter) set_error("bem_solve: max_iter reached");
   return result;
 }
 

@@ -87,3 +87,50 @@ def test_initial_guess_and_iteration_cap(torch_cuda, oracle_mod):
     _, q3, info3 = plan.solve(bc, u, tol=1e-14, restart=5, max_iter=3)
     assert info3["status"] == 4 and info3["iters"] == 3
     assert np.all(np.isfinite(q3))
+
+
+def test_fp32_refinement_reaches_fp64_tolerance(torch_cuda, oracle_mod):
+    """FP32 GMRES stalls near the FP32 operator's accuracy; with mixed-precision
+    refinement (FP64 residuals) the FP32 plan reaches 1e-8."""
+    b = I.star_boundary(512)
+    u, q = I.boundary_data(b, I.field_expcos)
+    bc = I.mixed_bc_theta(b)
+    data = np.where(bc == 0, u, q)
+    plan = _plan(b, "f32")
+    _, _, plain = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=1500)
+    assert plain["status"] == 4  # not reachable in FP32 alone
+    plan.enable_refinement(True)
+    u_out, q_out, info = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=1500)
+    assert info["status"] == 0 and info["refine_steps"] >= 1, info
+    x = np.where(bc == 0, q_out, u_out)
+    rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, u * (bc == 0), q * (bc == 1))
+    r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 2e-8
+
+
+def test_laplace3d_dirichlet_solve_matches_lu(torch_cuda, oracle_mod):
+    b = I.ellipsoid_boundary(32)
+    u, q = I.boundary_data(b, I.field_xy_z)
+    bc = np.zeros(b.nb, np.uint8)
+    from paper_1809_00845_gb300.bem import Plan
+    plan = Plan.from_boundary(b, "laplace3d", "f64")
+    _, q_out, info = plan.solve(bc, u, tol=1e-11, restart=100, max_iter=2000)
+    assert info["status"] == 0, info
+    A, rhs = oracle_mod.system("laplace3d", b.cell, b.h, b.w, b.normal, bc, u, np.zeros(b.nb))
+    x = oracle_mod.solve_lu(A, rhs)
+    assert np.linalg.norm(q_out - x) / np.linalg.norm(x) <= 1e-8
+
+
+def test_kelvin_mixed_solve_matches_lu(torch_cuda, oracle_mod):
+    b = I.cube_boundary(16)
+    rng = np.random.default_rng(4)
+    bc = (rng.uniform(size=(b.nb, 3)) < 0.3).astype(np.uint8)
+    data = rng.standard_normal((b.nb, 3))
+    from paper_1809_00845_gb300.bem import Plan
+    plan = Plan.from_boundary(b, "kelvin3d", "f64")
+    u_out, t_out, info = plan.solve(bc, data, tol=1e-11, restart=120, max_iter=3000)
+    assert info["status"] == 0, info
+    A, rhs = oracle_mod.system("kelvin3d", b.cell, b.h, b.w, b.normal, bc, data * (bc == 0), data * (bc == 1))
+    x = oracle_mod.solve_lu(A, rhs)
+    got = np.where(bc.reshape(-1) == 0, t_out, u_out)
+    assert np.linalg.norm(got - x) / np.linalg.norm(x) <= 1e-8
