@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
     return ap.parse_args()
 
 
@@ -125,6 +126,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one k_col2d_v2 launch on the n=4096 star, FP32
+# system operator, from ncu (profiles/col2d_v2_star4096_launches.md), keyed by
+# the hash of the kernel sources it was measured on; reported only while the
+# sources are unchanged.
+MEASURED_TRAFFIC = {"n4096_f32_system": ("f3fc397b626480bc", 204.98e6)}
+
+
+def kernel_source_hash():
+    import hashlib
+    hs = hashlib.sha256()
+    for f in ("apply2d.cu", "fft4step.cuh", "fft_reg.cuh"):
+        with open(os.path.join(ROOT, "paper_1809_00845_gb300", "csrc", f), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
 def workload(n):
     from paper_1809_00845_gb300 import inputs as I
     b = I.star_boundary(n)
@@ -179,6 +196,57 @@ def cpu_oracle_rate(b, bc, seconds):
     return {"value": (done / b.nb) / el, "unit": "applies/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{done} of {b.nb} target rows of the FP64 direct-sum system apply in {el:.1f} s "
                       f"(rows of one apply evaluated in blocks; applies = rows / nb)"}
+
+
+def _time_applies(plan, layer, x, reps):
+    import torch
+    y = torch.empty_like(x)
+    for _ in range(3):
+        plan.apply(layer, x, y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.apply(layer, x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary_configs(dev):
+    """Apply times (and the circle solve) of the other configurations, a few
+    repetitions each: circle n=128 FP64, ellipsoid n=256 FP32, Kelvin cube
+    n=128 FP32."""
+    import torch
+    from paper_1809_00845_gb300 import inputs as I
+    from paper_1809_00845_gb300.bem import Plan
+    out = {}
+    b = I.circle_boundary(128, 0.35)
+    p = Plan.from_boundary(b, "laplace2d", "f64")
+    x = torch.randn(b.nb, dtype=torch.float64, device=dev)
+    u, _ = I.boundary_data(b, I.field_x2y2)
+    p.solve(np.zeros(b.nb, np.uint8), u, tol=1e-10, restart=100, max_iter=1000)
+    _, _, info = p.solve(np.zeros(b.nb, np.uint8), u, tol=1e-10, restart=100, max_iter=1000)
+    out["circle_n128_f64"] = {"nb": b.nb, "single_apply_ms": _time_applies(p, "single", x, 50),
+                              "solve_1e-10_s": info["seconds"], "solve_iters": info["iters"],
+                              "solve_status": info["status"], "plan_s": p.info()["plan_seconds"]}
+    p.close()
+    b = I.ellipsoid_boundary(256)
+    p = Plan.from_boundary(b, "laplace3d", "f32")
+    x = torch.randn(b.nb, dtype=torch.float32, device=dev)
+    out["ellipsoid_n256_f32"] = {"nb": b.nb, "single_apply_ms": _time_applies(p, "single", x, 10),
+                                 "double_apply_ms": _time_applies(p, "double", x, 5),
+                                 "plan_s": p.info()["plan_seconds"]}
+    p.close()
+    b = I.cube_boundary(128)
+    p = Plan.from_boundary(b, "kelvin3d", "f32")
+    x = torch.randn(b.nb * 3, dtype=torch.float32, device=dev)
+    out["kelvin_cube_n128_f32"] = {"nb": b.nb, "U_apply_ms": _time_applies(p, "single", x, 10),
+                                   "T_apply_ms": _time_applies(p, "double", x, 3),
+                                   "plan_s": p.info()["plan_seconds"]}
+    p.close()
+    return out
 
 
 def run_reference(args):
@@ -303,14 +371,26 @@ def run_ours(args):
     e2e_val = world * e2e_steps / e2e_s
     nbytes = b.nb * (4 if args.precision == "f32" else 8)
 
-    # time-to-solve at 1e-6 (FP32 plan) and the FP64 solve for context
+    # time-to-solve at relative residual 1e-6: FP32 preconditioned GMRES with
+    # mixed-precision refinement (FP64 residuals), and the plain FP32 GMRES
+    # (same preconditioner, FP32 residuals) for comparison
     solve = None
     if not args.no_solve:
-        plan.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)  # warm
-        torch.cuda.synchronize()
-        _, _, info = plan.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
-        solve = {"tol": 1e-6, "seconds": info["seconds"], "iters": info["iters"], "status": info["status"],
-                 "rel_residual": info["rel_residual"], "applies": info["applies"], "precision": args.precision}
+        def run_solve(refine):
+            plan.enable_refinement(refine)
+            plan.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)  # warm (builds preconditioner)
+            torch.cuda.synchronize()
+            _, _, info = plan.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+            return {"seconds": info["seconds"], "iters": info["iters"], "status": info["status"],
+                    "converged": info["status"] == 0, "rel_residual": info["rel_residual"],
+                    "applies": info["applies"], "refine_steps": info["refine_steps"]}
+        plain = run_solve(False)
+        refined = run_solve(True) if args.precision == "f32" else None
+        solve = {"tol": 1e-6, "precision": args.precision, "preconditioner": "block Jacobi, 64 cells",
+                 "fp32_refined": refined, "plain_fp32": plain,
+                 "note": "plain_fp32 residuals use the FP32 operator and stall near its accuracy; "
+                         "fp32_refined residuals use the FP64 operator"}
+        plan.enable_refinement(False)
 
     if rank != 0:
         if world > 1:
@@ -338,9 +418,13 @@ def run_ours(args):
     if hbm_peak is None:
         hbm_peak = FALLBACK_HBM_GBS
     balg = b_alg_bytes(args.n, 3, 1, 3)
+    traffic = None
+    key, val = MEASURED_TRAFFIC.get(f"n{args.n}_{args.precision}_system", (None, None))
+    if key is not None and key == kernel_source_hash():
+        traffic = val
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": (achieved_tflops / peak_tflops) if peak_tflops else None, "traffic": None,
-                "kernel": "k_col2d<float,16,3,true>", "avg_launch_us": avg_col_s * 1e6,
+                "frac": (achieved_tflops / peak_tflops) if peak_tflops else None, "traffic": traffic,
+                "kernel": "k_col2d_v2<float,3,true>", "avg_launch_us": avg_col_s * 1e6,
                 "launches_timed": col_launches, "flops_per_launch": flops,
                 "peak_basis": f"FP32 FMA: {SM_COUNT_NOMINAL} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                               f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
@@ -350,6 +434,9 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_rate(b, bc, args.cpu_seconds)
+    extra = None
+    if not args.no_extra and world == 1:
+        extra = secondary_configs(dev)
     line = {"metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -361,7 +448,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "gpu_launches": args.steps * plan.launches_per_apply("system"),
             "roofline": roofline, "clocks": clk, "time_to_solve": solve, "cpu_baseline": cpu,
-            "plan_seconds": pinfo["plan_seconds"]}
+            "plan_seconds": pinfo["plan_seconds"], "other_configs": extra}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -431,17 +431,28 @@ __global__ void k_prep_v2(int nb, const int32_t* __restrict__ perm, const T* __r
   val[j] = {coefA[j] * x, coefB[j] * x};
 }
 
-// out[perm[j]] = sum_b partial[b*nb + j] (+ diag * in), FP64 sum in fixed order
+// out[perm[j]] = sum_b partial[b*nb + j] (+ diag * in), FP64 sum in a fixed
+// order: 32 cells per block, 8 warps each summing every 8th partial, then the
+// 8 warp sums in order.
 template <typename T>
-__global__ void k_reduce_v2(const T* __restrict__ partial, int grid, int nb, const int32_t* __restrict__ perm,
-                            const T* __restrict__ diag, const T* __restrict__ in, T* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nb) return;
+__global__ void __launch_bounds__(256) k_reduce_v2(const T* __restrict__ partial, int grid, int nb,
+                                                   const int32_t* __restrict__ perm, const T* __restrict__ diag,
+                                                   const T* __restrict__ in, T* __restrict__ out) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int b = 0; b < grid; ++b) s += (double)partial[(size_t)b * nb + j];
-  const int u = perm[j];
-  if (diag) s += (double)diag[u] * (double)in[u];
-  out[u] = (T)s;
+  if (j < nb)
+    for (int b = wp; b < grid; b += 8) s += (double)partial[(size_t)b * nb + j];
+  red[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && j < nb) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    const int u = perm[j];
+    if (diag) t += (double)diag[u] * (double)in[u];
+    out[u] = (T)t;
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -859,7 +870,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   else if (op.nf == 2) k_col2d_v2<T, 2, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
   else k_col2d_v2<T, 3, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k_reduce_v2<T><<<(nb + tb - 1) / tb, tb, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, nb, p->d_perm,
+  k_reduce_v2<T><<<(nb + 31) / 32, 256, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, nb, p->d_perm,
                                                     static_cast<const T*>(op.diag), static_cast<const T*>(in),
                                                     static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
