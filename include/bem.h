@@ -204,6 +204,35 @@ bem_status bem_kernel_time(bem_plan_t plan, double* total_ms, int64_t* launches)
 /* Number of kernel launches one apply of the given layer issues. */
 int bem_launches_per_apply(bem_plan_t plan, bem_layer layer);
 
+/* ---- learned initial guess (serving/training pattern on top of the operator;
+ * the paper has no learned component) ------------------------------------
+ * A 1D convolutional network over the arclength-ordered cells of closed
+ * curves: `layers` circular convolutions of odd width `ksize` with per-layer
+ * dilation, cin -> hidden -> ... -> hidden -> 1 channels, ReLU between layers.
+ * Weights and activations are stored in BF16 (round to nearest even), sums are
+ * FP32; the FP32 master weights are trained with Adam (beta 0.9/0.999,
+ * eps 1e-8) on the mean squared error.  A batch is nseq sequences stored back
+ * to back: feats device [T x cin] FP32 (position-major), offsets device
+ * [nseq + 1] int32 (offsets[0] = 0, offsets[nseq] = T), the circular padding
+ * wraps inside each sequence.  Parameter layout (host vectors): per layer the
+ * weights [cout][cin][ksize] followed by the biases [cout]. */
+typedef struct bem_net_s* bem_net_t;
+bem_status bem_net_create(bem_net_t* out, int cin, int hidden, int layers, int ksize, const int* dilations,
+                          uint64_t seed);
+bem_status bem_net_destroy(bem_net_t net);
+int64_t bem_net_num_params(bem_net_t net);
+bem_status bem_net_get_params(bem_net_t net, float* host_params);
+bem_status bem_net_set_params(bem_net_t net, const float* host_params);
+/* out: device [T] FP32 predictions */
+bem_status bem_net_forward(bem_net_t net, const float* feats, const int32_t* offsets, int nseq, int64_t T, float* out,
+                           void* stream);
+/* loss (host) and the gradient of the loss wrt the parameters (host, may be NULL) for target device [T] */
+bem_status bem_net_gradient(bem_net_t net, const float* feats, const int32_t* offsets, int nseq, int64_t T,
+                            const float* target, float* grad_host, double* loss, void* stream);
+/* one Adam step with learning rate lr; loss (host) of the batch before the step */
+bem_status bem_net_train_step(bem_net_t net, const float* feats, const int32_t* offsets, int nseq, int64_t T,
+                              const float* target, float lr, double* loss, void* stream);
+
 bem_status bem_destroy(bem_plan_t plan);
 const char* bem_status_string(bem_status s);
 const char* bem_last_error(void);

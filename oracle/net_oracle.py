@@ -1,0 +1,98 @@
+"""CPU FP64 oracle of the learned-guess network (test infrastructure).
+
+Plain numpy forward and backward of the circular 1D convolution network that
+``bem_net_*`` implements, with the same rounding points: every layer input and
+every weight rounded to BF16 (round to nearest even) before use, everything
+else in FP64.  With ``bf16=False`` no rounding happens (pure FP64), which the
+finite-difference check of the gradient uses.  Only the tests call it.
+
+Layer l: y[t, o] = b[o] + sum_c sum_k W[o, c, k] x[(t + (k - K//2) d_l) mod L, c]
+for each sequence of length L; ReLU between layers; loss = mean (y - target)^2.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unpack(params, cin, hidden, layers, ksize):
+    out, off = [], 0
+    for l in range(layers):
+        ci = cin if l == 0 else hidden
+        co = 1 if l == layers - 1 else hidden
+        W = np.asarray(params[off:off + co * ci * ksize], dtype=np.float64).reshape(co, ci, ksize)
+        off += co * ci * ksize
+        b = np.asarray(params[off:off + co], dtype=np.float64)
+        off += co
+        out.append((W, b))
+    return out
+
+
+def _conv(x, W, b, d, offsets):
+    co, ci, K = W.shape
+    y = np.empty((x.shape[0], co))
+    for s in range(len(offsets) - 1):
+        s0, s1 = offsets[s], offsets[s + 1]
+        L = s1 - s0
+        xs = x[s0:s1]
+        acc = np.tile(b, (L, 1))
+        for k in range(K):
+            shift = (k - K // 2) * d
+            idx = (np.arange(L) + shift) % L
+            acc += xs[idx] @ W[:, :, k].T
+        y[s0:s1] = acc
+    return y
+
+
+def forward(params, feats, offsets, cin, hidden, layers, ksize, dil, bf16=True):
+    rnd = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    layers_p = unpack(params, cin, hidden, layers, ksize)
+    x = rnd(feats)
+    cache = []
+    for l, (W, b) in enumerate(layers_p):
+        Wr = rnd(W)
+        y = _conv(x, Wr, b, dil[l], offsets)
+        cache.append((x, Wr, y))
+        if l < layers - 1:
+            x = rnd(np.maximum(y, 0.0))
+    return y[:, 0], cache
+
+
+def loss_and_grad(params, feats, offsets, target, cin, hidden, layers, ksize, dil, bf16=True):
+    y, cache = forward(params, feats, offsets, cin, hidden, layers, ksize, dil, bf16)
+    T = y.shape[0]
+    e = y - target
+    loss = float(np.mean(e * e))
+    g = (2.0 * e / T)[:, None]
+    grads = []
+    for l in range(layers - 1, -1, -1):
+        x, Wr, yl = cache[l]
+        if l < layers - 1:
+            g = g * (yl > 0)
+        co, ci, K = Wr.shape
+        gW = np.zeros_like(Wr)
+        gx = np.zeros_like(x)
+        for s in range(len(offsets) - 1):
+            s0, s1 = offsets[s], offsets[s + 1]
+            L = s1 - s0
+            for k in range(K):
+                shift = (k - K // 2) * dil[l]
+                idx = (np.arange(L) + shift) % L
+                gW[:, :, k] += g[s0:s1].T @ x[s0:s1][idx]
+                np.add.at(gx, s0 + idx, g[s0:s1] @ Wr[:, :, k])
+        gb = g.sum(axis=0)
+        grads.append((gW, gb))
+        g = gx
+    flat = []
+    for gW, gb in reversed(grads):
+        flat.append(gW.ravel())
+        flat.append(gb.ravel())
+    return loss, np.concatenate(flat)

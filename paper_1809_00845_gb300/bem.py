@@ -29,7 +29,8 @@ LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
-            "bem_status_string", "bem_last_error"]
+            "bem_status_string", "bem_last_error", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
+            "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step"]
 
 
 class BemError(RuntimeError):
@@ -85,6 +86,18 @@ def load_library(path: str = LIB_PATH):
     lib.bem_destroy.argtypes = [P]
     lib.bem_status_string.argtypes = [I]
     lib.bem_status_string.restype = ctypes.c_char_p
+    lib.bem_net_create.argtypes = [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64]
+    lib.bem_net_destroy.argtypes = [P]
+    lib.bem_net_num_params.argtypes = [P]
+    lib.bem_net_num_params.restype = I64
+    lib.bem_net_get_params.argtypes = [P, P]
+    lib.bem_net_set_params.argtypes = [P, P]
+    lib.bem_net_forward.argtypes = [P, P, P, I, I64, P, P]
+    lib.bem_net_gradient.argtypes = [P, P, P, I, I64, P, P, ctypes.POINTER(D), P]
+    lib.bem_net_train_step.argtypes = [P, P, P, I, I64, P, ctypes.c_float, ctypes.POINTER(D), P]
+    for name in ("bem_net_create", "bem_net_destroy", "bem_net_get_params", "bem_net_set_params", "bem_net_forward",
+                 "bem_net_gradient", "bem_net_train_step"):
+        getattr(lib, name).restype = I
     lib.bem_last_error.argtypes = []
     lib.bem_last_error.restype = ctypes.c_char_p
     for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
@@ -246,6 +259,80 @@ class Plan:
     def launches_per_apply(self, layer="system"):
         lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
         return int(load_library().bem_launches_per_apply(self._h, lay))
+
+
+class Net:
+    """Owning wrapper of a bem_net_t (learned initial guess network)."""
+
+    def __init__(self, cin=7, hidden=64, layers=4, ksize=5, dilations=(1, 2, 4, 8), seed=0):
+        lib = load_library()
+        self.cin, self.hidden, self.layers, self.ksize = int(cin), int(hidden), int(layers), int(ksize)
+        self.dilations = np.ascontiguousarray(dilations, dtype=np.int32)
+        self._h = ctypes.c_void_p()
+        _check(lib.bem_net_create(ctypes.byref(self._h), self.cin, self.hidden, self.layers, self.ksize,
+                                  _ptr(self.dilations), int(seed)))
+        self.nparams = int(lib.bem_net_num_params(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().bem_net_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(load_library().bem_net_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        _check(load_library().bem_net_set_params(self._h, _ptr(p)))
+
+    @staticmethod
+    def _dev(feats, offsets, target=None):
+        import torch
+        f = feats if isinstance(feats, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(feats, np.float32))
+        o = offsets if isinstance(offsets, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(offsets, np.int32))
+        f = f.to(device="cuda", dtype=torch.float32).contiguous()
+        o = o.to(device="cuda", dtype=torch.int32).contiguous()
+        t = None
+        if target is not None:
+            t = target if isinstance(target, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(target, np.float32))
+            t = t.to(device="cuda", dtype=torch.float32).contiguous()
+        return f, o, t
+
+    def forward(self, feats, offsets, stream=None):
+        import torch
+        f, o, _ = self._dev(feats, offsets)
+        T = f.shape[0]
+        out = torch.empty(T, dtype=torch.float32, device="cuda")
+        _check(load_library().bem_net_forward(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+                                              o.numel() - 1, T, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def gradient(self, feats, offsets, target, stream=None):
+        f, o, t = self._dev(feats, offsets, target)
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(load_library().bem_net_gradient(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+                                               o.numel() - 1, f.shape[0], ctypes.c_void_p(t.data_ptr()), _ptr(g),
+                                               ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value, g
+
+    def train_step(self, feats, offsets, target, lr=1e-3, stream=None):
+        f, o, t = self._dev(feats, offsets, target)
+        loss = ctypes.c_double()
+        _check(load_library().bem_net_train_step(self._h, ctypes.c_void_p(f.data_ptr()),
+                                                 ctypes.c_void_p(o.data_ptr()), o.numel() - 1, f.shape[0],
+                                                 ctypes.c_void_p(t.data_ptr()), float(lr), ctypes.byref(loss),
+                                                 _stream_ptr(stream)))
+        return loss.value
 
 
 def bem_plan(dim, n, h, cell, w, normal, kernel="laplace2d", precision="f32", nu=0.3, mu=1.0, stream=None):
