@@ -11,7 +11,9 @@ The network (``bem_net_*``, 4 circular conv layers, 64 channels, BF16) maps
 per-cell features in arclength order
     (x - 1/2, y - 1/2, n_x, n_y, w/h, u/s, (D u)/s),  s = rms(u),
 where D u is the double layer of the data applied with the FFT operator
-itself, to q/s.  Training targets are solutions of the FFT method (FP32 GMRES
+itself, to the carried flux w q / (h s).  The operator only ever sees w_j q_j
+(Section 4: the source weight), so q itself is ill-determined on cells that
+hold a sliver of the curve while w q is not; the guess is x0 = pred h s / w.  Training targets are solutions of the FFT method (FP32 GMRES
 with FP64 residual refinement to 1e-8).  At solve time the prediction is
 passed to ``bem_solve`` as x0; zero-start GMRES remains the fallback and the
 FP64 residual judges the answer.
@@ -106,7 +108,7 @@ def generate(seeds, rhs_per_geometry=4, n=None, tol=1e-8, log=None):
             if info["status"] != 0:
                 continue
             f, s = features(b, u, du)
-            data.append((f, (q / s).astype(np.float32)))
+            data.append((f, (q * b.w / (b.h * s)).astype(np.float32)))
         plan.close()
         if log and (k + 1) % 100 == 0:
             log(f"generated {k + 1}/{len(seeds)} geometries, {len(data)} solves, {time.time() - t0:.0f} s")
@@ -136,13 +138,35 @@ def train(net, data, epochs=20, batch=16, lr=1e-3, seed=0, log=None):
     return hist
 
 
-def predict(net, b, u, du):
+def target_scale(data):
+    """Global scale of the training targets (their RMS), so that the network
+    predicts O(1) values; stored with the weights."""
+    return float(np.sqrt(np.mean(np.concatenate([t for _, t in data]) ** 2))) or 1.0
+
+
+def predict(net, b, u, du, tscale=1.0):
     f, s = features(b, u, du)
     off = np.array([0, f.shape[0]], np.int32)
-    return net.forward(f, off).cpu().numpy().astype(np.float64) * s
+    return net.forward(f, off).cpu().numpy().astype(np.float64) * tscale * (s * b.h) / b.w
 
 
-def evaluate(net, seeds, tol=1e-6, log=None):
+def safeguard(plan, bc, u, x0):
+    """Scale the guess by the alpha minimising ||b - alpha A x0|| (one FP32
+    apply of the BC-split operator and one of the right-hand side), so the
+    starting residual never exceeds the zero start's; alpha = 0 falls back to
+    zero-start GMRES."""
+    import torch
+    plan.set_bc(bc, 0.5)
+    xt = torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32)).cuda()
+    ax = plan.apply("system", xt).cpu().numpy().astype(np.float64)
+    ut = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
+    rhs = 0.5 * u - plan.apply("double", ut).cpu().numpy().astype(np.float64)
+    den = float(ax @ ax)
+    alpha = max(0.0, float(ax @ rhs) / den) if den > 0 else 0.0
+    return alpha * x0, alpha
+
+
+def evaluate(net, seeds, tol=1e-6, log=None, tscale=1.0):
     """Time to relative residual `tol` (FP32 GMRES + FP64 residual refinement,
     block-Jacobi preconditioner) from zero and from the network's guess."""
     import torch
@@ -157,12 +181,12 @@ def evaluate(net, seeds, tol=1e-6, log=None):
         _, _, z = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000)
         t0 = time.perf_counter()
         du = double_layer(plan, u)
-        x0 = predict(net, b, u, du)
+        x0, alpha = safeguard(plan, bc, u, predict(net, b, u, du, tscale))
         t_guess = time.perf_counter() - t0
         _, _, g = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000, x0=x0)
         rows.append({"seed": seed, "n": b.n, "nb": b.nb, "zero_iters": z["iters"], "zero_s": z["seconds"],
                      "zero_status": z["status"], "guess_iters": g["iters"], "guess_s": g["seconds"] + t_guess,
-                     "guess_status": g["status"], "guess_overhead_s": t_guess})
+                     "guess_status": g["status"], "guess_overhead_s": t_guess, "alpha": alpha})
         plan.close()
         if log:
             log(json.dumps(rows[-1]))
@@ -207,15 +231,19 @@ def main():
     data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.geoms), args.rhs, n=args.train_n or None, log=log)
     t_gen = time.time() - t0
     net = Net(**NET_SHAPE, seed=1)
+    tscale = target_scale(data)
+    data = [(f, t / tscale) for f, t in data]
     t0 = time.time()
     hist = train(net, data, epochs=args.epochs, log=log)
     t_train = time.time() - t0
-    save(net, meta={"train_solves": len(data), "epochs": args.epochs, "final_loss": hist[-1]})
-    ev = evaluate(net, range(TEST_SEED0, TEST_SEED0 + args.test), log=log)
+    save(net, meta={"train_solves": len(data), "epochs": args.epochs, "final_loss": hist[-1], "tscale": tscale})
+    ev = evaluate(net, range(TEST_SEED0, TEST_SEED0 + args.test), log=log, tscale=tscale)
     ev.update({"train_solves": len(data), "gen_s": t_gen, "train_s": t_train, "loss_history": hist})
     if args.out:
         with open(args.out, "w") as f:
             json.dump(ev, f, indent=1)
+    with open(os.path.join(HERE, "weights", "guess_net_eval.json"), "w") as f:
+        json.dump({k: v for k, v in ev.items() if k != "rows"}, f, indent=1)
     log(json.dumps({k: v for k, v in ev.items() if k != "rows"}))
 
 
