@@ -239,6 +239,43 @@ def secondary_configs(dev):
                                  "double_apply_ms": _time_applies(p, "double", x, 5),
                                  "plan_s": p.info()["plan_seconds"]}
     p.close()
+    # batched: 64 random stars on uneven grids, one CUDA graph per batched apply
+    from paper_1809_00845_gb300.bem import Batch
+    rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 4))
+    plans = []
+    for _ in range(64):
+        n = int(rng.choice((512, 1024, 2048)))
+        plans.append(Plan.from_boundary(I.curve_boundary(n, I.random_star_curve(rng)), "laplace2d", "f32"))
+    batch = Batch(plans, "single", streams=4)
+    for _ in range(3):
+        batch.apply()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        batch.apply()
+    e1.record()
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    xs = [torch.randn(p.nb, dtype=torch.float32, device=dev) for p in plans]
+    ys = [torch.empty_like(x) for x in xs]
+    for p, x, y in zip(plans, xs, ys):
+        p.apply("single", x, y)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        for p, x, y in zip(plans, xs, ys):
+            p.apply("single", x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / reps
+    out["batched_stars_64_f32"] = {"geometries": 64, "cells": int(sum(p.nb for p in plans)),
+                                   "graph_ms_per_batch": graph_ms, "graph_applies_per_s": 64e3 / graph_ms,
+                                   "loop_ms_per_batch": loop_ms, "kernel_launches_per_batch": batch.launches}
+    batch.close()
+    for p in plans:
+        p.close()
     b = I.cube_boundary(128)
     p = Plan.from_boundary(b, "kelvin3d", "f32")
     x = torch.randn(b.nb * 3, dtype=torch.float32, device=dev)

@@ -204,6 +204,24 @@ bem_status bem_kernel_time(bem_plan_t plan, double* total_ms, int64_t* launches)
 /* Number of kernel launches one apply of the given layer issues. */
 int bem_launches_per_apply(bem_plan_t plan, bem_layer layer);
 
+/* ---- batched apply (many geometries, one CUDA graph) --------------------
+ * The applies of `count` plans (one precision, grids of any sizes) captured
+ * once into a CUDA graph, the plans spread round-robin over `streams` forked
+ * capture streams so that small geometries run side by side; bem_batch_apply
+ * then replays the whole batch with one graph launch.  Inputs and outputs are
+ * two packed device buffers owned by the batch (plan i's nb_i*ncomp_i values at
+ * element offset bem_batch_offset(i)), so the captured pointers stay valid.
+ * The plans must outlive the batch and keep their boundary conditions
+ * (BEM_SYSTEM) unchanged; their kernel timing is switched off. */
+typedef struct bem_batch_s* bem_batch_t;
+bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count, bem_layer layer, int streams,
+                            void* stream);
+bem_status bem_batch_buffers(bem_batch_t batch, void** in_dev, void** out_dev, size_t* total);
+bem_status bem_batch_offset(bem_batch_t batch, int i, size_t* offset);
+bem_status bem_batch_apply(bem_batch_t batch, void* stream);
+int bem_batch_launches(bem_batch_t batch);  /* kernel launches inside one replay */
+bem_status bem_batch_destroy(bem_batch_t batch);
+
 /* ---- learned initial guess (serving/training pattern on top of the operator;
  * the paper has no learned component) ------------------------------------
  * A 1D convolutional network over the arclength-ordered cells of closed

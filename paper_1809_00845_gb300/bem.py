@@ -29,7 +29,8 @@ LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
-            "bem_status_string", "bem_last_error", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
+            "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
+            "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step"]
 
 
@@ -86,6 +87,15 @@ def load_library(path: str = LIB_PATH):
     lib.bem_destroy.argtypes = [P]
     lib.bem_status_string.argtypes = [I]
     lib.bem_status_string.restype = ctypes.c_char_p
+    lib.bem_batch_create.argtypes = [ctypes.POINTER(P), P, I, I, I, P]
+    lib.bem_batch_buffers.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t)]
+    lib.bem_batch_offset.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
+    lib.bem_batch_apply.argtypes = [P, P]
+    lib.bem_batch_launches.argtypes = [P]
+    lib.bem_batch_launches.restype = I
+    lib.bem_batch_destroy.argtypes = [P]
+    for name in ("bem_batch_create", "bem_batch_buffers", "bem_batch_offset", "bem_batch_apply", "bem_batch_destroy"):
+        getattr(lib, name).restype = I
     lib.bem_net_create.argtypes = [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64]
     lib.bem_net_destroy.argtypes = [P]
     lib.bem_net_num_params.argtypes = [P]
@@ -259,6 +269,42 @@ class Plan:
     def launches_per_apply(self, layer="system"):
         lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
         return int(load_library().bem_launches_per_apply(self._h, lay))
+
+
+class Batch:
+    """One CUDA graph applying every plan's operator (bem_batch_*)."""
+
+    def __init__(self, plans, layer="single", streams=4, stream=None):
+        lib = load_library()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
+        self._h = ctypes.c_void_p()
+        _check(lib.bem_batch_create(ctypes.byref(self._h), arr, len(self.plans), lay, int(streams),
+                                    _stream_ptr(stream)))
+        din, dout, tot = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_size_t()
+        _check(lib.bem_batch_buffers(self._h, ctypes.byref(din), ctypes.byref(dout), ctypes.byref(tot)))
+        self.d_in, self.d_out, self.total = din.value, dout.value, tot.value
+        self.offsets = []
+        for i in range(len(self.plans)):
+            o = ctypes.c_size_t()
+            _check(lib.bem_batch_offset(self._h, i, ctypes.byref(o)))
+            self.offsets.append(o.value)
+        self.launches = int(lib.bem_batch_launches(self._h))
+
+    def apply(self, stream=None):
+        _check(load_library().bem_batch_apply(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().bem_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Net:
