@@ -324,8 +324,23 @@ __device__ __forceinline__ int oddy_of(const Col2Dv2Params<T>& p, int f) {
 
 template <typename T>
 __device__ __forceinline__ void load_spectrum(const Col2Dv2Params<T>& p, int f, int kx, T* sS) {
+  // asynchronous global -> shared copies (no register staging): issued before
+  // the forward transform, waited for (spectrum_ready) just before the
+  // multiply, so the HBM latency hides behind the transform
   const T* S = spec_of(p, f) + (size_t)kx * (p.n + 1);
-  for (int i = threadIdx.x; i <= p.n; i += blockDim.x) sS[swz16(i)] = __ldg(S + i);
+  for (int i = threadIdx.x; i <= p.n; i += blockDim.x) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sS + swz16(i));
+    if constexpr (sizeof(T) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(S + i) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(S + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void spectrum_ready() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
 }
 
 template <typename T>
@@ -377,6 +392,7 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
         __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
         load_spectrum(p, f, kx, sS);
         fs.template forward<true>(v);
+        spectrum_ready();
         const bool im = imag_of(p, f) != 0, oy = oddy_of(p, f) != 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -406,6 +422,7 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
         __syncthreads();
         load_spectrum(p, f, kx, sS);
         fs.template forward<true>(v);
+        spectrum_ready();
         const bool im = imag_of(p, f) != 0, oy = oddy_of(p, f) != 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = spectral_term(p, im, oy, sS, fs.freq(k), v[k]);
