@@ -190,26 +190,38 @@ __global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem,
 
 // ------------------------------------------------- four-step column kernel
 //
-// For N >= 512.  Thread t owns a contiguous range of grid rows
-// [rowbeg[t], rowbeg[t+1]) and therefore the contiguous range of sorted cells
-// [chunk[t], chunk[t+1]) lying in those rows (ranges balanced by cells + rows
-// at plan time).  Per column kx:
-//   1. the thread walks its cells (loads batched 8 at a time), forms the
-//      input-pruned x-DFT of every field row by row and writes its rows
-//      (zeros for empty rows) to shared memory: field 0 into the transform
-//      buffer, fields 1.. into staging rows;
+// For N >= 512.  Thread t owns the contiguous range of sorted cells
+// [chunk[t], chunk[t+1]) (equal cell counts, fixed at plan time; a grid row
+// may be split between neighbouring threads).  Per column kx:
+//   1. the thread walks its cells (loads and twiddles batched 8 at a time) and
+//      forms the input-pruned x-DFT of every field row by row.  A row sum is
+//      stored when the row's last cell in the chunk is reached (flag in the
+//      cell word): into shared memory (field 0 into the transform buffer,
+//      fields 1.. into staging rows), or, for the first row of a chunk that
+//      began in an earlier chunk, into the thread's carry slot.  Empty rows
+//      are never written: the transform input masks them (a per-thread bit
+//      mask of its eight rows).  After a barrier, the thread holding the
+//      first cell of a split row adds the carries of the following threads
+//      in thread order (deterministic);
 //   2. each field is loaded into the four-step engine's register map
 //      (rows t + m*TT), transformed, multiplied by the spectrum column (copied
-//      to shared memory with coalesced loads) and accumulated;
+//      to shared memory asynchronously during the transform) and accumulated;
 //   3. the inverse transform leaves rows t + m*TT in registers, they are
 //      written to shared memory and every thread gathers its own cells
 //      (output-pruned inverse x-DFT) into its accumulators.
+//
+// Cell word (plan time): x | row << 12 | FLUSH << 29 | CARRY << 30 | type << 31.
+constexpr uint32_t kMetaFlush = 1u << 29;
+constexpr uint32_t kMetaCarry = 1u << 30;
+__device__ __forceinline__ int meta_x(uint32_t m) { return (int)(m & 0xfffu); }
+__device__ __forceinline__ int meta_row(uint32_t m) { return (int)((m >> 12) & 0xfffu); }
+
 template <typename T>
 struct Col2Dv2Params {
   int n, log2N, nb;
   const int32_t* chunk;   // TT + 1
-  const int32_t* rowbeg;  // TT + 1
-  const uint32_t* meta;   // nb: x | row << 16 | type << 31
+  const int32_t* tinfo;   // TT: row mask (8 bits) | continuing threads << 8
+  const uint32_t* meta;   // nb cell words
   const cplx<T>* val;     // nb density pairs
   const T* spec[3];
   int imag[3];
@@ -217,6 +229,7 @@ struct Col2Dv2Params {
   const cplx<T>* fstab;  // four-step tables (lane, warp, t5) then sparse tables (hi, lo)
   T* partial;            // gridDim.x * nb, sorted cell order
   int acc_in_smem;
+  int has_carry;         // some row is split between threads
 };
 
 // number of table entries of the four-step kernel for TT threads, N = 16 TT
@@ -225,27 +238,19 @@ __host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 
 __host__ __device__ inline int sspec_entries(int n) { return ((n + 1 + (n + 1) / 16) + 3) & ~3; }
 __device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 
-// Walk cells [c0, c1) (rows r0 <= row < r1) and write the x-DFT of the
-// selected fields per row: FSEL < 0 = all NF fields (field 0 -> out0[row],
-// field f > 0 -> outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.
+// Walk cells [c0, c1) and store the x-DFT row sums of the selected fields:
+// FSEL < 0 = all NF fields (field 0 -> out0[row], field f > 0 ->
+// outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.  Carried sums go
+// to carry[f*TT + t] (f = 0 for FSEL >= 0).
 template <typename T, int NF, int FSEL>
-__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int c0, int c1, int r0, int r1,
-                                            cplx<T>* out0, cplx<T>* outF, const Twiddles2L<T>& tw) {
+__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int c0, int c1, cplx<T>* out0,
+                                            cplx<T>* outF, cplx<T>* carry, const Twiddles2L<T>& tw) {
   const int Nm = (1 << p.log2N) - 1;
+  const int t = threadIdx.x, TT = blockDim.x;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
-  int cur = r0;
-  auto flush = [&](int r) {
-    if (FSEL < 0) {
-      out0[r] = s0;
-      if (NF > 1) outF[r] = s1;
-      if (NF > 2) outF[p.n + r] = s2;
-    } else {
-      out0[r] = FSEL == 0 ? s0 : (FSEL == 1 ? s1 : s2);
-    }
-  };
   for (int j0 = c0; j0 < c1; j0 += 8) {
     uint32_t mt[8];
-    cplx<T> vv[8];
+    cplx<T> vv[8], w[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int j = j0 + i < c1 ? j0 + i : c1 - 1;
@@ -253,37 +258,57 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, i
       vv[i] = p.val[j];
     }
 #pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
+#pragma unroll
     for (int i = 0; i < 8; ++i) {
       if (j0 + i < c1) {
-        const int row = (int)((mt[i] >> 16) & 0x7fffu), x = (int)(mt[i] & 0xffffu);
         const bool ty = (mt[i] >> 31) != 0;
-        while (cur < row) {
-          flush(cur);
-          s0 = s1 = s2 = {T(0), T(0)};
-          ++cur;
-        }
-        const cplx<T> w = tw.template get<-1>((kx * x) & Nm);
         const T a = vv[i].x, b = vv[i].y;
         const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
         if (FSEL < 0 || FSEL == 0) {
-          s0.x += ca * w.x;
-          s0.y += ca * w.y;
+          s0.x += ca * w[i].x;
+          s0.y += ca * w[i].y;
         }
         if ((FSEL < 0 && NF > 1) || FSEL == 1) {
-          s1.x += cb * w.x;
-          s1.y += cb * w.y;
+          s1.x += cb * w[i].x;
+          s1.y += cb * w[i].y;
         }
         if ((FSEL < 0 && NF > 2) || FSEL == 2) {
-          s2.x += cc * w.x;
-          s2.y += cc * w.y;
+          s2.x += cc * w[i].x;
+          s2.y += cc * w[i].y;
+        }
+        if (mt[i] & kMetaFlush) {
+          const int row = meta_row(mt[i]);
+          const bool car = (mt[i] & kMetaCarry) != 0;
+          if (FSEL < 0) {
+            (car ? carry + t : out0 + row)[0] = s0;
+            if (NF > 1) (car ? carry + TT + t : outF + row)[0] = s1;
+            if (NF > 2) (car ? carry + 2 * TT + t : outF + p.n + row)[0] = s2;
+          } else {
+            (car ? carry + t : out0 + row)[0] = FSEL == 0 ? s0 : (FSEL == 1 ? s1 : s2);
+          }
+          s0 = s1 = s2 = {T(0), T(0)};
         }
       }
     }
   }
-  while (cur < r1) {
-    flush(cur);
-    s0 = s1 = s2 = {T(0), T(0)};
-    ++cur;
+}
+
+// After a barrier: the thread holding the first cell of a split row (its
+// last row) adds the carries of the `ncont` following threads, in order.
+template <typename T, int NF, int FSEL>
+__device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, int c1, int ncont, cplx<T>* out0,
+                                            cplx<T>* outF, const cplx<T>* carry) {
+  if (ncont == 0) return;
+  const int t = threadIdx.x, TT = blockDim.x;
+  const int row = meta_row(__ldg(p.meta + c1 - 1));
+  constexpr int nfs = FSEL < 0 ? NF : 1;
+#pragma unroll
+  for (int f = 0; f < nfs; ++f) {
+    cplx<T>* dst = f == 0 ? out0 + row : outF + (size_t)(f - 1) * p.n + row;
+    cplx<T> s = *dst;
+    for (int i = 1; i <= ncont; ++i) s = s + carry[f * TT + t + i];
+    *dst = s;
   }
 }
 
@@ -294,17 +319,17 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, 
   const T ckx = (kx == 0 || kx == p.n) ? T(1) : T(2);
   for (int j0 = c0; j0 < c1; j0 += 8) {
     uint32_t mt[8];
+    cplx<T> Y[8], w[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (j0 + i < c1 ? j0 + i : c1 - 1));
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      if (j0 + i < c1) {
-        const int row = (int)((mt[i] >> 16) & 0x7fffu), x = (int)(mt[i] & 0xffffu);
-        const cplx<T> Y = rows[row];
-        const cplx<T> w = tw.template get<+1>((kx * x) & Nm);
-        acc[j0 + i] += ckx * (Y.x * w.x - Y.y * w.y);
-      }
+      Y[i] = rows[meta_row(mt[i])];
+      w[i] = tw.template get<+1>((kx * meta_x(mt[i])) & Nm);
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (j0 + i < c1) acc[j0 + i] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
   }
 }
 
@@ -363,32 +388,47 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
   cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* stab = sA + nbuf;
   T* sS = reinterpret_cast<T*>(stab + ntab);
+  // carries of split rows (3 * TT entries) share the spectrum buffer: both
+  // are dead between the last multiply of a column and the first spectrum
+  // copy of the next one
+  cplx<T>* carry = reinterpret_cast<cplx<T>*>(sS);
   cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
   T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
                          : p.partial + (size_t)blockIdx.x * p.nb;
   for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
-  const int c0 = p.chunk[t], c1 = p.chunk[t + 1], r0 = p.rowbeg[t], r1 = p.rowbeg[t + 1];
-  for (int j = c0; j < c1; ++j) acc[j] = T(0);
+  // per-thread plan data is re-read (L1) where used rather than held in
+  // registers across the transforms
+#define C0 __ldg(p.chunk + t)
+#define C1 __ldg(p.chunk + t + 1)
+#define TINFO __ldg(p.tinfo + t)
+  for (int j = C0; j < C1; ++j) acc[j] = T(0);
   __syncthreads();
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
   const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + (N >> 6)};
   FourStep<T> fs;
   fs.init(t, TT, sA, ftab);
+  auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
+    const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[t + m * TT] : cplx<T>{T(0), T(0)};
+#pragma unroll
+    for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+  };
 
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
     __syncthreads();  // the previous column's gather has finished reading sA
     if constexpr (ACCREG) {
-      sparse_rows<T, NF, -1>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+      sparse_rows<T, NF, -1>(p, kx, C0, C1, sA, sF, carry, tw);
       __syncthreads();
+      if (p.has_carry) {
+        add_carries<T, NF, -1>(p, C1, TINFO >> 8, sA, sF, carry);
+        __syncthreads();
+      }
       cplx<T> y[16];
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
         cplx<T> v[16];
-        const cplx<T>* src = f == 0 ? sA : sF + (size_t)(f - 1) * n;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = src[t + m * TT];
-#pragma unroll
-        for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+        load_rows(f == 0 ? sA : sF + (size_t)(f - 1) * n, v);
         __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
         load_spectrum(p, f, kx, sS);
         fs.template forward<true>(v);
@@ -404,21 +444,22 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) sA[t + m * TT] = y[m];
       __syncthreads();
-      gather_cells(p, kx, c0, c1, sA, tw, acc);
+      gather_cells(p, kx, C0, C1, sA, tw, acc);
     } else {
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
         if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
-        if (NF == 1) sparse_rows<T, NF, -1>(p, kx, c0, c1, r0, r1, sA, sF, tw);
-        else if (f == 0) sparse_rows<T, NF, 0>(p, kx, c0, c1, r0, r1, sA, sF, tw);
-        else if (f == 1) sparse_rows<T, NF, 1>(p, kx, c0, c1, r0, r1, sA, sF, tw);
-        else sparse_rows<T, NF, 2>(p, kx, c0, c1, r0, r1, sA, sF, tw);
+        if (NF == 1) sparse_rows<T, NF, -1>(p, kx, C0, C1, sA, sF, carry, tw);
+        else if (f == 0) sparse_rows<T, NF, 0>(p, kx, C0, C1, sA, sF, carry, tw);
+        else if (f == 1) sparse_rows<T, NF, 1>(p, kx, C0, C1, sA, sF, carry, tw);
+        else sparse_rows<T, NF, 2>(p, kx, C0, C1, sA, sF, carry, tw);
         __syncthreads();
+        if (p.has_carry) {
+          add_carries<T, NF, 0>(p, C1, TINFO >> 8, sA, sF, carry);
+          __syncthreads();
+        }
         cplx<T> v[16];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = sA[t + m * TT];
-#pragma unroll
-        for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+        load_rows(sA, v);
         __syncthreads();
         load_spectrum(p, f, kx, sS);
         fs.template forward<true>(v);
@@ -430,12 +471,15 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) sA[t + m * TT] = v[m];
         __syncthreads();
-        gather_cells(p, kx, c0, c1, sA, tw, acc);
+        gather_cells(p, kx, C0, C1, sA, tw, acc);
       }
     }
   }
   if (p.acc_in_smem)
-    for (int j = c0; j < c1; ++j) p.partial[(size_t)blockIdx.x * p.nb + j] = acc[j];
+    for (int j = C0; j < C1; ++j) p.partial[(size_t)blockIdx.x * p.nb + j] = acc[j];
+#undef C0
+#undef C1
+#undef TINFO
 }
 
 // val[j] = (coefA[j], coefB[j]) * in[perm[j]]
@@ -594,7 +638,7 @@ static size_t smem_2d(int64_t N, int64_t nelem, bool acc) {
 template <typename T, int E, int NF, bool ACCREG>
 static cudaError_t configure_one(size_t smem, int threads, int* blocks_per_sm) {
   auto kern = k_col2d<T, E, NF, ACCREG>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_optin_smem(kern);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, threads, smem);
 }
@@ -660,7 +704,7 @@ static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc) {
 template <typename T, int NF, bool ACCREG>
 static cudaError_t configure_v2_one(size_t smem, int threads, int* bps) {
   auto kern = k_col2d_v2<T, NF, ACCREG>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_optin_smem(kern);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, threads, smem);
 }
@@ -671,26 +715,38 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   const int64_t n = p->n, nb = p->nb;
   const int TT = (int)(p->N / 16);
   p->threads = TT;
-  // balanced contiguous row ranges: cost of a row = 1 + its cells
-  std::vector<int64_t> rowcnt(n, 0);
-  for (int64_t j = 0; j < nb; ++j) rowcnt[p->h_row[j]]++;
-  const double total = (double)(n + nb);
-  std::vector<int32_t> rowbeg(TT + 1), chunk(TT + 1);
+  // equal contiguous cell ranges; a row may be split between neighbouring
+  // threads (its first holder stores the row, the others carry)
+  std::vector<int32_t> chunk(TT + 1), tinfo(TT, 0);
   {
-    int64_t r = 0, cells = 0;
-    double acc = 0;
-    for (int t = 0; t < TT; ++t) {
-      rowbeg[t] = (int32_t)r;
-      chunk[t] = (int32_t)cells;
-      const double target = total * (t + 1) / TT;
-      while (r < n && (t == TT - 1 || acc + 0.5 * (1 + rowcnt[r]) <= target)) {
-        acc += 1 + rowcnt[r];
-        cells += rowcnt[r];
-        ++r;
-      }
+    // q or q + 1 cells per thread; with fewer cells than threads the empty
+    // ranges all come last
+    const int64_t q = nb / TT, r = nb % TT;
+    for (int t = 0; t <= TT; ++t) chunk[t] = (int32_t)(t * q + std::min<int64_t>(t, r));
+  }
+  p->h_cellflag.assign(nb, 0u);
+  p->v2_carry = false;
+  for (int t = 0; t < TT; ++t) {
+    const int64_t c0 = chunk[t], c1 = chunk[t + 1];
+    if (c0 == c1) continue;
+    const bool cont = c0 > 0 && p->h_row[c0 - 1] == p->h_row[c0];
+    for (int64_t j = c0; j < c1; ++j) {
+      if (j + 1 == c1 || p->h_row[j + 1] != p->h_row[j]) p->h_cellflag[j] |= 1u;  // last of its row here
+      if (cont && p->h_row[j] == p->h_row[c0]) p->h_cellflag[j] |= 2u;            // carried
     }
-    rowbeg[TT] = (int32_t)n;
-    chunk[TT] = (int32_t)nb;
+    // threads after t whose first row continues t's last row (t holds its first cell)
+    const int32_t last = p->h_row[c1 - 1];
+    const bool owner = !(cont && last == p->h_row[c0]);
+    if (owner) {
+      int k = 0;
+      for (int u = t + 1; u < TT && chunk[u] < chunk[u + 1] && p->h_row[chunk[u]] == last; ++u) ++k;
+      tinfo[t] |= k << 8;
+      if (k) p->v2_carry = true;
+    }
+  }
+  for (int64_t j = 0; j < nb; ++j) {
+    const int32_t r = p->h_row[j];
+    tinfo[r % TT] |= 1 << (r / TT);  // row r = t + m*TT, m < 8
   }
   {
     // four-step and sparse twiddle tables, FP64 on the host, rounded once
@@ -717,9 +773,9 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     BEM_CUDA_TRY(cudaMalloc(&p->d_fstab, tab.size() * sizeof(cplx<T>)));
     BEM_CUDA_TRY(cudaMemcpy(p->d_fstab, tab.data(), tab.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
   }
-  BEM_CUDA_TRY(cudaMalloc(&p->d_rowbeg, (TT + 1) * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_tinfo, TT * sizeof(int32_t)));
   BEM_CUDA_TRY(cudaMalloc(&p->d_chunk, (TT + 1) * sizeof(int32_t)));
-  BEM_CUDA_TRY(cudaMemcpy(p->d_rowbeg, rowbeg.data(), (TT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMemcpy(p->d_tinfo, tinfo.data(), TT * sizeof(int32_t), cudaMemcpyHostToDevice));
   BEM_CUDA_TRY(cudaMemcpy(p->d_chunk, chunk.data(), (TT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
   int dev = 0, nsm = 0, smem_optin = 0;
   BEM_CUDA_TRY(cudaGetDevice(&dev));
@@ -763,7 +819,8 @@ bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& c
   const int64_t nb = p->nb;
   std::vector<uint32_t> meta(nb);
   for (int64_t j = 0; j < nb; ++j)
-    meta[j] = (uint32_t)p->h_col[j] | ((uint32_t)p->h_row[j] << 16) | ((uint32_t)(type[j] ? 1u : 0u) << 31);
+    meta[j] = (uint32_t)p->h_col[j] | ((uint32_t)p->h_row[j] << 12) | ((uint32_t)p->h_cellflag[j] << 29) |
+              ((uint32_t)(type[j] ? 1u : 0u) << 31);
   void* dm = nullptr;
   BEM_CUDA_TRY(cudaMalloc(&dm, nb * sizeof(uint32_t)));
   BEM_CUDA_TRY(cudaMemcpy(dm, meta.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -868,7 +925,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.log2N = p->log2N;
   cp.nb = nb;
   cp.chunk = p->d_chunk;
-  cp.rowbeg = p->d_rowbeg;
+  cp.tinfo = p->d_tinfo;
   cp.meta = op.meta;
   cp.val = static_cast<const cplx<T>*>(sp.val);
   for (int f = 0; f < op.nf; ++f) {
@@ -880,6 +937,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.fstab = static_cast<const cplx<T>*>(p->d_fstab);
   cp.partial = static_cast<T*>(sp.partial);
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
+  cp.has_carry = p->v2_carry ? 1 : 0;
   cudaEvent_t e1 = nullptr;
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   constexpr bool R = std::is_same<T, float>::value;

@@ -322,10 +322,10 @@ static bem_status configure3d_t(bem_plan_s* p) {
     set_error("3D grid too large for the shared-memory line buffers");
     return BEM_ERR_UNSUPPORTED;
   }
-  BEM_CUDA_TRY(cudaFuncSetAttribute(k3_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_y));
-  BEM_CUDA_TRY(cudaFuncSetAttribute(k3_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_y));
+  BEM_CUDA_TRY(allow_optin_smem(k3_ypass<T>));
+  BEM_CUDA_TRY(allow_optin_smem(k3_yinv<T>));
   // every operator's z pass stays within zpass_lpc's budget (<= 200 KB)
-  BEM_CUDA_TRY(cudaFuncSetAttribute(k3_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  BEM_CUDA_TRY(allow_optin_smem(k3_zpass<T>));
   return BEM_OK;
 }
 

@@ -130,9 +130,11 @@ struct bem_plan_s {
   bool have_bc = false;
   std::vector<uint8_t> h_bc;
   bemfft::BlockPrecond pc;
-  // four-step column kernel: per-thread balanced row ranges and cell ranges
+  // four-step column kernel: per-thread equal cell ranges
   bool v2 = false;
-  int32_t* d_rowbeg = nullptr;  // threads + 1
+  bool v2_carry = false;              // some grid row is split between threads
+  std::vector<uint32_t> h_cellflag;   // sorted order: 1 = last cell of its row in the chunk, 2 = carried
+  int32_t* d_tinfo = nullptr;   // threads: row mask | continuing threads << 8
   int32_t* d_chunk = nullptr;   // threads + 1
   void* d_val = nullptr;        // nb density pairs (scratch)
   void* d_fstab = nullptr;      // twiddle tables of the four-step kernel
@@ -212,6 +214,18 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
                        cudaStream_t st);
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);
 size_t prec_bytes(const bem_plan_s* p);
+// Lets `kern` launch with up to the device's opt-in shared-memory maximum.  The
+// limit is a property of the function, shared by every plan, so it is never set
+// to one plan's (smaller) need: a plan made later would otherwise lower it below
+// what an earlier plan launches with.
+template <typename K>
+inline cudaError_t allow_optin_smem(K kern) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return e;
+}
 bem_status build_preconditioner(bem_plan_s* p);
 double kernel2d_point(int kind, int dx, int dy, double h);
 

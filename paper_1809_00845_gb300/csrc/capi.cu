@@ -620,7 +620,7 @@ bem_status bem_destroy(bem_plan_t p) {
   free_operator(p->op_double);
   free_operator(p->op_system);
   free_slot_set(&p->all_set);
-  cudaFree(p->d_rowbeg);
+  cudaFree(p->d_tinfo);
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
   cudaFree(p->d_fstab);

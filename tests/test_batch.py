@@ -48,6 +48,32 @@ def test_batch_equals_individual_applies(torch_cuda, layer):
     batch.close()
 
 
+@pytest.mark.parametrize("kernel,sizes", [("laplace2d", (2048, 512)), ("laplace2d", (256, 64)),
+                                           ("laplace3d", (32, 16))])
+def test_larger_plan_still_applies_after_smaller_plan(torch_cuda, kernel, sizes):
+    """A plan keeps working (bit for bit) after a plan of a smaller grid, whose
+    kernels need less shared memory, has been made; the batch capture in
+    random size order depends on this."""
+    torch = torch_cuda
+    from paper_1809_00845_gb300.bem import Plan
+    rng = np.random.default_rng(7)
+    if kernel == "laplace2d":
+        big, small = (I.curve_boundary(n, I.random_star_curve(rng)) for n in sizes)
+    else:
+        big, small = (I.ellipsoid_boundary(n) for n in sizes)
+    p = Plan.from_boundary(big, kernel, "f32")
+    x = torch.from_numpy(rng.standard_normal(big.nb).astype(np.float32)).cuda()
+    before = p.apply("single", x)
+    torch.cuda.synchronize()
+    q = Plan.from_boundary(small, kernel, "f32")
+    q.apply("single", torch.ones(small.nb, dtype=torch.float32, device="cuda"))
+    after = p.apply("single", x)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+    p.close()
+    q.close()
+
+
 def _as_tensor(torch, ptr, numel):
     """A float32 CUDA tensor aliasing device memory at ptr (no copy)."""
     class _Cai:
