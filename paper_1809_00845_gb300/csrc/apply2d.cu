@@ -192,7 +192,10 @@ __global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem,
 //
 // For N >= 512.  Thread t owns the contiguous range of sorted cells
 // [chunk[t], chunk[t+1]) (equal cell counts, fixed at plan time; a grid row
-// may be split between neighbouring threads).  Per column kx:
+// may be split between neighbouring threads).  Per-cell arrays (cell words,
+// density pairs, accumulators) are stored interleaved: the i-th cell of
+// thread t sits at position i*TT + t, so every warp-wide access of the cell
+// loops is one contiguous segment.  Per column kx:
 //   1. the thread walks its cells (loads and twiddles batched 8 at a time) and
 //      forms the input-pruned x-DFT of every field row by row.  A row sum is
 //      stored when the row's last cell in the chunk is reached (flag in the
@@ -221,13 +224,14 @@ struct Col2Dv2Params {
   int n, log2N, nb;
   const int32_t* chunk;   // TT + 1
   const int32_t* tinfo;   // TT: row mask (8 bits) | continuing threads << 8
-  const uint32_t* meta;   // nb cell words
-  const cplx<T>* val;     // nb density pairs
+  const uint32_t* meta;   // Q*TT cell words, interleaved
+  const cplx<T>* val;     // Q*TT density pairs, interleaved
   const T* spec[3];
   int imag[3];
   int oddy[3];
   const cplx<T>* fstab;  // four-step tables (lane, warp, t5) then sparse tables (hi, lo)
-  T* partial;            // gridDim.x * nb, sorted cell order
+  T* partial;            // gridDim.x * npos, interleaved positions
+  int npos;              // Q*TT
   int acc_in_smem;
   int has_carry;         // some row is split between threads
 };
@@ -243,25 +247,25 @@ __device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 // outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.  Carried sums go
 // to carry[f*TT + t] (f = 0 for FSEL >= 0).
 template <typename T, int NF, int FSEL>
-__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int c0, int c1, cplx<T>* out0,
+__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int cnt, cplx<T>* out0,
                                             cplx<T>* outF, cplx<T>* carry, const Twiddles2L<T>& tw) {
   const int Nm = (1 << p.log2N) - 1;
   const int t = threadIdx.x, TT = blockDim.x;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
-  for (int j0 = c0; j0 < c1; j0 += 8) {
+  for (int i0 = 0; i0 < cnt; i0 += 8) {
     uint32_t mt[8];
     cplx<T> vv[8], w[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int j = j0 + i < c1 ? j0 + i : c1 - 1;
-      mt[i] = __ldg(p.meta + j);
-      vv[i] = p.val[j];
+      const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
+      mt[i] = __ldg(p.meta + pos);
+      vv[i] = p.val[pos];
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      if (j0 + i < c1) {
+      if (i0 + i < cnt) {
         const bool ty = (mt[i] >> 31) != 0;
         const T a = vv[i].x, b = vv[i].y;
         const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
@@ -297,11 +301,11 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, i
 // After a barrier: the thread holding the first cell of a split row (its
 // last row) adds the carries of the `ncont` following threads, in order.
 template <typename T, int NF, int FSEL>
-__device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, int c1, int ncont, cplx<T>* out0,
+__device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, int cnt, int ncont, cplx<T>* out0,
                                             cplx<T>* outF, const cplx<T>* carry) {
   if (ncont == 0) return;
   const int t = threadIdx.x, TT = blockDim.x;
-  const int row = meta_row(__ldg(p.meta + c1 - 1));
+  const int row = meta_row(__ldg(p.meta + (cnt - 1) * TT + t));
   constexpr int nfs = FSEL < 0 ? NF : 1;
 #pragma unroll
   for (int f = 0; f < nfs; ++f) {
@@ -313,15 +317,16 @@ __device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, int c1, i
 }
 
 template <typename T>
-__device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, int c0, int c1, const cplx<T>* rows,
+__device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, int cnt, const cplx<T>* rows,
                                              const Twiddles2L<T>& tw, T* acc) {
   const int Nm = (1 << p.log2N) - 1;
+  const int t = threadIdx.x, TT = blockDim.x;
   const T ckx = (kx == 0 || kx == p.n) ? T(1) : T(2);
-  for (int j0 = c0; j0 < c1; j0 += 8) {
+  for (int i0 = 0; i0 < cnt; i0 += 8) {
     uint32_t mt[8];
     cplx<T> Y[8], w[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (j0 + i < c1 ? j0 + i : c1 - 1));
+    for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       Y[i] = rows[meta_row(mt[i])];
@@ -329,7 +334,7 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, 
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      if (j0 + i < c1) acc[j0 + i] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
+      if (i0 + i < cnt) acc[(i0 + i) * TT + t] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
   }
 }
 
@@ -394,14 +399,14 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
   cplx<T>* carry = reinterpret_cast<cplx<T>*>(sS);
   cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
   T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
-                         : p.partial + (size_t)blockIdx.x * p.nb;
+                         : p.partial + (size_t)blockIdx.x * p.npos;
   for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
   // per-thread plan data is re-read (L1) where used rather than held in
   // registers across the transforms
 #define C0 __ldg(p.chunk + t)
-#define C1 __ldg(p.chunk + t + 1)
+#define CNT (__ldg(p.chunk + t + 1) - __ldg(p.chunk + t))
 #define TINFO __ldg(p.tinfo + t)
-  for (int j = C0; j < C1; ++j) acc[j] = T(0);
+  for (int i = 0; i < CNT; ++i) acc[i * TT + t] = T(0);
   __syncthreads();
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
   const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + (N >> 6)};
@@ -418,10 +423,10 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
     __syncthreads();  // the previous column's gather has finished reading sA
     if constexpr (ACCREG) {
-      sparse_rows<T, NF, -1>(p, kx, C0, C1, sA, sF, carry, tw);
+      sparse_rows<T, NF, -1>(p, kx, CNT, sA, sF, carry, tw);
       __syncthreads();
       if (p.has_carry) {
-        add_carries<T, NF, -1>(p, C1, TINFO >> 8, sA, sF, carry);
+        add_carries<T, NF, -1>(p, CNT, TINFO >> 8, sA, sF, carry);
         __syncthreads();
       }
       cplx<T> y[16];
@@ -444,18 +449,18 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) sA[t + m * TT] = y[m];
       __syncthreads();
-      gather_cells(p, kx, C0, C1, sA, tw, acc);
+      gather_cells(p, kx, CNT, sA, tw, acc);
     } else {
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
         if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
-        if (NF == 1) sparse_rows<T, NF, -1>(p, kx, C0, C1, sA, sF, carry, tw);
-        else if (f == 0) sparse_rows<T, NF, 0>(p, kx, C0, C1, sA, sF, carry, tw);
-        else if (f == 1) sparse_rows<T, NF, 1>(p, kx, C0, C1, sA, sF, carry, tw);
-        else sparse_rows<T, NF, 2>(p, kx, C0, C1, sA, sF, carry, tw);
+        if (NF == 1) sparse_rows<T, NF, -1>(p, kx, CNT, sA, sF, carry, tw);
+        else if (f == 0) sparse_rows<T, NF, 0>(p, kx, CNT, sA, sF, carry, tw);
+        else if (f == 1) sparse_rows<T, NF, 1>(p, kx, CNT, sA, sF, carry, tw);
+        else sparse_rows<T, NF, 2>(p, kx, CNT, sA, sF, carry, tw);
         __syncthreads();
         if (p.has_carry) {
-          add_carries<T, NF, 0>(p, C1, TINFO >> 8, sA, sF, carry);
+          add_carries<T, NF, 0>(p, CNT, TINFO >> 8, sA, sF, carry);
           __syncthreads();
         }
         cplx<T> v[16];
@@ -471,43 +476,46 @@ __global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) sA[t + m * TT] = v[m];
         __syncthreads();
-        gather_cells(p, kx, C0, C1, sA, tw, acc);
+        gather_cells(p, kx, CNT, sA, tw, acc);
       }
     }
   }
   if (p.acc_in_smem)
-    for (int j = C0; j < C1; ++j) p.partial[(size_t)blockIdx.x * p.nb + j] = acc[j];
+    for (int i = 0; i < CNT; ++i) p.partial[(size_t)blockIdx.x * p.npos + i * TT + t] = acc[i * TT + t];
 #undef C0
-#undef C1
+#undef CNT
 #undef TINFO
 }
 
-// val[j] = (coefA[j], coefB[j]) * in[perm[j]]
+// val[pos] = (coefA[pos], coefB[pos]) * in[perm[pos]] (interleaved positions;
+// padding positions have perm < 0 and get zero)
 template <typename T>
-__global__ void k_prep_v2(int nb, const int32_t* __restrict__ perm, const T* __restrict__ in,
+__global__ void k_prep_v2(int npos, const int32_t* __restrict__ perm, const T* __restrict__ in,
                           const T* __restrict__ coefA, const T* __restrict__ coefB, cplx<T>* __restrict__ val) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nb) return;
-  const T x = in[perm[j]];
+  if (j >= npos) return;
+  const int u = perm[j];
+  const T x = u >= 0 ? in[u] : T(0);
   val[j] = {coefA[j] * x, coefB[j] * x};
 }
 
-// out[perm[j]] = sum_b partial[b*nb + j] (+ diag * in), FP64 sum in a fixed
+// out[perm[j]] = sum_b partial[b*npos + j] (+ diag * in) over interleaved
+// positions j (padding skipped), FP64 sum in a fixed
 // order: 32 cells per block, 8 warps each summing every 8th partial, then the
 // 8 warp sums in order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce_v2(const T* __restrict__ partial, int grid, int nb,
+__global__ void __launch_bounds__(256) k_reduce_v2(const T* __restrict__ partial, int grid, int npos,
                                                    const int32_t* __restrict__ perm, const T* __restrict__ diag,
                                                    const T* __restrict__ in, T* __restrict__ out) {
   __shared__ double red[8][33];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
   double s = 0.0;
-  if (j < nb)
-    for (int b = wp; b < grid; b += 8) s += (double)partial[(size_t)b * nb + j];
+  if (j < npos)
+    for (int b = wp; b < grid; b += 8) s += (double)partial[(size_t)b * npos + j];
   red[wp][lane] = s;
   __syncthreads();
-  if (wp == 0 && j < nb) {
+  if (wp == 0 && j < npos && perm[j] >= 0) {
     double t = 0.0;
     for (int k = 0; k < 8; ++k) t += red[k][lane];
     const int u = perm[j];
@@ -748,6 +756,19 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     const int32_t r = p->h_row[j];
     tinfo[r % TT] |= 1 << (r / TT);  // row r = t + m*TT, m < 8
   }
+  // interleaved positions: i-th cell of thread t at i*TT + t
+  const int64_t Q = (nb + TT - 1) / TT;
+  p->v2_npos = Q * TT;
+  p->h_pos.assign(nb, 0);
+  std::vector<int32_t> perm_il(p->v2_npos, -1);
+  for (int t = 0; t < TT; ++t)
+    for (int64_t j = chunk[t]; j < chunk[t + 1]; ++j) {
+      const int64_t pos = (j - chunk[t]) * TT + t;
+      p->h_pos[j] = pos;
+      perm_il[pos] = p->h_perm[j];
+    }
+  BEM_CUDA_TRY(cudaMalloc(&p->d_perm_il, p->v2_npos * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMemcpy(p->d_perm_il, perm_il.data(), p->v2_npos * sizeof(int32_t), cudaMemcpyHostToDevice));
   {
     // four-step and sparse twiddle tables, FP64 on the host, rounded once
     const int W = TT / 32;
@@ -781,8 +802,8 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   BEM_CUDA_TRY(cudaGetDevice(&dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  p->acc_in_smem = smem_v2<T>(n, TT, nb, R, true) <= (size_t)smem_optin;
-  p->smem_bytes = smem_v2<T>(n, TT, nb, R, p->acc_in_smem);
+  p->acc_in_smem = smem_v2<T>(n, TT, p->v2_npos, R, true) <= (size_t)smem_optin;
+  p->smem_bytes = smem_v2<T>(n, TT, p->v2_npos, R, p->acc_in_smem);
   if (p->smem_bytes > (size_t)smem_optin) {
     set_error("grid too large for the shared-memory column buffers");
     return BEM_ERR_UNSUPPORTED;
@@ -798,9 +819,10 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   }
   p->grid = (int)std::min<int64_t>((int64_t)bps * nsm, n + 1);
   const size_t tb = sizeof(T);
-  BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * nb * tb));
-  BEM_CUDA_TRY(cudaMalloc(&p->d_val, (size_t)nb * 2 * tb));
-  p->scratch_bytes += (size_t)p->grid * nb * tb + (size_t)nb * 2 * tb;
+  const int64_t npos = p->v2_npos;
+  BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * npos * tb));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_val, (size_t)npos * 2 * tb));
+  p->scratch_bytes += (size_t)p->grid * npos * tb + (size_t)npos * 2 * tb;
   return BEM_OK;
 }
 
@@ -816,26 +838,30 @@ bem_status setup_apply_2d(bem_plan_s* p) {
 
 bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& coefA, const std::vector<double>& coefB,
                        const std::vector<uint8_t>& type) {
-  const int64_t nb = p->nb;
-  std::vector<uint32_t> meta(nb);
+  // cell words and coefficients in the interleaved position order (padding:
+  // zero word, zero coefficients)
+  const int64_t nb = p->nb, npos = p->v2_npos;
+  std::vector<uint32_t> meta(npos, 0u);
   for (int64_t j = 0; j < nb; ++j)
-    meta[j] = (uint32_t)p->h_col[j] | ((uint32_t)p->h_row[j] << 12) | ((uint32_t)p->h_cellflag[j] << 29) |
-              ((uint32_t)(type[j] ? 1u : 0u) << 31);
+    meta[p->h_pos[j]] = (uint32_t)p->h_col[j] | ((uint32_t)p->h_row[j] << 12) |
+                        ((uint32_t)p->h_cellflag[j] << 29) | ((uint32_t)(type[j] ? 1u : 0u) << 31);
   void* dm = nullptr;
-  BEM_CUDA_TRY(cudaMalloc(&dm, nb * sizeof(uint32_t)));
-  BEM_CUDA_TRY(cudaMemcpy(dm, meta.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMalloc(&dm, npos * sizeof(uint32_t)));
+  BEM_CUDA_TRY(cudaMemcpy(dm, meta.data(), npos * sizeof(uint32_t), cudaMemcpyHostToDevice));
   op.owned.push_back(dm);
   op.meta = static_cast<const uint32_t*>(dm);
   const size_t tb = prec_bytes(p);
   for (int k = 0; k < 2; ++k) {
-    const std::vector<double>& c = k == 0 ? coefA : coefB;
+    const std::vector<double>& csort = k == 0 ? coefA : coefB;
+    std::vector<double> c(npos, 0.0);
+    for (int64_t j = 0; j < nb; ++j) c[p->h_pos[j]] = csort[j];
     void* d = nullptr;
-    BEM_CUDA_TRY(cudaMalloc(&d, nb * tb));
+    BEM_CUDA_TRY(cudaMalloc(&d, npos * tb));
     if (p->prec == BEM_F64) {
-      BEM_CUDA_TRY(cudaMemcpy(d, c.data(), nb * tb, cudaMemcpyHostToDevice));
+      BEM_CUDA_TRY(cudaMemcpy(d, c.data(), npos * tb, cudaMemcpyHostToDevice));
     } else {
       std::vector<float> f(c.begin(), c.end());
-      BEM_CUDA_TRY(cudaMemcpy(d, f.data(), nb * tb, cudaMemcpyHostToDevice));
+      BEM_CUDA_TRY(cudaMemcpy(d, f.data(), npos * tb, cudaMemcpyHostToDevice));
     }
     op.owned.push_back(d);
     (k == 0 ? op.coefA : op.coefB) = d;
@@ -917,7 +943,8 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
                             bool timed, cudaStream_t st) {
   const int nb = (int)p->nb;
   const int tb = 256;
-  k_prep_v2<T><<<(nb + tb - 1) / tb, tb, 0, st>>>(nb, p->d_perm, static_cast<const T*>(in),
+  const int npos = (int)p->v2_npos;
+  k_prep_v2<T><<<(npos + tb - 1) / tb, tb, 0, st>>>(npos, p->d_perm_il, static_cast<const T*>(in),
                                                   static_cast<const T*>(op.coefA), static_cast<const T*>(op.coefB),
                                                   static_cast<cplx<T>*>(sp.val));
   Col2Dv2Params<T> cp{};
@@ -936,6 +963,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   }
   cp.fstab = static_cast<const cplx<T>*>(p->d_fstab);
   cp.partial = static_cast<T*>(sp.partial);
+  cp.npos = npos;
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
   cp.has_carry = p->v2_carry ? 1 : 0;
   cudaEvent_t e1 = nullptr;
@@ -945,7 +973,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   else if (op.nf == 2) k_col2d_v2<T, 2, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
   else k_col2d_v2<T, 3, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k_reduce_v2<T><<<(nb + 31) / 32, 256, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, nb, p->d_perm,
+  k_reduce_v2<T><<<(npos + 31) / 32, 256, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il,
                                                     static_cast<const T*>(op.diag), static_cast<const T*>(in),
                                                     static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
@@ -958,8 +986,8 @@ size_t apply_scratch_bytes(const bem_plan_s* p, const Operator& op) {
   const size_t tb = prec_bytes(p);
   size_t need = 0;
   if (p->v2) {
-    need += align256((size_t)p->nb * 2 * tb);
-    need += align256((size_t)p->grid * p->nb * tb);
+    need += align256((size_t)p->v2_npos * 2 * tb);
+    need += align256((size_t)p->grid * p->v2_npos * tb);
   } else {
     for (int f = 0; f < op.nf; ++f) need += align256((size_t)op.f[f].set->nelem * tb);
     need += align256((size_t)p->grid * p->all_set.nelem * p->ncomp * tb);
@@ -973,7 +1001,7 @@ void carve_scratch(const bem_plan_s* p, const Operator& op, void* base, ScratchP
   size_t off = 0;
   if (p->v2) {
     sp->val = b + off;
-    off += align256((size_t)p->nb * 2 * tb);
+    off += align256((size_t)p->v2_npos * 2 * tb);
     sp->partial = b + off;
   } else {
     for (int f = 0; f < op.nf; ++f) {

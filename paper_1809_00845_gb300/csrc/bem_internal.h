@@ -135,6 +135,9 @@ struct bem_plan_s {
   bool v2_carry = false;              // some grid row is split between threads
   std::vector<uint32_t> h_cellflag;   // sorted order: 1 = last cell of its row in the chunk, 2 = carried
   int32_t* d_tinfo = nullptr;   // threads: row mask | continuing threads << 8
+  int64_t v2_npos = 0;          // interleaved cell positions (cells rounded up to a multiple of threads)
+  std::vector<int64_t> h_pos;   // sorted cell -> interleaved position
+  int32_t* d_perm_il = nullptr; // interleaved position -> caller index (-1: padding)
   int32_t* d_chunk = nullptr;   // threads + 1
   void* d_val = nullptr;        // nb density pairs (scratch)
   void* d_fstab = nullptr;      // twiddle tables of the four-step kernel

@@ -621,6 +621,7 @@ bem_status bem_destroy(bem_plan_t p) {
   free_operator(p->op_system);
   free_slot_set(&p->all_set);
   cudaFree(p->d_tinfo);
+  cudaFree(p->d_perm_il);
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
   cudaFree(p->d_fstab);
