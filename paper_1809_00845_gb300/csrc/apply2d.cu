@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "bem_internal.h"
+#include "col2d_v2.h"
 #include "fft4step.cuh"
 #include "fft_reg.cuh"
 
@@ -187,305 +188,6 @@ __global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem,
   out[u] = (T)s;
 }
 
-
-// ------------------------------------------------- four-step column kernel
-//
-// For N >= 512.  Thread t owns the contiguous range of sorted cells
-// [chunk[t], chunk[t+1]) (equal cell counts, fixed at plan time; a grid row
-// may be split between neighbouring threads).  Per-cell arrays (cell words,
-// density pairs, accumulators) are stored interleaved: the i-th cell of
-// thread t sits at position i*TT + t, so every warp-wide access of the cell
-// loops is one contiguous segment.  Per column kx:
-//   1. the thread walks its cells (loads and twiddles batched 8 at a time) and
-//      forms the input-pruned x-DFT of every field row by row.  A row sum is
-//      stored when the row's last cell in the chunk is reached (flag in the
-//      cell word): into shared memory (field 0 into the transform buffer,
-//      fields 1.. into staging rows), or, for the first row of a chunk that
-//      began in an earlier chunk, into the thread's carry slot.  Empty rows
-//      are never written: the transform input masks them (a per-thread bit
-//      mask of its eight rows).  After a barrier, the thread holding the
-//      first cell of a split row adds the carries of the following threads
-//      in thread order (deterministic);
-//   2. each field is loaded into the four-step engine's register map
-//      (rows t + m*TT), transformed, multiplied by the spectrum column (copied
-//      to shared memory asynchronously during the transform) and accumulated;
-//   3. the inverse transform leaves rows t + m*TT in registers, they are
-//      written to shared memory and every thread gathers its own cells
-//      (output-pruned inverse x-DFT) into its accumulators.
-//
-// Cell word (plan time): x | row << 12 | FLUSH << 29 | CARRY << 30 | type << 31.
-constexpr uint32_t kMetaFlush = 1u << 29;
-constexpr uint32_t kMetaCarry = 1u << 30;
-__device__ __forceinline__ int meta_x(uint32_t m) { return (int)(m & 0xfffu); }
-__device__ __forceinline__ int meta_row(uint32_t m) { return (int)((m >> 12) & 0xfffu); }
-
-template <typename T>
-struct Col2Dv2Params {
-  int n, log2N, nb;
-  const int32_t* chunk;   // TT + 1
-  const int32_t* tinfo;   // TT: row mask (8 bits) | continuing threads << 8
-  const uint32_t* meta;   // Q*TT cell words, interleaved
-  const cplx<T>* val;     // Q*TT density pairs, interleaved
-  const T* spec[3];
-  int imag[3];
-  int oddy[3];
-  const cplx<T>* fstab;  // four-step tables (lane, warp, t5) then sparse tables (hi, lo)
-  T* partial;            // gridDim.x * npos, interleaved positions
-  int npos;              // Q*TT
-  int acc_in_smem;
-  int has_carry;         // some row is split between threads
-};
-
-// number of table entries of the four-step kernel for TT threads, N = 16 TT
-__host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 16 + 512 + TT / 4 + 64; }
-// spectrum column in shared memory, padded by one entry every 16
-__host__ __device__ inline int sspec_entries(int n) { return ((n + 1 + (n + 1) / 16) + 3) & ~3; }
-__device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
-
-// Walk cells [c0, c1) and store the x-DFT row sums of the selected fields:
-// FSEL < 0 = all NF fields (field 0 -> out0[row], field f > 0 ->
-// outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.  Carried sums go
-// to carry[f*TT + t] (f = 0 for FSEL >= 0).
-template <typename T, int NF, int FSEL>
-__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, int kx, int cnt, cplx<T>* out0,
-                                            cplx<T>* outF, cplx<T>* carry, const Twiddles2L<T>& tw) {
-  const int Nm = (1 << p.log2N) - 1;
-  const int t = threadIdx.x, TT = blockDim.x;
-  cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
-  for (int i0 = 0; i0 < cnt; i0 += 8) {
-    uint32_t mt[8];
-    cplx<T> vv[8], w[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
-      mt[i] = __ldg(p.meta + pos);
-      vv[i] = p.val[pos];
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i0 + i < cnt) {
-        const bool ty = (mt[i] >> 31) != 0;
-        const T a = vv[i].x, b = vv[i].y;
-        const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
-        if (FSEL < 0 || FSEL == 0) {
-          s0.x += ca * w[i].x;
-          s0.y += ca * w[i].y;
-        }
-        if ((FSEL < 0 && NF > 1) || FSEL == 1) {
-          s1.x += cb * w[i].x;
-          s1.y += cb * w[i].y;
-        }
-        if ((FSEL < 0 && NF > 2) || FSEL == 2) {
-          s2.x += cc * w[i].x;
-          s2.y += cc * w[i].y;
-        }
-        if (mt[i] & kMetaFlush) {
-          const int row = meta_row(mt[i]);
-          const bool car = (mt[i] & kMetaCarry) != 0;
-          if (FSEL < 0) {
-            (car ? carry + t : out0 + row)[0] = s0;
-            if (NF > 1) (car ? carry + TT + t : outF + row)[0] = s1;
-            if (NF > 2) (car ? carry + 2 * TT + t : outF + p.n + row)[0] = s2;
-          } else {
-            (car ? carry + t : out0 + row)[0] = FSEL == 0 ? s0 : (FSEL == 1 ? s1 : s2);
-          }
-          s0 = s1 = s2 = {T(0), T(0)};
-        }
-      }
-    }
-  }
-}
-
-// After a barrier: the thread holding the first cell of a split row (its
-// last row) adds the carries of the `ncont` following threads, in order.
-template <typename T, int NF, int FSEL>
-__device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, int cnt, int ncont, cplx<T>* out0,
-                                            cplx<T>* outF, const cplx<T>* carry) {
-  if (ncont == 0) return;
-  const int t = threadIdx.x, TT = blockDim.x;
-  const int row = meta_row(__ldg(p.meta + (cnt - 1) * TT + t));
-  constexpr int nfs = FSEL < 0 ? NF : 1;
-#pragma unroll
-  for (int f = 0; f < nfs; ++f) {
-    cplx<T>* dst = f == 0 ? out0 + row : outF + (size_t)(f - 1) * p.n + row;
-    cplx<T> s = *dst;
-    for (int i = 1; i <= ncont; ++i) s = s + carry[f * TT + t + i];
-    *dst = s;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, int kx, int cnt, const cplx<T>* rows,
-                                             const Twiddles2L<T>& tw, T* acc) {
-  const int Nm = (1 << p.log2N) - 1;
-  const int t = threadIdx.x, TT = blockDim.x;
-  const T ckx = (kx == 0 || kx == p.n) ? T(1) : T(2);
-  for (int i0 = 0; i0 < cnt; i0 += 8) {
-    uint32_t mt[8];
-    cplx<T> Y[8], w[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      Y[i] = rows[meta_row(mt[i])];
-      w[i] = tw.template get<+1>((kx * meta_x(mt[i])) & Nm);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (i0 + i < cnt) acc[(i0 + i) * TT + t] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
-  }
-}
-
-// field-indexed parameters without dynamic indexing of the parameter arrays
-template <typename T>
-__device__ __forceinline__ const T* spec_of(const Col2Dv2Params<T>& p, int f) {
-  return f == 0 ? p.spec[0] : (f == 1 ? p.spec[1] : p.spec[2]);
-}
-template <typename T>
-__device__ __forceinline__ int imag_of(const Col2Dv2Params<T>& p, int f) {
-  return f == 0 ? p.imag[0] : (f == 1 ? p.imag[1] : p.imag[2]);
-}
-template <typename T>
-__device__ __forceinline__ int oddy_of(const Col2Dv2Params<T>& p, int f) {
-  return f == 0 ? p.oddy[0] : (f == 1 ? p.oddy[1] : p.oddy[2]);
-}
-
-template <typename T>
-__device__ __forceinline__ void load_spectrum(const Col2Dv2Params<T>& p, int f, int kx, T* sS) {
-  // asynchronous global -> shared copies (no register staging): issued before
-  // the forward transform, waited for (spectrum_ready) just before the
-  // multiply, so the HBM latency hides behind the transform
-  const T* S = spec_of(p, f) + (size_t)kx * (p.n + 1);
-  for (int i = threadIdx.x; i <= p.n; i += blockDim.x) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(sS + swz16(i));
-    if constexpr (sizeof(T) == 4)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(S + i) : "memory");
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(S + i) : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void spectrum_ready() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-}
-
-template <typename T>
-__device__ __forceinline__ cplx<T> spectral_term(const Col2Dv2Params<T>& p, bool im, bool oy, const T* sS, int K,
-                                                 cplx<T> v) {
-  const int N = 1 << p.log2N;
-  const bool hi = K > p.n;
-  T sv = sS[swz16(hi ? N - K : K)];
-  if (hi && oy) sv = -sv;
-  return im ? cplx<T>{-v.y * sv, v.x * sv} : cplx<T>{v.x * sv, v.y * sv};
-}
-
-template <typename T, int NF, bool ACCREG>
-__global__ void __launch_bounds__(512) k_col2d_v2(const Col2Dv2Params<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int t = threadIdx.x, TT = blockDim.x, W = TT >> 5;
-  const int log2N = p.log2N, N = 1 << log2N, n = p.n;
-  const int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
-  const int ntab = fstab_entries(TT);
-  cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* stab = sA + nbuf;
-  T* sS = reinterpret_cast<T*>(stab + ntab);
-  // carries of split rows (3 * TT entries) share the spectrum buffer: both
-  // are dead between the last multiply of a column and the first spectrum
-  // copy of the next one
-  cplx<T>* carry = reinterpret_cast<cplx<T>*>(sS);
-  cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
-  T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
-                         : p.partial + (size_t)blockIdx.x * p.npos;
-  for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
-  // per-thread plan data is re-read (L1) where used rather than held in
-  // registers across the transforms
-#define C0 __ldg(p.chunk + t)
-#define CNT (__ldg(p.chunk + t + 1) - __ldg(p.chunk + t))
-#define TINFO __ldg(p.tinfo + t)
-  for (int i = 0; i < CNT; ++i) acc[i * TT + t] = T(0);
-  __syncthreads();
-  const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
-  const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + (N >> 6)};
-  FourStep<T> fs;
-  fs.init(t, TT, sA, ftab);
-  auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
-    const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[t + m * TT] : cplx<T>{T(0), T(0)};
-#pragma unroll
-    for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
-  };
-
-  for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
-    __syncthreads();  // the previous column's gather has finished reading sA
-    if constexpr (ACCREG) {
-      sparse_rows<T, NF, -1>(p, kx, CNT, sA, sF, carry, tw);
-      __syncthreads();
-      if (p.has_carry) {
-        add_carries<T, NF, -1>(p, CNT, TINFO >> 8, sA, sF, carry);
-        __syncthreads();
-      }
-      cplx<T> y[16];
-#pragma unroll 1
-      for (int f = 0; f < NF; ++f) {
-        cplx<T> v[16];
-        load_rows(f == 0 ? sA : sF + (size_t)(f - 1) * n, v);
-        __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
-        load_spectrum(p, f, kx, sS);
-        fs.template forward<true>(v);
-        spectrum_ready();
-        const bool im = imag_of(p, f) != 0, oy = oddy_of(p, f) != 0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const cplx<T> term = spectral_term(p, im, oy, sS, fs.freq(k), v[k]);
-          y[k] = f == 0 ? term : y[k] + term;
-        }
-      }
-      fs.inverse(y);
-#pragma unroll
-      for (int m = 0; m < 8; ++m) sA[t + m * TT] = y[m];
-      __syncthreads();
-      gather_cells(p, kx, CNT, sA, tw, acc);
-    } else {
-#pragma unroll 1
-      for (int f = 0; f < NF; ++f) {
-        if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
-        if (NF == 1) sparse_rows<T, NF, -1>(p, kx, CNT, sA, sF, carry, tw);
-        else if (f == 0) sparse_rows<T, NF, 0>(p, kx, CNT, sA, sF, carry, tw);
-        else if (f == 1) sparse_rows<T, NF, 1>(p, kx, CNT, sA, sF, carry, tw);
-        else sparse_rows<T, NF, 2>(p, kx, CNT, sA, sF, carry, tw);
-        __syncthreads();
-        if (p.has_carry) {
-          add_carries<T, NF, 0>(p, CNT, TINFO >> 8, sA, sF, carry);
-          __syncthreads();
-        }
-        cplx<T> v[16];
-        load_rows(sA, v);
-        __syncthreads();
-        load_spectrum(p, f, kx, sS);
-        fs.template forward<true>(v);
-        spectrum_ready();
-        const bool im = imag_of(p, f) != 0, oy = oddy_of(p, f) != 0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = spectral_term(p, im, oy, sS, fs.freq(k), v[k]);
-        fs.inverse(v);
-#pragma unroll
-        for (int m = 0; m < 8; ++m) sA[t + m * TT] = v[m];
-        __syncthreads();
-        gather_cells(p, kx, CNT, sA, tw, acc);
-      }
-    }
-  }
-  if (p.acc_in_smem)
-    for (int i = 0; i < CNT; ++i) p.partial[(size_t)blockIdx.x * p.npos + i * TT + t] = acc[i * TT + t];
-#undef C0
-#undef CNT
-#undef TINFO
-}
 
 // val[pos] = (coefA[pos], coefB[pos]) * in[perm[pos]] (interleaved positions;
 // padding positions have perm < 0 and get zero)
@@ -709,12 +411,37 @@ static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc) {
   return s;
 }
 
-template <typename T, int NF, bool ACCREG>
-static cudaError_t configure_v2_one(size_t smem, int threads, int* bps) {
-  auto kern = k_col2d_v2<T, NF, ACCREG>;
-  cudaError_t e = allow_optin_smem(kern);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, threads, smem);
+// the column kernels for TT threads: compile-time thread counts for FP32,
+// the generic kernel for FP64
+template <typename T>
+static cudaError_t configure_col2d(int TT, size_t smem, int* bps) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (TT) {
+      case 512: return Col2DKernels<float, 512>::configure(smem, TT, bps);
+      case 256: return Col2DKernels<float, 256>::configure(smem, TT, bps);
+      case 128: return Col2DKernels<float, 128>::configure(smem, TT, bps);
+      case 64: return Col2DKernels<float, 64>::configure(smem, TT, bps);
+      default: return Col2DKernels<float, 32>::configure(smem, TT, bps);
+    }
+  } else {
+    return Col2DKernels<double, 0>::configure(smem, TT, bps);
+  }
+}
+
+template <typename T>
+static void launch_col2d(const bem_plan_s* p, int nf, const Col2Dv2Params<T>& cp, cudaStream_t st) {
+  const int TT = p->threads;
+  if constexpr (std::is_same<T, float>::value) {
+    switch (TT) {
+      case 512: Col2DKernels<float, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 256: Col2DKernels<float, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 128: Col2DKernels<float, 128>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 64: Col2DKernels<float, 64>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      default: Col2DKernels<float, 32>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+    }
+  } else {
+    Col2DKernels<double, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp);
+  }
 }
 
 template <typename T>
@@ -808,11 +535,8 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     set_error("grid too large for the shared-memory column buffers");
     return BEM_ERR_UNSUPPORTED;
   }
-  int b1 = 0, b2 = 0, b3 = 0;
-  BEM_CUDA_TRY((configure_v2_one<T, 1, false>(p->smem_bytes, TT, &b1)));
-  BEM_CUDA_TRY((configure_v2_one<T, 2, R>(p->smem_bytes, TT, &b2)));
-  BEM_CUDA_TRY((configure_v2_one<T, 3, R>(p->smem_bytes, TT, &b3)));
-  const int bps = std::min(b1, std::min(b2, b3));
+  int bps = 0;
+  BEM_CUDA_TRY(configure_col2d<T>(TT, p->smem_bytes, &bps));
   if (bps < 1) {
     set_error("column kernel cannot be resident (registers/shared memory)");
     return BEM_ERR_UNSUPPORTED;
@@ -968,10 +692,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.has_carry = p->v2_carry ? 1 : 0;
   cudaEvent_t e1 = nullptr;
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
-  constexpr bool R = std::is_same<T, float>::value;
-  if (op.nf == 1) k_col2d_v2<T, 1, false><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
-  else if (op.nf == 2) k_col2d_v2<T, 2, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
-  else k_col2d_v2<T, 3, R><<<p->grid, p->threads, p->smem_bytes, st>>>(cp);
+  launch_col2d<T>(p, op.nf, cp, st);
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
   k_reduce_v2<T><<<(npos + 31) / 32, 256, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il,
                                                     static_cast<const T*>(op.diag), static_cast<const T*>(in),

@@ -1,0 +1,7 @@
+// Column kernels, FP32, N = 8192 and 4096 (TT = 512, 256 threads).
+#include "col2d_v2.cuh"
+
+namespace bemfft {
+template struct Col2DKernels<float, 512>;
+template struct Col2DKernels<float, 256>;
+}  // namespace bemfft

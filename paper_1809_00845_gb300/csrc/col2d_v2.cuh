@@ -1,0 +1,380 @@
+// Four-step column kernel of the 2D apply (Section 3-4, Eq. 15-16).
+//
+// For N >= 512.  Thread t owns the contiguous range of sorted cells
+// [chunk[t], chunk[t+1]) (equal cell counts, fixed at plan time; a grid row
+// may be split between neighbouring threads).  Per-cell arrays (cell words,
+// density pairs, accumulators) are stored interleaved: the i-th cell of
+// thread t sits at position i*TT + t, so every warp-wide access of the cell
+// loops is one contiguous segment.  Per column kx:
+//   1. the thread walks its cells (loads and twiddles batched 8 at a time) and
+//      forms the input-pruned x-DFT of every field row by row.  A row sum is
+//      stored when the row's last cell in the chunk is reached (flag in the
+//      cell word): into shared memory (field 0 into the transform buffer,
+//      fields 1.. into staging rows), or, for the first row of a chunk that
+//      began in an earlier chunk, into the thread's carry slot.  Empty rows
+//      are never written: the transform input masks them (a per-thread bit
+//      mask of its eight rows).  After a barrier, the thread holding the
+//      first cell of a split row adds the carries of the following threads
+//      in thread order (deterministic);
+//   2. each field is loaded into the four-step engine's register map
+//      (rows t + m*TT), transformed, multiplied by the spectrum column (copied
+//      to shared memory asynchronously during the transform) and accumulated;
+//   3. the inverse transform leaves rows t + m*TT in registers, they are
+//      written to shared memory and every thread gathers its own cells
+//      (output-pruned inverse x-DFT) into its accumulators.
+//
+// Included only by the translation units that instantiate Col2DKernels.
+#pragma once
+
+#include "col2d_v2.h"
+#include "fft4step.cuh"
+
+namespace bemfft {
+
+__device__ __forceinline__ int meta_x(uint32_t m) { return (int)(m & 0xfffu); }
+__device__ __forceinline__ int meta_row(uint32_t m) { return (int)((m >> 12) & 0xfffu); }
+__device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
+
+constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
+
+// Sizes of one launch: compile-time when TTC > 0, else from the launch and
+// the parameters.
+template <int TTC>
+struct ColDims {
+  int TT, log2N, N, n;
+  template <typename T>
+  __device__ __forceinline__ explicit ColDims(const Col2Dv2Params<T>& p) {
+    if constexpr (TTC > 0) {
+      TT = TTC;
+      log2N = 4 + clog2(TTC);
+      N = 16 * TTC;
+      n = 8 * TTC;
+    } else {
+      TT = (int)blockDim.x;
+      log2N = p.log2N;
+      N = 1 << p.log2N;
+      n = p.n;
+    }
+  }
+};
+
+// Walk the thread's cnt cells and store the x-DFT row sums of the selected
+// fields: FSEL < 0 = all NF fields (field 0 -> out0[row], field f > 0 ->
+// outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.  Carried sums go
+// to carry[f*TT + t] (f = 0 for FSEL >= 0).
+template <typename T, int NF, int FSEL, int TTC>
+__device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
+                                            cplx<T>* out0, cplx<T>* outF, cplx<T>* carry,
+                                            const Twiddles2L<T>& tw) {
+  const int Nm = g.N - 1;
+  const int t = threadIdx.x, TT = g.TT;
+  cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
+  for (int i0 = 0; i0 < cnt; i0 += 8) {
+    uint32_t mt[8];
+    cplx<T> vv[8], w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
+      mt[i] = __ldg(p.meta + pos);
+      vv[i] = p.val[pos];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i0 + i < cnt) {
+        const bool ty = (mt[i] >> 31) != 0;
+        const T a = vv[i].x, b = vv[i].y;
+        const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
+        if (FSEL < 0 || FSEL == 0) {
+          s0.x += ca * w[i].x;
+          s0.y += ca * w[i].y;
+        }
+        if ((FSEL < 0 && NF > 1) || FSEL == 1) {
+          s1.x += cb * w[i].x;
+          s1.y += cb * w[i].y;
+        }
+        if ((FSEL < 0 && NF > 2) || FSEL == 2) {
+          s2.x += cc * w[i].x;
+          s2.y += cc * w[i].y;
+        }
+        if (mt[i] & kMetaFlush) {
+          const int row = meta_row(mt[i]);
+          const bool car = (mt[i] & kMetaCarry) != 0;
+          if (FSEL < 0) {
+            (car ? carry + t : out0 + row)[0] = s0;
+            if (NF > 1) (car ? carry + TT + t : outF + row)[0] = s1;
+            if (NF > 2) (car ? carry + 2 * TT + t : outF + g.n + row)[0] = s2;
+          } else {
+            (car ? carry + t : out0 + row)[0] = FSEL == 0 ? s0 : (FSEL == 1 ? s1 : s2);
+          }
+          s0 = s1 = s2 = {T(0), T(0)};
+        }
+      }
+    }
+  }
+}
+
+// After a barrier: the thread holding the first cell of a split row (its
+// last row) adds the carries of the `ncont` following threads, in order.
+template <typename T, int NF, int FSEL, int TTC>
+__device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int cnt, int ncont,
+                                            cplx<T>* out0, cplx<T>* outF, const cplx<T>* carry) {
+  if (ncont == 0) return;
+  const int t = threadIdx.x, TT = g.TT;
+  const int row = meta_row(__ldg(p.meta + (cnt - 1) * TT + t));
+  constexpr int nfs = FSEL < 0 ? NF : 1;
+#pragma unroll
+  for (int f = 0; f < nfs; ++f) {
+    cplx<T>* dst = f == 0 ? out0 + row : outF + (size_t)(f - 1) * g.n + row;
+    cplx<T> s = *dst;
+    for (int i = 1; i <= ncont; ++i) s = s + carry[f * TT + t + i];
+    *dst = s;
+  }
+}
+
+template <typename T, int TTC>
+__device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
+                                             const cplx<T>* rows, const Twiddles2L<T>& tw, T* acc) {
+  const int Nm = g.N - 1;
+  const int t = threadIdx.x, TT = g.TT;
+  const T ckx = (kx == 0 || kx == g.n) ? T(1) : T(2);
+  for (int i0 = 0; i0 < cnt; i0 += 8) {
+    uint32_t mt[8];
+    cplx<T> Y[8], w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      Y[i] = rows[meta_row(mt[i])];
+      w[i] = tw.template get<+1>((kx * meta_x(mt[i])) & Nm);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i0 + i < cnt) acc[(i0 + i) * TT + t] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
+  }
+}
+
+// field-indexed parameters without dynamic indexing of the parameter arrays
+template <typename T>
+__device__ __forceinline__ const T* spec_of(const Col2Dv2Params<T>& p, int f) {
+  return f == 0 ? p.spec[0] : (f == 1 ? p.spec[1] : p.spec[2]);
+}
+template <typename T>
+__device__ __forceinline__ int imag_of(const Col2Dv2Params<T>& p, int f) {
+  return f == 0 ? p.imag[0] : (f == 1 ? p.imag[1] : p.imag[2]);
+}
+template <typename T>
+__device__ __forceinline__ int oddy_of(const Col2Dv2Params<T>& p, int f) {
+  return f == 0 ? p.oddy[0] : (f == 1 ? p.oddy[1] : p.oddy[2]);
+}
+
+template <typename T, int TTC>
+__device__ __forceinline__ void load_spectrum(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int f, int kx,
+                                              T* sS) {
+  // asynchronous global -> shared copies (no register staging): issued before
+  // the forward transform, waited for (spectrum_ready) just before the
+  // multiply, so the HBM latency hides behind the transform
+  const T* S = spec_of(p, f) + (size_t)kx * (g.n + 1);
+  for (int i = threadIdx.x; i <= g.n; i += g.TT) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sS + swz16(i));
+    if constexpr (sizeof(T) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(S + i) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(S + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void spectrum_ready() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+}
+
+// Where a thread reads the spectrum column.  After the forward transform
+// register k holds frequency K_k = K0 + S k (S = 16 J).  Lanes with h = 0 have
+// every K_k < n and read index K_k; lanes with h = 1 have every K_k >= n and
+// read the mirrored index N - K_k.  With S a multiple of 16 the padded
+// (swizzled) index is base + k * step for both, so the 16 reads are one base
+// register plus constant offsets.  The mirror flips the sign of kernels odd
+// in y, except on the line K = n itself (K_0 of one thread), which is its
+// own mirror.
+struct SpecAddr {
+  int base, step;
+  bool mirror, nyq;
+};
+
+template <typename T, int TTC>
+__device__ __forceinline__ SpecAddr spec_addr(const FourStep<T>& fs, const ColDims<TTC>& g) {
+  const int K0 = fs.freq0();
+  const int S = 16 * fs.J;
+  SpecAddr a;
+  a.mirror = K0 >= g.n;
+  a.nyq = K0 == g.n;
+  a.base = a.mirror ? swz16(g.N - K0) : swz16(K0);
+  a.step = a.mirror ? -(S + S / 16) : (S + S / 16);
+  return a;
+}
+
+// y[k] (+)= i^im * sign * S(K_k) * v[k]
+template <typename T, bool ACC>
+__device__ __forceinline__ void spectral_multiply(const T* sS, const SpecAddr& a, bool im, bool oy,
+                                                  const cplx<T> (&v)[16], cplx<T> (&y)[16]) {
+  const T sg = (a.mirror && oy) ? T(-1) : T(1);
+  const T sg0 = a.nyq ? T(1) : sg;
+  const T* s = sS + a.base;
+  if (im) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const T sv = s[k * a.step] * (k == 0 ? sg0 : sg);
+      const cplx<T> term = {-v[k].y * sv, v[k].x * sv};
+      y[k] = ACC ? y[k] + term : term;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const T sv = s[k * a.step] * (k == 0 ? sg0 : sg);
+      const cplx<T> term = {v[k].x * sv, v[k].y * sv};
+      y[k] = ACC ? y[k] + term : term;
+    }
+  }
+}
+
+template <int TTC>
+struct ColBounds {
+  static constexpr int threads = TTC > 0 ? TTC : 512;
+  static constexpr int blocks = TTC >= 64 ? 512 / TTC : (TTC > 0 ? 16 : 1);
+};
+
+template <typename T, int NF, bool ACCREG, int TTC>
+__global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::blocks)
+    k_col2d_v2(const Col2Dv2Params<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ColDims<TTC> g(p);
+  const int t = threadIdx.x, TT = g.TT, W = TT >> 5;
+  const int N = g.N, n = g.n;
+  const int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
+  const int ntab = fstab_entries(TT);
+  cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* stab = sA + nbuf;
+  T* sS = reinterpret_cast<T*>(stab + ntab);
+  // carries of split rows (3 * TT entries) share the spectrum buffer: both
+  // are dead between the last multiply of a column and the first spectrum
+  // copy of the next one
+  cplx<T>* carry = reinterpret_cast<cplx<T>*>(sS);
+  cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
+  T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
+                         : p.partial + (size_t)blockIdx.x * p.npos;
+  for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
+  // per-thread plan data is re-read (L1) where used rather than held in
+  // registers across the transforms
+#define C0 __ldg(p.chunk + t)
+#define CNT (__ldg(p.chunk + t + 1) - __ldg(p.chunk + t))
+#define TINFO __ldg(p.tinfo + t)
+  for (int i = 0; i < CNT; ++i) acc[i * TT + t] = T(0);
+  __syncthreads();
+  const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
+  const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + (N >> 6)};
+  FourStep<T> fs;
+  fs.init(t, TT, sA, ftab);
+  auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
+    const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[t + m * TT] : cplx<T>{T(0), T(0)};
+#pragma unroll
+    for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+  };
+
+  for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
+    __syncthreads();  // the previous column's gather has finished reading sA
+    if constexpr (ACCREG) {
+      sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw);
+      __syncthreads();
+      if (p.has_carry) {
+        add_carries<T, NF, -1>(p, g, CNT, TINFO >> 8, sA, sF, carry);
+        __syncthreads();
+      }
+      cplx<T> y[16];
+#pragma unroll 1
+      for (int f = 0; f < NF; ++f) {
+        cplx<T> v[16];
+        load_rows(f == 0 ? sA : sF + (size_t)(f - 1) * n, v);
+        __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
+        load_spectrum(p, g, f, kx, sS);
+        fs.template forward<true>(v);
+        spectrum_ready();
+        const SpecAddr sa = spec_addr(fs, g);
+        if (f == 0) spectral_multiply<T, false>(sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
+        else spectral_multiply<T, true>(sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
+      }
+      fs.inverse(y);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) sA[t + m * TT] = y[m];
+      __syncthreads();
+      gather_cells(p, g, kx, CNT, sA, tw, acc);
+    } else {
+#pragma unroll 1
+      for (int f = 0; f < NF; ++f) {
+        if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
+        if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw);
+        else if (f == 0) sparse_rows<T, NF, 0>(p, g, kx, CNT, sA, sF, carry, tw);
+        else if (f == 1) sparse_rows<T, NF, 1>(p, g, kx, CNT, sA, sF, carry, tw);
+        else sparse_rows<T, NF, 2>(p, g, kx, CNT, sA, sF, carry, tw);
+        __syncthreads();
+        if (p.has_carry) {
+          add_carries<T, NF, 0>(p, g, CNT, TINFO >> 8, sA, sF, carry);
+          __syncthreads();
+        }
+        cplx<T> v[16];
+        load_rows(sA, v);
+        __syncthreads();
+        load_spectrum(p, g, f, kx, sS);
+        fs.template forward<true>(v);
+        spectrum_ready();
+        spectral_multiply<T, false>(sS, spec_addr(fs, g), imag_of(p, f) != 0, oddy_of(p, f) != 0, v, v);
+        fs.inverse(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sA[t + m * TT] = v[m];
+        __syncthreads();
+        gather_cells(p, g, kx, CNT, sA, tw, acc);
+      }
+    }
+  }
+  if (p.acc_in_smem)
+    for (int i = 0; i < CNT; ++i) p.partial[(size_t)blockIdx.x * p.npos + i * TT + t] = acc[i * TT + t];
+#undef C0
+#undef CNT
+#undef TINFO
+}
+
+template <typename T, int TTC>
+cudaError_t Col2DKernels<T, TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
+  constexpr bool R = std::is_same<T, float>::value;
+  int b[3] = {0, 0, 0};
+  cudaError_t e;
+  if ((e = allow_optin_smem(k_col2d_v2<T, 1, false, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_v2<T, 2, R, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_v2<T, 3, R, TTC>)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_v2<T, 1, false, TTC>, threads, smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_v2<T, 2, R, TTC>, threads, smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_v2<T, 3, R, TTC>, threads, smem)) !=
+      cudaSuccess)
+    return e;
+  *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));
+  return cudaSuccess;
+}
+
+template <typename T, int TTC>
+void Col2DKernels<T, TTC>::launch(int nf, int grid, int threads, size_t smem, cudaStream_t st,
+                                  const Col2Dv2Params<T>& cp) {
+  constexpr bool R = std::is_same<T, float>::value;
+  if (nf == 1) k_col2d_v2<T, 1, false, TTC><<<grid, threads, smem, st>>>(cp);
+  else if (nf == 2) k_col2d_v2<T, 2, R, TTC><<<grid, threads, smem, st>>>(cp);
+  else k_col2d_v2<T, 3, R, TTC><<<grid, threads, smem, st>>>(cp);
+}
+
+}  // namespace bemfft

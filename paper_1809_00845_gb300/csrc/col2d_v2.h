@@ -1,0 +1,52 @@
+// Four-step column kernel of the 2D apply (N >= 512): kernel parameters and
+// the launch interface.  The kernel itself lives in col2d_v2.cuh and is
+// instantiated in separate translation units, one per precision and thread
+// count (the thread count TT = N / 16 is a compile-time constant there, so
+// every index of the transform, of the interleaved cell arrays and of the
+// spectrum column folds into immediate offsets).
+#pragma once
+
+#include <cstdint>
+
+#include "bem_internal.h"
+#include "fft_reg.cuh"
+
+namespace bemfft {
+
+// Cell word (plan time): x | row << 12 | FLUSH << 29 | CARRY << 30 | type << 31.
+constexpr uint32_t kMetaFlush = 1u << 29;
+constexpr uint32_t kMetaCarry = 1u << 30;
+
+template <typename T>
+struct Col2Dv2Params {
+  int n, log2N, nb;
+  const int32_t* chunk;   // TT + 1
+  const int32_t* tinfo;   // TT: row mask (8 bits) | continuing threads << 8
+  const uint32_t* meta;   // Q*TT cell words, interleaved
+  const cplx<T>* val;     // Q*TT density pairs, interleaved
+  const T* spec[3];
+  int imag[3];
+  int oddy[3];
+  const cplx<T>* fstab;  // four-step tables (lane, warp, t5) then sparse tables (hi, lo)
+  T* partial;            // gridDim.x * npos, interleaved positions
+  int npos;              // Q*TT
+  int acc_in_smem;
+  int has_carry;         // some row is split between threads
+};
+
+// number of table entries of the four-step kernel for TT threads, N = 16 TT
+__host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 16 + 512 + TT / 4 + 64; }
+// spectrum column in shared memory, padded by one entry every 16
+__host__ __device__ inline int sspec_entries(int n) { return ((n + 1 + (n + 1) / 16) + 3) & ~3; }
+
+// Column kernels of one precision T for TTC threads per CTA (TTC = 0: any
+// thread count, read from the launch).  configure() lifts the shared-memory
+// limit of the NF = 1, 2, 3 kernels and returns the smallest number of
+// resident CTAs per SM among them; launch() runs the kernel for nf fields.
+template <typename T, int TTC>
+struct Col2DKernels {
+  static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
+  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
+};
+
+}  // namespace bemfft
