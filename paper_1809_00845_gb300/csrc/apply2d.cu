@@ -512,8 +512,8 @@ static bem_status setup_v2_t(bem_plan_s* p) {
       for (int k = 0; k < 16; ++k) push((double)(32 * a * k % N), (double)N);         // warp
     for (int k = 0; k < 16; ++k)
       for (int l = 0; l < 32; ++l) push((double)((l * k) % TT), (double)TT);           // t5
-    for (int64_t i = 0; i < N / 64; ++i) push((double)(64 * i), (double)N);           // hi
-    for (int i = 0; i < 64; ++i) push((double)i, (double)N);                          // lo
+    for (int i = 0; i < 128; ++i) push((double)i, 128.0);                             // hi
+    for (int64_t i = 0; i < N / 128; ++i) push((double)i, (double)N);                 // lo
     if ((int)tab.size() != fstab_entries(TT)) {
       set_error("internal: twiddle table size");
       return BEM_ERR_CUDA;
@@ -567,7 +567,7 @@ bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& c
   const int64_t nb = p->nb, npos = p->v2_npos;
   std::vector<uint32_t> meta(npos, 0u);
   for (int64_t j = 0; j < nb; ++j)
-    meta[p->h_pos[j]] = (uint32_t)p->h_col[j] | ((uint32_t)p->h_row[j] << 12) |
+    meta[p->h_pos[j]] = (uint32_t)p->h_col[j] | ((uint32_t)rowslot(p->h_row[j]) << 12) |
                         ((uint32_t)p->h_cellflag[j] << 29) | ((uint32_t)(type[j] ? 1u : 0u) << 31);
   void* dm = nullptr;
   BEM_CUDA_TRY(cudaMalloc(&dm, npos * sizeof(uint32_t)));

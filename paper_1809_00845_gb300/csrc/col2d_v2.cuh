@@ -9,7 +9,8 @@
 //   1. the thread walks its cells (loads and twiddles batched 8 at a time) and
 //      forms the input-pruned x-DFT of every field row by row.  A row sum is
 //      stored when the row's last cell in the chunk is reached (flag in the
-//      cell word): into shared memory (field 0 into the transform buffer,
+//      cell word): into shared memory at the row's slot (rowslot), field 0
+//      into the transform buffer,
 //      fields 1.. into staging rows), or, for the first row of a chunk that
 //      began in an earlier chunk, into the thread's carry slot.  Empty rows
 //      are never written: the transform input masks them (a per-thread bit
@@ -32,7 +33,7 @@
 namespace bemfft {
 
 __device__ __forceinline__ int meta_x(uint32_t m) { return (int)(m & 0xfffu); }
-__device__ __forceinline__ int meta_row(uint32_t m) { return (int)((m >> 12) & 0xfffu); }
+__device__ __forceinline__ int meta_slot(uint32_t m) { return (int)((m >> 12) & 0xfffu); }  // rowslot(row)
 __device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 
 constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
@@ -99,7 +100,7 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const Col
           s2.y += cc * w[i].y;
         }
         if (mt[i] & kMetaFlush) {
-          const int row = meta_row(mt[i]);
+          const int row = meta_slot(mt[i]);
           const bool car = (mt[i] & kMetaCarry) != 0;
           if (FSEL < 0) {
             (car ? carry + t : out0 + row)[0] = s0;
@@ -122,7 +123,7 @@ __device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, const Col
                                             cplx<T>* out0, cplx<T>* outF, const cplx<T>* carry) {
   if (ncont == 0) return;
   const int t = threadIdx.x, TT = g.TT;
-  const int row = meta_row(__ldg(p.meta + (cnt - 1) * TT + t));
+  const int row = meta_slot(__ldg(p.meta + (cnt - 1) * TT + t));
   constexpr int nfs = FSEL < 0 ? NF : 1;
 #pragma unroll
   for (int f = 0; f < nfs; ++f) {
@@ -146,7 +147,7 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const Co
     for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      Y[i] = rows[meta_row(mt[i])];
+      Y[i] = rows[meta_slot(mt[i])];
       w[i] = tw.template get<+1>((kx * meta_x(mt[i])) & Nm);
     }
 #pragma unroll
@@ -274,13 +275,14 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   for (int i = 0; i < CNT; ++i) acc[i * TT + t] = T(0);
   __syncthreads();
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
-  const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + (N >> 6)};
+  const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + 128, g.log2N - 7,
+                         (T)(6.283185307179586476925 / (double)N)};
   FourStep<T> fs;
   fs.init(t, TT, sA, ftab);
   auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
     const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[t + m * TT] : cplx<T>{T(0), T(0)};
+    for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[rowslot(t + m * TT)] : cplx<T>{T(0), T(0)};
 #pragma unroll
     for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
   };
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
       }
       fs.inverse(y);
 #pragma unroll
-      for (int m = 0; m < 8; ++m) sA[t + m * TT] = y[m];
+      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
       __syncthreads();
       gather_cells(p, g, kx, CNT, sA, tw, acc);
     } else {
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
         spectral_multiply<T, false>(sS, spec_addr(fs, g), imag_of(p, f) != 0, oddy_of(p, f) != 0, v, v);
         fs.inverse(v);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) sA[t + m * TT] = v[m];
+        for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = v[m];
         __syncthreads();
         gather_cells(p, g, kx, CNT, sA, tw, acc);
       }

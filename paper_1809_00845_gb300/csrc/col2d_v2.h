@@ -13,7 +13,7 @@
 
 namespace bemfft {
 
-// Cell word (plan time): x | row << 12 | FLUSH << 29 | CARRY << 30 | type << 31.
+// Cell word (plan time): x | rowslot(row) << 12 | FLUSH << 29 | CARRY << 30 | type << 31.
 constexpr uint32_t kMetaFlush = 1u << 29;
 constexpr uint32_t kMetaCarry = 1u << 30;
 
@@ -34,8 +34,15 @@ struct Col2Dv2Params {
   int has_carry;         // some row is split between threads
 };
 
-// number of table entries of the four-step kernel for TT threads, N = 16 TT
-__host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 16 + 512 + TT / 4 + 64; }
+// number of table entries of the four-step kernel for TT threads, N = 16 TT:
+// lane, warp and T5 tables, then the sparse twiddles (hi: 128, lo: N / 128)
+__host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 16 + 512 + 128 + TT / 8; }
+// Shared-memory slot of grid row r.  Rows are read in two patterns: 16
+// consecutive rows per half-warp (transform input and output) and rows about
+// 8 apart across lanes (neighbouring threads' cells along the curve, in the
+// row sums and the gather).  XOR-ing the low 3 bits with bits 4..6 keeps both
+// free of bank conflicts (8-byte entries) and stays inside each block of 16.
+__host__ __device__ inline int rowslot(int r) { return r ^ ((r >> 4) & 7); }
 // spectrum column in shared memory, padded by one entry every 16
 __host__ __device__ inline int sspec_entries(int n) { return ((n + 1 + (n + 1) / 16) + 3) & ~3; }
 

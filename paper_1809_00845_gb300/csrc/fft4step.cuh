@@ -223,15 +223,30 @@ struct FourStep {
   }
 };
 
-// e^{DIR 2 pi i m / N} from two small tables: m = 64 hi + lo,
-// hi[i] = e^{2 pi i 64 i / N}, lo[i] = e^{2 pi i i / N} (N/64 + 64 entries).
+// e^{DIR 2 pi i m / N} for 0 <= m < N, with m = 2^L hi + lo and
+// L = log2(N) - 7: hi[i] = e^{2 pi i i / 128} (128 entries) and the low part
+// either from a second table lo[i] = e^{2 pi i i / N} (2^L entries; FP64) or,
+// for FP32, from short Taylor series: the angle 2 pi lo / N is below
+// 2 pi / 128 = 0.049, so cos to theta^4 and sin to theta^5 are exact to
+// 2e-11, well below FP32 rounding, and the table read becomes a few FMAs.
 template <typename T>
 struct Twiddles2L {
   const cplx<T>* hi;
   const cplx<T>* lo;
+  int L;
+  T dtheta;  // 2 pi / N
   template <int DIR>
   __device__ __forceinline__ cplx<T> get(int m) const {
-    cplx<T> z = cmul(hi[m >> 6], lo[m & 63]);
+    const cplx<T> a = hi[m >> L];
+    cplx<T> b;
+    if constexpr (sizeof(T) == 4) {
+      const T th = (T)(m & ((1 << L) - 1)) * dtheta, t2 = th * th;
+      b.x = fmaf(t2, fmaf(t2, 1.0f / 24.0f, -0.5f), 1.0f);
+      b.y = th * fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    } else {
+      b = lo[m & ((1 << L) - 1)];
+    }
+    cplx<T> z = cmul(a, b);
     if constexpr (DIR < 0) z.y = -z.y;
     return z;
   }
