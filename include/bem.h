@@ -66,7 +66,13 @@ typedef enum {
 } bem_status;
 
 typedef enum { BEM_LAPLACE_2D = 0, BEM_LAPLACE_3D = 1, BEM_KELVIN_3D = 2 } bem_kernel;
-typedef enum { BEM_F64 = 0, BEM_F32 = 1 } bem_precision;
+/* BEM_F64: FP64 arithmetic, double I/O.  BEM_F32: FP32 arithmetic, float I/O.
+ * BEM_F32X2: double-float arithmetic (each value a pair of FP32 numbers, a
+ * 48-bit significand) on the FP32 pipes, double I/O; about 1e-13 relative
+ * accuracy at several times the speed of FP64 on GPUs with reduced FP64
+ * throughput.  BEM_F32X2 is available for 2D plans with n >= 256 (the
+ * four-step column kernel) and returns BEM_ERR_UNSUPPORTED otherwise. */
+typedef enum { BEM_F64 = 0, BEM_F32 = 1, BEM_F32X2 = 2 } bem_precision;
 
 /* BEM_SINGLE: S (Laplace) or U (Kelvin).  BEM_DOUBLE: D (Laplace) or T
  * (Kelvin).  BEM_SYSTEM: the boundary-condition-split operator A of the last
@@ -126,7 +132,7 @@ bem_status bem_set_bc(bem_plan_t plan, const uint8_t* bc, double c);
 
 /* One operator apply on the device (Section 4, Eq. 15-16).
  *   in_dev, out_dev  device pointers, nb*ncomp values of the plan precision
- *                    (double for BEM_F64, float for BEM_F32), component
+ *                    (double for BEM_F64 and BEM_F32X2, float for BEM_F32), component
  *                    fastest; caller-owned; must not alias
  *   stream           cudaStream_t (may be NULL); the call is asynchronous
  * BEM_SYSTEM needs a prior bem_set_bc. */
@@ -183,12 +189,13 @@ bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, dou
 bem_status bem_set_preconditioner(bem_plan_t plan, int kind, int block_size);
 
 /* Mixed-precision iterative refinement for BEM_F32 plans: with enable != 0
- * the plan builds an FP64 plan of the same geometry; bem_solve then forms
- * the right-hand side and every residual with the FP64 operator and solves
+ * the plan builds a companion plan of the same geometry in BEM_F32X2 (2D,
+ * n >= 256) or BEM_F64 (otherwise); bem_solve then forms the right-hand side
+ * and every residual with the companion operator and solves
  * for the corrections with the preconditioned FP32 GMRES, so that tolerances
  * below the FP32 operator's own accuracy (a relative residual of ~3e-6 for
- * the 4096^2 star) are reached.  rel_residual then is the FP64 residual.
- * No effect on BEM_F64 plans. */
+ * the 4096^2 star) are reached.  rel_residual then is the companion's
+ * residual.  No effect on BEM_F64 and BEM_F32X2 plans. */
 bem_status bem_enable_refinement(bem_plan_t plan, int enable);
 
 /* Query sizes and launch shape of a plan. */

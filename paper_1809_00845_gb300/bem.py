@@ -20,11 +20,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbem_gb300.so")
 BEM_OK, BEM_ERR_ARG, BEM_ERR_CUDA, BEM_ERR_OOM, BEM_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 BEM_ERR_BREAKDOWN, BEM_ERR_NONFINITE, BEM_ERR_TIMEOUT, BEM_ERR_UNSUPPORTED = 5, 6, 7, 8
 BEM_LAPLACE_2D, BEM_LAPLACE_3D, BEM_KELVIN_3D = 0, 1, 2
-BEM_F64, BEM_F32 = 0, 1
+BEM_F64, BEM_F32, BEM_F32X2 = 0, 1, 2
 BEM_SINGLE, BEM_DOUBLE, BEM_SYSTEM = 0, 1, 2
 
 KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d": BEM_KELVIN_3D}
-PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32}
+PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32, "f32x2": BEM_F32X2}
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
@@ -177,11 +177,11 @@ class Plan:
     # --------------------------------------------------------------- helpers
     @property
     def np_dtype(self):
-        return np.float64 if self.precision == BEM_F64 else np.float32
+        return np.float32 if self.precision == BEM_F32 else np.float64
 
     def _tdtype(self):
         import torch
-        return torch.float64 if self.precision == BEM_F64 else torch.float32
+        return torch.float32 if self.precision == BEM_F32 else torch.float64
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

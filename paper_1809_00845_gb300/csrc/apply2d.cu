@@ -191,13 +191,13 @@ __global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem,
 
 // val[pos] = (coefA[pos], coefB[pos]) * in[perm[pos]] (interleaved positions;
 // padding positions have perm < 0 and get zero)
-template <typename T>
-__global__ void k_prep_v2(int npos, const int32_t* __restrict__ perm, const T* __restrict__ in,
+template <typename T, typename TIO>
+__global__ void k_prep_v2(int npos, const int32_t* __restrict__ perm, const TIO* __restrict__ in,
                           const T* __restrict__ coefA, const T* __restrict__ coefB, cplx<T>* __restrict__ val) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= npos) return;
   const int u = perm[j];
-  const T x = u >= 0 ? in[u] : T(0);
+  const T x = u >= 0 ? T(in[u]) : T(0);
   val[j] = {coefA[j] * x, coefB[j] * x};
 }
 
@@ -205,10 +205,10 @@ __global__ void k_prep_v2(int npos, const int32_t* __restrict__ perm, const T* _
 // positions j (padding skipped), FP64 sum in a fixed
 // order: 32 cells per block, 8 warps each summing every 8th partial, then the
 // 8 warp sums in order.
-template <typename T>
+template <typename T, typename TIO>
 __global__ void __launch_bounds__(256) k_reduce_v2(const T* __restrict__ partial, int grid, int npos,
-                                                   const int32_t* __restrict__ perm, const T* __restrict__ diag,
-                                                   const T* __restrict__ in, T* __restrict__ out) {
+                                                   const int32_t* __restrict__ perm, const TIO* __restrict__ diag,
+                                                   const TIO* __restrict__ in, TIO* __restrict__ out) {
   __shared__ double red[8][33];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_reduce_v2(const T* __restrict__ partial
     for (int k = 0; k < 8; ++k) t += red[k][lane];
     const int u = perm[j];
     if (diag) t += (double)diag[u] * (double)in[u];
-    out[u] = (T)t;
+    out[u] = (TIO)t;
   }
 }
 
@@ -424,7 +424,7 @@ static cudaError_t configure_col2d(int TT, size_t smem, int* bps) {
       default: return Col2DKernels<float, 32>::configure(smem, TT, bps);
     }
   } else {
-    return Col2DKernels<double, 0>::configure(smem, TT, bps);
+    return Col2DKernels<T, 0>::configure(smem, TT, bps);
   }
 }
 
@@ -440,7 +440,7 @@ static void launch_col2d(const bem_plan_s* p, int nf, const Col2Dv2Params<T>& cp
       default: Col2DKernels<float, 32>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
     }
   } else {
-    Col2DKernels<double, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp);
+    Col2DKernels<T, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp);
   }
 }
 
@@ -556,7 +556,14 @@ bem_status setup_apply_2d(bem_plan_s* p) {
     return BEM_ERR_UNSUPPORTED;
   }
   p->v2 = p->log2N >= 9;
-  if (p->v2) return p->prec == BEM_F64 ? setup_v2_t<double>(p) : setup_v2_t<float>(p);
+  if (p->v2) {
+    if (p->prec == BEM_F32X2) return setup_v2_t<f32x2>(p);
+    return p->prec == BEM_F64 ? setup_v2_t<double>(p) : setup_v2_t<float>(p);
+  }
+  if (p->prec == BEM_F32X2) {
+    set_error("BEM_F32X2 needs the four-step column kernel (n >= 256)");
+    return BEM_ERR_UNSUPPORTED;
+  }
   return p->prec == BEM_F64 ? setup_t<double>(p) : setup_t<float>(p);
 }
 
@@ -574,19 +581,13 @@ bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& c
   BEM_CUDA_TRY(cudaMemcpy(dm, meta.data(), npos * sizeof(uint32_t), cudaMemcpyHostToDevice));
   op.owned.push_back(dm);
   op.meta = static_cast<const uint32_t*>(dm);
-  const size_t tb = prec_bytes(p);
   for (int k = 0; k < 2; ++k) {
     const std::vector<double>& csort = k == 0 ? coefA : coefB;
     std::vector<double> c(npos, 0.0);
     for (int64_t j = 0; j < nb; ++j) c[p->h_pos[j]] = csort[j];
     void* d = nullptr;
-    BEM_CUDA_TRY(cudaMalloc(&d, npos * tb));
-    if (p->prec == BEM_F64) {
-      BEM_CUDA_TRY(cudaMemcpy(d, c.data(), npos * tb, cudaMemcpyHostToDevice));
-    } else {
-      std::vector<float> f(c.begin(), c.end());
-      BEM_CUDA_TRY(cudaMemcpy(d, f.data(), npos * tb, cudaMemcpyHostToDevice));
-    }
+    bem_status rc = upload_real(p, c.data(), c.size(), false, &d);
+    if (rc != BEM_OK) return rc;
     op.owned.push_back(d);
     (k == 0 ? op.coefA : op.coefB) = d;
   }
@@ -662,13 +663,14 @@ static bem_status launch_v1(bem_plan_s* p, const Operator& op, const void* in, v
   return BEM_OK;
 }
 
-template <typename T>
+// T: arithmetic type of the column kernel; TIO: type of the caller's vectors
+template <typename T, typename TIO>
 static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
                             bool timed, cudaStream_t st) {
   const int nb = (int)p->nb;
   const int tb = 256;
   const int npos = (int)p->v2_npos;
-  k_prep_v2<T><<<(npos + tb - 1) / tb, tb, 0, st>>>(npos, p->d_perm_il, static_cast<const T*>(in),
+  k_prep_v2<T, TIO><<<(npos + tb - 1) / tb, tb, 0, st>>>(npos, p->d_perm_il, static_cast<const TIO*>(in),
                                                   static_cast<const T*>(op.coefA), static_cast<const T*>(op.coefB),
                                                   static_cast<cplx<T>*>(sp.val));
   Col2Dv2Params<T> cp{};
@@ -694,9 +696,9 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   launch_col2d<T>(p, op.nf, cp, st);
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k_reduce_v2<T><<<(npos + 31) / 32, 256, 0, st>>>(static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il,
-                                                    static_cast<const T*>(op.diag), static_cast<const T*>(in),
-                                                    static_cast<T*>(out));
+  k_reduce_v2<T, TIO><<<(npos + 31) / 32, 256, 0, st>>>(
+      static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il, static_cast<const TIO*>(op.diag),
+      static_cast<const TIO*>(in), static_cast<TIO*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
@@ -739,9 +741,11 @@ bem_status launch_apply_2d_with(bem_plan_s* p, const Operator& op, const void* i
     set_error("2D operator with unsupported field count");
     return BEM_ERR_UNSUPPORTED;
   }
-  if (p->v2)
-    return p->prec == BEM_F64 ? launch_v2<double>(p, op, in, out, sp, timed, st)
-                              : launch_v2<float>(p, op, in, out, sp, timed, st);
+  if (p->v2) {
+    if (p->prec == BEM_F32X2) return launch_v2<f32x2, double>(p, op, in, out, sp, timed, st);
+    return p->prec == BEM_F64 ? launch_v2<double, double>(p, op, in, out, sp, timed, st)
+                              : launch_v2<float, float>(p, op, in, out, sp, timed, st);
+  }
   return p->prec == BEM_F64 ? launch_v1<double>(p, op, in, out, sp, timed, st)
                             : launch_v1<float>(p, op, in, out, sp, timed, st);
 }

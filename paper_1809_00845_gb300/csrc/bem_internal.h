@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/bem.h"
+#include "ff.cuh"
 
 namespace bemfft {
 
@@ -217,6 +218,7 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
                        cudaStream_t st);
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);
 size_t prec_bytes(const bem_plan_s* p);
+bem_status upload_real(const bem_plan_s* p, const double* v, size_t count, bool io, void** dst);
 // Lets `kern` launch with up to the device's opt-in shared-memory maximum.  The
 // limit is a property of the function, shared by every plan, so it is never set
 // to one plan's (smaller) need: a plan made later would otherwise lower it below

@@ -18,18 +18,40 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-size_t prec_bytes(const bem_plan_s* p) { return p->prec == BEM_F64 ? sizeof(double) : sizeof(float); }
+// bytes of one I/O value (float for BEM_F32, double otherwise); also the
+// storage size of one value of the plan's arithmetic type
+size_t prec_bytes(const bem_plan_s* p) { return p->prec == BEM_F32 ? sizeof(float) : sizeof(double); }
 
-static bem_status upload_coef(bem_plan_s* p, Operator& op, const std::vector<double>& v, const void** dst) {
+// v converted to the plan's arithmetic type (io = false) or to its I/O type
+// (io = true: the diagonal term, added in FP64 to FP64/FP32 I/O values)
+bem_status upload_real(const bem_plan_s* p, const double* v, size_t count, bool io, void** dst) {
   void* d = nullptr;
-  const size_t tb = prec_bytes(p);
-  BEM_CUDA_TRY(cudaMalloc(&d, v.size() * tb));
-  if (p->prec == BEM_F64) {
-    BEM_CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * tb, cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMalloc(&d, count * prec_bytes(p)));
+  cudaError_t e;
+  if (p->prec == BEM_F32) {
+    std::vector<float> f(v, v + count);
+    e = cudaMemcpy(d, f.data(), count * sizeof(float), cudaMemcpyHostToDevice);
+  } else if (p->prec == BEM_F32X2 && !io) {
+    std::vector<f32x2> f(count);
+    for (size_t i = 0; i < count; ++i) f[i] = f32x2(v[i]);
+    e = cudaMemcpy(d, f.data(), count * sizeof(f32x2), cudaMemcpyHostToDevice);
   } else {
-    std::vector<float> f(v.begin(), v.end());
-    BEM_CUDA_TRY(cudaMemcpy(d, f.data(), f.size() * tb, cudaMemcpyHostToDevice));
+    e = cudaMemcpy(d, v, count * sizeof(double), cudaMemcpyHostToDevice);
   }
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    set_error(std::string("upload: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  *dst = d;
+  return BEM_OK;
+}
+
+static bem_status upload_coef(bem_plan_s* p, Operator& op, const std::vector<double>& v, const void** dst,
+                              bool io = false) {
+  void* d = nullptr;
+  bem_status rc = upload_real(p, v.data(), v.size(), io, &d);
+  if (rc != BEM_OK) return rc;
   op.owned.push_back(d);
   *dst = d;
   return BEM_OK;
@@ -95,16 +117,10 @@ static bem_status build_op3(bem_plan_s* p, Operator3D& op, const std::vector<std
   free_operator3(op);
   const int nf = (int)coefs.size();
   std::vector<Field3D> fields(nf);
-  const size_t tb = prec_bytes(p);
   for (int f = 0; f < nf; ++f) {
     void* d = nullptr;
-    BEM_CUDA_TRY(cudaMalloc(&d, coefs[f].size() * tb));
-    if (p->prec == BEM_F64) {
-      BEM_CUDA_TRY(cudaMemcpy(d, coefs[f].data(), coefs[f].size() * tb, cudaMemcpyHostToDevice));
-    } else {
-      std::vector<float> v(coefs[f].begin(), coefs[f].end());
-      BEM_CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * tb, cudaMemcpyHostToDevice));
-    }
+    bem_status rc = upload_real(p, coefs[f].data(), coefs[f].size(), false, &d);
+    if (rc != BEM_OK) return rc;
     op.owned.push_back(d);
     fields[f] = {d, comps[f]};
   }
@@ -180,9 +196,13 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     set_error("bem_plan: dimension does not match the kernel");
     return BEM_ERR_ARG;
   }
-  if (prec != BEM_F64 && prec != BEM_F32) {
+  if (prec != BEM_F64 && prec != BEM_F32 && prec != BEM_F32X2) {
     set_error("bem_plan: unknown precision");
     return BEM_ERR_ARG;
+  }
+  if (prec == BEM_F32X2 && (dim != 2 || n[0] < 256)) {
+    set_error("bem_plan: BEM_F32X2 needs a 2D grid with n >= 256");
+    return BEM_ERR_UNSUPPORTED;
   }
   if (flags != 0) {
     set_error("bem_plan: flags must be 0");
@@ -304,7 +324,7 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   {
     const int64_t N = p->N;
     const double PI = 3.14159265358979323846;
-    if (prec == BEM_F64) {
+    if (prec != BEM_F32) {
       std::vector<cplx<double>> q(N / 4);
       for (int64_t r = 0; r < N / 4; ++r) q[r] = {std::cos(2.0 * PI * r / N), std::sin(2.0 * PI * r / N)};
       PLAN_CUDA(cudaMalloc(&p->d_qtab, q.size() * sizeof(q[0])));
@@ -404,7 +424,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       s.f[1] = {nullptr, 0, 1, 0, nullptr, nullptr};
       s.f[2] = {nullptr, 0, 2, 0, nullptr, nullptr};
       if ((rc = build_op_v2(p, s, ca, cb, ty)) != BEM_OK) return rc;
-      if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+      if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
       p->have_bc = true;
       p->pc.valid = false;
       return BEM_OK;
@@ -423,7 +443,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     if ((rc = upload_coef(p, s, aq, &s.f[0].coef)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, ax, &s.f[1].coef)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, ay, &s.f[2].coef)) != BEM_OK) return rc;
-    if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
     if ((rc = alloc_field_rho(p, s)) != BEM_OK) return rc;
   } else if (p->kernel == BEM_LAPLACE_3D) {
     // A x = S(x m_D) + D(x m_N) - c x m_N: fields U (w m_D), Q_a (w n_a m_N)
@@ -436,7 +456,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     }
     for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;
     if ((rc = build_op3(p, p->op3_system, cf, {0, 0, 0, 0}, 1, {0, 1, 2, 3})) != BEM_OK) return rc;
-    if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
     p->op3_system.diag = s.diag;
   } else {
     // Navier (Eq. 8): A x = U(x m_D) - T(x m_N) - c x m_N per component:
@@ -465,7 +485,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     std::vector<double> dg(nb * 3);
     for (int64_t i = 0; i < nb * 3; ++i) dg[i] = bc[i] ? -c : 0.0;
     if ((rc = build_op3(p, p->op3_system, cf, comps, 3, coup)) != BEM_OK) return rc;
-    if ((rc = upload_coef(p, s, dg, &s.diag)) != BEM_OK) return rc;
+    if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
     p->op3_system.diag = s.diag;
   }
   p->have_bc = true;
@@ -535,7 +555,7 @@ bem_status bem_enable_refinement(bem_plan_t p, int enable) {
     set_error("bem_enable_refinement: null plan");
     return BEM_ERR_ARG;
   }
-  if (!enable || p->prec == BEM_F64) {
+  if (!enable || p->prec != BEM_F32) {
     if (p->companion) bem_destroy(p->companion);
     p->companion = nullptr;
     return BEM_OK;
@@ -544,7 +564,8 @@ bem_status bem_enable_refinement(bem_plan_t p, int enable) {
   const int64_t n[3] = {p->n, p->n, p->n};
   bem_plan_t c = nullptr;
   bem_status rc = plan_impl(&c, p->dim, n, p->h, p->nb, p->h_cell_user.data(), p->h_w_user.data(),
-                            p->h_normal_user.data(), (bem_kernel)p->kernel, p->nu, p->mu, BEM_F64, 0, nullptr);
+                            p->h_normal_user.data(), (bem_kernel)p->kernel, p->nu, p->mu,
+                            p->dim == 2 && p->n >= 256 ? BEM_F32X2 : BEM_F64, 0, nullptr);
   if (rc != BEM_OK) return rc;
   c->pc.kind = 0;
   p->companion = c;

@@ -179,8 +179,8 @@ struct FourStep {
     for (int k = 0; k < 16; ++k) {
       cplx<T> mine = h ? twc<32, -1>(v[k], k) : v[k];
       cplx<T> other;
-      other.x = __shfl_xor_sync(0xffffffffu, mine.x, 1);
-      other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
+      other.x = shfl_xor(mine.x, 1);
+      other.y = shfl_xor(mine.y, 1);
       v[k] = h ? other - mine : mine + other;
     }
   }
@@ -198,8 +198,8 @@ struct FourStep {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       cplx<T> other;
-      other.x = __shfl_xor_sync(0xffffffffu, v[k].x, 1);
-      other.y = __shfl_xor_sync(0xffffffffu, v[k].y, 1);
+      other.x = shfl_xor(v[k].x, 1);
+      other.y = shfl_xor(v[k].y, 1);
       v[k] = h ? twc<32, +1>(other - v[k], k) : v[k] + other;
     }
     dft<16, +1>(v);

@@ -27,6 +27,15 @@ struct alignas(2 * sizeof(T)) cplx {
   T x, y;
 };
 
+// lane exchange of one real of the working type (float, double, or a
+// double-float pair, moved as its two floats)
+__device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <typename P>
+__device__ __forceinline__ P shfl_xor(P v, int m) {
+  return P(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
 template <typename T>
 __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T>

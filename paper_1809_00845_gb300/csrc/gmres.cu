@@ -334,8 +334,8 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
   double* d_h2 = d_h + 520;   // 520: second sweep
   double* d_y = d_h2 + 520;   // 520
   double* d_partial = d_y + 520;
-  Gm g{p, st, M, d_partial, nchunk, p->prec == BEM_F64};
-  Gm gr{R, st, M, d_partial, nchunk, R->prec == BEM_F64};
+  Gm g{p, st, M, d_partial, nchunk, p->prec != BEM_F32};
+  Gm gr{R, st, M, d_partial, nchunk, R->prec != BEM_F32};
   GmresWs ws{p->d_V, d_w, d_z, d_h, d_h2, d_y, m};
   int applies = 0;
 

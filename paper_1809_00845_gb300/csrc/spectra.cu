@@ -144,6 +144,9 @@ bem_status compute_spectra_2d(bem_plan_s* p, cudaStream_t st) {
     if (p->prec == BEM_F64)
       k_compress2d<double><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(buf, n, N, k.imag, scale,
                                                                        static_cast<double*>(s.data));
+    else if (p->prec == BEM_F32X2)
+      k_compress2d<f32x2><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(buf, n, N, k.imag, scale,
+                                                                      static_cast<f32x2*>(s.data));
     else
       k_compress2d<float><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(buf, n, N, k.imag, scale,
                                                                       static_cast<float*>(s.data));

@@ -66,6 +66,10 @@ def test_rejects_bad_arguments_on_host(lib):
     assert _plan_rc(3, 8, 0.125, cell, w, nrm)[0] == bem.BEM_ERR_ARG                   # dim vs kernel
     assert _plan_rc(2, 8, 0.125, cell, w, nrm, flags=7)[0] == bem.BEM_ERR_ARG          # reserved flags
     assert _plan_rc(2, 8, 0.125, cell, w, nrm, prec=9)[0] == bem.BEM_ERR_ARG           # precision
+    assert _plan_rc(2, 8, 0.125, cell, w, nrm, prec=2)[0] == bem.BEM_ERR_UNSUPPORTED   # f32x2 below n = 256
+    cell3 = np.array([[1, 2, 3], [3, 4, 5]])
+    nrm3 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    assert _plan_rc(3, 512, 1 / 512, cell3, w, nrm3, kernel=1, prec=2)[0] == bem.BEM_ERR_UNSUPPORTED  # f32x2 in 3D
     rc = lib.bem_plan(None, 2, None, 0.1, 1, None, None, None, 0, 0.3, 1.0, 1, 0, None)
     assert rc == bem.BEM_ERR_ARG
     assert lib.bem_apply(None, 0, None, None, None) == bem.BEM_ERR_ARG

@@ -1,6 +1,7 @@
 """Parity of the CUDA operator apply with the CPU FP64 oracle (GPU).
 
-Bars: relative L2 <= 1e-12 for FP64 plans and <= 2e-6 for FP32 plans on
+Bars: relative L2 <= 1e-12 for FP64 and double-float (f32x2) plans and
+<= 2e-6 for FP32 plans on
 random N(0,1) densities, element by element over every boundary cell.  Sizes
 span one-thread columns (n = 4) through multi-pass transforms with a ragged
 last pass (N = 2n = 2^k with k not a multiple of 4) up to the full 4096^2
@@ -13,7 +14,7 @@ from paper_1809_00845_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 2e-6}
+TOL = {"f64": 1e-12, "f32": 2e-6, "f32x2": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -141,7 +142,7 @@ def test_linearity_and_repeatability(torch_cuda):
     assert np.array_equal(gpu_apply(torch_cuda, plan, "single", x1), y1)
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "f32x2"])
 def test_star_4096_full_size_sampled_rows(torch_cuda, oracle_mod, prec):
     """The 4096^2 star (padded 8192^2), mixed BCs, in the launch configuration
     the benchmark times; the oracle evaluates 3 x 256 target rows exactly."""
@@ -160,7 +161,7 @@ def test_star_4096_full_size_sampled_rows(torch_cuda, oracle_mod, prec):
     assert rel_l2(s_out[1000:1256], ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 def test_fourstep_kernel_edge_cases(torch_cuda, oracle_mod, prec):
     """n >= 256 uses the four-step column kernel: one cell, the four grid
     corners (largest offsets), and a dense random set where many rows carry
@@ -178,7 +179,7 @@ def test_fourstep_kernel_edge_cases(torch_cuda, oracle_mod, prec):
     for layer, lid in (("single", 0), ("double", 1)):
         ref = oracle_mod.apply("laplace2d", lid, corners.cell, corners.h, corners.w, corners.normal, x)
         out = gpu_apply(torch_cuda, p, layer, x)
-        if prec == "f64":
+        if prec != "f32":
             assert rel_l2(out, ref) <= TOL[prec]
         else:  # four far-apart cells: outputs ~1e-4 of the near-field scale
             assert np.max(np.abs(out - ref)) <= fp32_abs_bound(corners, x, layer)
@@ -192,6 +193,20 @@ def test_fourstep_kernel_edge_cases(torch_cuda, oracle_mod, prec):
         assert rel_l2(gpu_apply(torch_cuda, p, layer, x), ref) <= TOL[prec]
     ref = oracle_mod.system_apply("laplace2d", dense.cell, dense.h, dense.w, dense.normal, bc, x)
     assert rel_l2(gpu_apply(torch_cuda, p, "system", x), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("n,nb", [(256, 1500), (512, 2000), (1024, 3000), (2048, 5000)])
+def test_f32x2_random_cells_single_double(torch_cuda, oracle_mod, n, nb):
+    """Double-float plans (pairs of FP32 numbers, FP64 I/O) on every
+    four-step grid size below the full one."""
+    rng = np.random.default_rng(2000 + n)
+    b = I.random_cells(n, nb, rng)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, "f32x2")
+    for layer, lid in (("single", 0), ("double", 1)):
+        ref = oracle_mod.apply("laplace2d", lid, b.cell, b.h, b.w, b.normal, x)
+        out = gpu_apply(torch_cuda, plan, layer, x)
+        assert rel_l2(out, ref) <= TOL["f32x2"], (layer, rel_l2(out, ref))
 
 
 def test_fourstep_global_accumulators(torch_cuda, oracle_mod):

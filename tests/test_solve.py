@@ -39,7 +39,7 @@ def test_circle_dirichlet_f64_matches_dense_lu(torch_cuda, oracle_mod):
     assert np.linalg.norm(A @ q_out - rhs) / np.linalg.norm(rhs) <= 2e-10
 
 
-@pytest.mark.parametrize("prec,tol,bound", [("f64", 1e-10, 2e-10), ("f32", 1e-5, 1e-4)])
+@pytest.mark.parametrize("prec,tol,bound", [("f64", 1e-10, 2e-10), ("f32", 1e-5, 1e-4), ("f32x2", 1e-10, 2e-10)])
 def test_star_mixed_bc_residual(torch_cuda, oracle_mod, prec, tol, bound):
     b = I.star_boundary(256)
     u, q = I.boundary_data(b, I.field_expcos)
@@ -91,7 +91,8 @@ def test_initial_guess_and_iteration_cap(torch_cuda, oracle_mod):
 
 def test_fp32_refinement_reaches_fp64_tolerance(torch_cuda, oracle_mod):
     """FP32 GMRES stalls near the FP32 operator's accuracy; with mixed-precision
-    refinement (FP64 residuals) the FP32 plan reaches 1e-8."""
+    refinement (residuals with the double-float companion plan) the FP32 plan
+    reaches 1e-8."""
     b = I.star_boundary(512)
     u, q = I.boundary_data(b, I.field_expcos)
     bc = I.mixed_bc_theta(b)
