@@ -6,12 +6,9 @@
 // = one component of the result; the operator couples them through kernel
 // spectra K_of):
 //   k3_prep   val_f[j]      = coef_f[j] * in[perm[j]*ncomp + comp_f]
-//   k3_xdft   X_f[kx][z][y] = sum over the cells of grid line (y, z) of
-//                             val_f e^{-2 pi i kx x / N}   (input-pruned x-DFT;
-//                             only z, y < n and kx <= n exist)
-//   k3_ypass  B_f[kx][ky][z] = FFT_y(X_f[kx][z][:])       (one line per 16-32
-//                             threads; written through a shared-memory
-//                             transpose so the next pass reads contiguous z)
+//   k3_yfwd   B_f[kx][ky][z] = FFT_y of the grid lines (y, z < n), each line
+//             the input-pruned x-DFT sum over its cells of
+//             val_f e^{-2 pi i kx x / N}, formed in registers (fft3d.cuh)
 //   k3_zpass  per (kx, ky): FFT_z of every B_f, multiply-accumulate
 //             Y_o = sum_f K_of * B_f, inverse FFT_z, B_o <- Y_o (z < n)
 //   k3_yinv   X_o[kx][z][y] = IFFT_y(B_o[kx][:][z])       (y < n kept)
@@ -24,6 +21,7 @@
 #include <vector>
 
 #include "bem_internal.h"
+#include "fft3d.h"
 #include "fft_reg.cuh"
 
 namespace bemfft {
@@ -51,168 +49,6 @@ __global__ void k3_prep(int nb, int ncomp, const int32_t* __restrict__ perm, con
   if (j >= nb) return;
   const Field3D fd = fields[f];
   val[(size_t)f * nb + j] = static_cast<const T*>(fd.coef)[j] * in[(size_t)perm[j] * ncomp + fd.comp];
-}
-
-// X[f][kx][z][y] for all kx <= n, z, y < n
-template <typename T>
-__global__ void k3_xdft(int n, int log2N, int nb, const int32_t* __restrict__ lptr, const uint16_t* __restrict__ xs,
-                        const T* __restrict__ val, const cplx<T>* __restrict__ tw2, cplx<T>* __restrict__ X) {
-  __shared__ cplx<T> stw[2048 / 64 + 64 + 64];
-  const int N = 1 << log2N;
-  const int nhi = N >= 64 ? N >> 6 : 1;
-  for (int i = threadIdx.x; i < nhi + 64; i += blockDim.x) stw[i] = tw2[i];
-  __syncthreads();
-  const Tw2<T> tw{stw, stw + nhi};
-  const int f = blockIdx.y;
-  const int64_t plane = (int64_t)n * n;
-  const int64_t total = (int64_t)(n + 1) * plane;
-  const T* v = val + (size_t)f * nb;
-  cplx<T>* out = X + (size_t)f * total;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(idx / plane);
-    const int64_t line = idx - (int64_t)kx * plane;  // z * n + y
-    const int j0 = lptr[line], j1 = lptr[line + 1];
-    cplx<T> s = {T(0), T(0)};
-    for (int j = j0; j < j1; ++j) {
-      const cplx<T> w = tw.template get<-1>((kx * (int)xs[j]) & (N - 1));
-      const T r = v[j];
-      s.x += r * w.x;
-      s.y += r * w.y;
-    }
-    out[idx] = s;
-  }
-}
-
-// y-FFT of the lines (kx, z0 .. z0+ZB-1) of field blockIdx.z; output
-// B[f][kx][ky][z] through a padded shared tile [ky][ZB+1].
-template <typename T>
-__global__ void __launch_bounds__(512) k3_ypass(int n, int log2N, int ZB, const cplx<T>* __restrict__ X,
-                                                cplx<T>* __restrict__ B, const cplx<T>* __restrict__ qtab) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = 1 << log2N, TT = N / 16;
-  const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
-  const int kx = blockIdx.y, z0 = blockIdx.x * ZB, f = blockIdx.z;
-  cplx<T>* sq = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* sbuf = sq + (N >> 2);  // ZB line buffers, later the tile
-  for (int i = threadIdx.x; i < (N >> 2); i += blockDim.x) sq[i] = qtab[i];
-  __syncthreads();
-  const Twiddles<T> tw{sq, log2N - 2};
-  const int64_t plane = (int64_t)n * n;
-  const cplx<T>* src = X + ((size_t)f * (n + 1) + kx) * plane + (size_t)(z0 + g) * n;
-  cplx<T> v[16];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = src[t + m * TT];
-#pragma unroll
-  for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
-  fft_line<16, -1, T, true>(v, t, TT, log2N, tw, sbuf + (size_t)g * (N + N / 16));
-  __syncthreads();
-  cplx<T>* tile = sbuf;  // [N][ZB + 1]
-#pragma unroll
-  for (int m = 0; m < 16; ++m) tile[(size_t)(t + m * TT) * (ZB + 1) + g] = v[m];
-  __syncthreads();
-  cplx<T>* dst = B + ((size_t)f * (n + 1) + kx) * (size_t)N * n + z0;
-  for (int i = threadIdx.x; i < N * ZB; i += blockDim.x) {
-    const int ky = i / ZB, zz = i - ky * ZB;
-    dst[(size_t)ky * n + zz] = tile[(size_t)ky * (ZB + 1) + zz];
-  }
-}
-
-// z-FFT of the columns (kx, ky0 .. ky0+LPC-1), all fields; multiply by the
-// coupled spectra; inverse z-FFT of every output; B_o <- result (z < n).
-template <typename T>
-__global__ void __launch_bounds__(512) k3_zpass(int n, int log2N, int nf, int no, int LPC,
-                                                const int16_t* __restrict__ coup, const Spec3D* __restrict__ specs,
-                                                cplx<T>* __restrict__ B, const cplx<T>* __restrict__ qtab) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = 1 << log2N, TT = N / 16;
-  const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
-  const int kx = blockIdx.y, ky = blockIdx.x * LPC + g;
-  cplx<T>* sq = reinterpret_cast<cplx<T>*>(smem_raw);
-  for (int i = threadIdx.x; i < (N >> 2); i += blockDim.x) sq[i] = qtab[i];
-  __syncthreads();
-  const Twiddles<T> tw{sq, log2N - 2};
-  const size_t per_line = (size_t)(N + N / 16) + (size_t)nf * N;
-  cplx<T>* sbuf = sq + (N >> 2) + (size_t)g * per_line;
-  cplx<T>* xh = sbuf + (N + N / 16);  // nf spectra of this column, position t + m*TT
-  const size_t fstride = (size_t)(n + 1) * N * n;
-  const size_t col = ((size_t)kx * N + ky) * n;
-  for (int f = 0; f < nf; ++f) {
-    const cplx<T>* src = B + f * fstride + col;
-    cplx<T> v[16];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = src[t + m * TT];
-#pragma unroll
-    for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
-    fft_line<16, -1, T, true>(v, t, TT, log2N, tw, sbuf);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) xh[(size_t)f * N + t + m * TT] = v[m];
-  }
-  const bool hiy = ky > n;
-  const int fy = hiy ? N - ky : ky;
-  for (int o = 0; o < no; ++o) {
-    cplx<T> y[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) y[m] = {T(0), T(0)};
-    for (int f = 0; f < nf; ++f) {
-      const int s = coup[o * nf + f];
-      if (s < 0) continue;
-      const Spec3D sp = specs[s];
-      const T* S = static_cast<const T*>(sp.data) + ((size_t)kx * (n + 1) + fy) * (n + 1);
-      const bool negy = hiy && sp.oddy;
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int kz = t + m * TT;
-        const bool hiz = kz > n;
-        T sv = __ldg(S + (hiz ? N - kz : kz));
-        if (negy != (hiz && sp.oddz)) sv = -sv;
-        const cplx<T> xv = xh[(size_t)f * N + kz];
-        cplx<T> term;  // i^q * sv * xv
-        switch (sp.q & 3) {
-          case 0: term = {xv.x * sv, xv.y * sv}; break;
-          case 1: term = {-xv.y * sv, xv.x * sv}; break;
-          case 2: term = {-xv.x * sv, -xv.y * sv}; break;
-          default: term = {xv.y * sv, -xv.x * sv}; break;
-        }
-        y[m] = y[m] + term;
-      }
-    }
-    fft_line<16, +1, T, true>(y, t, TT, log2N, tw, sbuf);
-    cplx<T>* dst = B + o * fstride + col;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) dst[t + m * TT] = y[m];
-  }
-}
-
-// inverse y-FFT of (kx, z0 .. z0+ZB-1) for output blockIdx.z; rows y < n
-// written to X[o][kx][z][y].
-template <typename T>
-__global__ void __launch_bounds__(512) k3_yinv(int n, int log2N, int ZB, const cplx<T>* __restrict__ B,
-                                               cplx<T>* __restrict__ X, const cplx<T>* __restrict__ qtab) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = 1 << log2N, TT = N / 16;
-  const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
-  const int kx = blockIdx.y, z0 = blockIdx.x * ZB, o = blockIdx.z;
-  cplx<T>* sq = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* sbuf = sq + (N >> 2);
-  for (int i = threadIdx.x; i < (N >> 2); i += blockDim.x) sq[i] = qtab[i];
-  const cplx<T>* src = B + ((size_t)o * (n + 1) + kx) * (size_t)N * n + z0;
-  cplx<T>* tile = sbuf;
-  for (int i = threadIdx.x; i < N * ZB; i += blockDim.x) {
-    const int ky = i / ZB, zz = i - ky * ZB;
-    tile[(size_t)ky * (ZB + 1) + zz] = src[(size_t)ky * n + zz];
-  }
-  __syncthreads();
-  const Twiddles<T> tw{sq, log2N - 2};
-  cplx<T> v[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = tile[(size_t)(t + m * TT) * (ZB + 1) + g];
-  __syncthreads();
-  fft_line<16, +1, T, true>(v, t, TT, log2N, tw, sbuf + (size_t)g * (N + N / 16));
-  const int64_t plane = (int64_t)n * n;
-  cplx<T>* dst = X + ((size_t)o * (n + 1) + kx) * plane + (size_t)(z0 + g) * n;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) dst[t + m * TT] = v[m];
 }
 
 // out[perm[j]*ncomp + o] = sum_kx c_kx Re(X_o[kx][z][y] e^{+2 pi i kx x/N}) + diag * in
@@ -255,28 +91,38 @@ __global__ void k3_gather(int n, int log2N, int nb, int ncomp, const int32_t* __
 
 // ------------------------------------------------------------------ host
 
-static int pick_zb(int n) { return n >= 16 ? 16 : n; }
-
 size_t buffers3d_bytes(const bem_plan_s* p, int nf) {
   const size_t tb = 2 * prec_bytes(p);
   const int64_t n = p->n, N = p->N;
   return (size_t)nf * (n + 1) * n * n * tb + (size_t)nf * (n + 1) * N * n * tb;
 }
 
+// the line-FFT passes instantiated for this plan's grid size
+template <typename T>
+struct Passes3D {
+  const bem_plan_s* p;
+  template <int L>
+  using K = Fft3DKernels<T, L>;
+  template <class F>
+  auto on(F&& f) const {
+    switch (p->log2N) {
+      case 5: return f(K<5>());
+      case 6: return f(K<6>());
+      case 7: return f(K<7>());
+      case 8: return f(K<8>());
+      case 9: return f(K<9>());
+      default: return f(K<10>());
+    }
+  }
+};
+
 template <typename T>
 static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in, void* out, void* val, void* X,
                              void* B, bool timed, cudaStream_t st) {
-  const int n = (int)p->n, N = (int)p->N, nb = (int)p->nb, log2N = p->log2N;
+  const int n = (int)p->n, nb = (int)p->nb;
   const int tb = 256;
   k3_prep<T><<<dim3((nb + tb - 1) / tb, op.nf), tb, 0, st>>>(nb, p->ncomp, p->d_perm, static_cast<const T*>(in),
                                                               op.d_fields, static_cast<T*>(val));
-  const int64_t total = (int64_t)(n + 1) * n * n;
-  const int xblocks = (int)std::min<int64_t>((total + tb - 1) / tb, 152 * 16);
-  k3_xdft<T><<<dim3(xblocks, op.nf), tb, 0, st>>>(n, log2N, nb, p->d_lptr, p->d_x3, static_cast<const T*>(val),
-                                                   static_cast<const cplx<T>*>(p->d_tw2), static_cast<cplx<T>*>(X));
-  const int TT = N / 16, ZB = pick_zb(n);
-  const size_t sm_y = (size_t)(N / 4) * sizeof(cplx<T>) +
-                      std::max((size_t)ZB * (N + N / 16), (size_t)N * (ZB + 1)) * sizeof(cplx<T>);
   cudaEvent_t e1 = nullptr;
   if (timed) {
     if (p->ev_used + 2 > (int)p->ev_pool.size())
@@ -289,20 +135,16 @@ static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in
     e1 = p->ev_pool[p->ev_used++];
     BEM_CUDA_TRY(cudaEventRecord(e0, st));
   }
-  k3_ypass<T><<<dim3(n / ZB, n + 1, op.nf), ZB * TT, sm_y, st>>>(n, log2N, ZB, static_cast<const cplx<T>*>(X),
-                                                                  static_cast<cplx<T>*>(B),
-                                                                  static_cast<const cplx<T>*>(p->d_qtab));
-  const int LPC = op.lpc;
-  const size_t sm_z = (size_t)(N / 4) * sizeof(cplx<T>) + (size_t)LPC * ((N + N / 16) + (size_t)op.nf * N) * sizeof(cplx<T>);
-  k3_zpass<T><<<dim3(N / LPC, n + 1), LPC * TT, sm_z, st>>>(n, log2N, op.nf, op.no, LPC, op.d_coup, p->d_specs3,
-                                                             static_cast<cplx<T>*>(B),
-                                                             static_cast<const cplx<T>*>(p->d_qtab));
-  k3_yinv<T><<<dim3(n / ZB, n + 1, op.no), ZB * TT, sm_y, st>>>(n, log2N, ZB, static_cast<const cplx<T>*>(B),
-                                                                 static_cast<cplx<T>*>(X),
-                                                                 static_cast<const cplx<T>*>(p->d_qtab));
+  Passes3D<T>{p}.on([&](auto k) {
+    using KK = decltype(k);
+    KK::yfwd(op.nf, nb, p->d_lptr, p->d_x3, val, p->d_tw2, B, p->d_qtab, st);
+    KK::zpass(op.nf, op.no, op.lpc, op.d_coup, p->d_specs3, B, p->d_qtab, st);
+    KK::yinv(op.no, B, X, p->d_qtab, st);
+    return 0;
+  });
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
   k3_gather<T><<<dim3((nb + tb - 1) / tb, op.no), tb, 0, st>>>(
-      n, log2N, nb, p->ncomp, p->d_perm, p->d_x3, p->d_yz3, static_cast<const cplx<T>*>(X),
+      n, p->log2N, nb, p->ncomp, p->d_perm, p->d_x3, p->d_yz3, static_cast<const cplx<T>*>(X),
       static_cast<const cplx<T>*>(p->d_tw2), static_cast<const T*>(op.diag), static_cast<const T*>(in),
       static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
@@ -311,21 +153,15 @@ static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in
 
 template <typename T>
 static bem_status configure3d_t(bem_plan_s* p) {
-  const int n = (int)p->n, N = (int)p->N;
-  const int ZB = pick_zb(n);
-  const size_t sm_y = (size_t)(N / 4) * sizeof(cplx<T>) +
-                      std::max((size_t)ZB * (N + N / 16), (size_t)N * (ZB + 1)) * sizeof(cplx<T>);
   int dev = 0, optin = 0;
   BEM_CUDA_TRY(cudaGetDevice(&dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t sm_y = Passes3D<T>{p}.on([](auto k) { return decltype(k)::smem_y(); });
   if (sm_y > (size_t)optin) {
     set_error("3D grid too large for the shared-memory line buffers");
     return BEM_ERR_UNSUPPORTED;
   }
-  BEM_CUDA_TRY(allow_optin_smem(k3_ypass<T>));
-  BEM_CUDA_TRY(allow_optin_smem(k3_yinv<T>));
-  // every operator's z pass stays within zpass_lpc's budget (<= 200 KB)
-  BEM_CUDA_TRY(allow_optin_smem(k3_zpass<T>));
+  BEM_CUDA_TRY(Passes3D<T>{p}.on([](auto k) { return decltype(k)::configure(); }));
   return BEM_OK;
 }
 
