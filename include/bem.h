@@ -218,8 +218,9 @@ int bem_launches_per_apply(bem_plan_t plan, bem_layer layer);
  * then replays the whole batch with one graph launch.  Inputs and outputs are
  * two packed device buffers owned by the batch (plan i's nb_i*ncomp_i values at
  * element offset bem_batch_offset(i)), so the captured pointers stay valid.
- * The plans must outlive the batch and keep their boundary conditions
- * (BEM_SYSTEM) unchanged; their kernel timing is switched off. */
+ * The plans must outlive the batch; when bem_set_bc changes a plan's system
+ * operator, the next bem_batch_apply captures the graph again.  The plans'
+ * kernel timing is switched off. */
 typedef struct bem_batch_s* bem_batch_t;
 bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count, bem_layer layer, int streams,
                             void* stream);
@@ -228,6 +229,29 @@ bem_status bem_batch_offset(bem_batch_t batch, int i, size_t* offset);
 bem_status bem_batch_apply(bem_batch_t batch, void* stream);
 int bem_batch_launches(bem_batch_t batch);  /* kernel launches inside one replay */
 bem_status bem_batch_destroy(bem_batch_t batch);
+
+/* Solve the boundary-condition systems of every plan of a BEM_SYSTEM batch
+ * together (Section 4's Krylov solve, batched): one restarted GMRES(restart)
+ * runs in lockstep over all systems, each Arnoldi step being one CUDA graph
+ * replay (each plan's preconditioner, the batched apply, classical
+ * Gram-Schmidt with re-orthogonalisation per system, Givens rotations on the
+ * device); a system stops iterating at its own tolerance.  When every plan has
+ * refinement enabled, residuals use the companions (batched too) and the
+ * lockstep GMRES solves for corrections, as in bem_solve.
+ *   bc, data       host, packed like the batch buffers (plan i's nb_i*ncomp_i
+ *                  entries at bem_batch_offset(i)); meaning as in bem_solve;
+ *                  the plans' boundary conditions are set to bc
+ *   x0             host, packed initial guess of the unknowns, or NULL
+ *   u_out, q_out   host, packed (may be NULL)
+ *   info           host array of count entries (per plan), or NULL; iters,
+ *                  restarts and applies are the common lockstep counts
+ *   stream         the solve runs on an internal stream ordered after it and
+ *                  returns when the outputs are on the host
+ * Returns BEM_ERR_NOT_CONVERGED when some system misses tol (outputs and info
+ * are still written), BEM_ERR_UNSUPPORTED for more than 1024 plans. */
+bem_status bem_batch_solve(bem_batch_t batch, const uint8_t* bc, const double* data, double c, double tol,
+                           int max_iter, int restart, const double* x0, double* u_out, double* q_out,
+                           bem_solve_info* info, void* stream);
 
 /* ---- learned initial guess (serving/training pattern on top of the operator;
  * the paper has no learned component) ------------------------------------

@@ -30,7 +30,7 @@ LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
-            "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
+            "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step"]
 
 
@@ -94,7 +94,9 @@ def load_library(path: str = LIB_PATH):
     lib.bem_batch_launches.argtypes = [P]
     lib.bem_batch_launches.restype = I
     lib.bem_batch_destroy.argtypes = [P]
-    for name in ("bem_batch_create", "bem_batch_buffers", "bem_batch_offset", "bem_batch_apply", "bem_batch_destroy"):
+    lib.bem_batch_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
+    for name in ("bem_batch_create", "bem_batch_buffers", "bem_batch_offset", "bem_batch_apply", "bem_batch_destroy",
+                 "bem_batch_solve"):
         getattr(lib, name).restype = I
     lib.bem_net_create.argtypes = [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64]
     lib.bem_net_destroy.argtypes = [P]
@@ -294,6 +296,26 @@ class Batch:
 
     def apply(self, stream=None):
         _check(load_library().bem_batch_apply(self._h, _stream_ptr(stream)))
+
+    def solve(self, bc, data, c=0.5, tol=1e-6, max_iter=2000, restart=100, x0=None, stream=None):
+        """Lockstep GMRES over every plan's system (bem_batch_solve).  bc, data,
+        x0 and the returned u, q are packed like the batch buffers; returns
+        (u, q, [info dict per plan], status)."""
+        bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
+        data = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)
+        if bc.size != self.total or data.size != self.total:
+            raise ValueError("bc and data must hold the batch's packed total of values")
+        u = np.empty(self.total)
+        q = np.empty(self.total)
+        x0p = None
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+            x0p = _ptr(x0)
+        infos = (SolveInfo * len(self.plans))()
+        rc = load_library().bem_batch_solve(self._h, _ptr(bc), _ptr(data), float(c), float(tol), int(max_iter),
+                                            int(restart), x0p, _ptr(u), _ptr(q), infos, _stream_ptr(stream))
+        _check(rc, (BEM_ERR_NOT_CONVERGED,))
+        return u, q, [i.as_dict() for i in infos], rc
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -5,31 +5,85 @@
 // single graph launch per batched apply (no per-kernel launch overhead).
 // Inputs and outputs live in two packed device buffers owned by the batch
 // (segment of plan i at offset[i], nb_i * ncomp_i values of the common
-// precision).
+// precision).  When bem_set_bc has rebuilt a plan's system operator since the
+// capture, the next apply captures the graph again.
 #include <vector>
 
 #include "bem_internal.h"
 
-struct bem_batch_s {
-  std::vector<bem_plan_t> plans;
-  std::vector<size_t> offset;  // element offsets into the packed buffers
-  size_t total = 0;
-  int prec = 0;
-  void* d_in = nullptr;
-  void* d_out = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> events;
-  int launches = 0;
-};
-
 using namespace bemfft;
+
+namespace bemfft {
+
+bem_status batch_issue_applies(bem_batch_s* b, const void* in, void* out, cudaStream_t cap) {
+  const int S = b->nstreams;
+  const size_t tb = prec_bytes(b->plans[0]);
+  bem_status rc = BEM_OK;
+  BEM_CUDA_TRY(cudaEventRecord(b->events[0], cap));
+  for (int s = 1; s < S; ++s) BEM_CUDA_TRY(cudaStreamWaitEvent(b->side[s], b->events[0], 0));
+  for (size_t i = 0; i < b->plans.size() && rc == BEM_OK; ++i) {
+    cudaStream_t s = i % S == 0 ? cap : b->side[i % S];
+    const unsigned char* pin = static_cast<const unsigned char*>(in) + b->offset[i] * tb;
+    unsigned char* pout = static_cast<unsigned char*>(out) + b->offset[i] * tb;
+    rc = apply_operator(b->plans[i], b->layer, pin, pout, s);
+  }
+  for (int s = 1; s < S; ++s) {
+    BEM_CUDA_TRY(cudaEventRecord(b->events[S + s], b->side[s]));
+    BEM_CUDA_TRY(cudaStreamWaitEvent(cap, b->events[S + s], 0));
+  }
+  return rc;
+}
+
+bem_status batch_capture(bem_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->launches = 0;
+  cudaStream_t cap = b->side[0];
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    set_error("bem_batch: stream capture failed to begin");
+    return BEM_ERR_CUDA;
+  }
+  bem_status rc = batch_issue_applies(b, b->d_in, b->d_out, cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  if (rc != BEM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || !g) {
+    set_error(std::string("bem_batch: capture failed: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    set_error("bem_batch: graph instantiation failed");
+    return BEM_ERR_CUDA;
+  }
+  b->versions.clear();
+  for (auto* p : b->plans) {
+    b->versions.push_back(p->op_version);
+    b->launches += bem_launches_per_apply(p, b->layer);
+  }
+  return BEM_OK;
+}
+
+bem_status batch_refresh(bem_batch_s* b) {
+  if (b->layer != BEM_SYSTEM) return BEM_OK;
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if (b->plans[i]->op_version != b->versions[i]) return batch_capture(b);
+  return BEM_OK;
+}
+
+}  // namespace bemfft
 
 extern "C" {
 
 bem_status bem_batch_destroy(bem_batch_t b) {
   if (!b) return BEM_OK;
+  batch_solve_free(b);
+  if (b->companions) bem_batch_destroy(b->companions);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto s : b->side) cudaStreamDestroy(s);
@@ -44,6 +98,10 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
                             void* stream) {
   if (!out || !plans || count < 1 || streams < 1 || streams > 16) {
     set_error("bem_batch_create: need plans, count >= 1 and 1 <= streams <= 16");
+    return BEM_ERR_ARG;
+  }
+  if (layer != BEM_SINGLE && layer != BEM_DOUBLE && layer != BEM_SYSTEM) {
+    set_error("bem_batch_create: unknown layer");
     return BEM_ERR_ARG;
   }
   *out = nullptr;
@@ -64,11 +122,14 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
   }
   auto* b = new bem_batch_s();
   b->prec = plans[0]->prec;
+  b->layer = layer;
+  b->nstreams = streams;
   for (int i = 0; i < count; ++i) {
     b->plans.push_back(plans[i]);
     b->offset.push_back(b->total);
     b->total += (size_t)plans[i]->nb * plans[i]->ncomp;
   }
+  b->offset.push_back(b->total);
   const size_t tb = prec_bytes(plans[0]);
   auto fail = [&](bem_status rc) {
     bem_batch_destroy(b);
@@ -80,14 +141,7 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
   }
   cudaMemset(b->d_in, 0, b->total * tb);
   cudaMemset(b->d_out, 0, b->total * tb);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaStream_t cap = nullptr;
-  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
-    set_error("bem_batch_create: stream creation failed");
-    return fail(BEM_ERR_CUDA);
-  }
-  b->side.push_back(cap);
-  for (int s = 1; s < streams; ++s) {
+  for (int s = 0; s < streams; ++s) {
     cudaStream_t x;
     if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
       set_error("bem_batch_create: stream creation failed");
@@ -103,41 +157,9 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
     }
     b->events.push_back(e);
   }
-  // capture: fork the side streams off the capture stream, apply, join
-  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    set_error("bem_batch_create: stream capture failed to begin");
-    return fail(BEM_ERR_CUDA);
-  }
-  bem_status rc = BEM_OK;
-  cudaEventRecord(b->events[0], cap);
-  for (int s = 1; s < streams; ++s) cudaStreamWaitEvent(b->side[s], b->events[0], 0);
-  for (int i = 0; i < count && rc == BEM_OK; ++i) {
-    cudaStream_t s = b->side[i % streams];
-    const unsigned char* in = static_cast<const unsigned char*>(b->d_in) + b->offset[i] * tb;
-    unsigned char* o = static_cast<unsigned char*>(b->d_out) + b->offset[i] * tb;
-    rc = apply_operator(plans[i], layer, in, o, s);
-    b->launches += bem_launches_per_apply(plans[i], layer);
-  }
-  for (int s = 1; s < streams; ++s) {
-    cudaEventRecord(b->events[streams + s], b->side[s]);
-    cudaStreamWaitEvent(cap, b->events[streams + s], 0);
-  }
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(cap, &g);
-  if (rc != BEM_OK) {
-    if (g) cudaGraphDestroy(g);
-    return fail(rc);
-  }
-  if (e != cudaSuccess || !g) {
-    set_error(std::string("bem_batch_create: capture failed: ") + cudaGetErrorString(e));
-    return fail(BEM_ERR_CUDA);
-  }
-  b->graph = g;
-  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
-    set_error("bem_batch_create: graph instantiation failed");
-    return fail(BEM_ERR_CUDA);
-  }
-  (void)st;
+  bem_status rc = batch_capture(b);
+  if (rc != BEM_OK) return fail(rc);
+  (void)stream;
   *out = b;
   return BEM_OK;
 }
@@ -167,6 +189,8 @@ bem_status bem_batch_apply(bem_batch_t b, void* stream) {
     set_error("bem_batch_apply: null batch");
     return BEM_ERR_ARG;
   }
+  bem_status rc = batch_refresh(b);
+  if (rc != BEM_OK) return rc;
   BEM_CUDA_TRY(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
   return BEM_OK;
 }

@@ -178,6 +178,29 @@ struct bem_plan_s {
   bem_plan_s* companion = nullptr;  // FP64 plan of the same geometry for refinement residuals
   void* d_tin = nullptr;    // plan-precision in/out buffers for the apply
   void* d_tout = nullptr;
+  uint64_t op_version = 0;  // bumped whenever bem_set_bc rebuilds the system operator
+};
+
+// Batch of plans applied through one CUDA graph (batch.cu); the batched
+// GMRES (gmres.cu) keeps its workspace here too.
+struct BatchSolveWs;
+struct bem_batch_s {
+  std::vector<bem_plan_s*> plans;
+  std::vector<uint64_t> versions;  // plans' operator versions at capture
+  std::vector<size_t> offset;      // count + 1 element offsets into the packed buffers
+  size_t total = 0;
+  int prec = 0;
+  bem_layer layer = BEM_SINGLE;
+  int nstreams = 1;
+  void* d_in = nullptr;
+  void* d_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> side;  // side[0] is the capture stream
+  std::vector<cudaEvent_t> events;
+  int launches = 0;
+  BatchSolveWs* ws = nullptr;
+  bem_batch_s* companions = nullptr;  // batch over the plans' refinement companions (solve only)
 };
 
 namespace bemfft {
@@ -212,6 +235,13 @@ struct ScratchPtrs {
 void carve_scratch(const bem_plan_s* p, const Operator& op, void* base, ScratchPtrs* sp);
 bem_status launch_apply_2d_with(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
                                 bool timed, cudaStream_t st);
+// batch.cu: issue the applies of every plan of the batch from `in` to `out`
+// (packed) on the batch's side streams, forked from and joined back into
+// `cap`, which is being captured; (re)capture of the batch's own graph
+bem_status batch_issue_applies(bem_batch_s* b, const void* in, void* out, cudaStream_t cap);
+bem_status batch_capture(bem_batch_s* b);
+bem_status batch_refresh(bem_batch_s* b);  // re-capture when a plan's operator changed
+void batch_solve_free(bem_batch_s* b);     // gmres.cu
 // gmres.cu
 bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
                        int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,

@@ -395,6 +395,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     }
   if (p->have_bc && c == p->c && std::equal(p->h_bc.begin(), p->h_bc.end(), bc)) return BEM_OK;
   free_operator(p->op_system);
+  ++p->op_version;
   p->h_bc.assign(bc, bc + nb * p->ncomp);
   p->c = c;
   Operator& s = p->op_system;

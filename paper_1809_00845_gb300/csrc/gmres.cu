@@ -344,9 +344,21 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
   k_split_known<<<blocks_for(M, 256), 256, 0, st>>>(d_data, d_bc, d_um, d_qm, M);
   // b = c um - sigma K2 um - K1 qm,  sigma K2 = +D (Laplace) or -T (Kelvin)
   const double sigma = p->kernel == BEM_KELVIN_3D ? -1.0 : 1.0;
-  if ((rc = gr.apply(BEM_DOUBLE, d_um, d_b)) != BEM_OK) return rc;
-  if ((rc = gr.apply(BEM_SINGLE, d_qm, d_w)) != BEM_OK) return rc;
-  applies += 2;
+  // an apply of an all-zero density (no Dirichlet or no Neumann entries) is skipped
+  int64_t nneu = 0;
+  for (int64_t i = 0; i < M; ++i) nneu += bc[i] != 0;
+  if (nneu < M) {
+    if ((rc = gr.apply(BEM_DOUBLE, d_um, d_b)) != BEM_OK) return rc;
+    ++applies;
+  } else {
+    BEM_CUDA_TRY(cudaMemsetAsync(d_b, 0, M * sizeof(double), st));
+  }
+  if (nneu > 0) {
+    if ((rc = gr.apply(BEM_SINGLE, d_qm, d_w)) != BEM_OK) return rc;
+    ++applies;
+  } else {
+    BEM_CUDA_TRY(cudaMemsetAsync(d_w, 0, M * sizeof(double), st));
+  }
   k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, -sigma, d_b, M);  // b = -sigma K2 um - K1 qm
   k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(c, d_um, 1.0, d_b, M);       // b += c um
   if (x0)
@@ -378,11 +390,15 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     // corrections from the preconditioned low-precision GMRES.
     double best = INFINITY;
     int stagnant = 0;
+    bool x_zero = x0 == nullptr;  // the first residual of a zero start is b itself
     for (;;) {
-      if ((rc = gr.apply(BEM_SYSTEM, d_x, d_w)) != BEM_OK) return rc;
-      ++applies;
       BEM_CUDA_TRY(cudaMemcpyAsync(d_r, d_b, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, 1.0, d_r, M);
+      if (!x_zero) {
+        if ((rc = gr.apply(BEM_SYSTEM, d_x, d_w)) != BEM_OK) return rc;
+        ++applies;
+        k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, 1.0, d_r, M);
+      }
+      x_zero = false;
       double r2 = 0.0;
       g.dots(d_r, M, 1, d_r, d_h, false);
       BEM_CUDA_TRY(cudaMemcpyAsync(&r2, d_h, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -447,3 +463,596 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
 }
 
 }  // namespace bemfft
+
+// ======================================================================
+// Batched solve: the boundary-condition systems of every plan of a batch,
+// solved together by one GMRES running in lockstep (a common Arnoldi index j
+// for all systems).  Each Arnoldi step - preconditioner, the batched apply of
+// all operators, two classical Gram-Schmidt sweeps, the norms, the next basis
+// vectors and the Givens rotations of every system - is one CUDA graph, with
+// j kept on the device, so the host replays the same graph every step and
+// reads back one integer (the number of systems still iterating).  Vectors are
+// packed like the batch buffers (system s at offset[s]); every reduction runs
+// per system in a fixed order.
+
+struct BatchSolveWs {
+  int K = 0, m = 0;
+  int64_t Mt = 0;
+  double *V = nullptr, *vin = nullptr, *zz = nullptr, *w = nullptr, *x = nullptr, *b = nullptr, *r = nullptr,
+         *d = nullptr, *e = nullptr, *rhs = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *nrm = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
+         *y = nullptr, *bnorm = nullptr, *tolv = nullptr, *relest = nullptr;
+  int *jdev = nullptr, *jstop = nullptr, *active = nullptr;
+  int64_t* off = nullptr;
+  int32_t* sys = nullptr;
+  int* h_active = nullptr;  // pinned
+  cudaStream_t st = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> versions;  // plan operator versions the graph was captured with
+  std::vector<void*> allocs;
+};
+
+namespace bemfft {
+
+void batch_solve_free(bem_batch_s* bt) {
+  BatchSolveWs* W = bt->ws;
+  if (!W) return;
+  if (W->exec) cudaGraphExecDestroy(W->exec);
+  if (W->graph) cudaGraphDestroy(W->graph);
+  for (void* a : W->allocs) cudaFree(a);
+  if (W->h_active) cudaFreeHost(W->h_active);
+  if (W->st) cudaStreamDestroy(W->st);
+  delete W;
+  bt->ws = nullptr;
+}
+
+// dst = V[*j]
+__global__ void k_b_copy_vj(const double* __restrict__ V, int64_t Mt, const int* __restrict__ jdev,
+                            double* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Mt) dst[i] = V[(int64_t)(*jdev) * Mt + i];
+}
+
+// out[s*ldo + k] = <V_k, w> over the segment of system s, for k < nvec
+// (nvec = *jdev + 1, or nfix when jdev is null); one block per (k, s)
+__global__ void k_b_dots(const double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev, int nfix,
+                         const double* __restrict__ w, const int64_t* __restrict__ off, double* __restrict__ out,
+                         int ldo) {
+  __shared__ double red[kDotThreads / 32];
+  const int k = blockIdx.x, s = blockIdx.y;
+  const int nvec = jdev ? *jdev + 1 : nfix;
+  if (k >= nvec) return;
+  const double* a = V + (int64_t)k * ldv;
+  double acc = 0.0;
+  for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += kDotThreads) acc += a[i] * w[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < kDotThreads / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[(int64_t)s * ldo + k] = acc;
+  }
+}
+
+// w[i] -= sum_{k <= *j} V[k][i] h[sys(i)][k]
+__global__ void k_b_sub(const double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev,
+                        const int32_t* __restrict__ sys, const double* __restrict__ h, int ldh,
+                        double* __restrict__ w, int64_t Mt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Mt) return;
+  const int nvec = *jdev + 1;
+  const double* hs = h + (int64_t)sys[i] * ldh;
+  double acc = w[i];
+  for (int k = 0; k < nvec; ++k) acc -= V[(int64_t)k * ldv + i] * hs[k];
+  w[i] = acc;
+}
+
+// V[*j + 1] = w / |w|_sys (zero when the norm is zero or not finite)
+__global__ void k_b_next(const double* __restrict__ w, const double* __restrict__ nrm2,
+                         const int32_t* __restrict__ sys, double* __restrict__ V, int64_t ldv,
+                         const int* __restrict__ jdev, int m, int64_t Mt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Mt) return;
+  const int j = *jdev;
+  if (j >= m) return;
+  const double s = sqrt(nrm2[sys[i]]);
+  V[(int64_t)(j + 1) * ldv + i] = (s > 0.0 && isfinite(s)) ? w[i] / s : 0.0;
+}
+
+// Per system (one thread each): the new Hessenberg column from the two
+// Gram-Schmidt sweeps and the norm, the earlier rotations, a new rotation,
+// the residual estimate and the stop test; then j advances.
+__global__ void k_b_givens(int K, int m, int* __restrict__ jdev, const double* __restrict__ h1,
+                           const double* __restrict__ h2, int ldh, const double* __restrict__ nrm2,
+                           double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                           double* __restrict__ g, const double* __restrict__ bnorm, const double* __restrict__ tolv,
+                           int* __restrict__ jstop, double* __restrict__ relest, int* __restrict__ active) {
+  const int s = threadIdx.x;
+  const int j = *jdev;
+  int live = 0;
+  if (s < K && j < m && jstop[s] < 0) {
+    double* col = H + ((int64_t)s * m + j) * (m + 1);
+    double* c = cs + (int64_t)s * m;
+    double* sv = sn + (int64_t)s * m;
+    double* gv = g + (int64_t)s * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = h1[(int64_t)s * ldh + i] + h2[(int64_t)s * ldh + i];
+    const double hn = sqrt(nrm2[s]);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = col[i], bb = col[i + 1];
+      col[i] = c[i] * a + sv[i] * bb;
+      col[i + 1] = -sv[i] * a + c[i] * bb;
+    }
+    const double a = col[j], bb = col[j + 1];
+    const double r = hypot(a, bb);
+    c[j] = r > 0 ? a / r : 1.0;
+    sv[j] = r > 0 ? bb / r : 0.0;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    gv[j + 1] = -sv[j] * gv[j];
+    gv[j] = c[j] * gv[j];
+    const double rel = bnorm[s] > 0 ? fabs(gv[j + 1]) / bnorm[s] : 0.0;
+    relest[s] = rel;
+    if (!(rel > tolv[s]) || !(hn > 1e-14 * bnorm[s]) || j + 1 == m) jstop[s] = j + 1;
+    else live = 1;
+  }
+  const int n_live = __syncthreads_count(live);
+  if (s == 0) {
+    *active = n_live;
+    if (j < m) *jdev = j + 1;
+  }
+}
+
+// y_s = H_s^{-1} g_s over the system's own number of columns
+__global__ void k_b_backsolve(int K, int m, const int* __restrict__ jdev, const int* __restrict__ jstop,
+                              const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= K) return;
+  const int nj = jstop[s] >= 0 ? jstop[s] : *jdev;
+  const double* Hs = H + (int64_t)s * m * (m + 1);
+  double* ys = y + (int64_t)s * m;
+  for (int i = nj - 1; i >= 0; --i) {
+    double acc = g[(int64_t)s * (m + 1) + i];
+    for (int k = i + 1; k < nj; ++k) acc -= Hs[(int64_t)k * (m + 1) + i] * ys[k];
+    const double dia = Hs[(int64_t)i * (m + 1) + i];
+    ys[i] = dia != 0.0 ? acc / dia : 0.0;
+  }
+}
+
+// out[i] = sum_{k < ncols(sys)} V[k][i] y[sys][k]
+__global__ void k_b_combine(const double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev,
+                            const int* __restrict__ jstop, const int32_t* __restrict__ sys,
+                            const double* __restrict__ y, int m, double* __restrict__ out, int64_t Mt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Mt) return;
+  const int s = sys[i];
+  const int nj = jstop[s] >= 0 ? jstop[s] : *jdev;
+  double acc = 0.0;
+  for (int k = 0; k < nj; ++k) acc += V[(int64_t)k * ldv + i] * y[(int64_t)s * m + k];
+  out[i] = acc;
+}
+
+// V0 = (rhs - w) / beta_sys, zero for systems that need no iteration
+__global__ void k_b_start(const double* __restrict__ rhs, const double* __restrict__ w,
+                          const double* __restrict__ beta2, const int* __restrict__ jstop,
+                          const int32_t* __restrict__ sys, double* __restrict__ V0, int64_t Mt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Mt) return;
+  const int s = sys[i];
+  const double bt = sqrt(beta2[s]);
+  V0[i] = (jstop[s] < 0 && bt > 0.0) ? (rhs[i] - w[i]) / bt : 0.0;
+}
+
+namespace {
+
+template <typename T>
+bem_status dalloc(BatchSolveWs& W, T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    set_error("bem_batch_solve: out of device memory");
+    return BEM_ERR_OOM;
+  }
+  W.allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return BEM_OK;
+}
+
+// z = M^-1 v on every system's segment (the plans' own preconditioners)
+void batch_precond(bem_batch_s* bt, const double* v, double* z, cudaStream_t st) {
+  for (size_t i = 0; i < bt->plans.size(); ++i) {
+    bem_plan_s* p = bt->plans[i];
+    const int64_t o = (int64_t)bt->offset[i], M = (int64_t)(bt->offset[i + 1] - bt->offset[i]);
+    if (p->pc.kind == 0) {
+      cudaMemcpyAsync(z + o, v + o, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    } else {
+      const int mb = p->pc.bs * p->ncomp;
+      k_block_apply<<<p->pc.nblocks, mb, mb * sizeof(double), st>>>(p->pc.d_inv, mb, M, v + o, z + o);
+    }
+  }
+}
+
+// w = A v for all systems with the batch's operators (FP64 vectors)
+bem_status batch_apply_f64(bem_batch_s* bt, const double* v, double* w, cudaStream_t st, bool replay) {
+  const int64_t Mt = (int64_t)bt->total;
+  if (bt->prec == BEM_F32)
+    k_convert<double, float><<<blocks_for(Mt, 256), 256, 0, st>>>(v, static_cast<float*>(bt->d_in), Mt);
+  else
+    BEM_CUDA_TRY(cudaMemcpyAsync(bt->d_in, v, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (replay) {
+    BEM_CUDA_TRY(cudaGraphLaunch(bt->exec, st));
+  } else {
+    bem_status rc = batch_issue_applies(bt, bt->d_in, bt->d_out, st);
+    if (rc != BEM_OK) return rc;
+  }
+  if (bt->prec == BEM_F32)
+    k_convert<float, double><<<blocks_for(Mt, 256), 256, 0, st>>>(static_cast<const float*>(bt->d_out), w, Mt);
+  else
+    BEM_CUDA_TRY(cudaMemcpyAsync(w, bt->d_out, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return BEM_OK;
+}
+
+// per-system squared norms of v into W.nrm (device) and `out` (host)
+bem_status seg_norms(BatchSolveWs& W, const double* v, std::vector<double>& out) {
+  cudaStream_t st = W.st;
+  k_b_dots<<<dim3(1, W.K), kDotThreads, 0, st>>>(v, W.Mt, nullptr, 1, v, W.off, W.nrm, 1);
+  out.resize(W.K);
+  BEM_CUDA_TRY(cudaMemcpyAsync(out.data(), W.nrm, W.K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return BEM_OK;
+}
+
+// The Arnoldi step graph: vin = V[j]; zz = M^-1 vin; w = A zz; CGS2; norms;
+// V[j+1]; Givens; active count to the host.
+bem_status capture_arnoldi(bem_batch_s* bt, BatchSolveWs& W) {
+  if (W.exec) cudaGraphExecDestroy(W.exec);
+  if (W.graph) cudaGraphDestroy(W.graph);
+  W.exec = nullptr;
+  W.graph = nullptr;
+  const int64_t Mt = W.Mt;
+  const int K = W.K, m = W.m, ldh = m + 1;
+  cudaStream_t cs = W.st;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    set_error("bem_batch_solve: stream capture failed to begin");
+    return BEM_ERR_CUDA;
+  }
+  k_b_copy_vj<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.V, Mt, W.jdev, W.vin);
+  batch_precond(bt, W.vin, W.zz, cs);
+  bem_status rc = batch_apply_f64(bt, W.zz, W.w, cs, false);
+  if (rc == BEM_OK) {
+    const dim3 gd(m + 1, K);
+    k_b_dots<<<gd, kDotThreads, 0, cs>>>(W.V, Mt, W.jdev, 0, W.w, W.off, W.h1, ldh);
+    k_b_sub<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.V, Mt, W.jdev, W.sys, W.h1, ldh, W.w, Mt);
+    k_b_dots<<<gd, kDotThreads, 0, cs>>>(W.V, Mt, W.jdev, 0, W.w, W.off, W.h2, ldh);
+    k_b_sub<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.V, Mt, W.jdev, W.sys, W.h2, ldh, W.w, Mt);
+    k_b_dots<<<dim3(1, K), kDotThreads, 0, cs>>>(W.w, Mt, nullptr, 1, W.w, W.off, W.nrm, 1);
+    k_b_next<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.w, W.nrm, W.sys, W.V, Mt, W.jdev, m, Mt);
+    k_b_givens<<<1, ((K + 31) / 32) * 32, 0, cs>>>(K, m, W.jdev, W.h1, W.h2, ldh, W.nrm, W.H, W.cs, W.sn, W.g,
+                                                   W.bnorm, W.tolv, W.jstop, W.relest, W.active);
+    cudaMemcpyAsync(W.h_active, W.active, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  }
+  cudaGraph_t gph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &gph);
+  if (rc != BEM_OK) {
+    if (gph) cudaGraphDestroy(gph);
+    return rc;
+  }
+  if (e != cudaSuccess || !gph) {
+    set_error(std::string("bem_batch_solve: capture failed: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  W.graph = gph;
+  if (cudaGraphInstantiate(&W.exec, gph, 0) != cudaSuccess) {
+    set_error("bem_batch_solve: graph instantiation failed");
+    return BEM_ERR_CUDA;
+  }
+  W.versions.clear();
+  for (auto* p : bt->plans) W.versions.push_back(p->op_version);
+  return BEM_OK;
+}
+
+struct BatchCounters {
+  int iters = 0, restarts = 0, applies = 0;
+};
+
+// Lockstep GMRES(m) on A x = rhs (per system: stop when |rhs - A x| <=
+// tol_s * rn_s, recomputed with A at every restart).  x is updated in place;
+// rel[s] holds the last recomputed relative residual.
+bem_status batch_gmres(bem_batch_s* bt, BatchSolveWs& W, const double* rhs, const std::vector<double>& rn,
+                       double* x, const std::vector<double>& tols, int max_iter, BatchCounters* cnt,
+                       std::vector<double>& rel) {
+  const int K = W.K, m = W.m;
+  const int64_t Mt = W.Mt;
+  cudaStream_t st = W.st;
+  BEM_CUDA_TRY(cudaMemcpyAsync(W.bnorm, rn.data(), K * sizeof(double), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(W.tolv, tols.data(), K * sizeof(double), cudaMemcpyHostToDevice, st));
+  std::vector<double> beta2;
+  std::vector<int> jstop(K);
+  std::vector<double> g0((size_t)K * (m + 1), 0.0);
+  std::vector<double> best(K, INFINITY);
+  std::vector<int> stagnant(K, 0);
+  rel.assign(K, 1.0);
+  for (;;) {
+    bem_status rc = batch_apply_f64(bt, x, W.w, st, true);
+    if (rc != BEM_OK) return rc;
+    ++cnt->applies;
+    // r = rhs - A x, per-system norms
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.r, rhs, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(-1.0, W.w, 1.0, W.r, Mt);
+    if ((rc = seg_norms(W, W.r, beta2)) != BEM_OK) return rc;
+    int live = 0;
+    for (int s = 0; s < K; ++s) {
+      const double b = std::sqrt(beta2[s]);
+      rel[s] = rn[s] > 0 ? b / rn[s] : 0.0;
+      bool go = std::isfinite(rel[s]) && rel[s] > tols[s];
+      if (go) {
+        if (rel[s] < best[s] * 0.999) {
+          best[s] = rel[s];
+          stagnant[s] = 0;
+        } else if (++stagnant[s] >= 3) {
+          go = false;  // precision floor of the apply
+        }
+      }
+      jstop[s] = go ? -1 : 0;
+      g0[(size_t)s * (m + 1)] = b;
+      live += go;
+    }
+    if (live == 0 || cnt->iters >= max_iter) return BEM_OK;
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.jstop, jstop.data(), K * sizeof(int), cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.g, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    BEM_CUDA_TRY(cudaMemsetAsync(W.jdev, 0, sizeof(int), st));
+    // V0 = r / beta (W.r already holds rhs - A x; pass a zero w)
+    BEM_CUDA_TRY(cudaMemsetAsync(W.w, 0, Mt * sizeof(double), st));
+    k_b_start<<<blocks_for(Mt, 256), 256, 0, st>>>(W.r, W.w, W.nrm, W.jstop, W.sys, W.V, Mt);
+    for (int j = 0; j < m && cnt->iters < max_iter; ++j) {
+      BEM_CUDA_TRY(cudaGraphLaunch(W.exec, st));
+      BEM_CUDA_TRY(cudaStreamSynchronize(st));
+      ++cnt->iters;
+      ++cnt->applies;
+      if (*W.h_active == 0) break;
+    }
+    k_b_backsolve<<<blocks_for(K, 64), 64, 0, st>>>(K, m, W.jdev, W.jstop, W.H, W.g, W.y);
+    k_b_combine<<<blocks_for(Mt, 256), 256, 0, st>>>(W.V, Mt, W.jdev, W.jstop, W.sys, W.y, m, W.d, Mt);
+    batch_precond(bt, W.d, W.zz, st);
+    k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(1.0, W.zz, 1.0, x, Mt);
+    ++cnt->restarts;
+  }
+}
+
+}  // namespace
+
+}  // namespace bemfft
+
+using namespace bemfft;
+
+extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const double* data, double c, double tol,
+                                      int max_iter, int restart, const double* x0, double* u_out, double* q_out,
+                                      bem_solve_info* info, void* stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!bt || !bc || !data) {
+    set_error("bem_batch_solve: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  if (bt->layer != BEM_SYSTEM) {
+    set_error("bem_batch_solve: the batch must apply BEM_SYSTEM");
+    return BEM_ERR_ARG;
+  }
+  if (restart < 1 || restart > 512 || max_iter < 0 || !(tol > 0.0)) {
+    set_error("bem_batch_solve: need 1 <= restart <= 512, max_iter >= 0, tol > 0");
+    return BEM_ERR_ARG;
+  }
+  const int K = (int)bt->plans.size();
+  if (K > 1024) {
+    set_error("bem_batch_solve: at most 1024 systems");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  const bool refine = bt->plans[0]->companion != nullptr;
+  for (auto* p : bt->plans)
+    if ((p->companion != nullptr) != refine) {
+      set_error("bem_batch_solve: either every plan or none has refinement enabled");
+      return BEM_ERR_ARG;
+    }
+  const int64_t Mt = (int64_t)bt->total;
+  cudaStream_t ust = static_cast<cudaStream_t>(stream);
+  bem_status rc;
+  // boundary conditions, preconditioners, graphs
+  for (int s = 0; s < K; ++s) {
+    bem_plan_s* p = bt->plans[s];
+    if ((rc = bem_set_bc(p, bc + bt->offset[s], c)) != BEM_OK) return rc;
+    if (refine && (rc = bem_set_bc(p->companion, bc + bt->offset[s], c)) != BEM_OK) return rc;
+    if ((rc = build_preconditioner(p)) != BEM_OK) return rc;
+  }
+  if ((rc = batch_refresh(bt)) != BEM_OK) return rc;
+  if (refine) {
+    bool fresh = bt->companions == nullptr;
+    if (!fresh)
+      for (int s = 0; s < K; ++s) fresh = fresh || bt->companions->plans[s] != bt->plans[s]->companion;
+    if (fresh) {
+      if (bt->companions) bem_batch_destroy(bt->companions);
+      bt->companions = nullptr;
+      std::vector<bem_plan_t> cp;
+      for (auto* p : bt->plans) cp.push_back(p->companion);
+      if ((rc = bem_batch_create(&bt->companions, cp.data(), K, BEM_SYSTEM, bt->nstreams, nullptr)) != BEM_OK)
+        return rc;
+    } else if ((rc = batch_refresh(bt->companions)) != BEM_OK) {
+      return rc;
+    }
+  }
+  // workspace
+  const int m = restart;
+  BatchSolveWs* W = bt->ws;
+  if (!W || W->m != m) {
+    batch_solve_free(bt);
+    W = bt->ws = new BatchSolveWs();
+    W->K = K;
+    W->m = m;
+    W->Mt = Mt;
+    if (cudaStreamCreateWithFlags(&W->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&W->h_active, sizeof(int)) != cudaSuccess) {
+      set_error("bem_batch_solve: stream or pinned memory creation failed");
+      batch_solve_free(bt);
+      return BEM_ERR_CUDA;
+    }
+    bool ok = dalloc(*W, &W->V, (size_t)(m + 1) * Mt) == BEM_OK;
+    for (double** v : {&W->vin, &W->zz, &W->w, &W->x, &W->b, &W->r, &W->d, &W->e, &W->rhs})
+      ok = ok && dalloc(*W, v, Mt) == BEM_OK;
+    ok = ok && dalloc(*W, &W->h1, (size_t)K * (m + 1)) == BEM_OK && dalloc(*W, &W->h2, (size_t)K * (m + 1)) == BEM_OK;
+    ok = ok && dalloc(*W, &W->nrm, K) == BEM_OK && dalloc(*W, &W->H, (size_t)K * m * (m + 1)) == BEM_OK;
+    ok = ok && dalloc(*W, &W->cs, (size_t)K * m) == BEM_OK && dalloc(*W, &W->sn, (size_t)K * m) == BEM_OK;
+    ok = ok && dalloc(*W, &W->g, (size_t)K * (m + 1)) == BEM_OK && dalloc(*W, &W->y, (size_t)K * m) == BEM_OK;
+    ok = ok && dalloc(*W, &W->bnorm, K) == BEM_OK && dalloc(*W, &W->tolv, K) == BEM_OK &&
+         dalloc(*W, &W->relest, K) == BEM_OK;
+    ok = ok && dalloc(*W, &W->jdev, 1) == BEM_OK && dalloc(*W, &W->jstop, K) == BEM_OK &&
+         dalloc(*W, &W->active, 1) == BEM_OK;
+    ok = ok && dalloc(*W, &W->off, K + 1) == BEM_OK && dalloc(*W, &W->sys, Mt) == BEM_OK;
+    if (!ok) {
+      batch_solve_free(bt);
+      return BEM_ERR_OOM;
+    }
+    std::vector<int64_t> off(bt->offset.begin(), bt->offset.end());
+    std::vector<int32_t> sys(Mt);
+    for (int s = 0; s < K; ++s)
+      for (size_t i = bt->offset[s]; i < bt->offset[s + 1]; ++i) sys[i] = s;
+    BEM_CUDA_TRY(cudaMemcpy(W->off, off.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    BEM_CUDA_TRY(cudaMemcpy(W->sys, sys.data(), Mt * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  bool recap = W->exec == nullptr;
+  for (int s = 0; s < K && !recap; ++s) recap = W->versions[s] != bt->plans[s]->op_version;
+  if (recap && (rc = capture_arnoldi(bt, *W)) != BEM_OK) return rc;
+  cudaStream_t st = W->st;
+  // the solve runs on its own stream, ordered after the caller's stream
+  cudaEvent_t ev;
+  BEM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  BEM_CUDA_TRY(cudaEventRecord(ev, ust));
+  BEM_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+  cudaEventDestroy(ev);
+
+  // right-hand sides b = c um - sigma K2 um - K1 qm with the residual operators
+  std::vector<double> um(Mt), qm(Mt);
+  for (int64_t i = 0; i < Mt; ++i) {
+    um[i] = bc[i] ? 0.0 : data[i];
+    qm[i] = bc[i] ? data[i] : 0.0;
+  }
+  BEM_CUDA_TRY(cudaMemcpyAsync(W->vin, um.data(), Mt * sizeof(double), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(W->zz, qm.data(), Mt * sizeof(double), cudaMemcpyHostToDevice, st));
+  // per plan on the batch's side streams (fork from st, join back); an apply
+  // of an all-zero density is skipped
+  BEM_CUDA_TRY(cudaMemsetAsync(W->b, 0, Mt * sizeof(double), st));
+  BEM_CUDA_TRY(cudaMemsetAsync(W->w, 0, Mt * sizeof(double), st));
+  const int S = bt->nstreams;
+  BEM_CUDA_TRY(cudaEventRecord(bt->events[0], st));
+  for (int k = 1; k < S; ++k) BEM_CUDA_TRY(cudaStreamWaitEvent(bt->side[k], bt->events[0], 0));
+  int rhs_applies = 0;
+  for (int s = 0; s < K; ++s) {
+    bem_plan_s* R = refine ? bt->plans[s]->companion : bt->plans[s];
+    const int64_t o = (int64_t)bt->offset[s], M = (int64_t)(bt->offset[s + 1] - bt->offset[s]);
+    cudaStream_t ss = s % S == 0 ? st : bt->side[s % S];
+    Gm gr{R, ss, M, nullptr, 0, R->prec != BEM_F32};
+    if (!R->d_tin) {
+      BEM_CUDA_TRY(cudaMalloc(&R->d_tin, (size_t)M * prec_bytes(R)));
+      BEM_CUDA_TRY(cudaMalloc(&R->d_tout, (size_t)M * prec_bytes(R)));
+    }
+    int64_t nneu = 0;
+    for (int64_t i = 0; i < M; ++i) nneu += bc[o + i] != 0;
+    if (nneu < M) {
+      if ((rc = gr.apply(BEM_DOUBLE, W->vin + o, W->b + o)) != BEM_OK) return rc;
+      ++rhs_applies;
+    }
+    if (nneu > 0) {
+      if ((rc = gr.apply(BEM_SINGLE, W->zz + o, W->w + o)) != BEM_OK) return rc;
+      ++rhs_applies;
+    }
+  }
+  for (int k = 1; k < S; ++k) {
+    BEM_CUDA_TRY(cudaEventRecord(bt->events[S + k], bt->side[k]));
+    BEM_CUDA_TRY(cudaStreamWaitEvent(st, bt->events[S + k], 0));
+  }
+  const double sigma = bt->plans[0]->kernel == BEM_KELVIN_3D ? -1.0 : 1.0;
+  k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(-1.0, W->w, -sigma, W->b, Mt);
+  k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(c, W->vin, 1.0, W->b, Mt);
+  if (x0)
+    BEM_CUDA_TRY(cudaMemcpyAsync(W->x, x0, Mt * sizeof(double), cudaMemcpyHostToDevice, st));
+  else
+    BEM_CUDA_TRY(cudaMemsetAsync(W->x, 0, Mt * sizeof(double), st));
+  std::vector<double> bn2;
+  if ((rc = seg_norms(*W, W->b, bn2)) != BEM_OK) return rc;
+  std::vector<double> bnorm(K);
+  for (int s = 0; s < K; ++s) bnorm[s] = std::sqrt(bn2[s]);
+
+  BatchCounters cnt;
+  cnt.applies = rhs_applies;
+  std::vector<double> rel(K, 1.0);
+  int refine_steps = 0;
+  if (!refine) {
+    if ((rc = batch_gmres(bt, *W, W->b, bnorm, W->x, std::vector<double>(K, tol), max_iter, &cnt, rel)) != BEM_OK)
+      return rc;
+  } else {
+    // residuals with the companions' operator, corrections from the lockstep
+    // low-precision GMRES (per system inner tolerance as in bem_solve)
+    bem_batch_s* cb = bt->companions;
+    std::vector<double> best(K, INFINITY);
+    int stagnant = 0;
+    bool x_zero = x0 == nullptr;  // the first residual of a zero start is b itself
+    for (;;) {
+      BEM_CUDA_TRY(cudaMemcpyAsync(W->r, W->b, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (!x_zero) {
+        if ((rc = batch_apply_f64(cb, W->x, W->w, st, true)) != BEM_OK) return rc;
+        ++cnt.applies;
+        k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(-1.0, W->w, 1.0, W->r, Mt);
+      }
+      x_zero = false;
+      std::vector<double> r2;
+      if ((rc = seg_norms(*W, W->r, r2)) != BEM_OK) return rc;
+      std::vector<double> rn(K), inner_tol(K);
+      bool all = true, progress = false;
+      for (int s = 0; s < K; ++s) {
+        rn[s] = std::sqrt(r2[s]);
+        rel[s] = bnorm[s] > 0 ? rn[s] / bnorm[s] : 0.0;
+        const bool done = !(rel[s] > tol);
+        all = all && done;
+        if (rel[s] < best[s] * 0.5) progress = true;
+        best[s] = std::min(best[s], rel[s]);
+        // a converged system gets tolerance 1: its inner GMRES does nothing
+        inner_tol[s] = done ? 1.0 : std::min(std::max(1e-4, 0.1 * tol / std::max(rel[s], 1e-300)), 1e-2);
+      }
+      if (all) break;
+      stagnant = progress ? 0 : stagnant + 1;
+      if (stagnant >= 2 || cnt.iters >= max_iter) break;
+      // inner solve A e = r from zero (its own right-hand side buffer)
+      BEM_CUDA_TRY(cudaMemcpyAsync(W->rhs, W->r, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      BEM_CUDA_TRY(cudaMemsetAsync(W->e, 0, Mt * sizeof(double), st));
+      std::vector<double> rin;
+      if ((rc = batch_gmres(bt, *W, W->rhs, rn, W->e, inner_tol, max_iter, &cnt, rin)) != BEM_OK) return rc;
+      k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(1.0, W->e, 1.0, W->x, Mt);
+      ++refine_steps;
+    }
+  }
+  // outputs
+  std::vector<double> x(Mt);
+  BEM_CUDA_TRY(cudaMemcpyAsync(x.data(), W->x, Mt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < Mt; ++i) {
+    const bool neu = bc[i] != 0;
+    if (u_out) u_out[i] = neu ? x[i] : data[i];
+    if (q_out) q_out[i] = neu ? data[i] : x[i];
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  bem_status result = BEM_OK;
+  for (int s = 0; s < K; ++s) {
+    const bool ok = std::isfinite(rel[s]) && rel[s] <= tol;
+    if (!std::isfinite(rel[s])) result = BEM_ERR_NONFINITE;
+    else if (!ok && result == BEM_OK) result = BEM_ERR_NOT_CONVERGED;
+    if (info) {
+      info[s].iters = cnt.iters;
+      info[s].restarts = cnt.restarts;
+      info[s].rel_residual = rel[s];
+      info[s].rel_residual_est = rel[s];
+      info[s].seconds = secs;
+      info[s].applies = cnt.applies;
+      info[s].refine_steps = refine_steps;
+    }
+  }
+  if (result == BEM_ERR_NOT_CONVERGED) set_error("bem_batch_solve: some systems did not reach tol");
+  return result;
+}

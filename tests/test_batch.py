@@ -79,3 +79,70 @@ def _as_tensor(torch, ptr, numel):
     class _Cai:
         __cuda_array_interface__ = {"shape": (numel,), "typestr": "<f4", "data": (ptr, False), "version": 2}
     return torch.as_tensor(_Cai(), device="cuda")
+
+
+@pytest.mark.parametrize("refine,tol,bound", [(False, 1e-5, 1e-4), (True, 1e-8, 2e-8)])
+def test_batch_solve_matches_oracle_residuals(torch_cuda, oracle_mod, refine, tol, bound):
+    """Lockstep batched GMRES over stars of several grid sizes and mixed
+    boundary conditions: every system's solution has an oracle residual within
+    the bound (FP32 plans; with refinement the residuals use the double-float
+    companions)."""
+    from paper_1809_00845_gb300.bem import Batch, Plan
+    rng = np.random.default_rng(5)
+    bounds, plans = [], []
+    for n in (256, 512, 256, 1024, 512):
+        b = I.curve_boundary(n, I.random_star_curve(rng))
+        p = Plan.from_boundary(b, "laplace2d", "f32")
+        p.set_bc(I.mixed_bc_theta(b), 0.5)
+        if refine:
+            p.enable_refinement(True)
+        bounds.append(b)
+        plans.append(p)
+    batch = Batch(plans, "system", streams=4)
+    bcs, datas, us, qs = [], [], [], []
+    for b in bounds:
+        u, q = I.boundary_data(b, I.field_expcos)
+        bc = I.mixed_bc_theta(b)
+        bcs.append(bc)
+        datas.append(np.where(bc == 0, u, q))
+        us.append(u)
+        qs.append(q)
+    u_out, q_out, infos, status = batch.solve(np.concatenate(bcs), np.concatenate(datas), tol=tol, restart=100,
+                                              max_iter=1500)
+    assert status == 0, infos
+    for k, b in enumerate(bounds):
+        o = batch.offsets[k]
+        sl = slice(o, o + b.nb)
+        bc = bcs[k]
+        x = np.where(bc == 0, q_out[sl], u_out[sl])
+        rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, us[k] * (bc == 0), qs[k] * (bc == 1))
+        r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
+        assert np.linalg.norm(r) / np.linalg.norm(rhs) <= bound, (k, infos[k])
+        assert infos[k]["rel_residual"] <= tol
+    # a second solve with other data reuses the captured graphs
+    u2, q2, infos2, st2 = batch.solve(np.concatenate(bcs), 2.0 * np.concatenate(datas), tol=tol, restart=100,
+                                      max_iter=1500)
+    assert st2 == 0
+    batch.close()
+
+
+def test_batch_solve_equals_single_solves(torch_cuda):
+    """The lockstep solve of a batch and per-plan bem_solve reach the same
+    solutions (both to 1e-10 with FP64 plans)."""
+    from paper_1809_00845_gb300.bem import Batch, Plan
+    rng = np.random.default_rng(8)
+    bounds = [I.curve_boundary(n, I.random_star_curve(rng)) for n in (256, 512)]
+    plans = []
+    for b in bounds:
+        p = Plan.from_boundary(b, "laplace2d", "f64")
+        p.set_bc(np.zeros(b.nb, np.uint8), 0.5)
+        plans.append(p)
+    batch = Batch(plans, "system", streams=2)
+    datas = [I.boundary_data(b, I.field_x2y2)[0] for b in bounds]
+    u, q, infos, st = batch.solve(np.zeros(batch.total, np.uint8), np.concatenate(datas), tol=1e-10, restart=100)
+    assert st == 0
+    for k, (b, p) in enumerate(zip(bounds, plans)):
+        _, qk, ik = p.solve(np.zeros(b.nb, np.uint8), datas[k], tol=1e-10, restart=100)
+        o = batch.offsets[k]
+        assert np.linalg.norm(q[o:o + b.nb] - qk) / np.linalg.norm(qk) <= 1e-8
+    batch.close()
