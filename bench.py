@@ -214,6 +214,46 @@ def _time_applies(plan, layer, x, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def _batched_solve_c5():
+    """Time to relative residual 1e-6 for 64 random stars on uneven grids with
+    harmonic Dirichlet data from 8 multipoles (the learned-guess workload's
+    held-out geometries): FP32 plans, double-float refinement, block-Jacobi
+    preconditioner.  One lockstep batched GMRES (Arnoldi steps as CUDA graph
+    replays) against 64 consecutive single-plan solves, both from zero."""
+    import time
+    from paper_1809_00845_gb300 import learned as L
+    from paper_1809_00845_gb300.bem import Batch, Plan
+    plans, datas = [], []
+    for seed in range(L.TEST_SEED0, L.TEST_SEED0 + 64):
+        b, rng = L.geometry(seed)
+        p = Plan.from_boundary(b, "laplace2d", "f32")
+        p.enable_refinement(True)
+        p.set_bc(np.zeros(b.nb, np.uint8), 0.5)
+        plans.append(p)
+        datas.append(L.multipoles(rng)(b.point))
+    zero = [np.zeros(p.nb, np.uint8) for p in plans]
+    for p, bc, u in zip(plans, zero, datas):  # warm: preconditioners, companions, workspaces
+        p.solve(bc, u, tol=1e-6, restart=100, max_iter=2000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = [p.solve(bc, u, tol=1e-6, restart=100, max_iter=2000)[2] for p, bc, u in zip(plans, zero, datas)]
+    t_seq = time.perf_counter() - t0
+    batch = Batch(plans, "system", streams=4)
+    bc_all, data_all = np.concatenate(zero), np.concatenate(datas)
+    batch.solve(bc_all, data_all, tol=1e-6, restart=100, max_iter=2000)
+    t0 = time.perf_counter()
+    _, _, infos, status = batch.solve(bc_all, data_all, tol=1e-6, restart=100, max_iter=2000)
+    t_b = time.perf_counter() - t0
+    batch.close()
+    for p in plans:
+        p.close()
+    return {"batched_s": t_b, "batched_status": status, "batched_lockstep_iters": infos[0]["iters"],
+            "batched_refine_steps": infos[0]["refine_steps"],
+            "batched_max_rel_residual": max(i["rel_residual"] for i in infos),
+            "sequential_s": t_seq, "sequential_mean_iters": float(np.mean([i["iters"] for i in its])),
+            "sequential_all_converged": all(i["status"] == 0 for i in its), "speedup": t_seq / t_b}
+
+
 def secondary_configs(dev):
     """Apply times (and the circle solve) of the other configurations, a few
     repetitions each: circle n=128 FP64, ellipsoid n=256 FP32, Kelvin cube
@@ -276,6 +316,7 @@ def secondary_configs(dev):
     batch.close()
     for p in plans:
         p.close()
+    out["batched_stars_64_f32"]["solve_1e-6"] = _batched_solve_c5()
     b = I.cube_boundary(128)
     p = Plan.from_boundary(b, "kelvin3d", "f32")
     x = torch.randn(b.nb * 3, dtype=torch.float32, device=dev)
