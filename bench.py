@@ -221,6 +221,8 @@ def _batched_solve_c5():
     preconditioner.  One lockstep batched GMRES (Arnoldi steps as CUDA graph
     replays) against 64 consecutive single-plan solves, both from zero."""
     import time
+
+    import torch
     from paper_1809_00845_gb300 import learned as L
     from paper_1809_00845_gb300.bem import Batch, Plan
     plans, datas = [], []
