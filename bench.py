@@ -466,7 +466,7 @@ def run_ours(args):
                     "applies": info["applies"], "refine_steps": info["refine_steps"]}
         plain = run_solve(False)
         refined = run_solve(True) if args.precision == "f32" else None
-        solve = {"tol": 1e-6, "precision": args.precision, "preconditioner": "block Jacobi, 64 cells",
+        solve = {"tol": 1e-6, "precision": args.precision, "preconditioner": "block Jacobi, 128-cell blocks inverted on the device",
                  "fp32_refined": refined, "plain_fp32": plain,
                  "note": "plain_fp32 residuals use the FP32 operator and stall near its accuracy; "
                          "fp32_refined forms the right-hand side and its residuals with the double-float "

@@ -177,12 +177,13 @@ bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, dou
                      void* stream);
 
 /* Preconditioner of bem_solve (right preconditioning, GMRES on A M^-1).
- *   kind 0: none.  kind 1 (default, block_size 64): block Jacobi on the near
- *   field: M = the diagonal blocks of A over consecutive cells in the caller's
- *   order (pass cells in boundary order, e.g. arclength along a curve, so that
- *   a block is a connected piece of S); the blocks are assembled from the same
- *   kernel point values as the operator and inverted in FP64 on the host when
- *   a solve first needs them after bem_set_bc.
+ *   kind 0: none.  kind 1 (default; block_size 128 cells in 2D, 64 in 3D):
+ *   block Jacobi on the near field: M = the diagonal blocks of A over
+ *   consecutive cells in the caller's order (pass cells in boundary order,
+ *   e.g. arclength along a curve, so that a block is a connected piece of S);
+ *   the blocks are assembled from the same kernel point values as the
+ *   operator when a solve first needs them after bem_set_bc, and inverted on
+ *   the device in FP32 (2D, block_size <= 128) or in FP64 on the host.
  * The paper solves without a preconditioner (Section 4); the single layer is
  * a first-kind operator whose condition number grows with n, so unpreconditioned
  * restarted GMRES stalls on mixed problems. */

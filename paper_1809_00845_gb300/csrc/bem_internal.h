@@ -256,12 +256,15 @@ bem_status upload_real(const bem_plan_s* p, const double* v, size_t count, bool 
 template <typename K>
 inline cudaError_t allow_optin_smem(K kern) {
   int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);  // the limit excludes static shared memory
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   return e;
 }
 bem_status build_preconditioner(bem_plan_s* p);
-double kernel2d_point(int kind, int dx, int dy, double h);
+__host__ __device__ double kernel2d_point(int kind, int dx, int dy, double h);
 
 }  // namespace bemfft

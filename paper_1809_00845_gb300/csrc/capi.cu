@@ -254,6 +254,7 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   p->ncomp = kernel == BEM_KELVIN_3D ? 3 : 1;
   p->kernel = kernel;
   p->prec = prec;
+  p->pc.bs = dim == 2 ? 128 : 64;  // default block-Jacobi block (cells)
   p->n = nn;
   p->N = 2 * nn;
   p->log2N = 0;

@@ -8,7 +8,11 @@
 // cells and using those inverses as a right preconditioner removes most of
 // that ill-conditioning.  Blocks are runs of consecutive cells in the
 // caller's order.  Entries are the same kernel point values (and singular-cell
-// average) as the FFT tables, assembled and inverted in FP64 on the host.
+// average) as the FFT tables.  2D blocks of up to 128 unknowns are assembled
+// and inverted on the device, one CTA per block (Gauss-Jordan with partial
+// pivoting in FP32 shared memory: the preconditioner only has to be a fixed
+// nonsingular approximation of the block inverse); other blocks are assembled
+// and inverted in FP64 on the host.
 #include <cmath>
 #include <vector>
 
@@ -19,15 +23,15 @@ namespace bemfft {
 // 2D kernel value at grid offset (dx, dy): kind 0 = U, 1 = Q_x, 2 = Q_y,
 // same definition as the FFT tables (Eq. 3, Eq. 15; singular cell = cell
 // average for U, 0 for the odd kernels).
-double kernel2d_point(int kind, int dx, int dy, double h) {
+__host__ __device__ double kernel2d_point(int kind, int dx, int dy, double h) {
   const double PI = 3.14159265358979323846;
   if (dx == 0 && dy == 0) {
     if (kind != 0) return 0.0;
-    const double L2 = PI / 4.0 - 1.5 - 0.5 * std::log(2.0);
-    return -(std::log(h) + L2) / (2.0 * PI);
+    const double L2 = PI / 4.0 - 1.5 - 0.5 * ::log(2.0);
+    return -(::log(h) + L2) / (2.0 * PI);
   }
   const double r2 = (double)dx * dx + (double)dy * dy;
-  if (kind == 0) return -(0.5 * std::log(r2) + std::log(h)) / (2.0 * PI);
+  if (kind == 0) return -(0.5 * ::log(r2) + ::log(h)) / (2.0 * PI);
   const double da = kind == 1 ? (double)dx : (double)dy;
   return -da / (2.0 * PI * h * r2);
 }
@@ -107,12 +111,159 @@ static bool invert(std::vector<double>& A, int m) {
   return true;
 }
 
+constexpr int kPcGpuMax = 128;  // largest block assembled and inverted on the device
+constexpr int kPcThreads = 256;
+
+// One CTA per block of bs consecutive caller-order cells (2D Laplace): the
+// block of the BC-split operator (U for Dirichlet columns, Q.n for Neumann
+// columns minus c on their diagonal), Gauss-Jordan with partial pivoting in
+// shared memory, inverse written as FP64 (padded to m x m).  A block whose
+// pivot vanishes gets the identity.
+__global__ void __launch_bounds__(kPcThreads) k_pc_build2d(int64_t nb, int bs, double h, double c,
+                                                          const int32_t* __restrict__ cell,
+                                                          const double* __restrict__ w,
+                                                          const double* __restrict__ nrm,
+                                                          const uint8_t* __restrict__ bc, double* __restrict__ inv) {
+  extern __shared__ float pcs[];
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int64_t i0 = (int64_t)b * bs;
+  const int sz = (int)(nb - i0 < bs ? nb - i0 : bs);
+  float* A = pcs;
+  float* I = A + sz * sz;
+  float* fac = I + sz * sz;
+  for (int e = tid; e < sz * sz; e += kPcThreads) {
+    const int ia = e / sz, jb = e - ia * sz;
+    const int64_t i = i0 + ia, j = i0 + jb;
+    const int dx = cell[2 * i] - cell[2 * j], dy = cell[2 * i + 1] - cell[2 * j + 1];
+    double v;
+    if (!bc[j]) {
+      v = kernel2d_point(0, dx, dy, h) * w[j];
+    } else {
+      v = (kernel2d_point(1, dx, dy, h) * nrm[2 * j] + kernel2d_point(2, dx, dy, h) * nrm[2 * j + 1]) * w[j];
+      if (i == j) v -= c;
+    }
+    A[e] = (float)v;
+    I[e] = ia == jb ? 1.0f : 0.0f;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int col = 0; col < sz; ++col) {
+    if (tid < 32) {
+      float best = -1.0f;
+      int bi = col;
+      for (int r = col + tid; r < sz; r += 32) {
+        const float a = fabsf(A[r * sz + col]);
+        if (a > best) {
+          best = a;
+          bi = r;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        if (!(best > 0.0f) || !isfinite(best)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int piv = s_piv;
+    if (piv != col)
+      for (int k = tid; k < sz; k += kPcThreads) {
+        float t = A[piv * sz + k];
+        A[piv * sz + k] = A[col * sz + k];
+        A[col * sz + k] = t;
+        t = I[piv * sz + k];
+        I[piv * sz + k] = I[col * sz + k];
+        I[col * sz + k] = t;
+      }
+    __syncthreads();
+    const float pinv = 1.0f / A[col * sz + col];
+    for (int r = tid; r < sz; r += kPcThreads) fac[r] = r == col ? 0.0f : A[r * sz + col];
+    __syncthreads();
+    for (int k = tid; k < sz; k += kPcThreads) {
+      A[col * sz + k] *= pinv;
+      I[col * sz + k] *= pinv;
+    }
+    __syncthreads();
+    for (int e = tid; e < sz * sz; e += kPcThreads) {
+      const int r = e / sz, k = e - r * sz;
+      const float f = fac[r];
+      if (f != 0.0f) {
+        A[e] -= f * A[col * sz + k];
+        I[e] -= f * I[col * sz + k];
+      }
+    }
+    __syncthreads();
+  }
+  const int m = bs;
+  double* dst = inv + (size_t)b * m * m;
+  for (int e = tid; e < m * m; e += kPcThreads) {
+    const int a = e / m, k = e - a * m;
+    double v = 0.0;
+    if (a < sz && k < sz) v = s_bad ? (a == k ? 1.0 : 0.0) : (double)I[a * sz + k];
+    dst[e] = v;
+  }
+}
+
+static bem_status build_preconditioner_gpu2d(bem_plan_s* p) {
+  const int64_t nb = p->nb;
+  const int bs = p->pc.bs;
+  const int nblocks = (int)((nb + bs - 1) / bs);
+  int32_t* d_cell = nullptr;
+  double *d_w = nullptr, *d_n = nullptr;
+  uint8_t* d_bc = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_cell);
+    cudaFree(d_w);
+    cudaFree(d_n);
+    cudaFree(d_bc);
+  };
+  if (cudaMalloc(&d_cell, nb * 2 * sizeof(int32_t)) != cudaSuccess || cudaMalloc(&d_w, nb * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&d_n, nb * 2 * sizeof(double)) != cudaSuccess || cudaMalloc(&d_bc, nb) != cudaSuccess) {
+    cleanup();
+    set_error("preconditioner: out of device memory");
+    return BEM_ERR_OOM;
+  }
+  cudaFree(p->pc.d_inv);
+  p->pc.d_inv = nullptr;
+  const size_t smem = ((size_t)2 * bs * bs + bs) * sizeof(float);
+  cudaError_t e = cudaMalloc(&p->pc.d_inv, (size_t)nblocks * bs * bs * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d_cell, p->h_cell_user.data(), nb * 2 * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_w, p->h_w_user.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_n, p->h_normal_user.data(), nb * 2 * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_bc, p->h_bc.data(), nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = allow_optin_smem(k_pc_build2d);
+  if (e == cudaSuccess) {
+    k_pc_build2d<<<nblocks, kPcThreads, smem>>>(nb, bs, p->h, p->c, d_cell, d_w, d_n, d_bc, p->pc.d_inv);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cleanup();
+  if (e != cudaSuccess) {
+    set_error(std::string("preconditioner: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  p->pc.nblocks = nblocks;
+  p->pc.valid = true;
+  return BEM_OK;
+}
+
 bem_status build_preconditioner(bem_plan_s* p) {
   if (p->pc.kind == 0 || p->pc.valid) return BEM_OK;
   if (!p->have_bc) {
     set_error("preconditioner needs boundary conditions");
     return BEM_ERR_ARG;
   }
+  if (p->dim == 2 && p->pc.bs * p->ncomp <= kPcGpuMax) return build_preconditioner_gpu2d(p);
   const int64_t nb = p->nb;
   const int bs = p->pc.bs;
   const int nc = p->ncomp;
