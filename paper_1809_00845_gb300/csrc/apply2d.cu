@@ -546,7 +546,8 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   const int64_t npos = p->v2_npos;
   BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * npos * tb));
   BEM_CUDA_TRY(cudaMalloc(&p->d_val, (size_t)npos * 2 * tb));
-  p->scratch_bytes += (size_t)p->grid * npos * tb + (size_t)npos * 2 * tb;
+  BEM_CUDA_TRY(cudaMalloc(&p->d_twc, (size_t)p->grid * npos * 2 * tb));
+  p->scratch_bytes += (size_t)p->grid * npos * tb + (size_t)npos * 2 * tb + (size_t)p->grid * npos * 2 * tb;
   return BEM_OK;
 }
 
@@ -689,6 +690,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   }
   cp.fstab = static_cast<const cplx<T>*>(p->d_fstab);
   cp.partial = static_cast<T*>(sp.partial);
+  cp.twc = static_cast<cplx<T>*>(sp.twc);
   cp.npos = npos;
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
   cp.has_carry = p->v2_carry ? 1 : 0;
@@ -758,6 +760,7 @@ bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, vo
     for (int f = 0; f < op.nf; ++f) sp.rho[f] = op.f[f].rho;
   }
   sp.partial = p->d_partial;
+  sp.twc = p->d_twc;
   return launch_apply_2d_with(p, op, in, out, sp, p->timing, st);
 }
 

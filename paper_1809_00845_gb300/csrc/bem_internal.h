@@ -141,6 +141,7 @@ struct bem_plan_s {
   int32_t* d_perm_il = nullptr; // interleaved position -> caller index (-1: padding)
   int32_t* d_chunk = nullptr;   // threads + 1
   void* d_val = nullptr;        // nb density pairs (scratch)
+  void* d_twc = nullptr;        // grid * npos cached sparse twiddles (scratch)
   void* d_fstab = nullptr;      // twiddle tables of the four-step kernel
   // 3D path
   int32_t* d_lptr = nullptr;    // n*n + 1 line pointers over sorted cells (line = z*n + y)
@@ -231,6 +232,7 @@ struct ScratchPtrs {
   void* rho[kMaxFields];
   void* val;
   void* partial;
+  void* twc = nullptr;  // per-CTA cached sparse twiddles (four-step kernel; optional)
 };
 void carve_scratch(const bem_plan_s* p, const Operator& op, void* base, ScratchPtrs* sp);
 bem_status launch_apply_2d_with(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,

@@ -647,6 +647,7 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_perm_il);
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
+  cudaFree(p->d_twc);
   cudaFree(p->d_fstab);
   free_operator3(p->op3_single);
   free_operator3(p->op3_double);

@@ -6,7 +6,7 @@
 // density pairs, accumulators) are stored interleaved: the i-th cell of
 // thread t sits at position i*TT + t, so every warp-wide access of the cell
 // loops is one contiguous segment.  Per column kx:
-//   1. the thread walks its cells (loads and twiddles batched 8 at a time) and
+//   1. the thread walks its cells (loads and twiddles batched CB at a time) and
 //      forms the input-pruned x-DFT of every field row by row.  A row sum is
 //      stored when the row's last cell in the chunk is reached (flag in the
 //      cell word): into shared memory at the row's slot (rowslot), field 0
@@ -38,6 +38,13 @@ __device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 
 constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
 
+// cells per batch of the row-sum and gather loops: the loads of a batch are
+// issued together, so each batch costs one memory round trip
+#ifndef COL2D_CELL_BATCH
+#define COL2D_CELL_BATCH 8
+#endif
+constexpr int CB = COL2D_CELL_BATCH;
+
 // Sizes of one launch: compile-time when TTC > 0, else from the launch and
 // the parameters.
 template <int TTC>
@@ -66,23 +73,29 @@ struct ColDims {
 template <typename T, int NF, int FSEL, int TTC>
 __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
                                             cplx<T>* out0, cplx<T>* outF, cplx<T>* carry,
-                                            const Twiddles2L<T>& tw) {
+                                            const Twiddles2L<T>& tw, cplx<T>* twc) {
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
-  for (int i0 = 0; i0 < cnt; i0 += 8) {
-    uint32_t mt[8];
-    cplx<T> vv[8], w[8];
+  for (int i0 = 0; i0 < cnt; i0 += CB) {
+    uint32_t mt[CB];
+    cplx<T> vv[CB], w[CB];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < CB; ++i) {
       const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
       mt[i] = __ldg(p.meta + pos);
       vv[i] = p.val[pos];
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
+    for (int i = 0; i < CB; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
+    if (twc) {
+      // kept for the gather of the same column (the conjugate twiddle)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < CB; ++i)
+        if (i0 + i < cnt) twc[(i0 + i) * TT + t] = w[i];
+    }
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
       if (i0 + i < cnt) {
         const bool ty = (mt[i] >> 31) != 0;
         const T a = vv[i].x, b = vv[i].y;
@@ -136,22 +149,28 @@ __device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, const Col
 
 template <typename T, int TTC>
 __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
-                                             const cplx<T>* rows, const Twiddles2L<T>& tw, T* acc) {
+                                             const cplx<T>* rows, const Twiddles2L<T>& tw, T* acc,
+                                             const cplx<T>* twc) {
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   const T ckx = (kx == 0 || kx == g.n) ? T(1) : T(2);
-  for (int i0 = 0; i0 < cnt; i0 += 8) {
-    uint32_t mt[8];
-    cplx<T> Y[8], w[8];
+  for (int i0 = 0; i0 < cnt; i0 += CB) {
+    uint32_t mt[CB];
+    cplx<T> Y[CB], w[CB];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) mt[i] = __ldg(p.meta + (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      Y[i] = rows[meta_slot(mt[i])];
-      w[i] = tw.template get<+1>((kx * meta_x(mt[i])) & Nm);
+    for (int i = 0; i < CB; ++i) {
+      const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
+      mt[i] = __ldg(p.meta + pos);
+      if (twc) w[i] = twc[pos];  // the sparse pass's e^{-i...}: conjugated below
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < CB; ++i) {
+      Y[i] = rows[meta_slot(mt[i])];
+      if (twc) w[i].y = -w[i].y;
+      else w[i] = tw.template get<+1>((kx * meta_x(mt[i])) & Nm);
+    }
+#pragma unroll
+    for (int i = 0; i < CB; ++i)
       if (i0 + i < cnt) acc[(i0 + i) * TT + t] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
   }
 }
@@ -266,6 +285,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
   T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
                          : p.partial + (size_t)blockIdx.x * p.npos;
+  cplx<T>* twc = p.twc ? p.twc + (size_t)blockIdx.x * p.npos : nullptr;
   for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
   // per-thread plan data is re-read (L1) where used rather than held in
   // registers across the transforms
@@ -290,7 +310,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
     __syncthreads();  // the previous column's gather has finished reading sA
     if constexpr (ACCREG) {
-      sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw);
+      sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
       __syncthreads();
       if (p.has_carry) {
         add_carries<T, NF, -1>(p, g, CNT, TINFO >> 8, sA, sF, carry);
@@ -313,15 +333,15 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
 #pragma unroll
       for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
       __syncthreads();
-      gather_cells(p, g, kx, CNT, sA, tw, acc);
+      gather_cells(p, g, kx, CNT, sA, tw, acc, twc);
     } else {
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
         if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
-        if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw);
-        else if (f == 0) sparse_rows<T, NF, 0>(p, g, kx, CNT, sA, sF, carry, tw);
-        else if (f == 1) sparse_rows<T, NF, 1>(p, g, kx, CNT, sA, sF, carry, tw);
-        else sparse_rows<T, NF, 2>(p, g, kx, CNT, sA, sF, carry, tw);
+        if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
+        else if (f == 0) sparse_rows<T, NF, 0>(p, g, kx, CNT, sA, sF, carry, tw, twc);
+        else if (f == 1) sparse_rows<T, NF, 1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
+        else sparse_rows<T, NF, 2>(p, g, kx, CNT, sA, sF, carry, tw, twc);
         __syncthreads();
         if (p.has_carry) {
           add_carries<T, NF, 0>(p, g, CNT, TINFO >> 8, sA, sF, carry);
@@ -338,7 +358,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
 #pragma unroll
         for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = v[m];
         __syncthreads();
-        gather_cells(p, g, kx, CNT, sA, tw, acc);
+        gather_cells(p, g, kx, CNT, sA, tw, acc, twc);
       }
     }
   }

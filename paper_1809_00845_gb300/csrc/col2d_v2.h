@@ -29,6 +29,7 @@ struct Col2Dv2Params {
   int oddy[3];
   const cplx<T>* fstab;  // four-step tables (lane, warp, t5) then sparse tables (hi, lo)
   T* partial;            // gridDim.x * npos, interleaved positions
+  cplx<T>* twc;          // gridDim.x * npos: each cell's sparse twiddle of the current column, or null
   int npos;              // Q*TT
   int acc_in_smem;
   int has_carry;         // some row is split between threads
