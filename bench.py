@@ -214,6 +214,68 @@ def _time_applies(plan, layer, x, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def cufft_comparator(b, bc, x, ours, reps=20):
+    """The same BC-split operator applied the way Eq. 16 writes it: densities
+    scattered on the full zero-padded N x N grid, real-to-complex FFT over the
+    whole grid (cuFFT through torch.fft), multiply by the kernel spectra, inverse
+    FFT, read the grid at the cells.  Kernel tables are built here from their
+    definitions (U = -ln r / 2 pi with the cell-averaged singular value, Q_a =
+    -d_a / 2 pi r^2, odd tables zero on the -n line) and transformed in FP64;
+    the applies run in FP32.  A timed comparator only: returns its time per
+    apply and its relative L2 distance from our apply's output."""
+    import torch
+    dev = torch.device("cuda")
+    n, N, h = b.n, 2 * b.n, b.h
+    d = torch.arange(N, device=dev, dtype=torch.float64)
+    d = torch.where(d < n, d, d - N)  # offsets -n .. n-1 along each axis
+    dy, dx = torch.meshgrid(d, d, indexing="ij")  # rows = y, columns = x
+    r2 = dx * dx + dy * dy
+    L2 = math.pi / 4 - 1.5 - 0.5 * math.log(2.0)
+    U = torch.where(r2 > 0, -(0.5 * torch.log(torch.clamp(r2, min=1.0)) + math.log(h)) / (2 * math.pi),
+                    torch.full_like(r2, -(math.log(h) + L2) / (2 * math.pi)))
+    Qx = torch.where(r2 > 0, -dx / (2 * math.pi * h * torch.clamp(r2, min=1.0)), torch.zeros_like(r2))
+    Qy = torch.where(r2 > 0, -dy / (2 * math.pi * h * torch.clamp(r2, min=1.0)), torch.zeros_like(r2))
+    Qx[:, n] = 0.0  # dx = -n
+    Qy[n, :] = 0.0  # dy = -n
+    spec = [torch.fft.rfft2(t).to(torch.complex64) for t in (U, Qx, Qy)]
+    del U, Qx, Qy, r2, dx, dy
+    cell = torch.from_numpy(b.cell.astype(np.int64)).to(dev)
+    lin = cell[:, 1] * N + cell[:, 0]
+    neu = torch.from_numpy(bc.astype(bool)).to(dev)
+    w = torch.from_numpy(b.w).to(dev)
+    nx = torch.from_numpy(b.normal[:, 0]).to(dev)
+    ny = torch.from_numpy(b.normal[:, 1]).to(dev)
+    coef = [torch.where(neu, 0.0, w), torch.where(neu, w * nx, 0.0), torch.where(neu, w * ny, 0.0)]
+    coef = [c.to(torch.float32) for c in coef]
+    diag = torch.where(neu, -0.5, 0.0).to(torch.float32)
+    xt = torch.as_tensor(x, device=dev, dtype=torch.float32)
+    grid = torch.zeros(N * N, device=dev, dtype=torch.float32)
+
+    def apply():
+        acc = None
+        for c, S in zip(coef, spec):
+            grid.zero_()
+            grid[lin] = c * xt
+            F = torch.fft.rfft2(grid.view(N, N)) * S
+            acc = F if acc is None else acc + F
+        out = torch.fft.irfft2(acc, s=(N, N)).reshape(-1)[lin]
+        return out + diag * xt
+
+    for _ in range(3):
+        y = apply()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        y = apply()
+    e1.record()
+    torch.cuda.synchronize()
+    ref = np.asarray(ours, dtype=np.float64)
+    dist = float(np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+    return {"ms_per_apply": e0.elapsed_time(e1) / reps, "rel_l2_vs_ours": dist,
+            "what": "full-grid cuFFT (torch.fft) R2C/C2R apply of the same operator, FP32, spectra from FP64 tables"}
+
+
 def _batched_solve_c5():
     """Time to relative residual 1e-6 for 64 random stars on uneven grids with
     harmonic Dirichlet data from 8 multipoles (the learned-guess workload's
@@ -515,6 +577,13 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_rate(b, bc, args.cpu_seconds)
+    cufft = None
+    if not args.no_extra and world == 1 and args.precision == "f32":
+        x0 = xs[0].double().cpu().numpy()
+        y0 = plan.apply("system", xs[0]).double().cpu().numpy()
+        cufft = cufft_comparator(b, bc, x0, y0)
+        cufft["ours_ms_per_apply"] = ms_max / args.steps
+        cufft["speedup_ours"] = cufft["ms_per_apply"] / cufft["ours_ms_per_apply"]
     extra = None
     if not args.no_extra and world == 1:
         extra = secondary_configs(dev)
@@ -529,7 +598,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "gpu_launches": args.steps * plan.launches_per_apply("system"),
             "roofline": roofline, "clocks": clk, "time_to_solve": solve, "cpu_baseline": cpu,
-            "plan_seconds": pinfo["plan_seconds"], "other_configs": extra}
+            "plan_seconds": pinfo["plan_seconds"], "cufft_comparator": cufft, "other_configs": extra}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
