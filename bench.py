@@ -130,7 +130,7 @@ class ClockSampler:
 # system operator, from ncu (profiles/col2d_v2_star4096_launches.md), keyed by
 # the hash of the kernel sources it was measured on; reported only while the
 # sources are unchanged.
-MEASURED_TRAFFIC = {"n4096_f32_system": ("9cbfc18557dca993", 201.98e6)}
+MEASURED_TRAFFIC = {"n4096_f32_system": ("1ff1ac15b8a2c67f", 202.10e6)}
 
 
 def kernel_source_hash():
