@@ -146,3 +146,34 @@ def test_batch_solve_equals_single_solves(torch_cuda):
         o = batch.offsets[k]
         assert np.linalg.norm(q[o:o + b.nb] - qk) / np.linalg.norm(qk) <= 1e-8
     batch.close()
+
+
+def test_batch_solve_3d_and_initial_guess(torch_cuda, oracle_mod):
+    """3D Laplace plans of two grid sizes in one batch (Dirichlet, FP64): the
+    batched solution equals the dense LU solution of each system; starting
+    from the solution itself ends at once with the same answer."""
+    from paper_1809_00845_gb300.bem import Batch, Plan
+    bounds = [I.ellipsoid_boundary(16), I.ellipsoid_boundary(32)]
+    plans = []
+    for b in bounds:
+        p = Plan.from_boundary(b, "laplace3d", "f64")
+        p.set_bc(np.zeros(b.nb, np.uint8), 0.5)
+        plans.append(p)
+    batch = Batch(plans, "system", streams=2)
+    datas = [I.boundary_data(b, I.field_xy_z)[0] for b in bounds]
+    bc = np.zeros(batch.total, np.uint8)
+    u, q, infos, st = batch.solve(bc, np.concatenate(datas), tol=1e-11, restart=100, max_iter=500)
+    assert st == 0, infos
+    refs = []
+    for k, b in enumerate(bounds):
+        A, rhs = oracle_mod.system("laplace3d", b.cell, b.h, b.w, b.normal, np.zeros(b.nb, np.uint8), datas[k],
+                                   np.zeros(b.nb))
+        ref = oracle_mod.solve_lu(A, rhs)
+        refs.append(ref)
+        o = batch.offsets[k]
+        assert np.linalg.norm(q[o:o + b.nb] - ref) / np.linalg.norm(ref) <= 1e-8
+    u2, q2, infos2, st2 = batch.solve(bc, np.concatenate(datas), tol=1e-10, restart=100, max_iter=500,
+                                      x0=np.concatenate(refs))
+    assert st2 == 0 and infos2[0]["iters"] <= 2, infos2[0]
+    assert np.linalg.norm(q2 - np.concatenate(refs)) / np.linalg.norm(np.concatenate(refs)) <= 1e-9
+    batch.close()
