@@ -351,6 +351,7 @@ def secondary_configs(dev):
         n = int(rng.choice((512, 1024, 2048)))
         plans.append(Plan.from_boundary(I.curve_boundary(n, I.random_star_curve(rng)), "laplace2d", "f32"))
     batch = Batch(plans, "single", streams=4)
+    tuned_streams = batch.tune(reps=10)
     for _ in range(3):
         batch.apply()
     torch.cuda.synchronize()
@@ -376,7 +377,8 @@ def secondary_configs(dev):
     loop_ms = e0.elapsed_time(e1) / reps
     out["batched_stars_64_f32"] = {"geometries": 64, "cells": int(sum(p.nb for p in plans)),
                                    "graph_ms_per_batch": graph_ms, "graph_applies_per_s": 64e3 / graph_ms,
-                                   "loop_ms_per_batch": loop_ms, "kernel_launches_per_batch": batch.launches}
+                                   "loop_ms_per_batch": loop_ms, "kernel_launches_per_batch": batch.launches,
+                                   "capture_streams_tuned": tuned_streams}
     batch.close()
     for p in plans:
         p.close()
@@ -518,6 +520,8 @@ def run_ours(args):
     # (same preconditioner, FP32 residuals) for comparison
     solve = None
     if not args.no_solve:
+        pc_block = plan.tune_preconditioner(bc, data, tol=1e-6, restart=100, max_iter=3000)
+
         def run_solve(refine):
             plan.enable_refinement(refine)
             plan.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)  # warm (builds preconditioner)
@@ -528,7 +532,8 @@ def run_ours(args):
                     "applies": info["applies"], "refine_steps": info["refine_steps"]}
         plain = run_solve(False)
         refined = run_solve(True) if args.precision == "f32" else None
-        solve = {"tol": 1e-6, "precision": args.precision, "preconditioner": "block Jacobi, 128-cell blocks inverted on the device",
+        solve = {"tol": 1e-6, "precision": args.precision,
+                 "preconditioner": f"block Jacobi, {pc_block}-cell blocks (tuned), inverted on the device",
                  "fp32_refined": refined, "plain_fp32": plain,
                  "note": "plain_fp32 residuals use the FP32 operator and stall near its accuracy; "
                          "fp32_refined forms the right-hand side and its residuals with the double-float "

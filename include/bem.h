@@ -254,6 +254,23 @@ bem_status bem_batch_solve(bem_batch_t batch, const uint8_t* bc, const double* d
                            int max_iter, int restart, const double* x0, double* u_out, double* q_out,
                            bem_solve_info* info, void* stream);
 
+/* ---- measured launch choices (autotuning) -------------------------------
+ * Choices that the problem's shape alone does not fix are timed on the device
+ * with the caller's data and kept in a process-wide table keyed by the shape
+ * (grid sizes, cell counts, kernel, precision), so later plans or batches of
+ * the same shape take the stored choice without timing again.
+ * bem_tune_batch: the number of forked capture streams of the batch graph
+ *   (candidates 1, 2, 4, 8; `reps` timed replays each); the batch is captured
+ *   again with the winner, returned in *streams (may be NULL).
+ * bem_tune_preconditioner: the block size of the block-Jacobi preconditioner
+ *   (candidates 32, 64, 128 cells, within 128 unknowns per block in 2D and 192
+ *   in 3D), by the wall time of a full bem_solve with these arguments,
+ *   including the block inversion; the plan keeps the winner, returned in
+ *   *block (may be NULL).  BEM_ERR_NOT_CONVERGED when no candidate converges. */
+bem_status bem_tune_batch(bem_batch_t batch, int reps, int* streams);
+bem_status bem_tune_preconditioner(bem_plan_t plan, const uint8_t* bc, const double* data, double c, double tol,
+                                   int max_iter, int restart, int* block);
+
 /* ---- learned initial guess (serving/training pattern on top of the operator;
  * the paper has no learned component) ------------------------------------
  * A 1D convolutional network over the arclength-ordered cells of closed

@@ -30,7 +30,8 @@ LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
-            "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
+            "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
+            "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step"]
 
 
@@ -95,8 +96,10 @@ def load_library(path: str = LIB_PATH):
     lib.bem_batch_launches.restype = I
     lib.bem_batch_destroy.argtypes = [P]
     lib.bem_batch_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
+    lib.bem_tune_batch.argtypes = [P, I, ctypes.POINTER(I)]
+    lib.bem_tune_preconditioner.argtypes = [P, P, P, D, D, I, I, ctypes.POINTER(I)]
     for name in ("bem_batch_create", "bem_batch_buffers", "bem_batch_offset", "bem_batch_apply", "bem_batch_destroy",
-                 "bem_batch_solve"):
+                 "bem_batch_solve", "bem_tune_batch", "bem_tune_preconditioner"):
         getattr(lib, name).restype = I
     lib.bem_net_create.argtypes = [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64]
     lib.bem_net_destroy.argtypes = [P]
@@ -254,6 +257,15 @@ class Plan:
         d["status"] = rc
         return u, q, d
 
+    def tune_preconditioner(self, bc, data, c=0.5, tol=1e-6, max_iter=2000, restart=100):
+        """Measured block size of the block-Jacobi preconditioner (bem_tune_preconditioner)."""
+        bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
+        data = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)
+        out = ctypes.c_int()
+        _check(load_library().bem_tune_preconditioner(self._h, _ptr(bc), _ptr(data), float(c), float(tol),
+                                                       int(max_iter), int(restart), ctypes.byref(out)))
+        return out.value
+
     def info(self):
         pi = PlanInfo()
         _check(load_library().bem_get_info(self._h, ctypes.byref(pi)))
@@ -296,6 +308,12 @@ class Batch:
 
     def apply(self, stream=None):
         _check(load_library().bem_batch_apply(self._h, _stream_ptr(stream)))
+
+    def tune(self, reps=10):
+        """Measured number of capture streams (bem_tune_batch); returns it."""
+        out = ctypes.c_int()
+        _check(load_library().bem_tune_batch(self._h, int(reps), ctypes.byref(out)))
+        return out.value
 
     def solve(self, bc, data, c=0.5, tol=1e-6, max_iter=2000, restart=100, x0=None, stream=None):
         """Lockstep GMRES over every plan's system (bem_batch_solve).  bc, data,

@@ -1,0 +1,151 @@
+// Measured choices the shape of a problem does not fix by itself:
+//   - the number of forked capture streams of a batch graph (how many of the
+//     geometries' applies run side by side);
+//   - the block size of the block-Jacobi preconditioner (fewer GMRES
+//     iterations against a costlier block inversion and apply).
+// Each candidate is timed on the device with the caller's own data; the
+// winner is kept in a process-wide table keyed by the problem's shape, so
+// later plans or batches of the same shape take it without timing again.
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bem_internal.h"
+
+namespace bemfft {
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+
+static bool tune_lookup(const std::string& key, int* v) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *v = it->second;
+  return true;
+}
+
+static void tune_store(const std::string& key, int v) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = v;
+}
+
+static std::string plan_shape(const bem_plan_s* p) {
+  return std::to_string(p->dim) + "/" + std::to_string(p->kernel) + "/" + std::to_string(p->n) + "/" +
+         std::to_string(p->nb) + "/" + std::to_string(p->prec);
+}
+
+// (re)create S side streams and 2S events and capture the batch graph again
+static bem_status batch_set_streams(bem_batch_s* b, int S) {
+  if (S == b->nstreams && b->exec) return BEM_OK;
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->events) cudaEventDestroy(e);
+  b->side.clear();
+  b->events.clear();
+  for (int s = 0; s < S; ++s) {
+    cudaStream_t x;
+    BEM_CUDA_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    b->side.push_back(x);
+  }
+  for (int s = 0; s < 2 * S; ++s) {
+    cudaEvent_t e;
+    BEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->events.push_back(e);
+  }
+  b->nstreams = S;
+  batch_solve_free(b);  // its step graph was captured with the old streams
+  return batch_capture(b);
+}
+
+}  // namespace bemfft
+
+using namespace bemfft;
+
+extern "C" {
+
+bem_status bem_tune_batch(bem_batch_t b, int reps, int* streams_out) {
+  if (!b || reps < 1) {
+    set_error("bem_tune_batch: need a batch and reps >= 1");
+    return BEM_ERR_ARG;
+  }
+  std::string key = "batch";
+  for (auto* p : b->plans) key += ":" + plan_shape(p);
+  key += ":" + std::to_string((int)b->layer);
+  int best = 0;
+  bem_status rc;
+  if (!tune_lookup(key, &best)) {
+    cudaStream_t st = b->side.empty() ? nullptr : b->side[0];
+    cudaStream_t ts;
+    BEM_CUDA_TRY(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    BEM_CUDA_TRY(cudaEventCreate(&e0));
+    BEM_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 0.0f;
+    (void)st;
+    for (int S : {1, 2, 4, 8}) {
+      if ((rc = batch_set_streams(b, S)) != BEM_OK) return rc;
+      for (int i = 0; i < 2; ++i) BEM_CUDA_TRY(cudaGraphLaunch(b->exec, ts));
+      BEM_CUDA_TRY(cudaEventRecord(e0, ts));
+      for (int i = 0; i < reps; ++i) BEM_CUDA_TRY(cudaGraphLaunch(b->exec, ts));
+      BEM_CUDA_TRY(cudaEventRecord(e1, ts));
+      BEM_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      BEM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (best == 0 || ms < best_ms) {
+        best = S;
+        best_ms = ms;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(ts);
+    tune_store(key, best);
+  }
+  if ((rc = batch_set_streams(b, best)) != BEM_OK) return rc;
+  if (streams_out) *streams_out = best;
+  return BEM_OK;
+}
+
+bem_status bem_tune_preconditioner(bem_plan_t p, const uint8_t* bc, const double* data, double c, double tol,
+                                   int max_iter, int restart, int* block_out) {
+  if (!p || !bc || !data || !(tol > 0.0)) {
+    set_error("bem_tune_preconditioner: null argument or tol <= 0");
+    return BEM_ERR_ARG;
+  }
+  const std::string key = "pc:" + plan_shape(p) + ":" + std::to_string(p->companion != nullptr) + ":" +
+                          std::to_string((int)std::floor(std::log10(tol)));
+  int best = 0;
+  bem_status rc;
+  if (!tune_lookup(key, &best)) {
+    const int64_t M = p->nb * p->ncomp;
+    std::vector<double> u(M), q(M);
+    std::vector<int> cand;
+    for (int bs : {32, 64, 128, 256})
+      if (bs * p->ncomp <= (p->dim == 2 ? 128 : 192)) cand.push_back(bs);  // device-built or small host blocks
+    double best_s = 0.0;
+    for (int bs : cand) {
+      if ((rc = bem_set_preconditioner(p, 1, bs)) != BEM_OK) return rc;
+      bem_solve_info info{};
+      const auto t0 = std::chrono::steady_clock::now();  // includes building the preconditioner
+      rc = bem_solve(p, bc, data, c, tol, max_iter, restart, nullptr, u.data(), q.data(), &info, nullptr);
+      const double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (rc != BEM_OK && rc != BEM_ERR_NOT_CONVERGED) return rc;
+      if (rc == BEM_OK && (best == 0 || s < best_s)) {
+        best = bs;
+        best_s = s;
+      }
+    }
+    if (best == 0) {
+      set_error("bem_tune_preconditioner: no candidate block size converged");
+      return BEM_ERR_NOT_CONVERGED;
+    }
+    tune_store(key, best);
+  }
+  if ((rc = bem_set_preconditioner(p, 1, best)) != BEM_OK) return rc;
+  if (block_out) *block_out = best;
+  return BEM_OK;
+}
+
+}  // extern "C"

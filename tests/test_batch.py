@@ -177,3 +177,41 @@ def test_batch_solve_3d_and_initial_guess(torch_cuda, oracle_mod):
     assert st2 == 0 and infos2[0]["iters"] <= 2, infos2[0]
     assert np.linalg.norm(q2 - np.concatenate(refs)) / np.linalg.norm(np.concatenate(refs)) <= 1e-9
     batch.close()
+
+
+def test_tuned_choices_are_cached_and_keep_results(torch_cuda):
+    """The autotuner picks a stream count for a batch and a preconditioner
+    block for a plan, stores them by shape (a second call returns at once with
+    the same choice), and the tuned objects give the same results."""
+    import time
+    from paper_1809_00845_gb300.bem import Batch, Plan
+    rng = np.random.default_rng(11)
+    bounds = [I.curve_boundary(n, I.random_star_curve(rng)) for n in (512, 256, 1024, 512)]
+    plans = [Plan.from_boundary(b, "laplace2d", "f32") for b in bounds]
+    batch = Batch(plans, "single", streams=4)
+    src = torch_cuda.from_numpy(rng.standard_normal(batch.total).astype(np.float32)).cuda()
+    raw_in = _as_tensor(torch_cuda, batch.d_in, batch.total)
+    raw_out = _as_tensor(torch_cuda, batch.d_out, batch.total)
+    raw_in.copy_(src)
+    batch.apply()
+    torch_cuda.cuda.synchronize()
+    before = raw_out.clone()
+    s1 = batch.tune(reps=5)
+    assert s1 in (1, 2, 4, 8)
+    t0 = time.perf_counter()
+    assert batch.tune(reps=5) == s1
+    assert time.perf_counter() - t0 < 0.5
+    batch.apply()
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.equal(raw_out, before)
+    batch.close()
+    b = bounds[2]
+    u, q = I.boundary_data(b, I.field_expcos)
+    bc = I.mixed_bc_theta(b)
+    data = np.where(bc == 0, u, q)
+    p = plans[2]
+    bs = p.tune_preconditioner(bc, data, tol=1e-5)
+    assert bs in (32, 64, 128)
+    assert p.tune_preconditioner(bc, data, tol=1e-5) == bs
+    _, _, info = p.solve(bc, data, tol=1e-5, restart=100)
+    assert info["status"] == 0
