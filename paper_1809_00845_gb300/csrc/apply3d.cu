@@ -137,9 +137,9 @@ static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in
   }
   Passes3D<T>{p}.on([&](auto k) {
     using KK = decltype(k);
-    KK::yfwd(op.nf, nb, p->d_lptr, p->d_x3, val, p->d_tw2, B, p->d_qtab, st);
-    KK::zpass(op.nf, op.no, op.lpc, op.d_coup, p->d_specs3, B, p->d_qtab, st);
-    KK::yinv(op.no, B, X, p->d_qtab, st);
+    KK::yfwd(op.nf, nb, p->d_lptr, p->d_x3, val, p->d_tw2, B, p->d_ptab3, st);
+    KK::zpass(op.nf, op.no, op.lpc, op.d_coup, p->d_specs3, B, p->d_ptab3, st);
+    KK::yinv(op.no, B, X, p->d_ptab3, st);
     return 0;
   });
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
@@ -195,6 +195,33 @@ bem_status setup_apply_3d(bem_plan_s* p, int maxnf) {
   for (int i = 0; i < 64; ++i) {
     re.push_back(std::cos(2 * PI * i / (double)N));
     im.push_back(std::sin(2 * PI * i / (double)N));
+  }
+  // Stockham pass twiddles of the line FFTs: pass q >= 1 (Ns = 16^q, radix R)
+  // holds e^{2 pi i k r / (Ns R)} at off(q) + r Ns + k
+  {
+    std::vector<double> pre, pim;
+    const int npass = (p->log2N + 3) / 4;
+    for (int q = 1; q < npass; ++q) {
+      const int left = p->log2N - 4 * q;
+      const int64_t R = left > 4 ? 16 : (1 << left), Ns = (int64_t)1 << (4 * q);
+      for (int64_t r = 0; r < R; ++r)
+        for (int64_t k = 0; k < Ns; ++k) {
+          pre.push_back(std::cos(2 * PI * (double)(k * r) / (double)(Ns * R)));
+          pim.push_back(std::sin(2 * PI * (double)(k * r) / (double)(Ns * R)));
+        }
+    }
+    const size_t np = std::max<size_t>(pre.size(), 1);
+    if (p->prec == BEM_F64) {
+      std::vector<cplx<double>> t(np);
+      for (size_t i = 0; i < pre.size(); ++i) t[i] = {pre[i], pim[i]};
+      BEM_CUDA_TRY(cudaMalloc(&p->d_ptab3, np * sizeof(t[0])));
+      BEM_CUDA_TRY(cudaMemcpy(p->d_ptab3, t.data(), np * sizeof(t[0]), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<cplx<float>> t(np);
+      for (size_t i = 0; i < pre.size(); ++i) t[i] = {(float)pre[i], (float)pim[i]};
+      BEM_CUDA_TRY(cudaMalloc(&p->d_ptab3, np * sizeof(t[0])));
+      BEM_CUDA_TRY(cudaMemcpy(p->d_ptab3, t.data(), np * sizeof(t[0]), cudaMemcpyHostToDevice));
+    }
   }
   const size_t m = re.size();
   if (p->prec == BEM_F64) {

@@ -148,6 +148,7 @@ struct bem_plan_s {
   uint16_t* d_x3 = nullptr;     // x per sorted cell
   uint32_t* d_yz3 = nullptr;    // y | z << 16 per sorted cell
   void* d_tw2 = nullptr;        // 2-level twiddles (N/64 + 64)
+  void* d_ptab3 = nullptr;      // Stockham pass twiddles of the 3D line FFTs
   void* d_val3 = nullptr;       // maxnf * nb
   void* d_X3 = nullptr;         // maxnf * (n+1) * n * n complex
   void* d_B3 = nullptr;         // maxnf * (n+1) * N * n complex

@@ -656,6 +656,7 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_x3);
   cudaFree(p->d_yz3);
   cudaFree(p->d_tw2);
+  cudaFree(p->d_ptab3);
   cudaFree(p->d_val3);
   cudaFree(p->d_X3);
   cudaFree(p->d_B3);

@@ -52,11 +52,11 @@ struct Line3D {
 // One Stockham pass of radix R, compile-time position in the transform.
 // LOWIN: the first pass's inputs 8..15 are zero.
 template <int LOG2N, int R, int LOG2NS, int DIR, bool LAST, bool LOWIN, typename T>
-__device__ __forceinline__ void stockham_ct(cplx<T> (&v)[16], const int t, const Twiddles<T>& tw, cplx<T>* sbuf) {
+__device__ __forceinline__ void stockham_ct(cplx<T> (&v)[16], const int t, const cplx<T>* pt, cplx<T>* sbuf) {
   using L = Line3D<LOG2N>;
   constexpr int S = 16 / R;
-  constexpr int LR = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
   constexpr int Ns = 1 << LOG2NS;
+  constexpr int OFF = PassTab<LOG2N>::off(LOG2NS / 4);
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int b = t + s * L::TT;
@@ -65,9 +65,12 @@ __device__ __forceinline__ void stockham_ct(cplx<T> (&v)[16], const int t, const
 #pragma unroll
     for (int r = 0; r < R; ++r) u[r] = v[s + r * S];
     if constexpr (Ns > 1) {
-      const int m1 = k << (LOG2N - LOG2NS - LR);
 #pragma unroll
-      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw.template get<DIR>(m1 * r));
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = pt[OFF + r * Ns + k];
+        if constexpr (DIR < 0) w.y = -w.y;
+        u[r] = cmul(u[r], w);
+      }
     }
     if constexpr (LOWIN && R == 16) dft16_lowhalf<DIR>(u);
     else dft<R, DIR>(u);
@@ -92,7 +95,7 @@ __device__ __forceinline__ void stockham_ct(cplx<T> (&v)[16], const int t, const
 // LOG2N is not a multiple of 4.  Natural order in and out (positions
 // t + m*TT).  Outputs the caller never reads are dead code after inlining.
 template <int LOG2N, int DIR, bool LOWIN, typename T, int PASS = 0>
-__device__ __forceinline__ void fft_ct(cplx<T> (&v)[16], const int t, const Twiddles<T>& tw, cplx<T>* sbuf) {
+__device__ __forceinline__ void fft_ct(cplx<T> (&v)[16], const int t, const cplx<T>* tw, cplx<T>* sbuf) {
   constexpr int done = 4 * PASS;
   constexpr int left = LOG2N - done;
   static_assert(left >= 1, "line too short");
@@ -119,12 +122,12 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
   const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
   const int kx = blockIdx.y, z0 = blockIdx.x * ZB, f = blockIdx.z;
   cplx<T>* sq = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* stw = sq + N / 4;
+  cplx<T>* stw = sq + PassTab<LOG2N>::size();
   cplx<T>* sbuf = stw + NHI + 64;  // ZB line buffers, later the tile
-  for (int i = threadIdx.x; i < N / 4; i += blockDim.x) sq[i] = qtab[i];
+  for (int i = threadIdx.x; i < PassTab<LOG2N>::size(); i += blockDim.x) sq[i] = qtab[i];
   for (int i = threadIdx.x; i < NHI + 64; i += blockDim.x) stw[i] = tw2[i];
   __syncthreads();
-  const Twiddles<T> tw{sq, LOG2N - 2};
+  const cplx<T>* tw = sq;
   const Tw64<T> t64{stw, stw + NHI};
   // x-DFT of the lines (y = t + m*TT, z = z0 + g) from the cells of each line
   const T* vf = val + (size_t)f * nb;
@@ -178,11 +181,11 @@ __global__ void __launch_bounds__(512) k3_zpass(int nf, int no, int LPC, const i
   const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
   const int kx = blockIdx.y, ky = blockIdx.x * LPC + g;
   cplx<T>* sq = reinterpret_cast<cplx<T>*>(smem_raw);
-  for (int i = threadIdx.x; i < N / 4; i += blockDim.x) sq[i] = qtab[i];
+  for (int i = threadIdx.x; i < PassTab<LOG2N>::size(); i += blockDim.x) sq[i] = qtab[i];
   __syncthreads();
-  const Twiddles<T> tw{sq, LOG2N - 2};
+  const cplx<T>* tw = sq;
   const size_t per_line = (size_t)L::SBUF + (no > 1 ? (size_t)nf * N : 0);
-  cplx<T>* sbuf = sq + N / 4 + (size_t)g * per_line;
+  cplx<T>* sbuf = sq + PassTab<LOG2N>::size() + (size_t)g * per_line;
   cplx<T>* xh = sbuf + L::SBUF;  // nf spectra of this column (several outputs only)
   const size_t fstride = (size_t)(n + 1) * N * n;
   const size_t col = ((size_t)kx * N + ky) * n;
@@ -266,8 +269,8 @@ __global__ void __launch_bounds__(512) k3_yinv(const cplx<T>* __restrict__ B, cp
   const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
   const int kx = blockIdx.y, z0 = blockIdx.x * ZB, o = blockIdx.z;
   cplx<T>* sq = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* sbuf = sq + N / 4;
-  for (int i = threadIdx.x; i < N / 4; i += blockDim.x) sq[i] = qtab[i];
+  cplx<T>* sbuf = sq + PassTab<LOG2N>::size();
+  for (int i = threadIdx.x; i < PassTab<LOG2N>::size(); i += blockDim.x) sq[i] = qtab[i];
   const cplx<T>* src = B + ((size_t)o * (n + 1) + kx) * (size_t)N * n + z0;
   cplx<T>* tile = sbuf;
   for (int i = threadIdx.x; i < N * ZB; i += blockDim.x) {
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(512) k3_yinv(const cplx<T>* __restrict__ B, cp
     tile[(size_t)ky * (ZB + 1) + zz] = src[(size_t)ky * n + zz];
   }
   __syncthreads();
-  const Twiddles<T> tw{sq, LOG2N - 2};
+  const cplx<T>* tw = sq;
   cplx<T> v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = tile[(size_t)(t + m * TT) * (ZB + 1) + g];
@@ -293,7 +296,7 @@ size_t Fft3DKernels<T, LOG2N>::smem_y() {
   using L = Line3D<LOG2N>;
   constexpr int ZB = L::LPB < L::n ? L::LPB : L::n;
   constexpr size_t lines = (size_t)ZB * L::SBUF, tile = (size_t)L::N * (ZB + 1);
-  return (size_t)(L::N / 4 + (L::N >= 64 ? L::N / 64 : 1) + 64) * sizeof(cplx<T>) +
+  return (size_t)(PassTab<LOG2N>::size() + (L::N >= 64 ? L::N / 64 : 1) + 64) * sizeof(cplx<T>) +
          (lines > tile ? lines : tile) * sizeof(cplx<T>);
 }
 
@@ -326,7 +329,7 @@ void Fft3DKernels<T, LOG2N>::zpass(int nf, int no, int lpc, const int16_t* coup,
                                    const void* qtab, cudaStream_t st) {
   using L = Line3D<LOG2N>;
   const size_t per_line = (size_t)L::SBUF + (no > 1 ? (size_t)nf * L::N : 0);
-  const size_t smem = ((size_t)L::N / 4 + (size_t)lpc * per_line) * sizeof(cplx<T>);
+  const size_t smem = ((size_t)PassTab<LOG2N>::size() + (size_t)lpc * per_line) * sizeof(cplx<T>);
   k3_zpass<T, LOG2N><<<dim3(L::N / lpc, L::n + 1), lpc * L::TT, smem, st>>>(
       nf, no, lpc, coup, specs, static_cast<cplx<T>*>(B), static_cast<const cplx<T>*>(qtab));
 }
