@@ -45,12 +45,22 @@ struct Line3D {
   static constexpr int n = N / 2;
   static constexpr int TT = N / 16;                     // threads per line
   static constexpr bool WARP = TT <= 32;                // lines never straddle warps
-  static constexpr int LPB = TT >= 64 ? 512 / TT : 16;  // lines per block (y passes: z planes)
+  static constexpr int LPB = TT >= 64 ? 512 / TT : 16;  // lines per block of the z pass
   static constexpr int SBUF = N + N / 16;               // padded exchange buffer per line
 };
 
 // One Stockham pass of radix R, compile-time position in the transform.
 // LOWIN: the first pass's inputs 8..15 are zero.
+// z planes per block of the y passes (16: wider blocks give longer contiguous
+// z runs of B but were measured slower, 32 planes lowering the resident warps)
+template <typename T, int LOG2N>
+__host__ __device__ constexpr int yblock() {
+  constexpr int TT = Line3D<LOG2N>::TT, n = Line3D<LOG2N>::n;
+  constexpr int want = 16;
+  constexpr int lim = TT * want > 512 ? 512 / TT : want;
+  return lim < n ? lim : n;
+}
+
 template <int LOG2N, int R, int LOG2NS, int DIR, bool LAST, bool LOWIN, typename T>
 __device__ __forceinline__ void stockham_ct(cplx<T> (&v)[16], const int t, const cplx<T>* pt, cplx<T>* sbuf) {
   using L = Line3D<LOG2N>;
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
                                                const cplx<T>* __restrict__ tw2, cplx<T>* __restrict__ B,
                                                const cplx<T>* __restrict__ qtab) {
   using L = Line3D<LOG2N>;
-  constexpr int N = L::N, n = L::n, TT = L::TT, ZB = L::LPB < n ? L::LPB : n;
+  constexpr int N = L::N, n = L::n, TT = L::TT, ZB = yblock<T, LOG2N>();
   constexpr int NHI = N >= 64 ? N / 64 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
@@ -264,7 +274,7 @@ template <typename T, int LOG2N>
 __global__ void __launch_bounds__(512) k3_yinv(const cplx<T>* __restrict__ B, cplx<T>* __restrict__ X,
                                                const cplx<T>* __restrict__ qtab) {
   using L = Line3D<LOG2N>;
-  constexpr int N = L::N, n = L::n, TT = L::TT, ZB = L::LPB < n ? L::LPB : n;
+  constexpr int N = L::N, n = L::n, TT = L::TT, ZB = yblock<T, LOG2N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
   const int kx = blockIdx.y, z0 = blockIdx.x * ZB, o = blockIdx.z;
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(512) k3_yinv(const cplx<T>* __restrict__ B, cp
 template <typename T, int LOG2N>
 size_t Fft3DKernels<T, LOG2N>::smem_y() {
   using L = Line3D<LOG2N>;
-  constexpr int ZB = L::LPB < L::n ? L::LPB : L::n;
+  constexpr int ZB = yblock<T, LOG2N>();
   constexpr size_t lines = (size_t)ZB * L::SBUF, tile = (size_t)L::N * (ZB + 1);
   return (size_t)(PassTab<LOG2N>::size() + (L::N >= 64 ? L::N / 64 : 1) + 64) * sizeof(cplx<T>) +
          (lines > tile ? lines : tile) * sizeof(cplx<T>);
@@ -303,7 +313,7 @@ size_t Fft3DKernels<T, LOG2N>::smem_y() {
 template <typename T, int LOG2N>
 int Fft3DKernels<T, LOG2N>::zblock() {
   using L = Line3D<LOG2N>;
-  return L::LPB < L::n ? L::LPB : L::n;
+  return yblock<T, LOG2N>();
 }
 
 template <typename T, int LOG2N>
