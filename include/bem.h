@@ -183,7 +183,7 @@ bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, dou
  *   e.g. arclength along a curve, so that a block is a connected piece of S);
  *   the blocks are assembled from the same kernel point values as the
  *   operator when a solve first needs them after bem_set_bc, and inverted on
- *   the device in FP32 (2D, block_size <= 128) or in FP64 on the host.
+ *   the device in FP32 (2D, block_size <= 512) or in FP64 on the host.
  * The paper solves without a preconditioner (Section 4); the single layer is
  * a first-kind operator whose condition number grows with n, so unpreconditioned
  * restarted GMRES stalls on mixed problems. */
@@ -263,8 +263,8 @@ bem_status bem_batch_solve(bem_batch_t batch, const uint8_t* bc, const double* d
  *   (candidates 1, 2, 4, 8; `reps` timed replays each); the batch is captured
  *   again with the winner, returned in *streams (may be NULL).
  * bem_tune_preconditioner: the block size of the block-Jacobi preconditioner
- *   (candidates 32, 64, 128 cells, within 128 unknowns per block in 2D and 192
- *   in 3D), by the wall time of a full bem_solve with these arguments,
+ *   (candidates 32, 64, 128, 256 cells, within 256 unknowns per block in 2D
+ *   and 192 in 3D), by the wall time of a full bem_solve with these arguments,
  *   including the block inversion; the plan keeps the winner, returned in
  *   *block (may be NULL).  BEM_ERR_NOT_CONVERGED when no candidate converges. */
 bem_status bem_tune_batch(bem_batch_t batch, int reps, int* streams);

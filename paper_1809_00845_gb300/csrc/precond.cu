@@ -8,11 +8,11 @@
 // cells and using those inverses as a right preconditioner removes most of
 // that ill-conditioning.  Blocks are runs of consecutive cells in the
 // caller's order.  Entries are the same kernel point values (and singular-cell
-// average) as the FFT tables.  2D blocks of up to 128 unknowns are assembled
+// average) as the FFT tables.  2D blocks of up to 512 unknowns are assembled
 // and inverted on the device, one CTA per block (Gauss-Jordan with partial
-// pivoting in FP32 shared memory: the preconditioner only has to be a fixed
-// nonsingular approximation of the block inverse); other blocks are assembled
-// and inverted in FP64 on the host.
+// pivoting in FP32: the preconditioner only has to be a fixed nonsingular
+// approximation of the block inverse); other blocks are assembled and
+// inverted in FP64 on the host.
 #include <cmath>
 #include <vector>
 
@@ -111,29 +111,35 @@ static bool invert(std::vector<double>& A, int m) {
   return true;
 }
 
-constexpr int kPcGpuMax = 128;  // largest block assembled and inverted on the device
+constexpr int kPcSmemMax = 128;  // largest block inverted in shared memory
+constexpr int kPcGpuMax = 512;   // largest block inverted on the device (in global scratch beyond 128)
 constexpr int kPcThreads = 256;
 
 // One CTA per block of bs consecutive caller-order cells (2D Laplace): the
 // block of the BC-split operator (U for Dirichlet columns, Q.n for Neumann
 // columns minus c on their diagonal), Gauss-Jordan with partial pivoting in
-// shared memory, inverse written as FP64 (padded to m x m).  A block whose
-// pivot vanishes gets the identity.
-__global__ void __launch_bounds__(kPcThreads) k_pc_build2d(int64_t nb, int bs, double h, double c,
+// shared memory (blocks up to 128 cells) or in an L2-resident global scratch
+// (up to 512), inverse written as FP64 (padded to m x m).  A block whose pivot
+// vanishes gets the identity.
+template <bool GLOBAL, int NT = GLOBAL ? 1024 : kPcThreads>
+__global__ void __launch_bounds__(NT) k_pc_build2d(int64_t nb, int bs, double h, double c,
                                                           const int32_t* __restrict__ cell,
                                                           const double* __restrict__ w,
                                                           const double* __restrict__ nrm,
-                                                          const uint8_t* __restrict__ bc, double* __restrict__ inv) {
+                                                          const uint8_t* __restrict__ bc, double* __restrict__ inv,
+                                                          float* __restrict__ scratch) {
   extern __shared__ float pcs[];
   __shared__ int s_piv;
   __shared__ int s_bad;
   const int b = blockIdx.x, tid = threadIdx.x;
   const int64_t i0 = (int64_t)b * bs;
   const int sz = (int)(nb - i0 < bs ? nb - i0 : bs);
-  float* A = pcs;
+  // working matrices: shared memory, or this block's slice of a global
+  // scratch (L2-resident) for blocks too large for shared memory
+  float* A = GLOBAL ? scratch + (size_t)b * (2 * (size_t)bs * bs + bs) : pcs;
   float* I = A + sz * sz;
   float* fac = I + sz * sz;
-  for (int e = tid; e < sz * sz; e += kPcThreads) {
+  for (int e = tid; e < sz * sz; e += NT) {
     const int ia = e / sz, jb = e - ia * sz;
     const int64_t i = i0 + ia, j = i0 + jb;
     const int dx = cell[2 * i] - cell[2 * j], dy = cell[2 * i + 1] - cell[2 * j + 1];
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_build2d(int64_t nb, int bs, d
     if (s_bad) break;
     const int piv = s_piv;
     if (piv != col)
-      for (int k = tid; k < sz; k += kPcThreads) {
+      for (int k = tid; k < sz; k += NT) {
         float t = A[piv * sz + k];
         A[piv * sz + k] = A[col * sz + k];
         A[col * sz + k] = t;
@@ -187,14 +193,14 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_build2d(int64_t nb, int bs, d
       }
     __syncthreads();
     const float pinv = 1.0f / A[col * sz + col];
-    for (int r = tid; r < sz; r += kPcThreads) fac[r] = r == col ? 0.0f : A[r * sz + col];
+    for (int r = tid; r < sz; r += NT) fac[r] = r == col ? 0.0f : A[r * sz + col];
     __syncthreads();
-    for (int k = tid; k < sz; k += kPcThreads) {
+    for (int k = tid; k < sz; k += NT) {
       A[col * sz + k] *= pinv;
       I[col * sz + k] *= pinv;
     }
     __syncthreads();
-    for (int e = tid; e < sz * sz; e += kPcThreads) {
+    for (int e = tid; e < sz * sz; e += NT) {
       const int r = e / sz, k = e - r * sz;
       const float f = fac[r];
       if (f != 0.0f) {
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_build2d(int64_t nb, int bs, d
   }
   const int m = bs;
   double* dst = inv + (size_t)b * m * m;
-  for (int e = tid; e < m * m; e += kPcThreads) {
+  for (int e = tid; e < m * m; e += NT) {
     const int a = e / m, k = e - a * m;
     double v = 0.0;
     if (a < sz && k < sz) v = s_bad ? (a == k ? 1.0 : 0.0) : (double)I[a * sz + k];
@@ -235,18 +241,26 @@ static bem_status build_preconditioner_gpu2d(bem_plan_s* p) {
   }
   cudaFree(p->pc.d_inv);
   p->pc.d_inv = nullptr;
-  const size_t smem = ((size_t)2 * bs * bs + bs) * sizeof(float);
+  const size_t per = ((size_t)2 * bs * bs + bs) * sizeof(float);
+  const bool global = bs > kPcSmemMax;
+  float* d_scr = nullptr;
   cudaError_t e = cudaMalloc(&p->pc.d_inv, (size_t)nblocks * bs * bs * sizeof(double));
+  if (e == cudaSuccess && global) e = cudaMalloc(&d_scr, (size_t)nblocks * per);
   if (e == cudaSuccess) e = cudaMemcpy(d_cell, p->h_cell_user.data(), nb * 2 * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_w, p->h_w_user.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_n, p->h_normal_user.data(), nb * 2 * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_bc, p->h_bc.data(), nb, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = allow_optin_smem(k_pc_build2d);
+  if (e == cudaSuccess && !global) e = allow_optin_smem(k_pc_build2d<false>);
   if (e == cudaSuccess) {
-    k_pc_build2d<<<nblocks, kPcThreads, smem>>>(nb, bs, p->h, p->c, d_cell, d_w, d_n, d_bc, p->pc.d_inv);
+    if (global)
+      k_pc_build2d<true><<<nblocks, 1024, 0>>>(nb, bs, p->h, p->c, d_cell, d_w, d_n, d_bc, p->pc.d_inv, d_scr);
+    else
+      k_pc_build2d<false><<<nblocks, kPcThreads, per>>>(nb, bs, p->h, p->c, d_cell, d_w, d_n, d_bc, p->pc.d_inv,
+                                                        nullptr);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_scr);
   cleanup();
   if (e != cudaSuccess) {
     set_error(std::string("preconditioner: ") + cudaGetErrorString(e));

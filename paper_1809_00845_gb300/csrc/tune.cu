@@ -123,7 +123,7 @@ bem_status bem_tune_preconditioner(bem_plan_t p, const uint8_t* bc, const double
     std::vector<double> u(M), q(M);
     std::vector<int> cand;
     for (int bs : {32, 64, 128, 256})
-      if (bs * p->ncomp <= (p->dim == 2 ? 128 : 192)) cand.push_back(bs);  // device-built or small host blocks
+      if (bs * p->ncomp <= (p->dim == 2 ? 256 : 192)) cand.push_back(bs);  // device-built or small host blocks
     double best_s = 0.0;
     for (int bs : cand) {
       if ((rc = bem_set_preconditioner(p, 1, bs)) != BEM_OK) return rc;
