@@ -114,3 +114,19 @@ def test_cube_kelvin_n128_full_size_sampled_rows(torch_cuda, oracle_mod):
         out = gpu_apply(torch_cuda, plan, layer, x).reshape(-1, 3)
         ref = oracle_mod.apply("kelvin3d", lid, b.cell, b.h, b.w, b.normal, x, rows=(1000, 128))
         assert rel_l2(out[1000:1128], ref) <= TOL["f32"], layer
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_largest_3d_grid_sampled_rows(torch_cuda, oracle_mod, prec):
+    """The largest supported 3D grid, n = 512 (padded 1024^3: line FFTs span
+    two warps, 8 planes per y-pass block), a small ellipsoid of 46k cells,
+    single and double layer; the oracle evaluates sampled target rows."""
+    b = I.ellipsoid_boundary(512, axes=(0.12, 0.1, 0.08))
+    rng = I.rng_for(4)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, "laplace3d", prec)
+    for layer, lid in (("single", 0), ("double", 1)):
+        out = gpu_apply(torch_cuda, plan, layer, x)
+        for row0 in (0, b.nb - 200):
+            ref = oracle_mod.apply("laplace3d", lid, b.cell, b.h, b.w, b.normal, x, rows=(row0, 200))
+            assert rel_l2(out[row0:row0 + 200], ref) <= TOL[prec], (layer, row0)
