@@ -520,6 +520,8 @@ def run_ours(args):
     # (same preconditioner, FP32 residuals) for comparison
     solve = None
     if not args.no_solve:
+        # block size measured on the refined solve (plain FP32 cannot reach 1e-6 here)
+        plan.enable_refinement(args.precision == "f32")
         pc_block = plan.tune_preconditioner(bc, data, tol=1e-6, restart=100, max_iter=3000)
 
         def run_solve(refine):
