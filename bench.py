@@ -64,6 +64,19 @@ def dist_env():
     return rank, world, local
 
 
+def replica_throughput(ms_local, steps, world, device=None):
+    """Whole-job applies/s of `world` independent replicas: every rank ran
+    `steps` applies in ms_local milliseconds; the job's time is the slowest
+    rank's (max over ranks).  Returns (ms_max, applies per second)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1e3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -484,12 +497,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     col_ms, col_launches = plan.kernel_time()
     plan.set_kernel_timing(False)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max, value = replica_throughput(ms, args.steps, world, dev)
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.empty(b.nb, dtype=tdt, pin_memory=True)
