@@ -71,8 +71,22 @@ typedef enum { BEM_LAPLACE_2D = 0, BEM_LAPLACE_3D = 1, BEM_KELVIN_3D = 2 } bem_k
  * 48-bit significand) on the FP32 pipes, double I/O; about 1e-13 relative
  * accuracy at several times the speed of FP64 on GPUs with reduced FP64
  * throughput.  BEM_F32X2 is available for 2D plans with n >= 256 (the
- * four-step column kernel) and returns BEM_ERR_UNSUPPORTED otherwise. */
-typedef enum { BEM_F64 = 0, BEM_F32 = 1, BEM_F32X2 = 2 } bem_precision;
+ * four-step column kernel) and returns BEM_ERR_UNSUPPORTED otherwise.
+ * BEM_TC_BF16X3, BEM_TC_F16X3: FP32 I/O and arithmetic except the radix-16
+ * DFT stages of the column transforms (Eq. 16), which run on the tensor cores
+ * as DFT-matrix products with every FP32 operand split into a 16-bit hi and
+ * lo part (BF16, or FP16 with each line scaled by a power of two) and three
+ * products accumulated in FP32.  2D plans with n = 1024, 2048 or 4096 only
+ * (BEM_ERR_UNSUPPORTED otherwise).  The paper transforms in full precision;
+ * these are an added speed/accuracy trade-off, with the error bound stated
+ * where they are tested. */
+typedef enum {
+  BEM_F64 = 0,
+  BEM_F32 = 1,
+  BEM_F32X2 = 2,
+  BEM_TC_BF16X3 = 3,
+  BEM_TC_F16X3 = 4
+} bem_precision;
 
 /* BEM_SINGLE: S (Laplace) or U (Kelvin).  BEM_DOUBLE: D (Laplace) or T
  * (Kelvin).  BEM_SYSTEM: the boundary-condition-split operator A of the last
@@ -211,6 +225,16 @@ bem_status bem_kernel_time(bem_plan_t plan, double* total_ms, int64_t* launches)
 
 /* Number of kernel launches one apply of the given layer issues. */
 int bem_launches_per_apply(bem_plan_t plan, bem_layer layer);
+
+/* Device-side status of the plan's kernels since the last call (tensor-core
+ * precisions: every wait of a kernel on its tensor-core products is bounded
+ * to about one second; a wait that gave up makes the kernel stop early and
+ * record it).  Synchronises `stream` (cudaStream_t, may be NULL), reads and
+ * clears the record.  Returns BEM_ERR_TIMEOUT when a wait gave up (the
+ * outputs of the applies since the last call are then invalid), else BEM_OK.
+ * No counterpart in the paper: a safeguard of the device implementation.
+ * bem_solve checks it before returning. */
+bem_status bem_device_status(bem_plan_t plan, void* stream);
 
 /* ---- batched apply (many geometries, one CUDA graph) --------------------
  * The applies of `count` plans (one precision, grids of any sizes) captured

@@ -20,15 +20,18 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbem_gb300.so")
 BEM_OK, BEM_ERR_ARG, BEM_ERR_CUDA, BEM_ERR_OOM, BEM_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 BEM_ERR_BREAKDOWN, BEM_ERR_NONFINITE, BEM_ERR_TIMEOUT, BEM_ERR_UNSUPPORTED = 5, 6, 7, 8
 BEM_LAPLACE_2D, BEM_LAPLACE_3D, BEM_KELVIN_3D = 0, 1, 2
-BEM_F64, BEM_F32, BEM_F32X2 = 0, 1, 2
+BEM_F64, BEM_F32, BEM_F32X2, BEM_TC_BF16X3, BEM_TC_F16X3 = 0, 1, 2, 3, 4
 BEM_SINGLE, BEM_DOUBLE, BEM_SYSTEM = 0, 1, 2
 
 KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d": BEM_KELVIN_3D}
-PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32, "f32x2": BEM_F32X2}
+PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32, "f32x2": BEM_F32X2, "tc_bf16x3": BEM_TC_BF16X3,
+              "tc_f16x3": BEM_TC_F16X3}
+# precisions whose plans take and return float32 vectors
+F32_IO = (BEM_F32, BEM_TC_BF16X3, BEM_TC_F16X3)
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
 EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
-            "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_destroy",
+            "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_device_status", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
             "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
             "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
@@ -85,6 +88,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_kernel_time.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.bem_launches_per_apply.argtypes = [P, I]
     lib.bem_launches_per_apply.restype = I
+    lib.bem_device_status.argtypes = [P, P]
     lib.bem_destroy.argtypes = [P]
     lib.bem_status_string.argtypes = [I]
     lib.bem_status_string.restype = ctypes.c_char_p
@@ -117,7 +121,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_last_error.restype = ctypes.c_char_p
     for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
                  "bem_apply_static_scratch", "bem_apply_host", "bem_solve", "bem_get_info",
-                 "bem_set_kernel_timing", "bem_kernel_time", "bem_destroy"):
+                 "bem_set_kernel_timing", "bem_kernel_time", "bem_device_status", "bem_destroy"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -182,11 +186,11 @@ class Plan:
     # --------------------------------------------------------------- helpers
     @property
     def np_dtype(self):
-        return np.float32 if self.precision == BEM_F32 else np.float64
+        return np.float32 if self.precision in F32_IO else np.float64
 
     def _tdtype(self):
         import torch
-        return torch.float32 if self.precision == BEM_F32 else torch.float64
+        return torch.float32 if self.precision in F32_IO else torch.float64
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -283,6 +287,10 @@ class Plan:
     def launches_per_apply(self, layer="system"):
         lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
         return int(load_library().bem_launches_per_apply(self._h, lay))
+
+    def device_status(self, stream=None):
+        """Raise BemError(BEM_ERR_TIMEOUT) if a kernel gave up a bounded device wait since the last check."""
+        _check(load_library().bem_device_status(self._h, _stream_ptr(stream)))
 
 
 class Batch:

@@ -400,22 +400,121 @@ static bem_status setup_t(bem_plan_s* p) {
   return BEM_OK;
 }
 
+// 16-bit encodings (round to nearest even) for the tensor-core B matrices
+static uint16_t bf16_bits(double x) {
+  const float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+static double bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+// |x| < 2 (DFT entries and their residuals)
+static uint16_t f16_bits(double x) {
+  const uint16_t sgn = x < 0 ? 0x8000u : 0u;
+  const double a = std::fabs(x);
+  if (a == 0.0) return sgn;
+  int E;
+  std::frexp(a, &E);  // a in [2^(E-1), 2^E)
+  const int e = E - 1;
+  if (e < -14) return (uint16_t)(sgn | (uint16_t)std::nearbyint(std::ldexp(a, 24)));  // subnormal (or min normal)
+  int q = (int)std::nearbyint((std::ldexp(a, -e) - 1.0) * 1024.0);
+  int eb = e + 15;
+  if (q == 1024) {
+    q = 0;
+    ++eb;
+  }
+  return (uint16_t)(sgn | (uint16_t)(eb << 10) | (uint16_t)q);
+}
+static double f16_value(uint16_t b) {
+  const int eb = (b >> 10) & 31, q = b & 1023;
+  const double v = eb == 0 ? std::ldexp((double)q, -24) : std::ldexp(1.0 + q / 1024.0, eb - 15);
+  return (b & 0x8000u) ? -v : v;
+}
+
+// B operands of the tensor-core stages (tc_dft.cuh): matrix 0 the forward
+// 16-point DFT, matrix 1 the J-point DFT blocks of the middle stage (J =
+// TT / 32), in the real form acting on (re, im) columns, each as hi then lo
+// 16-bit parts in the K-major core-matrix layout.  FP64 angles from the exact
+// index product mod J.
+static std::vector<uint16_t> tc_matrices(int kind, int J) {
+  const double PI = 3.14159265358979323846;
+  std::vector<uint16_t> out(2 * 2048, 0);  // 2 matrices x (hi, lo) x 32 x 32
+  for (int mat = 0; mat < 2; ++mat) {
+    const int B = mat == 0 ? 16 : J;
+    for (int n = 0; n < 32; ++n)
+      for (int k = 0; k < 32; ++k) {
+        const int f = n & 15, co = n >> 4;                 // output element, part
+        const int i = (k >> 4) * 8 + (k & 7), ci = (k >> 3) & 1;  // input element, part
+        double v = 0.0;
+        if (f / B == i / B) {
+          const int m = ((f % B) * (i % B)) % B;
+          double c = std::cos(2.0 * PI * m / B), sn = std::sin(2.0 * PI * m / B);
+          if (std::fabs(c) < 1e-15) c = 0.0;
+          if (std::fabs(sn) < 1e-15) sn = 0.0;
+          // forward: Re X = re c + im s, Im X = im c - re s
+          v = co == 0 ? (ci == 0 ? c : sn) : (ci == 0 ? -sn : c);
+        }
+        uint16_t hb, lb;
+        if (kind == kTcBf16) {
+          hb = bf16_bits(v);
+          lb = bf16_bits(v - bf16_value(hb));
+        } else {
+          hb = f16_bits(v);
+          lb = f16_bits(v - f16_value(hb));
+        }
+        const int idx = ((n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) / 2;
+        out[mat * 2048 + idx] = hb;
+        out[mat * 2048 + 1024 + idx] = lb;
+      }
+  }
+  return out;
+}
+
 // shared memory of the four-step kernel
 template <typename T>
-static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc) {
+static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc, bool tc) {
   const int W = TT / 32;
   const size_t nbuf = (size_t)std::max(16 * TT, W * 544);
   size_t s = (nbuf + (size_t)fstab_entries(TT)) * sizeof(cplx<T>) + (size_t)sspec_entries((int)n) * sizeof(T);
+  if (tc) s += kTcHeader;
   if (accreg) s += (size_t)2 * n * sizeof(cplx<T>);
   if (acc) s += (size_t)nb * sizeof(T);
   return s;
 }
 
 // the column kernels for TT threads: compile-time thread counts for FP32,
-// the generic kernel for FP64
+// the generic kernel for FP64; tc selects the tensor-core stages (FP32,
+// TT = 128, 256, 512; checked at plan time)
+template <int TCK>
+static cudaError_t configure_tc(int TT, size_t smem, int* bps) {
+  switch (TT) {
+    case 512: return Col2DTcKernels<512, TCK>::configure(smem, TT, bps);
+    case 256: return Col2DTcKernels<256, TCK>::configure(smem, TT, bps);
+    default: return Col2DTcKernels<128, TCK>::configure(smem, TT, bps);
+  }
+}
+
+template <int TCK>
+static void launch_tc(const bem_plan_s* p, int nf, const Col2Dv2Params<float>& cp, cudaStream_t st) {
+  const int TT = p->threads;
+  switch (TT) {
+    case 512: Col2DTcKernels<512, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+    case 256: Col2DTcKernels<256, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+    default: Col2DTcKernels<128, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+  }
+}
+
 template <typename T>
-static cudaError_t configure_col2d(int TT, size_t smem, int* bps) {
+static cudaError_t configure_col2d(int TT, int tc, size_t smem, int* bps) {
   if constexpr (std::is_same<T, float>::value) {
+    if (tc == kTcBf16) return configure_tc<kTcBf16>(TT, smem, bps);
+    if (tc == kTcF16) return configure_tc<kTcF16>(TT, smem, bps);
     switch (TT) {
       case 512: return Col2DKernels<float, 512>::configure(smem, TT, bps);
       case 256: return Col2DKernels<float, 256>::configure(smem, TT, bps);
@@ -432,6 +531,8 @@ template <typename T>
 static void launch_col2d(const bem_plan_s* p, int nf, const Col2Dv2Params<T>& cp, cudaStream_t st) {
   const int TT = p->threads;
   if constexpr (std::is_same<T, float>::value) {
+    if (p->tc == kTcBf16) return launch_tc<kTcBf16>(p, nf, cp, st);
+    if (p->tc == kTcF16) return launch_tc<kTcF16>(p, nf, cp, st);
     switch (TT) {
       case 512: Col2DKernels<float, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
       case 256: Col2DKernels<float, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
@@ -521,6 +622,17 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     BEM_CUDA_TRY(cudaMalloc(&p->d_fstab, tab.size() * sizeof(cplx<T>)));
     BEM_CUDA_TRY(cudaMemcpy(p->d_fstab, tab.data(), tab.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
   }
+  if (p->tc) {
+    if (!std::is_same<T, float>::value || (TT != 128 && TT != 256 && TT != 512)) {
+      set_error("tensor-core DFT stages need FP32 and n = 1024, 2048 or 4096");
+      return BEM_ERR_UNSUPPORTED;
+    }
+    const std::vector<uint16_t> mats = tc_matrices(p->tc, TT / 32);
+    BEM_CUDA_TRY(cudaMalloc(&p->d_tcmat, mats.size() * sizeof(uint16_t)));
+    BEM_CUDA_TRY(cudaMemcpy(p->d_tcmat, mats.data(), mats.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    BEM_CUDA_TRY(cudaMalloc(&p->d_status, sizeof(int)));
+    BEM_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
+  }
   BEM_CUDA_TRY(cudaMalloc(&p->d_tinfo, TT * sizeof(int32_t)));
   BEM_CUDA_TRY(cudaMalloc(&p->d_chunk, (TT + 1) * sizeof(int32_t)));
   BEM_CUDA_TRY(cudaMemcpy(p->d_tinfo, tinfo.data(), TT * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -529,14 +641,14 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   BEM_CUDA_TRY(cudaGetDevice(&dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  p->acc_in_smem = smem_v2<T>(n, TT, p->v2_npos, R, true) <= (size_t)smem_optin;
-  p->smem_bytes = smem_v2<T>(n, TT, p->v2_npos, R, p->acc_in_smem);
+  p->acc_in_smem = smem_v2<T>(n, TT, p->v2_npos, R, true, p->tc != 0) <= (size_t)smem_optin;
+  p->smem_bytes = smem_v2<T>(n, TT, p->v2_npos, R, p->acc_in_smem, p->tc != 0);
   if (p->smem_bytes > (size_t)smem_optin) {
     set_error("grid too large for the shared-memory column buffers");
     return BEM_ERR_UNSUPPORTED;
   }
   int bps = 0;
-  BEM_CUDA_TRY(configure_col2d<T>(TT, p->smem_bytes, &bps));
+  BEM_CUDA_TRY(configure_col2d<T>(TT, p->tc, p->smem_bytes, &bps));
   if (bps < 1) {
     set_error("column kernel cannot be resident (registers/shared memory)");
     return BEM_ERR_UNSUPPORTED;
@@ -694,6 +806,8 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.npos = npos;
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
   cp.has_carry = p->v2_carry ? 1 : 0;
+  cp.tcmat = static_cast<const uint4*>(p->d_tcmat);
+  cp.status = p->d_status;
   cudaEvent_t e1 = nullptr;
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   launch_col2d<T>(p, op.nf, cp, st);

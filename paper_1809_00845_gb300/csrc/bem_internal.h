@@ -143,6 +143,9 @@ struct bem_plan_s {
   void* d_val = nullptr;        // nb density pairs (scratch)
   void* d_twc = nullptr;        // grid * npos cached sparse twiddles (scratch)
   void* d_fstab = nullptr;      // twiddle tables of the four-step kernel
+  int tc = 0;                   // tensor-core DFT stages: 0 none, 1 BF16 hi + lo, 2 FP16 hi + lo
+  void* d_tcmat = nullptr;      // their B matrices (hi, lo; 8 KB)
+  int* d_status = nullptr;      // device status word (bit 0: a bounded wait gave up)
   // 3D path
   int32_t* d_lptr = nullptr;    // n*n + 1 line pointers over sorted cells (line = z*n + y)
   uint16_t* d_x3 = nullptr;     // x per sorted cell

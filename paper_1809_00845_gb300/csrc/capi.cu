@@ -196,13 +196,24 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     set_error("bem_plan: dimension does not match the kernel");
     return BEM_ERR_ARG;
   }
-  if (prec != BEM_F64 && prec != BEM_F32 && prec != BEM_F32X2) {
+  if (prec != BEM_F64 && prec != BEM_F32 && prec != BEM_F32X2 && prec != BEM_TC_BF16X3 && prec != BEM_TC_F16X3) {
     set_error("bem_plan: unknown precision");
     return BEM_ERR_ARG;
   }
   if (prec == BEM_F32X2 && (dim != 2 || n[0] < 256)) {
     set_error("bem_plan: BEM_F32X2 needs a 2D grid with n >= 256");
     return BEM_ERR_UNSUPPORTED;
+  }
+  // tensor-core DFT stages: an FP32 plan whose column kernel runs its
+  // radix-16 stages as split 16-bit products
+  int tc = 0;
+  if (prec == BEM_TC_BF16X3 || prec == BEM_TC_F16X3) {
+    if (dim != 2 || (n[0] != 1024 && n[0] != 2048 && n[0] != 4096)) {
+      set_error("bem_plan: tensor-core precisions need a 2D grid with n = 1024, 2048 or 4096");
+      return BEM_ERR_UNSUPPORTED;
+    }
+    tc = prec == BEM_TC_BF16X3 ? 1 : 2;
+    prec = BEM_F32;
   }
   if (flags != 0) {
     set_error("bem_plan: flags must be 0");
@@ -254,6 +265,7 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   p->ncomp = kernel == BEM_KELVIN_3D ? 3 : 1;
   p->kernel = kernel;
   p->prec = prec;
+  p->tc = tc;
   p->pc.bs = dim == 2 ? 128 : 64;  // default block-Jacobi block (cells)
   p->n = nn;
   p->N = 2 * nn;
@@ -548,8 +560,10 @@ bem_status bem_solve(bem_plan_t p, const uint8_t* bc, const double* data, double
     set_error("bem_solve: null pointer argument");
     return BEM_ERR_ARG;
   }
-  return solve_gmres(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info,
-                     static_cast<cudaStream_t>(stream));
+  const bem_status rc = solve_gmres(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info,
+                                    static_cast<cudaStream_t>(stream));
+  const bem_status ds = bem_device_status(p, stream);
+  return ds != BEM_OK ? ds : rc;
 }
 
 bem_status bem_enable_refinement(bem_plan_t p, int enable) {
@@ -584,7 +598,7 @@ bem_status bem_get_info(bem_plan_t p, bem_plan_info* info) {
   info->n = p->n;
   info->N = p->N;
   info->nb = p->nb;
-  info->precision = p->prec;
+  info->precision = p->tc == 1 ? BEM_TC_BF16X3 : (p->tc == 2 ? BEM_TC_F16X3 : p->prec);
   info->grid_ctas = p->grid;
   info->threads_per_cta = p->threads;
   info->scratch_bytes = p->scratch_bytes;
@@ -623,6 +637,23 @@ bem_status bem_kernel_time(bem_plan_t p, double* total_ms, int64_t* launches) {
   return BEM_OK;
 }
 
+bem_status bem_device_status(bem_plan_t p, void* stream) {
+  if (!p) {
+    set_error("bem_device_status: null plan");
+    return BEM_ERR_ARG;
+  }
+  if (!p->d_status) return BEM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  BEM_CUDA_TRY(cudaMemcpyAsync(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h == 0) return BEM_OK;
+  BEM_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
+  BEM_CUDA_TRY(cudaStreamSynchronize(st));
+  set_error("a tensor-core column kernel gave up waiting for its products; outputs since the last check are invalid");
+  return BEM_ERR_TIMEOUT;
+}
+
 int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
   (void)layer;
   if (!p) return -1;
@@ -649,6 +680,8 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_val);
   cudaFree(p->d_twc);
   cudaFree(p->d_fstab);
+  cudaFree(p->d_tcmat);
+  cudaFree(p->d_status);
   free_operator3(p->op3_single);
   free_operator3(p->op3_double);
   free_operator3(p->op3_system);

@@ -224,8 +224,8 @@ struct SpecAddr {
   bool mirror, nyq;
 };
 
-template <typename T, int TTC>
-__device__ __forceinline__ SpecAddr spec_addr(const FourStep<T>& fs, const ColDims<TTC>& g) {
+template <typename FS, int TTC>
+__device__ __forceinline__ SpecAddr spec_addr(const FS& fs, const ColDims<TTC>& g) {
   const int K0 = fs.freq0();
   const int S = 16 * fs.J;
   SpecAddr a;
@@ -266,16 +266,19 @@ struct ColBounds {
   static constexpr int blocks = TTC >= 64 ? 512 / TTC : (TTC > 0 ? 16 : 1);
 };
 
-template <typename T, int NF, bool ACCREG, int TTC>
+// TCK > 0: the radix-16 stages on the tensor cores (tc_dft.cuh; T = float,
+// TTC a multiple of 128); shared memory then starts with their header.
+template <typename T, int NF, bool ACCREG, int TTC, int TCK = 0>
 __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::blocks)
     k_col2d_v2(const Col2Dv2Params<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  static_assert(TCK == 0 || (std::is_same<T, float>::value && TTC % 128 == 0), "tensor-core stages: FP32, TT % 128");
   const ColDims<TTC> g(p);
   const int t = threadIdx.x, TT = g.TT, W = TT >> 5;
   const int N = g.N, n = g.n;
   const int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
   const int ntab = fstab_entries(TT);
-  cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw + (TCK > 0 ? kTcHeader : 0));
   cplx<T>* stab = sA + nbuf;
   T* sS = reinterpret_cast<T*>(stab + ntab);
   // carries of split rows (3 * TT entries) share the spectrum buffer: both
@@ -297,8 +300,18 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
   const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + 128, g.log2N - 7,
                          (T)(6.283185307179586476925 / (double)N)};
-  FourStep<T> fs;
+  FourStep<T, TCK> fs;
   fs.init(t, TT, sA, ftab);
+  if constexpr (TCK > 0) {
+    fs.tc.tmem = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 4);
+    fs.tc.mbar = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    fs.tc.b_base = fs.tc.mbar + 16u;
+    fs.tc.a_base = (uint32_t)__cvta_generic_to_shared(sA);
+    fs.tc.phase = 0u;
+    fs.tc.t = t;
+    fs.tc.TT = TT;
+    fs.tc.failed = false;
+  }
   auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
     const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
 #pragma unroll
@@ -308,7 +321,13 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   };
 
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
-    __syncthreads();  // the previous column's gather has finished reading sA
+    // the previous column's gather has finished reading sA; with tensor-core
+    // stages the CTA also stops after a device wait that gave up
+    if constexpr (TCK > 0) {
+      if (__syncthreads_or(fs.tc.failed ? 1 : 0)) break;
+    } else {
+      __syncthreads();
+    }
     if constexpr (ACCREG) {
       sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
       __syncthreads();
@@ -362,6 +381,13 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
       }
     }
   }
+  if constexpr (TCK > 0) {
+    if (fs.tc.failed) {
+      atomicOr(p.status, 1);
+      tc_wait(fs.tc.mbar, fs.tc.phase ^ 1u);  // bounded: the last commit, if it still arrives
+    }
+    tc_teardown(fs.tc.tmem, TTC / 4);
+  }
   if (p.acc_in_smem)
     for (int i = 0; i < CNT; ++i) p.partial[(size_t)blockIdx.x * p.npos + i * TT + t] = acc[i * TT + t];
 #undef C0
@@ -397,6 +423,35 @@ void Col2DKernels<T, TTC>::launch(int nf, int grid, int threads, size_t smem, cu
   if (nf == 1) k_col2d_v2<T, 1, false, TTC><<<grid, threads, smem, st>>>(cp);
   else if (nf == 2) k_col2d_v2<T, 2, R, TTC><<<grid, threads, smem, st>>>(cp);
   else k_col2d_v2<T, 3, R, TTC><<<grid, threads, smem, st>>>(cp);
+}
+
+template <int TTC, int TCK>
+cudaError_t Col2DTcKernels<TTC, TCK>::configure(size_t smem, int threads, int* blocks_per_sm) {
+  int b[3] = {0, 0, 0};
+  cudaError_t e;
+  if ((e = allow_optin_smem(k_col2d_v2<float, 1, false, TTC, TCK>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_v2<float, 2, true, TTC, TCK>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_v2<float, 3, true, TTC, TCK>)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_v2<float, 1, false, TTC, TCK>, threads,
+                                                         smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_v2<float, 2, true, TTC, TCK>, threads,
+                                                         smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_v2<float, 3, true, TTC, TCK>, threads,
+                                                         smem)) != cudaSuccess)
+    return e;
+  // each resident CTA holds TTC / 4 tensor-memory columns (512 per SM)
+  *blocks_per_sm = std::min(std::min(b[0], std::min(b[1], b[2])), 512 / (TTC / 4));
+  return cudaSuccess;
+}
+
+template <int TTC, int TCK>
+void Col2DTcKernels<TTC, TCK>::launch(int nf, int grid, int threads, size_t smem, cudaStream_t st,
+                                      const Col2Dv2Params<float>& cp) {
+  if (nf == 1) k_col2d_v2<float, 1, false, TTC, TCK><<<grid, threads, smem, st>>>(cp);
+  else if (nf == 2) k_col2d_v2<float, 2, true, TTC, TCK><<<grid, threads, smem, st>>>(cp);
+  else k_col2d_v2<float, 3, true, TTC, TCK><<<grid, threads, smem, st>>>(cp);
 }
 
 }  // namespace bemfft

@@ -33,6 +33,8 @@ struct Col2Dv2Params {
   int npos;              // Q*TT
   int acc_in_smem;
   int has_carry;         // some row is split between threads
+  const uint4* tcmat;    // tensor-core stages: the two B matrices (hi, lo), 8 KB
+  int* status;           // tensor-core stages: bit 0 set when a device wait gave up
 };
 
 // number of table entries of the four-step kernel for TT threads, N = 16 TT:
@@ -55,6 +57,15 @@ template <typename T, int TTC>
 struct Col2DKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
   static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
+};
+
+// The same kernels in FP32 with the radix-16 stages of the transforms on the
+// tensor cores, TCK = 1 (BF16 hi + lo) or 2 (FP16 hi + lo), TTC = 128, 256 or
+// 512.  configure() also bounds the resident CTAs by the tensor memory.
+template <int TTC, int TCK>
+struct Col2DTcKernels {
+  static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
+  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<float>& cp);
 };
 
 }  // namespace bemfft

@@ -20,9 +20,13 @@
 // (unnormalised) and returns natural order in the same register map.
 // Per transform: one CTA-wide exchange (two barriers) instead of one per
 // Stockham pass; the second exchange stays inside a warp.
+// With TCK > 0 (FP32 only, TT a multiple of 128) the three 16-point stages
+// S1, S4 and S7 (and their adjoints) run as split-precision tensor-core
+// products (tc_dft.cuh); twiddles, transposes and S8 stay on the FP32 pipes.
 #pragma once
 
 #include "fft_reg.cuh"
+#include "tc_dft.cuh"
 
 namespace bemfft {
 
@@ -74,7 +78,7 @@ struct FourStepTables {
   const cplx<T>* t5;
 };
 
-template <typename T>
+template <typename T, int TCK = 0>
 struct FourStep {
   int t, TT;
   int w, l;             // warp, lane
@@ -82,6 +86,7 @@ struct FourStep {
   int lgJ;              // log2(J)
   cplx<T>* sA;          // max(16*TT, W*16*34) elements, shared
   FourStepTables<T> tb; // shared-memory copies
+  TcDft<TCK> tc;        // tensor-core stages (TCK > 0)
 
   __device__ __forceinline__ void init(int t_, int TT_, cplx<T>* s, const FourStepTables<T>& tb_) {
     t = t_;
@@ -153,8 +158,9 @@ struct FourStep {
   // ---- forward: registers in natural position order -> scrambled spectrum.
   // The caller guarantees that nobody still reads sA (previous use).
   template <bool LOWHALF>
-  __device__ __forceinline__ void forward(cplx<T> (&v)[16]) const {
-    if constexpr (LOWHALF) dft16_lowhalf<-1>(v);
+  __device__ __forceinline__ void forward(cplx<T> (&v)[16]) {
+    if constexpr (TCK > 0) tc.template run<-1, LOWHALF, false>(v, 0);
+    else if constexpr (LOWHALF) dft16_lowhalf<-1>(v);
     else dft<16, -1>(v);
     twiddleT2<-1>(v);
 #pragma unroll
@@ -163,7 +169,8 @@ struct FourStep {
 #pragma unroll
     for (int a = 0; a < 16; ++a) v[a] = sA[lineidx(a)];
     cta_sync();
-    dftJ<-1>(v);
+    if constexpr (TCK > 0) tc.template run<-1, false, false>(v, 1);
+    else dftJ<-1>(v);
     twiddleT5<-1>(v);
     cplx<T>* sB = sA + w * (16 * 34);
 #pragma unroll
@@ -173,7 +180,10 @@ struct FourStep {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sB[d * 34 + 2 * i + h];
     __syncwarp();
-    dft<16, -1>(v);
+    // other warps may still read their transpose rows, which the
+    // tensor-core operand overwrites
+    if constexpr (TCK > 0) tc.template run<-1, false, true>(v, 0);
+    else dft<16, -1>(v);
     // S8: X[k] = E0[k] + w32^k E1[k], X[k+16] = E0[k] - w32^k E1[k]
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -193,7 +203,7 @@ struct FourStep {
   __device__ __forceinline__ int freq(int k) const { return freq0() + 16 * J * k; }
   // ---- inverse: scrambled spectrum -> registers in natural position order.
   // Ends with a barrier after its last shared-memory read.
-  __device__ __forceinline__ void inverse(cplx<T> (&v)[16]) const {
+  __device__ __forceinline__ void inverse(cplx<T> (&v)[16]) {
     const int d = l >> 1, h = l & 1;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -202,7 +212,8 @@ struct FourStep {
       other.y = shfl_xor(v[k].y, 1);
       v[k] = h ? twc<32, +1>(other - v[k], k) : v[k] + other;
     }
-    dft<16, +1>(v);
+    if constexpr (TCK > 0) tc.template run<+1, false, false>(v, 0);
+    else dft<16, +1>(v);
     cplx<T>* sB = sA + w * (16 * 34);
 #pragma unroll
     for (int i = 0; i < 16; ++i) sB[d * 34 + 2 * i + h] = v[i];
@@ -210,7 +221,8 @@ struct FourStep {
 #pragma unroll
     for (int dd = 0; dd < 16; ++dd) v[dd] = sB[dd * 34 + l];
     twiddleT5<+1>(v);
-    dftJ<+1>(v);
+    if constexpr (TCK > 0) tc.template run<+1, false, true>(v, 1);
+    else dftJ<+1>(v);
     cta_sync();  // every warp is done with its B region before A is rewritten
 #pragma unroll
     for (int a = 0; a < 16; ++a) sA[lineidx(a)] = v[a];
@@ -219,7 +231,8 @@ struct FourStep {
     for (int k = 0; k < 16; ++k) v[k] = sA[k * TT + t];
     cta_sync();
     twiddleT2<+1>(v);
-    dft<16, +1>(v);
+    if constexpr (TCK > 0) tc.template run<+1, false, false>(v, 0);
+    else dft<16, +1>(v);
   }
 };
 

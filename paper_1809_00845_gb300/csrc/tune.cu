@@ -34,7 +34,7 @@ static void tune_store(const std::string& key, int v) {
 
 static std::string plan_shape(const bem_plan_s* p) {
   return std::to_string(p->dim) + "/" + std::to_string(p->kernel) + "/" + std::to_string(p->n) + "/" +
-         std::to_string(p->nb) + "/" + std::to_string(p->prec);
+         std::to_string(p->nb) + "/" + std::to_string(p->prec) + "/" + std::to_string(p->tc);
 }
 
 // (re)create S side streams and 2S events and capture the batch graph again

@@ -70,7 +70,12 @@ def test_rejects_bad_arguments_on_host(lib):
     cell3 = np.array([[1, 2, 3], [3, 4, 5]])
     nrm3 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     assert _plan_rc(3, 512, 1 / 512, cell3, w, nrm3, kernel=1, prec=2)[0] == bem.BEM_ERR_UNSUPPORTED  # f32x2 in 3D
+    for tc in (bem.BEM_TC_BF16X3, bem.BEM_TC_F16X3):  # tensor-core stages: 2D, n = 1024 ... 4096 only
+        assert _plan_rc(2, 512, 1 / 512, cell, w, nrm, prec=tc)[0] == bem.BEM_ERR_UNSUPPORTED
+        assert _plan_rc(2, 8192, 1 / 8192, cell, w, nrm, prec=tc)[0] == bem.BEM_ERR_UNSUPPORTED
+        assert _plan_rc(3, 1024, 1 / 1024, cell3, w, nrm3, kernel=1, prec=tc)[0] == bem.BEM_ERR_UNSUPPORTED
     rc = lib.bem_plan(None, 2, None, 0.1, 1, None, None, None, 0, 0.3, 1.0, 1, 0, None)
     assert rc == bem.BEM_ERR_ARG
     assert lib.bem_apply(None, 0, None, None, None) == bem.BEM_ERR_ARG
     assert lib.bem_destroy(None) == bem.BEM_OK
+    assert lib.bem_device_status(None, None) == bem.BEM_ERR_ARG
