@@ -227,6 +227,48 @@ def _time_applies(plan, layer, x, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def tensor_core_variants(b, bc, data, x, ours_ms, pc_block, solve_ref, reps=200):
+    """The same system apply with the radix-16 DFT stages on the tensor cores
+    (BF16 / FP16 hi + lo operands, FP32 accumulation): kernel and apply time,
+    error against the double-float plan (itself within 1e-12 of the FP64
+    oracle), and time to relative residual 1e-6 with double-float residual
+    refinement."""
+    import torch
+    from paper_1809_00845_gb300.bem import Plan
+    ref_plan = Plan.from_boundary(b, "laplace2d", "f32x2")
+    ref_plan.set_bc(bc, 0.5)
+    y_ref = ref_plan.apply("system", x.double()).cpu().numpy()
+    ref_plan.close()
+    out = {}
+    for kind in ("tc_bf16x3", "tc_f16x3"):
+        p = Plan.from_boundary(b, "laplace2d", kind)
+        p.set_bc(bc, 0.5)
+        xf = x.float()
+        y = p.apply("system", xf).double().cpu().numpy()
+        err = float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
+        p.set_kernel_timing(True)
+        ms = _time_applies(p, "system", xf, reps)
+        col_ms, col_n = p.kernel_time()
+        p.set_kernel_timing(False)
+        p.set_preconditioner("block", pc_block)
+        p.enable_refinement(True)
+        p.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+        torch.cuda.synchronize()
+        _, _, info = p.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+        p.device_status()
+        out[kind] = {"ms_per_apply": ms, "kernel_us": 1e3 * col_ms / max(1, col_n),
+                     "rel_l2_vs_f32x2": err, "vs_fp32_apply": ms / ours_ms,
+                     "solve_refined": {"seconds": info["seconds"], "iters": info["iters"],
+                                       "status": info["status"], "rel_residual": info["rel_residual"],
+                                       "refine_steps": info["refine_steps"]}}
+        p.close()
+    out["fp32_rel_l2_vs_f32x2"] = None
+    out["what"] = ("FP32 apply with each radix-16 DFT stage of the column transforms as tcgen05 MMAs "
+                   "(hi + lo operand split, 3 products, FP32 accumulate in tensor memory); FP32 refined "
+                   f"time to 1e-6 for comparison: {solve_ref}")
+    return out
+
+
 def cufft_comparator(b, bc, x, ours, reps=20):
     """The same BC-split operator applied the way Eq. 16 writes it: densities
     scattered on the full zero-padded N x N grid, real-to-complex FFT over the
@@ -599,6 +641,17 @@ def run_ours(args):
         cufft = cufft_comparator(b, bc, x0, y0)
         cufft["ours_ms_per_apply"] = ms_max / args.steps
         cufft["speedup_ours"] = cufft["ms_per_apply"] / cufft["ours_ms_per_apply"]
+    tcv = None
+    if not args.no_extra and world == 1 and args.precision == "f32":
+        tcv = tensor_core_variants(b, bc, data, xs[0], ms_max / args.steps, pc_block if solve else 128,
+                                   solve["fp32_refined"]["seconds"] if solve else None)
+        from paper_1809_00845_gb300.bem import Plan as _P
+        rp = _P.from_boundary(b, "laplace2d", "f32x2")
+        rp.set_bc(bc, 0.5)
+        y_ref = rp.apply("system", xs[0].double()).cpu().numpy()
+        rp.close()
+        y32 = plan.apply("system", xs[0]).double().cpu().numpy()
+        tcv["fp32_rel_l2_vs_f32x2"] = float(np.linalg.norm(y32 - y_ref) / np.linalg.norm(y_ref))
     extra = None
     if not args.no_extra and world == 1:
         extra = secondary_configs(dev)
@@ -613,7 +666,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "gpu_launches": args.steps * plan.launches_per_apply("system"),
             "roofline": roofline, "clocks": clk, "time_to_solve": solve, "cpu_baseline": cpu,
-            "plan_seconds": pinfo["plan_seconds"], "cufft_comparator": cufft, "other_configs": extra}
+            "plan_seconds": pinfo["plan_seconds"], "cufft_comparator": cufft, "tensor_core_dft": tcv,
+            "other_configs": extra}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
