@@ -303,14 +303,8 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   FourStep<T, TCK> fs;
   fs.init(t, TT, sA, ftab);
   if constexpr (TCK > 0) {
-    fs.tc.tmem = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 4);
-    fs.tc.mbar = (uint32_t)__cvta_generic_to_shared(smem_raw);
-    fs.tc.b_base = fs.tc.mbar + 16u;
-    fs.tc.a_base = (uint32_t)__cvta_generic_to_shared(sA);
-    fs.tc.phase = 0u;
-    fs.tc.t = t;
-    fs.tc.TT = TT;
-    fs.tc.failed = false;
+    const uint32_t tm = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 128 * kTcGroupCols);
+    fs.tc.bind(t, (uint32_t)__cvta_generic_to_shared(smem_raw), tm);
   }
   auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
     const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
@@ -386,7 +380,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
       atomicOr(p.status, 1);
       tc_wait(fs.tc.mbar, fs.tc.phase ^ 1u);  // bounded: the last commit, if it still arrives
     }
-    tc_teardown(fs.tc.tmem, TTC / 4);
+    tc_teardown(fs.tc.tmem - (uint32_t)(kTcGroupCols * (t >> 7)), TTC / 128 * kTcGroupCols);
   }
   if (p.acc_in_smem)
     for (int i = 0; i < CNT; ++i) p.partial[(size_t)blockIdx.x * p.npos + i * TT + t] = acc[i * TT + t];
@@ -441,8 +435,8 @@ cudaError_t Col2DTcKernels<TTC, TCK>::configure(size_t smem, int threads, int* b
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_v2<float, 3, true, TTC, TCK>, threads,
                                                          smem)) != cudaSuccess)
     return e;
-  // each resident CTA holds TTC / 4 tensor-memory columns (512 per SM)
-  *blocks_per_sm = std::min(std::min(b[0], std::min(b[1], b[2])), 512 / (TTC / 4));
+  // each resident CTA holds TTC / 128 * kTcGroupCols tensor-memory columns (512 per SM)
+  *blocks_per_sm = std::min(std::min(b[0], std::min(b[1], b[2])), 512 / (TTC / 128 * kTcGroupCols));
   return cudaSuccess;
 }
 

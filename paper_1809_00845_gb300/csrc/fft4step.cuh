@@ -23,6 +23,8 @@
 // With TCK > 0 (FP32 only, TT a multiple of 128) the three 16-point stages
 // S1, S4 and S7 (and their adjoints) run as split-precision tensor-core
 // products (tc_dft.cuh); twiddles, transposes and S8 stay on the FP32 pipes.
+// Their operands live in tensor memory, so a stage touches no shared memory
+// but the DFT matrices and synchronises only its own warpgroup.
 #pragma once
 
 #include "fft_reg.cuh"
@@ -159,7 +161,7 @@ struct FourStep {
   // The caller guarantees that nobody still reads sA (previous use).
   template <bool LOWHALF>
   __device__ __forceinline__ void forward(cplx<T> (&v)[16]) {
-    if constexpr (TCK > 0) tc.template run<-1, LOWHALF, false>(v, 0);
+    if constexpr (TCK > 0) tc.template run<-1, LOWHALF>(v, 0);
     else if constexpr (LOWHALF) dft16_lowhalf<-1>(v);
     else dft<16, -1>(v);
     twiddleT2<-1>(v);
@@ -169,7 +171,7 @@ struct FourStep {
 #pragma unroll
     for (int a = 0; a < 16; ++a) v[a] = sA[lineidx(a)];
     cta_sync();
-    if constexpr (TCK > 0) tc.template run<-1, false, false>(v, 1);
+    if constexpr (TCK > 0) tc.template run<-1, false>(v, 1);
     else dftJ<-1>(v);
     twiddleT5<-1>(v);
     cplx<T>* sB = sA + w * (16 * 34);
@@ -180,9 +182,7 @@ struct FourStep {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sB[d * 34 + 2 * i + h];
     __syncwarp();
-    // other warps may still read their transpose rows, which the
-    // tensor-core operand overwrites
-    if constexpr (TCK > 0) tc.template run<-1, false, true>(v, 0);
+    if constexpr (TCK > 0) tc.template run<-1, false>(v, 0);
     else dft<16, -1>(v);
     // S8: X[k] = E0[k] + w32^k E1[k], X[k+16] = E0[k] - w32^k E1[k]
 #pragma unroll
@@ -212,7 +212,7 @@ struct FourStep {
       other.y = shfl_xor(v[k].y, 1);
       v[k] = h ? twc<32, +1>(other - v[k], k) : v[k] + other;
     }
-    if constexpr (TCK > 0) tc.template run<+1, false, false>(v, 0);
+    if constexpr (TCK > 0) tc.template run<+1, false>(v, 0);
     else dft<16, +1>(v);
     cplx<T>* sB = sA + w * (16 * 34);
 #pragma unroll
@@ -221,7 +221,7 @@ struct FourStep {
 #pragma unroll
     for (int dd = 0; dd < 16; ++dd) v[dd] = sB[dd * 34 + l];
     twiddleT5<+1>(v);
-    if constexpr (TCK > 0) tc.template run<+1, false, true>(v, 1);
+    if constexpr (TCK > 0) tc.template run<+1, false>(v, 1);
     else dftJ<+1>(v);
     cta_sync();  // every warp is done with its B region before A is rewritten
 #pragma unroll
@@ -231,7 +231,7 @@ struct FourStep {
     for (int k = 0; k < 16; ++k) v[k] = sA[k * TT + t];
     cta_sync();
     twiddleT2<+1>(v);
-    if constexpr (TCK > 0) tc.template run<+1, false, false>(v, 0);
+    if constexpr (TCK > 0) tc.template run<+1, false>(v, 0);
     else dft<16, +1>(v);
   }
 };

@@ -17,21 +17,26 @@
 // The inverse DFT uses the forward matrix on conjugated data:
 // IDFT(x) = conj(DFT(conj(x))).
 //
-// Operand layouts (K-major, no swizzle; "core matrices" of 8 rows x 16
-// bytes stored as 128 contiguous bytes):
-//   byte(r, k) = (r / 8) * 512 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
-// i.e. leading-dimension (K) core-matrix offset 128 B and stride-dimension
-// (row group) offset 512 B.  Input column k of complex element i, part
-// c (0 = real, 1 = imaginary): k = (i / 8) * 16 + c * 8 + i % 8, so that a
-// line whose upper 8 inputs are zero (the zero padding of the first stage)
-// needs only the first K = 16 half: one MMA per product instead of two.
-// Output column n of element f: n = c * 16 + f.
-// A: TT rows, hi half then lo half (TT * 64 bytes each), aliasing the
-// engine's transpose buffer, which is free at every stage.  B: per matrix
-// hi (2 KB) then lo (2 KB), built on the host in FP64.
-// Tensor memory: 32 FP32 columns per 128-row tile, lanes = rows; warp w reads
-// lanes 32 (w % 4) .. + 31 of tile w / 4, which are exactly its own threads'
-// lines (thread t = 32 w + lane = 128 (w / 4) + 32 (w % 4) + lane).
+// Operands.  A (each line's 32 input reals as 16-bit hi and lo parts) is
+// written by the threads straight from registers into tensor memory
+// (tcgen05.st) and read from there by the MMA, so neither the operand stores
+// nor the MMA's operand reads touch shared memory, which the transposes of
+// the engine keep busy.  Tensor-memory layout of A for M = 128: lane = line,
+// 32-bit column j = the 16-bit elements k = 2j (low half) and 2j + 1.  Input
+// element k of complex element i, part c (0 = real, 1 = imaginary):
+// k = (i / 8) * 16 + c * 8 + i % 8, so that a line whose upper 8 inputs are
+// zero (the zero padding of the first stage) needs only the first K = 16 half:
+// one MMA per product instead of two.  Output column n of element f:
+// n = c * 16 + f.  B (the DFT matrix, 32 x 32) sits in shared memory, K-major
+// without swizzle: core matrices of 8 rows x 16 bytes stored as 128
+// contiguous bytes, byte(n, k) = (n / 8) * 512 + (k / 8) * 128 + (n % 8) * 16
+// + (k % 8) * 2 (K-direction core-matrix offset 128 B, row-group offset
+// 512 B); per matrix hi (2 KB) then lo (2 KB), built on the host in FP64.
+// Every warpgroup (128 threads, 128 lines) runs its stage on its own, with
+// its own 64 tensor-memory columns (D: 32 FP32 columns, then A hi and A lo:
+// 16 each), mbarrier, issuing thread (its first) and 128-thread named
+// barrier (id 1 + g).  Warp w accesses lanes 32 (w % 4) .. + 31, which are
+// exactly its own threads' lines (thread t = 128 g + 32 (w % 4) + lane).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -44,10 +49,14 @@ namespace bemfft {
 
 constexpr int kTcBf16 = 1;
 constexpr int kTcF16 = 2;
-// shared-memory header of a tensor-core column kernel: mbarrier (8 B), tensor
-// memory address (4 B), padding, then two B matrices (4 KB each)
+// shared-memory header of a tensor-core column kernel: one mbarrier per
+// warpgroup (4 x 8 B), the tensor-memory address (4 B), padding, then two B
+// matrices (4 KB each)
 constexpr int kTcMatBytes = 4096;
-constexpr int kTcHeader = 16 + 2 * kTcMatBytes;
+constexpr int kTcMatOffset = 64;
+constexpr int kTcHeader = kTcMatOffset + 2 * kTcMatBytes;
+// tensor-memory columns per warpgroup: D (32 FP32) + A hi (16) + A lo (16)
+constexpr int kTcGroupCols = 64;
 // a bounded device wait gives up after this many nanoseconds
 constexpr unsigned long long kTcWaitNs = 1000000000ull;
 
@@ -66,11 +75,27 @@ __device__ __forceinline__ constexpr uint32_t tc_idesc() {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (tensor memory) (+)= A (tensor memory) x B (shared-memory descriptor)
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// this warp's 32 lanes, 8 or 16 consecutive 32-bit columns from taddr
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
@@ -91,29 +116,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // wait for the mbarrier phase of the given parity, at most kTcWaitNs;
-// false when the wait gave up
+// false when the wait gave up.  try_wait suspends the thread (up to a
+// hardware time limit per call) instead of spinning on issue slots.
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
   unsigned long long t0 = 0;
-  for (uint32_t i = 0;; ++i) {
+  for (;;) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(mbar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((i & 255u) == 0) {
-      const unsigned long long now = global_ns();
-      if (t0 == 0) t0 = now;
-      else if (now - t0 > kTcWaitNs) return false;
-    }
+    const unsigned long long now = global_ns();
+    if (t0 == 0) t0 = now;
+    else if (now - t0 > kTcWaitNs) return false;
   }
-}
-
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-               : "memory");
 }
 
 // hi and lo parts of two FP32 values packed as two 16-bit numbers (first
@@ -133,23 +152,24 @@ __device__ __forceinline__ void tc_split2(float a, float b, uint32_t& hi, uint32
   }
 }
 
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g) : "memory");
+}
+
 template <int KIND>
 struct TcDft {
-  uint32_t a_base;  // shared address of the A operand (TT rows, hi then lo)
   uint32_t b_base;  // shared address of the B matrices
-  uint32_t mbar;    // shared address of the mbarrier
-  uint32_t tmem;    // tensor-memory address of the accumulators
+  uint32_t mbar;    // shared address of this warpgroup's mbarrier
+  uint32_t tmem;    // tensor-memory address of this warpgroup's columns (lane 0)
   uint32_t phase;   // parity of the next mbarrier phase
-  int t, TT;
+  int t;            // thread index
   bool failed;      // a wait of this thread gave up (the kernel reports it)
 
   // One radix-16 stage: v[f] <- sum_i v[i] e^{DIR 2 pi i f i / 16} for the
   // matrix `mat` (0 = the 16-point DFT; 1 = the engine's J-point blocks).
-  // LOWHALF: v[8..15] are zero.  PRESYNC: another warp may still read the
-  // transpose buffer that A aliases.
-  template <int DIR, bool LOWHALF, bool PRESYNC>
+  // LOWHALF: v[8..15] are zero.
+  template <int DIR, bool LOWHALF>
   __device__ __forceinline__ void run(cplx<float> (&v)[16], int mat) {
-    if (PRESYNC) __syncthreads();
     constexpr int NI = LOWHALF ? 8 : 16;
     float sc = 1.0f, isc = 1.0f;
     if constexpr (KIND == kTcF16) {
@@ -162,77 +182,88 @@ struct TcDft {
       isc = __int_as_float((254 - es) << 23);
     }
     const float sy = DIR > 0 ? -sc : sc;  // conjugate the input of an inverse stage
-    const uint32_t row = a_base + (uint32_t)((t >> 3) * 512 + (t & 7) * 16);
-    const uint32_t lo_off = (uint32_t)TT * 64u;
+    uint32_t h[16], l[16];
 #pragma unroll
     for (int c = 0; c < (LOWHALF ? 2 : 4); ++c) {
       const int i0 = (c >> 1) * 8;
-      uint32_t h[4], l[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const cplx<float> p = v[i0 + 2 * j], q = v[i0 + 2 * j + 1];
-        if (c & 1) tc_split2<KIND>(p.y * sy, q.y * sy, h[j], l[j]);
-        else tc_split2<KIND>(p.x * sc, q.x * sc, h[j], l[j]);
+        if (c & 1) tc_split2<KIND>(p.y * sy, q.y * sy, h[c * 4 + j], l[c * 4 + j]);
+        else tc_split2<KIND>(p.x * sc, q.x * sc, h[c * 4 + j], l[c * 4 + j]);
       }
-      st_shared_v4(row + c * 128, h[0], h[1], h[2], h[3]);
-      st_shared_v4(row + lo_off + c * 128, l[0], l[1], l[2], l[3]);
     }
-    fence_async_smem();
+    const uint32_t lane_base = (uint32_t)(32 * ((t >> 5) & 3)) << 16;
+    const uint32_t a_hi = tmem + 32u, a_lo = tmem + 48u;
+    if constexpr (LOWHALF) {
+      tmem_st8(a_hi + lane_base, h);
+      tmem_st8(a_lo + lane_base, l);
+    } else {
+      tmem_st16(a_hi + lane_base, h);
+      tmem_st16(a_lo + lane_base, l);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     tc_fence_before();
-    __syncthreads();
-    if (t == 0) {
+    group_sync(t >> 7);
+    if ((t & 127) == 0) {
       tc_fence_after();
       constexpr uint32_t id = tc_idesc<KIND>();
       const uint32_t bh = b_base + (uint32_t)mat * 4096u, bl = bh + 2048u;
-      for (int m = 0; m < (TT >> 7); ++m) {
-        const uint32_t d = tmem + (uint32_t)m * 32u;
-        const uint32_t ah = a_base + (uint32_t)m * 8192u, al = ah + lo_off;
 #pragma unroll
-        for (int s = 0; s < (LOWHALF ? 1 : 2); ++s) {
-          const uint32_t ks = (uint32_t)s * 256u;
-          tc_mma(d, tc_sdesc(ah + ks), tc_sdesc(bh + ks), id, s > 0 ? 1u : 0u);
-          tc_mma(d, tc_sdesc(al + ks), tc_sdesc(bh + ks), id, 1u);
-          tc_mma(d, tc_sdesc(ah + ks), tc_sdesc(bl + ks), id, 1u);
-        }
+      for (int s = 0; s < (LOWHALF ? 1 : 2); ++s) {
+        const uint32_t ka = (uint32_t)s * 8u, kb = (uint32_t)s * 256u;
+        tc_mma(tmem, a_hi + ka, tc_sdesc(bh + kb), id, s > 0 ? 1u : 0u);
+        tc_mma(tmem, a_lo + ka, tc_sdesc(bh + kb), id, 1u);
+        tc_mma(tmem, a_hi + ka, tc_sdesc(bl + kb), id, 1u);
       }
       tc_commit(mbar);
     }
     if (!tc_wait(mbar, phase)) failed = true;
     phase ^= 1u;
     tc_fence_after();
-    uint32_t r[32];
-    const int w = t >> 5;
-    const uint32_t taddr = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(w >> 2) * 32u;
+    uint32_t q[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+          "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]),
+          "=r"(q[16]), "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]),
+          "=r"(q[24]), "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+        : "r"(tmem + lane_base));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
     const float oy = DIR > 0 ? -isc : isc;
 #pragma unroll
     for (int f = 0; f < 16; ++f) {
-      v[f].x = __uint_as_float(r[f]) * isc;
-      v[f].y = __uint_as_float(r[16 + f]) * oy;
+      v[f].x = __uint_as_float(q[f]) * isc;
+      v[f].y = __uint_as_float(q[16 + f]) * oy;
     }
-    // the next stage's MMAs overwrite these columns after a barrier
+    // the warpgroup's next stage overwrites these columns after its barrier
     tc_fence_before();
+  }
+
+  // bind this thread to its warpgroup's resources (after tc_setup)
+  __device__ __forceinline__ void bind(int t_, uint32_t hdr, uint32_t tmem_base) {
+    t = t_;
+    const int g = t >> 7;
+    mbar = hdr + 8u * (uint32_t)g;
+    b_base = hdr + kTcMatOffset;
+    tmem = tmem_base + (uint32_t)(kTcGroupCols * g);
+    phase = 0u;
+    failed = false;
   }
 };
 
-// Kernel prologue (all threads): mbarrier, tensor memory (warp 0 allocates
-// `ncols` columns) and the B matrices (nbytes from global) in shared memory.
-// Returns the tensor-memory base address.
+// Kernel prologue (all threads): one mbarrier per warpgroup, tensor memory
+// (warp 0 allocates `ncols` columns) and the B matrices (nbytes from global)
+// in shared memory.  Returns the tensor-memory base address.
 __device__ __forceinline__ uint32_t tc_setup(unsigned char* hdr, const uint4* mats, int nbytes, int ncols) {
-  const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(hdr);
-  const uint32_t slot = mbar + 8u;
-  uint4* dst = reinterpret_cast<uint4*>(hdr + 16);
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(hdr);
+  const uint32_t slot = base + 32u;
+  uint4* dst = reinterpret_cast<uint4*>(hdr + kTcMatOffset);
   for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) dst[i] = mats[i];
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+    for (int g = 0; g < (int)(blockDim.x >> 7); ++g)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(base + 8u * (uint32_t)g) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (threadIdx.x < 32) {
@@ -244,7 +275,7 @@ __device__ __forceinline__ uint32_t tc_setup(unsigned char* hdr, const uint4* ma
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  return *reinterpret_cast<volatile uint32_t*>(hdr + 8);
+  return *reinterpret_cast<volatile uint32_t*>(hdr + 32);
 }
 
 // Kernel epilogue (all threads): every tensor-memory read has completed
