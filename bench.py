@@ -149,7 +149,8 @@ MEASURED_TRAFFIC = {"n4096_f32_system": ("1ff1ac15b8a2c67f", 202.10e6)}
 def kernel_source_hash():
     import hashlib
     hs = hashlib.sha256()
-    for f in ("apply2d.cu", "col2d_v2.h", "col2d_v2.cuh", "col2d_f32_large.cu", "fft4step.cuh", "fft_reg.cuh"):
+    for f in ("apply2d.cu", "col2d_v2.h", "col2d_v2.cuh", "col2d_f32_large.cu", "fft4step.cuh", "fft_reg.cuh",
+              "tc_dft.cuh"):
         with open(os.path.join(ROOT, "paper_1809_00845_gb300", "csrc", f), "rb") as fh:
             hs.update(fh.read())
     return hs.hexdigest()[:16]

@@ -32,6 +32,13 @@
 
 namespace bemfft {
 
+// which radix-16 stages run on the tensor cores when TCK > 0: bit 0 S1,
+// 1 S4, 2 S7 (forward), 3 S7^H, 4 S4^H, 5 S1^H (inverse)
+#ifndef COL2D_TC_STAGES
+#define COL2D_TC_STAGES 0x3F
+#endif
+constexpr int kTcStages = COL2D_TC_STAGES;
+
 // a0..a3 with the upper half (a2, a3) known to be zero
 template <int DIR, typename T>
 __device__ __forceinline__ void dft4_lowhalf(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
@@ -161,7 +168,7 @@ struct FourStep {
   // The caller guarantees that nobody still reads sA (previous use).
   template <bool LOWHALF>
   __device__ __forceinline__ void forward(cplx<T> (&v)[16]) {
-    if constexpr (TCK > 0) tc.template run<-1, LOWHALF>(v, 0);
+    if constexpr (TCK > 0 && (kTcStages & 1)) tc.template run<-1, LOWHALF>(v, 0);
     else if constexpr (LOWHALF) dft16_lowhalf<-1>(v);
     else dft<16, -1>(v);
     twiddleT2<-1>(v);
@@ -171,7 +178,7 @@ struct FourStep {
 #pragma unroll
     for (int a = 0; a < 16; ++a) v[a] = sA[lineidx(a)];
     cta_sync();
-    if constexpr (TCK > 0) tc.template run<-1, false>(v, 1);
+    if constexpr (TCK > 0 && (kTcStages & 2)) tc.template run<-1, false>(v, 1);
     else dftJ<-1>(v);
     twiddleT5<-1>(v);
     cplx<T>* sB = sA + w * (16 * 34);
@@ -182,7 +189,7 @@ struct FourStep {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sB[d * 34 + 2 * i + h];
     __syncwarp();
-    if constexpr (TCK > 0) tc.template run<-1, false>(v, 0);
+    if constexpr (TCK > 0 && (kTcStages & 4)) tc.template run<-1, false>(v, 0);
     else dft<16, -1>(v);
     // S8: X[k] = E0[k] + w32^k E1[k], X[k+16] = E0[k] - w32^k E1[k]
 #pragma unroll
@@ -212,7 +219,7 @@ struct FourStep {
       other.y = shfl_xor(v[k].y, 1);
       v[k] = h ? twc<32, +1>(other - v[k], k) : v[k] + other;
     }
-    if constexpr (TCK > 0) tc.template run<+1, false>(v, 0);
+    if constexpr (TCK > 0 && (kTcStages & 8)) tc.template run<+1, false>(v, 0);
     else dft<16, +1>(v);
     cplx<T>* sB = sA + w * (16 * 34);
 #pragma unroll
@@ -221,7 +228,7 @@ struct FourStep {
 #pragma unroll
     for (int dd = 0; dd < 16; ++dd) v[dd] = sB[dd * 34 + l];
     twiddleT5<+1>(v);
-    if constexpr (TCK > 0) tc.template run<+1, false>(v, 1);
+    if constexpr (TCK > 0 && (kTcStages & 16)) tc.template run<+1, false>(v, 1);
     else dftJ<+1>(v);
     cta_sync();  // every warp is done with its B region before A is rewritten
 #pragma unroll
@@ -231,7 +238,7 @@ struct FourStep {
     for (int k = 0; k < 16; ++k) v[k] = sA[k * TT + t];
     cta_sync();
     twiddleT2<+1>(v);
-    if constexpr (TCK > 0) tc.template run<+1, false>(v, 0);
+    if constexpr (TCK > 0 && (kTcStages & 32)) tc.template run<+1, false>(v, 0);
     else dft<16, +1>(v);
   }
 };
