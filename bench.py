@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "tc_bf16x3", "tc_f16x3"],
+                    help="tc_*: FP32 plan whose radix-16 DFT stages run on the tensor cores")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -506,7 +507,8 @@ def run_ours(args):
     plan = Plan.from_boundary(b, "laplace2d", args.precision)
     plan.set_bc(bc, 0.5)
     pinfo = plan.info()
-    tdt = torch.float32 if args.precision == "f32" else torch.float64
+    f32io = args.precision != "f64"
+    tdt = torch.float32 if f32io else torch.float64
     gen = torch.Generator(device=dev)
     gen.manual_seed(1234 + rank)
     nbuf = 8
@@ -564,7 +566,7 @@ def run_ours(args):
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_val = world * e2e_steps / e2e_s
-    nbytes = b.nb * (4 if args.precision == "f32" else 8)
+    nbytes = b.nb * (4 if f32io else 8)
 
     # time-to-solve at relative residual 1e-6: FP32 preconditioned GMRES with
     # mixed-precision refinement (FP64 residuals), and the plain FP32 GMRES
@@ -572,7 +574,7 @@ def run_ours(args):
     solve = None
     if not args.no_solve:
         # block size measured on the refined solve (plain FP32 cannot reach 1e-6 here)
-        plan.enable_refinement(args.precision == "f32")
+        plan.enable_refinement(f32io)
         pc_block = plan.tune_preconditioner(bc, data, tol=1e-6, restart=100, max_iter=3000)
 
         def run_solve(refine):
@@ -584,7 +586,7 @@ def run_ours(args):
                     "converged": info["status"] == 0, "rel_residual": info["rel_residual"],
                     "applies": info["applies"], "refine_steps": info["refine_steps"]}
         plain = run_solve(False)
-        refined = run_solve(True) if args.precision == "f32" else None
+        refined = run_solve(True) if f32io else None
         solve = {"tol": 1e-6, "precision": args.precision,
                  "preconditioner": f"block Jacobi, {pc_block}-cell blocks (tuned), inverted on the device",
                  "fp32_refined": refined, "plain_fp32": plain,
@@ -625,7 +627,9 @@ def run_ours(args):
         traffic = val
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved_tflops / peak_tflops) if peak_tflops else None, "traffic": traffic,
-                "kernel": "k_col2d_v2<float,3,true,512>", "avg_launch_us": avg_col_s * 1e6,
+                "kernel": ("k_col2d_v2<double,3,false,0,0>" if not f32io else
+                           "k_col2d_v2<float,3,true,512,%d>" % {"tc_bf16x3": 1, "tc_f16x3": 2}.get(args.precision, 0)),
+                "avg_launch_us": avg_col_s * 1e6,
                 "launches_timed": col_launches, "flops_per_launch": flops,
                 "peak_basis": f"FP32 FMA: {SM_COUNT_NOMINAL} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                               f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
