@@ -263,6 +263,64 @@ def cube_boundary(n: int = 128, lo: int = None, hi: int = None) -> Boundary:
 
 # ------------------------------------------------------------ analytic fields --
 
+@dataclasses.dataclass
+class PanelBoundary:
+    """A closed curve as nb straight panels (accuracy mode): panel j runs from
+    vertex j to vertex j + 1 (cyclic), vertices on the curve, equally spaced in
+    arclength, counter-clockwise (outward normal = tangent turned clockwise).
+    ``param`` is the curve parameter of each panel's first vertex."""
+
+    n: int
+    panels: np.ndarray    # (nb, 4): A.x, A.y, B.x, B.y
+    param: np.ndarray     # (nb,)
+
+    @property
+    def nb(self) -> int:
+        return int(self.panels.shape[0])
+
+    @property
+    def h(self) -> float:
+        return 1.0 / self.n
+
+    @property
+    def mid(self) -> np.ndarray:
+        return 0.5 * (self.panels[:, 0:2] + self.panels[:, 2:4])
+
+    @property
+    def length(self) -> np.ndarray:
+        d = self.panels[:, 2:4] - self.panels[:, 0:2]
+        return np.hypot(d[:, 0], d[:, 1])
+
+    @property
+    def normal(self) -> np.ndarray:
+        d = self.panels[:, 2:4] - self.panels[:, 0:2]
+        d = d / np.hypot(d[:, 0], d[:, 1])[:, None]
+        return np.stack([d[:, 1], -d[:, 0]], axis=1)
+
+
+def curve_panels(n: int, curve, panels_per_h: float = 1.0, samples: int = 1 << 16) -> PanelBoundary:
+    """Flat panels of length about h / panels_per_h on a closed curve; the
+    vertices are placed at equal arclength (the curve's length from a fine
+    trapezoid sum, inverted by linear interpolation)."""
+    t = np.linspace(0.0, 2.0 * math.pi, samples + 1)
+    _, dp = curve(t)
+    sp = np.hypot(dp[:, 0], dp[:, 1])
+    s = np.concatenate([[0.0], np.cumsum(0.5 * (sp[1:] + sp[:-1]) * np.diff(t))])
+    nb = max(3, int(math.ceil(s[-1] * n * panels_per_h)))
+    tv = np.interp(np.arange(nb) * (s[-1] / nb), s, t)
+    v, _ = curve(tv)
+    if v.min() <= 0.0 or v.max() >= 1.0:
+        raise ValueError("curve leaves the unit square")
+    panels = np.concatenate([v, np.roll(v, -1, axis=0)], axis=1)
+    return PanelBoundary(n, panels, tv)
+
+
+def panel_data(b: PanelBoundary, field):
+    """(u, q) of an analytic field at the panel midpoints, q = n . grad u."""
+    u, g = field(b.mid)
+    return u, np.sum(g * b.normal, axis=-1)
+
+
 def field_x2y2(p):
     """u = x^2 - y^2 and its gradient (harmonic)."""
     x, y = p[..., 0], p[..., 1]
