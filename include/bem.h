@@ -138,6 +138,39 @@ bem_status bem_plan(bem_plan_t* out, int dim, const int64_t* n, double h, int64_
                     const double* w, const double* normal, bem_kernel kernel, double nu, double mu,
                     bem_precision prec, uint32_t flags, void* stream);
 
+/* Accuracy mode: a plan whose unknowns live on flat boundary panels instead
+ * of grid nodes (one value per panel), applied with the paper's grid
+ * convolution (Section 4, Eq. 16) by the precorrected-FFT construction.  The
+ * paper-form operator of bem_plan (sources and targets on grid nodes) does
+ * not converge on curved boundaries; this one converges to the flat-panel
+ * collocation BEM up to an error set by the stencil order and near radius.
+ *   n, h        grid (n a power of two in [4, 4096]; node k at (k + 1/2) h)
+ *   nb          number of panels (>= 1)
+ *   panels      host, nb*4 doubles: A.x, A.y, B.x, B.y of panel j; the
+ *               outward normal is the tangent (B - A) turned clockwise
+ *               (counter-clockwise closed curves); collocation at (A + B)/2;
+ *               every midpoint's stencil must lie inside the grid (about
+ *               two cells of margin), else BEM_ERR_ARG
+ *   order       2 or 3: (order + 1)^2-node Lagrange stencils
+ *   near_radius R >= order (at most 64): panel pairs whose stencil anchors
+ *               differ by at most R cells along both axes get exact panel
+ *               integrals (closed forms), the rest goes through the grid
+ *   prec        as bem_plan (the grid convolution's arithmetic and the I/O
+ *               type); the projection, interpolation and corrections sum in
+ *               FP64 and are stored in the I/O type
+ * Operators (bem_apply, BEM_SINGLE / BEM_DOUBLE / BEM_SYSTEM, and bem_solve):
+ * S and D with the paper's signs (Eq. 15), c = 1/2; the double layer carries a
+ * diagonal term that makes its rows sum to 1/2 (Gauss's law, exact for closed
+ * curves; the mode assumes closed curves and the interior problem).
+ * bem_set_bc, bem_solve, bem_enable_refinement (companion: the same panels in
+ * BEM_F32X2 for n >= 256, else BEM_F64), bem_set_preconditioner (blocks of
+ * consecutive panels from the exact panel integrals), batches, bem_get_info
+ * and kernel timing (the grid convolution) apply; bem_apply_static_scratch
+ * returns BEM_ERR_UNSUPPORTED.  Not in the paper: an added discretisation
+ * (Phillips and White, IEEE TCAD 16(10), 1997) around the paper's kernels. */
+bem_status bem_plan_panels(bem_plan_t* out, int64_t n, double h, int64_t nb, const double* panels, int order,
+                           int near_radius, bem_precision prec, uint32_t flags, void* stream);
+
 /* Set the boundary-condition types used by BEM_SYSTEM and bem_solve.
  *   bc  host, nb*ncomp bytes: 0 = Dirichlet (u known, q/t unknown),
  *       1 = Neumann (q/t known, u unknown)

@@ -30,7 +30,7 @@ PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32, "f32x2": BEM_F32X2, "tc_bf16x3": B
 F32_IO = (BEM_F32, BEM_TC_BF16X3, BEM_TC_F16X3)
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
-EXPORTED = ["bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
+EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_device_status", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
             "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
     lib = ctypes.CDLL(path)
     P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
     lib.bem_plan.argtypes = [ctypes.POINTER(P), I, P, D, I64, P, P, P, I, D, D, I, ctypes.c_uint32, P]
+    lib.bem_plan_panels.argtypes = [ctypes.POINTER(P), I64, D, I64, P, I, I, I, ctypes.c_uint32, P]
     lib.bem_set_bc.argtypes = [P, P, D]
     lib.bem_set_preconditioner.argtypes = [P, I, I]
     lib.bem_enable_refinement.argtypes = [P, I]
@@ -119,7 +120,7 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = I
     lib.bem_last_error.argtypes = []
     lib.bem_last_error.restype = ctypes.c_char_p
-    for name in ("bem_plan", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
+    for name in ("bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
                  "bem_apply_static_scratch", "bem_apply_host", "bem_solve", "bem_get_info",
                  "bem_set_kernel_timing", "bem_kernel_time", "bem_device_status", "bem_destroy"):
         getattr(lib, name).restype = I
@@ -182,6 +183,27 @@ class Plan:
     @classmethod
     def from_boundary(cls, b, kernel="laplace2d", precision="f32", **kw):
         return cls(b.dim, b.n, b.h, b.cell, b.w, b.normal, kernel=kernel, precision=precision, **kw)
+
+    @classmethod
+    def from_panels(cls, n, h, panels, precision="f32", order=3, near_radius=3, stream=None):
+        """Accuracy-mode plan (bem_plan_panels): panels (nb, 4) = A.x, A.y, B.x, B.y."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self.kernel = BEM_LAPLACE_2D
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.dim = 2
+        self.ncomp = 1
+        panels = np.ascontiguousarray(panels, dtype=np.float64)
+        self.nb = int(panels.shape[0])
+        self._h = ctypes.c_void_p()
+        _check(lib.bem_plan_panels(ctypes.byref(self._h), int(n), float(h), self.nb, _ptr(panels), int(order),
+                                   int(near_radius), self.precision, 0, _stream_ptr(stream)))
+        self.torch_dtype = None
+        return self
+
+    @classmethod
+    def from_panel_boundary(cls, b, precision="f32", order=3, near_radius=3, stream=None):
+        return cls.from_panels(b.n, b.h, b.panels, precision, order, near_radius, stream)
 
     # --------------------------------------------------------------- helpers
     @property

@@ -106,6 +106,41 @@ struct BlockPrecond {
   bool valid = false;
 };
 
+// Accuracy mode (panels.cu): the unknowns live on flat boundary panels; a
+// panel's source and dipole are projected onto a stencil of grid nodes, the
+// grid convolution of an inner node plan carries the far field, the
+// potential is interpolated back to the panel midpoints, and near pairs get
+// their exact panel integrals (precorrection).
+struct PanelOp {
+  int order = 3, R = 3, S = 16;       // stencil order, near radius (anchor cells), nodes per stencil
+  int64_t nnodes = 0;
+  bem_plan_s* inner = nullptr;        // paper-form plan over the active nodes (w = 1)
+  int public_prec = 0;                // precision requested by the caller
+  std::vector<double> h_panels;       // nb * 4 (A.x, A.y, B.x, B.y)
+  std::vector<double> h_delta;        // nb: Gauss row-sum term of the double layer
+  // near pairs, CSR by target: exact panel integrals (preconditioner) and
+  // precorrections exact - grid-mediated
+  std::vector<int64_t> h_nptr;
+  std::vector<int32_t> h_nj;
+  std::vector<double> h_eS, h_eD, h_cS, h_cD;
+  // device (T = the plan's I/O type)
+  int32_t* d_node = nullptr;          // nb * S inner node indices of each midpoint's stencil
+  void* d_W = nullptr;                // nb * S interpolation weights
+  int64_t* d_pptr = nullptr;          // nnodes + 1: projection CSR by node
+  int32_t* d_pj = nullptr;
+  void* d_pws = nullptr;              // single-layer moments
+  void* d_pwd = nullptr;              // dipole moments
+  int64_t* d_nptr = nullptr;          // nb + 1: near CSR by target
+  int32_t* d_nj = nullptr;
+  void* d_cS = nullptr;
+  void* d_cD = nullptr;
+  void* d_delta = nullptr;            // nb
+  uint8_t* d_bc = nullptr;            // nb
+  void* d_rho = nullptr;              // nnodes node charges
+  void* d_phi = nullptr;              // nnodes node potentials
+  size_t bytes = 0;
+};
+
 }  // namespace bemfft
 
 struct bem_plan_s {
@@ -184,6 +219,7 @@ struct bem_plan_s {
   void* d_tin = nullptr;    // plan-precision in/out buffers for the apply
   void* d_tout = nullptr;
   uint64_t op_version = 0;  // bumped whenever bem_set_bc rebuilds the system operator
+  bemfft::PanelOp* pf = nullptr;  // accuracy mode (bem_plan_panels), else null
 };
 
 // Batch of plans applied through one CUDA graph (batch.cu); the batched
@@ -271,6 +307,14 @@ inline cudaError_t allow_optin_smem(K kern) {
   return e;
 }
 bem_status build_preconditioner(bem_plan_s* p);
+// accuracy mode (panels.cu)
+bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, const double* panels, int order,
+                           int R, bem_precision prec, cudaStream_t st);
+bem_status launch_apply_panels(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);
+bem_status panel_set_bc(bem_plan_s* p, const uint8_t* bc, double c);
+void panel_destroy(bem_plan_s* p);
+// the system operator's exact entries (block of consecutive panels i0 .. i0+sz)
+void panel_block(const bem_plan_s* p, int64_t i0, int sz, double* A);
 __host__ __device__ double kernel2d_point(int kind, int dx, int dy, double h);
 
 }  // namespace bemfft

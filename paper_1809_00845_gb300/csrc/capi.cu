@@ -391,6 +391,28 @@ bem_status bem_plan(bem_plan_t* out, int dim, const int64_t* n, double h, int64_
   return plan_impl(out, dim, n, h, nb, cell, w, normal, kernel, nu, mu, prec, flags, stream);
 }
 
+bem_status bem_plan_panels(bem_plan_t* out, int64_t n, double h, int64_t nb, const double* panels, int order,
+                           int near_radius, bem_precision prec, uint32_t flags, void* stream) {
+  if (!out || !panels) {
+    set_error("bem_plan_panels: null pointer argument");
+    return BEM_ERR_ARG;
+  }
+  *out = nullptr;
+  if (flags != 0) {
+    set_error("bem_plan_panels: flags must be 0");
+    return BEM_ERR_ARG;
+  }
+  if (prec != BEM_F64 && prec != BEM_F32 && prec != BEM_F32X2 && prec != BEM_TC_BF16X3 && prec != BEM_TC_F16X3) {
+    set_error("bem_plan_panels: unknown precision");
+    return BEM_ERR_ARG;
+  }
+  if ((n & (n - 1)) != 0 || n < 4 || n > 4096) {
+    set_error("bem_plan_panels: n must be a power of two in [4, 4096]");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  return panel_plan_impl(out, n, h, nb, panels, order, near_radius, prec, static_cast<cudaStream_t>(stream));
+}
+
 bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
   if (!p || !bc) {
     set_error("bem_set_bc: null pointer argument");
@@ -406,6 +428,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       set_error("bem_set_bc: bc entries must be 0 or 1");
       return BEM_ERR_ARG;
     }
+  if (p->pf) return panel_set_bc(p, bc, c);
   if (p->have_bc && c == p->c && std::equal(p->h_bc.begin(), p->h_bc.end(), bc)) return BEM_OK;
   free_operator(p->op_system);
   ++p->op_version;
@@ -579,6 +602,15 @@ bem_status bem_enable_refinement(bem_plan_t p, int enable) {
   if (p->companion) return BEM_OK;
   const int64_t n[3] = {p->n, p->n, p->n};
   bem_plan_t c = nullptr;
+  if (p->pf) {
+    const PanelOp& f = *p->pf;
+    bem_status rc = panel_plan_impl(&c, p->n, p->h, p->nb, f.h_panels.data(), f.order, f.R,
+                                    p->n >= 256 ? BEM_F32X2 : BEM_F64, nullptr);
+    if (rc != BEM_OK) return rc;
+    c->pc.kind = 0;
+    p->companion = c;
+    return BEM_OK;
+  }
   bem_status rc = plan_impl(&c, p->dim, n, p->h, p->nb, p->h_cell_user.data(), p->h_w_user.data(),
                             p->h_normal_user.data(), (bem_kernel)p->kernel, p->nu, p->mu,
                             p->dim == 2 && p->n >= 256 ? BEM_F32X2 : BEM_F64, 0, nullptr);
@@ -598,7 +630,7 @@ bem_status bem_get_info(bem_plan_t p, bem_plan_info* info) {
   info->n = p->n;
   info->N = p->N;
   info->nb = p->nb;
-  info->precision = p->tc == 1 ? BEM_TC_BF16X3 : (p->tc == 2 ? BEM_TC_F16X3 : p->prec);
+  info->precision = p->pf ? p->pf->public_prec : (p->tc == 1 ? BEM_TC_BF16X3 : (p->tc == 2 ? BEM_TC_F16X3 : p->prec));
   info->grid_ctas = p->grid;
   info->threads_per_cta = p->threads;
   info->scratch_bytes = p->scratch_bytes;
@@ -616,6 +648,7 @@ bem_status bem_set_kernel_timing(bem_plan_t p, int enable) {
   p->ev_used = 0;
   p->timed_ms = 0;
   p->timed_launches = 0;
+  if (p->pf) return bem_set_kernel_timing(p->pf->inner, enable);
   return BEM_OK;
 }
 
@@ -624,6 +657,7 @@ bem_status bem_kernel_time(bem_plan_t p, double* total_ms, int64_t* launches) {
     set_error("bem_kernel_time: null pointer argument");
     return BEM_ERR_ARG;
   }
+  if (p->pf) return bem_kernel_time(p->pf->inner, total_ms, launches);
   for (int i = 0; i + 1 < p->ev_used; i += 2) {
     BEM_CUDA_TRY(cudaEventSynchronize(p->ev_pool[i + 1]));
     float ms = 0.f;
@@ -642,6 +676,7 @@ bem_status bem_device_status(bem_plan_t p, void* stream) {
     set_error("bem_device_status: null plan");
     return BEM_ERR_ARG;
   }
+  if (p->pf) return bem_device_status(p->pf->inner, stream);
   if (!p->d_status) return BEM_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int h = 0;
@@ -657,6 +692,7 @@ bem_status bem_device_status(bem_plan_t p, void* stream) {
 int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
   (void)layer;
   if (!p) return -1;
+  if (p->pf) return 2 + bem_launches_per_apply(p->pf->inner, BEM_SINGLE);  // project, node plan, interpolate
   if (p->dim == 3) return 6;  // prep, x-DFT, y pass, z pass, inverse y pass, gather
   return 3;                   // prep (weighted densities), fused column kernel, reduction
 }
@@ -664,6 +700,7 @@ int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
 bem_status bem_destroy(bem_plan_t p) {
   if (!p) return BEM_OK;
   if (p->companion) bem_destroy(p->companion);
+  panel_destroy(p);
   cudaFree(p->d_perm);
   cudaFree(p->d_rowptr);
   cudaFree(p->d_col);
@@ -730,6 +767,7 @@ const char* bem_last_error(void) { return g_last_error.c_str(); }
 namespace bemfft {
 
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st) {
+  if (p->pf) return launch_apply_panels(p, layer, in, out, st);
   if (p->dim == 3) {
     const Operator3D* op3 = nullptr;
     if (layer == BEM_SINGLE) op3 = &p->op3_single;

@@ -50,6 +50,10 @@ extern "C" bem_status bem_apply_static_scratch(bem_plan_t p, bem_layer layer, co
     set_error("bem_apply_static_scratch: input and output must not alias");
     return BEM_ERR_ARG;
   }
+  if (p->pf) {
+    set_error("bem_apply_static_scratch: accuracy-mode plans apply through bem_apply");
+    return BEM_ERR_UNSUPPORTED;
+  }
   if (p->dim != 2) {
     set_error("bem_apply_static_scratch: 3D plans need more scratch than the static buffer holds; use bem_apply");
     return BEM_ERR_UNSUPPORTED;

@@ -277,7 +277,7 @@ bem_status build_preconditioner(bem_plan_s* p) {
     set_error("preconditioner needs boundary conditions");
     return BEM_ERR_ARG;
   }
-  if (p->dim == 2 && p->pc.bs * p->ncomp <= kPcGpuMax) return build_preconditioner_gpu2d(p);
+  if (p->dim == 2 && !p->pf && p->pc.bs * p->ncomp <= kPcGpuMax) return build_preconditioner_gpu2d(p);
   const int64_t nb = p->nb;
   const int bs = p->pc.bs;
   const int nc = p->ncomp;
@@ -291,7 +291,8 @@ bem_status build_preconditioner(bem_plan_s* p) {
     const int64_t i0 = (int64_t)b * bs;
     const int sz = (int)std::min<int64_t>(bs, nb - i0) * nc;
     std::vector<double> A((size_t)sz * sz);
-    for (int ia = 0; ia < sz; ++ia) {
+    if (p->pf) panel_block(p, i0, sz, A.data());  // accuracy mode: exact panel integrals
+    for (int ia = 0; ia < sz && !p->pf; ++ia) {
       const int64_t i = i0 + ia / nc;
       const int ca = ia % nc;
       for (int jb = 0; jb < sz; ++jb) {
