@@ -244,10 +244,10 @@ def projection_weights(panels, h, order):
     return idx, PS, PD
 
 
-def accelerated_matrices(panels, h, order=3, R=3):
-    """Dense single- and double-layer matrices of the grid-accelerated
-    operator: near entries exact (as O2), far entries through the projected
-    moments, the grid kernel and the interpolation (module docstring)."""
+def accelerated_parts(panels, h, order=3, R=3):
+    """The pieces of the accelerated operator: interpolation I (nb, nodes),
+    grid kernel G (nodes, nodes), projections PS, PD (nodes, nb), the near
+    mask and the exact matrices (module docstring)."""
     if R < order:
         raise ValueError("R must be at least the stencil order")
     m, _, _, _ = panel_geometry(panels)
@@ -266,12 +266,19 @@ def accelerated_matrices(panels, h, order=3, R=3):
     np.add.at(PS, (inv.ravel(), rows), PSw.ravel())
     np.add.at(PD, (inv.ravel(), rows), PDw.ravel())
     Gn = grid_kernel(nk[:, None, :] - nk[None, :, :], h)
-    Sg = I @ Gn @ PS
-    Dg = I @ Gn @ PD
     near = near_mask(m, h, order, R)
     S_ex, D_ex = o2_matrices(panels)
-    S_acc = np.where(near, S_ex, Sg)
-    D_acc = np.where(near, D_ex, Dg)
+    return I, Gn, PS, PD, near, S_ex, D_ex
+
+
+def accelerated_matrices(panels, h, order=3, R=3):
+    """Dense single- and double-layer matrices of the grid-accelerated
+    operator: near entries exact (as O2), far entries through the projected
+    moments, the grid kernel and the interpolation, and the double layer's
+    row-sum term (module docstring)."""
+    I, Gn, PS, PD, near, S_ex, D_ex = accelerated_parts(panels, h, order, R)
+    S_acc = np.where(near, S_ex, I @ Gn @ PS)
+    D_acc = np.where(near, D_ex, I @ Gn @ PD)
     D_acc = D_acc + np.diag(0.5 - D_acc.sum(axis=1))
     return S_acc, D_acc
 
