@@ -375,6 +375,52 @@ def _batched_solve_c5():
             "sequential_all_converged": all(i["status"] == 0 for i in its), "speedup": t_seq / t_b}
 
 
+def accuracy_mode(dev, n=4096, order=3, R=5):
+    """The star as flat panels (accuracy mode, bem_plan_panels): system apply
+    time, plan time, and the mixed-condition solve of u = e^x cos y to 1e-6
+    with double-float refinement, its error against the analytic field
+    beside the paper-form (grid-node) operator's on the same problem."""
+    import torch
+    from paper_1809_00845_gb300 import inputs as I
+    from paper_1809_00845_gb300.bem import Plan
+    b = I.curve_panels(n, I.star_curve(0.3, 0.3, 5))
+    u, q = I.panel_data(b, I.field_expcos)
+    bc = (np.asarray(b.param) >= math.pi).astype(np.uint8)
+    data = np.where(bc == 0, u, q)
+    p = Plan.from_panel_boundary(b, "f32", order, R)
+    p.set_bc(bc, 0.5)
+    x = torch.randn(b.nb, dtype=torch.float32, device=dev)
+    p.set_kernel_timing(True)
+    ms = _time_applies(p, "system", x, 100)
+    col_ms, col_n = p.kernel_time()
+    p.set_kernel_timing(False)
+    p.enable_refinement(True)
+    p.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+    torch.cuda.synchronize()
+    u_out, q_out, info = p.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+    xs = np.where(bc == 0, q_out, u_out)
+    truth = np.where(bc == 0, q, u)
+    res = {"panels": b.nb, "order": order, "near_radius": R,
+           "system_apply_ms": ms, "node_convolution_kernel_us": 1e3 * col_ms / max(1, col_n),
+           "plan_s": p.info()["plan_seconds"],
+           "solve_1e-6": {"seconds": info["seconds"], "iters": info["iters"], "status": info["status"],
+                          "rel_residual": info["rel_residual"], "refine_steps": info["refine_steps"]},
+           "rel_error_vs_analytic": float(np.linalg.norm(xs - truth) / np.linalg.norm(truth))}
+    p.close()
+    # the paper-form operator (sources and targets on grid nodes) on the same field and conditions
+    bg = I.star_boundary(n)
+    ug, qg = I.boundary_data(bg, I.field_expcos)
+    bcg = I.mixed_bc_theta(bg)
+    pg = Plan.from_boundary(bg, "laplace2d", "f32")
+    pg.enable_refinement(True)
+    ug_out, qg_out, infog = pg.solve(bcg, np.where(bcg == 0, ug, qg), tol=1e-6, restart=100, max_iter=3000)
+    xg = np.where(bcg == 0, qg_out, ug_out)
+    tg = np.where(bcg == 0, qg, ug)
+    res["paper_form_rel_error_vs_analytic"] = float(np.linalg.norm(xg - tg) / np.linalg.norm(tg))
+    pg.close()
+    return res
+
+
 def secondary_configs(dev):
     """Apply times (and the circle solve) of the other configurations, a few
     repetitions each: circle n=128 FP64, ellipsoid n=256 FP32, Kelvin cube
@@ -440,6 +486,7 @@ def secondary_configs(dev):
     for p in plans:
         p.close()
     out["batched_stars_64_f32"]["solve_1e-6"] = _batched_solve_c5()
+    out["accuracy_mode_star_n4096"] = accuracy_mode(dev)
     b = I.cube_boundary(128)
     p = Plan.from_boundary(b, "kelvin3d", "f32")
     x = torch.randn(b.nb * 3, dtype=torch.float32, device=dev)
