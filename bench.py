@@ -36,6 +36,8 @@ if ROOT not in sys.path:
 
 METRIC = "BIE applies/s & time-to-solve @ rel. residual 1e-6 vs plain FP32; % HBM roofline"
 WORKLOAD = "2D Laplace star r=0.3(1+0.3cos5t), n=4096 (padded 8192^2), mixed BC, system apply"
+WORKLOAD_PANELS = ("2D Laplace star r=0.3(1+0.3cos5t) as flat panels (accuracy mode, order 3, R 5), n=4096 "
+                   "(padded 8192^2), mixed BC, system apply")
 FALLBACK_HBM_GBS = 6800.0
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
+    ap.add_argument("--workload", default="star", choices=["star", "star_panels"],
+                    help="star_panels: the same star and conditions in the accuracy mode (flat panels, p=3, R=5)")
     return ap.parse_args()
 
 
@@ -144,7 +148,7 @@ class ClockSampler:
 # system operator, from ncu (profiles/col2d_v2_star4096_launches.md), keyed by
 # the hash of the kernel sources it was measured on; reported only while the
 # sources are unchanged.
-MEASURED_TRAFFIC = {"n4096_f32_system": ("f2540eb150d387b2", 205.12e6)}
+MEASURED_TRAFFIC = {"n4096_f32_star_system": ("f2540eb150d387b2", 205.12e6)}
 
 
 def kernel_source_hash():
@@ -157,11 +161,16 @@ def kernel_source_hash():
     return hs.hexdigest()[:16]
 
 
-def workload(n):
+def workload(n, kind="star"):
     from paper_1809_00845_gb300 import inputs as I
-    b = I.star_boundary(n)
-    u, q = I.boundary_data(b, I.field_expcos)
-    bc = I.mixed_bc_theta(b)
+    if kind == "star_panels":
+        b = I.curve_panels(n, I.star_curve(0.3, 0.3, 5))
+        u, q = I.panel_data(b, I.field_expcos)
+        bc = (np.asarray(b.param) >= math.pi).astype(np.uint8)
+    else:
+        b = I.star_boundary(n)
+        u, q = I.boundary_data(b, I.field_expcos)
+        bc = I.mixed_bc_theta(b)
     data = np.where(bc == 0, u, q)
     return b, bc, data
 
@@ -550,8 +559,10 @@ def run_ours(args):
     B.build()
     from paper_1809_00845_gb300.bem import Plan
 
-    b, bc, data = workload(args.n)
-    plan = Plan.from_boundary(b, "laplace2d", args.precision)
+    b, bc, data = workload(args.n, args.workload)
+    panels = args.workload == "star_panels"
+    plan = (Plan.from_panel_boundary(b, args.precision, 3, 5) if panels
+            else Plan.from_boundary(b, "laplace2d", args.precision))
     plan.set_bc(bc, 0.5)
     pinfo = plan.info()
     f32io = args.precision != "f64"
@@ -650,7 +661,10 @@ def run_ours(args):
         return 0
 
     avg_col_s = (col_ms / max(1, col_launches)) / 1e3
-    flops = col_kernel_flops(args.n, b.nb, 3, 1)
+    # the fused column kernel's work: 3 fields over the cells, or (accuracy
+    # mode) 1 field over the active grid nodes of the inner convolution
+    flops = (col_kernel_flops(args.n, pinfo["grid_nodes"], 1, 1) if panels
+             else col_kernel_flops(args.n, b.nb, 3, 1))
     sm_mhz = clk.get("sm_max_mhz") or SM_MAX_MHZ_NOMINAL
     peak_tflops = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     if args.precision == "f64":
@@ -667,15 +681,16 @@ def run_ours(args):
                 break
     if hbm_peak is None:
         hbm_peak = FALLBACK_HBM_GBS
-    balg = b_alg_bytes(args.n, 3, 1, 3)
+    balg = b_alg_bytes(args.n, 1, 1, 1) if panels else b_alg_bytes(args.n, 3, 1, 3)
     traffic = None
-    key, val = MEASURED_TRAFFIC.get(f"n{args.n}_{args.precision}_system", (None, None))
+    key, val = MEASURED_TRAFFIC.get(f"n{args.n}_{args.precision}_{args.workload}_system", (None, None))
     if key is not None and key == kernel_source_hash():
         traffic = val
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved_tflops / peak_tflops) if peak_tflops else None, "traffic": traffic,
-                "kernel": ("k_col2d_v2<double,3,false,0,0>" if not f32io else
-                           "k_col2d_v2<float,3,true,512,%d>" % {"tc_bf16x3": 1, "tc_f16x3": 2}.get(args.precision, 0)),
+                "kernel": ("k_col2d_v2<double,%d,false,0,0>" % (1 if panels else 3) if not f32io else
+                           "k_col2d_v2<float,%d,%s,512,%d>" % (1 if panels else 3, "false" if panels else "true",
+                                                               {"tc_bf16x3": 1, "tc_f16x3": 2}.get(args.precision, 0))),
                 "avg_launch_us": avg_col_s * 1e6,
                 "launches_timed": col_launches, "flops_per_launch": flops,
                 "peak_basis": f"FP32 FMA: {SM_COUNT_NOMINAL} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
@@ -687,14 +702,14 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_rate(b, bc, args.cpu_seconds)
     cufft = None
-    if not args.no_extra and world == 1 and args.precision == "f32":
+    if not args.no_extra and world == 1 and args.precision == "f32" and not panels:
         x0 = xs[0].double().cpu().numpy()
         y0 = plan.apply("system", xs[0]).double().cpu().numpy()
         cufft = cufft_comparator(b, bc, x0, y0)
         cufft["ours_ms_per_apply"] = ms_max / args.steps
         cufft["speedup_ours"] = cufft["ms_per_apply"] / cufft["ours_ms_per_apply"]
     tcv = None
-    if not args.no_extra and world == 1 and args.precision == "f32":
+    if not args.no_extra and world == 1 and args.precision == "f32" and not panels:
         tcv = tensor_core_variants(b, bc, data, xs[0], ms_max / args.steps, pc_block if solve else 128,
                                    solve["fp32_refined"]["seconds"] if solve else None)
         from paper_1809_00845_gb300.bem import Plan as _P
@@ -710,7 +725,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": args.n, "N": 2 * args.n, "nb": b.nb, "precision": args.precision,
+            "config": {"workload": WORKLOAD_PANELS if panels else WORKLOAD, "n": args.n, "N": 2 * args.n,
+                       "nb": b.nb, "precision": args.precision, "grid_nodes": pinfo["grid_nodes"],
                        "parallelism": f"replicas{world}", "grid_ctas": pinfo["grid_ctas"],
                        "threads_per_cta": pinfo["threads_per_cta"],
                        "l2": "working set > L2: spectra 3 x (n+1)^2 x 4 B = 201 MB stream each apply (no flush)"},

@@ -114,6 +114,7 @@ typedef struct {
   size_t scratch_bytes;      /* device scratch owned by the plan (partials, weighted densities) */
   size_t spectra_bytes;      /* device bytes of the compressed kernel spectra */
   double plan_seconds;       /* wall time of bem_plan */
+  int64_t grid_nodes;        /* accuracy mode: active grid nodes of the inner convolution; else nb */
 } bem_plan_info;
 
 /* Build a plan (Section 3-4: kernel tables on the padded grid and their

@@ -57,7 +57,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("ncomp", ctypes.c_int), ("n", ctypes.c_int64), ("N", ctypes.c_int64),
                 ("nb", ctypes.c_int64), ("precision", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("threads_per_cta", ctypes.c_int), ("scratch_bytes", ctypes.c_size_t),
-                ("spectra_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double)]
+                ("spectra_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double),
+                ("grid_nodes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -636,6 +636,7 @@ bem_status bem_get_info(bem_plan_t p, bem_plan_info* info) {
   info->scratch_bytes = p->scratch_bytes;
   info->spectra_bytes = p->spectra_bytes;
   info->plan_seconds = p->plan_seconds;
+  info->grid_nodes = p->pf ? p->pf->nnodes : p->nb;
   return BEM_OK;
 }
 
