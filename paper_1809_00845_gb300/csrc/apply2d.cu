@@ -476,6 +476,9 @@ static std::vector<uint16_t> tc_matrices(int kind, int J) {
   return out;
 }
 
+// largest per-CTA twiddle cache (bytes over all CTAs) the column kernel keeps
+constexpr size_t kTwiddleCacheMax = (size_t)40 << 20;
+
 // shared memory of the four-step kernel
 template <typename T>
 static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc, bool tc) {
@@ -658,8 +661,12 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   const int64_t npos = p->v2_npos;
   BEM_CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->grid * npos * tb));
   BEM_CUDA_TRY(cudaMalloc(&p->d_val, (size_t)npos * 2 * tb));
-  BEM_CUDA_TRY(cudaMalloc(&p->d_twc, (size_t)p->grid * npos * 2 * tb));
-  p->scratch_bytes += (size_t)p->grid * npos * tb + (size_t)npos * 2 * tb + (size_t)p->grid * npos * 2 * tb;
+  // per-CTA cache of each cell's sparse twiddle for the gather: kept only while
+  // it stays L2-resident beside the streamed spectra and the partial sums
+  // (larger cell sets recompute the twiddle in the gather)
+  const size_t twc_bytes = (size_t)p->grid * npos * 2 * tb;
+  if (twc_bytes <= kTwiddleCacheMax) BEM_CUDA_TRY(cudaMalloc(&p->d_twc, twc_bytes));
+  p->scratch_bytes += (size_t)p->grid * npos * tb + (size_t)npos * 2 * tb + (p->d_twc ? twc_bytes : 0);
   return BEM_OK;
 }
 
