@@ -141,3 +141,43 @@ def test_panel_mixed_solve_with_refinement(torch_cuda, prec):
     err = rel_l2(x, truth)
     print(f"error against the analytic field {err:.3e}")
     assert err < 1e-2
+
+
+def test_panel_plans_in_a_batch_graph(torch_cuda):
+    """Accuracy-mode plans of several grid sizes captured into one CUDA graph
+    (bem_batch_*): every segment equals the plan's own apply bit for bit, and
+    the lockstep batched solve reaches the tolerance on each."""
+    torch = torch_cuda
+    from paper_1809_00845_gb300.bem import Batch, Plan
+    rng = np.random.default_rng(9)
+    plans, bcs, datas = [], [], []
+    for n in (128, 256, 512, 256):
+        b = I.curve_panels(n, I.random_star_curve(rng))
+        p = Plan.from_panel_boundary(b, "f32", 3, 4)
+        u, q = I.panel_data(b, I.field_expcos)
+        bc = (np.asarray(b.param) >= np.pi).astype(np.uint8)
+        p.set_bc(bc, 0.5)
+        plans.append(p)
+        bcs.append(bc)
+        datas.append(np.where(bc == 0, u, q))
+    batch = Batch(plans, "system", streams=2)
+    assert batch.launches == 5 * len(plans)
+
+    class _Cai:
+        def __init__(self, ptr, numel):
+            self.__cuda_array_interface__ = {"shape": (numel,), "typestr": "<f4", "data": (ptr, False), "version": 2}
+    raw_in = torch.as_tensor(_Cai(batch.d_in, batch.total), device="cuda")
+    raw_out = torch.as_tensor(_Cai(batch.d_out, batch.total), device="cuda")
+    src = torch.from_numpy(rng.standard_normal(batch.total).astype(np.float32)).cuda()
+    raw_in.copy_(src)
+    batch.apply()
+    torch.cuda.synchronize()
+    for p, off in zip(plans, batch.offsets):
+        ref = p.apply("system", src[off:off + p.nb].contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(raw_out[off:off + p.nb], ref)
+    _, _, infos, rc = batch.solve(np.concatenate(bcs), np.concatenate(datas), tol=1e-5, restart=100, max_iter=2000)
+    assert rc == 0
+    for info in infos:
+        assert info["rel_residual"] <= 1e-5, info
+    batch.close()
