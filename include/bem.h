@@ -130,11 +130,16 @@ typedef struct {
  *   nu, mu  Poisson ratio and shear modulus (Kelvin only; ignored otherwise)
  *   prec    arithmetic of the apply; spectra are always computed in FP64 on
  *           the device and rounded to prec
- *   flags   reserved, pass 0
+ *   flags   0, or BEM_PLAN_SINGLE_LAYER_ONLY: the plan serves BEM_SINGLE
+ *           applies only (bem_set_bc and the other layers return
+ *           BEM_ERR_UNSUPPORTED); the column kernel then needs no staging
+ *           rows for the double layer's fields and keeps more of its
+ *           accumulators in shared memory
  *   stream  cudaStream_t (may be NULL) used for the set-up kernels; the call
  *           synchronises it before returning
  * The plan copies every input.  Device memory: spectra (ncomp-dependent,
  * (n+1)^dim reals each), scratch, boundary metadata. */
+#define BEM_PLAN_SINGLE_LAYER_ONLY 1u
 bem_status bem_plan(bem_plan_t* out, int dim, const int64_t* n, double h, int64_t nb, const int32_t* cell,
                     const double* w, const double* normal, bem_kernel kernel, double nu, double mu,
                     bem_precision prec, uint32_t flags, void* stream);

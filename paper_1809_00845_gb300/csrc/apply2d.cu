@@ -644,8 +644,18 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   BEM_CUDA_TRY(cudaGetDevice(&dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  p->acc_in_smem = smem_v2<T>(n, TT, p->v2_npos, R, true, p->tc != 0) <= (size_t)smem_optin;
-  p->smem_bytes = smem_v2<T>(n, TT, p->v2_npos, R, p->acc_in_smem, p->tc != 0);
+  // staging rows for fields 1, 2 only when the multi-field kernels can run
+  const bool staging = R && !p->single_only;
+  p->acc_in_smem = smem_v2<T>(n, TT, p->v2_npos, staging, true, p->tc != 0) <= (size_t)smem_optin;
+  p->acc_rows = p->acc_in_smem ? (int)Q : 0;
+  if (!p->acc_in_smem && TT == 512) {
+    // one CTA per SM either way: fill the rest of shared memory with as many
+    // accumulator rows as fit, the others stay in the partial sums
+    const size_t base = smem_v2<T>(n, TT, 0, staging, false, p->tc != 0);
+    if (base < (size_t)smem_optin)
+      p->acc_rows = (int)std::min<int64_t>(Q, (int64_t)(((size_t)smem_optin - base) / ((size_t)TT * sizeof(T))));
+  }
+  p->smem_bytes = smem_v2<T>(n, TT, 0, staging, false, p->tc != 0) + (size_t)p->acc_rows * TT * sizeof(T);
   if (p->smem_bytes > (size_t)smem_optin) {
     set_error("grid too large for the shared-memory column buffers");
     return BEM_ERR_UNSUPPORTED;
@@ -811,7 +821,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.partial = static_cast<T*>(sp.partial);
   cp.twc = static_cast<cplx<T>*>(sp.twc);
   cp.npos = npos;
-  cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
+  cp.acc_rows = p->acc_rows;
   cp.has_carry = p->v2_carry ? 1 : 0;
   cp.tcmat = static_cast<const uint4*>(p->d_tcmat);
   cp.status = p->d_status;

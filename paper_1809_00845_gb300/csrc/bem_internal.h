@@ -201,6 +201,8 @@ struct bem_plan_s {
   int grid = 0, threads = 0;
   size_t smem_bytes = 0;
   bool acc_in_smem = false;
+  int acc_rows = 0;             // four-step kernel: interleaved cell rows accumulated in shared memory
+  bool single_only = false;     // BEM_PLAN_SINGLE_LAYER_ONLY: only BEM_SINGLE applies (smaller footprint)
   size_t scratch_bytes = 0, spectra_bytes = 0;
   double plan_seconds = 0;
   // timing

@@ -215,8 +215,8 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     tc = prec == BEM_TC_BF16X3 ? 1 : 2;
     prec = BEM_F32;
   }
-  if (flags != 0) {
-    set_error("bem_plan: flags must be 0");
+  if ((flags & ~BEM_PLAN_SINGLE_LAYER_ONLY) != 0) {
+    set_error("bem_plan: unknown flags");
     return BEM_ERR_ARG;
   }
   if (!(h > 0.0) || !std::isfinite(h) || nb < 1 || nb > (int64_t)1 << 30) {
@@ -266,6 +266,7 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   p->kernel = kernel;
   p->prec = prec;
   p->tc = tc;
+  p->single_only = (flags & BEM_PLAN_SINGLE_LAYER_ONLY) != 0;
   p->pc.bs = dim == 2 ? 128 : 64;  // default block-Jacobi block (cells)
   p->n = nn;
   p->N = 2 * nn;
@@ -429,6 +430,10 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       return BEM_ERR_ARG;
     }
   if (p->pf) return panel_set_bc(p, bc, c);
+  if (p->single_only) {
+    set_error("bem_set_bc: the plan serves the single layer only (BEM_PLAN_SINGLE_LAYER_ONLY)");
+    return BEM_ERR_UNSUPPORTED;
+  }
   if (p->have_bc && c == p->c && std::equal(p->h_bc.begin(), p->h_bc.end(), bc)) return BEM_OK;
   free_operator(p->op_system);
   ++p->op_version;
@@ -769,6 +774,10 @@ namespace bemfft {
 
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st) {
   if (p->pf) return launch_apply_panels(p, layer, in, out, st);
+  if (p->single_only && layer != BEM_SINGLE) {
+    set_error("bem_apply: the plan serves the single layer only (BEM_PLAN_SINGLE_LAYER_ONLY)");
+    return BEM_ERR_UNSUPPORTED;
+  }
   if (p->dim == 3) {
     const Operator3D* op3 = nullptr;
     if (layer == BEM_SINGLE) op3 = &p->op3_single;

@@ -147,10 +147,18 @@ __device__ __forceinline__ void add_carries(const Col2Dv2Params<T>& p, const Col
   }
 }
 
+// accumulators: rows i < qs of the thread's cells in shared memory (sacc), the
+// rest in the CTA's slice of the partial sums (gacc); the row index is the
+// same for every lane of a warp, so the choice never diverges
+template <typename T>
+__device__ __forceinline__ T* acc_at(T* sacc, T* gacc, int qs, int i, int TT, int t) {
+  return (i < qs ? sacc : gacc) + (size_t)i * TT + t;
+}
+
 template <typename T, int TTC>
 __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
-                                             const cplx<T>* rows, const Twiddles2L<T>& tw, T* acc,
-                                             const cplx<T>* twc) {
+                                             const cplx<T>* rows, const Twiddles2L<T>& tw, T* sacc, T* gacc,
+                                             int qs, const cplx<T>* twc) {
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   const T ckx = (kx == 0 || kx == g.n) ? T(1) : T(2);
@@ -171,7 +179,7 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const Co
     }
 #pragma unroll
     for (int i = 0; i < CB; ++i)
-      if (i0 + i < cnt) acc[(i0 + i) * TT + t] += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
+      if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
   }
 }
 
@@ -286,8 +294,9 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   // copy of the next one
   cplx<T>* carry = reinterpret_cast<cplx<T>*>(sS);
   cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
-  T* acc = p.acc_in_smem ? reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0))
-                         : p.partial + (size_t)blockIdx.x * p.npos;
+  T* sacc = reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0));
+  T* gacc = p.partial + (size_t)blockIdx.x * p.npos;
+  const int qs = p.acc_rows;
   cplx<T>* twc = p.twc ? p.twc + (size_t)blockIdx.x * p.npos : nullptr;
   for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
   // per-thread plan data is re-read (L1) where used rather than held in
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
 #define C0 __ldg(p.chunk + t)
 #define CNT (__ldg(p.chunk + t + 1) - __ldg(p.chunk + t))
 #define TINFO __ldg(p.tinfo + t)
-  for (int i = 0; i < CNT; ++i) acc[i * TT + t] = T(0);
+  for (int i = 0; i < CNT; ++i) *acc_at(sacc, gacc, qs, i, TT, t) = T(0);
   __syncthreads();
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
   const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + 128, g.log2N - 7,
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
 #pragma unroll
       for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
       __syncthreads();
-      gather_cells(p, g, kx, CNT, sA, tw, acc, twc);
+      gather_cells(p, g, kx, CNT, sA, tw, sacc, gacc, qs, twc);
     } else {
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
 #pragma unroll
         for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = v[m];
         __syncthreads();
-        gather_cells(p, g, kx, CNT, sA, tw, acc, twc);
+        gather_cells(p, g, kx, CNT, sA, tw, sacc, gacc, qs, twc);
       }
     }
   }
@@ -382,8 +391,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     }
     tc_teardown(fs.tc.tmem - (uint32_t)(kTcGroupCols * (t >> 7)), TTC / 128 * kTcGroupCols);
   }
-  if (p.acc_in_smem)
-    for (int i = 0; i < CNT; ++i) p.partial[(size_t)blockIdx.x * p.npos + i * TT + t] = acc[i * TT + t];
+  for (int i = 0; i < CNT && i < qs; ++i) gacc[(size_t)i * TT + t] = sacc[(size_t)i * TT + t];
 #undef C0
 #undef CNT
 #undef TINFO

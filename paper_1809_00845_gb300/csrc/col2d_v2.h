@@ -31,7 +31,7 @@ struct Col2Dv2Params {
   T* partial;            // gridDim.x * npos, interleaved positions
   cplx<T>* twc;          // gridDim.x * npos: each cell's sparse twiddle of the current column, or null
   int npos;              // Q*TT
-  int acc_in_smem;
+  int acc_rows;          // interleaved cell rows i < acc_rows accumulate in shared memory, the rest in partial
   int has_carry;         // some row is split between threads
   const uint4* tcmat;    // tensor-core stages: the two B matrices (hi, lo), 8 KB
   int* status;           // tensor-core stages: bit 0 set when a device wait gave up

@@ -398,7 +398,7 @@ bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, co
     }
     const int64_t nn2[2] = {n, n};
     bem_status rc = bem_plan(&f.inner, 2, nn2, h, nn, cell.data(), w1.data(), nrm.data(), BEM_LAPLACE_2D, 0.3, 1.0,
-                             prec, 0, st);
+                             prec, BEM_PLAN_SINGLE_LAYER_ONLY, st);
     if (rc != BEM_OK) return fail(rc);
   }
   p->prec = f.inner->prec;
