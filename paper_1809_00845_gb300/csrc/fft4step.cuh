@@ -133,22 +133,9 @@ struct FourStep {
       v[k] = cmul(v[k], z);
     }
   }
-  // T5: u[a*J + kj] *= e^{DIR 2 pi i l kj / TT}.  With J = 16 (one line per
-  // register set) the factors come like T2's from the table at kj = 1, 4, 8,
-  // 12 and short products in between.
+  // T5: u[a*J + kj] *= e^{DIR 2 pi i l kj / TT}
   template <int DIR>
   __device__ __forceinline__ void twiddleT5(cplx<T> (&u)[16]) const {
-    if (J == 16) {
-      const cplx<T> z1 = dirw<DIR>(tb.t5[32 + l]);
-      cplx<T> z = z1;
-#pragma unroll
-      for (int kj = 1; kj < 16; ++kj) {
-        if (kj == 4 || kj == 8 || kj == 12) z = dirw<DIR>(tb.t5[kj * 32 + l]);
-        else if (kj > 1) z = cmul(z, z1);
-        u[kj] = cmul(u[kj], z);
-      }
-      return;
-    }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int kj = i & (J - 1);
