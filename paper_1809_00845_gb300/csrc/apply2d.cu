@@ -202,24 +202,34 @@ __global__ void k_prep_v2(int npos, const int32_t* __restrict__ perm, const TIO*
 }
 
 // out[perm[j]] = sum_b partial[b*npos + j] (+ diag * in) over interleaved
-// positions j (padding skipped), FP64 sum in a fixed
-// order: 32 cells per block, 8 warps each summing every 8th partial, then the
-// 8 warp sums in order.
+// positions j (padding skipped), FP64 sum in a fixed order: 32 cells per
+// block, 16 warps each summing every 16th partial (four interleaved chains, so
+// that four loads are in flight), then the 16 warp sums in order.
 template <typename T, typename TIO>
-__global__ void __launch_bounds__(256) k_reduce_v2(const T* __restrict__ partial, int grid, int npos,
+__global__ void __launch_bounds__(512) k_reduce_v2(const T* __restrict__ partial, int grid, int npos,
                                                    const int32_t* __restrict__ perm, const TIO* __restrict__ diag,
                                                    const TIO* __restrict__ in, TIO* __restrict__ out) {
-  __shared__ double red[8][33];
+  constexpr int W = 16;  // warps, each summing every W-th CTA's partial
+  __shared__ double red[W][33];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (j < npos)
-    for (int b = wp; b < grid; b += 8) s += (double)partial[(size_t)b * npos + j];
-  red[wp][lane] = s;
+  // four independent chains keep four loads in flight; fixed order throughout
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (j < npos) {
+    int b = wp;
+    for (; b + 3 * W < grid; b += 4 * W) {
+      s0 += (double)partial[(size_t)b * npos + j];
+      s1 += (double)partial[(size_t)(b + W) * npos + j];
+      s2 += (double)partial[(size_t)(b + 2 * W) * npos + j];
+      s3 += (double)partial[(size_t)(b + 3 * W) * npos + j];
+    }
+    for (; b < grid; b += W) s0 += (double)partial[(size_t)b * npos + j];
+  }
+  red[wp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (wp == 0 && j < npos && perm[j] >= 0) {
     double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    for (int k = 0; k < W; ++k) t += red[k][lane];
     const int u = perm[j];
     if (diag) t += (double)diag[u] * (double)in[u];
     out[u] = (TIO)t;
@@ -829,7 +839,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   launch_col2d<T>(p, op.nf, cp, st);
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k_reduce_v2<T, TIO><<<(npos + 31) / 32, 256, 0, st>>>(
+  k_reduce_v2<T, TIO><<<(npos + 31) / 32, 512, 0, st>>>(
       static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il, static_cast<const TIO*>(op.diag),
       static_cast<const TIO*>(in), static_cast<TIO*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
