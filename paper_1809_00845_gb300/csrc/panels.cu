@@ -269,24 +269,29 @@ static bem_status upload_all(bem_plan_s* p, const std::vector<int32_t>& node, co
                                2 * f.nnodes) * sizeof(T) +
             (pptr.size() + f.h_nptr.size()) * 8 + (pj.size() + f.h_nj.size()) * 4 + p->nb;
   // Gauss row-sum term: delta = 1/2 - (D 1) of the operator without it
-  T* ones = nullptr;
-  T* dl = nullptr;
-  BEM_CUDA_TRY(cudaMalloc(&ones, p->nb * sizeof(T)));
-  BEM_CUDA_TRY(cudaMalloc(&dl, p->nb * sizeof(T)));
+  // (ones and the result share one scratch allocation, freed on every path)
+  T* buf = nullptr;
+  BEM_CUDA_TRY(cudaMalloc(&buf, 2 * p->nb * sizeof(T)));
+  T* ones = buf;
+  T* dl = buf + p->nb;
   std::vector<T> h1(p->nb, (T)1);
-  BEM_CUDA_TRY(cudaMemcpy(ones, h1.data(), p->nb * sizeof(T), cudaMemcpyHostToDevice));
-  rc = launch_t<T>(p, BEM_DOUBLE, ones, dl, nullptr);
-  if (rc == BEM_OK) {
-    BEM_CUDA_TRY(cudaMemcpy(h1.data(), dl, p->nb * sizeof(T), cudaMemcpyDeviceToHost));
-    f.h_delta.resize(p->nb);
-    for (int64_t i = 0; i < p->nb; ++i) f.h_delta[i] = 0.5 - (double)h1[i];
-    std::vector<T> dt(p->nb);
-    for (int64_t i = 0; i < p->nb; ++i) dt[i] = (T)f.h_delta[i];
-    BEM_CUDA_TRY(cudaMemcpy(f.d_delta, dt.data(), p->nb * sizeof(T), cudaMemcpyHostToDevice));
+  cudaError_t e = cudaMemcpy(ones, h1.data(), p->nb * sizeof(T), cudaMemcpyHostToDevice);
+  rc = e == cudaSuccess ? launch_t<T>(p, BEM_DOUBLE, ones, dl, nullptr) : BEM_ERR_CUDA;
+  if (rc == BEM_OK) e = cudaMemcpy(h1.data(), dl, p->nb * sizeof(T), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_error(std::string("bem_plan_panels: row-sum term: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
   }
-  cudaFree(ones);
-  cudaFree(dl);
-  return rc;
+  if (rc != BEM_OK) return rc;
+  f.h_delta.resize(p->nb);
+  std::vector<T> dt(p->nb);
+  for (int64_t i = 0; i < p->nb; ++i) {
+    f.h_delta[i] = 0.5 - (double)h1[i];
+    dt[i] = (T)f.h_delta[i];
+  }
+  BEM_CUDA_TRY(cudaMemcpy(f.d_delta, dt.data(), p->nb * sizeof(T), cudaMemcpyHostToDevice));
+  return BEM_OK;
 }
 
 bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, const double* panels, int order,

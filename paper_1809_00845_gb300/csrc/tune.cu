@@ -76,31 +76,34 @@ bem_status bem_tune_batch(bem_batch_t b, int reps, int* streams_out) {
   int best = 0;
   bem_status rc;
   if (!tune_lookup(key, &best)) {
-    cudaStream_t st = b->side.empty() ? nullptr : b->side[0];
-    cudaStream_t ts;
-    BEM_CUDA_TRY(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
-    cudaEvent_t e0, e1;
-    BEM_CUDA_TRY(cudaEventCreate(&e0));
-    BEM_CUDA_TRY(cudaEventCreate(&e1));
+    // timing stream and events, released on every path
+    struct Timing {
+      cudaStream_t ts = nullptr;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      ~Timing() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ts) cudaStreamDestroy(ts);
+      }
+    } tm;
+    BEM_CUDA_TRY(cudaStreamCreateWithFlags(&tm.ts, cudaStreamNonBlocking));
+    BEM_CUDA_TRY(cudaEventCreate(&tm.e0));
+    BEM_CUDA_TRY(cudaEventCreate(&tm.e1));
     float best_ms = 0.0f;
-    (void)st;
     for (int S : {1, 2, 4, 8}) {
       if ((rc = batch_set_streams(b, S)) != BEM_OK) return rc;
-      for (int i = 0; i < 2; ++i) BEM_CUDA_TRY(cudaGraphLaunch(b->exec, ts));
-      BEM_CUDA_TRY(cudaEventRecord(e0, ts));
-      for (int i = 0; i < reps; ++i) BEM_CUDA_TRY(cudaGraphLaunch(b->exec, ts));
-      BEM_CUDA_TRY(cudaEventRecord(e1, ts));
-      BEM_CUDA_TRY(cudaEventSynchronize(e1));
+      for (int i = 0; i < 2; ++i) BEM_CUDA_TRY(cudaGraphLaunch(b->exec, tm.ts));
+      BEM_CUDA_TRY(cudaEventRecord(tm.e0, tm.ts));
+      for (int i = 0; i < reps; ++i) BEM_CUDA_TRY(cudaGraphLaunch(b->exec, tm.ts));
+      BEM_CUDA_TRY(cudaEventRecord(tm.e1, tm.ts));
+      BEM_CUDA_TRY(cudaEventSynchronize(tm.e1));
       float ms = 0.0f;
-      BEM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      BEM_CUDA_TRY(cudaEventElapsedTime(&ms, tm.e0, tm.e1));
       if (best == 0 || ms < best_ms) {
         best = S;
         best_ms = ms;
       }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamDestroy(ts);
     tune_store(key, best);
   }
   if ((rc = batch_set_streams(b, best)) != BEM_OK) return rc;
