@@ -275,6 +275,17 @@ int bem_launches_per_apply(bem_plan_t plan, bem_layer layer);
  * bem_solve checks it before returning. */
 bem_status bem_device_status(bem_plan_t plan, void* stream);
 
+/* Test hook for the bounded device waits (no counterpart in the paper).
+ * BEM_TEST_WAIT_RUNS_OUT: the tensor-core column kernels of this plan issue no
+ * tensor-core product and no completion signal, so every wait of theirs runs
+ * out after its bound (about one second); the CTAs then stop, free their tensor
+ * memory and record the event for bem_device_status.  Nothing faults, traps
+ * or hangs; outputs of such applies are invalid.  Pass 0 to clear.  Plans
+ * without tensor-core stages ignore the flag.  Returns BEM_ERR_ARG for a null
+ * plan or unknown bits. */
+#define BEM_TEST_WAIT_RUNS_OUT 1u
+bem_status bem_set_test_flags(bem_plan_t plan, uint32_t flags);
+
 /* ---- batched apply (many geometries, one CUDA graph) --------------------
  * The applies of `count` plans (one precision, grids of any sizes) captured
  * once into a CUDA graph, the plans spread round-robin over `streams` forked

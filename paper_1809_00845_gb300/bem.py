@@ -22,6 +22,7 @@ BEM_ERR_BREAKDOWN, BEM_ERR_NONFINITE, BEM_ERR_TIMEOUT, BEM_ERR_UNSUPPORTED = 5, 
 BEM_LAPLACE_2D, BEM_LAPLACE_3D, BEM_KELVIN_3D = 0, 1, 2
 BEM_F64, BEM_F32, BEM_F32X2, BEM_TC_BF16X3, BEM_TC_F16X3 = 0, 1, 2, 3, 4
 BEM_SINGLE, BEM_DOUBLE, BEM_SYSTEM = 0, 1, 2
+BEM_TEST_WAIT_RUNS_OUT = 1
 
 KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d": BEM_KELVIN_3D}
 PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32, "f32x2": BEM_F32X2, "tc_bf16x3": BEM_TC_BF16X3,
@@ -31,7 +32,7 @@ F32_IO = (BEM_F32, BEM_TC_BF16X3, BEM_TC_F16X3)
 LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 
 EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
-            "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_device_status", "bem_destroy",
+            "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_device_status", "bem_set_test_flags", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
             "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
             "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_launches_per_apply.argtypes = [P, I]
     lib.bem_launches_per_apply.restype = I
     lib.bem_device_status.argtypes = [P, P]
+    lib.bem_set_test_flags.argtypes = [P, ctypes.c_uint32]
     lib.bem_destroy.argtypes = [P]
     lib.bem_status_string.argtypes = [I]
     lib.bem_status_string.restype = ctypes.c_char_p
@@ -123,7 +125,8 @@ def load_library(path: str = LIB_PATH):
     lib.bem_last_error.restype = ctypes.c_char_p
     for name in ("bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
                  "bem_apply_static_scratch", "bem_apply_host", "bem_solve", "bem_get_info",
-                 "bem_set_kernel_timing", "bem_kernel_time", "bem_device_status", "bem_destroy"):
+                 "bem_set_kernel_timing", "bem_kernel_time", "bem_device_status", "bem_set_test_flags",
+                 "bem_destroy"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -310,6 +313,10 @@ class Plan:
     def launches_per_apply(self, layer="system"):
         lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
         return int(load_library().bem_launches_per_apply(self._h, lay))
+
+    def set_test_flags(self, flags: int):
+        """Test hook for the bounded device waits (bem_set_test_flags)."""
+        _check(load_library().bem_set_test_flags(self._h, int(flags)))
 
     def device_status(self, stream=None):
         """Raise BemError(BEM_ERR_TIMEOUT) if a kernel gave up a bounded device wait since the last check."""

@@ -835,6 +835,7 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.has_carry = p->v2_carry ? 1 : 0;
   cp.tcmat = static_cast<const uint4*>(p->d_tcmat);
   cp.status = p->d_status;
+  cp.tc_no_commit = (p->test_flags & BEM_TEST_WAIT_RUNS_OUT) != 0 ? 1 : 0;
   cudaEvent_t e1 = nullptr;
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   launch_col2d<T>(p, op.nf, cp, st);

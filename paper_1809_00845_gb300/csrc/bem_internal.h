@@ -181,6 +181,7 @@ struct bem_plan_s {
   int tc = 0;                   // tensor-core DFT stages: 0 none, 1 BF16 hi + lo, 2 FP16 hi + lo
   void* d_tcmat = nullptr;      // their B matrices (hi, lo; 8 KB)
   int* d_status = nullptr;      // device status word (bit 0: a bounded wait gave up)
+  uint32_t test_flags = 0;      // bem_set_test_flags (bounded-wait tests)
   // 3D path
   int32_t* d_lptr = nullptr;    // n*n + 1 line pointers over sorted cells (line = z*n + y)
   uint16_t* d_x3 = nullptr;     // x per sorted cell

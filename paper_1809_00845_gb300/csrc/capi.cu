@@ -695,6 +695,16 @@ bem_status bem_device_status(bem_plan_t p, void* stream) {
   return BEM_ERR_TIMEOUT;
 }
 
+bem_status bem_set_test_flags(bem_plan_t p, uint32_t flags) {
+  if (!p || (flags & ~BEM_TEST_WAIT_RUNS_OUT) != 0) {
+    set_error("bem_set_test_flags: null plan or unknown flags");
+    return BEM_ERR_ARG;
+  }
+  p->test_flags = flags;
+  if (p->pf) p->pf->inner->test_flags = flags;
+  return BEM_OK;
+}
+
 int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
   (void)layer;
   if (!p) return -1;

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   fs.init(t, TT, sA, ftab);
   if constexpr (TCK > 0) {
     const uint32_t tm = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 128 * kTcGroupCols);
-    fs.tc.bind(t, (uint32_t)__cvta_generic_to_shared(smem_raw), tm);
+    fs.tc.bind(t, (uint32_t)__cvta_generic_to_shared(smem_raw), tm, p.tc_no_commit != 0);
   }
   auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
     const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells

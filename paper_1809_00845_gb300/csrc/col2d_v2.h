@@ -35,6 +35,7 @@ struct Col2Dv2Params {
   int has_carry;         // some row is split between threads
   const uint4* tcmat;    // tensor-core stages: the two B matrices (hi, lo), 8 KB
   int* status;           // tensor-core stages: bit 0 set when a device wait gave up
+  int tc_no_commit;      // test hook: issue no MMA and no commit, so every wait runs out
 };
 
 // number of table entries of the four-step kernel for TT threads, N = 16 TT:

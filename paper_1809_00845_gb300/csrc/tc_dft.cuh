@@ -164,6 +164,7 @@ struct TcDft {
   uint32_t phase;   // parity of the next mbarrier phase
   int t;            // thread index
   bool failed;      // a wait of this thread gave up (the kernel reports it)
+  bool no_commit;   // test hook: issue nothing, so the wait runs out
 
   // One radix-16 stage: v[f] <- sum_i v[i] e^{DIR 2 pi i f i / 16} for the
   // matrix `mat` (0 = the 16-point DFT; 1 = the engine's J-point blocks).
@@ -205,7 +206,7 @@ struct TcDft {
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     tc_fence_before();
     group_sync(t >> 7);
-    if ((t & 127) == 0) {
+    if ((t & 127) == 0 && !no_commit) {
       tc_fence_after();
       constexpr uint32_t id = tc_idesc<KIND>();
       const uint32_t bh = b_base + (uint32_t)mat * 4096u, bl = bh + 2048u;
@@ -218,7 +219,9 @@ struct TcDft {
       }
       tc_commit(mbar);
     }
-    if (!tc_wait(mbar, phase)) failed = true;
+    // after a wait that gave up, the rest of the column skips its waits (the
+    // CTA stops at the next column)
+    if (!failed && !tc_wait(mbar, phase)) failed = true;
     phase ^= 1u;
     tc_fence_after();
     uint32_t q[32];
@@ -242,8 +245,9 @@ struct TcDft {
   }
 
   // bind this thread to its warpgroup's resources (after tc_setup)
-  __device__ __forceinline__ void bind(int t_, uint32_t hdr, uint32_t tmem_base) {
+  __device__ __forceinline__ void bind(int t_, uint32_t hdr, uint32_t tmem_base, bool no_commit_) {
     t = t_;
+    no_commit = no_commit_;
     const int g = t >> 7;
     mbar = hdr + 8u * (uint32_t)g;
     b_base = hdr + kTcMatOffset;

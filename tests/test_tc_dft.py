@@ -147,3 +147,31 @@ def test_tc_refined_solve_reaches_1e6(torch_cuda, oracle_mod, kind):
     rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, u * (bc == 0), q * (bc == 1))
     r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
     assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 2e-6
+
+
+def test_tc_wait_that_runs_out_is_reported_and_the_context_survives(torch_cuda, oracle_mod):
+    """The test hook makes every tensor-core stage issue nothing, so its
+    bounded wait runs out (about a second; nothing faults, traps or hangs);
+    the CTAs stop and free their tensor memory, bem_device_status reports
+    BEM_ERR_TIMEOUT once, and the next apply without the hook is correct."""
+    import time
+    from paper_1809_00845_gb300 import bem
+    b = I.star_boundary(1024)
+    bc = I.mixed_bc_theta(b)
+    x = np.random.default_rng(3).standard_normal(b.nb)
+    plan = _plan(b, "tc_bf16x3")
+    plan.set_bc(bc, 0.5)
+    plan.set_test_flags(bem.BEM_TEST_WAIT_RUNS_OUT)
+    t0 = time.perf_counter()
+    gpu_apply(torch_cuda, plan, "system", x)
+    elapsed = time.perf_counter() - t0
+    with pytest.raises(bem.BemError) as e:
+        plan.device_status()
+    assert e.value.status == bem.BEM_ERR_TIMEOUT
+    assert 0.5 < elapsed < 30.0, elapsed
+    plan.device_status()  # the record was cleared
+    plan.set_test_flags(0)
+    out = gpu_apply(torch_cuda, plan, "system", x)
+    plan.device_status()
+    ref = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x, rows=(0, 400))
+    assert rel_l2(out[:400], ref) <= TOL["tc_bf16x3"]
