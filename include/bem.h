@@ -302,6 +302,17 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
 bem_status bem_batch_buffers(bem_batch_t batch, void** in_dev, void** out_dev, size_t* total);
 bem_status bem_batch_offset(bem_batch_t batch, int i, size_t* offset);
 bem_status bem_batch_apply(bem_batch_t batch, void* stream);
+
+/* Grouped launches (default on): the batch's FP32 four-step plans (2D,
+ * n >= 256, no tensor-core stages) that share a grid size are applied by ONE
+ * persistent column-kernel launch per size, whose CTAs take contiguous ranges
+ * of the columns of all those plans (no per-plan tail), between the plans'
+ * own density and reduction launches; the other plans are applied one by one.
+ * Results are deterministic but, the columns being split over the CTAs
+ * differently, not bit-identical to bem_apply of each plan (FP32 rounding).
+ * enable = 0 applies every plan on its own (bit-identical to bem_apply).  The
+ * batch graph is captured again. */
+bem_status bem_batch_set_grouping(bem_batch_t batch, int enable);
 int bem_batch_launches(bem_batch_t batch);  /* kernel launches inside one replay */
 bem_status bem_batch_destroy(bem_batch_t batch);
 

@@ -34,7 +34,7 @@ LAYERS = {"single": BEM_SINGLE, "double": BEM_DOUBLE, "system": BEM_SYSTEM}
 EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner", "bem_apply", "bem_apply_host", "bem_apply_static_scratch", "bem_solve",
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_device_status", "bem_set_test_flags", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
-            "bem_batch_apply", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
+            "bem_batch_apply", "bem_batch_set_grouping", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
             "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step"]
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_batch_buffers.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t)]
     lib.bem_batch_offset.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
     lib.bem_batch_apply.argtypes = [P, P]
+    lib.bem_batch_set_grouping.argtypes = [P, I]
     lib.bem_batch_launches.argtypes = [P]
     lib.bem_batch_launches.restype = I
     lib.bem_batch_destroy.argtypes = [P]
@@ -107,6 +108,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_tune_batch.argtypes = [P, I, ctypes.POINTER(I)]
     lib.bem_tune_preconditioner.argtypes = [P, P, P, D, D, I, I, ctypes.POINTER(I)]
     for name in ("bem_batch_create", "bem_batch_buffers", "bem_batch_offset", "bem_batch_apply", "bem_batch_destroy",
+                 "bem_batch_set_grouping",
                  "bem_batch_solve", "bem_tune_batch", "bem_tune_preconditioner"):
         getattr(lib, name).restype = I
     lib.bem_net_create.argtypes = [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64]
@@ -346,6 +348,12 @@ class Batch:
 
     def apply(self, stream=None):
         _check(load_library().bem_batch_apply(self._h, _stream_ptr(stream)))
+
+    def set_grouping(self, enable: bool):
+        """Grouped persistent launches per grid size (bem_batch_set_grouping)."""
+        lib = load_library()
+        _check(lib.bem_batch_set_grouping(self._h, 1 if enable else 0))
+        self.launches = int(lib.bem_batch_launches(self._h))
 
     def tune(self, reps=10):
         """Measured number of capture streams (bem_tune_batch); returns it."""

@@ -803,16 +803,11 @@ static bem_status launch_v1(bem_plan_s* p, const Operator& op, const void* in, v
   return BEM_OK;
 }
 
-// T: arithmetic type of the column kernel; TIO: type of the caller's vectors
-template <typename T, typename TIO>
-static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
-                            bool timed, cudaStream_t st) {
+// kernel parameters of one plan's four-step apply
+template <typename T>
+static Col2Dv2Params<T> col2d_params(const bem_plan_s* p, const Operator& op, const ScratchPtrs& sp) {
   const int nb = (int)p->nb;
-  const int tb = 256;
   const int npos = (int)p->v2_npos;
-  k_prep_v2<T, TIO><<<(npos + tb - 1) / tb, tb, 0, st>>>(npos, p->d_perm_il, static_cast<const TIO*>(in),
-                                                  static_cast<const T*>(op.coefA), static_cast<const T*>(op.coefB),
-                                                  static_cast<cplx<T>*>(sp.val));
   Col2Dv2Params<T> cp{};
   cp.n = (int)p->n;
   cp.log2N = p->log2N;
@@ -836,6 +831,19 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   cp.tcmat = static_cast<const uint4*>(p->d_tcmat);
   cp.status = p->d_status;
   cp.tc_no_commit = (p->test_flags & BEM_TEST_WAIT_RUNS_OUT) != 0 ? 1 : 0;
+  return cp;
+}
+
+// T: arithmetic type of the column kernel; TIO: type of the caller's vectors
+template <typename T, typename TIO>
+static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, void* out, const ScratchPtrs& sp,
+                            bool timed, cudaStream_t st) {
+  const int tb = 256;
+  const int npos = (int)p->v2_npos;
+  k_prep_v2<T, TIO><<<(npos + tb - 1) / tb, tb, 0, st>>>(npos, p->d_perm_il, static_cast<const TIO*>(in),
+                                                  static_cast<const T*>(op.coefA), static_cast<const T*>(op.coefB),
+                                                  static_cast<cplx<T>*>(sp.val));
+  const Col2Dv2Params<T> cp = col2d_params<T>(p, op, sp);
   cudaEvent_t e1 = nullptr;
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
   launch_col2d<T>(p, op.nf, cp, st);
@@ -843,6 +851,129 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   k_reduce_v2<T, TIO><<<(npos + 31) / 32, 512, 0, st>>>(
       static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il, static_cast<const TIO*>(op.diag),
       static_cast<const TIO*>(in), static_cast<TIO*>(out));
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ------------------------------------------------------ grouped batch applies
+
+bool group_eligible(const bem_plan_s* p) {
+  return p->dim == 2 && p->v2 && p->prec == BEM_F32 && p->tc == 0 && !p->pf && p->threads >= 32;
+}
+
+static const Operator* op_of(const bem_plan_s* p, bem_layer layer) {
+  if (layer == BEM_SINGLE) return &p->op_single;
+  if (layer == BEM_DOUBLE) return &p->op_double;
+  return p->have_bc ? &p->op_system : nullptr;
+}
+
+void group_free(BatchGroup& g) {
+  cudaFree(g.d_params);
+  cudaFree(g.d_c0);
+  g.d_params = nullptr;
+  g.d_c0 = nullptr;
+}
+
+// resident CTAs per SM of the grouped kernels (their registers may differ
+// from the per-plan kernels')
+static cudaError_t group_configure(int TT, size_t smem, int* bps) {
+  switch (TT) {
+    case 512: return Col2DKernels<float, 512>::configure_group(smem, TT, bps);
+    case 256: return Col2DKernels<float, 256>::configure_group(smem, TT, bps);
+    case 128: return Col2DKernels<float, 128>::configure_group(smem, TT, bps);
+    case 64: return Col2DKernels<float, 64>::configure_group(smem, TT, bps);
+    default: return Col2DKernels<float, 32>::configure_group(smem, TT, bps);
+  }
+}
+
+bem_status group_build(BatchGroup& g, const std::vector<bem_plan_s*>& plans, bem_layer layer) {
+  group_free(g);
+  const int P = (int)g.members.size();
+  const bem_plan_s* p0 = plans[g.members[0]];
+  g.threads = p0->threads;
+  g.smem = 0;
+  std::vector<Col2Dv2Params<float>> hp(P);
+  for (int m = 0; m < P; ++m) {
+    const bem_plan_s* p = plans[g.members[m]];
+    const Operator* op = op_of(p, layer);
+    if (!op) {
+      set_error("bem_batch: BEM_SYSTEM needs bem_set_bc on every plan");
+      return BEM_ERR_ARG;
+    }
+    ScratchPtrs sp{};
+    sp.val = p->d_val;
+    sp.partial = p->d_partial;
+    sp.twc = p->d_twc;
+    hp[m] = col2d_params<float>(p, *op, sp);
+    g.nf = op->nf;
+    g.smem = std::max(g.smem, p->smem_bytes);
+  }
+  int dev = 0, nsm = 0, bps = 0;
+  BEM_CUDA_TRY(cudaGetDevice(&dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  BEM_CUDA_TRY(group_configure(g.threads, g.smem, &bps));
+  // never more CTAs than any member's partial sums have rows for
+  int rows_max = p0->grid;
+  for (int m = 0; m < P; ++m) rows_max = std::min(rows_max, plans[g.members[m]]->grid);
+  const int64_t cols = (int64_t)P * (p0->n + 1);
+  g.grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(std::min<int64_t>((int64_t)std::max(bps, 1) * nsm, cols), (int64_t)P * (rows_max - 1)));
+  // contiguous column ranges [b C / G, (b + 1) C / G); a member's rows are the
+  // CTAs whose range meets its columns
+  std::vector<int> c0(P, -1);
+  g.rows.assign(P, 0);
+  for (int b = 0; b < g.grid; ++b) {
+    const int64_t lo = (int64_t)b * cols / g.grid, hi = ((int64_t)b + 1) * cols / g.grid;
+    if (lo >= hi) continue;
+    const int m0 = (int)(lo / (p0->n + 1)), m1 = (int)((hi - 1) / (p0->n + 1));
+    for (int m = m0; m <= m1; ++m) {
+      if (c0[m] < 0) c0[m] = b;
+      g.rows[m] = b - c0[m] + 1;
+    }
+  }
+  for (int m = 0; m < P; ++m)
+    if (g.rows[m] > rows_max) {
+      set_error("internal: grouped launch needs more partial rows than a plan holds");
+      return BEM_ERR_UNSUPPORTED;
+    }
+  BEM_CUDA_TRY(cudaMalloc(&g.d_params, P * sizeof(Col2Dv2Params<float>)));
+  BEM_CUDA_TRY(cudaMalloc(&g.d_c0, P * sizeof(int)));
+  BEM_CUDA_TRY(cudaMemcpy(g.d_params, hp.data(), P * sizeof(Col2Dv2Params<float>), cudaMemcpyHostToDevice));
+  BEM_CUDA_TRY(cudaMemcpy(g.d_c0, c0.data(), P * sizeof(int), cudaMemcpyHostToDevice));
+  return BEM_OK;
+}
+
+bem_status group_issue(const BatchGroup& g, const std::vector<bem_plan_s*>& plans, bem_layer layer, const void* in,
+                       void* out, const std::vector<size_t>& offset, cudaStream_t st) {
+  const int tb = 256;
+  const int P = (int)g.members.size();
+  const float* fin = static_cast<const float*>(in);
+  float* fout = static_cast<float*>(out);
+  for (int m = 0; m < P; ++m) {
+    const bem_plan_s* p = plans[g.members[m]];
+    const Operator* op = op_of(p, layer);
+    const int npos = (int)p->v2_npos;
+    k_prep_v2<float, float><<<(npos + tb - 1) / tb, tb, 0, st>>>(
+        npos, p->d_perm_il, fin + offset[g.members[m]], static_cast<const float*>(op->coefA),
+        static_cast<const float*>(op->coefB), static_cast<cplx<float>*>(p->d_val));
+  }
+  const auto* dp = static_cast<const Col2Dv2Params<float>*>(g.d_params);
+  switch (g.threads) {
+    case 512: Col2DKernels<float, 512>::launch_group(g.nf, g.grid, 512, g.smem, st, dp, g.d_c0, P); break;
+    case 256: Col2DKernels<float, 256>::launch_group(g.nf, g.grid, 256, g.smem, st, dp, g.d_c0, P); break;
+    case 128: Col2DKernels<float, 128>::launch_group(g.nf, g.grid, 128, g.smem, st, dp, g.d_c0, P); break;
+    case 64: Col2DKernels<float, 64>::launch_group(g.nf, g.grid, 64, g.smem, st, dp, g.d_c0, P); break;
+    default: Col2DKernels<float, 32>::launch_group(g.nf, g.grid, 32, g.smem, st, dp, g.d_c0, P); break;
+  }
+  for (int m = 0; m < P; ++m) {
+    const bem_plan_s* p = plans[g.members[m]];
+    const Operator* op = op_of(p, layer);
+    const int npos = (int)p->v2_npos;
+    const size_t o = offset[g.members[m]];
+    k_reduce_v2<float, float><<<(npos + 31) / 32, 512, 0, st>>>(
+        static_cast<const float*>(p->d_partial), g.rows[m], npos, p->d_perm_il, static_cast<const float*>(op->diag),
+        fin + o, fout + o);
+  }
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }

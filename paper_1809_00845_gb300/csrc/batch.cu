@@ -7,6 +7,7 @@
 // (segment of plan i at offset[i], nb_i * ncomp_i values of the common
 // precision).  When bem_set_bc has rebuilt a plan's system operator since the
 // capture, the next apply captures the graph again.
+#include <algorithm>
 #include <vector>
 
 #include "bem_internal.h"
@@ -21,8 +22,15 @@ bem_status batch_issue_applies(bem_batch_s* b, const void* in, void* out, cudaSt
   bem_status rc = BEM_OK;
   BEM_CUDA_TRY(cudaEventRecord(b->events[0], cap));
   for (int s = 1; s < S; ++s) BEM_CUDA_TRY(cudaStreamWaitEvent(b->side[s], b->events[0], 0));
-  for (size_t i = 0; i < b->plans.size() && rc == BEM_OK; ++i) {
-    cudaStream_t s = i % S == 0 ? cap : b->side[i % S];
+  // grouped launches first (one stream each), then the remaining plans round-robin
+  int k = 0;
+  for (size_t gi = 0; gi < b->groups.size() && rc == BEM_OK; ++gi, ++k) {
+    cudaStream_t s = k % S == 0 ? cap : b->side[k % S];
+    rc = group_issue(b->groups[gi], b->plans, b->layer, in, out, b->offset, s);
+  }
+  for (size_t si = 0; si < b->solo.size() && rc == BEM_OK; ++si, ++k) {
+    const int i = b->solo[si];
+    cudaStream_t s = k % S == 0 ? cap : b->side[k % S];
     const unsigned char* pin = static_cast<const unsigned char*>(in) + b->offset[i] * tb;
     unsigned char* pout = static_cast<unsigned char*>(out) + b->offset[i] * tb;
     rc = apply_operator(b->plans[i], b->layer, pin, pout, s);
@@ -34,12 +42,55 @@ bem_status batch_issue_applies(bem_batch_s* b, const void* in, void* out, cudaSt
   return rc;
 }
 
+// Plans that share a grid (FP32 four-step, same thread count) are applied by
+// one grouped persistent launch; the kernel parameters of a group are built
+// here, before any capture, from the plans' current operators.
+static bem_status batch_build_groups(bem_batch_s* b) {
+  for (auto& g : b->groups) group_free(g);
+  b->groups.clear();
+  b->solo.clear();
+  std::vector<int> by_threads;  // distinct thread counts of the eligible plans
+  std::vector<std::vector<int>> members;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const bem_plan_s* p = b->plans[i];
+    if (!b->grouped || !group_eligible(p) || (b->layer == BEM_SYSTEM && !p->have_bc)) {
+      b->solo.push_back((int)i);
+      continue;
+    }
+    size_t k = 0;
+    while (k < by_threads.size() && by_threads[k] != p->threads) ++k;
+    if (k == by_threads.size()) {
+      by_threads.push_back(p->threads);
+      members.emplace_back();
+    }
+    members[k].push_back((int)i);
+  }
+  for (size_t k = 0; k < members.size(); ++k) {
+    if (members[k].size() < 2) {
+      b->solo.push_back(members[k][0]);
+      continue;
+    }
+    BatchGroup g;
+    g.members = members[k];
+    bem_status rc = group_build(g, b->plans, b->layer);
+    if (rc != BEM_OK) {
+      group_free(g);
+      return rc;
+    }
+    b->groups.push_back(g);
+  }
+  std::sort(b->solo.begin(), b->solo.end());
+  return BEM_OK;
+}
+
 bem_status batch_capture(bem_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
   b->launches = 0;
+  bem_status grc = batch_build_groups(b);
+  if (grc != BEM_OK) return grc;
   cudaStream_t cap = b->side[0];
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     set_error("bem_batch: stream capture failed to begin");
@@ -62,10 +113,9 @@ bem_status batch_capture(bem_batch_s* b) {
     return BEM_ERR_CUDA;
   }
   b->versions.clear();
-  for (auto* p : b->plans) {
-    b->versions.push_back(p->op_version);
-    b->launches += bem_launches_per_apply(p, b->layer);
-  }
+  for (auto* p : b->plans) b->versions.push_back(p->op_version);
+  for (const auto& g : b->groups) b->launches += 2 * (int)g.members.size() + 1;  // preps, one column launch, reductions
+  for (int i : b->solo) b->launches += bem_launches_per_apply(b->plans[i], b->layer);
   return BEM_OK;
 }
 
@@ -86,6 +136,7 @@ bem_status bem_batch_destroy(bem_batch_t b) {
   if (b->companions) bem_batch_destroy(b->companions);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& g : b->groups) group_free(g);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->events) cudaEventDestroy(e);
   cudaFree(b->d_in);
@@ -196,5 +247,15 @@ bem_status bem_batch_apply(bem_batch_t b, void* stream) {
 }
 
 int bem_batch_launches(bem_batch_t b) { return b ? b->launches : -1; }
+
+bem_status bem_batch_set_grouping(bem_batch_t b, int enable) {
+  if (!b) {
+    set_error("bem_batch_set_grouping: null batch");
+    return BEM_ERR_ARG;
+  }
+  b->grouped = enable != 0;
+  batch_solve_free(b);  // its step graph holds the old launches
+  return batch_capture(b);
+}
 
 }  // extern "C"

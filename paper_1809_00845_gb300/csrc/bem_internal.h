@@ -225,6 +225,19 @@ struct bem_plan_s {
   bemfft::PanelOp* pf = nullptr;  // accuracy mode (bem_plan_panels), else null
 };
 
+namespace bemfft {
+// Plans of a batch applied by one persistent column-kernel launch (FP32
+// four-step plans with the same grid and thread count; apply2d.cu)
+struct BatchGroup {
+  std::vector<int> members;  // indices into the batch's plans
+  std::vector<int> rows;     // per member: CTAs whose column range reaches it (rows of its partial sums)
+  void* d_params = nullptr;  // Col2Dv2Params<float>[members]
+  int* d_c0 = nullptr;       // per member: the first such CTA
+  int grid = 0, threads = 0, nf = 0;
+  size_t smem = 0;
+};
+}  // namespace bemfft
+
 // Batch of plans applied through one CUDA graph (batch.cu); the batched
 // GMRES (gmres.cu) keeps its workspace here too.
 struct BatchSolveWs;
@@ -245,6 +258,9 @@ struct bem_batch_s {
   int launches = 0;
   BatchSolveWs* ws = nullptr;
   bem_batch_s* companions = nullptr;  // batch over the plans' refinement companions (solve only)
+  std::vector<bemfft::BatchGroup> groups;  // plans applied by one grouped launch per grid size
+  std::vector<int> solo;                   // the others, applied one by one
+  bool grouped = true;                     // form grouped launches (bem_batch_set_grouping)
 };
 
 namespace bemfft {
@@ -268,6 +284,12 @@ bem_status alloc_field_rho(bem_plan_s* p, Operator& op);
 bem_status build_op_v2(bem_plan_s* p, Operator& op, const std::vector<double>& coefA, const std::vector<double>& coefB,
                        const std::vector<uint8_t>& type);
 size_t apply_scratch_bytes(const bem_plan_s* p, const Operator& op);
+// grouped batch applies (apply2d.cu)
+bool group_eligible(const bem_plan_s* p);
+bem_status group_build(BatchGroup& g, const std::vector<bem_plan_s*>& plans, bem_layer layer);
+bem_status group_issue(const BatchGroup& g, const std::vector<bem_plan_s*>& plans, bem_layer layer,
+                       const void* in, void* out, const std::vector<size_t>& offset, cudaStream_t st);
+void group_free(BatchGroup& g);
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st);
 // Device scratch of one apply: per-field densities (slot layout kernel) or
 // density pairs (four-step kernel), and the per-CTA partial sums.

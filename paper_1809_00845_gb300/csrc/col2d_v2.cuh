@@ -268,6 +268,93 @@ __device__ __forceinline__ void spectral_multiply(const T* sS, const SpecAddr& a
   }
 }
 
+// rows t + m*TT (m < 8) of a field into the engine's register map (rows the
+// thread holds no cell in are zero)
+template <typename T, int TTC>
+__device__ __forceinline__ void load_rows(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, const cplx<T>* src,
+                                          cplx<T> (&v)[16]) {
+  const int t = threadIdx.x;
+  const unsigned rmask = (unsigned)__ldg(p.tinfo + t) & 0xffu;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[rowslot(t + m * g.TT)] : cplx<T>{T(0), T(0)};
+#pragma unroll
+  for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
+}
+
+// Shared-memory regions of a column CTA
+template <typename T>
+struct ColSmem {
+  cplx<T>* sA;     // transform buffer / row sums of field 0
+  cplx<T>* sF;     // row sums of fields 1, 2 (ACCREG kernels)
+  T* sS;           // spectrum column
+  cplx<T>* carry;  // carries of split rows (aliases sS)
+};
+
+// One x-frequency column kx of plan p: sparse x-DFT of the fields, column
+// transforms, spectral multiply, inverse, gather into the accumulators.  The
+// caller has synchronised since the previous column's gather.
+template <typename T, int NF, bool ACCREG, int TTC, int TCK>
+__device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx,
+                                             FourStep<T, TCK>& fs, const Twiddles2L<T>& tw, const ColSmem<T>& sm,
+                                             T* sacc, T* gacc, int qs, cplx<T>* twc) {
+  const int t = threadIdx.x, TT = g.TT, n = g.n;
+  const int cnt = __ldg(p.chunk + t + 1) - __ldg(p.chunk + t);
+  cplx<T>* sA = sm.sA;
+  cplx<T>* sF = sm.sF;
+  if constexpr (ACCREG) {
+    sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+    __syncthreads();
+    if (p.has_carry) {
+      add_carries<T, NF, -1>(p, g, cnt, __ldg(p.tinfo + t) >> 8, sA, sF, sm.carry);
+      __syncthreads();
+    }
+    cplx<T> y[16];
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+      cplx<T> v[16];
+      load_rows(p, g, f == 0 ? sA : sF + (size_t)(f - 1) * n, v);
+      __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
+      load_spectrum(p, g, f, kx, sm.sS);
+      fs.template forward<true>(v);
+      spectrum_ready();
+      const SpecAddr sa = spec_addr(fs, g);
+      if (f == 0) spectral_multiply<T, false>(sm.sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
+      else spectral_multiply<T, true>(sm.sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
+    }
+    fs.inverse(y);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
+    __syncthreads();
+    gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
+  } else {
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+      if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
+      if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+      else if (f == 0) sparse_rows<T, NF, 0>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+      else if (f == 1) sparse_rows<T, NF, 1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+      else sparse_rows<T, NF, 2>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+      __syncthreads();
+      if (p.has_carry) {
+        add_carries<T, NF, 0>(p, g, cnt, __ldg(p.tinfo + t) >> 8, sA, sF, sm.carry);
+        __syncthreads();
+      }
+      cplx<T> v[16];
+      load_rows(p, g, sA, v);
+      __syncthreads();
+      load_spectrum(p, g, f, kx, sm.sS);
+      fs.template forward<true>(v);
+      spectrum_ready();
+      spectral_multiply<T, false>(sm.sS, spec_addr(fs, g), imag_of(p, f) != 0, oddy_of(p, f) != 0, v, v);
+      fs.inverse(v);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = v[m];
+      __syncthreads();
+      gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
+    }
+  }
+}
+
 template <int TTC>
 struct ColBounds {
   static constexpr int threads = TTC > 0 ? TTC : 512;
@@ -299,12 +386,8 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   const int qs = p.acc_rows;
   cplx<T>* twc = p.twc ? p.twc + (size_t)blockIdx.x * p.npos : nullptr;
   for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
-  // per-thread plan data is re-read (L1) where used rather than held in
-  // registers across the transforms
-#define C0 __ldg(p.chunk + t)
-#define CNT (__ldg(p.chunk + t + 1) - __ldg(p.chunk + t))
-#define TINFO __ldg(p.tinfo + t)
-  for (int i = 0; i < CNT; ++i) *acc_at(sacc, gacc, qs, i, TT, t) = T(0);
+  const int cnt = __ldg(p.chunk + t + 1) - __ldg(p.chunk + t);
+  for (int i = 0; i < cnt; ++i) *acc_at(sacc, gacc, qs, i, TT, t) = T(0);
   __syncthreads();
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
   const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + 128, g.log2N - 7,
@@ -315,14 +398,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     const uint32_t tm = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 128 * kTcGroupCols);
     fs.tc.bind(t, (uint32_t)__cvta_generic_to_shared(smem_raw), tm, p.tc_no_commit != 0);
   }
-  auto load_rows = [&](const cplx<T>* src, cplx<T> (&v)[16]) {
-    const unsigned rmask = (unsigned)TINFO & 0xffu;  // rows t + m*TT (m < 8) holding cells
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = (rmask >> m) & 1u ? src[rowslot(t + m * TT)] : cplx<T>{T(0), T(0)};
-#pragma unroll
-    for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
-  };
-
+  const ColSmem<T> sm{sA, sF, sS, carry};
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
     // the previous column's gather has finished reading sA; with tensor-core
     // stages the CTA also stops after a device wait that gave up
@@ -331,58 +407,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     } else {
       __syncthreads();
     }
-    if constexpr (ACCREG) {
-      sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
-      __syncthreads();
-      if (p.has_carry) {
-        add_carries<T, NF, -1>(p, g, CNT, TINFO >> 8, sA, sF, carry);
-        __syncthreads();
-      }
-      cplx<T> y[16];
-#pragma unroll 1
-      for (int f = 0; f < NF; ++f) {
-        cplx<T> v[16];
-        load_rows(f == 0 ? sA : sF + (size_t)(f - 1) * n, v);
-        __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
-        load_spectrum(p, g, f, kx, sS);
-        fs.template forward<true>(v);
-        spectrum_ready();
-        const SpecAddr sa = spec_addr(fs, g);
-        if (f == 0) spectral_multiply<T, false>(sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
-        else spectral_multiply<T, true>(sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
-      }
-      fs.inverse(y);
-#pragma unroll
-      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
-      __syncthreads();
-      gather_cells(p, g, kx, CNT, sA, tw, sacc, gacc, qs, twc);
-    } else {
-#pragma unroll 1
-      for (int f = 0; f < NF; ++f) {
-        if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
-        if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
-        else if (f == 0) sparse_rows<T, NF, 0>(p, g, kx, CNT, sA, sF, carry, tw, twc);
-        else if (f == 1) sparse_rows<T, NF, 1>(p, g, kx, CNT, sA, sF, carry, tw, twc);
-        else sparse_rows<T, NF, 2>(p, g, kx, CNT, sA, sF, carry, tw, twc);
-        __syncthreads();
-        if (p.has_carry) {
-          add_carries<T, NF, 0>(p, g, CNT, TINFO >> 8, sA, sF, carry);
-          __syncthreads();
-        }
-        cplx<T> v[16];
-        load_rows(sA, v);
-        __syncthreads();
-        load_spectrum(p, g, f, kx, sS);
-        fs.template forward<true>(v);
-        spectrum_ready();
-        spectral_multiply<T, false>(sS, spec_addr(fs, g), imag_of(p, f) != 0, oddy_of(p, f) != 0, v, v);
-        fs.inverse(v);
-#pragma unroll
-        for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = v[m];
-        __syncthreads();
-        gather_cells(p, g, kx, CNT, sA, tw, sacc, gacc, qs, twc);
-      }
-    }
+    col2d_column<T, NF, ACCREG, TTC, TCK>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc);
   }
   if constexpr (TCK > 0) {
     if (fs.tc.failed) {
@@ -391,10 +416,63 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     }
     tc_teardown(fs.tc.tmem - (uint32_t)(kTcGroupCols * (t >> 7)), TTC / 128 * kTcGroupCols);
   }
-  for (int i = 0; i < CNT && i < qs; ++i) gacc[(size_t)i * TT + t] = sacc[(size_t)i * TT + t];
-#undef C0
-#undef CNT
-#undef TINFO
+  for (int i = 0; i < cnt && i < qs; ++i) gacc[(size_t)i * TT + t] = sacc[(size_t)i * TT + t];
+}
+
+// Grouped launch: the plans of a batch that share the grid (same N and thread
+// count) in one persistent launch.  The P (n + 1) columns of the group are
+// split into gridDim.x contiguous ranges, one per CTA; a CTA walks the plans
+// its range touches, for each one zeroing its accumulators, running its
+// columns and flushing them into the plan's partial sums at row
+// blockIdx.x - c0[plan] (c0: the first CTA whose range reaches the plan, so
+// the plan's reduction sums the rows of the CTAs that touched it).  Every plan
+// passed here has the same n, TT and field count as the launch.
+template <typename T, int NF, bool ACCREG, int TTC>
+__global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::blocks)
+    k_col2d_group(const Col2Dv2Params<T>* __restrict__ plans, const int* __restrict__ c0, int nplans) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Col2Dv2Params<T>& p0 = plans[0];
+  const ColDims<TTC> g(p0);
+  const int t = threadIdx.x, TT = g.TT, W = TT >> 5;
+  const int N = g.N, n = g.n;
+  const int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
+  const int ntab = fstab_entries(TT);
+  cplx<T>* sA = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* stab = sA + nbuf;
+  T* sS = reinterpret_cast<T*>(stab + ntab);
+  cplx<T>* carry = reinterpret_cast<cplx<T>*>(sS);
+  cplx<T>* sF = reinterpret_cast<cplx<T>*>(sS + sspec_entries(n));
+  T* sacc = reinterpret_cast<T*>(sF + (ACCREG ? (NF - 1) * n : 0));
+  for (int i = t; i < ntab; i += TT) stab[i] = p0.fstab[i];  // tables depend on N and TT only
+  __syncthreads();
+  const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
+  const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + 128, g.log2N - 7,
+                         (T)(6.283185307179586476925 / (double)N)};
+  FourStep<T, 0> fs;
+  fs.init(t, TT, sA, ftab);
+  const ColSmem<T> sm{sA, sF, sS, carry};
+  const int64_t C = (int64_t)nplans * (n + 1);
+  const int64_t lo = (int64_t)blockIdx.x * C / gridDim.x, hi = ((int64_t)blockIdx.x + 1) * C / gridDim.x;
+  for (int64_t c = lo; c < hi;) {
+    const int pi = (int)(c / (n + 1));
+    const Col2Dv2Params<T>& p = plans[pi];
+    const int k0 = (int)(c - (int64_t)pi * (n + 1));
+    const int k1 = (int)std::min<int64_t>(hi - (int64_t)pi * (n + 1), n + 1);
+    const int slot = blockIdx.x - c0[pi];
+    T* gacc = p.partial + (size_t)slot * p.npos;
+    cplx<T>* twc = p.twc ? p.twc + (size_t)slot * p.npos : nullptr;
+    const int qs = p.acc_rows;
+    const int cnt = __ldg(p.chunk + t + 1) - __ldg(p.chunk + t);
+    __syncthreads();  // the previous plan's accumulators have been flushed
+    for (int i = 0; i < cnt; ++i) *acc_at(sacc, gacc, qs, i, TT, t) = T(0);
+    for (int kx = k0; kx < k1; ++kx) {
+      __syncthreads();
+      col2d_column<T, NF, ACCREG, TTC, 0>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc);
+    }
+    __syncthreads();
+    for (int i = 0; i < cnt && i < qs; ++i) gacc[(size_t)i * TT + t] = sacc[(size_t)i * TT + t];
+    c = (int64_t)(pi + 1) * (n + 1);
+  }
 }
 
 template <typename T, int TTC>
@@ -412,6 +490,36 @@ cudaError_t Col2DKernels<T, TTC>::configure(size_t smem, int threads, int* block
       cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_v2<T, 3, R, TTC>, threads, smem)) !=
+      cudaSuccess)
+    return e;
+  *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));
+  return cudaSuccess;
+}
+
+template <typename T, int TTC>
+void Col2DKernels<T, TTC>::launch_group(int nf, int grid, int threads, size_t smem, cudaStream_t st,
+                                        const Col2Dv2Params<T>* plans, const int* c0, int nplans) {
+  constexpr bool R = std::is_same<T, float>::value;
+  if (nf == 1) k_col2d_group<T, 1, false, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
+  else if (nf == 2) k_col2d_group<T, 2, R, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
+  else k_col2d_group<T, 3, R, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
+}
+
+template <typename T, int TTC>
+cudaError_t Col2DKernels<T, TTC>::configure_group(size_t smem, int threads, int* blocks_per_sm) {
+  constexpr bool R = std::is_same<T, float>::value;
+  int b[3] = {0, 0, 0};
+  cudaError_t e;
+  if ((e = allow_optin_smem(k_col2d_group<T, 1, false, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_group<T, 2, R, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_group<T, 3, R, TTC>)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_group<T, 1, false, TTC>, threads, smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_group<T, 2, R, TTC>, threads, smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_group<T, 3, R, TTC>, threads, smem)) !=
       cudaSuccess)
     return e;
   *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));

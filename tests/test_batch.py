@@ -18,13 +18,20 @@ def torch_cuda():
     return torch
 
 
+@pytest.mark.parametrize("grouped", [False, True])
 @pytest.mark.parametrize("layer", ["single", "system"])
-def test_batch_equals_individual_applies(torch_cuda, layer):
+def test_batch_equals_individual_applies(torch_cuda, layer, grouped):
+    """Every segment of a batched apply equals the plan's own apply: bit for
+    bit when each plan is applied on its own; with grouped launches (FP32
+    four-step plans of a grid size share one persistent launch, so the columns
+    are split over the CTAs differently) to FP32 rounding, and the same on
+    every replay."""
     torch = torch_cuda
     from paper_1809_00845_gb300.bem import Batch, Plan
     rng = np.random.default_rng(42)
     plans, bounds = [], []
-    for k, n in enumerate((64, 128, 256, 512, 512, 1024, 256, 2048)):
+    sizes = (64, 128, 256, 512, 512, 1024, 256, 2048)
+    for k, n in enumerate(sizes):
         b = I.curve_boundary(n, I.random_star_curve(rng))
         p = Plan.from_boundary(b, "laplace2d", "f32")
         if layer == "system":
@@ -32,19 +39,35 @@ def test_batch_equals_individual_applies(torch_cuda, layer):
         plans.append(p)
         bounds.append(b)
     batch = Batch(plans, layer, streams=4)
-    assert batch.launches == 3 * len(plans)
+    batch.set_grouping(grouped)
+    if grouped:
+        # four-step plans (n >= 256) of one size share a launch: preps, one column launch, reductions
+        counts = {n: sizes.count(n) for n in set(sizes) if n >= 256}
+        expect = sum(2 * c + 1 if c > 1 else 3 * c for c in counts.values()) + 3 * sum(n < 256 for n in sizes)
+        assert batch.launches == expect
+    else:
+        assert batch.launches == 3 * len(plans)
     src = torch.from_numpy(rng.standard_normal(batch.total).astype(np.float32)).cuda()
     raw_in = _as_tensor(torch, batch.d_in, batch.total)
     raw_out = _as_tensor(torch, batch.d_out, batch.total)
     raw_in.copy_(src)
+    first = None
     for _ in range(2):
         batch.apply()
         torch.cuda.synchronize()
+        if first is None:
+            first = raw_out.clone()
+        else:
+            assert torch.equal(raw_out, first)
         for p, off in zip(plans, batch.offsets):
             seg = src[off:off + p.nb].contiguous()
             ref = p.apply(layer, seg)
             torch.cuda.synchronize()
-            assert torch.equal(raw_out[off:off + p.nb], ref)
+            if grouped:
+                got = raw_out[off:off + p.nb].double()
+                assert float(torch.linalg.norm(got - ref.double()) / torch.linalg.norm(ref.double())) <= 1e-6
+            else:
+                assert torch.equal(raw_out[off:off + p.nb], ref)
     batch.close()
 
 
