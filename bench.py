@@ -464,17 +464,24 @@ def secondary_configs(dev):
         plans.append(Plan.from_boundary(I.curve_boundary(n, I.random_star_curve(rng)), "laplace2d", "f32"))
     batch = Batch(plans, "single", streams=4)
     tuned_streams = batch.tune(reps=10)
-    for _ in range(3):
-        batch.apply()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 20
-    e0.record()
-    for _ in range(reps):
-        batch.apply()
-    e1.record()
-    torch.cuda.synchronize()
-    graph_ms = e0.elapsed_time(e1) / reps
+
+    def time_batch():
+        for _ in range(3):
+            batch.apply()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            batch.apply()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    batch.set_grouping(False)
+    ungrouped_ms = time_batch()
+    ungrouped_launches = batch.launches
+    batch.set_grouping(True)
+    graph_ms = time_batch()
     xs = [torch.randn(p.nb, dtype=torch.float32, device=dev) for p in plans]
     ys = [torch.empty_like(x) for x in xs]
     for p, x, y in zip(plans, xs, ys):
@@ -490,6 +497,8 @@ def secondary_configs(dev):
     out["batched_stars_64_f32"] = {"geometries": 64, "cells": int(sum(p.nb for p in plans)),
                                    "graph_ms_per_batch": graph_ms, "graph_applies_per_s": 64e3 / graph_ms,
                                    "loop_ms_per_batch": loop_ms, "kernel_launches_per_batch": batch.launches,
+                                   "graph_one_launch_per_plan_ms": ungrouped_ms,
+                                   "kernel_launches_one_per_plan": ungrouped_launches,
                                    "capture_streams_tuned": tuned_streams}
     batch.close()
     for p in plans:
