@@ -525,7 +525,15 @@ static void launch_tc(const bem_plan_s* p, int nf, const Col2Dv2Params<float>& c
 
 template <typename T>
 static cudaError_t configure_col2d(int TT, int tc, size_t smem, int* bps) {
-  if constexpr (std::is_same<T, float>::value) {
+  if constexpr (std::is_same<T, f32x2>::value) {
+    switch (TT) {
+      case 512: return Col2DKernels<f32x2, 512>::configure(smem, TT, bps);
+      case 256: return Col2DKernels<f32x2, 256>::configure(smem, TT, bps);
+      case 128: return Col2DKernels<f32x2, 128>::configure(smem, TT, bps);
+      case 64: return Col2DKernels<f32x2, 64>::configure(smem, TT, bps);
+      default: return Col2DKernels<f32x2, 0>::configure(smem, TT, bps);
+    }
+  } else if constexpr (std::is_same<T, float>::value) {
     if (tc == kTcBf16) return configure_tc<kTcBf16>(TT, smem, bps);
     if (tc == kTcF16) return configure_tc<kTcF16>(TT, smem, bps);
     switch (TT) {
@@ -543,7 +551,15 @@ static cudaError_t configure_col2d(int TT, int tc, size_t smem, int* bps) {
 template <typename T>
 static void launch_col2d(const bem_plan_s* p, int nf, const Col2Dv2Params<T>& cp, cudaStream_t st) {
   const int TT = p->threads;
-  if constexpr (std::is_same<T, float>::value) {
+  if constexpr (std::is_same<T, f32x2>::value) {
+    switch (TT) {
+      case 512: Col2DKernels<f32x2, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 256: Col2DKernels<f32x2, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 128: Col2DKernels<f32x2, 128>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 64: Col2DKernels<f32x2, 64>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      default: Col2DKernels<f32x2, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+    }
+  } else if constexpr (std::is_same<T, float>::value) {
     if (p->tc == kTcBf16) return launch_tc<kTcBf16>(p, nf, cp, st);
     if (p->tc == kTcF16) return launch_tc<kTcF16>(p, nf, cp, st);
     switch (TT) {
@@ -878,11 +894,11 @@ void group_free(BatchGroup& g) {
 // from the per-plan kernels')
 static cudaError_t group_configure(int TT, size_t smem, int* bps) {
   switch (TT) {
-    case 512: return Col2DKernels<float, 512>::configure_group(smem, TT, bps);
-    case 256: return Col2DKernels<float, 256>::configure_group(smem, TT, bps);
-    case 128: return Col2DKernels<float, 128>::configure_group(smem, TT, bps);
-    case 64: return Col2DKernels<float, 64>::configure_group(smem, TT, bps);
-    default: return Col2DKernels<float, 32>::configure_group(smem, TT, bps);
+    case 512: return Col2DGroupKernels<512>::configure(smem, TT, bps);
+    case 256: return Col2DGroupKernels<256>::configure(smem, TT, bps);
+    case 128: return Col2DGroupKernels<128>::configure(smem, TT, bps);
+    case 64: return Col2DGroupKernels<64>::configure(smem, TT, bps);
+    default: return Col2DGroupKernels<32>::configure(smem, TT, bps);
   }
 }
 
@@ -959,11 +975,11 @@ bem_status group_issue(const BatchGroup& g, const std::vector<bem_plan_s*>& plan
   }
   const auto* dp = static_cast<const Col2Dv2Params<float>*>(g.d_params);
   switch (g.threads) {
-    case 512: Col2DKernels<float, 512>::launch_group(g.nf, g.grid, 512, g.smem, st, dp, g.d_c0, P); break;
-    case 256: Col2DKernels<float, 256>::launch_group(g.nf, g.grid, 256, g.smem, st, dp, g.d_c0, P); break;
-    case 128: Col2DKernels<float, 128>::launch_group(g.nf, g.grid, 128, g.smem, st, dp, g.d_c0, P); break;
-    case 64: Col2DKernels<float, 64>::launch_group(g.nf, g.grid, 64, g.smem, st, dp, g.d_c0, P); break;
-    default: Col2DKernels<float, 32>::launch_group(g.nf, g.grid, 32, g.smem, st, dp, g.d_c0, P); break;
+    case 512: Col2DGroupKernels<512>::launch(g.nf, g.grid, 512, g.smem, st, dp, g.d_c0, P); break;
+    case 256: Col2DGroupKernels<256>::launch(g.nf, g.grid, 256, g.smem, st, dp, g.d_c0, P); break;
+    case 128: Col2DGroupKernels<128>::launch(g.nf, g.grid, 128, g.smem, st, dp, g.d_c0, P); break;
+    case 64: Col2DGroupKernels<64>::launch(g.nf, g.grid, 64, g.smem, st, dp, g.d_c0, P); break;
+    default: Col2DGroupKernels<32>::launch(g.nf, g.grid, 32, g.smem, st, dp, g.d_c0, P); break;
   }
   for (int m = 0; m < P; ++m) {
     const bem_plan_s* p = plans[g.members[m]];

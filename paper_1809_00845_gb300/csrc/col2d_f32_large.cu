@@ -4,4 +4,6 @@
 namespace bemfft {
 template struct Col2DKernels<float, 512>;
 template struct Col2DKernels<float, 256>;
+template struct Col2DGroupKernels<512>;
+template struct Col2DGroupKernels<256>;
 }  // namespace bemfft

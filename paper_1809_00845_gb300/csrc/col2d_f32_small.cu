@@ -5,4 +5,7 @@ namespace bemfft {
 template struct Col2DKernels<float, 128>;
 template struct Col2DKernels<float, 64>;
 template struct Col2DKernels<float, 32>;
+template struct Col2DGroupKernels<128>;
+template struct Col2DGroupKernels<64>;
+template struct Col2DGroupKernels<32>;
 }  // namespace bemfft

@@ -496,31 +496,29 @@ cudaError_t Col2DKernels<T, TTC>::configure(size_t smem, int threads, int* block
   return cudaSuccess;
 }
 
-template <typename T, int TTC>
-void Col2DKernels<T, TTC>::launch_group(int nf, int grid, int threads, size_t smem, cudaStream_t st,
-                                        const Col2Dv2Params<T>* plans, const int* c0, int nplans) {
-  constexpr bool R = std::is_same<T, float>::value;
-  if (nf == 1) k_col2d_group<T, 1, false, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
-  else if (nf == 2) k_col2d_group<T, 2, R, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
-  else k_col2d_group<T, 3, R, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
+template <int TTC>
+void Col2DGroupKernels<TTC>::launch(int nf, int grid, int threads, size_t smem, cudaStream_t st,
+                                    const Col2Dv2Params<float>* plans, const int* c0, int nplans) {
+  if (nf == 1) k_col2d_group<float, 1, false, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
+  else if (nf == 2) k_col2d_group<float, 2, true, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
+  else k_col2d_group<float, 3, true, TTC><<<grid, threads, smem, st>>>(plans, c0, nplans);
 }
 
-template <typename T, int TTC>
-cudaError_t Col2DKernels<T, TTC>::configure_group(size_t smem, int threads, int* blocks_per_sm) {
-  constexpr bool R = std::is_same<T, float>::value;
+template <int TTC>
+cudaError_t Col2DGroupKernels<TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
   int b[3] = {0, 0, 0};
   cudaError_t e;
-  if ((e = allow_optin_smem(k_col2d_group<T, 1, false, TTC>)) != cudaSuccess) return e;
-  if ((e = allow_optin_smem(k_col2d_group<T, 2, R, TTC>)) != cudaSuccess) return e;
-  if ((e = allow_optin_smem(k_col2d_group<T, 3, R, TTC>)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_group<T, 1, false, TTC>, threads, smem)) !=
-      cudaSuccess)
+  if ((e = allow_optin_smem(k_col2d_group<float, 1, false, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_group<float, 2, true, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_col2d_group<float, 3, true, TTC>)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_group<float, 1, false, TTC>, threads,
+                                                         smem)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_group<T, 2, R, TTC>, threads, smem)) !=
-      cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_group<float, 2, true, TTC>, threads,
+                                                         smem)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_group<T, 3, R, TTC>, threads, smem)) !=
-      cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_group<float, 3, true, TTC>, threads,
+                                                         smem)) != cudaSuccess)
     return e;
   *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));
   return cudaSuccess;

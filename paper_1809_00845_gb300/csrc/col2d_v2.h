@@ -58,11 +58,15 @@ template <typename T, int TTC>
 struct Col2DKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
   static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
-  // one persistent launch over the columns of several plans of the same grid
-  // (device arrays: plans[nplans] parameters, c0[nplans] first CTA per plan)
-  static cudaError_t configure_group(size_t smem, int threads, int* blocks_per_sm);
-  static void launch_group(int nf, int grid, int threads, size_t smem, cudaStream_t st,
-                           const Col2Dv2Params<T>* plans, const int* c0, int nplans);
+};
+
+// One persistent launch over the columns of several FP32 plans of the same
+// grid (device arrays: plans[nplans] parameters, c0[nplans] first CTA per plan)
+template <int TTC>
+struct Col2DGroupKernels {
+  static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
+  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<float>* plans,
+                     const int* c0, int nplans);
 };
 
 // The same kernels in FP32 with the radix-16 stages of the transforms on the
