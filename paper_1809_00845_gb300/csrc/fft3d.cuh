@@ -139,21 +139,46 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
   __syncthreads();
   const cplx<T>* tw = sq;
   const Tw64<T> t64{stw, stw + NHI};
-  // x-DFT of the lines (y = t + m*TT, z = z0 + g) from the cells of each line
+  // x-DFT of the lines (y = t + m*TT, z = z0 + g) from the cells of each line.
+  // The bounds of all eight lines are read first, then the first CB3 cells of
+  // every line with their loads issued together (a line holds a handful of
+  // cells); longer lines finish in a loop.
+  constexpr int CB3 = 4;
   const T* vf = val + (size_t)f * nb;
   cplx<T> v[16];
+  int j0[8], j1[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int line = (z0 + g) * n + t + m * TT;
-    const int j0 = __ldg(lptr + line), j1 = __ldg(lptr + line + 1);
-    cplx<T> s = {T(0), T(0)};
-    for (int j = j0; j < j1; ++j) {
-      const cplx<T> w = t64.template get<-1>((kx * (int)__ldg(xs + j)) & (N - 1));
-      const T r = vf[j];
-      s.x += r * w.x;
-      s.y += r * w.y;
+    j0[m] = __ldg(lptr + line);
+    j1[m] = __ldg(lptr + line + 1);
+    v[m] = {T(0), T(0)};
+  }
+#pragma unroll
+  for (int c = 0; c < CB3; ++c) {
+    int xv[8];
+    T rv[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int j = j0[m] + c < j1[m] ? j0[m] + c : 0;  // index 0 exists: nb >= 1
+      xv[m] = (int)__ldg(xs + j);
+      rv[m] = j0[m] + c < j1[m] ? __ldg(vf + j) : T(0);
     }
-    v[m] = s;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const cplx<T> w = t64.template get<-1>((kx * xv[m]) & (N - 1));
+      v[m].x += rv[m] * w.x;
+      v[m].y += rv[m] * w.y;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    for (int j = j0[m] + CB3; j < j1[m]; ++j) {
+      const cplx<T> w = t64.template get<-1>((kx * (int)__ldg(xs + j)) & (N - 1));
+      const T r = __ldg(vf + j);
+      v[m].x += r * w.x;
+      v[m].y += r * w.y;
+    }
   }
 #pragma unroll
   for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
@@ -283,9 +308,22 @@ __global__ void __launch_bounds__(512) k3_yinv(const cplx<T>* __restrict__ B, cp
   for (int i = threadIdx.x; i < PassTab<LOG2N>::size(); i += blockDim.x) sq[i] = qtab[i];
   const cplx<T>* src = B + ((size_t)o * (n + 1) + kx) * (size_t)N * n + z0;
   cplx<T>* tile = sbuf;
-  for (int i = threadIdx.x; i < N * ZB; i += blockDim.x) {
+  // the block is ZB * TT threads: a compile-time trip count puts every load of
+  // the tile in flight at once (one load at a time left the pass latency-bound)
+  constexpr int THREADS = ZB * TT, PER = N * ZB / THREADS;
+  static_assert(N * ZB % THREADS == 0, "tile / threads");
+  cplx<T> ld[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = threadIdx.x + j * THREADS;
     const int ky = i / ZB, zz = i - ky * ZB;
-    tile[(size_t)ky * (ZB + 1) + zz] = src[(size_t)ky * n + zz];
+    ld[j] = src[(size_t)ky * n + zz];
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = threadIdx.x + j * THREADS;
+    const int ky = i / ZB, zz = i - ky * ZB;
+    tile[(size_t)ky * (ZB + 1) + zz] = ld[j];
   }
   __syncthreads();
   const cplx<T>* tw = sq;
