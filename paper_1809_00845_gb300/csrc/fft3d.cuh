@@ -26,6 +26,11 @@
 
 namespace bemfft {
 
+// cells per line whose loads the y-forward pass issues together
+#ifndef FFT3D_CELL_BATCH
+#define FFT3D_CELL_BATCH 2
+#endif
+
 // e^{DIR 2 pi i m / N}, m = 64 hi + lo (tables hi: max(1, N/64), lo: 64)
 template <typename T>
 struct Tw64 {
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
   // The bounds of all eight lines are read first, then the first CB3 cells of
   // every line with their loads issued together (a line holds a handful of
   // cells); longer lines finish in a loop.
-  constexpr int CB3 = 4;
+  constexpr int CB3 = FFT3D_CELL_BATCH;
   const T* vf = val + (size_t)f * nb;
   cplx<T> v[16];
   int j0[8], j1[8];
