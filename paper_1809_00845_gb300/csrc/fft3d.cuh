@@ -26,11 +26,6 @@
 
 namespace bemfft {
 
-// cells per line whose loads the y-forward pass issues together
-#ifndef FFT3D_CELL_BATCH
-#define FFT3D_CELL_BATCH 2
-#endif
-
 // e^{DIR 2 pi i m / N}, m = 64 hi + lo (tables hi: max(1, N/64), lo: 64)
 template <typename T>
 struct Tw64 {
@@ -144,11 +139,10 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
   __syncthreads();
   const cplx<T>* tw = sq;
   const Tw64<T> t64{stw, stw + NHI};
-  // x-DFT of the lines (y = t + m*TT, z = z0 + g) from the cells of each line.
-  // The bounds of all eight lines are read first, then the first CB3 cells of
-  // every line with their loads issued together (a line holds a handful of
-  // cells); longer lines finish in a loop.
-  constexpr int CB3 = FFT3D_CELL_BATCH;
+  // x-DFT of the lines (y = t + m*TT, z = z0 + g) from the cells of each line;
+  // the bounds of all eight lines are read first.  (Issuing the first cells of
+  // every line together was measured slower: the twiddles of the many empty
+  // slots cost more than the latency they hide.)
   const T* vf = val + (size_t)f * nb;
   cplx<T> v[16];
   int j0[8], j1[8];
@@ -157,33 +151,17 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
     const int line = (z0 + g) * n + t + m * TT;
     j0[m] = __ldg(lptr + line);
     j1[m] = __ldg(lptr + line + 1);
-    v[m] = {T(0), T(0)};
-  }
-#pragma unroll
-  for (int c = 0; c < CB3; ++c) {
-    int xv[8];
-    T rv[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int j = j0[m] + c < j1[m] ? j0[m] + c : 0;  // index 0 exists: nb >= 1
-      xv[m] = (int)__ldg(xs + j);
-      rv[m] = j0[m] + c < j1[m] ? __ldg(vf + j) : T(0);
-    }
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const cplx<T> w = t64.template get<-1>((kx * xv[m]) & (N - 1));
-      v[m].x += rv[m] * w.x;
-      v[m].y += rv[m] * w.y;
-    }
   }
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    for (int j = j0[m] + CB3; j < j1[m]; ++j) {
+    cplx<T> sum = {T(0), T(0)};
+    for (int j = j0[m]; j < j1[m]; ++j) {
       const cplx<T> w = t64.template get<-1>((kx * (int)__ldg(xs + j)) & (N - 1));
       const T r = __ldg(vf + j);
-      v[m].x += r * w.x;
-      v[m].y += r * w.y;
+      sum.x += r * w.x;
+      sum.y += r * w.y;
     }
+    v[m] = sum;
   }
 #pragma unroll
   for (int m = 8; m < 16; ++m) v[m] = {T(0), T(0)};
