@@ -293,9 +293,11 @@ bem_status bem_set_test_flags(bem_plan_t plan, uint32_t flags);
  * then replays the whole batch with one graph launch.  Inputs and outputs are
  * two packed device buffers owned by the batch (plan i's nb_i*ncomp_i values at
  * element offset bem_batch_offset(i)), so the captured pointers stay valid.
- * The plans must outlive the batch; when bem_set_bc changes a plan's system
- * operator, the next bem_batch_apply captures the graph again.  The plans'
- * kernel timing is switched off. */
+ * The plans must outlive the batch and be distinct (a plan listed twice
+ * returns BEM_ERR_ARG); when bem_set_bc changes a plan's system operator, the
+ * next bem_batch_apply captures the graph again.  The plans' kernel timing is
+ * switched off.  FP32 four-step plans of one grid size are applied by one
+ * grouped launch (bem_batch_set_grouping). */
 typedef struct bem_batch_s* bem_batch_t;
 bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count, bem_layer layer, int streams,
                             void* stream);

@@ -161,6 +161,11 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
       set_error("bem_batch_create: null plan");
       return BEM_ERR_ARG;
     }
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == plans[i]) {
+        set_error("bem_batch_create: a plan appears twice (its scratch would be shared by two applies)");
+        return BEM_ERR_ARG;
+      }
     if (plans[i]->prec != plans[0]->prec) {
       set_error("bem_batch_create: all plans must share one precision");
       return BEM_ERR_ARG;
