@@ -195,8 +195,10 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
     set_error("bem_batch_create: out of device memory");
     return fail(BEM_ERR_OOM);
   }
-  cudaMemset(b->d_in, 0, b->total * tb);
-  cudaMemset(b->d_out, 0, b->total * tb);
+  if (cudaMemset(b->d_in, 0, b->total * tb) != cudaSuccess || cudaMemset(b->d_out, 0, b->total * tb) != cudaSuccess) {
+    set_error("bem_batch_create: clearing the batch buffers failed");
+    return fail(BEM_ERR_CUDA);
+  }
   for (int s = 0; s < streams; ++s) {
     cudaStream_t x;
     if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {

@@ -306,9 +306,12 @@ bem_status bem_net_create(bem_net_t* out, int cin, int hidden, int layers, int k
     set_error("bem_net_create: out of device memory");
     return fail(BEM_ERR_OOM);
   }
-  cudaMemcpy(net->d_w, w.data(), off * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemset(net->d_m, 0, off * sizeof(float));
-  cudaMemset(net->d_v, 0, off * sizeof(float));
+  if (cudaMemcpy(net->d_w, w.data(), off * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(net->d_m, 0, off * sizeof(float)) != cudaSuccess ||
+      cudaMemset(net->d_v, 0, off * sizeof(float)) != cudaSuccess) {
+    set_error("bem_net_create: initialising the parameters on the device failed");
+    return fail(BEM_ERR_CUDA);
+  }
   *out = net;
   return BEM_OK;
 }
@@ -347,8 +350,8 @@ bem_status bem_net_set_params(bem_net_t net, const float* host) {
     return BEM_ERR_ARG;
   }
   BEM_CUDA_TRY(cudaMemcpy(net->d_w, host, net->nparams * sizeof(float), cudaMemcpyHostToDevice));
-  cudaMemset(net->d_m, 0, net->nparams * sizeof(float));
-  cudaMemset(net->d_v, 0, net->nparams * sizeof(float));
+  BEM_CUDA_TRY(cudaMemset(net->d_m, 0, net->nparams * sizeof(float)));
+  BEM_CUDA_TRY(cudaMemset(net->d_v, 0, net->nparams * sizeof(float)));
   net->step = 0;
   return BEM_OK;
 }
