@@ -146,3 +146,27 @@ def test_accelerated_error_falls_with_stencil_order_and_radius():
             assert np.linalg.norm(xn - xe) / np.linalg.norm(xe) > 3 * errs[(3, 3)]
     assert errs[(2, 2)] < 1e-2
     assert errs[(3, 3)] < errs[(2, 2)] and errs[(3, 5)] < errs[(3, 3)]
+
+
+@pytest.mark.parametrize("curve", [I.circle_curve(0.35), I.star_curve(0.3, 0.3, 5)])
+def test_curve_panels_close_the_curve_with_equal_arclength_and_outward_normals(curve):
+    """The accuracy mode's input recipe: the panels form a closed polygon whose
+    vertices lie on the curve at (nearly) equal arclength spacing, about h
+    long, numbered counter-clockwise so that the normals point outward."""
+    n = 256
+    b = I.curve_panels(n, curve)
+    P = b.panels
+    assert np.array_equal(P[:, 2:4], np.roll(P[:, 0:2], -1, axis=0))  # closed, consecutive
+    L = b.length
+    assert abs(L.mean() * n - 1.0) < 0.05 and L.std() / L.mean() < 0.05
+    # vertices on the curve
+    pv, _ = curve(b.param)
+    assert np.max(np.abs(pv - P[:, 0:2])) < 1e-12
+    # outward: the normal points away from the centre for these star-shaped curves
+    out = np.sum(b.normal * (b.mid - 0.5), axis=1)
+    assert np.all(out > 0)
+    # the polygon's length approaches the curve's (chords of length ~h)
+    t = np.linspace(0, 2 * np.pi, 200001)
+    _, dp = curve(t)
+    length = np.trapezoid(np.hypot(dp[:, 0], dp[:, 1]), t)
+    assert 0 < length - L.sum() < 1e-4 * length
