@@ -412,13 +412,25 @@ def accuracy_mode(dev, n=4096, order=3, R=5):
     u_out, q_out, info = p.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
     xs = np.where(bc == 0, q_out, u_out)
     truth = np.where(bc == 0, q, u)
-    res = {"panels": b.nb, "order": order, "near_radius": R,
+    res = {"panels": b.nb, "order": order, "near_radius": R, "grid_nodes": p.info()["grid_nodes"],
            "system_apply_ms": ms, "node_convolution_kernel_us": 1e3 * col_ms / max(1, col_n),
            "plan_s": p.info()["plan_seconds"],
            "solve_1e-6": {"seconds": info["seconds"], "iters": info["iters"], "status": info["status"],
                           "rel_residual": info["rel_residual"], "refine_steps": info["refine_steps"]},
            "rel_error_vs_analytic": float(np.linalg.norm(xs - truth) / np.linalg.norm(truth))}
     p.close()
+    # a cheaper setting (order 2, R = 3): fewer active nodes, larger far-field error
+    p2 = Plan.from_panel_boundary(b, "f32", 2, 3)
+    p2.set_bc(bc, 0.5)
+    ms2 = _time_applies(p2, "system", x, 100)
+    p2.enable_refinement(True)
+    p2.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+    u2, q2, info2 = p2.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
+    x2 = np.where(bc == 0, q2, u2)
+    res["order2_R3"] = {"system_apply_ms": ms2, "grid_nodes": p2.info()["grid_nodes"],
+                        "solve_1e-6_s": info2["seconds"], "iters": info2["iters"], "status": info2["status"],
+                        "rel_error_vs_analytic": float(np.linalg.norm(x2 - truth) / np.linalg.norm(truth))}
+    p2.close()
     # the paper-form operator (sources and targets on grid nodes) on the same field and conditions
     bg = I.star_boundary(n)
     ug, qg = I.boundary_data(bg, I.field_expcos)
