@@ -305,3 +305,56 @@ def interior_potential(x, panels, q, u):
     """Representation formula at interior points x (m, 2): u(x) = S q + D u
     (c = 1 inside), panel integrals evaluated exactly."""
     return panel_single(x, panels) @ q + panel_double(x, panels) @ u
+
+
+def accelerated_rows(panels, h, order, R, x, rows, layer, bc=None, c=0.5):
+    """Rows `rows` of the accelerated operator applied to x, for grids too large
+    for the dense matrices: (A x)_i = sum_s L_s(m_i) sum_l U_grid(x_s - x_l) rho_l
+    (rho = the projection of x, all panels) plus, for the near pairs, the exact
+    integral minus the grid-mediated value of the pair, plus the double layer's
+    row-sum term (module docstring).  layer: "single", "double" or "system"
+    (with bc: 0 = the column carries the flux through S, 1 = the potential
+    through D, minus c on the diagonal)."""
+    P = np.asarray(panels, np.float64)
+    x = np.asarray(x, np.float64)
+    rows = np.asarray(rows)
+    m, _, _, _ = panel_geometry(P)
+    idx, PSw, PDw = projection_weights(P, h, order)
+    _, W, _ = stencils(m, h, order)
+    nb, S = W.shape
+    keys = idx[..., 1] * (1 << 32) + idx[..., 0]
+    nodes, inv = np.unique(keys.ravel(), return_inverse=True)
+    inv = inv.reshape(nb, S)
+    nk = np.stack([nodes % (1 << 32), nodes // (1 << 32)], axis=1)
+    bc = np.zeros(nb, np.uint8) if bc is None else np.asarray(bc)
+    if layer == "single":
+        dip = np.zeros(nb, bool)
+    elif layer == "double":
+        dip = np.ones(nb, bool)
+    else:
+        dip = bc == 1
+    Pw = np.where(dip[:, None], PDw, PSw)
+    rho = np.zeros(nodes.size)
+    np.add.at(rho, inv.ravel(), (Pw * x[:, None]).ravel())
+    rho1 = np.zeros(nodes.size)  # the double layer of x = 1, for its row-sum term
+    np.add.at(rho1, inv.ravel(), PDw.ravel())
+    a = anchors(m, h, order)
+    out = np.zeros(rows.size)
+    for r, i in enumerate(rows):
+        Gi = grid_kernel(nk[inv[i]][:, None, :] - nk[None, :, :], h)  # (S, nodes)
+        far = W[i] @ (Gi @ rho)
+        near = np.nonzero(np.abs(a - a[i]).max(axis=1) <= R)[0]
+        ex_s = panel_single(m[i:i + 1], P[near])[0]
+        ex_d = panel_double(m[i:i + 1], P[near])[0]
+        # grid-mediated value of each near pair: sum_s W_is sum_t U(x_s - x_t) P_jt
+        cols = inv[near]  # (k, S) node indices of the sources' stencils
+        Gn = Gi[:, cols]  # (S, k, S)
+        grid_s = np.einsum("s,skt,kt->k", W[i], Gn, PSw[near])
+        grid_d = np.einsum("s,skt,kt->k", W[i], Gn, PDw[near])
+        corr = np.where(dip[near], ex_d - grid_d, ex_s - grid_s)
+        val = far + corr @ x[near]
+        if layer == "double" or (layer == "system" and bc[i] == 1):
+            delta = 0.5 - (W[i] @ (Gi @ rho1) + (ex_d - grid_d).sum())
+            val += delta * x[i] - (c * x[i] if layer == "system" else 0.0)
+        out[r] = val
+    return out

@@ -170,3 +170,19 @@ def test_curve_panels_close_the_curve_with_equal_arclength_and_outward_normals(c
     _, dp = curve(t)
     length = np.trapezoid(np.hypot(dp[:, 0], dp[:, 1]), t)
     assert 0 < length - L.sum() < 1e-4 * length
+
+
+@pytest.mark.parametrize("layer", ["single", "double", "system"])
+def test_row_wise_accelerated_operator_equals_the_dense_one(layer):
+    """The row-wise form (used on grids too large for dense matrices) agrees
+    with the dense accelerated matrices on every row."""
+    rng = np.random.default_rng(3)
+    b = I.curve_panels(64, I.star_curve(0.3, 0.3, 5))
+    x = rng.standard_normal(b.nb)
+    bc = (rng.uniform(size=b.nb) < 0.5).astype(np.uint8)
+    S, D = PO.accelerated_matrices(b.panels, b.h, 3, 3)
+    M = {"single": S, "double": D, "system": PO.system(S, D, bc)}[layer]
+    rows = np.arange(0, b.nb, 7)
+    got = PO.accelerated_rows(b.panels, b.h, 3, 3, x, rows, layer, bc)
+    ref = (M @ x)[rows]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
