@@ -220,9 +220,23 @@ def cpu_oracle_rate(b, bc, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    return {"value": (done / b.nb) / el, "unit": "applies/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same sample size on one thread, about a tenth of the time budget
+    one = None
+    if cores > 1:
+        oracle.set_threads(1)
+        try:
+            n1 = max(16, int(rows * 0.1 * seconds / max(el / max(done / rows, 1), 1e-6) / cores))
+            t1 = time.perf_counter()
+            oracle.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x, rows=(0, min(n1, b.nb)))
+            one = (min(n1, b.nb) / b.nb) / (time.perf_counter() - t1)
+        finally:
+            oracle.set_threads(cores)
+    return {"value": (done / b.nb) / el, "unit": "applies/s", "cores": cores, "kind": "oracle",
+            "one_core_value": one,
             "sample": f"{done} of {b.nb} target rows of the FP64 direct-sum system apply in {el:.1f} s "
-                      f"(rows of one apply evaluated in blocks; applies = rows / nb)"}
+                      f"(rows of one apply evaluated in blocks; applies = rows / nb); one_core_value: a "
+                      f"shorter sample of the same rows on one thread"}
 
 
 def _time_applies(plan, layer, x, reps):
