@@ -39,9 +39,11 @@ __device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
 
 // cells per batch of the row-sum and gather loops: the loads of a batch are
-// issued together, so each batch costs one memory round trip
+// issued together, one batch ahead of its use, so each batch's memory round
+// trip overlaps the arithmetic of the one before (two batches of loads live
+// at once: 4 cells keep the 512-thread kernels within their 128 registers)
 #ifndef COL2D_CELL_BATCH
-#define COL2D_CELL_BATCH 8
+#define COL2D_CELL_BATCH 4
 #endif
 constexpr int CB = COL2D_CELL_BATCH;
 
@@ -77,14 +79,31 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const Col
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
+  uint32_t mn[CB];
+  cplx<T> vn[CB];
+  if (cnt > 0) {
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      const int pos = (i < cnt ? i : cnt - 1) * TT + t;
+      mn[i] = __ldg(p.meta + pos);
+      vn[i] = p.val[pos];
+    }
+  }
   for (int i0 = 0; i0 < cnt; i0 += CB) {
     uint32_t mt[CB];
     cplx<T> vv[CB], w[CB];
 #pragma unroll
     for (int i = 0; i < CB; ++i) {
-      const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
-      mt[i] = __ldg(p.meta + pos);
-      vv[i] = p.val[pos];
+      mt[i] = mn[i];
+      vv[i] = vn[i];
+    }
+    if (i0 + CB < cnt) {
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        const int pos = (i0 + CB + i < cnt ? i0 + CB + i : cnt - 1) * TT + t;
+        mn[i] = __ldg(p.meta + pos);
+        vn[i] = p.val[pos];
+      }
     }
 #pragma unroll
     for (int i = 0; i < CB; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
@@ -162,14 +181,31 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const Co
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   const T ckx = (kx == 0 || kx == g.n) ? T(1) : T(2);
+  uint32_t mn[CB];
+  cplx<T> wn[CB];
+  if (cnt > 0) {
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      const int pos = (i < cnt ? i : cnt - 1) * TT + t;
+      mn[i] = __ldg(p.meta + pos);
+      if (twc) wn[i] = twc[pos];
+    }
+  }
   for (int i0 = 0; i0 < cnt; i0 += CB) {
     uint32_t mt[CB];
     cplx<T> Y[CB], w[CB];
 #pragma unroll
     for (int i = 0; i < CB; ++i) {
-      const int pos = (i0 + i < cnt ? i0 + i : cnt - 1) * TT + t;
-      mt[i] = __ldg(p.meta + pos);
-      if (twc) w[i] = twc[pos];  // the sparse pass's e^{-i...}: conjugated below
+      mt[i] = mn[i];
+      if (twc) w[i] = wn[i];  // the sparse pass's e^{-i...}: conjugated below
+    }
+    if (i0 + CB < cnt) {
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        const int pos = (i0 + CB + i < cnt ? i0 + CB + i : cnt - 1) * TT + t;
+        mn[i] = __ldg(p.meta + pos);
+        if (twc) wn[i] = twc[pos];
+      }
     }
 #pragma unroll
     for (int i = 0; i < CB; ++i) {
