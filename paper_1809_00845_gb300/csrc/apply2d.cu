@@ -201,38 +201,99 @@ __global__ void k_prep_v2(int npos, const int32_t* __restrict__ perm, const TIO*
   val[j] = {coefA[j] * x, coefB[j] * x};
 }
 
+// Error-free sum (Knuth's TwoSum): returns s = fl(a + b) and sets e so that
+// a + b = s + e exactly (round-to-nearest, no contraction).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return s;
+}
+
+// Running compensated FP32 sum (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), algorithm Sum2): p carries the
+// rounded sum, c the exactly captured rounding errors; the result p + c is as
+// accurate as the sum taken in twice the working precision and rounded once.
+struct CompSum {
+  float p, c;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    p = two_sum(p, x, e);
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ void add(const CompSum& o) {
+    add(o.p);
+    c = __fadd_rn(c, o.c);
+  }
+};
+
 // out[perm[j]] = sum_b partial[b*npos + j] (+ diag * in) over interleaved
-// positions j (padding skipped), FP64 sum in a fixed order: 32 cells per
-// block, 16 warps each summing every 16th partial (four interleaved chains, so
-// that four loads are in flight), then the 16 warp sums in order.
+// positions j (padding skipped), in a fixed order: 32 cells per block, 16
+// warps each summing every 16th partial (four interleaved chains, so that four
+// loads are in flight), then the 16 warp sums in order.  FP32 plans sum with
+// the compensated FP32 sum above (GB300's FP64 rate would make the FP64 adds
+// and conversions the reduction's cost); FP64 and double-float plans in FP64.
 template <typename T, typename TIO>
 __global__ void __launch_bounds__(512) k_reduce_v2(const T* __restrict__ partial, int grid, int npos,
                                                    const int32_t* __restrict__ perm, const TIO* __restrict__ diag,
                                                    const TIO* __restrict__ in, TIO* __restrict__ out) {
   constexpr int W = 16;  // warps, each summing every W-th CTA's partial
-  __shared__ double red[W][33];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
-  // four independent chains keep four loads in flight; fixed order throughout
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  if (j < npos) {
-    int b = wp;
-    for (; b + 3 * W < grid; b += 4 * W) {
-      s0 += (double)partial[(size_t)b * npos + j];
-      s1 += (double)partial[(size_t)(b + W) * npos + j];
-      s2 += (double)partial[(size_t)(b + 2 * W) * npos + j];
-      s3 += (double)partial[(size_t)(b + 3 * W) * npos + j];
+  if constexpr (std::is_same<T, float>::value && std::is_same<TIO, float>::value) {
+    __shared__ CompSum red[W][33];
+    CompSum s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f}, s3{0.f, 0.f};
+    if (j < npos) {
+      int b = wp;
+      for (; b + 3 * W < grid; b += 4 * W) {
+        s0.add(partial[(size_t)b * npos + j]);
+        s1.add(partial[(size_t)(b + W) * npos + j]);
+        s2.add(partial[(size_t)(b + 2 * W) * npos + j]);
+        s3.add(partial[(size_t)(b + 3 * W) * npos + j]);
+      }
+      for (; b < grid; b += W) s0.add(partial[(size_t)b * npos + j]);
     }
-    for (; b < grid; b += W) s0 += (double)partial[(size_t)b * npos + j];
-  }
-  red[wp][lane] = (s0 + s1) + (s2 + s3);
-  __syncthreads();
-  if (wp == 0 && j < npos && perm[j] >= 0) {
-    double t = 0.0;
-    for (int k = 0; k < W; ++k) t += red[k][lane];
-    const int u = perm[j];
-    if (diag) t += (double)diag[u] * (double)in[u];
-    out[u] = (TIO)t;
+    s0.add(s1);
+    s0.add(s2);
+    s0.add(s3);
+    red[wp][lane] = s0;
+    __syncthreads();
+    if (wp == 0 && j < npos && perm[j] >= 0) {
+      CompSum t{0.f, 0.f};
+      for (int k = 0; k < W; ++k) t.add(red[k][lane]);
+      const int u = perm[j];
+      if (diag) {
+        // exact product as pr + epr (FMA error term)
+        const float pr = __fmul_rn(diag[u], in[u]);
+        const float epr = fmaf(diag[u], in[u], -pr);
+        t.add(pr);
+        t.c = __fadd_rn(t.c, epr);
+      }
+      out[u] = __fadd_rn(t.p, t.c);
+    }
+  } else {
+    __shared__ double red[W][33];
+    // four independent chains keep four loads in flight; fixed order throughout
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (j < npos) {
+      int b = wp;
+      for (; b + 3 * W < grid; b += 4 * W) {
+        s0 += (double)partial[(size_t)b * npos + j];
+        s1 += (double)partial[(size_t)(b + W) * npos + j];
+        s2 += (double)partial[(size_t)(b + 2 * W) * npos + j];
+        s3 += (double)partial[(size_t)(b + 3 * W) * npos + j];
+      }
+      for (; b < grid; b += W) s0 += (double)partial[(size_t)b * npos + j];
+    }
+    red[wp][lane] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (wp == 0 && j < npos && perm[j] >= 0) {
+      double t = 0.0;
+      for (int k = 0; k < W; ++k) t += red[k][lane];
+      const int u = perm[j];
+      if (diag) t += (double)diag[u] * (double)in[u];
+      out[u] = (TIO)t;
+    }
   }
 }
 
