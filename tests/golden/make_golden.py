@@ -80,14 +80,14 @@ def main():
          "discretised boundary integral as a sum over boundary cells with w = in-cell arc length) and the",
          "boundary-condition split A x of Eq. 4 at c = 1/2 (bc 0: Dirichlet, x is q; bc 1: Neumann, x is u)"],
         "laplace2d", I.circle_boundary(16), seed=1016)
-    cube = I.cube_boundary(8, 3, 5)
+    cube = I.cube_boundary(16, 7, 9)
     write_operator_fixture(
-        os.path.join(HERE, "cube_n8_laplace3d.txt"),
-        ["3D Laplace, surface cells of the cube [3, 5]^3 on an 8^3 grid: S x, D x and the split A x",
+        os.path.join(HERE, "cube_n16_laplace3d.txt"),
+        ["3D Laplace, surface cells of the cube [7, 9]^3 on a 16^3 grid: S x, D x and the split A x",
          "(the 3D analogue of Eq. 15 and Eq. 4, kernel 1 / (4 pi r), c = 1/2)"],
         "laplace3d", cube, seed=308)
     write_operator_fixture(
-        os.path.join(HERE, "cube_n8_kelvin3d.txt"),
+        os.path.join(HERE, "cube_n16_kelvin3d.txt"),
         ["Kelvin (3D elasticity), same cube, nu = 0.3, mu = 1: U t (Eq. 7), T u (traction kernel) and",
          "the split A x of Eq. 8 at c = 1/2 (A x = U (x on Dirichlet) - T (x on Neumann) - c x on Neumann)"],
         "kelvin3d", cube, seed=708)

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-OPERATOR_FIXTURES = ["circle_n16_laplace2d.txt", "cube_n8_laplace3d.txt", "cube_n8_kelvin3d.txt"]
+OPERATOR_FIXTURES = ["circle_n16_laplace2d.txt", "cube_n16_laplace3d.txt", "cube_n16_kelvin3d.txt"]
 TOL = {"f64": 1e-12, "f32": 2e-6}
 
 
