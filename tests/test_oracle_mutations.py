@@ -2,10 +2,11 @@
 
 Each case rewrites one expression of a copy of ``oracle/bem_oracle.c`` (a
 wrong sign, prefactor, power or constant, a dropped term, a transposed or
-reversed offset, a dropped weight), compiles it with gcc into a library of its
-own and runs the pins of ``test_oracle_pins.py`` against it: at least one of
-them must fail.  The committed oracle is never modified; the pins are shown to
-see the mistakes they are there to see.
+reversed offset, a dropped weight; compiled with gcc into a library of its
+own) or of ``oracle/oracle.py`` (the boundary-condition split), and runs the
+pins of ``test_oracle_pins.py`` against it: at least one of them must fail.
+The committed oracle is never modified; the pins are shown to see the
+mistakes they are there to see.
 """
 import importlib.util
 import os
@@ -48,6 +49,22 @@ def mutant_oracle(tmp_path, old, new):
     return mod
 
 
+def python_mutant(tmp_path, old, new):
+    """A fresh oracle module whose Python source has `old` replaced by `new`
+    (the compiled kernels unchanged)."""
+    src = open(ORACLE_PY).read()
+    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    path = tmp_path / "oracle_py_mutant.py"
+    path.write_text(src.replace(old, new))
+    mod = _load_by_path(f"oracle_py_mutant_{abs(hash((old, new)))}", str(path))
+    here = os.path.dirname(ORACLE_PY)
+    mod._SRC = ORACLE_C
+    mod._BUILD = os.path.join(here, "_build")
+    mod._LIB_PATH = os.path.join(here, "_build", "libbem_oracle.so")
+    mod._lib = None
+    return mod
+
+
 # pins (functions of the oracle module) that each mutation must break
 green2d = lambda o: PINS.test_green_identity_2d(o, I.field_x2y2)  # noqa: E731
 green3d = lambda o: PINS.test_green_identity_3d(o)  # noqa: E731
@@ -59,6 +76,12 @@ cell3d = lambda o: PINS.test_3d_singular_cell_is_cell_average(o, 1.0 / 16)  # no
 cell_kelvin = lambda o: PINS.test_kelvin_singular_cell_is_cell_average(o)  # noqa: E731
 plane_D = lambda o: PINS.test_full_plane_is_plain_convolution(o, 1)  # noqa: E731
 plane_S = lambda o: PINS.test_full_plane_is_plain_convolution(o, 0)  # noqa: E731
+
+
+def split_pins(o):
+    for kernel in ("laplace2d", "kelvin3d"):
+        PINS.test_split_system_is_the_unsplit_equation(o, kernel)
+
 
 MUTATIONS = [
     # 2D Laplace (Eq. 15)
@@ -97,12 +120,29 @@ MUTATIONS = [
 ]
 
 
+PY_MUTATIONS = [
+    ("Navier double-layer sign", "return -1.0 if _kernel_id(kernel) == KELVIN_3D else 1.0", "return 1.0"),
+    ("split diagonal sign", "A = K1 * mD[None, :] + K2 * mN[None, :] - np.diag(c * mN)",
+     "A = K1 * mD[None, :] + K2 * mN[None, :] + np.diag(c * mN)"),
+    ("split masks swapped", "A = K1 * mD[None, :] + K2 * mN[None, :] - np.diag(c * mN)",
+     "A = K1 * mN[None, :] + K2 * mD[None, :] - np.diag(c * mN)"),
+    ("split right-hand side sign", "b = c * u * mD - K2 @ (u * mD) - K1 @ (q * mN)",
+     "b = c * u * mD + K2 @ (u * mD) - K1 @ (q * mN)"),
+    ("matrix-free split diagonal sign", "return y1 + double_sign(k) * y2 - c * (x * mN)[sl]",
+     "return y1 + double_sign(k) * y2 + c * (x * mN)[sl]"),
+    ("matrix-free right-hand side sign", "return c * u * mD - double_sign(k) * k2u - k1q",
+     "return c * u * mD + double_sign(k) * k2u - k1q"),
+]
+
+
 def test_unmutated_copy_passes_the_pins(tmp_path):
     """The harness itself: a copy with a no-op rewrite passes every pin used below."""
     o = mutant_oracle(tmp_path, "/* ---------------------------------------------------------------- kernels -- */",
                       "/* kernels */")
-    for pin in (green2d, green3d, somigliana, L2_pin, C3_pin, cell2d, cell3d, cell_kelvin, plane_D, plane_S):
+    for pin in (green2d, green3d, somigliana, L2_pin, C3_pin, cell2d, cell3d, cell_kelvin, plane_D, plane_S,
+                split_pins):
         pin(o)
+    split_pins(python_mutant(tmp_path, "_lock = threading.Lock()", "_lock = threading.Lock()  # copy"))
 
 
 @pytest.mark.parametrize("what,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
@@ -110,3 +150,10 @@ def test_planted_mistake_fails_a_pin(tmp_path, what, old, new, pin):
     o = mutant_oracle(tmp_path, old, new)
     with pytest.raises(AssertionError):
         pin(o)
+
+
+@pytest.mark.parametrize("what,old,new", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_planted_mistake_in_the_split_fails_a_pin(tmp_path, what, old, new):
+    o = python_mutant(tmp_path, old, new)
+    with pytest.raises(AssertionError):
+        split_pins(o)

@@ -235,3 +235,30 @@ def test_rows_slice_matches_full(oracle_mod):
     full = oracle_mod.apply("kelvin3d", 1, b.cell, b.h, b.w, b.normal, x)
     part = oracle_mod.apply("kelvin3d", 1, b.cell, b.h, b.w, b.normal, x, rows=(5, 7))
     assert np.array_equal(full[5:12], part)
+
+
+@pytest.mark.parametrize("kernel", ["laplace2d", "laplace3d", "kelvin3d"])
+def test_split_system_is_the_unsplit_equation(oracle_mod, kernel):
+    """The boundary-condition split against the equation it splits: for any
+    data (u, q) and any split, A x - b with x = q on Dirichlet and u on
+    Neumann entries equals the residual of the BIE as the paper writes it,
+    S q + D u - c u for Laplace (Eq. 15, Eq. 4) and U t - T u - c u for Navier
+    (Eq. 8), with the direct-sum operators."""
+    rng = np.random.default_rng(17)
+    dim = 2 if kernel == "laplace2d" else 3
+    b = I.random_cells(16, 30, rng, dim=dim)
+    nc = 3 if kernel == "kelvin3d" else 1
+    u = rng.standard_normal(b.nb * nc)
+    q = rng.standard_normal(b.nb * nc)
+    c = 0.5
+    args = (b.cell, b.h, b.w, b.normal)
+    Sq = oracle_mod.apply(kernel, 0, *args, q).reshape(-1)
+    Du = oracle_mod.apply(kernel, 1, *args, u).reshape(-1)
+    residual = Sq + (Du if kernel != "kelvin3d" else -Du) - c * u
+    for trial in range(3):
+        bc = (rng.uniform(size=b.nb * nc) < 0.5).astype(np.uint8)
+        x = np.where(bc == 0, q, u)
+        A, rhs = oracle_mod.system(kernel, *args, bc, u, q, c=c)
+        assert np.allclose(A @ x - rhs, residual, rtol=1e-12, atol=1e-12)
+        y = oracle_mod.system_apply(kernel, *args, bc, x, c=c) - oracle_mod.system_rhs(kernel, *args, bc, u, q, c=c)
+        assert np.allclose(y, residual, rtol=1e-12, atol=1e-12)
