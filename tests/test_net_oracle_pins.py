@@ -48,3 +48,21 @@ def test_gradient_matches_finite_differences(dil):
         fd[i] = (N.loss_and_grad(pp, f, off, tg, cin, h, L, K, dil, bf16=False)[0] -
                  N.loss_and_grad(pm, f, off, tg, cin, h, L, K, dil, bf16=False)[0]) / (2 * eps)
     assert np.linalg.norm(fd - g) / np.linalg.norm(g) < 1e-7
+
+
+def test_bf16_rounding_points():
+    """With rounding on, every layer input and every weight the forward uses
+    is a BF16 value (the rounding points of the kernels), the first layer's
+    input is the rounded features and the last layer's output is not rounded."""
+    rng = np.random.default_rng(2)
+    cin, h, L, K, dil = 3, 4, 3, 3, [1, 2, 4]
+    n = sum((1 if l == L - 1 else h) * (cin if l == 0 else h) * K + (1 if l == L - 1 else h) for l in range(L))
+    p = rng.standard_normal(n) * 0.5
+    f = rng.standard_normal((21, cin))
+    y, cache = N.forward(p, f, [0, 9, 21], cin, h, L, K, dil, bf16=True)
+    assert np.array_equal(cache[0][0], N.bf16_round(f))
+    for x, Wr, _ in cache:
+        assert np.array_equal(x, N.bf16_round(x)) and np.array_equal(Wr, N.bf16_round(Wr))
+    for l in range(1, L):
+        assert np.array_equal(cache[l][0], N.bf16_round(np.maximum(cache[l - 1][2], 0.0)))
+    assert not np.array_equal(y, N.bf16_round(y))
