@@ -41,15 +41,15 @@ def test_status_strings(lib):
         assert lib.bem_status_string(s)
 
 
-def _plan_rc(dim, n, h, cell, w, normal, kernel=0, prec=1, flags=0):
+def _plan_rc(dim, n, h, cell, w, normal, kernel=0, prec=1, flags=0, nu=0.3, mu=1.0):
     lib = bem.load_library()
     hnd = ctypes.c_void_p()
-    nn = np.full(dim, n, dtype=np.int64)
+    nn = np.full(dim, n, dtype=np.int64) if np.isscalar(n) else np.asarray(n, dtype=np.int64)
     cell = np.ascontiguousarray(cell, dtype=np.int32)
     w = np.ascontiguousarray(w, dtype=np.float64)
     normal = np.ascontiguousarray(normal, dtype=np.float64)
     rc = lib.bem_plan(ctypes.byref(hnd), dim, bem._ptr(nn), h, cell.shape[0], bem._ptr(cell), bem._ptr(w),
-                      bem._ptr(normal), kernel, 0.3, 1.0, prec, flags, None)
+                      bem._ptr(normal), kernel, nu, mu, prec, flags, None)
     return rc, lib.bem_last_error().decode()
 
 
@@ -67,9 +67,16 @@ def test_rejects_bad_arguments_on_host(lib):
     assert _plan_rc(2, 8, 0.125, cell, w, nrm, flags=6)[0] == bem.BEM_ERR_ARG          # unknown flags
     assert _plan_rc(2, 8, 0.125, cell, w, nrm, prec=9)[0] == bem.BEM_ERR_ARG           # precision
     assert _plan_rc(2, 8, 0.125, cell, w, nrm, prec=2)[0] == bem.BEM_ERR_UNSUPPORTED   # f32x2 below n = 256
+    empty = np.zeros((0, 2))
+    assert _plan_rc(2, 8, 0.125, empty, np.zeros(0), empty)[0] == bem.BEM_ERR_ARG       # empty boundary
+    assert _plan_rc(2, 8, 0.125, cell, w, [[np.inf, 0.0], [0.0, 1.0]])[0] == bem.BEM_ERR_ARG  # non-finite normal
+    assert _plan_rc(2, 2, 0.5, [[0, 1], [1, 0]], w, nrm)[0] == bem.BEM_ERR_UNSUPPORTED  # n < 4
+    assert _plan_rc(2, [8, 16], 0.125, cell, w, nrm)[0] == bem.BEM_ERR_UNSUPPORTED     # unequal axes
     cell3 = np.array([[1, 2, 3], [3, 4, 5]])
     nrm3 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     assert _plan_rc(3, 512, 1 / 512, cell3, w, nrm3, kernel=1, prec=2)[0] == bem.BEM_ERR_UNSUPPORTED  # f32x2 in 3D
+    for nu, mu in ((0.5, 1.0), (-1.0, 1.0), (0.3, 0.0), (0.3, -2.0)):  # Kelvin material out of range
+        assert _plan_rc(3, 16, 1 / 16, cell3, w, nrm3, kernel=2, nu=nu, mu=mu)[0] == bem.BEM_ERR_ARG
     for tc in (bem.BEM_TC_BF16X3, bem.BEM_TC_F16X3):  # tensor-core stages: 2D, n = 1024 ... 4096 only
         assert _plan_rc(2, 512, 1 / 512, cell, w, nrm, prec=tc)[0] == bem.BEM_ERR_UNSUPPORTED
         assert _plan_rc(2, 8192, 1 / 8192, cell, w, nrm, prec=tc)[0] == bem.BEM_ERR_UNSUPPORTED
