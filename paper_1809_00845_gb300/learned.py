@@ -16,7 +16,7 @@ itself, to the carried flux w q / (h s).  The operator only ever sees w_j q_j
 hold a sliver of the curve while w q is not; the guess is x0 = pred h s / w.  Training targets are solutions of the FFT method (FP32 GMRES
 with FP64 residual refinement to 1e-8).  At solve time the prediction is
 passed to ``bem_solve`` as x0; zero-start GMRES remains the fallback and the
-FP64 residual judges the answer.
+FP64 residual decides when the answer is good enough.
 
 Everything that computes runs in the library's CUDA kernels; this module
 prepares arrays and drives the loops.
