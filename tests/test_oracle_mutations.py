@@ -76,6 +76,9 @@ cell3d = lambda o: PINS.test_3d_singular_cell_is_cell_average(o, 1.0 / 16)  # no
 cell_kelvin = lambda o: PINS.test_kelvin_singular_cell_is_cell_average(o)  # noqa: E731
 plane_D = lambda o: PINS.test_full_plane_is_plain_convolution(o, 1)  # noqa: E731
 plane_S = lambda o: PINS.test_full_plane_is_plain_convolution(o, 0)  # noqa: E731
+const2d = lambda o: PINS.test_discrete_double_layer_of_a_constant(o, "laplace2d")  # noqa: E731
+const3d = lambda o: PINS.test_discrete_double_layer_of_a_constant(o, "laplace3d")  # noqa: E731
+const_kelvin = lambda o: PINS.test_discrete_double_layer_of_a_constant(o, "kelvin3d")  # noqa: E731
 
 
 def split_pins(o):
@@ -117,6 +120,14 @@ MUTATIONS = [
     ("normal components swapped in the 2d double layer",
      "bo_lap2d_Q(0, d[0], d[1]) * nj[0] + bo_lap2d_Q(1, d[0], d[1]) * nj[1]) * wj;",
      "bo_lap2d_Q(0, d[0], d[1]) * nj[1] + bo_lap2d_Q(1, d[0], d[1]) * nj[0]) * wj;", plane_D),
+    ("offset reversed, seen by the constant-density invariant", "d[a] = (double)(ci[a] - cj[a]) * h;",
+     "d[a] = (double)(cj[a] - ci[a]) * h;", const2d),
+    ("weight dropped from the 3d double layer", "               wj;", "               1.0;", const3d),
+    ("normal components permuted in the 3d double layer",
+     "bo_lap3d_Q(0, d[0], d[1], d[2]) * nj[0] + bo_lap3d_Q(1, d[0], d[1], d[2]) * nj[1] +",
+     "bo_lap3d_Q(0, d[0], d[1], d[2]) * nj[1] + bo_lap3d_Q(1, d[0], d[1], d[2]) * nj[0] +", const3d),
+    ("weight dropped from the Kelvin blocks", "for (int k = 0; k < 9; ++k) blk[k] = K[k] * wj;",
+     "for (int k = 0; k < 9; ++k) blk[k] = K[k];", const_kelvin),
 ]
 
 
@@ -140,7 +151,7 @@ def test_unmutated_copy_passes_the_pins(tmp_path):
     o = mutant_oracle(tmp_path, "/* ---------------------------------------------------------------- kernels -- */",
                       "/* kernels */")
     for pin in (green2d, green3d, somigliana, L2_pin, C3_pin, cell2d, cell3d, cell_kelvin, plane_D, plane_S,
-                split_pins):
+                const2d, const3d, const_kelvin, split_pins):
         pin(o)
     split_pins(python_mutant(tmp_path, "_lock = threading.Lock()", "_lock = threading.Lock()  # copy"))
 
