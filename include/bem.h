@@ -247,8 +247,8 @@ bem_status bem_set_preconditioner(bem_plan_t plan, int kind, int block_size);
  * n >= 256) or BEM_F64 (otherwise); bem_solve then forms the right-hand side
  * and every residual with the companion operator and solves
  * for the corrections with the preconditioned FP32 GMRES, so that tolerances
- * below the FP32 operator's own accuracy (a relative residual of ~3e-6 for
- * the 4096^2 star) are reached.  rel_residual then is the companion's
+ * below the FP32 operator's own accuracy (plain FP32 GMRES stalls at a
+ * relative residual of 1.7e-6 on the 4096^2 star) are reached.  rel_residual then is the companion's
  * residual.  No effect on BEM_F64 and BEM_F32X2 plans. */
 bem_status bem_enable_refinement(bem_plan_t plan, int enable);
 

@@ -23,7 +23,8 @@
 // across a warp and every loop has a warp-uniform trip count.  Each CTA
 // accumulates the contributions of its columns per cell slot (shared memory
 // when it fits, else its own slice of the partial buffer), and a reduction
-// kernel sums the per-CTA partials in FP64 in the caller's cell order.
+// kernel sums the per-CTA partials in a fixed order (compensated FP32 for FP32
+// plans, FP64 otherwise) in the caller's cell order.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
