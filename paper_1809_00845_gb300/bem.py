@@ -164,6 +164,19 @@ class Geometry:
     normal: np.ndarray
 
 
+def _check_out_tensor(x, out):
+    """An output tensor for an apply of x: same device, dtype and size as x,
+    contiguous, and not overlapping x (the library writes nb*ncomp values)."""
+    import torch
+    if not (isinstance(out, torch.Tensor) and out.device == x.device and out.dtype == x.dtype
+            and out.is_contiguous() and out.numel() == x.numel()):
+        raise ValueError("out must be a contiguous tensor on the input's device, of its dtype and size")
+    nbytes = x.numel() * x.element_size()
+    xa, oa = x.data_ptr(), out.data_ptr()
+    if xa < oa + nbytes and oa < xa + nbytes:
+        raise ValueError("out must not overlap the input")
+
+
 class Plan:
     """Owning wrapper of a bem_plan_t."""
 
@@ -253,6 +266,8 @@ class Plan:
             raise ValueError("input must be a contiguous tensor of nb*ncomp values in the plan precision")
         if out is None:
             out = torch.empty_like(x)
+        else:
+            _check_out_tensor(x, out)
         _check(load_library().bem_apply(self._h, lay, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                         _stream_ptr(stream)))
         return out
@@ -264,6 +279,11 @@ class Plan:
             raise ValueError("input must hold nb*ncomp values")
         if out is None:
             out = np.empty_like(x)
+        elif not (isinstance(out, np.ndarray) and out.dtype == x.dtype and out.size == x.size
+                  and out.flags.c_contiguous and out.flags.writeable):
+            raise ValueError("out must be a writeable contiguous array of nb*ncomp values in the plan precision")
+        elif np.shares_memory(out, x):
+            raise ValueError("out must not overlap the input")
         _check(load_library().bem_apply_host(self._h, lay, _ptr(x), _ptr(out), _stream_ptr(stream)))
         return out
 
@@ -279,6 +299,8 @@ class Plan:
         x0p = None
         if x0 is not None:
             x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+            if x0.size != m:
+                raise ValueError("x0 must hold nb*ncomp values")
             x0p = _ptr(x0)
         info = SolveInfo()
         rc = load_library().bem_solve(self._h, _ptr(bc), _ptr(data), float(c), float(tol), int(max_iter),
