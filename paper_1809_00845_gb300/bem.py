@@ -190,10 +190,14 @@ class Plan:
         cell = np.ascontiguousarray(cell, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
         normal = np.ascontiguousarray(normal, dtype=np.float64)
-        self.nb = int(cell.shape[0])
+        self.nb = int(cell.shape[0]) if cell.ndim == 2 else -1
         nn = np.ascontiguousarray(np.full(self.dim, int(n), dtype=np.int64) if np.isscalar(n) else n,
-                                  dtype=np.int64)
+                                  dtype=np.int64).reshape(-1)
         self._h = ctypes.c_void_p()
+        if cell.ndim != 2 or cell.shape[1] != self.dim or w.size != self.nb or normal.size != self.nb * self.dim:
+            raise ValueError("cell must be (nb, dim), w hold nb values and normal nb*dim values")
+        if nn.size != self.dim:
+            raise ValueError("n must be a scalar or hold dim grid sizes")
         rc = lib.bem_plan(ctypes.byref(self._h), self.dim, _ptr(nn), float(h), self.nb, _ptr(cell), _ptr(w),
                           _ptr(normal), self.kernel, float(nu), float(mu), self.precision, 0, _stream_ptr(stream))
         _check(rc)
@@ -213,8 +217,10 @@ class Plan:
         self.dim = 2
         self.ncomp = 1
         panels = np.ascontiguousarray(panels, dtype=np.float64)
-        self.nb = int(panels.shape[0])
         self._h = ctypes.c_void_p()
+        if panels.ndim != 2 or panels.shape[1] != 4:
+            raise ValueError("panels must be (nb, 4): A.x, A.y, B.x, B.y")
+        self.nb = int(panels.shape[0])
         _check(lib.bem_plan_panels(ctypes.byref(self._h), int(n), float(h), self.nb, _ptr(panels), int(order),
                                    int(near_radius), self.precision, 0, _stream_ptr(stream)))
         self.torch_dtype = None
@@ -247,6 +253,8 @@ class Plan:
     # ------------------------------------------------------------------ calls
     def set_bc(self, bc, c=0.5):
         bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
+        if bc.size != self.nb * self.ncomp:
+            raise ValueError("bc must hold nb*ncomp values")
         _check(load_library().bem_set_bc(self._h, _ptr(bc), float(c)))
 
     def set_preconditioner(self, kind="block", block_size=64):
@@ -315,6 +323,8 @@ class Plan:
         """Measured block size of the block-Jacobi preconditioner (bem_tune_preconditioner)."""
         bc = np.ascontiguousarray(bc, dtype=np.uint8).reshape(-1)
         data = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)
+        if bc.size != self.nb * self.ncomp or data.size != self.nb * self.ncomp:
+            raise ValueError("bc and data must hold nb*ncomp values")
         out = ctypes.c_int()
         _check(load_library().bem_tune_preconditioner(self._h, _ptr(bc), _ptr(data), float(c), float(tol),
                                                        int(max_iter), int(restart), ctypes.byref(out)))
@@ -396,6 +406,8 @@ class Batch:
         x0p = None
         if x0 is not None:
             x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+            if x0.size != self.total:
+                raise ValueError("x0 must hold the batch's packed total of values")
             x0p = _ptr(x0)
         infos = (SolveInfo * len(self.plans))()
         rc = load_library().bem_batch_solve(self._h, _ptr(bc), _ptr(data), float(c), float(tol), int(max_iter),
@@ -444,9 +456,27 @@ class Net:
         return out
 
     def set_params(self, p):
-        p = np.ascontiguousarray(p, dtype=np.float32)
-        assert p.size == self.nparams
+        p = np.ascontiguousarray(p, dtype=np.float32).reshape(-1)
+        if p.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters, got {p.size}")
         _check(load_library().bem_net_set_params(self._h, _ptr(p)))
+
+    def _check_batch(self, feats, offsets, target=None):
+        """Shapes of a batch: feats (T, cin), target T values; host offsets
+        start at 0, do not decrease and end at T (device offsets are the
+        caller's responsibility, as the ABI states)."""
+        import torch
+        shape = tuple(feats.shape) if hasattr(feats, "shape") else np.shape(feats)
+        if len(shape) != 2 or shape[1] != self.cin or shape[0] < 1:
+            raise ValueError(f"feats must be (T, {self.cin})")
+        T = shape[0]
+        if not (isinstance(offsets, torch.Tensor) and offsets.is_cuda):
+            o = offsets.numpy() if isinstance(offsets, torch.Tensor) else np.asarray(offsets)
+            o = o.reshape(-1)
+            if o.size < 2 or o[0] != 0 or o[-1] != T or np.any(np.diff(o) < 0):
+                raise ValueError("offsets must start at 0, not decrease and end at T")
+        if target is not None and int(np.prod(target.shape if hasattr(target, "shape") else np.shape(target))) != T:
+            raise ValueError("target must hold T values")
 
     @staticmethod
     def _dev(feats, offsets, target=None):
@@ -463,6 +493,7 @@ class Net:
 
     def forward(self, feats, offsets, stream=None):
         import torch
+        self._check_batch(feats, offsets)
         f, o, _ = self._dev(feats, offsets)
         T = f.shape[0]
         out = torch.empty(T, dtype=torch.float32, device="cuda")
@@ -471,6 +502,7 @@ class Net:
         return out
 
     def gradient(self, feats, offsets, target, stream=None):
+        self._check_batch(feats, offsets, target)
         f, o, t = self._dev(feats, offsets, target)
         g = np.empty(self.nparams, dtype=np.float32)
         loss = ctypes.c_double()
@@ -480,6 +512,7 @@ class Net:
         return loss.value, g
 
     def train_step(self, feats, offsets, target, lr=1e-3, stream=None):
+        self._check_batch(feats, offsets, target)
         f, o, t = self._dev(feats, offsets, target)
         loss = ctypes.c_double()
         _check(load_library().bem_net_train_step(self._h, ctypes.c_void_p(f.data_ptr()),

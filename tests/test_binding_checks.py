@@ -64,3 +64,58 @@ def test_solve_initial_guess_size():
     with pytest.raises(bem.BemError) as e:
         p.solve(bc, data, x0=np.zeros(8))
     assert e.value.status == bem.BEM_ERR_ARG
+
+
+def test_plan_geometry_shapes():
+    cell = np.array([[1, 2], [3, 4]])
+    w = np.ones(2)
+    nrm = np.array([[1.0, 0.0], [0.0, 1.0]])
+    for args in ((2, 8, 0.125, np.array([[1, 2, 3], [3, 4, 5]]), w, nrm),      # cell columns != dim
+                 (2, 8, 0.125, np.array([1, 2, 3, 4]), w, nrm),                # cell not (nb, dim)
+                 (2, 8, 0.125, cell, np.ones(3), nrm),                         # w size
+                 (2, 8, 0.125, cell, w, np.ones(3)),                           # normal size
+                 (2, [8, 8, 8], 0.125, cell, w, nrm)):                         # n per axis
+        with pytest.raises(ValueError):
+            bem.Plan(*args)
+    with pytest.raises(ValueError):
+        bem.Plan.from_panels(8, 0.125, np.zeros((3, 3)))
+
+
+def test_boundary_condition_sizes():
+    p = _shell_plan()
+    with pytest.raises(ValueError):
+        p.set_bc(np.zeros(7, np.uint8))
+    with pytest.raises(ValueError):
+        p.tune_preconditioner(np.zeros(8, np.uint8), np.ones(7))
+    with pytest.raises(bem.BemError) as e:  # right size: the library refuses the null plan
+        p.set_bc(np.zeros(8, np.uint8))
+    assert e.value.status == bem.BEM_ERR_ARG
+
+
+def test_batch_initial_guess_size():
+    b = bem.Batch.__new__(bem.Batch)
+    b.total, b.plans, b._h = 10, [None, None], ctypes.c_void_p()
+    with pytest.raises(ValueError):
+        b.solve(np.zeros(10, np.uint8), np.ones(10), x0=np.zeros(9))
+    with pytest.raises(ValueError):
+        b.solve(np.zeros(9, np.uint8), np.ones(10))
+
+
+def test_network_batch_shapes():
+    net = bem.Net.__new__(bem.Net)
+    net.cin, net.nparams, net._h = 3, 10, ctypes.c_void_p()
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(9, np.float32))
+    f = np.zeros((5, 3), np.float32)
+    for feats, off in ((np.zeros((5, 4), np.float32), [0, 5]),   # channels != cin
+                       (np.zeros(15, np.float32), [0, 5]),        # not (T, cin)
+                       (f, [0, 3]),                               # does not end at T
+                       (f, [1, 5]),                               # does not start at 0
+                       (f, [0, 4, 2, 5]),                         # decreasing
+                       (f, [0])):                                 # no sequence
+        with pytest.raises(ValueError):
+            net.forward(feats, np.asarray(off, np.int32))
+    with pytest.raises(ValueError):
+        net.gradient(f, np.array([0, 5], np.int32), np.zeros(4, np.float32))
+    with pytest.raises(ValueError):
+        net.train_step(f, np.array([0, 5], np.int32), np.zeros(6, np.float32))
