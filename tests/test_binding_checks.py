@@ -119,3 +119,23 @@ def test_network_batch_shapes():
         net.gradient(f, np.array([0, 5], np.int32), np.zeros(4, np.float32))
     with pytest.raises(ValueError):
         net.train_step(f, np.array([0, 5], np.int32), np.zeros(6, np.float32))
+
+
+def test_valid_arguments_pass_the_checks():
+    """The shapes every caller uses pass: a valid network batch (host or torch
+    CPU offsets), and valid geometry reaches the library (which, without a
+    GPU, fails at its first CUDA call)."""
+    torch = pytest.importorskip("torch")
+    net = bem.Net.__new__(bem.Net)
+    net.cin, net.nparams, net._h = 3, 10, ctypes.c_void_p()
+    f = np.zeros((5, 3), np.float32)
+    net._check_batch(f, np.array([0, 2, 5], np.int32), np.zeros(5, np.float32))
+    net._check_batch(torch.zeros(5, 3), torch.tensor([0, 5], dtype=torch.int32), torch.zeros(5))
+    net._check_batch(f.tolist(), [0, 5], [0.0] * 5)
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1809_00845_gb300 import inputs as I
+    b = I.curve_panels(64, I.circle_curve(0.35))
+    with pytest.raises(bem.BemError) as e:
+        bem.Plan.from_panel_boundary(b, "f32", 3, 3)
+    assert e.value.status == bem.BEM_ERR_CUDA
