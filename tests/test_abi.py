@@ -21,7 +21,7 @@ def lib():
 
 def _declared():
     txt = open(os.path.join(ROOT, "include", "bem.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(bem_[a-z_]+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(bem_[a-z_]+)\s*\(", txt, re.M)))
 
 
 def test_header_declares_the_abi():
@@ -86,3 +86,13 @@ def test_rejects_bad_arguments_on_host(lib):
     assert lib.bem_apply(None, 0, None, None, None) == bem.BEM_ERR_ARG
     assert lib.bem_destroy(None) == bem.BEM_OK
     assert lib.bem_device_status(None, None) == bem.BEM_ERR_ARG
+
+
+def test_binding_calls_only_declared_functions():
+    """Every library function the Python binding calls is declared in
+    include/bem.h (the binding and the header cannot drift apart)."""
+    src = open(os.path.join(ROOT, "paper_1809_00845_gb300", "bem.py")).read()
+    called = set(re.findall(r"\.(bem_[a-z_]+)\b", src))
+    assert called, "no library calls found"
+    missing = sorted(called - set(_declared()))
+    assert not missing, missing
