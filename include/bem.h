@@ -183,16 +183,26 @@ bem_status bem_plan_panels(bem_plan_t* out, int64_t n, double h, int64_t nb, con
  *   c   free-term coefficient (Section 2: 1/2 on a smooth boundary) */
 bem_status bem_set_bc(bem_plan_t plan, const uint8_t* bc, double c);
 
-/* One operator apply on the device (Section 4, Eq. 15-16).
- *   in_dev, out_dev  device pointers, nb*ncomp values of the plan precision
- *                    (double for BEM_F64 and BEM_F32X2, float for BEM_F32), component
- *                    fastest; caller-owned; must not alias
- *   stream           cudaStream_t (may be NULL); the call is asynchronous
+/* Operator applies on the device (Section 4, Eq. 15-16): nbatch densities
+ * through the same operator.  The kernel spectra are fixed per plan (Eq. 16),
+ * so every right-hand side reuses them.
+ *   in_dev, out_dev  device pointers, nbatch*nb*ncomp values of the plan
+ *                    precision (double for BEM_F64 and BEM_F32X2, float for
+ *                    BEM_F32 and the tensor-core forms); vector r at element
+ *                    offset r*nb*ncomp, component fastest; caller-owned; the
+ *                    two ranges must not overlap (BEM_ERR_ARG), and device
+ *                    memory of another GPU than the plan's is refused
+ *                    (BEM_ERR_ARG)
+ *   nbatch           number of vectors (>= 1)
+ *   stream           cudaStream_t (may be NULL); the call is asynchronous and
+ *                    the vectors are applied in order on this stream
+ * The plan's device must be the current device (BEM_ERR_ARG otherwise).
  * BEM_SYSTEM needs a prior bem_set_bc. */
-bem_status bem_apply(bem_plan_t plan, bem_layer layer, const void* in_dev, void* out_dev, void* stream);
+bem_status bem_apply(bem_plan_t plan, bem_layer layer, const void* in_dev, void* out_dev, int nbatch, void* stream);
 
-/* The same apply with HOST buffers (plan precision): copies in, applies,
- * copies out and synchronises the stream before returning. */
+/* One apply with HOST buffers (nb*ncomp values, plan precision): copies in,
+ * applies, copies out and synchronises the stream before returning.  The
+ * plan's device must be current. */
 bem_status bem_apply_host(bem_plan_t plan, bem_layer layer, const void* in_host, void* out_host, void* stream);
 
 /* bem_apply without touching the CUDA allocator, for callers that cannot
@@ -224,7 +234,8 @@ bem_status bem_apply_static_scratch(bem_plan_t plan, bem_layer layer, const void
  *             copied from data, unknown ones from the solution); either may be NULL
  *   info      may be NULL
  * Returns BEM_ERR_NOT_CONVERGED with the best iterate written if max_iter is
- * reached.  Arnoldi, Givens rotations and residual norms are FP64. */
+ * reached.  Arnoldi, Givens rotations and residual norms are FP64.  The
+ * plan's device must be current (BEM_ERR_ARG otherwise). */
 bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
                      int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
                      void* stream);

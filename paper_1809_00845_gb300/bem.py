@@ -82,7 +82,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_set_bc.argtypes = [P, P, D]
     lib.bem_set_preconditioner.argtypes = [P, I, I]
     lib.bem_enable_refinement.argtypes = [P, I]
-    lib.bem_apply.argtypes = [P, I, P, P, P]
+    lib.bem_apply.argtypes = [P, I, P, P, I, P]
     lib.bem_apply_host.argtypes = [P, I, P, P, P]
     lib.bem_apply_static_scratch.argtypes = [P, I, P, P, P]
     lib.bem_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
@@ -164,6 +164,20 @@ class Geometry:
     normal: np.ndarray
 
 
+def _current_device():
+    """Index of the current CUDA device (the one a plan is built on), or None."""
+    import torch
+    return torch.cuda.current_device() if torch.cuda.is_available() else None
+
+
+def _check_tensor_device(plan_device, t):
+    """A tensor handed to a plan's kernels must live on the plan's GPU (the
+    library would otherwise launch on one device with pointers into another)."""
+    if plan_device is not None and t.device.type == "cuda" and t.device.index is not None \
+            and t.device.index != plan_device:
+        raise ValueError(f"tensor on {t.device}, but the plan was built on cuda:{plan_device}")
+
+
 def _check_out_tensor(x, out):
     """An output tensor for an apply of x: same device, dtype and size as x,
     contiguous, and not overlapping x (the library writes nb*ncomp values)."""
@@ -202,6 +216,7 @@ class Plan:
                           _ptr(normal), self.kernel, float(nu), float(mu), self.precision, 0, _stream_ptr(stream))
         _check(rc)
         self.torch_dtype = None
+        self.device = _current_device()
 
     @classmethod
     def from_boundary(cls, b, kernel="laplace2d", precision="f32", **kw):
@@ -224,6 +239,7 @@ class Plan:
         _check(lib.bem_plan_panels(ctypes.byref(self._h), int(n), float(h), self.nb, _ptr(panels), int(order),
                                    int(near_radius), self.precision, 0, _stream_ptr(stream)))
         self.torch_dtype = None
+        self.device = _current_device()
         return self
 
     @classmethod
@@ -265,19 +281,23 @@ class Plan:
         _check(load_library().bem_enable_refinement(self._h, 1 if enable else 0))
 
     def apply(self, layer, x, out=None, stream=None):
-        """Device apply.  x: CUDA tensor of nb*ncomp plan-precision values."""
+        """Device apply.  x: CUDA tensor of nb*ncomp plan-precision values, or
+        of nbatch*nb*ncomp values (shape (nbatch, nb*ncomp) or flat): every
+        vector through the same operator (bem_apply's nbatch)."""
         import torch
         lay = LAYERS[layer] if isinstance(layer, str) else int(layer)
         if not (isinstance(x, torch.Tensor) and x.is_cuda):
             raise TypeError("apply expects a CUDA tensor; use apply_host for host arrays")
-        if x.dtype != self._tdtype() or not x.is_contiguous() or x.numel() != self.nb * self.ncomp:
-            raise ValueError("input must be a contiguous tensor of nb*ncomp values in the plan precision")
+        m = self.nb * self.ncomp
+        if x.dtype != self._tdtype() or not x.is_contiguous() or x.numel() < m or x.numel() % m != 0:
+            raise ValueError("input must be a contiguous tensor of nbatch*nb*ncomp values in the plan precision")
+        _check_tensor_device(getattr(self, "device", None), x)
         if out is None:
             out = torch.empty_like(x)
         else:
             _check_out_tensor(x, out)
         _check(load_library().bem_apply(self._h, lay, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                        _stream_ptr(stream)))
+                                        x.numel() // m, _stream_ptr(stream)))
         return out
 
     def apply_host(self, layer, x, out=None, stream=None):
@@ -462,19 +482,25 @@ class Net:
         _check(load_library().bem_net_set_params(self._h, _ptr(p)))
 
     def _check_batch(self, feats, offsets, target=None):
-        """Shapes of a batch: feats (T, cin), target T values; host offsets
-        start at 0, do not decrease and end at T (device offsets are the
-        caller's responsibility, as the ABI states)."""
+        """Shapes of a batch: feats (T, cin), target T values; offsets (host
+        or device) start at 0, do not decrease and end at T, so that the
+        network kernels never index past feats or target."""
         import torch
         shape = tuple(feats.shape) if hasattr(feats, "shape") else np.shape(feats)
         if len(shape) != 2 or shape[1] != self.cin or shape[0] < 1:
             raise ValueError(f"feats must be (T, {self.cin})")
         T = shape[0]
-        if not (isinstance(offsets, torch.Tensor) and offsets.is_cuda):
+        if isinstance(offsets, torch.Tensor) and offsets.is_cuda:
+            o = offsets.reshape(-1)
+            # two scalars and one flag come back to the host
+            bad = o.numel() < 2 or int(o[0].item()) != 0 or int(o[-1].item()) != T or \
+                bool((o[1:] < o[:-1]).any().item())
+        else:
             o = offsets.numpy() if isinstance(offsets, torch.Tensor) else np.asarray(offsets)
             o = o.reshape(-1)
-            if o.size < 2 or o[0] != 0 or o[-1] != T or np.any(np.diff(o) < 0):
-                raise ValueError("offsets must start at 0, not decrease and end at T")
+            bad = o.size < 2 or o[0] != 0 or o[-1] != T or bool(np.any(np.diff(o) < 0))
+        if bad:
+            raise ValueError("offsets must start at 0, not decrease and end at T")
         if target is not None and int(np.prod(target.shape if hasattr(target, "shape") else np.shape(target))) != T:
             raise ValueError("target must hold T values")
 

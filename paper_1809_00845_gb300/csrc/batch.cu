@@ -166,6 +166,7 @@ bem_status bem_batch_create(bem_batch_t* out, const bem_plan_t* plans, int count
         set_error("bem_batch_create: a plan appears twice (its scratch would be shared by two applies)");
         return BEM_ERR_ARG;
       }
+    if (bem_status dc = check_device(plans[i], "bem_batch_create"); dc != BEM_OK) return dc;
     if (plans[i]->prec != plans[0]->prec) {
       set_error("bem_batch_create: all plans must share one precision");
       return BEM_ERR_ARG;
@@ -247,8 +248,9 @@ bem_status bem_batch_apply(bem_batch_t b, void* stream) {
     set_error("bem_batch_apply: null batch");
     return BEM_ERR_ARG;
   }
-  bem_status rc = batch_refresh(b);
+  bem_status rc = check_device(b->plans[0], "bem_batch_apply");
   if (rc != BEM_OK) return rc;
+  if ((rc = batch_refresh(b)) != BEM_OK) return rc;
   BEM_CUDA_TRY(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
   return BEM_OK;
 }

@@ -314,6 +314,10 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
                        int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
                        cudaStream_t st);
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);
+// argument checks of the entry points (capi.cu)
+bem_status check_device(const bem_plan_s* p, const char* who);
+bem_status check_buffer_device(const bem_plan_s* p, const void* ptr, const char* who);
+bool ranges_overlap(const void* a, const void* b, size_t bytes);
 size_t prec_bytes(const bem_plan_s* p);
 bem_status upload_real(const bem_plan_s* p, const double* v, size_t count, bool io, void** dst);
 // Lets `kern` launch with up to the device's opt-in shared-memory maximum.  The

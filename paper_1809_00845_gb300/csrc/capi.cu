@@ -47,6 +47,46 @@ bem_status upload_real(const bem_plan_s* p, const double* v, size_t count, bool 
   return BEM_OK;
 }
 
+// The calling thread's current device must be the one the plan was built
+// on: every array the plan holds lives there, and its kernels launch there.
+bem_status check_device(const bem_plan_s* p, const char* who) {
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error(std::string(who) + ": cudaGetDevice: " + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  if (dev != p->device) {
+    set_error(std::string(who) + ": the plan belongs to device " + std::to_string(p->device) + " but device " +
+              std::to_string(dev) + " is current");
+    return BEM_ERR_ARG;
+  }
+  return BEM_OK;
+}
+
+// A caller buffer handed to the plan's kernels: device (or managed) memory of
+// another device is refused; host memory is left to the caller's contract.
+bem_status check_buffer_device(const bem_plan_s* p, const void* ptr, const char* who) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA allocation: clear the sticky-free error state
+    return BEM_OK;
+  }
+  if ((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device != p->device) {
+    set_error(std::string(who) + ": a buffer lives on device " + std::to_string(a.device) +
+              ", the plan on device " + std::to_string(p->device));
+    return BEM_ERR_ARG;
+  }
+  return BEM_OK;
+}
+
+// [a, a + bytes) and [b, b + bytes) share at least one byte
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
 static bem_status upload_coef(bem_plan_s* p, Operator& op, const std::vector<double>& v, const void** dst,
                               bool io = false) {
   void* d = nullptr;
@@ -550,16 +590,32 @@ bem_status bem_set_preconditioner(bem_plan_t p, int kind, int block_size) {
   return BEM_OK;
 }
 
-bem_status bem_apply(bem_plan_t p, bem_layer layer, const void* in_dev, void* out_dev, void* stream) {
+bem_status bem_apply(bem_plan_t p, bem_layer layer, const void* in_dev, void* out_dev, int nbatch, void* stream) {
   if (!p || !in_dev || !out_dev) {
     set_error("bem_apply: null pointer argument");
     return BEM_ERR_ARG;
   }
-  if (in_dev == out_dev) {
-    set_error("bem_apply: input and output must not alias");
+  if (nbatch < 1) {
+    set_error("bem_apply: nbatch must be >= 1");
     return BEM_ERR_ARG;
   }
-  return apply_operator(p, layer, in_dev, out_dev, static_cast<cudaStream_t>(stream));
+  const size_t vec = (size_t)p->nb * p->ncomp * prec_bytes(p);
+  if (ranges_overlap(in_dev, out_dev, vec * (size_t)nbatch)) {
+    set_error("bem_apply: input and output must not overlap");
+    return BEM_ERR_ARG;
+  }
+  bem_status rc;
+  if ((rc = check_device(p, "bem_apply")) != BEM_OK) return rc;
+  if ((rc = check_buffer_device(p, in_dev, "bem_apply")) != BEM_OK) return rc;
+  if ((rc = check_buffer_device(p, out_dev, "bem_apply")) != BEM_OK) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned char* in = static_cast<const unsigned char*>(in_dev);
+  unsigned char* out = static_cast<unsigned char*>(out_dev);
+  // the vectors one after another on the stream: every apply reuses the plan's
+  // scratch, so they must not run concurrently
+  for (int r = 0; r < nbatch; ++r)
+    if ((rc = apply_operator(p, layer, in + (size_t)r * vec, out + (size_t)r * vec, st)) != BEM_OK) return rc;
+  return BEM_OK;
 }
 
 bem_status bem_apply_host(bem_plan_t p, bem_layer layer, const void* in_host, void* out_host, void* stream) {
@@ -567,6 +623,8 @@ bem_status bem_apply_host(bem_plan_t p, bem_layer layer, const void* in_host, vo
     set_error("bem_apply_host: null pointer argument");
     return BEM_ERR_ARG;
   }
+  bem_status rc = check_device(p, "bem_apply_host");
+  if (rc != BEM_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)p->nb * p->ncomp * prec_bytes(p);
   if (!p->d_tin) {
@@ -574,7 +632,7 @@ bem_status bem_apply_host(bem_plan_t p, bem_layer layer, const void* in_host, vo
     BEM_CUDA_TRY(cudaMalloc(&p->d_tout, bytes));
   }
   BEM_CUDA_TRY(cudaMemcpyAsync(p->d_tin, in_host, bytes, cudaMemcpyHostToDevice, st));
-  bem_status rc = apply_operator(p, layer, p->d_tin, p->d_tout, st);
+  rc = apply_operator(p, layer, p->d_tin, p->d_tout, st);
   if (rc != BEM_OK) return rc;
   BEM_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_tout, bytes, cudaMemcpyDeviceToHost, st));
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -588,6 +646,8 @@ bem_status bem_solve(bem_plan_t p, const uint8_t* bc, const double* data, double
     set_error("bem_solve: null pointer argument");
     return BEM_ERR_ARG;
   }
+  const bem_status dc = check_device(p, "bem_solve");
+  if (dc != BEM_OK) return dc;
   const bem_status rc = solve_gmres(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info,
                                     static_cast<cudaStream_t>(stream));
   const bem_status ds = bem_device_status(p, stream);

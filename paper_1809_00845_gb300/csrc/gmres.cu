@@ -838,6 +838,7 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     set_error("bem_batch_solve: the batch must apply BEM_SYSTEM");
     return BEM_ERR_ARG;
   }
+  if (bem_status dc = check_device(bt->plans[0], "bem_batch_solve"); dc != BEM_OK) return dc;
   if (restart < 1 || restart > 512 || max_iter < 0 || !(tol > 0.0)) {
     set_error("bem_batch_solve: need 1 <= restart <= 512, max_iter >= 0, tol > 0");
     return BEM_ERR_ARG;

@@ -46,8 +46,8 @@ extern "C" bem_status bem_apply_static_scratch(bem_plan_t p, bem_layer layer, co
     set_error("bem_apply_static_scratch: null pointer argument");
     return BEM_ERR_ARG;
   }
-  if (in_dev == out_dev) {
-    set_error("bem_apply_static_scratch: input and output must not alias");
+  if (ranges_overlap(in_dev, out_dev, (size_t)p->nb * p->ncomp * prec_bytes(p))) {
+    set_error("bem_apply_static_scratch: input and output must not overlap");
     return BEM_ERR_ARG;
   }
   if (p->pf) {
@@ -77,6 +77,9 @@ extern "C" bem_status bem_apply_static_scratch(bem_plan_t p, bem_layer layer, co
     set_error("bem_apply_static_scratch: the plan's device must be current");
     return BEM_ERR_ARG;
   }
+  bem_status rc;
+  if ((rc = check_buffer_device(p, in_dev, "bem_apply_static_scratch")) != BEM_OK) return rc;
+  if ((rc = check_buffer_device(p, out_dev, "bem_apply_static_scratch")) != BEM_OK) return rc;
   // bytes needed: the densities of every field, then the per-CTA partial sums
   const size_t need = apply_scratch_bytes(p, *op);
   if (need > kStaticScratchBytes) {

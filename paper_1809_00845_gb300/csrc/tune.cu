@@ -70,6 +70,7 @@ bem_status bem_tune_batch(bem_batch_t b, int reps, int* streams_out) {
     set_error("bem_tune_batch: need a batch and reps >= 1");
     return BEM_ERR_ARG;
   }
+  if (bem_status dc = check_device(b->plans[0], "bem_tune_batch"); dc != BEM_OK) return dc;
   std::string key = "batch";
   for (auto* p : b->plans) key += ":" + plan_shape(p);
   key += ":" + std::to_string((int)b->layer);

@@ -83,7 +83,7 @@ def test_rejects_bad_arguments_on_host(lib):
         assert _plan_rc(3, 1024, 1 / 1024, cell3, w, nrm3, kernel=1, prec=tc)[0] == bem.BEM_ERR_UNSUPPORTED
     rc = lib.bem_plan(None, 2, None, 0.1, 1, None, None, None, 0, 0.3, 1.0, 1, 0, None)
     assert rc == bem.BEM_ERR_ARG
-    assert lib.bem_apply(None, 0, None, None, None) == bem.BEM_ERR_ARG
+    assert lib.bem_apply(None, 0, None, None, 1, None) == bem.BEM_ERR_ARG
     assert lib.bem_destroy(None) == bem.BEM_OK
     assert lib.bem_device_status(None, None) == bem.BEM_ERR_ARG
 

@@ -139,3 +139,21 @@ def test_valid_arguments_pass_the_checks():
     with pytest.raises(bem.BemError) as e:
         bem.Plan.from_panel_boundary(b, "f32", 3, 3)
     assert e.value.status == bem.BEM_ERR_CUDA
+
+
+def test_tensor_on_another_gpu_is_refused():
+    """A plan records the GPU it was built on; a tensor on another GPU is
+    refused before its pointer reaches the library (the kernels would run on
+    the plan's GPU with addresses of the other one)."""
+    torch = pytest.importorskip("torch")
+
+    class FakeTensor:
+        def __init__(self, dev):
+            self.device = torch.device(dev)
+    bem._check_tensor_device(0, FakeTensor("cuda:0"))
+    bem._check_tensor_device(None, FakeTensor("cuda:3"))  # no device recorded (no CUDA at plan time)
+    bem._check_tensor_device(1, FakeTensor("cpu"))       # host tensors are refused elsewhere
+    with pytest.raises(ValueError):
+        bem._check_tensor_device(0, FakeTensor("cuda:1"))
+    with pytest.raises(ValueError):
+        bem._check_tensor_device(2, FakeTensor("cuda:0"))
