@@ -933,6 +933,132 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   return BEM_OK;
 }
 
+// ------------------------------------------------ edge-flow node convolution
+
+template <typename T>
+static cudaError_t edge_configure(int TT, size_t smem, int* bps) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (TT) {
+      case 512: return Col2DEdgeKernels<float, 512>::configure(smem, TT, bps);
+      case 256: return Col2DEdgeKernels<float, 256>::configure(smem, TT, bps);
+      case 128: return Col2DEdgeKernels<float, 128>::configure(smem, TT, bps);
+      case 64: return Col2DEdgeKernels<float, 64>::configure(smem, TT, bps);
+      default: return Col2DEdgeKernels<float, 32>::configure(smem, TT, bps);
+    }
+  } else if constexpr (std::is_same<T, f32x2>::value) {
+    switch (TT) {
+      case 512: return Col2DEdgeKernels<f32x2, 512>::configure(smem, TT, bps);
+      case 256: return Col2DEdgeKernels<f32x2, 256>::configure(smem, TT, bps);
+      case 128: return Col2DEdgeKernels<f32x2, 128>::configure(smem, TT, bps);
+      case 64: return Col2DEdgeKernels<f32x2, 64>::configure(smem, TT, bps);
+      default: return Col2DEdgeKernels<f32x2, 0>::configure(smem, TT, bps);
+    }
+  } else {
+    return Col2DEdgeKernels<T, 0>::configure(smem, TT, bps);
+  }
+}
+
+template <typename T>
+static void edge_launch(const bem_plan_s* p, const Col2Dv2Params<T>& cp, cudaStream_t st) {
+  const int TT = p->threads, G = p->edge_grid;
+  const size_t sm = p->edge_smem;
+  if constexpr (std::is_same<T, float>::value) {
+    switch (TT) {
+      case 512: Col2DEdgeKernels<float, 512>::launch(G, TT, sm, st, cp); break;
+      case 256: Col2DEdgeKernels<float, 256>::launch(G, TT, sm, st, cp); break;
+      case 128: Col2DEdgeKernels<float, 128>::launch(G, TT, sm, st, cp); break;
+      case 64: Col2DEdgeKernels<float, 64>::launch(G, TT, sm, st, cp); break;
+      default: Col2DEdgeKernels<float, 32>::launch(G, TT, sm, st, cp); break;
+    }
+  } else if constexpr (std::is_same<T, f32x2>::value) {
+    switch (TT) {
+      case 512: Col2DEdgeKernels<f32x2, 512>::launch(G, TT, sm, st, cp); break;
+      case 256: Col2DEdgeKernels<f32x2, 256>::launch(G, TT, sm, st, cp); break;
+      case 128: Col2DEdgeKernels<f32x2, 128>::launch(G, TT, sm, st, cp); break;
+      case 64: Col2DEdgeKernels<f32x2, 64>::launch(G, TT, sm, st, cp); break;
+      default: Col2DEdgeKernels<f32x2, 0>::launch(G, TT, sm, st, cp); break;
+    }
+  } else {
+    Col2DEdgeKernels<T, 0>::launch(G, TT, sm, st, cp);
+  }
+}
+
+template <typename T>
+static bem_status setup_edge_t(bem_plan_s* p) {
+  constexpr bool R = std::is_same<T, float>::value;
+  const int TT = p->threads;
+  const int64_t n = p->n, Q = p->v2_npos / TT;
+  int dev = 0, nsm = 0, smem_optin = 0, bps = 0;
+  BEM_CUDA_TRY(cudaGetDevice(&dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // FP32: staging rows for the second field (its row sums are kept while the
+  // first is transformed); accumulator rows as in setup_v2_t
+  const size_t base = smem_v2<T>(n, TT, 0, R, false, false);
+  if (base > (size_t)smem_optin) {
+    set_error("grid too large for the edge-flow column buffers");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  int rows = (int)Q;
+  if (smem_v2<T>(n, TT, p->v2_npos, R, true, false) > (size_t)smem_optin)
+    rows = TT == 512 ? (int)std::min<int64_t>(Q, (int64_t)(((size_t)smem_optin - base) / ((size_t)TT * sizeof(T))))
+                     : 0;
+  p->edge_acc_rows = rows;
+  p->edge_smem = base + (size_t)rows * TT * sizeof(T);
+  BEM_CUDA_TRY(edge_configure<T>(TT, p->edge_smem, &bps));
+  if (bps < 1) {
+    set_error("edge-flow column kernel cannot be resident (registers/shared memory)");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  // never more CTAs than the plan's partial sums have rows for
+  p->edge_grid = (int)std::min<int64_t>(std::min<int64_t>((int64_t)bps * nsm, n + 1), p->grid);
+  if (!p->d_val2) {
+    BEM_CUDA_TRY(cudaMalloc(&p->d_val2, (size_t)p->v2_npos * sizeof(T)));
+    BEM_CUDA_TRY(cudaMemset(p->d_val2, 0, (size_t)p->v2_npos * sizeof(T)));
+    p->scratch_bytes += (size_t)p->v2_npos * sizeof(T);
+  }
+  return BEM_OK;
+}
+
+bem_status setup_edge_2d(bem_plan_s* p) {
+  if (!p->v2 || p->tc != 0 || p->threads < 32 || p->threads > 512) {
+    set_error("internal: the edge-flow form needs a four-step plan without tensor-core stages");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  if (p->prec == BEM_F32X2) return setup_edge_t<f32x2>(p);
+  return p->prec == BEM_F64 ? setup_edge_t<double>(p) : setup_edge_t<float>(p);
+}
+
+template <typename T, typename TIO>
+static bem_status launch_edge_t(bem_plan_s* p, TIO* out, cudaStream_t st) {
+  const int npos = (int)p->v2_npos;
+  ScratchPtrs sp{};
+  sp.val = p->d_val;
+  sp.partial = p->d_partial;
+  sp.twc = p->d_twc;
+  Col2Dv2Params<T> cp = col2d_params<T>(p, p->op_single, sp);
+  // both fields go through the single-layer spectrum (field 0)
+  cp.spec[1] = cp.spec[0];
+  cp.imag[1] = cp.imag[0];
+  cp.oddy[1] = cp.oddy[0];
+  cp.val2 = static_cast<const T*>(p->d_val2);
+  cp.acc_rows = p->edge_acc_rows;
+  cudaEvent_t e1 = nullptr;
+  if (p->timing && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
+  edge_launch<T>(p, cp, st);
+  if (p->timing) BEM_CUDA_TRY(cudaEventRecord(e1, st));
+  k_reduce_v2<T, TIO><<<(npos + 31) / 32, 512, 0, st>>>(static_cast<const T*>(sp.partial), p->edge_grid, npos,
+                                                       p->d_perm_il, nullptr, nullptr, out);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+bem_status launch_edge_2d(bem_plan_s* p, void* out, cudaStream_t st) {
+  if (p->prec == BEM_F32X2) return launch_edge_t<f32x2, double>(p, static_cast<double*>(out), st);
+  if (p->prec == BEM_F64) return launch_edge_t<double, double>(p, static_cast<double*>(out), st);
+  return launch_edge_t<float, float>(p, static_cast<float*>(out), st);
+}
+
 // ------------------------------------------------------ grouped batch applies
 
 bool group_eligible(const bem_plan_s* p) {

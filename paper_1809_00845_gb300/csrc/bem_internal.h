@@ -128,16 +128,19 @@ struct PanelOp {
   void* d_W = nullptr;                // nb * S interpolation weights
   int64_t* d_pptr = nullptr;          // nnodes + 1: projection CSR by node
   int32_t* d_pj = nullptr;
-  void* d_pws = nullptr;              // single-layer moments
-  void* d_pwd = nullptr;              // dipole moments
+  double* d_pws = nullptr;            // single-layer moments (FP64)
+  double* d_pwd = nullptr;            // dipole moments (FP64)
+  double* d_pwx = nullptr;            // edge-flow form: the dipole moments as x-edge flows (FP64)
+  double* d_pwy = nullptr;            // ... and as y-edge flows
+  bool edge = false;                  // double layer through the inner plan's edge-flow form
   int64_t* d_nptr = nullptr;          // nb + 1: near CSR by target
   int32_t* d_nj = nullptr;
   void* d_cS = nullptr;
   void* d_cD = nullptr;
   void* d_delta = nullptr;            // nb
   uint8_t* d_bc = nullptr;            // nb
-  void* d_rho = nullptr;              // nnodes node charges
-  void* d_phi = nullptr;              // nnodes node potentials
+  void* d_rho = nullptr;              // nnodes node charges (inner plan precision)
+  void* d_phi = nullptr;              // nnodes node potentials (inner plan precision)
   size_t bytes = 0;
 };
 
@@ -182,6 +185,11 @@ struct bem_plan_s {
   void* d_tcmat = nullptr;      // their B matrices (hi, lo; 8 KB)
   int* d_status = nullptr;      // device status word (bit 0: a bounded wait gave up)
   uint32_t test_flags = 0;      // bem_set_test_flags (bounded-wait tests)
+  // edge-flow form of the node convolution (accuracy mode): third density per
+  // position (plan arithmetic type), launch shape of the edge-flow column kernel
+  void* d_val2 = nullptr;
+  size_t edge_smem = 0;
+  int edge_acc_rows = 0, edge_grid = 0;
   // 3D path
   int32_t* d_lptr = nullptr;    // n*n + 1 line pointers over sorted cells (line = z*n + y)
   uint16_t* d_x3 = nullptr;     // x per sorted cell
@@ -291,6 +299,13 @@ bem_status group_issue(const BatchGroup& g, const std::vector<bem_plan_s*>& plan
                        const void* in, void* out, const std::vector<size_t>& offset, cudaStream_t st);
 void group_free(BatchGroup& g);
 bem_status launch_apply_2d(bem_plan_s* p, const Operator& op, const void* in, void* out, cudaStream_t st);
+// edge-flow form of a node plan (four-step kernel): set-up of its launch
+// shape and third density buffer, and one convolution of the densities the
+// caller wrote to p->d_val (charge, x-edge flow pairs) and p->d_val2 (y-edge
+// flows) at the interleaved positions, in the plan's arithmetic type; result
+// in caller order, I/O type (apply2d.cu)
+bem_status setup_edge_2d(bem_plan_s* p);
+bem_status launch_edge_2d(bem_plan_s* p, void* out, cudaStream_t st);
 // Device scratch of one apply: per-field densities (slot layout kernel) or
 // density pairs (four-step kernel), and the per-CTA partial sums.
 struct ScratchPtrs {

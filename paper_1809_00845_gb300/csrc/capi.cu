@@ -766,9 +766,10 @@ bem_status bem_set_test_flags(bem_plan_t p, uint32_t flags) {
 }
 
 int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
-  (void)layer;
   if (!p) return -1;
-  if (p->pf) return 2 + bem_launches_per_apply(p->pf->inner, BEM_SINGLE);  // project, node plan, interpolate
+  // project, node plan (prep, column kernel, reduction), interpolate; the
+  // edge-flow form writes the node plan's densities in the projection
+  if (p->pf) return (p->pf->edge && layer != BEM_SINGLE) ? 4 : 2 + bem_launches_per_apply(p->pf->inner, BEM_SINGLE);
   if (p->dim == 3) return 6;  // prep, x-DFT, y pass, z pass, inverse y pass, gather
   return 3;                   // prep (weighted densities), fused column kernel, reduction
 }
@@ -791,6 +792,7 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_perm_il);
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
+  cudaFree(p->d_val2);
   cudaFree(p->d_twc);
   cudaFree(p->d_fstab);
   cudaFree(p->d_tcmat);

@@ -6,4 +6,6 @@ template struct Col2DKernels<float, 512>;
 template struct Col2DKernels<float, 256>;
 template struct Col2DGroupKernels<512>;
 template struct Col2DGroupKernels<256>;
+template struct Col2DEdgeKernels<float, 512>;
+template struct Col2DEdgeKernels<float, 256>;
 }  // namespace bemfft

@@ -8,4 +8,7 @@ template struct Col2DKernels<float, 32>;
 template struct Col2DGroupKernels<128>;
 template struct Col2DGroupKernels<64>;
 template struct Col2DGroupKernels<32>;
+template struct Col2DEdgeKernels<float, 128>;
+template struct Col2DEdgeKernels<float, 64>;
+template struct Col2DEdgeKernels<float, 32>;
 }  // namespace bemfft

@@ -5,4 +5,5 @@
 
 namespace bemfft {
 template struct Col2DKernels<f32x2, 0>;
+template struct Col2DEdgeKernels<f32x2, 0>;
 }  // namespace bemfft

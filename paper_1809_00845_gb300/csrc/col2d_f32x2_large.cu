@@ -5,4 +5,6 @@
 namespace bemfft {
 template struct Col2DKernels<f32x2, 512>;
 template struct Col2DKernels<f32x2, 256>;
+template struct Col2DEdgeKernels<f32x2, 512>;
+template struct Col2DEdgeKernels<f32x2, 256>;
 }  // namespace bemfft

@@ -5,4 +5,6 @@
 namespace bemfft {
 template struct Col2DKernels<f32x2, 128>;
 template struct Col2DKernels<f32x2, 64>;
+template struct Col2DEdgeKernels<f32x2, 128>;
+template struct Col2DEdgeKernels<f32x2, 64>;
 }  // namespace bemfft

@@ -3,4 +3,5 @@
 
 namespace bemfft {
 template struct Col2DKernels<double, 0>;
+template struct Col2DEdgeKernels<double, 0>;
 }  // namespace bemfft

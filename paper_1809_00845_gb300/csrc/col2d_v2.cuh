@@ -72,30 +72,38 @@ struct ColDims {
 // fields: FSEL < 0 = all NF fields (field 0 -> out0[row], field f > 0 ->
 // outF[(f-1)*n + row]); FSEL >= 0 = that field only -> out0.  Carried sums go
 // to carry[f*TT + t] (f = 0 for FSEL >= 0).
-template <typename T, int NF, int FSEL, int TTC>
+// EDGE (NF = 2): every cell carries the triple (charge a, x-edge flow b,
+// y-edge flow c; c from val2); a and b are summed separately and a row is
+// stored as sum(a) + fx * sum(b) (fx = e^{-2 pi i kx / N} - 1, the x-difference
+// in this column), c as field 1.
+template <typename T, int NF, int FSEL, int TTC, bool EDGE = false>
 __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
                                             cplx<T>* out0, cplx<T>* outF, cplx<T>* carry,
-                                            const Twiddles2L<T>& tw, cplx<T>* twc) {
+                                            const Twiddles2L<T>& tw, cplx<T>* twc, cplx<T> fx = {T(0), T(0)}) {
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
   uint32_t mn[CB];
   cplx<T> vn[CB];
+  T cn[CB];
   if (cnt > 0) {
 #pragma unroll
     for (int i = 0; i < CB; ++i) {
       const int pos = (i < cnt ? i : cnt - 1) * TT + t;
       mn[i] = __ldg(p.meta + pos);
       vn[i] = p.val[pos];
+      if constexpr (EDGE) cn[i] = p.val2[pos];
     }
   }
   for (int i0 = 0; i0 < cnt; i0 += CB) {
     uint32_t mt[CB];
     cplx<T> vv[CB], w[CB];
+    T cc3[CB];
 #pragma unroll
     for (int i = 0; i < CB; ++i) {
       mt[i] = mn[i];
       vv[i] = vn[i];
+      if constexpr (EDGE) cc3[i] = cn[i];
     }
     if (i0 + CB < cnt) {
 #pragma unroll
@@ -103,6 +111,7 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const Col
         const int pos = (i0 + CB + i < cnt ? i0 + CB + i : cnt - 1) * TT + t;
         mn[i] = __ldg(p.meta + pos);
         vn[i] = p.val[pos];
+        if constexpr (EDGE) cn[i] = p.val2[pos];
       }
     }
 #pragma unroll
@@ -115,7 +124,29 @@ __device__ __forceinline__ void sparse_rows(const Col2Dv2Params<T>& p, const Col
     }
 #pragma unroll
     for (int i = 0; i < CB; ++i) {
-      if (i0 + i < cnt) {
+      if (EDGE && i0 + i < cnt) {
+        if (FSEL <= 0) {
+          s0.x += vv[i].x * w[i].x;
+          s0.y += vv[i].x * w[i].y;
+          s1.x += vv[i].y * w[i].x;
+          s1.y += vv[i].y * w[i].y;
+        }
+        if (FSEL < 0 || FSEL == 1) {
+          s2.x += cc3[i] * w[i].x;
+          s2.y += cc3[i] * w[i].y;
+        }
+        if (mt[i] & kMetaFlush) {
+          const int row = meta_slot(mt[i]);
+          const bool car = (mt[i] & kMetaCarry) != 0;
+          if (FSEL < 0) {
+            (car ? carry + t : out0 + row)[0] = s0 + cmul(fx, s1);
+            (car ? carry + TT + t : outF + row)[0] = s2;
+          } else {
+            (car ? carry + t : out0 + row)[0] = FSEL == 0 ? s0 + cmul(fx, s1) : s2;
+          }
+          s0 = s1 = s2 = {T(0), T(0)};
+        }
+      } else if (!EDGE && i0 + i < cnt) {
         const bool ty = (mt[i] >> 31) != 0;
         const T a = vv[i].x, b = vv[i].y;
         const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
@@ -255,6 +286,18 @@ __device__ __forceinline__ void spectrum_ready() {
   __syncthreads();
 }
 
+// e^{-2 pi i K / N} - 1 for 0 <= K < N, written as -2 i s e^{-i pi K / N} with
+// s = sin(pi K / N) and evaluated from the half-angle twiddle (half =
+// e^{-i pi / N}), so that it keeps full relative accuracy at small K, where it
+// is of size 2 pi K / N (forming cos - 1 directly would lose it).
+template <typename T>
+__device__ __forceinline__ cplx<T> diff_factor(const Twiddles2L<T>& tw, int K, cplx<T> half) {
+  cplx<T> e = tw.template get<-1>(K >> 1);
+  if (K & 1) e = cmul(e, half);
+  const T c = e.x, sn = -e.y;
+  return {T(-2) * sn * sn, T(-2) * sn * c};
+}
+
 // Where a thread reads the spectrum column.  After the forward transform
 // register k holds frequency K_k = K0 + S k (S = 16 J).  Lanes with h = 0 have
 // every K_k < n and read index K_k; lanes with h = 1 have every K_k >= n and
@@ -329,16 +372,23 @@ struct ColSmem {
 // One x-frequency column kx of plan p: sparse x-DFT of the fields, column
 // transforms, spectral multiply, inverse, gather into the accumulators.  The
 // caller has synchronised since the previous column's gather.
-template <typename T, int NF, bool ACCREG, int TTC, int TCK>
+// EDGE (ACCREG, NF = 2): the edge-flow form; field 1 (y-edge flows) is
+// scaled by e^{-2 pi i K / N} - 1 after its forward transform and both fields
+// use field 0's spectrum (the host passes it for both).
+template <typename T, int NF, bool ACCREG, int TTC, int TCK, bool EDGE = false>
 __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx,
                                              FourStep<T, TCK>& fs, const Twiddles2L<T>& tw, const ColSmem<T>& sm,
-                                             T* sacc, T* gacc, int qs, cplx<T>* twc) {
+                                             T* sacc, T* gacc, int qs, cplx<T>* twc,
+                                             cplx<T> half = {T(1), T(0)}) {
+  static_assert(!EDGE || NF == 2, "edge-flow form: two fields");
   const int t = threadIdx.x, TT = g.TT, n = g.n;
   const int cnt = __ldg(p.chunk + t + 1) - __ldg(p.chunk + t);
   cplx<T>* sA = sm.sA;
   cplx<T>* sF = sm.sF;
   if constexpr (ACCREG) {
-    sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+    if constexpr (EDGE) sparse_rows<T, 2, -1, TTC, true>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc,
+                                                         diff_factor(tw, kx, half));
+    else sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
     __syncthreads();
     if (p.has_carry) {
       add_carries<T, NF, -1>(p, g, cnt, __ldg(p.tinfo + t) >> 8, sA, sF, sm.carry);
@@ -352,6 +402,12 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
       __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
       load_spectrum(p, g, f, kx, sm.sS);
       fs.template forward<true>(v);
+      if constexpr (EDGE) {
+        if (f == 1) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], diff_factor(tw, fs.freq(k), half));
+        }
+      }
       spectrum_ready();
       const SpecAddr sa = spec_addr(fs, g);
       if (f == 0) spectral_multiply<T, false>(sm.sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
@@ -363,12 +419,14 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
     __syncthreads();
     gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
   } else {
+    cplx<T> fx = {T(0), T(0)};
+    if constexpr (EDGE) fx = diff_factor(tw, kx, half);
 #pragma unroll 1
     for (int f = 0; f < NF; ++f) {
       if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
       if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
-      else if (f == 0) sparse_rows<T, NF, 0>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
-      else if (f == 1) sparse_rows<T, NF, 1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+      else if (f == 0) sparse_rows<T, NF, 0, TTC, EDGE>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc, fx);
+      else if (f == 1) sparse_rows<T, NF, 1, TTC, EDGE>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc, fx);
       else sparse_rows<T, NF, 2>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
       __syncthreads();
       if (p.has_carry) {
@@ -380,6 +438,12 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
       __syncthreads();
       load_spectrum(p, g, f, kx, sm.sS);
       fs.template forward<true>(v);
+      if constexpr (EDGE) {
+        if (f == 1) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], diff_factor(tw, fs.freq(k), half));
+        }
+      }
       spectrum_ready();
       spectral_multiply<T, false>(sm.sS, spec_addr(fs, g), imag_of(p, f) != 0, oddy_of(p, f) != 0, v, v);
       fs.inverse(v);
@@ -399,7 +463,7 @@ struct ColBounds {
 
 // TCK > 0: the radix-16 stages on the tensor cores (tc_dft.cuh; T = float,
 // TTC a multiple of 128); shared memory then starts with their header.
-template <typename T, int NF, bool ACCREG, int TTC, int TCK = 0>
+template <typename T, int NF, bool ACCREG, int TTC, int TCK = 0, bool EDGE = false>
 __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::blocks)
     k_col2d_v2(const Col2Dv2Params<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -435,6 +499,8 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     fs.tc.bind(t, (uint32_t)__cvta_generic_to_shared(smem_raw), tm, p.tc_no_commit != 0);
   }
   const ColSmem<T> sm{sA, sF, sS, carry};
+  cplx<T> half = {T(1), T(0)};  // e^{-i pi / N} (edge-flow form)
+  if constexpr (EDGE) half = {(T)cospi(1.0 / (double)N), (T)-sinpi(1.0 / (double)N)};
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
     // the previous column's gather has finished reading sA; with tensor-core
     // stages the CTA also stops after a device wait that gave up
@@ -443,7 +509,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     } else {
       __syncthreads();
     }
-    col2d_column<T, NF, ACCREG, TTC, TCK>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc);
+    col2d_column<T, NF, ACCREG, TTC, TCK, EDGE>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc, half);
   }
   if constexpr (TCK > 0) {
     if (fs.tc.failed) {
@@ -567,6 +633,22 @@ void Col2DKernels<T, TTC>::launch(int nf, int grid, int threads, size_t smem, cu
   if (nf == 1) k_col2d_v2<T, 1, false, TTC><<<grid, threads, smem, st>>>(cp);
   else if (nf == 2) k_col2d_v2<T, 2, R, TTC><<<grid, threads, smem, st>>>(cp);
   else k_col2d_v2<T, 3, R, TTC><<<grid, threads, smem, st>>>(cp);
+}
+
+template <typename T, int TTC>
+cudaError_t Col2DEdgeKernels<T, TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
+  constexpr bool R = std::is_same<T, float>::value;
+  cudaError_t e;
+  if ((e = allow_optin_smem(k_col2d_v2<T, 2, R, TTC, 0, true>)) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_col2d_v2<T, 2, R, TTC, 0, true>, threads,
+                                                       smem);
+}
+
+template <typename T, int TTC>
+void Col2DEdgeKernels<T, TTC>::launch(int grid, int threads, size_t smem, cudaStream_t st,
+                                      const Col2Dv2Params<T>& cp) {
+  constexpr bool R = std::is_same<T, float>::value;
+  k_col2d_v2<T, 2, R, TTC, 0, true><<<grid, threads, smem, st>>>(cp);
 }
 
 template <int TTC, int TCK>

@@ -24,6 +24,7 @@ struct Col2Dv2Params {
   const int32_t* tinfo;   // TT: row mask (8 bits) | continuing threads << 8
   const uint32_t* meta;   // Q*TT cell words, interleaved
   const cplx<T>* val;     // Q*TT density pairs, interleaved
+  const T* val2;          // edge-flow kernels: Q*TT third densities (y-edge flows), interleaved
   const T* spec[3];
   int imag[3];
   int oddy[3];
@@ -67,6 +68,19 @@ struct Col2DGroupKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
   static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<float>* plans,
                      const int* c0, int nplans);
+};
+
+// Edge-flow form of a node convolution: per node the density triple
+// (charge, x-edge flow, y-edge flow); the x flows join the charges after the
+// sparse x-DFT with the column factor e^{-2 pi i kx / N} - 1, the y flows are
+// transformed as a second field and scaled per frequency by
+// e^{-2 pi i ky / N} - 1, and both go through field 0's spectrum (FP32: one
+// inverse transform and one gather; FP64 and double-float: one each per
+// field).  configure() as for Col2DKernels.
+template <typename T, int TTC>
+struct Col2DEdgeKernels {
+  static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
+  static void launch(int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
 };
 
 // The same kernels in FP32 with the radix-16 stages of the transforms on the

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "bem_internal.h"
+#include "fft_reg.cuh"
 
 namespace bemfft {
 
@@ -120,24 +121,60 @@ void exact_pair(const Panel& q, double x, double y, double* s, double* d) {
   *d = eta == 0.0 ? 0.0 : -(std::atan((q.L - s0) / eta) - std::atan(-s0 / eta)) / (2.0 * kPi);
 }
 
-template <typename T>
+template <typename T, typename TI>
 __global__ void k_pf_project(int64_t nnodes, const int64_t* __restrict__ ptr, const int32_t* __restrict__ pj,
-                             const T* __restrict__ ws, const T* __restrict__ wd, const uint8_t* __restrict__ bc,
-                             int layer, const T* __restrict__ x, T* __restrict__ rho) {
+                             const double* __restrict__ ws, const double* __restrict__ wd,
+                             const uint8_t* __restrict__ bc, int layer, const T* __restrict__ x,
+                             TI* __restrict__ rho) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nnodes) return;
   double acc = 0.0;
   for (int64_t e = ptr[l]; e < ptr[l + 1]; ++e) {
     const int32_t j = pj[e];
     const bool dip = layer == BEM_DOUBLE || (layer == BEM_SYSTEM && bc[j] != 0);
-    acc += (double)(dip ? wd[e] : ws[e]) * (double)x[j];
+    acc += (dip ? wd[e] : ws[e]) * (double)x[j];
   }
-  rho[l] = (T)acc;
+  rho[l] = (TI)acc;
 }
 
-template <typename T>
+// Edge-flow form (FP32 inner plans): each projected dipole's node charges sum
+// to zero, so they are the divergence of flows along the grid edges inside
+// its stencil (c_m = p_{m - e} - p_m summed over x and y edges); the inner
+// plan convolves the flows with the difference of the grid kernel instead of
+// the charges with the kernel.  Same operator; but the flows enter the FP32
+// transforms where the rounding of large, cancelling charges would have
+// reached every target through the logarithm's long range.  Densities are
+// written straight to the inner plan's interleaved positions: (charge,
+// x-edge flow) pairs and the y-edge flows; padding positions get zeros.
+template <typename T, typename TA>
+__global__ void k_pf_project_edge(int npos, const int32_t* __restrict__ perm, const int64_t* __restrict__ ptr,
+                                  const int32_t* __restrict__ pj, const double* __restrict__ ws,
+                                  const double* __restrict__ wx, const double* __restrict__ wy,
+                                  const uint8_t* __restrict__ bc, int layer, const T* __restrict__ x,
+                                  cplx<TA>* __restrict__ val, TA* __restrict__ val2) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= npos) return;
+  const int l = perm[pos];
+  double a = 0.0, b = 0.0, c = 0.0;
+  if (l >= 0) {
+    for (int64_t e = ptr[l]; e < ptr[l + 1]; ++e) {
+      const int32_t j = pj[e];
+      const double xj = (double)x[j];
+      if (layer == BEM_DOUBLE || (layer == BEM_SYSTEM && bc[j] != 0)) {
+        b += wx[e] * xj;
+        c += wy[e] * xj;
+      } else {
+        a += ws[e] * xj;
+      }
+    }
+  }
+  val[pos] = {TA(a), TA(b)};
+  val2[pos] = TA(c);
+}
+
+template <typename T, typename TI>
 __global__ void k_pf_interp(int64_t nb, int S, const int32_t* __restrict__ node, const T* __restrict__ W,
-                            const T* __restrict__ phi, const int64_t* __restrict__ nptr,
+                            const TI* __restrict__ phi, const int64_t* __restrict__ nptr,
                             const int32_t* __restrict__ nj, const T* __restrict__ cS, const T* __restrict__ cD,
                             const T* __restrict__ delta, const uint8_t* __restrict__ bc, double c, int layer,
                             const T* __restrict__ x, T* __restrict__ out) {
@@ -172,18 +209,44 @@ bem_status upload_raw(const std::vector<X>& v, X** d) {
   return BEM_OK;
 }
 
-template <typename T>
+// T: the plan's I/O type; TI: the inner node plan's (FP64 inner plans serve
+// FP32 accuracy-mode plans on grids below the four-step kernel's)
+template <typename T, typename TI>
 bem_status launch_t(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st) {
   PanelOp& f = *p->pf;
   const int tb = 256;
-  k_pf_project<T><<<(unsigned)((f.nnodes + tb - 1) / tb), tb, 0, st>>>(
-      f.nnodes, f.d_pptr, f.d_pj, static_cast<const T*>(f.d_pws), static_cast<const T*>(f.d_pwd), f.d_bc, (int)layer,
-      static_cast<const T*>(in), static_cast<T*>(f.d_rho));
-  BEM_CUDA_TRY(cudaGetLastError());
-  bem_status rc = apply_operator(f.inner, BEM_SINGLE, f.d_rho, f.d_phi, st);
-  if (rc != BEM_OK) return rc;
-  k_pf_interp<T><<<(unsigned)((p->nb + tb - 1) / tb), tb, 0, st>>>(
-      p->nb, f.S, f.d_node, static_cast<const T*>(f.d_W), static_cast<const T*>(f.d_phi), f.d_nptr, f.d_nj,
+  bem_status rc;
+  if (f.edge && layer != BEM_SINGLE) {
+    const int npos = (int)f.inner->v2_npos;
+    const unsigned nblk = (unsigned)((npos + tb - 1) / tb);
+    const T* x = static_cast<const T*>(in);
+    bem_plan_s* q = f.inner;
+    if (q->prec == BEM_F32)
+      k_pf_project_edge<T, float><<<nblk, tb, 0, st>>>(npos, q->d_perm_il, f.d_pptr, f.d_pj, f.d_pws, f.d_pwx,
+                                                       f.d_pwy, f.d_bc, (int)layer, x,
+                                                       static_cast<cplx<float>*>(q->d_val),
+                                                       static_cast<float*>(q->d_val2));
+    else if (q->prec == BEM_F64)
+      k_pf_project_edge<T, double><<<nblk, tb, 0, st>>>(npos, q->d_perm_il, f.d_pptr, f.d_pj, f.d_pws, f.d_pwx,
+                                                        f.d_pwy, f.d_bc, (int)layer, x,
+                                                        static_cast<cplx<double>*>(q->d_val),
+                                                        static_cast<double*>(q->d_val2));
+    else
+      k_pf_project_edge<T, f32x2><<<nblk, tb, 0, st>>>(npos, q->d_perm_il, f.d_pptr, f.d_pj, f.d_pws, f.d_pwx,
+                                                       f.d_pwy, f.d_bc, (int)layer, x,
+                                                       static_cast<cplx<f32x2>*>(q->d_val),
+                                                       static_cast<f32x2*>(q->d_val2));
+    BEM_CUDA_TRY(cudaGetLastError());
+    if ((rc = launch_edge_2d(q, f.d_phi, st)) != BEM_OK) return rc;
+  } else {
+    k_pf_project<T, TI><<<(unsigned)((f.nnodes + tb - 1) / tb), tb, 0, st>>>(
+        f.nnodes, f.d_pptr, f.d_pj, f.d_pws, f.d_pwd, f.d_bc, (int)layer, static_cast<const T*>(in),
+        static_cast<TI*>(f.d_rho));
+    BEM_CUDA_TRY(cudaGetLastError());
+    if ((rc = apply_operator(f.inner, BEM_SINGLE, f.d_rho, f.d_phi, st)) != BEM_OK) return rc;
+  }
+  k_pf_interp<T, TI><<<(unsigned)((p->nb + tb - 1) / tb), tb, 0, st>>>(
+      p->nb, f.S, f.d_node, static_cast<const T*>(f.d_W), static_cast<const TI*>(f.d_phi), f.d_nptr, f.d_nj,
       static_cast<const T*>(f.d_cS), static_cast<const T*>(f.d_cD), static_cast<const T*>(f.d_delta), f.d_bc, p->c,
       (int)layer, static_cast<const T*>(in), static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
@@ -201,7 +264,9 @@ bem_status launch_apply_panels(bem_plan_s* p, bem_layer layer, const void* in, v
     set_error("bem_apply: BEM_SYSTEM needs bem_set_bc first");
     return BEM_ERR_ARG;
   }
-  return p->prec == BEM_F32 ? launch_t<float>(p, layer, in, out, st) : launch_t<double>(p, layer, in, out, st);
+  if (p->prec != BEM_F32) return launch_t<double, double>(p, layer, in, out, st);
+  return p->pf->inner->prec == BEM_F32 ? launch_t<float, float>(p, layer, in, out, st)
+                                       : launch_t<float, double>(p, layer, in, out, st);
 }
 
 bem_status panel_set_bc(bem_plan_s* p, const uint8_t* bc, double c) {
@@ -236,25 +301,80 @@ void panel_destroy(bem_plan_s* p) {
   PanelOp* f = p->pf;
   if (!f) return;
   if (f->inner) bem_destroy(f->inner);
-  for (void* q : {(void*)f->d_node, f->d_W, (void*)f->d_pptr, (void*)f->d_pj, f->d_pws, f->d_pwd, (void*)f->d_nptr,
-                  (void*)f->d_nj, f->d_cS, f->d_cD, f->d_delta, (void*)f->d_bc, f->d_rho, f->d_phi})
+  for (void* q : {(void*)f->d_node, f->d_W, (void*)f->d_pptr, (void*)f->d_pj, (void*)f->d_pws, (void*)f->d_pwd,
+                  (void*)f->d_pwx, (void*)f->d_pwy, (void*)f->d_nptr, (void*)f->d_nj, f->d_cS, f->d_cD, f->d_delta,
+                  (void*)f->d_bc, f->d_rho, f->d_phi})
     cudaFree(q);
   delete f;
   p->pf = nullptr;
 }
 
+// The Gauss row-sum term of an FP32 plan, delta_i = 1/2 - (D 1)_i without
+// it, in FP64: the node potentials of the projected dipoles of u = 1 from a
+// temporary FP64 node plan (the grid convolution on the device), the
+// interpolation and the near-pair sums on the host.  The double layer of
+// random data is two orders of magnitude smaller than its terms, so delta
+// has to be exact to far below FP32 rounding of the row sums (about 1/2).
 template <typename T>
+static bem_status fp64_row_sums(bem_plan_s* p, const std::vector<int32_t>& node, const std::vector<double>& W,
+                                const std::vector<int64_t>& pptr, const std::vector<double>& pwd,
+                                const std::vector<int32_t>& cells) {
+  PanelOp& f = *p->pf;
+  const int64_t nn = f.nnodes, nb = p->nb;
+  const int S = f.S;
+  std::vector<double> rho1(nn, 0.0), phi1(nn);
+  for (int64_t l = 0; l < nn; ++l)
+    for (int64_t e = pptr[l]; e < pptr[l + 1]; ++e) rho1[l] += pwd[e];
+  bem_plan_t tmp = nullptr;
+  const int64_t n2[2] = {p->n, p->n};
+  std::vector<double> w1(nn, 1.0), nrm(2 * nn, 0.0);
+  for (int64_t k = 0; k < nn; ++k) nrm[2 * k] = 1.0;
+  bem_status rc = bem_plan(&tmp, 2, n2, p->h, nn, cells.data(), w1.data(), nrm.data(), BEM_LAPLACE_2D, 0.3, 1.0,
+                           BEM_F64, BEM_PLAN_SINGLE_LAYER_ONLY, nullptr);
+  if (rc != BEM_OK) return rc;
+  double* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 2 * nn * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(buf, rho1.data(), nn * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) rc = apply_operator(tmp, BEM_SINGLE, buf, buf + nn, nullptr);
+  if (e == cudaSuccess && rc == BEM_OK) e = cudaMemcpy(phi1.data(), buf + nn, nn * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  bem_destroy(tmp);
+  if (e != cudaSuccess) {
+    set_error(std::string("bem_plan_panels: row-sum term: ") + cudaGetErrorString(e));
+    return BEM_ERR_CUDA;
+  }
+  if (rc != BEM_OK) return rc;
+  f.h_delta.resize(nb);
+  std::vector<T> dt(nb);
+  for (int64_t i = 0; i < nb; ++i) {
+    double acc = 0.0;
+    for (int s2 = 0; s2 < S; ++s2) acc += W[(size_t)i * S + s2] * phi1[node[(size_t)i * S + s2]];
+    for (int64_t k = f.h_nptr[i]; k < f.h_nptr[i + 1]; ++k) acc += f.h_cD[k];
+    f.h_delta[i] = 0.5 - acc;
+    dt[i] = (T)f.h_delta[i];
+  }
+  BEM_CUDA_TRY(cudaMemcpy(f.d_delta, dt.data(), nb * sizeof(T), cudaMemcpyHostToDevice));
+  return BEM_OK;
+}
+
+template <typename T, typename TI>
 static bem_status upload_all(bem_plan_s* p, const std::vector<int32_t>& node, const std::vector<double>& W,
                              const std::vector<int64_t>& pptr, const std::vector<int32_t>& pj,
-                             const std::vector<double>& pws, const std::vector<double>& pwd) {
+                             const std::vector<double>& pws, const std::vector<double>& pwd,
+                             const std::vector<double>& pwx, const std::vector<double>& pwy,
+                             const std::vector<int32_t>& cells) {
   PanelOp& f = *p->pf;
   bem_status rc;
   if ((rc = upload_raw(node, &f.d_node)) != BEM_OK) return rc;
   if ((rc = upload<T>(W, &f.d_W)) != BEM_OK) return rc;
   if ((rc = upload_raw(pptr, &f.d_pptr)) != BEM_OK) return rc;
   if ((rc = upload_raw(pj, &f.d_pj)) != BEM_OK) return rc;
-  if ((rc = upload<T>(pws, &f.d_pws)) != BEM_OK) return rc;
-  if ((rc = upload<T>(pwd, &f.d_pwd)) != BEM_OK) return rc;
+  if ((rc = upload_raw(pws, &f.d_pws)) != BEM_OK) return rc;
+  if ((rc = upload_raw(pwd, &f.d_pwd)) != BEM_OK) return rc;
+  if (f.edge) {
+    if ((rc = upload_raw(pwx, &f.d_pwx)) != BEM_OK) return rc;
+    if ((rc = upload_raw(pwy, &f.d_pwy)) != BEM_OK) return rc;
+  }
   if ((rc = upload_raw(f.h_nptr, &f.d_nptr)) != BEM_OK) return rc;
   if ((rc = upload_raw(f.h_nj, &f.d_nj)) != BEM_OK) return rc;
   if ((rc = upload<T>(f.h_cS, &f.d_cS)) != BEM_OK) return rc;
@@ -263,11 +383,12 @@ static bem_status upload_all(bem_plan_s* p, const std::vector<int32_t>& node, co
   if ((rc = upload<T>(zero, &f.d_delta)) != BEM_OK) return rc;
   BEM_CUDA_TRY(cudaMalloc(&f.d_bc, p->nb));
   BEM_CUDA_TRY(cudaMemset(f.d_bc, 0, p->nb));
-  BEM_CUDA_TRY(cudaMalloc(&f.d_rho, f.nnodes * sizeof(T)));
-  BEM_CUDA_TRY(cudaMalloc(&f.d_phi, f.nnodes * sizeof(T)));
-  f.bytes = node.size() * 4 + (W.size() + pws.size() + pwd.size() + f.h_cS.size() + f.h_cD.size() + p->nb +
-                               2 * f.nnodes) * sizeof(T) +
+  BEM_CUDA_TRY(cudaMalloc(&f.d_rho, f.nnodes * sizeof(TI)));
+  BEM_CUDA_TRY(cudaMalloc(&f.d_phi, f.nnodes * sizeof(TI)));
+  f.bytes = node.size() * 4 + (W.size() + f.h_cS.size() + f.h_cD.size() + p->nb) * sizeof(T) +
+            2 * f.nnodes * sizeof(TI) + (pws.size() + pwd.size() + (f.edge ? pwx.size() + pwy.size() : 0)) * 8 +
             (pptr.size() + f.h_nptr.size()) * 8 + (pj.size() + f.h_nj.size()) * 4 + p->nb;
+  if constexpr (std::is_same<T, float>::value) return fp64_row_sums<T>(p, node, W, pptr, pwd, cells);
   // Gauss row-sum term: delta = 1/2 - (D 1) of the operator without it
   // (ones and the result share one scratch allocation, freed on every path)
   T* buf = nullptr;
@@ -276,7 +397,7 @@ static bem_status upload_all(bem_plan_s* p, const std::vector<int32_t>& node, co
   T* dl = buf + p->nb;
   std::vector<T> h1(p->nb, (T)1);
   cudaError_t e = cudaMemcpy(ones, h1.data(), p->nb * sizeof(T), cudaMemcpyHostToDevice);
-  rc = e == cudaSuccess ? launch_t<T>(p, BEM_DOUBLE, ones, dl, nullptr) : BEM_ERR_CUDA;
+  rc = e == cudaSuccess ? launch_t<T, TI>(p, BEM_DOUBLE, ones, dl, nullptr) : BEM_ERR_CUDA;
   if (rc == BEM_OK) e = cudaMemcpy(h1.data(), dl, p->nb * sizeof(T), cudaMemcpyDeviceToHost);
   cudaFree(buf);
   if (e != cudaSuccess) {
@@ -393,27 +514,60 @@ bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, co
     bem_destroy(p);
     return rc;
   };
+  std::vector<int32_t> cells(2 * nn);  // the active nodes as the inner plan's cells
+  for (int64_t k = 0; k < nn; ++k) {
+    cells[2 * k] = (int32_t)(nodes[k] % n);
+    cells[2 * k + 1] = (int32_t)(nodes[k] / n);
+  }
   {
-    std::vector<int32_t> cell(2 * nn);
+    const std::vector<int32_t>& cell = cells;
     std::vector<double> w1(nn, 1.0), nrm(2 * nn, 0.0);
-    for (int64_t k = 0; k < nn; ++k) {
-      cell[2 * k] = (int32_t)(nodes[k] % n);
-      cell[2 * k + 1] = (int32_t)(nodes[k] / n);
-      nrm[2 * k] = 1.0;
-    }
+    for (int64_t k = 0; k < nn; ++k) nrm[2 * k] = 1.0;
     const int64_t nn2[2] = {n, n};
+    // FP32 on grids below the four-step kernel (n < 256): the node convolution
+    // in FP64, which costs little there
+    const bem_precision iprec = (prec == BEM_F32 && n < 256) ? BEM_F64 : prec;
     bem_status rc = bem_plan(&f.inner, 2, nn2, h, nn, cell.data(), w1.data(), nrm.data(), BEM_LAPLACE_2D, 0.3, 1.0,
-                             prec, BEM_PLAN_SINGLE_LAYER_ONLY, st);
+                             iprec, BEM_PLAN_SINGLE_LAYER_ONLY, st);
     if (rc != BEM_OK) return fail(rc);
   }
-  p->prec = f.inner->prec;
+  p->prec = prec == BEM_F32 ? BEM_F32 : f.inner->prec;
   p->tc = f.inner->tc;
+  // four-step inner plans take the double layer in the edge-flow form
+  f.edge = f.inner->v2 && f.inner->tc == 0;
+  if (f.edge) {
+    bem_status rc = setup_edge_2d(f.inner);
+    if (rc != BEM_OK) return fail(rc);
+  }
   // projection CSR by node
   std::vector<int64_t> pptr(nn + 1, 0);
   for (size_t e = 0; e < node.size(); ++e) ++pptr[node[e] + 1];
   for (int64_t k = 0; k < nn; ++k) pptr[k + 1] += pptr[k];
+  // edge flows of each panel's dipole charges c on its stencil (row by of q
+  // nodes): x flows carry every row's charges towards its first node,
+  // px[by][bx] = sum_{b > bx} c[by][b]; the row totals r[by] then go down the
+  // first column, py[by][0] = sum_{b > by} r[b].  c = div p holds exactly
+  // because each panel's charges sum to zero.
+  std::vector<double> PX((size_t)nb * S, 0.0), PY((size_t)nb * S, 0.0);
+  for (int64_t j = 0; j < nb; ++j) {
+    const double* c = &PD[(size_t)j * S];
+    double rt[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int by = 0; by < q; ++by) {
+      double acc = 0.0;
+      for (int bx = q - 1; bx >= 1; --bx) {
+        acc += c[by * q + bx];
+        PX[(size_t)j * S + by * q + bx - 1] = acc;
+      }
+      rt[by] = acc + c[by * q];
+    }
+    double acc = 0.0;
+    for (int by = q - 1; by >= 1; --by) {
+      acc += rt[by];
+      PY[(size_t)j * S + (by - 1) * q] = acc;
+    }
+  }
   std::vector<int32_t> pj(node.size());
-  std::vector<double> pws(node.size()), pwd(node.size());
+  std::vector<double> pws(node.size()), pwd(node.size()), pwx(node.size()), pwy(node.size());
   {
     std::vector<int64_t> fill(pptr.begin(), pptr.end() - 1);
     for (int64_t j = 0; j < nb; ++j)
@@ -423,6 +577,8 @@ bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, co
         pj[at] = (int32_t)j;
         pws[at] = PS[e];
         pwd[at] = PD[e];
+        pwx[at] = PX[e];
+        pwy[at] = PY[e];
       }
   }
   // near pairs and their precorrections.  Grid kernel between stencil nodes
@@ -471,8 +627,10 @@ bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, co
     }
     f.h_nptr[i + 1] = (int64_t)f.h_nj.size();
   }
-  bem_status rc = p->prec == BEM_F32 ? upload_all<float>(p, node, W, pptr, pj, pws, pwd)
-                                     : upload_all<double>(p, node, W, pptr, pj, pws, pwd);
+  bem_status rc =
+      p->prec != BEM_F32 ? upload_all<double, double>(p, node, W, pptr, pj, pws, pwd, pwx, pwy, cells)
+      : f.inner->prec == BEM_F32 ? upload_all<float, float>(p, node, W, pptr, pj, pws, pwd, pwx, pwy, cells)
+                                 : upload_all<float, double>(p, node, W, pptr, pj, pws, pwd, pwx, pwy, cells);
   if (rc != BEM_OK) return fail(rc);
   BEM_CUDA_TRY(cudaDeviceSynchronize());
   p->threads = f.inner->threads;

@@ -4,17 +4,12 @@ Parity: the GPU apply equals the oracle's grid-accelerated operator (dense,
 built from its definition: exact near pairs, projected moments through the
 grid kernel, interpolation, Gauss row-sum term) to 1e-12 relative L2 in FP64
 and double-float, on random densities, for the single, double and
-boundary-condition-split operators.  FP32: the single layer is held to
-2e-6.  A projected dipole is a set of node charges of size ~L/h ~ 1 that sum
-to zero; rounding them (and the convolution) to FP32 leaves a monopole of
-relative size ~eps32 per charge, whose log potential reaches every target,
-while the dipole field decays like h/d.  Over nb random panels the leaks add
-like a random walk, so the double-layer and system bound is
-    max(2e-6, 4 eps32 sqrt(nb) ln N)
-(measured 7e-6 .. 1.2e-5 at nb = 141 .. 693 against 1.4e-5 .. 3.9e-5);
-FP32 solves reach FP64-level residuals through double-float refinement; on grids served by both column kernels
-(n = 64, 128: one CTA per column; n = 256: four-step) and both stencil
-orders.  Accuracy: solves reach the flux of the analytic field to the error
+boundary-condition-split operators.  FP32: every layer is held to 2e-6 (the
+projected dipoles enter the FP32 transforms as edge flows with the
+difference of the grid kernel, and grids below the four-step kernel convolve
+the node charges in FP64); FP32 solves reach FP64-level residuals through
+double-float refinement; on grids served by both column kernels (n = 64,
+128: one CTA per column; n = 256: four-step) and both stencil orders.  Accuracy: solves reach the flux of the analytic field to the error
 the oracle's own accelerated solve has, far below the paper-form operator's.
 """
 import numpy as np
@@ -65,16 +60,14 @@ def test_panel_apply_matches_oracle(torch_cuda, prec, n, curve, order, R):
     bc = (rng.uniform(size=b.nb) < 0.5).astype(np.uint8)
     S, D = PO.accelerated_matrices(b.panels, b.h, order, R)
     A = PO.system(S, D, bc)
-    leak = max(2e-6, 4 * 2.0 ** -24 * np.sqrt(b.nb) * np.log(2 * n))
     plan = _plan(b, prec, order, R)
     plan.set_bc(bc, 0.5)
-    errs, bounds = {}, {}
+    errs = {}
     for layer, M in (("single", S), ("double", D), ("system", A)):
         errs[layer] = rel_l2(gpu_apply(torch_cuda, plan, layer, x), M @ x)
-        bounds[layer] = TOL[prec] if prec != "f32" or layer == "single" else leak
-    print(f"{prec} n={n} nb={b.nb} p={order} R={R}: errors {errs} bounds {bounds}")
+    print(f"{prec} n={n} nb={b.nb} p={order} R={R}: errors {errs} bound {TOL[prec]}")
     for layer, e in errs.items():
-        assert e <= bounds[layer], (layer, e, bounds[layer])
+        assert e <= TOL[prec], (layer, e, TOL[prec])
 
 
 def test_panel_info_and_rejections(torch_cuda):
@@ -188,20 +181,27 @@ def test_panel_apply_full_size_star_sampled_rows(torch_cuda, prec):
     """The benchmark's accuracy-mode workload (the star at n = 4096 as 11,081
     panels, order 3, R = 5, mixed conditions) in its launch configuration,
     against the oracle's row-wise accelerated operator on 3 x 40 sampled
-    targets: 1e-12 in FP64; in FP32 2e-6 for the single layer and the
-    projected-dipole bound for the system operator."""
+    targets: 1e-12 in FP64, 2e-6 in FP32; single layer and system operator on
+    random densities, the double layer on the smooth density e^x cos y.  (The
+    double layer of random data is about 150 times smaller than the terms it
+    sums at this size, so there the oracle's own FP64 sums carry 4e-12; its
+    error is printed, not gated.)"""
     b = I.curve_panels(4096, I.star_curve(0.3, 0.3, 5))
     bc = (np.asarray(b.param) >= np.pi).astype(np.uint8)
     rng = np.random.default_rng(4096)
     x = rng.standard_normal(b.nb)
+    u_smooth, _ = I.panel_data(b, I.field_expcos)
     plan = _plan(b, prec, 3, 5)
     plan.set_bc(bc, 0.5)
     rows = np.concatenate([np.arange(0, 40), np.arange(b.nb // 2, b.nb // 2 + 40), np.arange(b.nb - 40, b.nb)])
-    leak = max(2e-6, 4 * 2.0 ** -24 * np.sqrt(b.nb) * np.log(2 * 4096))
-    for layer in ("single", "system"):
-        ref = PO.accelerated_rows(b.panels, b.h, 3, 5, x, rows, layer, bc)
-        out = gpu_apply(torch_cuda, plan, layer, x)[rows]
+    bound = 1e-12 if prec == "f64" else 2e-6
+    for layer, dens, gated in (("single", x, True), ("system", x, True), ("double", u_smooth, True),
+                               ("double", x, False)):
+        ref = PO.accelerated_rows(b.panels, b.h, 3, 5, dens, rows, layer, bc)
+        out = gpu_apply(torch_cuda, plan, layer, dens)[rows]
         err = rel_l2(out, ref)
-        bound = 1e-12 if prec == "f64" else (2e-6 if layer == "single" else leak)
-        print(f"{prec} star 4096 panels {layer}: rel L2 {err:.3e} (bound {bound:.1e})")
-        assert err <= bound, (layer, err)
+        what = "random" if dens is x else "smooth"
+        print(f"{prec} star 4096 panels {layer} ({what} density): rel L2 {err:.3e}"
+              + (f" (bound {bound:.1e})" if gated else " (not gated)"))
+        if gated:
+            assert err <= bound, (layer, what, err)
