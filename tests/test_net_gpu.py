@@ -36,11 +36,47 @@ def test_forward_and_gradient_match_oracle(torch_cuda, shape):
     p = net.get_params().astype(np.float64)
     y_gpu = net.forward(f, off).cpu().numpy()
     y_ref, _ = N.forward(p, f, off, cin, h, L, K, list(dil))
-    assert np.linalg.norm(y_gpu - y_ref) / np.linalg.norm(y_ref) < 2e-3
+    e_fwd = np.linalg.norm(y_gpu - y_ref) / np.linalg.norm(y_ref)
     loss_gpu, g_gpu = net.gradient(f, off, tg)
     loss_ref, g_ref = N.loss_and_grad(p, f, off, tg, cin, h, L, K, list(dil))
-    assert abs(loss_gpu - loss_ref) / loss_ref < 2e-3
-    assert np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref) < 1e-2
+    e_loss = abs(loss_gpu - loss_ref) / loss_ref
+    e_grad = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    print(f"network {shape}: forward {e_fwd:.2e}, loss {e_loss:.2e}, gradient {e_grad:.2e}")
+    assert e_fwd < 1e-3 and e_loss < 1e-3 and e_grad < 1e-3, (e_fwd, e_loss, e_grad)
+
+
+def test_cuda_gradient_matches_finite_differences(torch_cuda):
+    """The CUDA gradient against the CUDA loss itself: directional derivatives
+    g . d along random parameter directions against the slope at t = 0 of a
+    quadratic fitted to the loss over t in [-tau, tau] (9 points; tau moves the
+    weights by about 2% so that the BF16 rounding of weights and activations
+    averages out).  Independent of the oracle.  The loss of a BF16 network is
+    a step function of the weights, and the backward pass treats each rounding
+    as the identity, so the two differ by a few per cent even in exact
+    arithmetic: the FP64 oracle with the same rounding points shows 1.6-5.3%
+    with this procedure (and 0.4-2% without rounding, from the ReLU kinks),
+    hence the 10% bar; the tight check of the gradient is the oracle parity
+    above (1e-3)."""
+    net = _net(3, 16, 3, 5, (1, 2, 4), seed=5)
+    rng = np.random.default_rng(21)
+    off = np.array([0, 150, 400], np.int32)
+    f = rng.standard_normal((400, 3)).astype(np.float32)
+    tg = rng.standard_normal(400).astype(np.float32)
+    p0 = net.get_params().astype(np.float64)
+    _, g = net.gradient(f, off, tg)
+    ts = np.linspace(-1.0, 1.0, 9)
+    for k in range(4):
+        d = rng.standard_normal(p0.size) * np.abs(p0)
+        tau = 0.02
+        losses = []
+        for t in ts:
+            net.set_params((p0 + tau * t * d).astype(np.float32))
+            losses.append(net.gradient(f, off, tg)[0])
+        net.set_params(p0.astype(np.float32))
+        slope = np.polyfit(tau * ts, np.asarray(losses), 2)[1]  # derivative at t = 0 of the quadratic fit
+        gd = float(g.astype(np.float64) @ d)
+        print(f"direction {k}: finite differences {slope:.6e}, gradient {gd:.6e}")
+        assert abs(slope - gd) <= 0.1 * abs(gd) + 1e-6, (slope, gd)
 
 
 def test_adam_steps_reduce_loss(torch_cuda):
