@@ -398,6 +398,14 @@ bem_status bem_net_gradient(bem_net_t net, const float* feats, const int32_t* of
 bem_status bem_net_train_step(bem_net_t net, const float* feats, const int32_t* offsets, int nseq, int64_t T,
                               const float* target, float lr, double* loss, void* stream);
 
+/* Arithmetic peak of the current device for the rooflines of the column
+ * kernels, measured with a timed loop of independent fused multiply-adds
+ * (CUDA events on `stream`, which the call synchronises; no clock or device
+ * setting is changed).  kind 0: FP32 FMA, 1: FP64 FMA, 2: packed FP32 pairs
+ * (two FMAs per instruction).  *tflops receives TFLOP/s (2 flops per FMA).
+ * No counterpart in the paper: a measurement helper. */
+bem_status bem_measure_peak(int kind, double* tflops, void* stream);
+
 bem_status bem_destroy(bem_plan_t plan);
 const char* bem_status_string(bem_status s);
 const char* bem_last_error(void);

@@ -36,7 +36,8 @@ EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
             "bem_batch_apply", "bem_batch_set_grouping", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
             "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
-            "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step"]
+            "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step",
+            "bem_measure_peak"]
 
 
 class BemError(RuntimeError):
@@ -123,6 +124,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("bem_net_create", "bem_net_destroy", "bem_net_get_params", "bem_net_set_params", "bem_net_forward",
                  "bem_net_gradient", "bem_net_train_step"):
         getattr(lib, name).restype = I
+    lib.bem_measure_peak.argtypes = [I, ctypes.POINTER(D), P]
+    lib.bem_measure_peak.restype = I
     lib.bem_last_error.argtypes = []
     lib.bem_last_error.restype = ctypes.c_char_p
     for name in ("bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner", "bem_enable_refinement", "bem_apply",
@@ -546,6 +549,15 @@ class Net:
                                                  ctypes.c_void_p(t.data_ptr()), float(lr), ctypes.byref(loss),
                                                  _stream_ptr(stream)))
         return loss.value
+
+
+def measure_peak(kind="fp32", stream=None):
+    """Measured arithmetic peak of the current GPU in TFLOP/s (bem_measure_peak):
+    kind "fp32", "fp64" or "fp32x2" (packed pairs)."""
+    k = {"fp32": 0, "fp64": 1, "fp32x2": 2}[kind]
+    out = ctypes.c_double()
+    _check(load_library().bem_measure_peak(k, ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def bem_plan(dim, n, h, cell, w, normal, kernel="laplace2d", precision="f32", nu=0.3, mu=1.0, stream=None):

@@ -533,8 +533,10 @@ bem_status panel_plan_impl(bem_plan_s** out, int64_t n, double h, int64_t nb, co
   }
   p->prec = prec == BEM_F32 ? BEM_F32 : f.inner->prec;
   p->tc = f.inner->tc;
-  // four-step inner plans take the double layer in the edge-flow form
-  f.edge = f.inner->v2 && f.inner->tc == 0;
+  // FP32 four-step inner plans take the double layer in the edge-flow form
+  // (FP64 and double-float convolve the charges to 1e-13 already; the edge
+  // form would cost them a second inverse transform and gather per apply)
+  f.edge = f.inner->prec == BEM_F32 && f.inner->v2 && f.inner->tc == 0;
   if (f.edge) {
     bem_status rc = setup_edge_2d(f.inner);
     if (rc != BEM_OK) return fail(rc);
