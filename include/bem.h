@@ -223,7 +223,12 @@ bem_status bem_apply_static_scratch(bem_plan_t plan, bem_layer layer, const void
                                     void* stream);
 
 /* Solve the boundary-condition split system for the unknowns (Section 4:
- * Krylov iteration on the FFT apply; restarted GMRES here).
+ * Krylov iteration on the FFT apply; restarted GMRES here).  Each Arnoldi step
+ * (preconditioner, apply, two Gram-Schmidt sweeps, norm, next basis vector,
+ * Givens rotation) is one CUDA graph replay with the step index and the
+ * rotations kept on the device; the host reads one integer per step.  The
+ * solve runs on an internal stream ordered after `stream` and returns when
+ * the outputs are on the host.
  *   bc        host nb*ncomp (as bem_set_bc; also sets the plan's BC state)
  *   data      host nb*ncomp FP64 known values: u where bc = 0, q/t where bc = 1
  *   c         free-term coefficient
@@ -295,6 +300,11 @@ bem_status bem_device_status(bem_plan_t plan, void* stream);
  * without tensor-core stages ignore the flag.  Returns BEM_ERR_ARG for a null
  * plan or unknown bits. */
 #define BEM_TEST_WAIT_RUNS_OUT 1u
+/* BEM_TEST_HOST_ARNOLDI: bem_solve runs the host-driven Arnoldi loop (Givens
+ * rotations on the host, one stream synchronisation per step) instead of its
+ * default path (each Arnoldi step one CUDA graph replay, Givens rotations on
+ * the device); for comparing the two. */
+#define BEM_TEST_HOST_ARNOLDI 2u
 bem_status bem_set_test_flags(bem_plan_t plan, uint32_t flags);
 
 /* ---- batched apply (many geometries, one CUDA graph) --------------------

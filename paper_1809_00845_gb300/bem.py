@@ -23,6 +23,7 @@ BEM_LAPLACE_2D, BEM_LAPLACE_3D, BEM_KELVIN_3D = 0, 1, 2
 BEM_F64, BEM_F32, BEM_F32X2, BEM_TC_BF16X3, BEM_TC_F16X3 = 0, 1, 2, 3, 4
 BEM_SINGLE, BEM_DOUBLE, BEM_SYSTEM = 0, 1, 2
 BEM_TEST_WAIT_RUNS_OUT = 1
+BEM_TEST_HOST_ARNOLDI = 2
 
 KERNELS = {"laplace2d": BEM_LAPLACE_2D, "laplace3d": BEM_LAPLACE_3D, "kelvin3d": BEM_KELVIN_3D}
 PRECISIONS = {"f64": BEM_F64, "f32": BEM_F32, "f32x2": BEM_F32X2, "tc_bf16x3": BEM_TC_BF16X3,

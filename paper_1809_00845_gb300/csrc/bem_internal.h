@@ -230,6 +230,8 @@ struct bem_plan_s {
   void* d_tin = nullptr;    // plan-precision in/out buffers for the apply
   void* d_tout = nullptr;
   uint64_t op_version = 0;  // bumped whenever bem_set_bc rebuilds the system operator
+  uint64_t pc_version = 0;  // bumped whenever the preconditioner changes (captured solve graphs hold it)
+  bem_batch_s* self_batch = nullptr;  // one-plan batch that runs bem_solve's Arnoldi steps as graphs
   bemfft::PanelOp* pf = nullptr;  // accuracy mode (bem_plan_panels), else null
 };
 
@@ -326,6 +328,11 @@ bem_status batch_refresh(bem_batch_s* b);  // re-capture when a plan's operator 
 void batch_solve_free(bem_batch_s* b);     // gmres.cu
 // gmres.cu
 bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
+                       int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
+                       cudaStream_t st);
+// bem_solve's default path: the same GMRES with every Arnoldi step one CUDA
+// graph replay and the Givens rotations on the device (a one-plan batch)
+bem_status solve_graph(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
                        int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
                        cudaStream_t st);
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);

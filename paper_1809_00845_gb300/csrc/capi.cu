@@ -587,6 +587,7 @@ bem_status bem_set_preconditioner(bem_plan_t p, int kind, int block_size) {
   p->pc.kind = kind;
   if (kind == 1) p->pc.bs = block_size;
   p->pc.valid = false;
+  ++p->pc_version;
   return BEM_OK;
 }
 
@@ -648,8 +649,10 @@ bem_status bem_solve(bem_plan_t p, const uint8_t* bc, const double* data, double
   }
   const bem_status dc = check_device(p, "bem_solve");
   if (dc != BEM_OK) return dc;
-  const bem_status rc = solve_gmres(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info,
-                                    static_cast<cudaStream_t>(stream));
+  const bem_status rc =
+      (p->test_flags & BEM_TEST_HOST_ARNOLDI)
+          ? solve_gmres(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info, static_cast<cudaStream_t>(stream))
+          : solve_graph(p, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info, static_cast<cudaStream_t>(stream));
   const bem_status ds = bem_device_status(p, stream);
   return ds != BEM_OK ? ds : rc;
 }
@@ -660,11 +663,18 @@ bem_status bem_enable_refinement(bem_plan_t p, int enable) {
     return BEM_ERR_ARG;
   }
   if (!enable || p->prec != BEM_F32) {
-    if (p->companion) bem_destroy(p->companion);
+    if (p->companion) {
+      // the solve graphs of the plan's one-plan batch hold the companion
+      if (p->self_batch) bem_batch_destroy(p->self_batch);
+      p->self_batch = nullptr;
+      bem_destroy(p->companion);
+    }
     p->companion = nullptr;
     return BEM_OK;
   }
   if (p->companion) return BEM_OK;
+  if (p->self_batch) bem_batch_destroy(p->self_batch);
+  p->self_batch = nullptr;
   const int64_t n[3] = {p->n, p->n, p->n};
   bem_plan_t c = nullptr;
   if (p->pf) {
@@ -756,7 +766,7 @@ bem_status bem_device_status(bem_plan_t p, void* stream) {
 }
 
 bem_status bem_set_test_flags(bem_plan_t p, uint32_t flags) {
-  if (!p || (flags & ~BEM_TEST_WAIT_RUNS_OUT) != 0) {
+  if (!p || (flags & ~(BEM_TEST_WAIT_RUNS_OUT | BEM_TEST_HOST_ARNOLDI)) != 0) {
     set_error("bem_set_test_flags: null plan or unknown flags");
     return BEM_ERR_ARG;
   }
@@ -776,6 +786,7 @@ int bem_launches_per_apply(bem_plan_t p, bem_layer layer) {
 
 bem_status bem_destroy(bem_plan_t p) {
   if (!p) return BEM_OK;
+  if (p->self_batch) bem_batch_destroy(p->self_batch);
   if (p->companion) bem_destroy(p->companion);
   panel_destroy(p);
   cudaFree(p->d_perm);

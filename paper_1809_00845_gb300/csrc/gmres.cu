@@ -489,7 +489,8 @@ struct BatchSolveWs {
   cudaStream_t st = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<uint64_t> versions;  // plan operator versions the graph was captured with
+  std::vector<uint64_t> versions;     // plan operator versions the graph was captured with
+  std::vector<uint64_t> pc_versions;  // and their preconditioner versions
   std::vector<void*> allocs;
 };
 
@@ -748,7 +749,11 @@ bem_status capture_arnoldi(bem_batch_s* bt, BatchSolveWs& W) {
     return BEM_ERR_CUDA;
   }
   W.versions.clear();
-  for (auto* p : bt->plans) W.versions.push_back(p->op_version);
+  W.pc_versions.clear();
+  for (auto* p : bt->plans) {
+    W.versions.push_back(p->op_version);
+    W.pc_versions.push_back(p->pc_version);
+  }
   return BEM_OK;
 }
 
@@ -919,7 +924,8 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     BEM_CUDA_TRY(cudaMemcpy(W->sys, sys.data(), Mt * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   bool recap = W->exec == nullptr;
-  for (int s = 0; s < K && !recap; ++s) recap = W->versions[s] != bt->plans[s]->op_version;
+  for (int s = 0; s < K && !recap; ++s)
+    recap = W->versions[s] != bt->plans[s]->op_version || W->pc_versions[s] != bt->plans[s]->pc_version;
   if (recap && (rc = capture_arnoldi(bt, *W)) != BEM_OK) return rc;
   cudaStream_t st = W->st;
   // the solve runs on its own stream, ordered after the caller's stream
@@ -1057,3 +1063,34 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
   if (result == BEM_ERR_NOT_CONVERGED) set_error("bem_batch_solve: some systems did not reach tol");
   return result;
 }
+
+namespace bemfft {
+
+bem_status solve_graph(bem_plan_s* p, const uint8_t* bc, const double* data, double c, double tol, int max_iter,
+                       int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
+                       cudaStream_t st) {
+  if (restart < 1 || restart > 512 || max_iter < 0 || !(tol > 0.0)) {
+    set_error("bem_solve: need 1 <= restart <= 512, max_iter >= 0, tol > 0");
+    return BEM_ERR_ARG;
+  }
+  bem_status rc = bem_set_bc(p, bc, c);
+  if (rc != BEM_OK) return rc;
+  // the batch switches its plans' kernel timing off (no event records inside
+  // captured graphs); the caller's setting comes back after the solve
+  const bool timing = p->timing;
+  if (!p->self_batch) {
+    bem_plan_t one = p;
+    rc = bem_batch_create(&p->self_batch, &one, 1, BEM_SYSTEM, 1, st);
+    if (rc != BEM_OK) {
+      p->self_batch = nullptr;
+      p->timing = timing;
+      return rc;
+    }
+  }
+  p->timing = false;
+  rc = bem_batch_solve(p->self_batch, bc, data, c, tol, max_iter, restart, x0, u_out, q_out, info, st);
+  p->timing = timing;
+  return rc;
+}
+
+}  // namespace bemfft

@@ -277,6 +277,7 @@ bem_status build_preconditioner(bem_plan_s* p) {
     set_error("preconditioner needs boundary conditions");
     return BEM_ERR_ARG;
   }
+  ++p->pc_version;  // new inverse blocks (a new allocation): captured solve graphs are stale
   if (p->dim == 2 && !p->pf && p->pc.bs * p->ncomp <= kPcGpuMax) return build_preconditioner_gpu2d(p);
   const int64_t nb = p->nb;
   const int bs = p->pc.bs;
