@@ -151,7 +151,7 @@ class ClockSampler:
 # system operator, from one ncu capture of the launch list, keyed by the hash of
 # the kernel sources it was measured on; reported (as a stored measurement) only
 # while the sources are unchanged.
-MEASURED_TRAFFIC = {"n4096_f32_star_system": ("5e025760142f0490", 201.95e6)}
+MEASURED_TRAFFIC = {"n4096_f32_star_system": ("ab10c93e4877b2de", 201.83e6)}
 
 
 def kernel_source_hash():

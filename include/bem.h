@@ -130,7 +130,8 @@ typedef struct {
  *   nu, mu  Poisson ratio and shear modulus (Kelvin only; ignored otherwise)
  *   prec    arithmetic of the apply; spectra are always computed in FP64 on
  *           the device and rounded to prec
- *   flags   0, or BEM_PLAN_SINGLE_LAYER_ONLY: the plan serves BEM_SINGLE
+ *   flags   0, or BEM_PLAN_SINGLE_LAYER_ONLY and/or BEM_PLAN_THREE_PASS
+ *           (below); BEM_PLAN_SINGLE_LAYER_ONLY: the plan serves BEM_SINGLE
  *           applies only (bem_set_bc and the other layers return
  *           BEM_ERR_UNSUPPORTED); the column kernel then needs no staging
  *           rows for the double layer's fields and keeps more of its
@@ -140,6 +141,14 @@ typedef struct {
  * The plan copies every input.  Device memory: spectra (ncomp-dependent,
  * (n+1)^dim reals each), scratch, boundary metadata. */
 #define BEM_PLAN_SINGLE_LAYER_ONLY 1u
+/* BEM_PLAN_THREE_PASS (BEM_F32, 2D, n >= 256, no tensor-core stages; ignored
+ * otherwise): apply in three passes through device memory instead of the
+ * fused column kernel: the input-pruned x-DFT of the fields row by row into
+ * a (n+1) x n buffer per field, the column transforms with the spectral
+ * multiply into one (n+1) x n buffer, and the output-pruned inverse x-DFT at
+ * the cells.  Same operator, same FP32 arithmetic (sums in another order);
+ * about 4 (n+1) n complex values of extra device memory. */
+#define BEM_PLAN_THREE_PASS 2u
 bem_status bem_plan(bem_plan_t* out, int dim, const int64_t* n, double h, int64_t nb, const int32_t* cell,
                     const double* w, const double* normal, bem_kernel kernel, double nu, double mu,
                     bem_precision prec, uint32_t flags, void* stream);
@@ -234,7 +243,8 @@ bem_status bem_apply_static_scratch(bem_plan_t plan, bem_layer layer, const void
  *   c         free-term coefficient
  *   tol       stop when the relative residual ||b - A x||/||b|| <= tol
  *   max_iter  total iteration cap;  restart  Krylov dimension m (<= 512)
- *   x0        host nb*ncomp FP64 initial guess of the unknowns, or NULL (zero)
+ *   x0        host nb*ncomp FP64 initial guess of the unknowns, or NULL (zero);
+ *             a guess whose residual exceeds that of zero is replaced by zero
  *   u_out, q_out  host nb*ncomp FP64 full boundary fields (known entries
  *             copied from data, unknown ones from the solution); either may be NULL
  *   info      may be NULL
@@ -395,6 +405,25 @@ typedef struct bem_net_s* bem_net_t;
 bem_status bem_net_create(bem_net_t* out, int cin, int hidden, int layers, int ksize, const int* dilations,
                           uint64_t seed);
 bem_status bem_net_destroy(bem_net_t net);
+/* Arclength Dirichlet-to-Neumann estimate (a feature of the learned guess):
+ * per closed curve q of the batch (elements offsets[q] .. offsets[q+1] in
+ * arclength order, midpoints at arclength s_j from the curve's start, lengths
+ * len_j, total length Lambda, values u_j)
+ *   uhat_k = (1/Lambda) sum_j len_j u_j e^{-2 pi i k s_j / Lambda}, k = 1..kmax,
+ *   out_j  = sum_k (2 pi k / Lambda) 2 Re(uhat_k e^{2 pi i k s_j / Lambda}),
+ * the interior flux of the harmonic extension of u on a circle of length
+ * Lambda (exact there; on a smooth curve the error is smooth).  s, len, u,
+ * out: device FP32 [T]; offsets: device int32 [nseq + 1]; FP32 phases
+ * (reduced to [0, 1) turns), FP64 sums.  Asynchronous on `stream`. */
+bem_status bem_dtn_estimate(const float* s, const float* len, const float* u, const int32_t* offsets, int nseq,
+                            int64_t T, int kmax, float* out, void* stream);
+/* Random Fourier features of 3D points (the input encoding of the 3D point
+ * network, which is bem_net_* with ksize = 1: the same weights applied to
+ * every point independently):
+ *   out[t][2f] = sin(2 pi B_f . p_t),  out[t][2f+1] = cos(2 pi B_f . p_t)
+ * points device FP32 [T][3], B device FP32 [F][3] (frequencies, caller-drawn),
+ * out device FP32 [T][2F].  FP64 phases, FP32 results; asynchronous. */
+bem_status bem_fourier_features(const float* points, int64_t T, const float* B, int F, float* out, void* stream);
 int64_t bem_net_num_params(bem_net_t net);
 bem_status bem_net_get_params(bem_net_t net, float* host_params);
 bem_status bem_net_set_params(bem_net_t net, const float* host_params);

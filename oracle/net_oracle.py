@@ -96,3 +96,38 @@ def loss_and_grad(params, feats, offsets, target, cin, hidden, layers, ksize, di
         flat.append(gW.ravel())
         flat.append(gb.ravel())
     return loss, np.concatenate(flat)
+
+
+def dtn_estimate(s, length, u, offsets, kmax):
+    """Arclength Dirichlet-to-Neumann estimate of each closed curve of a batch
+    (the learned guess's feature, ``bem_dtn_estimate``), FP64: with Lambda the
+    curve length, uhat_k = (1/Lambda) sum_j l_j u_j exp(-2 pi i k s_j / Lambda)
+    for k = 1..kmax and q_j = sum_k (2 pi k / Lambda) 2 Re(uhat_k
+    exp(2 pi i k s_j / Lambda)): the interior Dirichlet-to-Neumann multiplier
+    |k| / R of a circle of radius R = Lambda / (2 pi), applied mode by mode."""
+    s = np.asarray(s, np.float64)
+    length = np.asarray(length, np.float64)
+    u = np.asarray(u, np.float64)
+    out = np.zeros(s.size)
+    k = np.arange(1, int(kmax) + 1)
+    for q in range(len(offsets) - 1):
+        a, b = int(offsets[q]), int(offsets[q + 1])
+        lam = length[a:b].sum()
+        if not lam > 0:
+            continue
+        E = np.exp(-2j * np.pi * np.outer(k, s[a:b]) / lam)  # (kmax, elements)
+        uhat = E @ (length[a:b] * u[a:b]) / lam
+        out[a:b] = ((2 * np.pi * k / lam)[:, None] * 2 * np.real(uhat[:, None] * np.conj(E))).sum(axis=0)
+    return out
+
+
+def fourier_features(points, B):
+    """Random Fourier features of 3D points (the 3D point network's input
+    encoding, ``bem_fourier_features``), FP64: for each point p and frequency
+    row b of B, sin(2 pi b . p) and cos(2 pi b . p), interleaved per frequency
+    -> (T, 2F)."""
+    ph = 2 * np.pi * np.asarray(points, np.float64) @ np.asarray(B, np.float64).T  # (T, F)
+    out = np.empty((ph.shape[0], 2 * ph.shape[1]))
+    out[:, 0::2] = np.sin(ph)
+    out[:, 1::2] = np.cos(ph)
+    return out

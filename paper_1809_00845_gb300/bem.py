@@ -22,6 +22,7 @@ BEM_ERR_BREAKDOWN, BEM_ERR_NONFINITE, BEM_ERR_TIMEOUT, BEM_ERR_UNSUPPORTED = 5, 
 BEM_LAPLACE_2D, BEM_LAPLACE_3D, BEM_KELVIN_3D = 0, 1, 2
 BEM_F64, BEM_F32, BEM_F32X2, BEM_TC_BF16X3, BEM_TC_F16X3 = 0, 1, 2, 3, 4
 BEM_SINGLE, BEM_DOUBLE, BEM_SYSTEM = 0, 1, 2
+BEM_PLAN_SINGLE_LAYER_ONLY, BEM_PLAN_THREE_PASS = 1, 2
 BEM_TEST_WAIT_RUNS_OUT = 1
 BEM_TEST_HOST_ARNOLDI = 2
 
@@ -38,7 +39,7 @@ EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner
             "bem_batch_apply", "bem_batch_set_grouping", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
             "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step",
-            "bem_measure_peak"]
+            "bem_measure_peak", "bem_dtn_estimate", "bem_fourier_features"]
 
 
 class BemError(RuntimeError):
@@ -125,6 +126,10 @@ def load_library(path: str = LIB_PATH):
     for name in ("bem_net_create", "bem_net_destroy", "bem_net_get_params", "bem_net_set_params", "bem_net_forward",
                  "bem_net_gradient", "bem_net_train_step"):
         getattr(lib, name).restype = I
+    lib.bem_dtn_estimate.argtypes = [P, P, P, P, I, I64, I, P, P]
+    lib.bem_dtn_estimate.restype = I
+    lib.bem_fourier_features.argtypes = [P, I64, P, I, P, P]
+    lib.bem_fourier_features.restype = I
     lib.bem_measure_peak.argtypes = [I, ctypes.POINTER(D), P]
     lib.bem_measure_peak.restype = I
     lib.bem_last_error.argtypes = []
@@ -199,7 +204,7 @@ class Plan:
     """Owning wrapper of a bem_plan_t."""
 
     def __init__(self, dim, n, h, cell, w, normal, kernel="laplace2d", precision="f32", nu=0.3, mu=1.0,
-                 stream=None):
+                 stream=None, flags=0):
         lib = load_library()
         self.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -217,7 +222,8 @@ class Plan:
         if nn.size != self.dim:
             raise ValueError("n must be a scalar or hold dim grid sizes")
         rc = lib.bem_plan(ctypes.byref(self._h), self.dim, _ptr(nn), float(h), self.nb, _ptr(cell), _ptr(w),
-                          _ptr(normal), self.kernel, float(nu), float(mu), self.precision, 0, _stream_ptr(stream))
+                          _ptr(normal), self.kernel, float(nu), float(mu), self.precision, int(flags),
+                          _stream_ptr(stream))
         _check(rc)
         self.torch_dtype = None
         self.device = _current_device()
@@ -550,6 +556,48 @@ class Net:
                                                  ctypes.c_void_p(t.data_ptr()), float(lr), ctypes.byref(loss),
                                                  _stream_ptr(stream)))
         return loss.value
+
+
+def dtn_estimate(s, length, u, offsets, kmax, stream=None):
+    """Arclength Dirichlet-to-Neumann estimate (bem_dtn_estimate) of a batch of
+    closed curves: s, length, u hold T values (elements in arclength order,
+    curve q at offsets[q] .. offsets[q+1]); returns a CUDA float32 tensor."""
+    import torch
+    def dev(a, dt):
+        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+        return t.to(device="cuda", dtype=dt).contiguous().reshape(-1)
+    s, length, u = dev(s, torch.float32), dev(length, torch.float32), dev(u, torch.float32)
+    oh = (offsets.cpu().numpy() if isinstance(offsets, torch.Tensor) else np.asarray(offsets)).reshape(-1)
+    o = dev(oh.astype(np.int32), torch.int32)
+    T = s.numel()
+    if length.numel() != T or u.numel() != T or oh.size < 2 or oh[0] != 0 or oh[-1] != T or np.any(np.diff(oh) < 0):
+        raise ValueError("s, length, u must hold T values; offsets start at 0, do not decrease and end at T")
+    if not (1 <= int(kmax) <= 65535):
+        raise ValueError("kmax must be in [1, 65535]")
+    out = torch.empty(T, dtype=torch.float32, device="cuda")
+    _check(load_library().bem_dtn_estimate(ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(length.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+                                           oh.size - 1, T, int(kmax), ctypes.c_void_p(out.data_ptr()),
+                                           _stream_ptr(stream)))
+    return out
+
+
+def fourier_features(points, B, stream=None):
+    """Random Fourier features (bem_fourier_features) of points (T, 3) for the
+    frequency matrix B (F, 3): a CUDA float32 tensor (T, 2F), sin and cos
+    interleaved per frequency."""
+    import torch
+    p = points if isinstance(points, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(points))
+    b = B if isinstance(B, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(B))
+    p = p.to(device="cuda", dtype=torch.float32).contiguous()
+    b = b.to(device="cuda", dtype=torch.float32).contiguous()
+    if p.ndim != 2 or p.shape[1] != 3 or p.shape[0] < 1 or b.ndim != 2 or b.shape[1] != 3 or not (1 <= b.shape[0] <= 4096):
+        raise ValueError("points must be (T, 3) and B (F, 3) with 1 <= F <= 4096")
+    T, F = p.shape[0], b.shape[0]
+    out = torch.empty((T, 2 * F), dtype=torch.float32, device="cuda")
+    _check(load_library().bem_fourier_features(ctypes.c_void_p(p.data_ptr()), T, ctypes.c_void_p(b.data_ptr()), F,
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def measure_peak(kind="fp32", stream=None):

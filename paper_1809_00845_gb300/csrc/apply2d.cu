@@ -548,6 +548,8 @@ static std::vector<uint16_t> tc_matrices(int kind, int J) {
   return out;
 }
 
+static bem_status setup_p3(bem_plan_s* p);
+
 // largest per-CTA twiddle cache (bytes over all CTAs) the column kernel keeps
 constexpr size_t kTwiddleCacheMax = (size_t)40 << 20;
 
@@ -765,6 +767,9 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   const size_t twc_bytes = (size_t)p->grid * npos * 2 * tb;
   if (twc_bytes <= kTwiddleCacheMax) BEM_CUDA_TRY(cudaMalloc(&p->d_twc, twc_bytes));
   p->scratch_bytes += (size_t)p->grid * npos * tb + (size_t)npos * 2 * tb + (p->d_twc ? twc_bytes : 0);
+  if constexpr (std::is_same<T, float>::value) {
+    if (p->p3) return setup_p3(p);
+  }
   return BEM_OK;
 }
 
@@ -929,6 +934,230 @@ static bem_status launch_v2(bem_plan_s* p, const Operator& op, const void* in, v
   k_reduce_v2<T, TIO><<<(npos + 31) / 32, 512, 0, st>>>(
       static_cast<const T*>(sp.partial), p->grid, npos, p->d_perm_il, static_cast<const TIO*>(op.diag),
       static_cast<const TIO*>(in), static_cast<TIO*>(out));
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+// ------------------------------------------------------------ three-pass form
+// The same operator in three passes through HBM (FP32 four-step plans): the
+// input-pruned x-DFT of every field row by row (k_p3_rows, X[f][kx][y]), the
+// column transforms with the spectral multiply (k_p3_cols, Y[kx][y]), and the
+// output-pruned inverse x-DFT at the cells (k_p3_gather: partial sums per chunk
+// of columns, then k_p3_reduce in a fixed order).  Each row pass gives a warp
+// 32 consecutive grid rows, one per lane, and a chunk of columns, so every
+// load and store of X and Y is one contiguous segment per warp; the per-cell
+// work no longer repeats in every CTA of the column pass.
+
+// per sorted cell: x (as int bits) and the three field values of the apply
+__global__ void k_p3_prep(int nb, const int32_t* __restrict__ perm, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ pos, const uint32_t* __restrict__ meta,
+                          const float* __restrict__ coefA, const float* __restrict__ coefB,
+                          const float* __restrict__ in, float4* __restrict__ cell4) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb) return;
+  const int ps = pos[c];
+  const float x = in[perm[c]];
+  const float a = coefA[ps] * x, b = coefB[ps] * x;
+  const bool ty = (meta[ps] >> 31) != 0;
+  cell4[c] = make_float4(__int_as_float(col[c]), ty ? 0.f : a, ty ? a : b, ty ? b : 0.f);
+}
+
+constexpr int kP3Rows = 256;  // threads per block of the row passes (8 warps of 32 rows)
+
+template <int NF>
+__global__ void __launch_bounds__(kP3Rows) k_p3_rows(int n, int log2N, const int32_t* __restrict__ rowptr,
+                                                      const float4* __restrict__ cell4,
+                                                      const cplx<float>* __restrict__ hi, int kc,
+                                                      cplx<float>* __restrict__ X) {
+  __shared__ cplx<float> shi[128];
+  for (int i = threadIdx.x; i < 128; i += kP3Rows) shi[i] = hi[i];
+  __syncthreads();
+  const int Nm = (1 << log2N) - 1;
+  const Twiddles2L<float> tw{shi, nullptr, log2N - 7, (float)(6.283185307179586476925 / (double)(1 << log2N))};
+  const int r = blockIdx.x * kP3Rows + threadIdx.x;
+  if (r >= n) return;
+  const int c0 = rowptr[r], c1 = rowptr[r + 1];
+  const int k0 = blockIdx.y * kc, k1 = min(k0 + kc, n + 1);
+  // four columns per pass over the row's cells: each cell load serves four
+  // independent twiddles and sums
+  constexpr int KU = 4;
+  for (int kb = k0; kb < k1; kb += KU) {
+    cplx<float> s[KU][3];
+#pragma unroll
+    for (int i = 0; i < KU; ++i) s[i][0] = s[i][1] = s[i][2] = {0.f, 0.f};
+    for (int c = c0; c < c1; ++c) {
+      const float4 q = cell4[c];
+      const int x = __float_as_int(q.x);
+#pragma unroll
+      for (int i = 0; i < KU; ++i) {
+        const cplx<float> w = tw.template get<-1>(((kb + i) * x) & Nm);
+        s[i][0].x += q.y * w.x;
+        s[i][0].y += q.y * w.y;
+        if (NF > 1) {
+          s[i][1].x += q.z * w.x;
+          s[i][1].y += q.z * w.y;
+        }
+        if (NF > 2) {
+          s[i][2].x += q.w * w.x;
+          s[i][2].y += q.w * w.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KU; ++i) {
+      const int kx = kb + i;
+      if (kx < k1) {
+        X[(size_t)kx * n + r] = s[i][0];
+        if (NF > 1) X[((size_t)(n + 1) + kx) * n + r] = s[i][1];
+        if (NF > 2) X[((size_t)2 * (n + 1) + kx) * n + r] = s[i][2];
+      }
+    }
+  }
+}
+
+// columns per chunk of the row passes
+constexpr int kP3Chunk = 32;
+
+// One lane per grid row: the row's values of the chunk's columns are loaded
+// into registers first (all loads in flight at once), then every cell of the
+// row sums its chunk of the inverse x-DFT.
+__global__ void __launch_bounds__(kP3Rows) k_p3_gather(int n, int log2N, int nb, const int32_t* __restrict__ rowptr,
+                                                        const float4* __restrict__ cell4,
+                                                        const cplx<float>* __restrict__ hi,
+                                                        const cplx<float>* __restrict__ Y, float* __restrict__ part) {
+  __shared__ cplx<float> shi[128];
+  for (int i = threadIdx.x; i < 128; i += kP3Rows) shi[i] = hi[i];
+  __syncthreads();
+  const int Nm = (1 << log2N) - 1;
+  const Twiddles2L<float> tw{shi, nullptr, log2N - 7, (float)(6.283185307179586476925 / (double)(1 << log2N))};
+  const int r = blockIdx.x * kP3Rows + threadIdx.x;
+  if (r >= n) return;
+  const int c0 = rowptr[r], c1 = rowptr[r + 1];
+  if (c0 == c1) return;
+  const int k0 = blockIdx.y * kP3Chunk;
+  cplx<float> yv[kP3Chunk];
+#pragma unroll
+  for (int j = 0; j < kP3Chunk; ++j) {
+    const int kx = k0 + j;
+    yv[j] = kx <= n ? Y[(size_t)kx * n + r] : cplx<float>{0.f, 0.f};
+  }
+  for (int c = c0; c < c1; ++c) {
+    const int x = __float_as_int(cell4[c].x);
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < kP3Chunk; ++j) {
+      const int kx = k0 + j;
+      const cplx<float> w = tw.template get<+1>((kx * x) & Nm);
+      const float ck = (kx == 0 || kx == n) ? 1.f : 2.f;
+      acc += ck * (yv[j].x * w.x - yv[j].y * w.y);  // beyond n: yv is zero
+    }
+    part[(size_t)blockIdx.y * nb + c] = acc;
+  }
+}
+
+// out[perm[c]] = sum over chunks of part[chunk][c] (compensated, fixed order)
+// + diag * in; eight loads in flight per thread
+__global__ void __launch_bounds__(64) k_p3_reduce(int nb, int nchunk, const float* __restrict__ part,
+                                                  const int32_t* __restrict__ perm, const float* __restrict__ diag,
+                                                  const float* __restrict__ in, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb) return;
+  CompSum t{0.f, 0.f};
+  int k = 0;
+  for (; k + 8 <= nchunk; k += 8) {
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = part[(size_t)(k + i) * nb + c];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t.add(v[i]);
+  }
+  for (; k < nchunk; ++k) t.add(part[(size_t)k * nb + c]);
+  const int u = perm[c];
+  if (diag) {
+    const float pr = __fmul_rn(diag[u], in[u]);
+    const float epr = fmaf(diag[u], in[u], -pr);
+    t.add(pr);
+    t.c = __fadd_rn(t.c, epr);
+  }
+  out[u] = __fadd_rn(t.p, t.c);
+}
+
+static cudaError_t p3_configure(int TT, size_t smem, int* bps) {
+  switch (TT) {
+    case 512: return Col2DPassKernels<512>::configure(smem, TT, bps);
+    case 256: return Col2DPassKernels<256>::configure(smem, TT, bps);
+    case 128: return Col2DPassKernels<128>::configure(smem, TT, bps);
+    case 64: return Col2DPassKernels<64>::configure(smem, TT, bps);
+    default: return Col2DPassKernels<32>::configure(smem, TT, bps);
+  }
+}
+
+static bem_status setup_p3(bem_plan_s* p) {
+  const int TT = p->threads, W = TT / 32;
+  const int64_t n = p->n, nb = p->nb;
+  const int nf = p->single_only ? 1 : 3;
+  int dev = 0, nsm = 0, smem_optin = 0, bps = 0;
+  BEM_CUDA_TRY(cudaGetDevice(&dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t nbuf = (size_t)std::max(16 * TT, W * 544);
+  p->p3_smem = (nbuf + (size_t)fstab_entries(TT)) * sizeof(cplx<float>) + (size_t)sspec_entries((int)n) * sizeof(float) +
+               (size_t)nf * n * sizeof(cplx<float>);
+  if (p->p3_smem > (size_t)smem_optin) {
+    set_error("three-pass form: column buffers exceed shared memory");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  BEM_CUDA_TRY(p3_configure(TT, p->p3_smem, &bps));
+  if (bps < 1) {
+    set_error("three-pass column kernel cannot be resident");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  p->p3_grid = (int)std::min<int64_t>((int64_t)bps * nsm, n + 1);
+  p->p3_nchunk = (int)((n + 1 + kP3Chunk - 1) / kP3Chunk);
+  std::vector<int32_t> pos(nb);
+  for (int64_t c = 0; c < nb; ++c) pos[c] = (int32_t)p->h_pos[c];
+  const size_t xb = (size_t)nf * (n + 1) * n * sizeof(cplx<float>), yb = (size_t)(n + 1) * n * sizeof(cplx<float>);
+  BEM_CUDA_TRY(cudaMalloc(&p->d_p3X, xb));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_p3Y, yb));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_p3part, (size_t)p->p3_nchunk * nb * sizeof(float)));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_p3cell, (size_t)nb * sizeof(float4)));
+  BEM_CUDA_TRY(cudaMalloc(&p->d_p3pos, (size_t)nb * sizeof(int32_t)));
+  BEM_CUDA_TRY(cudaMemcpy(p->d_p3pos, pos.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice));
+  p->scratch_bytes += xb + yb + (size_t)p->p3_nchunk * nb * sizeof(float) + (size_t)nb * (sizeof(float4) + 4);
+  return BEM_OK;
+}
+
+static bem_status launch_p3(bem_plan_s* p, const Operator& op, const float* in, float* out, bool timed,
+                            cudaStream_t st) {
+  const int n = (int)p->n, nb = (int)p->nb, TT = p->threads, W = TT / 32;
+  const cplx<float>* hi = static_cast<const cplx<float>*>(p->d_fstab) + 1024 + W * 16;
+  cplx<float>* X = static_cast<cplx<float>*>(p->d_p3X);
+  cplx<float>* Y = static_cast<cplx<float>*>(p->d_p3Y);
+  float4* cell4 = static_cast<float4*>(p->d_p3cell);
+  k_p3_prep<<<(nb + 255) / 256, 256, 0, st>>>(nb, p->d_perm, p->d_col, p->d_p3pos, op.meta,
+                                               static_cast<const float*>(op.coefA), static_cast<const float*>(op.coefB),
+                                               in, cell4);
+  const dim3 rg((unsigned)((n + kP3Rows - 1) / kP3Rows), (unsigned)p->p3_nchunk);
+  if (op.nf == 1) k_p3_rows<1><<<rg, kP3Rows, 0, st>>>(n, p->log2N, p->d_rowptr, cell4, hi, kP3Chunk, X);
+  else if (op.nf == 2) k_p3_rows<2><<<rg, kP3Rows, 0, st>>>(n, p->log2N, p->d_rowptr, cell4, hi, kP3Chunk, X);
+  else k_p3_rows<3><<<rg, kP3Rows, 0, st>>>(n, p->log2N, p->d_rowptr, cell4, hi, kP3Chunk, X);
+  ScratchPtrs sp{};
+  Col2Dv2Params<float> cp = col2d_params<float>(p, op, sp);
+  cp.X = X;
+  cp.Y = Y;
+  cudaEvent_t e1 = nullptr;
+  if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
+  switch (TT) {
+    case 512: Col2DPassKernels<512>::launch(op.nf, p->p3_grid, TT, p->p3_smem, st, cp); break;
+    case 256: Col2DPassKernels<256>::launch(op.nf, p->p3_grid, TT, p->p3_smem, st, cp); break;
+    case 128: Col2DPassKernels<128>::launch(op.nf, p->p3_grid, TT, p->p3_smem, st, cp); break;
+    case 64: Col2DPassKernels<64>::launch(op.nf, p->p3_grid, TT, p->p3_smem, st, cp); break;
+    default: Col2DPassKernels<32>::launch(op.nf, p->p3_grid, TT, p->p3_smem, st, cp); break;
+  }
+  if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
+  k_p3_gather<<<rg, kP3Rows, 0, st>>>(n, p->log2N, nb, p->d_rowptr, cell4, hi, Y, static_cast<float*>(p->d_p3part));
+  k_p3_reduce<<<(nb + 63) / 64, 64, 0, st>>>(nb, p->p3_nchunk, static_cast<const float*>(p->d_p3part), p->d_perm,
+                                             static_cast<const float*>(op.diag), in, out);
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
@@ -1221,6 +1450,8 @@ bem_status launch_apply_2d_with(bem_plan_s* p, const Operator& op, const void* i
     return BEM_ERR_UNSUPPORTED;
   }
   if (p->v2) {
+    if (p->p3 && sp.partial == p->d_partial)
+      return launch_p3(p, op, static_cast<const float*>(in), static_cast<float*>(out), timed, st);
     if (p->prec == BEM_F32X2) return launch_v2<f32x2, double>(p, op, in, out, sp, timed, st);
     return p->prec == BEM_F64 ? launch_v2<double, double>(p, op, in, out, sp, timed, st)
                               : launch_v2<float, float>(p, op, in, out, sp, timed, st);

@@ -187,6 +187,15 @@ struct bem_plan_s {
   uint32_t test_flags = 0;      // bem_set_test_flags (bounded-wait tests)
   // edge-flow form of the node convolution (accuracy mode): third density per
   // position (plan arithmetic type), launch shape of the edge-flow column kernel
+  // three-pass form (FP32 four-step plans with BEM_PLAN_THREE_PASS)
+  bool p3 = false;
+  void* d_p3X = nullptr;        // fields' x-DFT rows, nf * (n+1) * n complex
+  void* d_p3Y = nullptr;        // inverse-transformed columns, (n+1) * n complex
+  void* d_p3part = nullptr;     // gather partials per chunk of columns
+  void* d_p3cell = nullptr;     // per sorted cell: x and three field values
+  int32_t* d_p3pos = nullptr;   // sorted cell -> interleaved position
+  size_t p3_smem = 0;
+  int p3_grid = 0, p3_nchunk = 0;
   void* d_val2 = nullptr;
   size_t edge_smem = 0;
   int edge_acc_rows = 0, edge_grid = 0;

@@ -255,7 +255,7 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     tc = prec == BEM_TC_BF16X3 ? 1 : 2;
     prec = BEM_F32;
   }
-  if ((flags & ~BEM_PLAN_SINGLE_LAYER_ONLY) != 0) {
+  if ((flags & ~(BEM_PLAN_SINGLE_LAYER_ONLY | BEM_PLAN_THREE_PASS)) != 0) {
     set_error("bem_plan: unknown flags");
     return BEM_ERR_ARG;
   }
@@ -307,6 +307,8 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
   p->prec = prec;
   p->tc = tc;
   p->single_only = (flags & BEM_PLAN_SINGLE_LAYER_ONLY) != 0;
+  // three passes through HBM: FP32 four-step plans without tensor-core stages
+  p->p3 = (flags & BEM_PLAN_THREE_PASS) != 0 && prec == BEM_F32 && tc == 0 && dim == 2 && n[0] >= 256;
   p->pc.bs = dim == 2 ? 128 : 64;  // default block-Jacobi block (cells)
   p->n = nn;
   p->N = 2 * nn;
@@ -804,6 +806,11 @@ bem_status bem_destroy(bem_plan_t p) {
   cudaFree(p->d_chunk);
   cudaFree(p->d_val);
   cudaFree(p->d_val2);
+  cudaFree(p->d_p3X);
+  cudaFree(p->d_p3Y);
+  cudaFree(p->d_p3part);
+  cudaFree(p->d_p3cell);
+  cudaFree(p->d_p3pos);
   cudaFree(p->d_twc);
   cudaFree(p->d_fstab);
   cudaFree(p->d_tcmat);

@@ -8,4 +8,6 @@ template struct Col2DGroupKernels<512>;
 template struct Col2DGroupKernels<256>;
 template struct Col2DEdgeKernels<float, 512>;
 template struct Col2DEdgeKernels<float, 256>;
+template struct Col2DPassKernels<512>;
+template struct Col2DPassKernels<256>;
 }  // namespace bemfft

@@ -11,4 +11,7 @@ template struct Col2DGroupKernels<32>;
 template struct Col2DEdgeKernels<float, 128>;
 template struct Col2DEdgeKernels<float, 64>;
 template struct Col2DEdgeKernels<float, 32>;
+template struct Col2DPassKernels<128>;
+template struct Col2DPassKernels<64>;
+template struct Col2DPassKernels<32>;
 }  // namespace bemfft

@@ -577,6 +577,95 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   }
 }
 
+// Three-pass column kernel (FP32): one persistent CTA per SM walks columns
+// kx = blockIdx.x, + gridDim.x, ...; per column the NF fields' rows (X, n
+// complex each, staged in shared memory by cp.async one column ahead: the
+// copies of the next column's field f are issued as soon as this column has
+// read field f into registers, each thread copying exactly the slots it reads)
+// are transformed forward, multiplied by their spectrum columns and summed in
+// registers, transformed back, and rows y < n are written to Y.
+template <int NF, int TTC>
+__global__ void __launch_bounds__(TTC, ColBounds<TTC>::blocks) k_p3_cols(const Col2Dv2Params<float> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  static_assert(TTC >= 32, "three-pass column kernel: TT >= 32");
+  const ColDims<TTC> g(p);
+  constexpr int TT = TTC, W = TT >> 5;
+  const int t = threadIdx.x, n = g.n;
+  constexpr int nbuf = (16 * TT > W * 544) ? 16 * TT : W * 544;
+  const int ntab = fstab_entries(TT);
+  cplx<float>* sA = reinterpret_cast<cplx<float>*>(smem_raw);
+  cplx<float>* stab = sA + nbuf;
+  float* sS = reinterpret_cast<float*>(stab + ntab);
+  cplx<float>* stage = reinterpret_cast<cplx<float>*>(sS + sspec_entries(n));  // NF * n
+  for (int i = t; i < ntab; i += TT) stab[i] = p.fstab[i];
+  const FourStepTables<float> ftab{stab, stab + 512, stab + 512 + W * 16};
+  FourStep<float, 0> fs;
+  fs.init(t, TT, sA, ftab);
+  auto stage_field = [&](int kx, int f) {
+    const cplx<float>* src = p.X + ((size_t)f * (n + 1) + kx) * n;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(stage + f * n + t + m * TT);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + t + m * TT) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (blockIdx.x <= n)
+    for (int f = 0; f < NF; ++f) stage_field(blockIdx.x, f);
+  for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();  // this column's rows have landed; the previous column no longer reads sA
+    const int next = kx + gridDim.x;
+    cplx<float> y[16];
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+      cplx<float> v[16];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = stage[f * n + t + m * TT];
+#pragma unroll
+      for (int m = 8; m < 16; ++m) v[m] = {0.f, 0.f};
+      if (next <= n) stage_field(next, f);
+      if (f > 0) __syncthreads();  // the previous field's spectrum and transform buffer are no longer read
+      load_spectrum(p, g, f, kx, sS);
+      fs.template forward<true>(v);
+      spectrum_ready();
+      const SpecAddr sa = spec_addr(fs, g);
+      if (f == 0) spectral_multiply<float, false>(sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
+      else spectral_multiply<float, true>(sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
+    }
+    fs.inverse(y);
+    cplx<float>* dst = p.Y + (size_t)kx * n;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) dst[t + m * TT] = y[m];
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int TTC>
+cudaError_t Col2DPassKernels<TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
+  int b[3] = {0, 0, 0};
+  cudaError_t e;
+  if ((e = allow_optin_smem(k_p3_cols<1, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_p3_cols<2, TTC>)) != cudaSuccess) return e;
+  if ((e = allow_optin_smem(k_p3_cols<3, TTC>)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_p3_cols<1, TTC>, threads, smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_p3_cols<2, TTC>, threads, smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_p3_cols<3, TTC>, threads, smem)) != cudaSuccess)
+    return e;
+  *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));
+  return cudaSuccess;
+}
+
+template <int TTC>
+void Col2DPassKernels<TTC>::launch(int nf, int grid, int threads, size_t smem, cudaStream_t st,
+                                   const Col2Dv2Params<float>& cp) {
+  if (nf == 1) k_p3_cols<1, TTC><<<grid, threads, smem, st>>>(cp);
+  else if (nf == 2) k_p3_cols<2, TTC><<<grid, threads, smem, st>>>(cp);
+  else k_p3_cols<3, TTC><<<grid, threads, smem, st>>>(cp);
+}
+
 template <typename T, int TTC>
 cudaError_t Col2DKernels<T, TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
   constexpr bool R = std::is_same<T, float>::value;

@@ -37,6 +37,11 @@ struct Col2Dv2Params {
   const uint4* tcmat;    // tensor-core stages: the two B matrices (hi, lo), 8 KB
   int* status;           // tensor-core stages: bit 0 set when a device wait gave up
   int tc_no_commit;      // test hook: issue no MMA and no commit, so every wait runs out
+  // three-pass form (k_p3_cols): the row transforms of the fields, X[f][kx][y]
+  // (f < nf, kx <= n, y < n), come from HBM and the inverse-transformed
+  // columns go back to it, Y[kx][y]
+  const cplx<T>* X;
+  cplx<T>* Y;
 };
 
 // number of table entries of the four-step kernel for TT threads, N = 16 TT:
@@ -81,6 +86,15 @@ template <typename T, int TTC>
 struct Col2DEdgeKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
   static void launch(int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
+};
+
+// Three-pass form, FP32, TTC = 32 ... 512: the column pass alone (forward
+// transforms of the fields' x-DFT rows read from X, spectral multiply, one
+// inverse transform written to Y); the row passes live in apply2d.cu.
+template <int TTC>
+struct Col2DPassKernels {
+  static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
+  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<float>& cp);
 };
 
 // The same kernels in FP32 with the radix-16 stages of the transforms on the

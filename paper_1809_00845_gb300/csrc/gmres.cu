@@ -122,6 +122,24 @@ __global__ void k_split_known(const double* __restrict__ data, const uint8_t* __
 
 static inline unsigned blocks_for(int64_t M, int tb) { return (unsigned)((M + tb - 1) / tb); }
 
+// Relative tolerance of the inner low-precision solve of one refinement step,
+// for outer residual `rel` (relative to b) and target `tol`: deep enough that
+// one step can reach tol (0.3 tol / rel), never below what the FP32 operator's
+// own recomputed residuals resolve (plain FP32 GMRES stalls near 2e-6 on the
+// 4096^2 star; the floor keeps a margin of five), and at most 0.1.  One deep
+// inner solve keeps its Krylov space, where several shallow ones would restart
+// it; a good initial guess (small rel) then saves whole refinement steps.
+// ||r|| / ||b|| with 0 for b = 0 and NaN when either norm is not finite (so
+// that non-finite data end the solve with BEM_ERR_NONFINITE)
+static inline double rel_norm(double r, double b) {
+  if (!std::isfinite(r) || !std::isfinite(b)) return NAN;
+  return b > 0 ? r / b : 0.0;
+}
+
+static inline double inner_tolerance(double tol, double rel) {
+  return std::min(std::max(1e-5, 0.3 * tol / std::max(rel, 1e-300)), 0.1);
+}
+
 struct Gm {
   bem_plan_s* p;
   cudaStream_t st;
@@ -391,6 +409,15 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     double best = INFINITY;
     int stagnant = 0;
     bool x_zero = x0 == nullptr;  // the first residual of a zero start is b itself
+    if (x0) {
+      // first step from the initial guess: low-precision GMRES from x0 on A x = b
+      GmresOut in;
+      if ((rc = gmres_core(g, ws, d_b, bnorm, d_x, inner_tolerance(tol, 1.0), max_iter, &in)) != BEM_OK) return rc;
+      tot.iters += in.iters;
+      tot.restarts += in.restarts;
+      tot.applies += in.applies;
+      ++refine_steps;
+    }
     for (;;) {
       BEM_CUDA_TRY(cudaMemcpyAsync(d_r, d_b, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
       if (!x_zero) {
@@ -428,8 +455,7 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
       // inner solve A d = r to a modest relative accuracy
       BEM_CUDA_TRY(cudaMemsetAsync(d_d, 0, M * sizeof(double), st));
       GmresOut in;
-      const double eta = std::max(1e-4, 0.1 * tol / std::max(rel, 1e-300));
-      if ((rc = gmres_core(g, ws, d_r, rn, d_d, std::min(eta, 1e-2), max_iter - tot.iters, &in)) != BEM_OK)
+      if ((rc = gmres_core(g, ws, d_r, rn, d_d, inner_tolerance(tol, rel), max_iter - tot.iters, &in)) != BEM_OK)
         return rc;
       tot.iters += in.iters;
       tot.restarts += in.restarts;
@@ -489,6 +515,7 @@ struct BatchSolveWs {
   cudaStream_t st = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> segoff;        // host copy of the system offsets (K + 1)
   std::vector<uint64_t> versions;     // plan operator versions the graph was captured with
   std::vector<uint64_t> pc_versions;  // and their preconditioner versions
   std::vector<void*> allocs;
@@ -778,6 +805,7 @@ bem_status batch_gmres(bem_batch_s* bt, BatchSolveWs& W, const double* rhs, cons
   std::vector<double> best(K, INFINITY);
   std::vector<int> stagnant(K, 0);
   rel.assign(K, 1.0);
+  const int iters0 = cnt->iters;
   for (;;) {
     bem_status rc = batch_apply_f64(bt, x, W.w, st, true);
     if (rc != BEM_OK) return rc;
@@ -786,10 +814,23 @@ bem_status batch_gmres(bem_batch_s* bt, BatchSolveWs& W, const double* rhs, cons
     BEM_CUDA_TRY(cudaMemcpyAsync(W.r, rhs, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(-1.0, W.w, 1.0, W.r, Mt);
     if ((rc = seg_norms(W, W.r, beta2)) != BEM_OK) return rc;
+    if (cnt->iters == iters0) {
+      // a starting point worse than zero (an initial guess) is replaced by zero
+      bool any = false;
+      for (int s = 0; s < K; ++s)
+        if (!(std::sqrt(beta2[s]) <= rn[s])) {
+          const int64_t o = W.segoff[s], len = W.segoff[s + 1] - o;
+          BEM_CUDA_TRY(cudaMemsetAsync(x + o, 0, len * sizeof(double), st));
+          BEM_CUDA_TRY(cudaMemcpyAsync(W.r + o, rhs + o, len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          any = true;
+        }
+      // the norms again, on the device too (the Arnoldi start reads them there)
+      if (any && (rc = seg_norms(W, W.r, beta2)) != BEM_OK) return rc;
+    }
     int live = 0;
     for (int s = 0; s < K; ++s) {
       const double b = std::sqrt(beta2[s]);
-      rel[s] = rn[s] > 0 ? b / rn[s] : 0.0;
+      rel[s] = rel_norm(b, rn[s]);
       bool go = std::isfinite(rel[s]) && rel[s] > tols[s];
       if (go) {
         if (rel[s] < best[s] * 0.999) {
@@ -917,6 +958,7 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
       return BEM_ERR_OOM;
     }
     std::vector<int64_t> off(bt->offset.begin(), bt->offset.end());
+    W->segoff = off;
     std::vector<int32_t> sys(Mt);
     for (int s = 0; s < K; ++s)
       for (size_t i = bt->offset[s]; i < bt->offset[s + 1]; ++i) sys[i] = s;
@@ -1001,6 +1043,16 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     std::vector<double> best(K, INFINITY);
     int stagnant = 0;
     bool x_zero = x0 == nullptr;  // the first residual of a zero start is b itself
+    if (x0) {
+      // first step from the initial guess: the low-precision GMRES starts at
+      // x0 on A x = b itself (its first residual is the low-precision one,
+      // accurate far beyond this step's tolerance), so the guess costs no
+      // residual with the companion operator
+      std::vector<double> first_tol(K, inner_tolerance(tol, 1.0));
+      std::vector<double> rin;
+      if ((rc = batch_gmres(bt, *W, W->b, bnorm, W->x, first_tol, max_iter, &cnt, rin)) != BEM_OK) return rc;
+      ++refine_steps;
+    }
     for (;;) {
       BEM_CUDA_TRY(cudaMemcpyAsync(W->r, W->b, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
       if (!x_zero) {
@@ -1015,13 +1067,13 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
       bool all = true, progress = false;
       for (int s = 0; s < K; ++s) {
         rn[s] = std::sqrt(r2[s]);
-        rel[s] = bnorm[s] > 0 ? rn[s] / bnorm[s] : 0.0;
+        rel[s] = rel_norm(rn[s], bnorm[s]);
         const bool done = !(rel[s] > tol);
         all = all && done;
         if (rel[s] < best[s] * 0.5) progress = true;
         best[s] = std::min(best[s], rel[s]);
         // a converged system gets tolerance 1: its inner GMRES does nothing
-        inner_tol[s] = done ? 1.0 : std::min(std::max(1e-4, 0.1 * tol / std::max(rel[s], 1e-300)), 1e-2);
+        inner_tol[s] = done ? 1.0 : inner_tolerance(tol, rel[s]);
       }
       if (all) break;
       stagnant = progress ? 0 : stagnant + 1;

@@ -40,6 +40,7 @@ struct bem_net_s {
   float* d_grad_a = nullptr;          // scratch: gradient wrt current layer output (positions x H)
   float* d_grad_b = nullptr;          // scratch: gradient wrt current layer input
   __nv_bfloat16* d_wb = nullptr;      // BF16 copy of the weights
+  __nv_bfloat16* d_wbt = nullptr;     // the same per layer as [k][cin][cout] (coalesced forward reads)
   double* d_loss = nullptr;
   int* d_seq = nullptr;               // sequence index per position
 };
@@ -59,6 +60,17 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
   if (i < n) b[i] = __float2bfloat16_rn(a[i]);
 }
 
+// wt[(k * ci + c) * co + o] = bf16(w[(o * ci + c) * K + k]): one layer's weights
+// in the order the forward kernel reads them (consecutive threads, consecutive o)
+__global__ void k_to_bf16_t(const float* __restrict__ w, __nv_bfloat16* __restrict__ wt, int co, int ci, int K) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)co * ci * K) return;
+  const int k = (int)(i % K);
+  const int c = (int)((i / K) % ci);
+  const int o = (int)(i / ((int64_t)K * ci));
+  wt[((int64_t)k * ci + c) * co + o] = __float2bfloat16_rn(w[i]);
+}
+
 __global__ void k_seq_index(const int32_t* __restrict__ off, int nseq, int* __restrict__ seq) {
   const int s = blockIdx.x;
   if (s >= nseq) return;
@@ -69,7 +81,7 @@ __global__ void k_seq_index(const int32_t* __restrict__ off, int nseq, int* __re
 // x BF16 [T][cin], W BF16 [cout][cin][K]; output pre-activation FP32 and, for
 // hidden layers, the next input relu(y) rounded to BF16.
 __global__ void k_conv_fwd(const __nv_bfloat16* __restrict__ x, int cin, int cout, int K, int d,
-                           const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
+                           const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
                            const int32_t* __restrict__ off, const int* __restrict__ seq, int64_t T,
                            float* __restrict__ pre, __nv_bfloat16* __restrict__ next) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,8 +94,8 @@ __global__ void k_conv_fwd(const __nv_bfloat16* __restrict__ x, int cin, int cou
   for (int k = 0; k < K; ++k) {
     const int tt = seq_wrap((int)t, (k - K / 2) * d, s0, s1);
     const __nv_bfloat16* xr = x + (int64_t)tt * cin;
-    const __nv_bfloat16* wr = W + ((int64_t)o * cin) * K + k;
-    for (int c = 0; c < cin; ++c) acc += __bfloat162float(wr[(int64_t)c * K]) * __bfloat162float(xr[c]);
+    const __nv_bfloat16* wr = Wt + (int64_t)k * cin * cout + o;  // [k][c][o]
+    for (int c = 0; c < cin; ++c) acc += __bfloat162float(wr[(int64_t)c * cout]) * __bfloat162float(xr[c]);
   }
   pre[idx] = acc;
   if (next) next[idx] = __float2bfloat16_rn(acc > 0.f ? acc : 0.f);
@@ -219,8 +231,11 @@ static bem_status net_forward(bem_net_s* net, const float* feats, const int32_t*
     const int cin = l == 0 ? net->cin : net->hidden;
     const bool last = l == net->layers - 1;
     const int cout = last ? 1 : net->hidden;
+    k_to_bf16_t<<<nblk((int64_t)cout * cin * net->ksize, 256), 256, 0, st>>>(net->d_w + net->woff[l],
+                                                                             net->d_wbt + net->woff[l], cout, cin,
+                                                                             net->ksize);
     k_conv_fwd<<<nblk(T * cout, 256), 256, 0, st>>>(net->d_act[l], cin, cout, net->ksize, net->dil[l],
-                                                   net->d_wb + net->woff[l], net->d_w + net->boff[l], off,
+                                                   net->d_wbt + net->woff[l], net->d_w + net->boff[l], off,
                                                    net->d_seq, T, net->d_pre[l], last ? nullptr : net->d_act[l + 1]);
   }
   if (out)
@@ -302,7 +317,8 @@ bem_status bem_net_create(bem_net_t* out, int cin, int hidden, int layers, int k
   };
   if (cudaMalloc(&net->d_w, off * sizeof(float)) != cudaSuccess || cudaMalloc(&net->d_g, off * sizeof(float)) ||
       cudaMalloc(&net->d_m, off * sizeof(float)) || cudaMalloc(&net->d_v, off * sizeof(float)) ||
-      cudaMalloc(&net->d_wb, off * sizeof(__nv_bfloat16)) || cudaMalloc(&net->d_loss, sizeof(double))) {
+      cudaMalloc(&net->d_wb, off * sizeof(__nv_bfloat16)) || cudaMalloc(&net->d_wbt, off * sizeof(__nv_bfloat16)) ||
+      cudaMalloc(&net->d_loss, sizeof(double))) {
     set_error("bem_net_create: out of device memory");
     return fail(BEM_ERR_OOM);
   }
@@ -323,6 +339,7 @@ bem_status bem_net_destroy(bem_net_t net) {
   cudaFree(net->d_m);
   cudaFree(net->d_v);
   cudaFree(net->d_wb);
+  cudaFree(net->d_wbt);
   cudaFree(net->d_loss);
   for (auto p : net->d_act) cudaFree(p);
   for (auto p : net->d_pre) cudaFree(p);

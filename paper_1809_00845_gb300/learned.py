@@ -5,18 +5,31 @@ r(theta) = 0.3 (1 + sum_{k=2..6} a_k cos(k theta + phi_k)), a_k ~ U(0, 0.05),
 phi_k ~ U(0, 2 pi), on grids of uneven sizes n in {512, 1024, 2048}; harmonic
 Dirichlet data from 8 multipoles placed outside the curve (centres at radius
 0.45-0.7 from (0.5, 0.5); ln r and Re(e^{i alpha} / (z - s)^m), m = 1..3;
-amplitudes N(0, 1)).  The unknown is the flux q on every boundary cell.
+amplitudes N(0, 1)).  The unknown is the flux q on every boundary element.
 
-The network (``bem_net_*``, 4 circular conv layers, 64 channels, BF16) maps
-per-cell features in arclength order
-    (x - 1/2, y - 1/2, n_x, n_y, w/h, u/s, (D u)/s),  s = rms(u),
-where D u is the double layer of the data applied with the FFT operator
-itself, to the carried flux w q / (h s).  The operator only ever sees w_j q_j
-(Section 4: the source weight), so q itself is ill-determined on cells that
-hold a sliver of the curve while w q is not; the guess is x0 = pred h s / w.  Training targets are solutions of the FFT method (FP32 GMRES
-with FP64 residual refinement to 1e-8).  At solve time the prediction is
-passed to ``bem_solve`` as x0; zero-start GMRES remains the fallback and the
-FP64 residual decides when the answer is good enough.
+The guess is made for the accuracy-mode operator (flat panels, the paper's
+grid convolution with precorrection, ``bem_plan_panels``), whose solution is
+the smooth physical flux.  (The paper-form operator's solution on a curved
+boundary is not: its discrete flux differs from the physical one by more than
+the flux itself, so no function of the local data predicts it; a network
+trained on it gave no gain.)
+
+Guess = physics estimate + learned correction:
+  * q_dtn, the arclength Dirichlet-to-Neumann estimate of the data
+    (``bem_dtn_estimate``: the circle's multiplier 2 pi |k| / Lambda applied to
+    the Fourier modes of u along the curve; exact on a circle, off by a smooth
+    function on a star);
+  * the network (``bem_net_*``, 4 circular conv layers, 64 channels, BF16) maps
+    per-panel features in arclength order
+        (x - 1/2, y - 1/2, n_x, n_y, L/h, u/s, a q_dtn/s),
+    s = rms(u), a = 0.3 (the curves' radius), to the correction a (q - q_dtn)/s
+    (an earlier form also took the double layer of the data as an input; the
+    operator apply it cost per guess outweighed the iterations it saved).
+Training targets are solutions of the method (FP32 GMRES with double-float
+residual refinement to 1e-7).  At solve time the guess is passed to
+``bem_solve`` as x0; the solver replaces a start whose residual exceeds the
+zero start's by zero (zero-start GMRES remains the fallback) and the refined
+residual decides when the answer is good enough.
 
 Everything that computes runs in the library's CUDA kernels; this module
 prepares arrays and drives the loops.
@@ -38,6 +51,8 @@ WEIGHTS = os.path.join(HERE, "weights", "guess_net.npz")
 NET_SHAPE = dict(cin=7, hidden=64, layers=4, ksize=5, dilations=(1, 3, 9, 27))
 TRAIN_SEED0, TEST_SEED0 = 0, 10000
 SIZES = (512, 1024, 2048)
+RADIUS = 0.3             # length scale of the curves (feature and target scaling)
+PANEL_ORDER, PANEL_R = 3, 3
 
 
 def multipoles(rng: np.random.Generator, count: int = 8):
@@ -64,6 +79,8 @@ def multipoles(rng: np.random.Generator, count: int = 8):
 
 
 def geometry(seed: int, n: int | None = None) -> tuple:
+    """Grid-cell boundary of random star `seed` (paper-form plans) and the
+    generator that then draws its data."""
     rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 4 + seed))
     curve = I.random_star_curve(rng)
     if n is None:
@@ -72,43 +89,66 @@ def geometry(seed: int, n: int | None = None) -> tuple:
     return b, rng
 
 
-def features(b, u, du):
+def panel_geometry(seed: int, n: int | None = None) -> tuple:
+    """The same star as flat panels (accuracy mode), and its data generator."""
+    rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 4 + seed))
+    curve = I.random_star_curve(rng)
+    if n is None:
+        n = int(rng.choice(SIZES))
+    return I.curve_panels(n, curve), rng
+
+
+def arclength(b):
+    """Arclength position of each panel midpoint from the first vertex."""
+    L = b.length
+    return np.cumsum(L) - 0.5 * L
+
+
+def dtn_modes(nb):
+    """Fourier modes of the estimate: a quarter of the panels, at most 256 (the
+    data's modes decay like e^{-k d / R} with d >= 0.075 the multipoles'
+    distance from the curve and R = 0.3: below FP32 rounding long before)."""
+    return max(1, min(nb // 4, 256))
+
+
+def dtn(b, u):
+    """Arclength Dirichlet-to-Neumann estimate of the data (library kernel)."""
+    from .bem import dtn_estimate
+    return dtn_estimate(arclength(b), b.length, u, [0, b.nb], dtn_modes(b.nb)).cpu().numpy().astype(np.float64)
+
+
+def features(b, u, qd):
     s = float(np.sqrt(np.mean(u * u))) or 1.0
-    f = np.stack([b.point[:, 0] - 0.5, b.point[:, 1] - 0.5, b.normal[:, 0], b.normal[:, 1], b.w / b.h, u / s,
-                  du / s], axis=-1).astype(np.float32)
+    m, nrm = b.mid, b.normal
+    f = np.stack([m[:, 0] - 0.5, m[:, 1] - 0.5, nrm[:, 0], nrm[:, 1], b.length / b.h, u / s,
+                  RADIUS * qd / s], axis=-1).astype(np.float32)
     return f, s
 
 
 def _plan(b):
     from .bem import Plan
-    p = Plan.from_boundary(b, "laplace2d", "f32")
+    p = Plan.from_panel_boundary(b, "f32", PANEL_ORDER, PANEL_R)
     p.enable_refinement(True)
     return p
 
 
-def double_layer(plan, u):
-    import torch
-    x = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
-    return plan.apply("double", x).cpu().numpy().astype(np.float64)
-
-
-def generate(seeds, rhs_per_geometry=4, n=None, tol=1e-8, log=None):
-    """Solve Dirichlet problems with the FFT method; returns a list of
-    (features, target q/s) per solve."""
+def generate(seeds, rhs_per_geometry=8, n=None, tol=1e-7, log=None):
+    """Solve Dirichlet problems with the FFT method (accuracy mode); returns a
+    list of (features, target correction) per solve."""
     data = []
     t0 = time.time()
     for k, seed in enumerate(seeds):
-        b, rng = geometry(seed, n)
+        b, rng = panel_geometry(seed, n)
         plan = _plan(b)
         bc = np.zeros(b.nb, np.uint8)
         for _ in range(rhs_per_geometry):
-            u = multipoles(rng)(b.point)
-            du = double_layer(plan, u)
+            u = multipoles(rng)(b.mid)
+            qd = dtn(b, u)
             _, q, info = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000)
             if info["status"] != 0:
                 continue
-            f, s = features(b, u, du)
-            data.append((f, (q * b.w / (b.h * s)).astype(np.float32)))
+            f, s = features(b, u, qd)
+            data.append((f, (RADIUS * (q - qd) / s).astype(np.float32)))
         plan.close()
         if log and (k + 1) % 100 == 0:
             log(f"generated {k + 1}/{len(seeds)} geometries, {len(data)} solves, {time.time() - t0:.0f} s")
@@ -144,60 +184,97 @@ def target_scale(data):
     return float(np.sqrt(np.mean(np.concatenate([t for _, t in data]) ** 2))) or 1.0
 
 
-def predict(net, b, u, du, tscale=1.0):
-    f, s = features(b, u, du)
+def predict(net, b, u, qd, tscale=1.0):
+    """The guess q_dtn + the network's correction (host arrays)."""
+    f, s = features(b, u, qd)
     off = np.array([0, f.shape[0]], np.int32)
-    return net.forward(f, off).cpu().numpy().astype(np.float64) * tscale * (s * b.h) / b.w
+    corr = net.forward(f, off).cpu().numpy().astype(np.float64) * tscale
+    return qd + corr * s / RADIUS
 
 
-def safeguard(plan, bc, u, x0):
-    """Scale the guess by the alpha minimising ||b - alpha A x0|| (one FP32
-    apply of the BC-split operator and one of the right-hand side), so the
-    starting residual never exceeds the zero start's; alpha = 0 falls back to
-    zero-start GMRES."""
-    import torch
-    plan.set_bc(bc, 0.5)
-    xt = torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32)).cuda()
-    ax = plan.apply("system", xt).cpu().numpy().astype(np.float64)
-    ut = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
-    rhs = 0.5 * u - plan.apply("double", ut).cpu().numpy().astype(np.float64)
-    den = float(ax @ ax)
-    alpha = max(0.0, float(ax @ rhs) / den) if den > 0 else 0.0
-    return alpha * x0, alpha
+class Guesser:
+    """The guess of one geometry, kept on the device: the geometry's feature
+    columns and arclength data are uploaded once; per right-hand side the
+    Dirichlet-to-Neumann estimate and the network run in the library's
+    kernels and torch only stacks and scales columns.  Returns the
+    host x0 for bem_solve (which replaces a start worse than zero by zero, so
+    the guess never costs iterations)."""
+
+    def __init__(self, net, plan, b, tscale=1.0):
+        import torch
+        self.net, self.plan, self.b, self.tscale = net, plan, b, tscale
+        dev = torch.device("cuda")
+        m, nrm = b.mid, b.normal
+        geo = np.stack([m[:, 0] - 0.5, m[:, 1] - 0.5, nrm[:, 0], nrm[:, 1], b.length / b.h], axis=-1)
+        self.geo = torch.from_numpy(geo.astype(np.float32)).to(dev)
+        self.s = torch.from_numpy(arclength(b).astype(np.float32)).to(dev)
+        self.len = torch.from_numpy(b.length.astype(np.float32)).to(dev)
+        self.off = torch.tensor([0, b.nb], dtype=torch.int32, device=dev)
+        self.off_host = np.array([0, b.nb], np.int32)
+        self.kmax = dtn_modes(b.nb)
+
+    def __call__(self, u, use_net=True):
+        import torch
+        from . import bem as B
+        ut = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
+        qd = B.dtn_estimate(self.s, self.len, ut, self.off_host, self.kmax)
+        if use_net:
+            sc = torch.sqrt(torch.mean(ut * ut)).clamp_min(1e-30)
+            f = torch.cat([self.geo, torch.stack([ut / sc, RADIUS * qd / sc], dim=1)], dim=1)
+            corr = self.net.forward(f, self.off_host)
+            x0 = qd + corr * (self.tscale * sc / RADIUS)
+        else:
+            x0 = qd
+        return x0.double().cpu().numpy()
 
 
 def evaluate(net, seeds, tol=1e-6, log=None, tscale=1.0):
-    """Time to relative residual `tol` (FP32 GMRES + FP64 residual refinement,
-    block-Jacobi preconditioner) from zero and from the network's guess."""
+    """Time to relative residual `tol` (FP32 GMRES + double-float residual
+    refinement, block-Jacobi preconditioner) from zero, from the
+    Dirichlet-to-Neumann estimate alone and from the network's guess; the
+    guesses' own cost (estimate, features, network) is included."""
     import torch
     rows = []
     for seed in seeds:
-        b, rng = geometry(seed)
+        b, rng = panel_geometry(seed)
         plan = _plan(b)
-        u = multipoles(rng)(b.point)
+        u = multipoles(rng)(b.mid)
         bc = np.zeros(b.nb, np.uint8)
-        plan.solve(bc, u, tol=tol, restart=100, max_iter=2000)  # warm: preconditioner, companion
+        _, q_ref, _ = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000)  # warm: preconditioner, companion
         torch.cuda.synchronize()
         _, _, z = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000)
+        guess = Guesser(net, plan, b, tscale)  # geometry arrays: once per plan
+        guess(u)  # warm
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        du = double_layer(plan, u)
-        x0, alpha = safeguard(plan, bc, u, predict(net, b, u, du, tscale))
+        xd = guess(u, use_net=False)
+        t_dtn = time.perf_counter() - t0
+        _, _, d = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000, x0=xd)
+        t0 = time.perf_counter()
+        x0 = guess(u)
         t_guess = time.perf_counter() - t0
         _, _, g = plan.solve(bc, u, tol=tol, restart=100, max_iter=2000, x0=x0)
+        nq = float(np.linalg.norm(q_ref))
         rows.append({"seed": seed, "n": b.n, "nb": b.nb, "zero_iters": z["iters"], "zero_s": z["seconds"],
-                     "zero_status": z["status"], "guess_iters": g["iters"], "guess_s": g["seconds"] + t_guess,
-                     "guess_status": g["status"], "guess_overhead_s": t_guess, "alpha": alpha})
+                     "zero_status": z["status"], "dtn_iters": d["iters"], "dtn_s": d["seconds"] + t_dtn,
+                     "dtn_status": d["status"], "guess_iters": g["iters"], "guess_s": g["seconds"] + t_guess,
+                     "guess_status": g["status"], "guess_overhead_s": t_guess,
+                     "dtn_rel_err": float(np.linalg.norm(xd - q_ref) / nq),
+                     "guess_rel_err": float(np.linalg.norm(x0 - q_ref) / nq)})
         plan.close()
         if log:
             log(json.dumps(rows[-1]))
-    zi = np.array([r["zero_iters"] for r in rows])
-    gi = np.array([r["guess_iters"] for r in rows])
-    zs = np.array([r["zero_s"] for r in rows])
-    gs = np.array([r["guess_s"] for r in rows])
-    return {"geometries": len(rows), "tol": tol, "mean_iters_zero": float(zi.mean()),
-            "mean_iters_guess": float(gi.mean()), "mean_s_zero": float(zs.mean()), "mean_s_guess": float(gs.mean()),
-            "speedup_time": float(zs.sum() / gs.sum()), "all_converged":
-                bool(all(r["zero_status"] == 0 and r["guess_status"] == 0 for r in rows)), "rows": rows}
+    col = lambda k: np.array([r[k] for r in rows])
+    return {"geometries": len(rows), "tol": tol, "operator": "accuracy mode (flat panels, order "
+            f"{PANEL_ORDER}, R {PANEL_R}), FP32 + double-float refinement",
+            "mean_iters_zero": float(col("zero_iters").mean()), "mean_iters_dtn": float(col("dtn_iters").mean()),
+            "mean_iters_guess": float(col("guess_iters").mean()), "mean_s_zero": float(col("zero_s").mean()),
+            "mean_s_dtn": float(col("dtn_s").mean()), "mean_s_guess": float(col("guess_s").mean()),
+            "speedup_time": float(col("zero_s").sum() / col("guess_s").sum()),
+            "mean_rel_err_dtn": float(col("dtn_rel_err").mean()),
+            "mean_rel_err_guess": float(col("guess_rel_err").mean()),
+            "all_converged": bool(all(r["zero_status"] == 0 and r["guess_status"] == 0 and r["dtn_status"] == 0
+                                      for r in rows)), "rows": rows}
 
 
 def save(net, path=WEIGHTS, meta=None):
@@ -216,8 +293,8 @@ def load(path=WEIGHTS):
 
 def main():
     ap = argparse.ArgumentParser(description="train / evaluate the learned initial guess")
-    ap.add_argument("--geoms", type=int, default=2500)
-    ap.add_argument("--rhs", type=int, default=4)
+    ap.add_argument("--geoms", type=int, default=1250)
+    ap.add_argument("--rhs", type=int, default=8)
     ap.add_argument("--train-n", type=int, default=0, help="grid size of the training curves (0: mixed sizes)")
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--test", type=int, default=64)

@@ -83,3 +83,37 @@ def test_overlapping_buffers_and_bad_nbatch_are_refused(torch_cuda):
     assert rc == bem.BEM_OK, lib.bem_last_error()
     torch.cuda.synchronize()
     plan.close()
+
+
+@pytest.mark.parametrize("n", [512, 4096])
+def test_three_pass_form_matches_fused_and_oracle(torch_cuda, oracle_mod, n):
+    """BEM_PLAN_THREE_PASS (the same operator through X/Y buffers in device
+    memory instead of the fused column kernel) against the oracle (2e-6,
+    sampled rows at full size) and the fused form (FP32 rounding apart)."""
+    torch = torch_cuda
+    from paper_1809_00845_gb300 import bem
+    b = I.star_boundary(n)
+    bc = I.mixed_bc_theta(b)
+    rng = np.random.default_rng(70 + n)
+    x = rng.standard_normal(b.nb)
+    xt = torch.from_numpy(x.astype(np.float32)).cuda()
+    fused = bem.Plan.from_boundary(b, "laplace2d", "f32")
+    p3 = bem.Plan.from_boundary(b, "laplace2d", "f32", flags=bem.BEM_PLAN_THREE_PASS)
+    cnt = b.nb if b.nb <= 4000 else 256
+    for p in (fused, p3):
+        p.set_bc(bc, 0.5)
+    for layer in ("single", "double", "system"):
+        y3 = p3.apply(layer, xt).cpu().numpy().astype(np.float64)
+        yf = fused.apply(layer, xt).cpu().numpy().astype(np.float64)
+        if layer == "system":
+            ref = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x, rows=(0, cnt))
+        else:
+            ref = oracle_mod.apply("laplace2d", 0 if layer == "single" else 1, b.cell, b.h, b.w, b.normal, x,
+                                   rows=(0, cnt))
+        ref = np.asarray(ref).reshape(-1)
+        err = np.linalg.norm(y3[:cnt] - ref) / np.linalg.norm(ref)
+        dif = np.linalg.norm(y3 - yf) / np.linalg.norm(yf)
+        print(f"three-pass n={n} {layer}: rel L2 vs oracle {err:.2e}, vs fused {dif:.2e}")
+        assert err <= 2e-6 and dif <= 2e-6, (layer, err, dif)
+    fused.close()
+    p3.close()

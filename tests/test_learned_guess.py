@@ -1,7 +1,8 @@
 """The trained initial-guess network against zero-start GMRES on held-out
-random stars (GPU).  Reports iterations and seconds to 1e-6 both ways; the
-safeguarded guess (optimal scaling, alpha >= 0) must never start from a larger
-residual than zero, and every solve must converge."""
+random stars (GPU).  Reports iterations and seconds to 1e-6 from zero, from
+the Dirichlet-to-Neumann estimate alone and from the network's guess (the
+guess's own cost included); the guess must shorten the solve on average, in
+iterations and in wall time, and every solve must converge."""
 import json
 import os
 
@@ -26,9 +27,9 @@ def test_learned_guess_on_held_out_geometries(torch_cuda):
     if not os.path.exists(L.WEIGHTS):
         pytest.skip("no trained weights (run python -m paper_1809_00845_gb300.learned)")
     net, meta = L.load()
-    ev = L.evaluate(net, range(L.TEST_SEED0 + 100, L.TEST_SEED0 + 104), tscale=meta.get("tscale", 1.0))
+    assert meta["cin"] == L.NET_SHAPE["cin"]
+    ev = L.evaluate(net, range(L.TEST_SEED0 + 100, L.TEST_SEED0 + 116), tscale=meta.get("tscale", 1.0))
     print(json.dumps({k: v for k, v in ev.items() if k != "rows"}))
     assert ev["all_converged"]
-    for r in ev["rows"]:
-        assert r["alpha"] >= 0.0
-        assert r["guess_iters"] <= r["zero_iters"] + 3
+    assert ev["mean_iters_guess"] < ev["mean_iters_zero"]
+    assert ev["mean_s_guess"] < ev["mean_s_zero"]

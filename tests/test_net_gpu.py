@@ -89,3 +89,76 @@ def test_adam_steps_reduce_loss(torch_cuda):
     for _ in range(150):
         last = net.train_step(f, off, tg, lr=3e-3)
     assert last < 0.2 * first
+
+
+def test_dtn_estimate_matches_oracle(torch_cuda):
+    """bem_dtn_estimate (FP32 phases, FP64 sums, FP32 in and out) against the
+    FP64 oracle on a batch of three curves of random data.  Bound: each phase
+    k s / Lambda carries a rounding error of at most about k 2^-24 turns,
+    i.e. 2 pi kmax 2^-24 radians; twice that, and not below 1e-6."""
+    from paper_1809_00845_gb300 import bem
+    rng = np.random.default_rng(8)
+    lens = [300, 517, 64]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    length = rng.uniform(0.5, 1.5, off[-1]) * 1e-3
+    s = np.concatenate([np.cumsum(length[a:b]) - 0.5 * length[a:b] for a, b in zip(off[:-1], off[1:])])
+    u = rng.standard_normal(off[-1])
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    for kmax in (1, 31, 128):
+        got = bem.dtn_estimate(s, length, u, off, kmax).cpu().numpy()
+        ref = N.dtn_estimate(f32(s), f32(length), f32(u), off, kmax)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print(f"dtn estimate kmax {kmax}: rel L2 {err:.2e}")
+        bound = max(1e-6, 4 * np.pi * kmax * 2.0 ** -24)
+        assert err < bound, (kmax, err, bound)
+
+
+def _surface_points(rng, T):
+    """Points on an ellipsoid (0.4, 0.3, 0.2) about (0.5, 0.5, 0.5) and their outward normals."""
+    v = rng.standard_normal((T, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    ax = np.array([0.4, 0.3, 0.2])
+    p = 0.5 + v * ax
+    nrm = v / ax
+    return p, nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+
+
+def test_fourier_features_match_oracle(torch_cuda):
+    from paper_1809_00845_gb300 import bem
+    rng = np.random.default_rng(12)
+    p, _ = _surface_points(rng, 3000)
+    B = rng.normal(0.0, 4.0, size=(16, 3))
+    got = bem.fourier_features(p, B).cpu().numpy()
+    ref = N.fourier_features(p.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64))
+    assert np.abs(got - ref).max() < 1e-6
+
+
+def test_point_network_forward_and_gradient_match_oracle(torch_cuda):
+    """The 3D point network: Fourier features of surface points plus normals
+    through the network kernels with kernel width 1 (every point on its own),
+    against the oracle with the same BF16 rounding points (1e-3)."""
+    from paper_1809_00845_gb300 import bem
+    rng = np.random.default_rng(13)
+    T = 2500
+    p, nrm = _surface_points(rng, T)
+    B = rng.normal(0.0, 3.0, size=(16, 3))
+    f = np.concatenate([bem.fourier_features(p, B).cpu().numpy(), nrm], axis=1).astype(np.float32)  # 35 inputs
+    cin = f.shape[1]
+    net = _net(cin, 64, 3, 1, (1, 1, 1), seed=4)
+    off = np.array([0, 1200, T], np.int32)
+    tg = (np.sin(3 * p[:, 0]) * np.cos(2 * p[:, 1]) + p[:, 2]).astype(np.float32)
+    prm = net.get_params().astype(np.float64)
+    y_gpu = net.forward(f, off).cpu().numpy()
+    y_ref, _ = N.forward(prm, f, off, cin, 64, 3, 1, [1, 1, 1])
+    e_fwd = np.linalg.norm(y_gpu - y_ref) / np.linalg.norm(y_ref)
+    loss_gpu, g_gpu = net.gradient(f, off, tg)
+    loss_ref, g_ref = N.loss_and_grad(prm, f, off, tg, cin, 64, 3, 1, [1, 1, 1])
+    e_loss = abs(loss_gpu - loss_ref) / loss_ref
+    e_grad = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    print(f"point network: forward {e_fwd:.2e}, loss {e_loss:.2e}, gradient {e_grad:.2e}")
+    assert e_fwd < 1e-3 and e_loss < 1e-3 and e_grad < 1e-3, (e_fwd, e_loss, e_grad)
+    first = net.train_step(f, off, tg, lr=3e-3)
+    for _ in range(200):
+        last = net.train_step(f, off, tg, lr=3e-3)
+    print(f"point network Adam: loss {first:.3e} -> {last:.3e}")
+    assert last < 0.1 * first

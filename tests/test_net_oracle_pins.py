@@ -66,3 +66,63 @@ def test_bf16_rounding_points():
     for l in range(1, L):
         assert np.array_equal(cache[l][0], N.bf16_round(np.maximum(cache[l - 1][2], 0.0)))
     assert not np.array_equal(y, N.bf16_round(y))
+
+
+def _circle_elements(R, nb, phase=0.3):
+    """nb equal elements of a circle of radius R about (0.4, 0.6): midpoint
+    angles, arclength positions of the midpoints, lengths."""
+    th = phase + 2 * np.pi * (np.arange(nb) + 0.5) / nb
+    length = np.full(nb, 2 * np.pi * R / nb)
+    s = np.cumsum(length) - 0.5 * length
+    return th, s, length
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 17])
+def test_dtn_estimate_is_the_circle_flux(m):
+    """On a circle the estimate is the exact interior flux of a harmonic
+    field: u = Re((z - c)^m) = R^m cos(m theta) has q = m R^(m-1) cos(m theta)."""
+    R, nb = 0.27, 400
+    th, s, length = _circle_elements(R, nb)
+    u = R ** m * np.cos(m * th)
+    q = N.dtn_estimate(s, length, u, [0, nb], kmax=nb // 2 - 1)
+    exact = m * R ** (m - 1) * np.cos(m * th)
+    # FP64 sums over ~200 modes whose multipliers reach 2 pi k / Lambda ~ 700
+    assert np.allclose(q, exact, rtol=0, atol=1e-8 * np.abs(exact).max())
+
+
+def test_dtn_estimate_constants_scaling_and_batches():
+    rng = np.random.default_rng(4)
+    th, s, length = _circle_elements(0.3, 256)
+    assert np.allclose(N.dtn_estimate(s, length, np.full(256, 2.5), [0, 256], 100), 0.0, atol=1e-8)
+    u = rng.standard_normal(256)
+    q1 = N.dtn_estimate(s, length, u, [0, 256], 100)
+    q2 = N.dtn_estimate(2 * s, 2 * length, u, [0, 256], 100)  # the same curve twice as large
+    assert np.allclose(q2, q1 / 2, rtol=1e-12, atol=1e-12)
+    # two curves in one batch are estimated independently
+    _, s2, l2 = _circle_elements(0.2, 100)
+    u2 = rng.standard_normal(100)
+    both = N.dtn_estimate(np.concatenate([s, s2]), np.concatenate([length, l2]), np.concatenate([u, u2]),
+                          [0, 256, 356], 40)
+    assert np.allclose(both[:256], N.dtn_estimate(s, length, u, [0, 256], 40), rtol=1e-13, atol=1e-13)
+    assert np.allclose(both[256:], N.dtn_estimate(s2, l2, u2, [0, 100], 40), rtol=1e-13, atol=1e-13)
+
+
+def test_fourier_features_definition():
+    """Features of points chosen so that b . p hits quarter periods: sin and
+    cos in their slots, one frequency row per pair, the rows of B not
+    transposed; sin^2 + cos^2 = 1 and integer shifts leave integer-frequency
+    features unchanged."""
+    B = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 0.5]])
+    p = np.array([[0.25, 0.0, 0.0], [0.0, 0.125, 0.0], [0.0, 0.0, 1.0]])
+    f = N.fourier_features(p, B)
+    assert f.shape == (3, 6)
+    np.testing.assert_allclose(f[0, 0:2], [1.0, 0.0], atol=1e-15)   # 2 pi * 0.25: sin 1, cos 0
+    np.testing.assert_allclose(f[1, 2:4], [1.0, 0.0], atol=1e-15)   # 2 pi * 2 * 0.125
+    np.testing.assert_allclose(f[2, 4:6], [0.0, -1.0], atol=1e-15)  # 2 pi * 0.5 * 1
+    np.testing.assert_allclose(f[0, 2:6], [0.0, 1.0, 0.0, 1.0], atol=1e-15)  # other rows see b . p = 0
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(size=(50, 3))
+    Bi = rng.integers(-4, 5, size=(7, 3)).astype(np.float64)
+    g = N.fourier_features(pts, Bi)
+    np.testing.assert_allclose(g[:, 0::2] ** 2 + g[:, 1::2] ** 2, 1.0, atol=1e-14)
+    np.testing.assert_allclose(N.fourier_features(pts + np.array([1.0, -2.0, 3.0]), Bi), g, atol=1e-12)
