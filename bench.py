@@ -401,6 +401,22 @@ def _batched_solve_c5():
             "sequential_all_converged": all(i["status"] == 0 for i in its), "speedup": t_seq / t_b}
 
 
+def learned_guess_eval():
+    """The learned initial guess on the 64 held-out random stars (the
+    accuracy-mode operator, FP32 + double-float refinement, tolerance 1e-6):
+    mean iterations and seconds from zero, from the Dirichlet-to-Neumann
+    estimate alone and from the network's guess (the guess's own cost
+    included), and the guesses' distance from the solution."""
+    import os
+    from paper_1809_00845_gb300 import learned as L
+    if not os.path.exists(L.WEIGHTS):
+        return None
+    net, meta = L.load()
+    ev = L.evaluate(net, range(L.TEST_SEED0, L.TEST_SEED0 + 64), tscale=meta.get("tscale", 1.0))
+    net.close()
+    return {k: v for k, v in ev.items() if k != "rows"}
+
+
 def accuracy_mode(dev, n=4096, order=3, R=5):
     """The star as flat panels (accuracy mode, bem_plan_panels): system apply
     time, plan time, and the mixed-condition solve of u = e^x cos y to 1e-6
@@ -618,6 +634,7 @@ def secondary_configs(dev):
     for p in plans:
         p.close()
     out["batched_stars_64_f32"]["solve_1e-6"] = _batched_solve_c5()
+    out["batched_stars_64_f32"]["learned_guess_1e-6"] = learned_guess_eval()
     out["accuracy_mode_star_n4096"] = accuracy_mode(dev)
     b = I.cube_boundary(128)
     p = Plan.from_boundary(b, "kelvin3d", "f32")

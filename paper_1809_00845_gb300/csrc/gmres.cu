@@ -1113,6 +1113,7 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     }
   }
   if (result == BEM_ERR_NOT_CONVERGED) set_error("bem_batch_solve: some systems did not reach tol");
+  if (result == BEM_ERR_NONFINITE) set_error("bem_solve: non-finite data or residual");
   return result;
 }
 

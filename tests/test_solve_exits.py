@@ -48,8 +48,9 @@ def test_solve_exits(torch_cuda, prec, refine):
     # non-finite data
     nan_data = data.copy()
     nan_data[7] = np.nan
-    _, _, info6 = p.solve(bc, nan_data, tol=1e-6, restart=100, max_iter=2000)
-    assert info6["status"] == bem.BEM_ERR_NONFINITE, info6
+    with pytest.raises(bem.BemError) as e:
+        p.solve(bc, nan_data, tol=1e-6, restart=100, max_iter=2000)
+    assert e.value.status == bem.BEM_ERR_NONFINITE
     # the plan is still usable afterwards
     _, _, info7 = p.solve(bc, data, tol=1e-6, restart=100, max_iter=2000)
     assert info7["status"] == bem.BEM_OK
