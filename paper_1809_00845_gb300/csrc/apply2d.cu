@@ -558,7 +558,8 @@ template <typename T>
 static size_t smem_v2(int64_t n, int TT, int64_t nb, bool accreg, bool acc, bool tc) {
   const int W = TT / 32;
   const size_t nbuf = (size_t)std::max(16 * TT, W * 544);
-  size_t s = (nbuf + (size_t)fstab_entries(TT)) * sizeof(cplx<T>) + (size_t)sspec_entries((int)n) * sizeof(T);
+  size_t s = (nbuf + (size_t)fstab_entries(TT) + kColTwEntries) * sizeof(cplx<T>) +
+             (size_t)sspec_entries((int)n) * sizeof(T);
   if (tc) s += kTcHeader;
   if (accreg) s += (size_t)2 * n * sizeof(cplx<T>);
   if (acc) s += (size_t)nb * sizeof(T);
@@ -678,7 +679,7 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     tinfo[r % TT] |= 1 << (r / TT);  // row r = t + m*TT, m < 8
   }
   // interleaved positions: i-th cell of thread t at i*TT + t
-  const int64_t Q = (nb + TT - 1) / TT;
+  const int64_t Q = (nb + TT * CB - 1) / (TT * CB) * CB;  // a multiple of the cell batch
   p->v2_npos = Q * TT;
   p->h_pos.assign(nb, 0);
   std::vector<int32_t> perm_il(p->v2_npos, -1);
@@ -736,14 +737,15 @@ static bem_status setup_v2_t(bem_plan_s* p) {
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // staging rows for fields 1, 2 only when the multi-field kernels can run
   const bool staging = R && !p->single_only;
-  p->acc_in_smem = smem_v2<T>(n, TT, p->v2_npos, staging, true, p->tc != 0) <= (size_t)smem_optin;
-  p->acc_rows = p->acc_in_smem ? (int)Q : 0;
+  const int64_t Qc = (nb + TT - 1) / TT;  // most cells of one thread
+  p->acc_in_smem = smem_v2<T>(n, TT, Qc * TT, staging, true, p->tc != 0) <= (size_t)smem_optin;
+  p->acc_rows = p->acc_in_smem ? (int)Qc : 0;
   if (!p->acc_in_smem && TT == 512) {
     // one CTA per SM either way: fill the rest of shared memory with as many
     // accumulator rows as fit, the others stay in the partial sums
     const size_t base = smem_v2<T>(n, TT, 0, staging, false, p->tc != 0);
     if (base < (size_t)smem_optin)
-      p->acc_rows = (int)std::min<int64_t>(Q, (int64_t)(((size_t)smem_optin - base) / ((size_t)TT * sizeof(T))));
+      p->acc_rows = (int)std::min<int64_t>(Qc, (int64_t)(((size_t)smem_optin - base) / ((size_t)TT * sizeof(T))));
   }
   p->smem_bytes = smem_v2<T>(n, TT, 0, staging, false, p->tc != 0) + (size_t)p->acc_rows * TT * sizeof(T);
   if (p->smem_bytes > (size_t)smem_optin) {
@@ -1216,7 +1218,7 @@ template <typename T>
 static bem_status setup_edge_t(bem_plan_s* p) {
   constexpr bool R = std::is_same<T, float>::value;
   const int TT = p->threads;
-  const int64_t n = p->n, Q = p->v2_npos / TT;
+  const int64_t n = p->n, Q = (p->nb + TT - 1) / TT;  // most cells of one thread
   int dev = 0, nsm = 0, smem_optin = 0, bps = 0;
   BEM_CUDA_TRY(cudaGetDevice(&dev));
   BEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1229,7 +1231,7 @@ static bem_status setup_edge_t(bem_plan_s* p) {
     return BEM_ERR_UNSUPPORTED;
   }
   int rows = (int)Q;
-  if (smem_v2<T>(n, TT, p->v2_npos, R, true, false) > (size_t)smem_optin)
+  if (smem_v2<T>(n, TT, Q * TT, R, true, false) > (size_t)smem_optin)
     rows = TT == 512 ? (int)std::min<int64_t>(Q, (int64_t)(((size_t)smem_optin - base) / ((size_t)TT * sizeof(T))))
                      : 0;
   p->edge_acc_rows = rows;

@@ -23,6 +23,12 @@
 //   3. the inverse transform leaves rows t + m*TT in registers, they are
 //      written to shared memory and every thread gathers its own cells
 //      (output-pruned inverse x-DFT) into its accumulators.
+// In the kernels that keep every field's row sums in shared memory (FP32 with
+// two or three fields) steps 3 and 1 of consecutive columns share one walk
+// over the cells (walk_cells): the gather of the CTA's previous column and the
+// row sums of the current one, with the sparse twiddles of the current column
+// from two 64-entry tables built per column; the CTA's last column is
+// gathered after its loop.
 //
 // Included only by the translation units that instantiate Col2DKernels.
 #pragma once
@@ -37,15 +43,6 @@ __device__ __forceinline__ int meta_slot(uint32_t m) { return (int)((m >> 12) & 
 __device__ __forceinline__ int swz16(int i) { return i + (i >> 4); }
 
 constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
-
-// cells per batch of the row-sum and gather loops: the loads of a batch are
-// issued together, one batch ahead of its use, so each batch's memory round
-// trip overlaps the arithmetic of the one before (two batches of loads live
-// at once: 4 cells keep the 512-thread kernels within their 128 registers)
-#ifndef COL2D_CELL_BATCH
-#define COL2D_CELL_BATCH 4
-#endif
-constexpr int CB = COL2D_CELL_BATCH;
 
 // Sizes of one launch: compile-time when TTC > 0, else from the launch and
 // the parameters.
@@ -250,6 +247,146 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const Co
   }
 }
 
+// Per-column sparse twiddles of the fused walk (kColTwEntries entries):
+// stw[j] = e^{-2 pi i kx j / N} and stw[64 + j] = e^{-2 pi i kx 64 j / N}
+// (j < 64), so a cell at x < 4096 takes stw[64 + (x >> 6)] * stw[x & 63]:
+// two table reads and one product instead of the table-and-series twiddle.
+template <typename T, int TTC>
+__device__ __forceinline__ void column_twiddles(const ColDims<TTC>& g, int kx, const Twiddles2L<T>& tw,
+                                                cplx<T>* stw) {
+  const int Nm = g.N - 1;
+  for (int i = threadIdx.x; i < kColTwEntries; i += g.TT) {
+    const int j = i & 63;
+    stw[i] = tw.template get<-1>((kx * (i < 64 ? j : 64 * j)) & Nm);
+  }
+}
+
+// One batch of CB cells of a walk: cell words, densities (EDGE: and the third
+// density) and the cached twiddles of the previous column.
+template <typename T>
+struct CellBatch {
+  uint32_t m[CB];
+  cplx<T> v[CB], w[CB];
+  T c[CB];
+};
+
+// One walk over the thread's cells that serves two columns (kernels with the
+// field sums in shared memory): GATHER adds the output-pruned inverse x-DFT
+// of the previous column kxp (its rows already scaled by the column weight, 1
+// or 2) into the accumulators, SPARSE forms the x-DFT row sums of every field
+// for column kx (as sparse_rows with FSEL < 0; field 0 to out0 at the row
+// slot), with the twiddles of the column's tables stw.  The cell words are
+// loaded once for both; the gather's twiddle is column kxp's cached one
+// (conjugated), which the sparse pass then replaces by column kx's.  Sums and
+// accumulators see the same terms in the same order as the separate passes.
+// The next batch's loads are issued before the current batch is used (two
+// alternating register sets spill in the 512-thread kernels); the cell arrays
+// hold a multiple of CB cells per thread, so every batch load stays inside
+// them.
+template <typename T, int NF, int TTC, bool EDGE, bool SPARSE, bool GATHER>
+__device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kxp, int cnt,
+                                           cplx<T>* out0, cplx<T>* outF, cplx<T>* carry, const cplx<T>* rows,
+                                           T* sacc, T* gacc, int qs, const Twiddles2L<T>& tw, const cplx<T>* stw,
+                                           cplx<T>* twc, cplx<T> fx) {
+  const int Nm = g.N - 1;
+  const int t = threadIdx.x, TT = g.TT;
+  cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
+  auto fetch = [&](CellBatch<T>& B, int base) {
+    const int pos = base * TT + t;
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      B.m[i] = __ldg(p.meta + pos + i * TT);
+      if constexpr (SPARSE) {
+        B.v[i] = p.val[pos + i * TT];
+        if constexpr (EDGE) B.c[i] = p.val2[pos + i * TT];
+      }
+      if constexpr (GATHER) {
+        if (twc) B.w[i] = twc[pos + i * TT];
+      }
+    }
+  };
+  auto process = [&](CellBatch<T>& B, int i0) {
+    if constexpr (GATHER) {
+      cplx<T> Y[CB], wp[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        Y[i] = rows[meta_slot(B.m[i])];
+        if (twc) wp[i] = {B.w[i].x, -B.w[i].y};
+        else wp[i] = tw.template get<+1>((kxp * meta_x(B.m[i])) & Nm);
+      }
+      if (i0 + CB <= qs) {
+        T* acc = sacc + (size_t)i0 * TT + t;
+#pragma unroll
+        for (int i = 0; i < CB; ++i)
+          if (i0 + i < cnt) acc[i * TT] += Y[i].x * wp[i].x - Y[i].y * wp[i].y;
+      } else {
+#pragma unroll
+        for (int i = 0; i < CB; ++i)
+          if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += Y[i].x * wp[i].x - Y[i].y * wp[i].y;
+      }
+    }
+    if constexpr (SPARSE) {
+      cplx<T> w[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) w[i] = cmul(stw[64 + ((B.m[i] >> 6) & 63)], stw[B.m[i] & 63]);
+      if (twc) {
+#pragma unroll
+        for (int i = 0; i < CB; ++i)
+          if (i0 + i < cnt) twc[(i0 + i) * TT + t] = w[i];
+      }
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        if (i0 + i >= cnt) continue;
+        const uint32_t mt = B.m[i];
+        if constexpr (EDGE) {
+          s0.x += B.v[i].x * w[i].x;
+          s0.y += B.v[i].x * w[i].y;
+          s1.x += B.v[i].y * w[i].x;
+          s1.y += B.v[i].y * w[i].y;
+          s2.x += B.c[i] * w[i].x;
+          s2.y += B.c[i] * w[i].y;
+          if (mt & kMetaFlush) {
+            const int row = meta_slot(mt);
+            const bool car = (mt & kMetaCarry) != 0;
+            (car ? carry + t : out0 + row)[0] = s0 + cmul(fx, s1);
+            (car ? carry + TT + t : outF + row)[0] = s2;
+            s0 = s1 = s2 = {T(0), T(0)};
+          }
+        } else {
+          const bool ty = (mt >> 31) != 0;
+          const T a = B.v[i].x, b = B.v[i].y;
+          const T ca = ty ? T(0) : a, cb = ty ? a : b, cc = ty ? b : T(0);
+          s0.x += ca * w[i].x;
+          s0.y += ca * w[i].y;
+          if (NF > 1) {
+            s1.x += cb * w[i].x;
+            s1.y += cb * w[i].y;
+          }
+          if (NF > 2) {
+            s2.x += cc * w[i].x;
+            s2.y += cc * w[i].y;
+          }
+          if (mt & kMetaFlush) {
+            const int row = meta_slot(mt);
+            const bool car = (mt & kMetaCarry) != 0;
+            (car ? carry + t : out0 + row)[0] = s0;
+            if (NF > 1) (car ? carry + TT + t : outF + row)[0] = s1;
+            if (NF > 2) (car ? carry + 2 * TT + t : outF + g.n + row)[0] = s2;
+            s0 = s1 = s2 = {T(0), T(0)};
+          }
+        }
+      }
+    }
+  };
+  CellBatch<T> A, B;
+  if (cnt > 0) fetch(B, 0);
+  for (int i0 = 0; i0 < cnt; i0 += CB) {
+    A = B;
+    if (i0 + CB < cnt) fetch(B, i0 + CB);
+    process(A, i0);
+  }
+}
+
 // field-indexed parameters without dynamic indexing of the parameter arrays
 template <typename T>
 __device__ __forceinline__ const T* spec_of(const Col2Dv2Params<T>& p, int f) {
@@ -367,6 +504,7 @@ struct ColSmem {
   cplx<T>* sF;     // row sums of fields 1, 2 (ACCREG kernels)
   T* sS;           // spectrum column
   cplx<T>* carry;  // carries of split rows (aliases sS)
+  cplx<T>* stw;    // per-column sparse twiddles (fused walks)
 };
 
 // One x-frequency column kx of plan p: sparse x-DFT of the fields, column
@@ -375,30 +513,48 @@ struct ColSmem {
 // EDGE (ACCREG, NF = 2): the edge-flow form; field 1 (y-edge flows) is
 // scaled by e^{-2 pi i K / N} - 1 after its forward transform and both fields
 // use field 0's spectrum (the host passes it for both).
-template <typename T, int NF, bool ACCREG, int TTC, int TCK, bool EDGE = false>
+// FUSED (ACCREG only): the cell walk of column kx also gathers the previous
+// column kxp (kxp < 0: none), field 0's row sums go to the upper half of the
+// transform buffer (sA + n; rows y < n of the previous column's output stay
+// in sA[0, n) until that gather), and the column ends with its scaled output
+// rows in sA: the caller gathers the CTA's last column after its loop.
+template <typename T, int NF, bool ACCREG, int TTC, int TCK, bool EDGE = false, bool FUSED = false>
 __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx,
                                              FourStep<T, TCK>& fs, const Twiddles2L<T>& tw, const ColSmem<T>& sm,
                                              T* sacc, T* gacc, int qs, cplx<T>* twc,
-                                             cplx<T> half = {T(1), T(0)}) {
+                                             cplx<T> half = {T(1), T(0)}, int kxp = -1) {
   static_assert(!EDGE || NF == 2, "edge-flow form: two fields");
+  static_assert(!FUSED || ACCREG, "fused cell walk: field sums in shared memory");
   const int t = threadIdx.x, TT = g.TT, n = g.n;
   const int cnt = __ldg(p.chunk + t + 1) - __ldg(p.chunk + t);
   cplx<T>* sA = sm.sA;
   cplx<T>* sF = sm.sF;
   if constexpr (ACCREG) {
-    if constexpr (EDGE) sparse_rows<T, 2, -1, TTC, true>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc,
-                                                         diff_factor(tw, kx, half));
-    else sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+    cplx<T>* r0 = FUSED ? sA + n : sA;  // field 0's row sums
+    if constexpr (FUSED) {
+      cplx<T> fx = {T(0), T(0)};
+      if constexpr (EDGE) fx = diff_factor(tw, kx, half);
+      if (kxp >= 0)
+        walk_cells<T, NF, TTC, EDGE, true, true>(p, g, kxp, cnt, r0, sF, sm.carry, sA, sacc, gacc, qs, tw, sm.stw,
+                                                 twc, fx);
+      else
+        walk_cells<T, NF, TTC, EDGE, true, false>(p, g, kxp, cnt, r0, sF, sm.carry, sA, sacc, gacc, qs, tw, sm.stw,
+                                                  twc, fx);
+    } else if constexpr (EDGE) {
+      sparse_rows<T, 2, -1, TTC, true>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc, diff_factor(tw, kx, half));
+    } else {
+      sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+    }
     __syncthreads();
     if (p.has_carry) {
-      add_carries<T, NF, -1>(p, g, cnt, __ldg(p.tinfo + t) >> 8, sA, sF, sm.carry);
+      add_carries<T, NF, -1>(p, g, cnt, __ldg(p.tinfo + t) >> 8, r0, sF, sm.carry);
       __syncthreads();
     }
     cplx<T> y[16];
 #pragma unroll 1
     for (int f = 0; f < NF; ++f) {
       cplx<T> v[16];
-      load_rows(p, g, f == 0 ? sA : sF + (size_t)(f - 1) * n, v);
+      load_rows(p, g, f == 0 ? r0 : sF + (size_t)(f - 1) * n, v);
       __syncthreads();  // rows read before the transform reuses sA; previous spectrum no longer read
       load_spectrum(p, g, f, kx, sm.sS);
       fs.template forward<true>(v);
@@ -414,10 +570,18 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
       else spectral_multiply<T, true>(sm.sS, sa, imag_of(p, f) != 0, oddy_of(p, f) != 0, v, y);
     }
     fs.inverse(y);
+    if constexpr (FUSED) {
+      // the gather's column weight (2 for the columns whose mirror image is
+      // not computed) applied to the rows: exact, so the sums are unchanged
+      const T sc = (kx == 0 || kx == n) ? T(1) : T(2);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
-    __syncthreads();
-    gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
+      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = cscale(y[m], sc);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = y[m];
+      __syncthreads();
+      gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
+    }
   } else {
     cplx<T> fx = {T(0), T(0)};
     if constexpr (EDGE) fx = diff_factor(tw, kx, half);
@@ -498,18 +662,34 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     const uint32_t tm = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 128 * kTcGroupCols);
     fs.tc.bind(t, (uint32_t)__cvta_generic_to_shared(smem_raw), tm, p.tc_no_commit != 0);
   }
-  const ColSmem<T> sm{sA, sF, sS, carry};
+  // per-column twiddles of the fused walks, after the accumulator rows
+  cplx<T>* stw = reinterpret_cast<cplx<T>*>(sacc + (size_t)qs * TT);
+  const ColSmem<T> sm{sA, sF, sS, carry, stw};
+  if constexpr (ACCREG) column_twiddles(g, (int)blockIdx.x, tw, stw);
   cplx<T> half = {T(1), T(0)};  // e^{-i pi / N} (edge-flow form)
   if constexpr (EDGE) half = {(T)cospi(1.0 / (double)N), (T)-sinpi(1.0 / (double)N)};
+  int kxp = -1;  // the column whose gather is pending (fused walks)
   for (int kx = blockIdx.x; kx <= n; kx += gridDim.x) {
-    // the previous column's gather has finished reading sA; with tensor-core
-    // stages the CTA also stops after a device wait that gave up
+    // the previous column's output rows are in place (fused walks) or its
+    // gather has finished reading sA; with tensor-core stages the CTA also
+    // stops after a device wait that gave up
     if constexpr (TCK > 0) {
       if (__syncthreads_or(fs.tc.failed ? 1 : 0)) break;
     } else {
       __syncthreads();
     }
-    col2d_column<T, NF, ACCREG, TTC, TCK, EDGE>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc, half);
+    col2d_column<T, NF, ACCREG, TTC, TCK, EDGE, ACCREG>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc, half, kxp);
+    // the next column's tables: this column's walk read the current ones
+    // several barriers ago, the next walk follows the loop's barrier
+    if constexpr (ACCREG) column_twiddles(g, kx + (int)gridDim.x, tw, stw);
+    kxp = kx;
+  }
+  if constexpr (ACCREG) {
+    if (kxp >= 0) {
+      __syncthreads();
+      walk_cells<T, NF, TTC, EDGE, false, true>(p, g, kxp, cnt, nullptr, nullptr, nullptr, sA, sacc, gacc, qs, tw,
+                                                sm.stw, twc, cplx<T>{T(0), T(0)});
+    }
   }
   if constexpr (TCK > 0) {
     if (fs.tc.failed) {
@@ -552,7 +732,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
                          (T)(6.283185307179586476925 / (double)N)};
   FourStep<T, 0> fs;
   fs.init(t, TT, sA, ftab);
-  const ColSmem<T> sm{sA, sF, sS, carry};
+  const ColSmem<T> sm{sA, sF, sS, carry, nullptr};
   const int64_t C = (int64_t)nplans * (n + 1);
   const int64_t lo = (int64_t)blockIdx.x * C / gridDim.x, hi = ((int64_t)blockIdx.x + 1) * C / gridDim.x;
   for (int64_t c = lo; c < hi;) {

@@ -44,6 +44,21 @@ struct Col2Dv2Params {
   cplx<T>* Y;
 };
 
+// cells per batch of the cell walks of the column kernel: the loads of a
+// batch are issued together, one batch ahead of its use, so each batch's
+// memory round trip overlaps the arithmetic of the one before (two batches of
+// loads live at once: 4 cells keep the 512-thread kernels within their 128
+// registers).  The interleaved cell arrays hold a multiple of CB cells per
+// thread, so a batch is always read whole.
+#ifndef COL2D_CELL_BATCH
+#define COL2D_CELL_BATCH 4
+#endif
+constexpr int CB = COL2D_CELL_BATCH;
+
+// per-column sparse twiddles of the fused cell walk: e^{-2 pi i kx x / N} =
+// A[x >> 6] * B[x & 63] (x < 4096), B in entries 0..63 and A in 64..127
+constexpr int kColTwEntries = 128;
+
 // number of table entries of the four-step kernel for TT threads, N = 16 TT:
 // lane, warp and T5 tables, then the sparse twiddles (hi: 128, lo: N / 128)
 __host__ __device__ inline int fstab_entries(int TT) { return 512 + (TT / 32) * 16 + 512 + 128 + TT / 8; }
