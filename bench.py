@@ -151,7 +151,7 @@ class ClockSampler:
 # system operator, from one ncu capture of the launch list, keyed by the hash of
 # the kernel sources it was measured on; reported (as a stored measurement) only
 # while the sources are unchanged.
-MEASURED_TRAFFIC = {"n4096_f32_star_system": ("ab10c93e4877b2de", 201.83e6)}
+MEASURED_TRAFFIC = {"n4096_f32_star_system": ("6a4eaff781ab489a", 202.33e6)}
 
 
 def kernel_source_hash():
