@@ -154,6 +154,24 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+_OFFSETS_CACHE = {}
+
+
+def _device_offsets(oh):
+    """A CUDA int32 copy of the host sequence offsets oh (already checked),
+    reused while the same offsets come back (a few recent ones are kept), so
+    repeated calls on one batch layout upload nothing."""
+    import torch
+    key = oh.astype(np.int32).tobytes()
+    t = _OFFSETS_CACHE.get(key)
+    if t is None:
+        if len(_OFFSETS_CACHE) >= 16:
+            _OFFSETS_CACHE.pop(next(iter(_OFFSETS_CACHE)))
+        t = torch.from_numpy(np.frombuffer(key, dtype=np.int32).copy()).to("cuda")
+        _OFFSETS_CACHE[key] = t
+    return t
+
+
 def _stream_ptr(stream):
     import torch
     if stream is None:
@@ -518,9 +536,11 @@ class Net:
     def _dev(feats, offsets, target=None):
         import torch
         f = feats if isinstance(feats, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(feats, np.float32))
-        o = offsets if isinstance(offsets, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(offsets, np.int32))
+        if isinstance(offsets, torch.Tensor):
+            o = offsets.to(device="cuda", dtype=torch.int32).contiguous()
+        else:
+            o = _device_offsets(np.asarray(offsets).reshape(-1))
         f = f.to(device="cuda", dtype=torch.float32).contiguous()
-        o = o.to(device="cuda", dtype=torch.int32).contiguous()
         t = None
         if target is not None:
             t = target if isinstance(target, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(target, np.float32))
@@ -568,10 +588,10 @@ def dtn_estimate(s, length, u, offsets, kmax, stream=None):
         return t.to(device="cuda", dtype=dt).contiguous().reshape(-1)
     s, length, u = dev(s, torch.float32), dev(length, torch.float32), dev(u, torch.float32)
     oh = (offsets.cpu().numpy() if isinstance(offsets, torch.Tensor) else np.asarray(offsets)).reshape(-1)
-    o = dev(oh.astype(np.int32), torch.int32)
     T = s.numel()
     if length.numel() != T or u.numel() != T or oh.size < 2 or oh[0] != 0 or oh[-1] != T or np.any(np.diff(oh) < 0):
         raise ValueError("s, length, u must hold T values; offsets start at 0, do not decrease and end at T")
+    o = _device_offsets(oh)
     if not (1 <= int(kmax) <= 65535):
         raise ValueError("kmax must be in [1, 65535]")
     out = torch.empty(T, dtype=torch.float32, device="cuda")

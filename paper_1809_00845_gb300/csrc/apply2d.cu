@@ -173,20 +173,40 @@ __global__ void k_prep(const PrepParams<T> p) {
   p.rho[f][e] = c >= 0 ? p.coef[f][c] * p.in[(int64_t)p.perm[c] * p.ncomp + p.comp[f]] : T(0);
 }
 
-// out[perm[cidx[e]]] = sum_b partial[b][e] + diag * in  over valid slots e
+// out[perm[cidx[e]]] = sum_b partial[b][e] + diag * in  over valid slots e,
+// in FP64 and a fixed order: 32 slots per block, 16 warps each summing every
+// 16th CTA's partial (four interleaved chains keep four loads in flight),
+// then the 16 warp sums in order
 template <typename T>
-__global__ void k_reduce(const T* __restrict__ partial, int grid, int64_t nelem, const int32_t* __restrict__ cidx,
-                         const int32_t* __restrict__ perm, const T* __restrict__ diag, const T* __restrict__ in,
-                         T* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nelem) return;
-  const int c = cidx[e];
-  if (c < 0) return;
-  double s = 0.0;
-  for (int b = 0; b < grid; ++b) s += (double)partial[(size_t)b * nelem + e];
-  const int u = perm[c];
-  if (diag) s += (double)diag[u] * (double)in[u];
-  out[u] = (T)s;
+__global__ void __launch_bounds__(512) k_reduce(const T* __restrict__ partial, int grid, int64_t nelem,
+                                                const int32_t* __restrict__ cidx, const int32_t* __restrict__ perm,
+                                                const T* __restrict__ diag, const T* __restrict__ in,
+                                                T* __restrict__ out) {
+  constexpr int W = 16;
+  __shared__ double red[W][33];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int c = e < nelem ? cidx[e] : -1;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (c >= 0) {
+    int b = wp;
+    for (; b + 3 * W < grid; b += 4 * W) {
+      s0 += (double)partial[(size_t)b * nelem + e];
+      s1 += (double)partial[(size_t)(b + W) * nelem + e];
+      s2 += (double)partial[(size_t)(b + 2 * W) * nelem + e];
+      s3 += (double)partial[(size_t)(b + 3 * W) * nelem + e];
+    }
+    for (; b < grid; b += W) s0 += (double)partial[(size_t)b * nelem + e];
+  }
+  red[wp][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (wp == 0 && c >= 0) {
+    double t = 0.0;
+    for (int k = 0; k < W; ++k) t += red[k][lane];
+    const int u = perm[c];
+    if (diag) t += (double)diag[u] * (double)in[u];
+    out[u] = (T)t;
+  }
 }
 
 
@@ -300,7 +320,11 @@ __global__ void __launch_bounds__(512) k_reduce_v2(const T* __restrict__ partial
 
 // ------------------------------------------------------------------ host side
 
-static int elems_per_thread(int log2N) { return log2N >= 8 ? 16 : 8; }
+// elements per thread of the small-grid column kernel (N <= 256): four, so a
+// column of N = 256 runs on 64 threads (two warps: its FP64 arithmetic issues
+// from two SM sub-partitions and every thread's dependent chains are short),
+// eight below N = 64
+static int elems_per_thread(int log2N) { return log2N >= 6 ? 4 : 8; }
 
 // Records the start event of a timed column-kernel launch on st and returns
 // the end event to record after it (nullptr on failure).
@@ -457,8 +481,8 @@ static bem_status setup_t(bem_plan_s* p) {
     return BEM_ERR_UNSUPPORTED;
   }
   int bps = 0;
-  if (E == 16)
-    BEM_CUDA_TRY((configure_all<T, 16>(p->smem_bytes, p->threads, &bps)));
+  if (E == 4)
+    BEM_CUDA_TRY((configure_all<T, 4>(p->smem_bytes, p->threads, &bps)));
   else
     BEM_CUDA_TRY((configure_all<T, 8>(p->smem_bytes, p->threads, &bps)));
   if (bps < 1) {
@@ -876,12 +900,12 @@ static bem_status launch_v1(bem_plan_s* p, const Operator& op, const void* in, v
   cp.acc_in_smem = p->acc_in_smem ? 1 : 0;
   cudaEvent_t e1 = nullptr;
   if (timed && (e1 = timing_begin(p, st)) == nullptr) return BEM_ERR_CUDA;
-  if (elems_per_thread(p->log2N) == 16)
-    launch_col_nf<T, 16>(p, op.nf, cp, st);
+  if (elems_per_thread(p->log2N) == 4)
+    launch_col_nf<T, 4>(p, op.nf, cp, st);
   else
     launch_col_nf<T, 8>(p, op.nf, cp, st);
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k_reduce<T><<<(unsigned)((ga.nelem + tb - 1) / tb), tb, 0, st>>>(
+  k_reduce<T><<<(unsigned)((ga.nelem + 31) / 32), 512, 0, st>>>(
       static_cast<const T*>(sp.partial), p->grid, ga.nelem, ga.d_cidx, p->d_perm, static_cast<const T*>(op.diag),
       static_cast<const T*>(in), static_cast<T*>(out));
   BEM_CUDA_TRY(cudaGetLastError());

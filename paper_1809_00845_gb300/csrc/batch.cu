@@ -42,14 +42,15 @@ bem_status batch_issue_applies(bem_batch_s* b, const void* in, void* out, cudaSt
   return rc;
 }
 
-// Plans that share a grid (FP32 four-step, same thread count) are applied by
-// one grouped persistent launch; the kernel parameters of a group are built
-// here, before any capture, from the plans' current operators.
+// Plans that share a grid (FP32 four-step, same thread count) and a field
+// count are applied by one grouped persistent launch; the kernel parameters of
+// a group are built here, before any capture, from the plans' current
+// operators.
 static bem_status batch_build_groups(bem_batch_s* b) {
   for (auto& g : b->groups) group_free(g);
   b->groups.clear();
   b->solo.clear();
-  std::vector<int> by_threads;  // distinct thread counts of the eligible plans
+  std::vector<int> keys;  // distinct (thread count, field count) of the eligible plans
   std::vector<std::vector<int>> members;
   for (size_t i = 0; i < b->plans.size(); ++i) {
     const bem_plan_s* p = b->plans[i];
@@ -57,10 +58,13 @@ static bem_status batch_build_groups(bem_batch_s* b) {
       b->solo.push_back((int)i);
       continue;
     }
+    const Operator& op =
+        b->layer == BEM_SINGLE ? p->op_single : (b->layer == BEM_DOUBLE ? p->op_double : p->op_system);
+    const int key = p->threads * 8 + op.nf;
     size_t k = 0;
-    while (k < by_threads.size() && by_threads[k] != p->threads) ++k;
-    if (k == by_threads.size()) {
-      by_threads.push_back(p->threads);
+    while (k < keys.size() && keys[k] != key) ++k;
+    if (k == keys.size()) {
+      keys.push_back(key);
       members.emplace_back();
     }
     members[k].push_back((int)i);

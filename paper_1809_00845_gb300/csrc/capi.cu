@@ -180,6 +180,31 @@ static bem_status build_op3(bem_plan_s* p, Operator3D& op, const std::vector<std
   return BEM_OK;
 }
 
+// Leaves out the fields whose coefficients are all zero (for the boundary
+// conditions set, no cell feeds them: the sums they would add are zeros);
+// coup holds no rows of one entry per field.  At least one field stays.
+static void drop_zero_fields(std::vector<std::vector<double>>& cf, std::vector<int>& comps, int no,
+                             std::vector<int16_t>& coup) {
+  const int nf = (int)cf.size();
+  std::vector<int> keep;
+  for (int f = 0; f < nf; ++f)
+    if (std::any_of(cf[f].begin(), cf[f].end(), [](double v) { return v != 0.0; })) keep.push_back(f);
+  if (keep.empty()) keep.push_back(0);
+  if ((int)keep.size() == nf) return;
+  std::vector<std::vector<double>> cf2;
+  std::vector<int> comps2;
+  std::vector<int16_t> coup2;
+  for (int f : keep) {
+    cf2.push_back(std::move(cf[f]));
+    comps2.push_back(comps[f]);
+  }
+  for (int o = 0; o < no; ++o)
+    for (int f : keep) coup2.push_back(coup[(size_t)o * nf + f]);
+  cf.swap(cf2);
+  comps.swap(comps2);
+  coup.swap(coup2);
+}
+
 // Single and double layer of the 3D kernels.  Laplace: U / (Q_x, Q_y, Q_z)
 // (spectra 0, 1..3).  Kelvin: U_ab (fields b, outputs a) and T_ab = sum_c
 // G_abc n_c (fields (b, c) with coefficient w n_c, outputs a).
@@ -494,18 +519,25 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       ay[j] = p->h_w[j] * p->h_normal[2 * j + 1] * mN;
     }
     for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;  // user order
+    // fields that no cell feeds are left out (exact: they would add zeros):
+    // all-Dirichlet data needs U alone, all-Neumann data Q_x and Q_y alone
+    int64_t nneu = 0;
+    for (int64_t i = 0; i < nb; ++i) nneu += bc[i] ? 1 : 0;
+    const bool all_d = nneu == 0, all_n = nneu == nb;
     if (p->v2) {
-      // type 0 (Dirichlet): (w, 0) -> fields (U, -); type 1 (Neumann): (w n_x, w n_y) -> (Q_x, Q_y)
+      // type 0 (Dirichlet): (w, 0) -> fields (U, -); type 1 (Neumann): (w n_x, w n_y) -> (Q_x, Q_y);
+      // all-Neumann: type 0 with (w n_x, w n_y) -> fields (Q_x, Q_y)
       std::vector<double> ca(nb), cb(nb);
       std::vector<uint8_t> ty(nb);
       for (int64_t j = 0; j < nb; ++j) {
-        ty[j] = bc[p->h_perm[j]] ? 1 : 0;
-        ca[j] = ty[j] ? p->h_w[j] * p->h_normal[2 * j] : p->h_w[j];
-        cb[j] = ty[j] ? p->h_w[j] * p->h_normal[2 * j + 1] : 0.0;
+        const bool neu = bc[p->h_perm[j]] != 0;
+        ty[j] = neu && !all_n ? 1 : 0;
+        ca[j] = neu ? p->h_w[j] * p->h_normal[2 * j] : p->h_w[j];
+        cb[j] = neu ? p->h_w[j] * p->h_normal[2 * j + 1] : 0.0;
       }
-      s.nf = 3;
-      s.f[0] = {nullptr, 0, 0, 0, nullptr, nullptr};
-      s.f[1] = {nullptr, 0, 1, 0, nullptr, nullptr};
+      s.nf = all_d ? 1 : (all_n ? 2 : 3);
+      s.f[0] = {nullptr, 0, all_n ? 1 : 0, 0, nullptr, nullptr};
+      s.f[1] = {nullptr, 0, all_n ? 2 : 1, 0, nullptr, nullptr};
       s.f[2] = {nullptr, 0, 2, 0, nullptr, nullptr};
       if ((rc = build_op_v2(p, s, ca, cb, ty)) != BEM_OK) return rc;
       if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
@@ -520,13 +552,17 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     }
     if ((rc = build_slot_set(p, memD, &s.sets[0])) != BEM_OK) return rc;
     if ((rc = build_slot_set(p, memN, &s.sets[1])) != BEM_OK) return rc;
-    s.nf = 3;
-    s.f[0] = {nullptr, 0, 0, 0, &s.sets[0], nullptr};
-    s.f[1] = {nullptr, 0, 1, 0, &s.sets[1], nullptr};
-    s.f[2] = {nullptr, 0, 2, 0, &s.sets[1], nullptr};
-    if ((rc = upload_coef(p, s, aq, &s.f[0].coef)) != BEM_OK) return rc;
-    if ((rc = upload_coef(p, s, ax, &s.f[1].coef)) != BEM_OK) return rc;
-    if ((rc = upload_coef(p, s, ay, &s.f[2].coef)) != BEM_OK) return rc;
+    s.nf = 0;
+    if (!all_n) {
+      s.f[s.nf] = {nullptr, 0, 0, 0, &s.sets[0], nullptr};
+      if ((rc = upload_coef(p, s, aq, &s.f[s.nf++].coef)) != BEM_OK) return rc;
+    }
+    if (!all_d) {
+      s.f[s.nf] = {nullptr, 0, 1, 0, &s.sets[1], nullptr};
+      if ((rc = upload_coef(p, s, ax, &s.f[s.nf++].coef)) != BEM_OK) return rc;
+      s.f[s.nf] = {nullptr, 0, 2, 0, &s.sets[1], nullptr};
+      if ((rc = upload_coef(p, s, ay, &s.f[s.nf++].coef)) != BEM_OK) return rc;
+    }
     if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
     if ((rc = alloc_field_rho(p, s)) != BEM_OK) return rc;
   } else if (p->kernel == BEM_LAPLACE_3D) {
@@ -539,7 +575,10 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
       for (int a = 0; a < 3; ++a) cf[1 + a][j] = p->h_w[j] * p->h_normal[3 * j + a] * mN;
     }
     for (int64_t i = 0; i < nb; ++i) dg[i] = bc[i] ? -c : 0.0;
-    if ((rc = build_op3(p, p->op3_system, cf, {0, 0, 0, 0}, 1, {0, 1, 2, 3})) != BEM_OK) return rc;
+    std::vector<int> comps = {0, 0, 0, 0};
+    std::vector<int16_t> coup = {0, 1, 2, 3};
+    drop_zero_fields(cf, comps, 1, coup);
+    if ((rc = build_op3(p, p->op3_system, cf, comps, 1, coup)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
     p->op3_system.diag = s.diag;
   } else {
@@ -568,6 +607,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     }
     std::vector<double> dg(nb * 3);
     for (int64_t i = 0; i < nb * 3; ++i) dg[i] = bc[i] ? -c : 0.0;
+    drop_zero_fields(cf, comps, 3, coup);
     if ((rc = build_op3(p, p->op3_system, cf, comps, 3, coup)) != BEM_OK) return rc;
     if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
     p->op3_system.diag = s.diag;

@@ -93,20 +93,31 @@ __global__ void k_axpby(double a, const double* __restrict__ x, double b, double
   if (i < M) y[i] = a * x[i] + b * y[i];
 }
 
-// out[b*bs + i] = sum_j inv_b[i][j] in[b*bs + j]   (block-Jacobi M^-1)
-__global__ void k_block_apply(const double* __restrict__ inv, int bs, int64_t M, const double* __restrict__ in,
-                              double* __restrict__ out) {
+// out[b*bs + i] = sum_j inv_b[i][j] in[b*bs + j]   (block-Jacobi M^-1): CTA
+// (b, r) computes rows r*8 .. r*8+7 of block b, one warp per row (the lanes
+// read the row contiguously and add their products in a fixed tree)
+constexpr int kBlockApplyRows = 8;
+__global__ void __launch_bounds__(32 * kBlockApplyRows) k_block_apply(const double* __restrict__ inv, int bs,
+                                                                     int64_t M, const double* __restrict__ in,
+                                                                     double* __restrict__ out) {
   extern __shared__ double xin[];
-  const int b = blockIdx.x, i = threadIdx.x;
+  const int b = blockIdx.x, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t i0 = (int64_t)b * bs;
   const int sz = (int)(M - i0 < bs ? M - i0 : bs);
-  if (i < sz) xin[i] = in[i0 + i];
+  for (int j = threadIdx.x; j < sz; j += blockDim.x) xin[j] = in[i0 + j];
   __syncthreads();
+  const int i = blockIdx.y * kBlockApplyRows + wp;
   if (i >= sz) return;
   const double* row = inv + ((size_t)b * bs + i) * bs;
   double s = 0.0;
-  for (int j = 0; j < sz; ++j) s += row[j] * xin[j];
-  out[i0 + i] = s;
+  for (int j = lane; j < sz; j += 32) s += row[j] * xin[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[i0 + i] = s;
+}
+
+static inline dim3 block_apply_grid(int nblocks, int bs) {
+  return dim3((unsigned)nblocks, (unsigned)((bs + kBlockApplyRows - 1) / kBlockApplyRows));
 }
 
 // masked copies: um = data * (1 - bc), qm = data * bc
@@ -163,7 +174,8 @@ struct Gm {
       cudaMemcpyAsync(z, v, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
     } else {
       const int m = p->pc.bs * p->ncomp;
-      k_block_apply<<<p->pc.nblocks, m, m * sizeof(double), st>>>(p->pc.d_inv, m, M, v, z);
+      k_block_apply<<<block_apply_grid(p->pc.nblocks, m), 32 * kBlockApplyRows, m * sizeof(double), st>>>(
+          p->pc.d_inv, m, M, v, z);
     }
   }
   // out[0..nvec) = V[0..nvec) . w   (device)
@@ -605,15 +617,20 @@ __global__ void k_b_givens(int K, int m, int* __restrict__ jdev, const double* _
     double* c = cs + (int64_t)s * m;
     double* sv = sn + (int64_t)s * m;
     double* gv = g + (int64_t)s * (m + 1);
-    for (int i = 0; i <= j; ++i) col[i] = h1[(int64_t)s * ldh + i] + h2[(int64_t)s * ldh + i];
+    // the earlier rotations down the new column: entry i + 1 enters rotation
+    // i unrotated, entry i leaves it final, so only the running entry is
+    // carried from one rotation to the next (the loads do not wait on it)
+    const double* h1s = h1 + (int64_t)s * ldh;
+    const double* h2s = h2 + (int64_t)s * ldh;
     const double hn = sqrt(nrm2[s]);
-    col[j + 1] = hn;
+    double run = h1s[0] + h2s[0];
+#pragma unroll 4
     for (int i = 0; i < j; ++i) {
-      const double a = col[i], bb = col[i + 1];
-      col[i] = c[i] * a + sv[i] * bb;
-      col[i + 1] = -sv[i] * a + c[i] * bb;
+      const double bb = h1s[i + 1] + h2s[i + 1];
+      col[i] = c[i] * run + sv[i] * bb;
+      run = -sv[i] * run + c[i] * bb;
     }
-    const double a = col[j], bb = col[j + 1];
+    const double a = run, bb = hn;
     const double r = hypot(a, bb);
     c[j] = r > 0 ? a / r : 1.0;
     sv[j] = r > 0 ? bb / r : 0.0;
@@ -696,7 +713,8 @@ void batch_precond(bem_batch_s* bt, const double* v, double* z, cudaStream_t st)
       cudaMemcpyAsync(z + o, v + o, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
     } else {
       const int mb = p->pc.bs * p->ncomp;
-      k_block_apply<<<p->pc.nblocks, mb, mb * sizeof(double), st>>>(p->pc.d_inv, mb, M, v + o, z + o);
+      k_block_apply<<<block_apply_grid(p->pc.nblocks, mb), 32 * kBlockApplyRows, mb * sizeof(double), st>>>(
+          p->pc.d_inv, mb, M, v + o, z + o);
     }
   }
 }

@@ -41,6 +41,9 @@ struct bem_net_s {
   float* d_grad_b = nullptr;          // scratch: gradient wrt current layer input
   __nv_bfloat16* d_wb = nullptr;      // BF16 copy of the weights
   __nv_bfloat16* d_wbt = nullptr;     // the same per layer as [k][cin][cout] (coalesced forward reads)
+  // the BF16 copies match d_w: refreshed by the first forward after the
+  // parameters change (creation, set_params, a training step), on its stream
+  bool wb_fresh = false;
   double* d_loss = nullptr;
   int* d_seq = nullptr;               // sequence index per position
 };
@@ -226,14 +229,20 @@ static bem_status net_forward(bem_net_s* net, const float* feats, const int32_t*
   if (rc != BEM_OK) return rc;
   k_seq_index<<<nseq, 256, 0, st>>>(off, nseq, net->d_seq);
   k_to_bf16<<<nblk(T * net->cin, 256), 256, 0, st>>>(feats, net->d_act[0], T * net->cin);
-  k_to_bf16<<<nblk(net->nparams, 256), 256, 0, st>>>(net->d_w, net->d_wb, net->nparams);
+  if (!net->wb_fresh) {
+    k_to_bf16<<<nblk(net->nparams, 256), 256, 0, st>>>(net->d_w, net->d_wb, net->nparams);
+    for (int l = 0; l < net->layers; ++l) {
+      const int cin = l == 0 ? net->cin : net->hidden;
+      const int cout = l == net->layers - 1 ? 1 : net->hidden;
+      k_to_bf16_t<<<nblk((int64_t)cout * cin * net->ksize, 256), 256, 0, st>>>(
+          net->d_w + net->woff[l], net->d_wbt + net->woff[l], cout, cin, net->ksize);
+    }
+    net->wb_fresh = true;
+  }
   for (int l = 0; l < net->layers; ++l) {
     const int cin = l == 0 ? net->cin : net->hidden;
     const bool last = l == net->layers - 1;
     const int cout = last ? 1 : net->hidden;
-    k_to_bf16_t<<<nblk((int64_t)cout * cin * net->ksize, 256), 256, 0, st>>>(net->d_w + net->woff[l],
-                                                                             net->d_wbt + net->woff[l], cout, cin,
-                                                                             net->ksize);
     k_conv_fwd<<<nblk(T * cout, 256), 256, 0, st>>>(net->d_act[l], cin, cout, net->ksize, net->dil[l],
                                                    net->d_wbt + net->woff[l], net->d_w + net->boff[l], off,
                                                    net->d_seq, T, net->d_pre[l], last ? nullptr : net->d_act[l + 1]);
@@ -370,6 +379,7 @@ bem_status bem_net_set_params(bem_net_t net, const float* host) {
   BEM_CUDA_TRY(cudaMemset(net->d_m, 0, net->nparams * sizeof(float)));
   BEM_CUDA_TRY(cudaMemset(net->d_v, 0, net->nparams * sizeof(float)));
   net->step = 0;
+  net->wb_fresh = false;
   return BEM_OK;
 }
 
@@ -417,6 +427,7 @@ bem_status bem_net_train_step(bem_net_t net, const float* feats, const int32_t* 
   const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
   k_adam<<<nblk(net->nparams, 256), 256, 0, st>>>(net->d_w, net->d_g, net->d_m, net->d_v, net->nparams, lr, b1, b2,
                                                  1e-8f, c1, c2);
+  net->wb_fresh = false;
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
