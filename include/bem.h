@@ -417,6 +417,25 @@ bem_status bem_net_destroy(bem_net_t net);
  * (reduced to [0, 1) turns), FP64 sums.  Asynchronous on `stream`. */
 bem_status bem_dtn_estimate(const float* s, const float* len, const float* u, const int32_t* offsets, int nseq,
                             int64_t T, int kmax, float* out, void* stream);
+/* Input columns of the 2D guess network per curve q (elements offsets[q] ..
+ * offsets[q+1]): with sc_q the root mean square of u over the curve (1 when it
+ * is zero),
+ *   feats[j] = (geo[j][0 .. G), u_j / sc_q, radius * qd_j / sc_q),
+ * geo device FP32 [T][G] (G <= 64), u and qd (the Dirichlet-to-Neumann
+ * estimate) device FP32 [T], feats device FP32 [T][G + 2]; offsets device
+ * int32 [nseq + 1], non-decreasing from 0 to T (not checked on the device).
+ * FP64 scale, FP32 results; asynchronous on `stream`. */
+bem_status bem_guess_features(const float* geo, int G, const float* u, const float* qd, const int32_t* offsets,
+                              int nseq, int64_t T, float radius, float* feats, void* stream);
+/* The guess of the interior Dirichlet problem from the network's output per
+ * curve q (sc_q as above):
+ *   x_j = qd_j + cscale * sc_q * corr_j,
+ *   out_j = x_j - (sum_j len_j x_j) / (sum_j len_j),
+ * so that the guessed flux integrates to zero over the curve, as the flux of
+ * every field harmonic inside does (divergence theorem).  qd, corr, u, len,
+ * out device FP32 [T]; offsets as above; FP64 sums; asynchronous. */
+bem_status bem_guess_finish(const float* qd, const float* corr, const float* u, const float* len,
+                            const int32_t* offsets, int nseq, int64_t T, float cscale, float* out, void* stream);
 /* Random Fourier features of 3D points (the input encoding of the 3D point
  * network, which is bem_net_* with ksize = 1: the same weights applied to
  * every point independently):

@@ -131,3 +131,40 @@ def fourier_features(points, B):
     out[:, 0::2] = np.sin(ph)
     out[:, 1::2] = np.cos(ph)
     return out
+
+
+def _rms_or_one(u):
+    r = float(np.sqrt(np.mean(np.asarray(u, np.float64) ** 2))) if np.size(u) else 0.0
+    return r if r > 0 else 1.0
+
+
+def guess_features(geo, u, qd, offsets, radius):
+    """Input columns of the 2D guess network (``bem_guess_features``), FP64:
+    per curve, with s the root mean square of u over it (1 when zero), the
+    geometry columns followed by u / s and radius * qd / s -> (T, G + 2)."""
+    geo = np.asarray(geo, np.float64).reshape(len(u), -1)
+    u = np.asarray(u, np.float64)
+    qd = np.asarray(qd, np.float64)
+    out = np.zeros((u.size, geo.shape[1] + 2))
+    for q in range(len(offsets) - 1):
+        a, b = int(offsets[q]), int(offsets[q + 1])
+        s = _rms_or_one(u[a:b])
+        out[a:b, :geo.shape[1]] = geo[a:b]
+        out[a:b, -2] = u[a:b] / s
+        out[a:b, -1] = radius * qd[a:b] / s
+    return out
+
+
+def guess_finish(qd, corr, u, length, offsets, cscale):
+    """The learned guess (``bem_guess_finish``), FP64: per curve x = qd +
+    cscale * s * corr (s the rms of u), shifted by the length-weighted mean of
+    x so that sum_j length_j x_j = 0 (the zero net flux of a field harmonic
+    inside the curve)."""
+    qd, corr, u, length = (np.asarray(a, np.float64) for a in (qd, corr, u, length))
+    out = np.zeros(qd.size)
+    for q in range(len(offsets) - 1):
+        a, b = int(offsets[q]), int(offsets[q + 1])
+        x = qd[a:b] + cscale * _rms_or_one(u[a:b]) * corr[a:b]
+        L = length[a:b].sum()
+        out[a:b] = x - (np.dot(length[a:b], x) / L if L > 0 else 0.0)
+    return out

@@ -39,7 +39,7 @@ EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner
             "bem_batch_apply", "bem_batch_set_grouping", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
             "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step",
-            "bem_measure_peak", "bem_dtn_estimate", "bem_fourier_features"]
+            "bem_measure_peak", "bem_dtn_estimate", "bem_guess_features", "bem_guess_finish", "bem_fourier_features"]
 
 
 class BemError(RuntimeError):
@@ -128,6 +128,10 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = I
     lib.bem_dtn_estimate.argtypes = [P, P, P, P, I, I64, I, P, P]
     lib.bem_dtn_estimate.restype = I
+    lib.bem_guess_features.argtypes = [P, I, P, P, P, I, I64, ctypes.c_float, P, P]
+    lib.bem_guess_features.restype = I
+    lib.bem_guess_finish.argtypes = [P, P, P, P, P, I, I64, ctypes.c_float, P, P]
+    lib.bem_guess_finish.restype = I
     lib.bem_fourier_features.argtypes = [P, I64, P, I, P, P]
     lib.bem_fourier_features.restype = I
     lib.bem_measure_peak.argtypes = [I, ctypes.POINTER(D), P]
@@ -599,6 +603,56 @@ def dtn_estimate(s, length, u, offsets, kmax, stream=None):
                                            ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(o.data_ptr()),
                                            oh.size - 1, T, int(kmax), ctypes.c_void_p(out.data_ptr()),
                                            _stream_ptr(stream)))
+    return out
+
+
+def _seq_offsets(offsets, T):
+    """Host copy of sequence offsets, checked: start at 0, do not decrease,
+    end at T (so the kernels never index past their arrays)."""
+    import torch
+    oh = (offsets.cpu().numpy() if isinstance(offsets, torch.Tensor) else np.asarray(offsets)).reshape(-1)
+    if oh.size < 2 or oh[0] != 0 or oh[-1] != T or np.any(np.diff(oh) < 0):
+        raise ValueError("offsets must start at 0, not decrease and end at T")
+    return oh
+
+
+def _cuda_f32(a):
+    import torch
+    t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+    return t.to(device="cuda", dtype=torch.float32).contiguous()
+
+
+def guess_features(geo, u, qd, offsets, radius, stream=None):
+    """Input columns of the 2D guess network (bem_guess_features): geo (T, G)
+    geometry columns, u and qd (T); returns a CUDA float32 tensor (T, G + 2)."""
+    import torch
+    g, u, qd = _cuda_f32(geo), _cuda_f32(u).reshape(-1), _cuda_f32(qd).reshape(-1)
+    T = u.numel()
+    if g.ndim != 2 or g.shape[0] != T or not (0 <= g.shape[1] <= 64) or qd.numel() != T:
+        raise ValueError("geo must be (T, G) with G <= 64, u and qd T values")
+    oh = _seq_offsets(offsets, T)
+    out = torch.empty((T, g.shape[1] + 2), dtype=torch.float32, device="cuda")
+    _check(load_library().bem_guess_features(ctypes.c_void_p(g.data_ptr()), int(g.shape[1]),
+                                             ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(qd.data_ptr()),
+                                             ctypes.c_void_p(_device_offsets(oh).data_ptr()), oh.size - 1, T,
+                                             float(radius), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def guess_finish(qd, corr, u, length, offsets, cscale, stream=None):
+    """The zero-flux guess from the network's output (bem_guess_finish); a
+    CUDA float32 tensor (T)."""
+    import torch
+    qd, corr, u, ln = (_cuda_f32(a).reshape(-1) for a in (qd, corr, u, length))
+    T = qd.numel()
+    if corr.numel() != T or u.numel() != T or ln.numel() != T:
+        raise ValueError("qd, corr, u, length must hold T values")
+    oh = _seq_offsets(offsets, T)
+    out = torch.empty(T, dtype=torch.float32, device="cuda")
+    _check(load_library().bem_guess_finish(ctypes.c_void_p(qd.data_ptr()), ctypes.c_void_p(corr.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(ln.data_ptr()),
+                                           ctypes.c_void_p(_device_offsets(oh).data_ptr()), oh.size - 1, T,
+                                           float(cscale), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
 

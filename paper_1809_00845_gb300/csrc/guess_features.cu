@@ -1,6 +1,7 @@
 // Input features of the learned initial guesses (the paper has no learned
 // component): the arclength Dirichlet-to-Neumann estimate of closed curves
-// (2D) and random Fourier features of surface points (3D point network).
+// (2D), the network's input columns and the assembled guess (2D), and random
+// Fourier features of surface points (3D point network).
 //
 // Dirichlet-to-Neumann estimate.
 // For the interior Laplace problem on a circle the Dirichlet-to-Neumann map is
@@ -118,10 +119,86 @@ __global__ void k_fourier_features(const float* __restrict__ pts, int64_t T, con
   out[t * 2 * F + 2 * f + 1] = (float)cs;
 }
 
+// root mean square of u over the sequence's elements, 1 when it is zero (the
+// scale of the guess's inputs and outputs)
+__device__ __forceinline__ double seq_rms(const float* __restrict__ u, int j0, int j1, double* red) {
+  double s = 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += kDtnThreads) s += (double)u[j] * (double)u[j];
+  s = block_sum(s, red);
+  const double r = j1 > j0 ? sqrt(s / (double)(j1 - j0)) : 0.0;
+  return r > 0.0 ? r : 1.0;
+}
+
+// block q: feats[j] = (geo[j][0..G), u_j / sc, radius qd_j / sc), sc the rms of u
+__global__ void __launch_bounds__(kDtnThreads) k_guess_features(const float* __restrict__ geo, int G,
+                                                                const float* __restrict__ u,
+                                                                const float* __restrict__ qd,
+                                                                const int32_t* __restrict__ off, float radius,
+                                                                float* __restrict__ feats) {
+  __shared__ double red[kDtnThreads / 32];
+  const int q = blockIdx.x, j0 = off[q], j1 = off[q + 1];
+  const double sc = seq_rms(u, j0, j1, red);
+  const int C = G + 2;
+  for (int j = j0 + threadIdx.x; j < j1; j += kDtnThreads) {
+    for (int c = 0; c < G; ++c) feats[(size_t)j * C + c] = geo[(size_t)j * G + c];
+    feats[(size_t)j * C + G] = (float)((double)u[j] / sc);
+    feats[(size_t)j * C + G + 1] = (float)((double)radius * (double)qd[j] / sc);
+  }
+}
+
+// block q: x_j = qd_j + cscale sc corr_j, out_j = x_j - sum(len x) / sum(len)
+__global__ void __launch_bounds__(kDtnThreads) k_guess_finish(const float* __restrict__ qd,
+                                                              const float* __restrict__ corr,
+                                                              const float* __restrict__ u,
+                                                              const float* __restrict__ len,
+                                                              const int32_t* __restrict__ off, float cscale,
+                                                              float* __restrict__ out) {
+  __shared__ double red[kDtnThreads / 32];
+  const int q = blockIdx.x, j0 = off[q], j1 = off[q + 1];
+  const double f = (double)cscale * seq_rms(u, j0, j1, red);
+  double sl = 0.0, sx = 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += kDtnThreads) {
+    const double x = (double)qd[j] + f * (double)corr[j];
+    sl += (double)len[j];
+    sx += (double)len[j] * x;
+  }
+  sl = block_sum(sl, red);
+  sx = block_sum(sx, red);
+  const double mean = sl > 0.0 ? sx / sl : 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += kDtnThreads)
+    out[j] = (float)((double)qd[j] + f * (double)corr[j] - mean);
+}
+
 }  // namespace
 }  // namespace bemfft
 
 using namespace bemfft;
+
+extern "C" bem_status bem_guess_features(const float* geo, int G, const float* u, const float* qd,
+                                         const int32_t* offsets, int nseq, int64_t T, float radius, float* feats,
+                                         void* stream) {
+  if (!geo || !u || !qd || !offsets || !feats || G < 0 || G > 64 || nseq < 1 || T < 1) {
+    set_error("bem_guess_features: null pointer, or G, nseq, T out of range");
+    return BEM_ERR_ARG;
+  }
+  k_guess_features<<<nseq, kDtnThreads, 0, static_cast<cudaStream_t>(stream)>>>(geo, G, u, qd, offsets, radius,
+                                                                               feats);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
+
+extern "C" bem_status bem_guess_finish(const float* qd, const float* corr, const float* u, const float* len,
+                                       const int32_t* offsets, int nseq, int64_t T, float cscale, float* out,
+                                       void* stream) {
+  if (!qd || !corr || !u || !len || !offsets || !out || nseq < 1 || T < 1) {
+    set_error("bem_guess_finish: null pointer, or nseq, T out of range");
+    return BEM_ERR_ARG;
+  }
+  k_guess_finish<<<nseq, kDtnThreads, 0, static_cast<cudaStream_t>(stream)>>>(qd, corr, u, len, offsets, cscale,
+                                                                             out);
+  BEM_CUDA_TRY(cudaGetLastError());
+  return BEM_OK;
+}
 
 extern "C" bem_status bem_fourier_features(const float* points, int64_t T, const float* B, int F, float* out,
                                            void* stream) {

@@ -24,7 +24,13 @@ Guess = physics estimate + learned correction:
         (x - 1/2, y - 1/2, n_x, n_y, L/h, u/s, a q_dtn/s),
     s = rms(u), a = 0.3 (the curves' radius), to the correction a (q - q_dtn)/s
     (an earlier form also took the double layer of the data as an input; the
-    operator apply it cost per guess outweighed the iterations it saved).
+    operator apply it cost per guess outweighed the iterations it saved);
+  * the sum is shifted so that its flux integrates to zero over the curve
+    (``bem_guess_finish``), as the flux of a field harmonic inside does.  The
+    network's correction alone leaves a net flux of a few per cent, and the
+    single layer weighs that constant mode most: measured on 12 held-out
+    stars, the shift cuts the guess's initial residual from 0.13 to 0.05 of
+    the zero start's (the estimate alone: 0.15).
 Training targets are solutions of the method (FP32 GMRES with double-float
 residual refinement to 1e-7).  At solve time the guess is passed to
 ``bem_solve`` as x0; the solver replaces a start whose residual exceeds the
@@ -189,7 +195,8 @@ def predict(net, b, u, qd, tscale=1.0):
     f, s = features(b, u, qd)
     off = np.array([0, f.shape[0]], np.int32)
     corr = net.forward(f, off).cpu().numpy().astype(np.float64) * tscale
-    return qd + corr * s / RADIUS
+    x = qd + corr * s / RADIUS
+    return x - np.sum(b.length * x) / np.sum(b.length)
 
 
 class Guesser:
@@ -219,10 +226,12 @@ class Guesser:
         ut = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
         qd = B.dtn_estimate(self.s, self.len, ut, self.off_host, self.kmax)
         if use_net:
-            sc = torch.sqrt(torch.mean(ut * ut)).clamp_min(1e-30)
-            f = torch.cat([self.geo, torch.stack([ut / sc, RADIUS * qd / sc], dim=1)], dim=1)
+            f = B.guess_features(self.geo, ut, qd, self.off_host, RADIUS)
             corr = self.net.forward(f, self.off_host)
-            x0 = qd + corr * (self.tscale * sc / RADIUS)
+            # the network's correction carries a net flux, which the single
+            # layer amplifies most; the guess drops it (zero for a field
+            # harmonic inside)
+            x0 = B.guess_finish(qd, corr, ut, self.len, self.off_host, self.tscale / RADIUS)
         else:
             x0 = qd
         return x0.double().cpu().numpy()

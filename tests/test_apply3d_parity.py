@@ -70,6 +70,32 @@ def test_kelvin_random_cells(torch_cuda, oracle_mod, prec, n, nb):
     assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_system_operator_uniform_bc_3d(torch_cuda, oracle_mod, prec):
+    """All-Dirichlet and all-Neumann data in 3D (Laplace and Kelvin, the
+    latter also with one component Neumann everywhere): the system operator
+    leaves out the fields no cell feeds and must still be the oracle's."""
+    rng = np.random.default_rng(77)
+    b = I.random_cells(32, 300, rng, dim=3)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, "laplace3d", prec)
+    for fill in (0, 1, 0):
+        bc = np.full(b.nb, fill, np.uint8)
+        plan.set_bc(bc, 0.5)
+        ref = oracle_mod.system_apply("laplace3d", b.cell, b.h, b.w, b.normal, bc, x)
+        assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref) <= TOL[prec], fill
+    plan.close()
+    xk = rng.standard_normal((b.nb, 3))
+    plan = _plan(b, "kelvin3d", prec, nu=0.3, mu=1.0)
+    patterns = [np.zeros((b.nb, 3), np.uint8), np.ones((b.nb, 3), np.uint8), np.zeros((b.nb, 3), np.uint8)]
+    patterns[2][:, 1] = 1
+    for bc in patterns:
+        plan.set_bc(bc, 0.5)
+        ref = oracle_mod.system_apply("kelvin3d", b.cell, b.h, b.w, b.normal, bc, xk, nu=0.3, mu=1.0)
+        assert rel_l2(gpu_apply(torch_cuda, plan, "system", xk), ref) <= TOL[prec], bc[0]
+    plan.close()
+
+
 def test_kelvin_other_material(torch_cuda, oracle_mod):
     rng = np.random.default_rng(5)
     b = I.random_cells(16, 40, rng, dim=3)

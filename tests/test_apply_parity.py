@@ -91,6 +91,31 @@ def test_system_operator_mixed_bc(torch_cuda, oracle_mod, prec):
     assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref2) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n", [64, 256, 512])
+def test_system_operator_uniform_bc(torch_cuda, oracle_mod, prec, n):
+    """All-Dirichlet and all-Neumann data: the system operator leaves out the
+    fields no cell feeds (U alone, or Q_x and Q_y alone) and must still be
+    the oracle's BC-split operator (Eq. 15), on both column kernels (n < 256:
+    the small-grid kernel; n >= 256: the four-step kernel)."""
+    rng = np.random.default_rng(50 + n)
+    b = I.star_boundary(n)
+    x = rng.standard_normal(b.nb)
+    plan = _plan(b, prec)
+    for fill, c in ((0, 0.5), (1, 0.5), (1, 0.25), (0, 0.5)):
+        bc = np.full(b.nb, fill, np.uint8)
+        plan.set_bc(bc, c)
+        ref = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x, c=c)
+        err = rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref)
+        assert err <= TOL[prec], (fill, c, err)
+    # back to mixed data: all three fields again
+    bc = I.mixed_bc_theta(b)
+    plan.set_bc(bc, 0.5)
+    ref = oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
+    assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref) <= TOL[prec]
+    plan.close()
+
+
 def test_circle_config_f64(torch_cuda, oracle_mod):
     """Circle R = 0.35 on 128^2 (356 cells), FP64, single and double layer."""
     b = I.circle_boundary(128, 0.35)

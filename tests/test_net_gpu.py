@@ -113,6 +113,31 @@ def test_dtn_estimate_matches_oracle(torch_cuda):
         assert err < bound, (kmax, err, bound)
 
 
+def test_guess_features_and_finish_match_oracle(torch_cuda):
+    """bem_guess_features and bem_guess_finish (FP64 sums, FP32 in and out)
+    against the FP64 oracle on a batch of three curves; the guess's flux
+    integrates to zero on every curve to FP32 rounding."""
+    from paper_1809_00845_gb300 import bem
+    rng = np.random.default_rng(31)
+    lens = [300, 517, 64]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    T = int(off[-1])
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    geo, u, qd, corr = rng.standard_normal((T, 5)), 3 * rng.standard_normal(T), rng.standard_normal(T), \
+        rng.standard_normal(T)
+    length = rng.uniform(0.5, 1.5, T) * 1e-3
+    got = bem.guess_features(geo, u, qd, off, 0.3).cpu().numpy()
+    ref = N.guess_features(f32(geo), f32(u), f32(qd), off, 0.3)
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
+    got = bem.guess_finish(qd, corr, u, length, off, 0.8).cpu().numpy().astype(np.float64)
+    ref = N.guess_finish(f32(qd), f32(corr), f32(u), f32(length), off, 0.8)
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+    for a, b in zip(off[:-1], off[1:]):
+        assert abs(np.dot(length[a:b], got[a:b])) <= 1e-6 * np.dot(length[a:b], np.abs(got[a:b]))
+    with pytest.raises(ValueError):
+        bem.guess_finish(qd, corr, u, length, [0, 5, 4, T], 1.0)
+
+
 def _surface_points(rng, T):
     """Points on an ellipsoid (0.4, 0.3, 0.2) about (0.5, 0.5, 0.5) and their outward normals."""
     v = rng.standard_normal((T, 3))

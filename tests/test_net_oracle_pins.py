@@ -126,3 +126,41 @@ def test_fourier_features_definition():
     g = N.fourier_features(pts, Bi)
     np.testing.assert_allclose(g[:, 0::2] ** 2 + g[:, 1::2] ** 2, 1.0, atol=1e-14)
     np.testing.assert_allclose(N.fourier_features(pts + np.array([1.0, -2.0, 3.0]), Bi), g, atol=1e-12)
+
+
+def test_guess_features_definition():
+    """Hand-computed columns: a curve with u = (3, -4) (rms 3.5355...) and
+    qd = (1, 2), radius 0.3; a second curve of zeros keeps scale 1; the
+    geometry columns pass through in order."""
+    geo = np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0]])
+    u = np.array([3.0, -4.0, 0.0])
+    qd = np.array([1.0, 2.0, 0.0])
+    f = N.guess_features(geo, u, qd, [0, 2, 3], 0.3)
+    s = np.sqrt(12.5)
+    np.testing.assert_allclose(f[:, :2], geo, rtol=0, atol=0)
+    np.testing.assert_allclose(f[:2, 2], [3 / s, -4 / s], rtol=1e-15)
+    np.testing.assert_allclose(f[:2, 3], [0.3 / s, 0.6 / s], rtol=1e-15)
+    np.testing.assert_array_equal(f[2, 2:], [0.0, 0.0])
+
+
+def test_guess_finish_zero_flux_and_scaling():
+    """The guess has zero length-weighted sum on every curve, leaves a
+    zero-flux qd unchanged when corr = 0, is linear in corr with the factor
+    cscale * rms(u), and a constant corr is removed entirely."""
+    rng = np.random.default_rng(21)
+    off = [0, 40, 100]
+    length = rng.uniform(0.5, 2.0, 100)
+    u = rng.standard_normal(100)
+    corr = rng.standard_normal(100)
+    qd = rng.standard_normal(100)
+    for a, b in zip(off[:-1], off[1:]):
+        qd[a:b] -= np.dot(length[a:b], qd[a:b]) / length[a:b].sum()
+    out = N.guess_finish(qd, corr, u, length, off, 0.7)
+    for a, b in zip(off[:-1], off[1:]):
+        assert abs(np.dot(length[a:b], out[a:b])) < 1e-12 * length[a:b].sum()
+    np.testing.assert_allclose(N.guess_finish(qd, np.zeros(100), u, length, off, 0.7), qd, atol=1e-14)
+    np.testing.assert_allclose(N.guess_finish(qd, np.ones(100), u, length, off, 0.7), qd, atol=1e-14)
+    d = N.guess_finish(qd, 2 * corr, u, length, off, 0.7) - N.guess_finish(qd, corr, u, length, off, 0.7)
+    s0 = np.sqrt(np.mean(u[:40] ** 2))
+    c0 = 0.7 * s0 * corr[:40]
+    np.testing.assert_allclose(d[:40], c0 - np.dot(length[:40], c0) / length[:40].sum(), atol=1e-13)
