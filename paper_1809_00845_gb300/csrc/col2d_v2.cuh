@@ -387,6 +387,108 @@ __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColD
   }
 }
 
+// One walk over the thread's cells for the kernels that take the fields one at
+// a time (FP64, double-float, one field): SPARSE forms the x-DFT row sums of
+// field FSEL of column kx (as sparse_rows; to out0 at the row slot), GATHER
+// adds the output-pruned inverse x-DFT of the field transformed before it in
+// the same column from its rows (scaled by the column weight) into the
+// accumulators.  Both use the column's sparse twiddle: the first walk of a
+// column (FIRST) evaluates it and keeps it in the cache, the later walks read
+// it there (or evaluate it again when there is no cache).
+template <typename T, int NF, int FSEL, int TTC, bool EDGE, bool SPARSE, bool GATHER, bool FIRST>
+__device__ __forceinline__ void walk_field(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx, int cnt,
+                                           cplx<T>* out0, cplx<T>* carry, const cplx<T>* rows, T* sacc, T* gacc,
+                                           int qs, const Twiddles2L<T>& tw, cplx<T>* twc, cplx<T> fx) {
+  static_assert(!(FIRST && GATHER), "the first walk of a column gathers nothing");
+  const int Nm = g.N - 1;
+  const int t = threadIdx.x, TT = g.TT;
+  const bool cached = !FIRST && twc != nullptr;
+  cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
+  uint32_t mn[CB];
+  cplx<T> vn[CB], wn[CB];
+  T cn[CB];
+  auto fetch = [&](int base) {
+    const int pos = base * TT + t;
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      mn[i] = __ldg(p.meta + pos + i * TT);
+      if constexpr (SPARSE) {
+        vn[i] = p.val[pos + i * TT];
+        if constexpr (EDGE) cn[i] = p.val2[pos + i * TT];
+      }
+      if (cached) wn[i] = twc[pos + i * TT];
+    }
+  };
+  if (cnt > 0) fetch(0);
+  for (int i0 = 0; i0 < cnt; i0 += CB) {
+    uint32_t mt[CB];
+    cplx<T> vv[CB], w[CB];
+    T cc3[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      mt[i] = mn[i];
+      if constexpr (SPARSE) {
+        vv[i] = vn[i];
+        if constexpr (EDGE) cc3[i] = cn[i];
+      }
+      if (cached) w[i] = wn[i];
+    }
+    if (i0 + CB < cnt) fetch(i0 + CB);
+    if (!cached) {
+#pragma unroll
+      for (int i = 0; i < CB; ++i) w[i] = tw.template get<-1>((kx * meta_x(mt[i])) & Nm);
+      if (FIRST && twc) {
+#pragma unroll
+        for (int i = 0; i < CB; ++i)
+          if (i0 + i < cnt) twc[(i0 + i) * TT + t] = w[i];
+      }
+    }
+    if constexpr (GATHER) {
+      cplx<T> Y[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) Y[i] = rows[meta_slot(mt[i])];
+#pragma unroll
+      for (int i = 0; i < CB; ++i)
+        if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += Y[i].x * w[i].x + Y[i].y * w[i].y;
+    }
+    if constexpr (SPARSE) {
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        if (i0 + i >= cnt) continue;
+        if constexpr (EDGE) {
+          if (FSEL <= 0) {
+            s0.x += vv[i].x * w[i].x;
+            s0.y += vv[i].x * w[i].y;
+            s1.x += vv[i].y * w[i].x;
+            s1.y += vv[i].y * w[i].y;
+          } else {
+            s2.x += cc3[i] * w[i].x;
+            s2.y += cc3[i] * w[i].y;
+          }
+          if (mt[i] & kMetaFlush) {
+            const int row = meta_slot(mt[i]);
+            const bool car = (mt[i] & kMetaCarry) != 0;
+            (car ? carry + t : out0 + row)[0] = FSEL <= 0 ? s0 + cmul(fx, s1) : s2;
+            s0 = s1 = s2 = {T(0), T(0)};
+          }
+        } else {
+          const bool ty = (mt[i] >> 31) != 0;
+          const T a = vv[i].x, b = vv[i].y;
+          const T c = FSEL <= 0 ? (ty ? T(0) : a) : (FSEL == 1 ? (ty ? a : b) : (ty ? b : T(0)));
+          s0.x += c * w[i].x;
+          s0.y += c * w[i].y;
+          if (mt[i] & kMetaFlush) {
+            const int row = meta_slot(mt[i]);
+            const bool car = (mt[i] & kMetaCarry) != 0;
+            (car ? carry + t : out0 + row)[0] = s0;
+            s0 = {T(0), T(0)};
+          }
+        }
+      }
+    }
+  }
+}
+
 // field-indexed parameters without dynamic indexing of the parameter arrays
 template <typename T>
 __device__ __forceinline__ const T* spec_of(const Col2Dv2Params<T>& p, int f) {
@@ -583,22 +685,28 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
       gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
     }
   } else {
+    // one field at a time; the walk that forms field f's rows also gathers
+    // field f - 1 (whose output rows wait in sA[0, n) while the new sums go to
+    // sA + n), and the column's last field is gathered by a walk of its own
     cplx<T> fx = {T(0), T(0)};
     if constexpr (EDGE) fx = diff_factor(tw, kx, half);
+    cplx<T>* r0 = sA + n;
+    const bool dbl = kx != 0 && kx != n;  // the gather's column weight 2
 #pragma unroll 1
     for (int f = 0; f < NF; ++f) {
-      if (f > 0) __syncthreads();  // previous field's gather has finished reading sA
-      if (NF == 1) sparse_rows<T, NF, -1>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
-      else if (f == 0) sparse_rows<T, NF, 0, TTC, EDGE>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc, fx);
-      else if (f == 1) sparse_rows<T, NF, 1, TTC, EDGE>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc, fx);
-      else sparse_rows<T, NF, 2>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc);
+      if (f == 0) walk_field<T, NF, 0, TTC, EDGE, true, false, true>(p, g, kx, cnt, r0, sm.carry, sA, sacc, gacc, qs,
+                                                                     tw, twc, fx);
+      else if (f == 1) walk_field<T, NF, 1, TTC, EDGE, true, true, false>(p, g, kx, cnt, r0, sm.carry, sA, sacc, gacc,
+                                                                          qs, tw, twc, fx);
+      else walk_field<T, NF, 2, TTC, EDGE, true, true, false>(p, g, kx, cnt, r0, sm.carry, sA, sacc, gacc, qs, tw,
+                                                              twc, fx);
       __syncthreads();
       if (p.has_carry) {
-        add_carries<T, NF, 0>(p, g, cnt, __ldg(p.tinfo + t) >> 8, sA, sF, sm.carry);
+        add_carries<T, NF, 0>(p, g, cnt, __ldg(p.tinfo + t) >> 8, r0, sF, sm.carry);
         __syncthreads();
       }
       cplx<T> v[16];
-      load_rows(p, g, sA, v);
+      load_rows(p, g, r0, v);
       __syncthreads();
       load_spectrum(p, g, f, kx, sm.sS);
       fs.template forward<true>(v);
@@ -612,10 +720,11 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
       spectral_multiply<T, false>(sm.sS, spec_addr(fs, g), imag_of(p, f) != 0, oddy_of(p, f) != 0, v, v);
       fs.inverse(v);
 #pragma unroll
-      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = v[m];
+      for (int m = 0; m < 8; ++m) sA[rowslot(t + m * TT)] = dbl ? v[m] + v[m] : v[m];
       __syncthreads();
-      gather_cells(p, g, kx, cnt, sA, tw, sacc, gacc, qs, twc);
     }
+    walk_field<T, NF, 0, TTC, EDGE, false, true, false>(p, g, kx, cnt, nullptr, nullptr, sA, sacc, gacc, qs, tw, twc,
+                                                        fx);
   }
 }
 

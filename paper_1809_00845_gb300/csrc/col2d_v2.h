@@ -47,11 +47,13 @@ struct Col2Dv2Params {
 // cells per batch of the cell walks of the column kernel: the loads of a
 // batch are issued together, one batch ahead of its use, so each batch's
 // memory round trip overlaps the arithmetic of the one before (two batches of
-// loads live at once: 4 cells keep the 512-thread kernels within their 128
-// registers).  The interleaved cell arrays hold a multiple of CB cells per
+// loads live at once).  Measured on the 4096^2 star (system apply, us): 1
+// cell 612, 2 cells 588, 3 cells 593, 4 cells 599, 5 cells 653, 6 cells 691
+// (spills); 2 cells also give the fastest accuracy-mode, double-float and
+// FP64 applies.  The interleaved cell arrays hold a multiple of CB cells per
 // thread, so a batch is always read whole.
 #ifndef COL2D_CELL_BATCH
-#define COL2D_CELL_BATCH 4
+#define COL2D_CELL_BATCH 2
 #endif
 constexpr int CB = COL2D_CELL_BATCH;
 
