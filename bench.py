@@ -151,7 +151,7 @@ class ClockSampler:
 # system operator, from one ncu capture of the launch list, keyed by the hash of
 # the kernel sources it was measured on; reported (as a stored measurement) only
 # while the sources are unchanged.
-MEASURED_TRAFFIC = {"n4096_f32_star_system": ("6a4eaff781ab489a", 202.33e6)}
+MEASURED_TRAFFIC = {"n4096_f32_star_system": ("6c9140433d1272b9", 202.55e6)}
 
 
 def kernel_source_hash():
