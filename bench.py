@@ -151,7 +151,7 @@ class ClockSampler:
 # system operator, from one ncu capture of the launch list, keyed by the hash of
 # the kernel sources it was measured on; reported (as a stored measurement) only
 # while the sources are unchanged.
-MEASURED_TRAFFIC = {"n4096_f32_star_system": ("6c9140433d1272b9", 202.55e6)}
+MEASURED_TRAFFIC = {"n4096_f32_star_system": ("13495a60927cd084", 202.51e6)}
 
 
 def kernel_source_hash():
@@ -271,6 +271,7 @@ def tensor_core_variants(b, bc, data, x, ours_ms, pc_block, solve_ref, reps=200)
     for kind in ("tc_bf16x3", "tc_f16x3"):
         p = Plan.from_boundary(b, "laplace2d", kind)
         p.set_bc(bc, 0.5)
+        tuned = p.tune_shapes(reps=10)[0]
         xf = x.float()
         y = p.apply("system", xf).double().cpu().numpy()
         err = float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
@@ -284,7 +285,7 @@ def tensor_core_variants(b, bc, data, x, ours_ms, pc_block, solve_ref, reps=200)
         torch.cuda.synchronize()
         _, _, info = p.solve(bc, data, tol=1e-6, restart=100, max_iter=3000)
         p.device_status()
-        out[kind] = {"ms_per_apply": ms, "kernel_us": 1e3 * col_ms / max(1, col_n),
+        out[kind] = {"ms_per_apply": ms, "cell_batch_tuned": tuned, "kernel_us": 1e3 * col_ms / max(1, col_n),
                      "rel_l2_vs_f32x2": err, "vs_fp32_apply": ms / ours_ms,
                      "solve_refined": {"seconds": info["seconds"], "iters": info["iters"],
                                        "status": info["status"], "rel_residual": info["rel_residual"],
@@ -431,6 +432,7 @@ def accuracy_mode(dev, n=4096, order=3, R=5):
     data = np.where(bc == 0, u, q)
     p = Plan.from_panel_boundary(b, "f32", order, R)
     p.set_bc(bc, 0.5)
+    tuned = p.tune_shapes(reps=10)[0]
     x = torch.randn(b.nb, dtype=torch.float32, device=dev)
     p.set_kernel_timing(True)
     ms = _time_applies(p, "system", x, 100)
@@ -443,7 +445,7 @@ def accuracy_mode(dev, n=4096, order=3, R=5):
     xs = np.where(bc == 0, q_out, u_out)
     truth = np.where(bc == 0, q, u)
     res = {"panels": b.nb, "order": order, "near_radius": R, "grid_nodes": p.info()["grid_nodes"],
-           "system_apply_ms": ms, "node_convolution_kernel_us": 1e3 * col_ms / max(1, col_n),
+           "system_apply_ms": ms, "cell_batch_tuned": tuned, "node_convolution_kernel_us": 1e3 * col_ms / max(1, col_n),
            "plan_s": p.info()["plan_seconds"],
            "solve_1e-6": {"seconds": info["seconds"], "iters": info["iters"], "status": info["status"],
                           "rel_residual": info["rel_residual"], "refine_steps": info["refine_steps"]},
@@ -580,10 +582,11 @@ def secondary_configs(dev):
     p.close()
     b = I.ellipsoid_boundary(256)
     p = Plan.from_boundary(b, "laplace3d", "f32")
+    zl = p.tune_shapes(reps=5)[0]
     x = torch.randn(b.nb, dtype=torch.float32, device=dev)
     out["ellipsoid_n256_f32"] = {"nb": b.nb, "single_apply_ms": _time_applies(p, "single", x, 10),
                                  "double_apply_ms": _time_applies(p, "double", x, 5),
-                                 "plan_s": p.info()["plan_seconds"]}
+                                 "plan_s": p.info()["plan_seconds"], "zpass_lines_tuned": zl}
     p.close()
     # batched: 64 random stars on uneven grids, one CUDA graph per batched apply
     from paper_1809_00845_gb300.bem import Batch
@@ -638,10 +641,11 @@ def secondary_configs(dev):
     out["accuracy_mode_star_n4096"] = accuracy_mode(dev)
     b = I.cube_boundary(128)
     p = Plan.from_boundary(b, "kelvin3d", "f32")
+    zl = p.tune_shapes(reps=5)[0]
     x = torch.randn(b.nb * 3, dtype=torch.float32, device=dev)
     out["kelvin_cube_n128_f32"] = {"nb": b.nb, "U_apply_ms": _time_applies(p, "single", x, 10),
                                    "T_apply_ms": _time_applies(p, "double", x, 3),
-                                   "plan_s": p.info()["plan_seconds"]}
+                                   "plan_s": p.info()["plan_seconds"], "zpass_lines_tuned": zl}
     p.close()
     return out
 
@@ -704,6 +708,8 @@ def run_ours(args):
     plan = (Plan.from_panel_boundary(b, args.precision, 3, 5) if panels
             else Plan.from_boundary(b, "laplace2d", args.precision))
     plan.set_bc(bc, 0.5)
+    # the apply's runtime launch shape (cells per batch of the fused walks), measured by the library's tuner
+    tuned_shape, tuned_ms = plan.tune_shapes(reps=10)
     pinfo = plan.info()
     f32io = args.precision != "f64"
     tdt = torch.float32 if f32io else torch.float64
@@ -890,6 +896,8 @@ def run_ours(args):
                        "nb": b.nb, "precision": args.precision, "grid_nodes": pinfo["grid_nodes"],
                        "parallelism": f"replicas{world}", "grid_ctas": pinfo["grid_ctas"],
                        "threads_per_cta": pinfo["threads_per_cta"],
+                       "cell_batch": {"tuned": tuned_shape, "tuner_ms_per_apply": tuned_ms,
+                                      "what": "cells per load batch of the fused cell walks, bem_tune_shapes"},
                        "l2": "working set > L2: spectra 3 x (n+1)^2 x 4 B = 201 MB stream each apply (no flush)"},
             "e2e": {"value": e2e_val, "unit": "applies/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},

@@ -386,6 +386,20 @@ bem_status bem_batch_solve(bem_batch_t batch, const uint8_t* bc, const double* d
  *   including the block inversion; the plan keeps the winner, returned in
  *   *block (may be NULL).  BEM_ERR_NOT_CONVERGED when no candidate converges. */
 bem_status bem_tune_batch(bem_batch_t batch, int reps, int* streams);
+/* bem_tune_shapes: the launch shape of the plan's apply that is a runtime
+ *   choice - the cells per load batch of the 2D fused cell walks (2 or 4;
+ *   FP32 and tensor-core plans with n >= 256, and the node plan of an
+ *   accuracy-mode plan) or the lines per CTA of the 3D z pass (1, 2, 4, 8,
+ *   16, capped by shared memory and 512 threads).  Each candidate is timed
+ *   over `reps` applies (after one warm-up) of the system operator when
+ *   boundary conditions are set, else the single layer, on zero data with
+ *   CUDA events on `stream` (synchronised); the plan keeps the fastest,
+ *   returned in *chosen with its milliseconds per apply in *best_ms (both may
+ *   be NULL; the time is 0 when the choice came from the table).  Captured
+ *   solve and batch graphs of the plan are captured again on their next use.
+ *   Plans without such a choice return BEM_OK with *chosen = 0.  The
+ *   operator's result does not depend on the choice. */
+bem_status bem_tune_shapes(bem_plan_t plan, int reps, void* stream, int* chosen, double* best_ms);
 bem_status bem_tune_preconditioner(bem_plan_t plan, const uint8_t* bc, const double* data, double c, double tol,
                                    int max_iter, int restart, int* block);
 

@@ -37,7 +37,7 @@ EXPORTED = ["bem_plan", "bem_plan_panels", "bem_set_bc", "bem_set_preconditioner
             "bem_get_info", "bem_enable_refinement", "bem_set_kernel_timing", "bem_kernel_time", "bem_launches_per_apply", "bem_device_status", "bem_set_test_flags", "bem_destroy",
             "bem_status_string", "bem_last_error", "bem_batch_create", "bem_batch_buffers", "bem_batch_offset",
             "bem_batch_apply", "bem_batch_set_grouping", "bem_batch_launches", "bem_batch_destroy", "bem_batch_solve", "bem_tune_batch",
-            "bem_tune_preconditioner", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
+            "bem_tune_preconditioner", "bem_tune_shapes", "bem_net_create", "bem_net_destroy", "bem_net_num_params",
             "bem_net_get_params", "bem_net_set_params", "bem_net_forward", "bem_net_gradient", "bem_net_train_step",
             "bem_measure_peak", "bem_dtn_estimate", "bem_guess_features", "bem_guess_finish", "bem_fourier_features"]
 
@@ -110,6 +110,8 @@ def load_library(path: str = LIB_PATH):
     lib.bem_batch_solve.argtypes = [P, P, P, D, D, I, I, P, P, P, ctypes.POINTER(SolveInfo), P]
     lib.bem_tune_batch.argtypes = [P, I, ctypes.POINTER(I)]
     lib.bem_tune_preconditioner.argtypes = [P, P, P, D, D, I, I, ctypes.POINTER(I)]
+    lib.bem_tune_shapes.argtypes = [P, I, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.bem_tune_shapes.restype = I
     for name in ("bem_batch_create", "bem_batch_buffers", "bem_batch_offset", "bem_batch_apply", "bem_batch_destroy",
                  "bem_batch_set_grouping",
                  "bem_batch_solve", "bem_tune_batch", "bem_tune_preconditioner"):
@@ -381,6 +383,16 @@ class Plan:
         _check(load_library().bem_tune_preconditioner(self._h, _ptr(bc), _ptr(data), float(c), float(tol),
                                                        int(max_iter), int(restart), ctypes.byref(out)))
         return out.value
+
+    def tune_shapes(self, reps=20, stream=None):
+        """Measured runtime launch shape of the apply (bem_tune_shapes): the
+        cells per batch of the 2D fused walks or the lines per CTA of the 3D z
+        pass; returns (chosen, ms per apply), (0, 0.0) when the plan has no
+        such choice."""
+        ch, ms = ctypes.c_int(), ctypes.c_double()
+        _check(load_library().bem_tune_shapes(self._h, int(reps), _stream_ptr(stream), ctypes.byref(ch),
+                                              ctypes.byref(ms)))
+        return ch.value, ms.value
 
     def info(self):
         pi = PlanInfo()

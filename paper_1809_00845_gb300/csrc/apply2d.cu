@@ -606,9 +606,9 @@ template <int TCK>
 static void launch_tc(const bem_plan_s* p, int nf, const Col2Dv2Params<float>& cp, cudaStream_t st) {
   const int TT = p->threads;
   switch (TT) {
-    case 512: Col2DTcKernels<512, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-    case 256: Col2DTcKernels<256, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-    default: Col2DTcKernels<128, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+    case 512: Col2DTcKernels<512, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+    case 256: Col2DTcKernels<256, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+    default: Col2DTcKernels<128, TCK>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
   }
 }
 
@@ -642,24 +642,24 @@ static void launch_col2d(const bem_plan_s* p, int nf, const Col2Dv2Params<T>& cp
   const int TT = p->threads;
   if constexpr (std::is_same<T, f32x2>::value) {
     switch (TT) {
-      case 512: Col2DKernels<f32x2, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      case 256: Col2DKernels<f32x2, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      case 128: Col2DKernels<f32x2, 128>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      case 64: Col2DKernels<f32x2, 64>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      default: Col2DKernels<f32x2, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 512: Col2DKernels<f32x2, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      case 256: Col2DKernels<f32x2, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      case 128: Col2DKernels<f32x2, 128>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      case 64: Col2DKernels<f32x2, 64>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      default: Col2DKernels<f32x2, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
     }
   } else if constexpr (std::is_same<T, float>::value) {
     if (p->tc == kTcBf16) return launch_tc<kTcBf16>(p, nf, cp, st);
     if (p->tc == kTcF16) return launch_tc<kTcF16>(p, nf, cp, st);
     switch (TT) {
-      case 512: Col2DKernels<float, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      case 256: Col2DKernels<float, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      case 128: Col2DKernels<float, 128>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      case 64: Col2DKernels<float, 64>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
-      default: Col2DKernels<float, 32>::launch(nf, p->grid, TT, p->smem_bytes, st, cp); break;
+      case 512: Col2DKernels<float, 512>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      case 256: Col2DKernels<float, 256>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      case 128: Col2DKernels<float, 128>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      case 64: Col2DKernels<float, 64>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
+      default: Col2DKernels<float, 32>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch); break;
     }
   } else {
-    Col2DKernels<T, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp);
+    Col2DKernels<T, 0>::launch(nf, p->grid, TT, p->smem_bytes, st, cp, p->cell_batch);
   }
 }
 
@@ -703,7 +703,7 @@ static bem_status setup_v2_t(bem_plan_s* p) {
     tinfo[r % TT] |= 1 << (r / TT);  // row r = t + m*TT, m < 8
   }
   // interleaved positions: i-th cell of thread t at i*TT + t
-  const int64_t Q = (nb + TT * CB - 1) / (TT * CB) * CB;  // a multiple of the cell batch
+  const int64_t Q = (nb + TT * kCellPad - 1) / (TT * kCellPad) * kCellPad;  // whole batches of either size
   p->v2_npos = Q * TT;
   p->h_pos.assign(nb, 0);
   std::vector<int32_t> perm_il(p->v2_npos, -1);
@@ -1219,22 +1219,22 @@ static void edge_launch(const bem_plan_s* p, const Col2Dv2Params<T>& cp, cudaStr
   const size_t sm = p->edge_smem;
   if constexpr (std::is_same<T, float>::value) {
     switch (TT) {
-      case 512: Col2DEdgeKernels<float, 512>::launch(G, TT, sm, st, cp); break;
-      case 256: Col2DEdgeKernels<float, 256>::launch(G, TT, sm, st, cp); break;
-      case 128: Col2DEdgeKernels<float, 128>::launch(G, TT, sm, st, cp); break;
-      case 64: Col2DEdgeKernels<float, 64>::launch(G, TT, sm, st, cp); break;
-      default: Col2DEdgeKernels<float, 32>::launch(G, TT, sm, st, cp); break;
+      case 512: Col2DEdgeKernels<float, 512>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      case 256: Col2DEdgeKernels<float, 256>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      case 128: Col2DEdgeKernels<float, 128>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      case 64: Col2DEdgeKernels<float, 64>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      default: Col2DEdgeKernels<float, 32>::launch(G, TT, sm, st, cp, p->cell_batch); break;
     }
   } else if constexpr (std::is_same<T, f32x2>::value) {
     switch (TT) {
-      case 512: Col2DEdgeKernels<f32x2, 512>::launch(G, TT, sm, st, cp); break;
-      case 256: Col2DEdgeKernels<f32x2, 256>::launch(G, TT, sm, st, cp); break;
-      case 128: Col2DEdgeKernels<f32x2, 128>::launch(G, TT, sm, st, cp); break;
-      case 64: Col2DEdgeKernels<f32x2, 64>::launch(G, TT, sm, st, cp); break;
-      default: Col2DEdgeKernels<f32x2, 0>::launch(G, TT, sm, st, cp); break;
+      case 512: Col2DEdgeKernels<f32x2, 512>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      case 256: Col2DEdgeKernels<f32x2, 256>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      case 128: Col2DEdgeKernels<f32x2, 128>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      case 64: Col2DEdgeKernels<f32x2, 64>::launch(G, TT, sm, st, cp, p->cell_batch); break;
+      default: Col2DEdgeKernels<f32x2, 0>::launch(G, TT, sm, st, cp, p->cell_batch); break;
     }
   } else {
-    Col2DEdgeKernels<T, 0>::launch(G, TT, sm, st, cp);
+    Col2DEdgeKernels<T, 0>::launch(G, TT, sm, st, cp, p->cell_batch);
   }
 }
 

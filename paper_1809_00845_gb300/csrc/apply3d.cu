@@ -138,7 +138,7 @@ static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in
   Passes3D<T>{p}.on([&](auto k) {
     using KK = decltype(k);
     KK::yfwd(op.nf, nb, p->d_lptr, p->d_x3, val, p->d_tw2, B, p->d_ptab3, st);
-    KK::zpass(op.nf, op.no, op.lpc, op.d_coup, p->d_specs3, B, p->d_ptab3, st);
+    KK::zpass(op.nf, op.no, zpass_lpc(p, op.nf), op.d_coup, p->d_specs3, B, p->d_ptab3, st);
     KK::yinv(op.no, B, X, p->d_ptab3, st);
     return 0;
   });
@@ -165,8 +165,9 @@ static bem_status configure3d_t(bem_plan_s* p) {
   return BEM_OK;
 }
 
-// lines per CTA of the z pass: four, fewer where their buffers would pass
-// ~200 KB of shared memory or the CTA 512 threads
+// lines per CTA of the z pass: four (or the plan's tuned count,
+// bem_tune_shapes), fewer where their buffers would pass ~200 KB of shared
+// memory or the CTA 512 threads
 int zpass_lpc(const bem_plan_s* p, int nf) {
   const size_t cb = 2 * prec_bytes(p);
   const int64_t N = p->N;
@@ -176,7 +177,7 @@ int zpass_lpc(const bem_plan_s* p, int nf) {
   // registers a thread, so small CTAs let several reside per SM and one CTA's
   // loads overlap another's transforms (measured: 16 lines 0.629 ms, 8 lines
   // 0.601 ms, 4 lines 0.588 ms per 256^3 ellipsoid single-layer apply)
-  int lpc = 4;
+  int lpc = p->zpass_lines > 0 ? p->zpass_lines : 4;
   while (lpc > 1 && (size_t)lpc * per > budget) lpc >>= 1;
   while (lpc > 1 && (lpc * (N / 16)) > 512) lpc >>= 1;
   return lpc;

@@ -180,6 +180,8 @@ struct bem_plan_s {
   int32_t* d_chunk = nullptr;   // threads + 1
   void* d_val = nullptr;        // nb density pairs (scratch)
   void* d_twc = nullptr;        // grid * npos cached sparse twiddles (scratch)
+  int cell_batch = 2;           // cells per load batch of the fused 2D cell walks (2 or 4; bem_tune_shapes)
+  int zpass_lines = 0;          // 3D z-pass lines per CTA (0: the default rule; bem_tune_shapes)
   void* d_fstab = nullptr;      // twiddle tables of the four-step kernel
   int tc = 0;                   // tensor-core DFT stages: 0 none, 1 BF16 hi + lo, 2 FP16 hi + lo
   void* d_tcmat = nullptr;      // their B matrices (hi, lo; 8 KB)

@@ -261,13 +261,13 @@ __device__ __forceinline__ void column_twiddles(const ColDims<TTC>& g, int kx, c
   }
 }
 
-// One batch of CB cells of a walk: cell words, densities (EDGE: and the third
+// One batch of NB cells of a walk: cell words, densities (EDGE: and the third
 // density) and the cached twiddles of the previous column.
-template <typename T>
+template <typename T, int NB>
 struct CellBatch {
-  uint32_t m[CB];
-  cplx<T> v[CB], w[CB];
-  T c[CB];
+  uint32_t m[NB];
+  cplx<T> v[NB], w[NB];
+  T c[NB];
 };
 
 // One walk over the thread's cells that serves two columns (kernels with the
@@ -279,11 +279,11 @@ struct CellBatch {
 // loaded once for both; the gather's twiddle is column kxp's cached one
 // (conjugated), which the sparse pass then replaces by column kx's.  Sums and
 // accumulators see the same terms in the same order as the separate passes.
-// The next batch's loads are issued before the current batch is used (two
-// alternating register sets spill in the 512-thread kernels); the cell arrays
-// hold a multiple of CB cells per thread, so every batch load stays inside
-// them.
-template <typename T, int NF, int TTC, bool EDGE, bool SPARSE, bool GATHER>
+// Batches of NB cells (2 or 4, a launch shape the tuner picks); the next
+// batch's loads are issued before the current batch is used (two alternating
+// register sets spill in the 512-thread kernels); the cell arrays hold a
+// multiple of 4 cells per thread, so every batch load stays inside them.
+template <typename T, int NF, int TTC, bool EDGE, bool SPARSE, bool GATHER, int NB>
 __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kxp, int cnt,
                                            cplx<T>* out0, cplx<T>* outF, cplx<T>* carry, const cplx<T>* rows,
                                            T* sacc, T* gacc, int qs, const Twiddles2L<T>& tw, const cplx<T>* stw,
@@ -291,10 +291,10 @@ __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColD
   const int Nm = g.N - 1;
   const int t = threadIdx.x, TT = g.TT;
   cplx<T> s0 = {T(0), T(0)}, s1 = {T(0), T(0)}, s2 = {T(0), T(0)};
-  auto fetch = [&](CellBatch<T>& B, int base) {
+  auto fetch = [&](CellBatch<T, NB>& B, int base) {
     const int pos = base * TT + t;
 #pragma unroll
-    for (int i = 0; i < CB; ++i) {
+    for (int i = 0; i < NB; ++i) {
       B.m[i] = __ldg(p.meta + pos + i * TT);
       if constexpr (SPARSE) {
         B.v[i] = p.val[pos + i * TT];
@@ -305,37 +305,37 @@ __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColD
       }
     }
   };
-  auto process = [&](CellBatch<T>& B, int i0) {
+  auto process = [&](CellBatch<T, NB>& B, int i0) {
     if constexpr (GATHER) {
-      cplx<T> Y[CB], wp[CB];
+      cplx<T> Y[NB], wp[NB];
 #pragma unroll
-      for (int i = 0; i < CB; ++i) {
+      for (int i = 0; i < NB; ++i) {
         Y[i] = rows[meta_slot(B.m[i])];
         if (twc) wp[i] = {B.w[i].x, -B.w[i].y};
         else wp[i] = tw.template get<+1>((kxp * meta_x(B.m[i])) & Nm);
       }
-      if (i0 + CB <= qs) {
+      if (i0 + NB <= qs) {
         T* acc = sacc + (size_t)i0 * TT + t;
 #pragma unroll
-        for (int i = 0; i < CB; ++i)
+        for (int i = 0; i < NB; ++i)
           if (i0 + i < cnt) acc[i * TT] += Y[i].x * wp[i].x - Y[i].y * wp[i].y;
       } else {
 #pragma unroll
-        for (int i = 0; i < CB; ++i)
+        for (int i = 0; i < NB; ++i)
           if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += Y[i].x * wp[i].x - Y[i].y * wp[i].y;
       }
     }
     if constexpr (SPARSE) {
-      cplx<T> w[CB];
+      cplx<T> w[NB];
 #pragma unroll
-      for (int i = 0; i < CB; ++i) w[i] = cmul(stw[64 + ((B.m[i] >> 6) & 63)], stw[B.m[i] & 63]);
+      for (int i = 0; i < NB; ++i) w[i] = cmul(stw[64 + ((B.m[i] >> 6) & 63)], stw[B.m[i] & 63]);
       if (twc) {
 #pragma unroll
-        for (int i = 0; i < CB; ++i)
+        for (int i = 0; i < NB; ++i)
           if (i0 + i < cnt) twc[(i0 + i) * TT + t] = w[i];
       }
 #pragma unroll
-      for (int i = 0; i < CB; ++i) {
+      for (int i = 0; i < NB; ++i) {
         if (i0 + i >= cnt) continue;
         const uint32_t mt = B.m[i];
         if constexpr (EDGE) {
@@ -378,11 +378,11 @@ __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColD
       }
     }
   };
-  CellBatch<T> A, B;
+  CellBatch<T, NB> A, B;
   if (cnt > 0) fetch(B, 0);
-  for (int i0 = 0; i0 < cnt; i0 += CB) {
+  for (int i0 = 0; i0 < cnt; i0 += NB) {
     A = B;
-    if (i0 + CB < cnt) fetch(B, i0 + CB);
+    if (i0 + NB < cnt) fetch(B, i0 + NB);
     process(A, i0);
   }
 }
@@ -620,7 +620,7 @@ struct ColSmem {
 // transform buffer (sA + n; rows y < n of the previous column's output stay
 // in sA[0, n) until that gather), and the column ends with its scaled output
 // rows in sA: the caller gathers the CTA's last column after its loop.
-template <typename T, int NF, bool ACCREG, int TTC, int TCK, bool EDGE = false, bool FUSED = false>
+template <typename T, int NF, bool ACCREG, int TTC, int TCK, bool EDGE = false, bool FUSED = false, int NB = CB>
 __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx,
                                              FourStep<T, TCK>& fs, const Twiddles2L<T>& tw, const ColSmem<T>& sm,
                                              T* sacc, T* gacc, int qs, cplx<T>* twc,
@@ -637,10 +637,10 @@ __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const Co
       cplx<T> fx = {T(0), T(0)};
       if constexpr (EDGE) fx = diff_factor(tw, kx, half);
       if (kxp >= 0)
-        walk_cells<T, NF, TTC, EDGE, true, true>(p, g, kxp, cnt, r0, sF, sm.carry, sA, sacc, gacc, qs, tw, sm.stw,
+        walk_cells<T, NF, TTC, EDGE, true, true, NB>(p, g, kxp, cnt, r0, sF, sm.carry, sA, sacc, gacc, qs, tw, sm.stw,
                                                  twc, fx);
       else
-        walk_cells<T, NF, TTC, EDGE, true, false>(p, g, kxp, cnt, r0, sF, sm.carry, sA, sacc, gacc, qs, tw, sm.stw,
+        walk_cells<T, NF, TTC, EDGE, true, false, NB>(p, g, kxp, cnt, r0, sF, sm.carry, sA, sacc, gacc, qs, tw, sm.stw,
                                                   twc, fx);
     } else if constexpr (EDGE) {
       sparse_rows<T, 2, -1, TTC, true>(p, g, kx, cnt, sA, sF, sm.carry, tw, twc, diff_factor(tw, kx, half));
@@ -736,7 +736,7 @@ struct ColBounds {
 
 // TCK > 0: the radix-16 stages on the tensor cores (tc_dft.cuh; T = float,
 // TTC a multiple of 128); shared memory then starts with their header.
-template <typename T, int NF, bool ACCREG, int TTC, int TCK = 0, bool EDGE = false>
+template <typename T, int NF, bool ACCREG, int TTC, int TCK = 0, bool EDGE = false, int NB = CB>
 __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::blocks)
     k_col2d_v2(const Col2Dv2Params<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     } else {
       __syncthreads();
     }
-    col2d_column<T, NF, ACCREG, TTC, TCK, EDGE, ACCREG>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc, half, kxp);
+    col2d_column<T, NF, ACCREG, TTC, TCK, EDGE, ACCREG, NB>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc, half, kxp);
     // the next column's tables: this column's walk read the current ones
     // several barriers ago, the next walk follows the loop's barrier
     if constexpr (ACCREG) column_twiddles(g, kx + (int)gridDim.x, tw, stw);
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   if constexpr (ACCREG) {
     if (kxp >= 0) {
       __syncthreads();
-      walk_cells<T, NF, TTC, EDGE, false, true>(p, g, kxp, cnt, nullptr, nullptr, nullptr, sA, sacc, gacc, qs, tw,
+      walk_cells<T, NF, TTC, EDGE, false, true, NB>(p, g, kxp, cnt, nullptr, nullptr, nullptr, sA, sacc, gacc, qs, tw,
                                                 sm.stw, twc, cplx<T>{T(0), T(0)});
     }
   }
@@ -955,24 +955,30 @@ void Col2DPassKernels<TTC>::launch(int nf, int grid, int threads, size_t smem, c
   else k_p3_cols<3, TTC><<<grid, threads, smem, st>>>(cp);
 }
 
+// resident CTAs of one kernel, folded into the running minimum
+template <typename K>
+static cudaError_t min_residency(K kern, int threads, size_t smem, int* bmin) {
+  cudaError_t e = allow_optin_smem(kern);
+  if (e != cudaSuccess) return e;
+  int b = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem)) != cudaSuccess) return e;
+  *bmin = std::min(*bmin, b);
+  return cudaSuccess;
+}
+
 template <typename T, int TTC>
 cudaError_t Col2DKernels<T, TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
   constexpr bool R = std::is_same<T, float>::value;
-  int b[3] = {0, 0, 0};
+  int b = 1 << 30;
   cudaError_t e;
-  if ((e = allow_optin_smem(k_col2d_v2<T, 1, false, TTC>)) != cudaSuccess) return e;
-  if ((e = allow_optin_smem(k_col2d_v2<T, 2, R, TTC>)) != cudaSuccess) return e;
-  if ((e = allow_optin_smem(k_col2d_v2<T, 3, R, TTC>)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_v2<T, 1, false, TTC>, threads, smem)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_v2<T, 2, R, TTC>, threads, smem)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_v2<T, 3, R, TTC>, threads, smem)) !=
-      cudaSuccess)
-    return e;
-  *blocks_per_sm = std::min(b[0], std::min(b[1], b[2]));
+  if ((e = min_residency(k_col2d_v2<T, 1, false, TTC>, threads, smem, &b)) != cudaSuccess) return e;
+  if ((e = min_residency(k_col2d_v2<T, 2, R, TTC>, threads, smem, &b)) != cudaSuccess) return e;
+  if ((e = min_residency(k_col2d_v2<T, 3, R, TTC>, threads, smem, &b)) != cudaSuccess) return e;
+  if constexpr (R) {
+    if ((e = min_residency(k_col2d_v2<T, 2, true, TTC, 0, false, 4>, threads, smem, &b)) != cudaSuccess) return e;
+    if ((e = min_residency(k_col2d_v2<T, 3, true, TTC, 0, false, 4>, threads, smem, &b)) != cudaSuccess) return e;
+  }
+  *blocks_per_sm = b;
   return cudaSuccess;
 }
 
@@ -1006,55 +1012,69 @@ cudaError_t Col2DGroupKernels<TTC>::configure(size_t smem, int threads, int* blo
 
 template <typename T, int TTC>
 void Col2DKernels<T, TTC>::launch(int nf, int grid, int threads, size_t smem, cudaStream_t st,
-                                  const Col2Dv2Params<T>& cp) {
+                                  const Col2Dv2Params<T>& cp, int nb) {
   constexpr bool R = std::is_same<T, float>::value;
-  if (nf == 1) k_col2d_v2<T, 1, false, TTC><<<grid, threads, smem, st>>>(cp);
-  else if (nf == 2) k_col2d_v2<T, 2, R, TTC><<<grid, threads, smem, st>>>(cp);
-  else k_col2d_v2<T, 3, R, TTC><<<grid, threads, smem, st>>>(cp);
+  if (nf == 1) {
+    k_col2d_v2<T, 1, false, TTC><<<grid, threads, smem, st>>>(cp);
+  } else if constexpr (R) {
+    // the fused walks take the tuned cell batch
+    if (nf == 2 && nb == 4) k_col2d_v2<T, 2, true, TTC, 0, false, 4><<<grid, threads, smem, st>>>(cp);
+    else if (nf == 2) k_col2d_v2<T, 2, true, TTC><<<grid, threads, smem, st>>>(cp);
+    else if (nb == 4) k_col2d_v2<T, 3, true, TTC, 0, false, 4><<<grid, threads, smem, st>>>(cp);
+    else k_col2d_v2<T, 3, true, TTC><<<grid, threads, smem, st>>>(cp);
+  } else {
+    if (nf == 2) k_col2d_v2<T, 2, false, TTC><<<grid, threads, smem, st>>>(cp);
+    else k_col2d_v2<T, 3, false, TTC><<<grid, threads, smem, st>>>(cp);
+  }
 }
 
 template <typename T, int TTC>
 cudaError_t Col2DEdgeKernels<T, TTC>::configure(size_t smem, int threads, int* blocks_per_sm) {
   constexpr bool R = std::is_same<T, float>::value;
+  int b = 1 << 30;
   cudaError_t e;
-  if ((e = allow_optin_smem(k_col2d_v2<T, 2, R, TTC, 0, true>)) != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_col2d_v2<T, 2, R, TTC, 0, true>, threads,
-                                                       smem);
+  if ((e = min_residency(k_col2d_v2<T, 2, R, TTC, 0, true>, threads, smem, &b)) != cudaSuccess) return e;
+  if constexpr (R) {
+    if ((e = min_residency(k_col2d_v2<T, 2, true, TTC, 0, true, 4>, threads, smem, &b)) != cudaSuccess) return e;
+  }
+  *blocks_per_sm = b;
+  return cudaSuccess;
 }
 
 template <typename T, int TTC>
 void Col2DEdgeKernels<T, TTC>::launch(int grid, int threads, size_t smem, cudaStream_t st,
-                                      const Col2Dv2Params<T>& cp) {
+                                      const Col2Dv2Params<T>& cp, int nb) {
   constexpr bool R = std::is_same<T, float>::value;
+  if constexpr (R) {
+    if (nb == 4) {
+      k_col2d_v2<T, 2, true, TTC, 0, true, 4><<<grid, threads, smem, st>>>(cp);
+      return;
+    }
+  }
   k_col2d_v2<T, 2, R, TTC, 0, true><<<grid, threads, smem, st>>>(cp);
 }
 
 template <int TTC, int TCK>
 cudaError_t Col2DTcKernels<TTC, TCK>::configure(size_t smem, int threads, int* blocks_per_sm) {
-  int b[3] = {0, 0, 0};
+  int b = 1 << 30;
   cudaError_t e;
-  if ((e = allow_optin_smem(k_col2d_v2<float, 1, false, TTC, TCK>)) != cudaSuccess) return e;
-  if ((e = allow_optin_smem(k_col2d_v2<float, 2, true, TTC, TCK>)) != cudaSuccess) return e;
-  if ((e = allow_optin_smem(k_col2d_v2<float, 3, true, TTC, TCK>)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_col2d_v2<float, 1, false, TTC, TCK>, threads,
-                                                         smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_col2d_v2<float, 2, true, TTC, TCK>, threads,
-                                                         smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col2d_v2<float, 3, true, TTC, TCK>, threads,
-                                                         smem)) != cudaSuccess)
-    return e;
+  if ((e = min_residency(k_col2d_v2<float, 1, false, TTC, TCK>, threads, smem, &b)) != cudaSuccess) return e;
+  if ((e = min_residency(k_col2d_v2<float, 2, true, TTC, TCK>, threads, smem, &b)) != cudaSuccess) return e;
+  if ((e = min_residency(k_col2d_v2<float, 3, true, TTC, TCK>, threads, smem, &b)) != cudaSuccess) return e;
+  if ((e = min_residency(k_col2d_v2<float, 2, true, TTC, TCK, false, 4>, threads, smem, &b)) != cudaSuccess) return e;
+  if ((e = min_residency(k_col2d_v2<float, 3, true, TTC, TCK, false, 4>, threads, smem, &b)) != cudaSuccess) return e;
   // each resident CTA holds TTC / 128 * kTcGroupCols tensor-memory columns (512 per SM)
-  *blocks_per_sm = std::min(std::min(b[0], std::min(b[1], b[2])), 512 / (TTC / 128 * kTcGroupCols));
+  *blocks_per_sm = std::min(b, 512 / (TTC / 128 * kTcGroupCols));
   return cudaSuccess;
 }
 
 template <int TTC, int TCK>
 void Col2DTcKernels<TTC, TCK>::launch(int nf, int grid, int threads, size_t smem, cudaStream_t st,
-                                      const Col2Dv2Params<float>& cp) {
+                                      const Col2Dv2Params<float>& cp, int nb) {
   if (nf == 1) k_col2d_v2<float, 1, false, TTC, TCK><<<grid, threads, smem, st>>>(cp);
+  else if (nf == 2 && nb == 4) k_col2d_v2<float, 2, true, TTC, TCK, false, 4><<<grid, threads, smem, st>>>(cp);
   else if (nf == 2) k_col2d_v2<float, 2, true, TTC, TCK><<<grid, threads, smem, st>>>(cp);
+  else if (nb == 4) k_col2d_v2<float, 3, true, TTC, TCK, false, 4><<<grid, threads, smem, st>>>(cp);
   else k_col2d_v2<float, 3, true, TTC, TCK><<<grid, threads, smem, st>>>(cp);
 }
 

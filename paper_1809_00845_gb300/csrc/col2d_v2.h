@@ -56,6 +56,10 @@ struct Col2Dv2Params {
 #define COL2D_CELL_BATCH 2
 #endif
 constexpr int CB = COL2D_CELL_BATCH;
+// the interleaved cell arrays hold a multiple of kCellPad cells per thread: a
+// whole number of batches for CB and for the other batch size of the fused
+// walks (2 or 4 cells, chosen per plan by bem_tune_shapes)
+constexpr int kCellPad = 4;
 
 // per-column sparse twiddles of the fused cell walk: e^{-2 pi i kx x / N} =
 // A[x >> 6] * B[x & 63] (x < 4096), B in entries 0..63 and A in 64..127
@@ -80,7 +84,8 @@ __host__ __device__ inline int sspec_entries(int n) { return ((n + 1 + (n + 1) /
 template <typename T, int TTC>
 struct Col2DKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
-  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
+  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp,
+                     int nb);
 };
 
 // One persistent launch over the columns of several FP32 plans of the same
@@ -102,7 +107,7 @@ struct Col2DGroupKernels {
 template <typename T, int TTC>
 struct Col2DEdgeKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
-  static void launch(int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp);
+  static void launch(int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<T>& cp, int nb);
 };
 
 // Three-pass form, FP32, TTC = 32 ... 512: the column pass alone (forward
@@ -120,7 +125,8 @@ struct Col2DPassKernels {
 template <int TTC, int TCK>
 struct Col2DTcKernels {
   static cudaError_t configure(size_t smem, int threads, int* blocks_per_sm);
-  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<float>& cp);
+  static void launch(int nf, int grid, int threads, size_t smem, cudaStream_t st, const Col2Dv2Params<float>& cp,
+                     int nb);
 };
 
 }  // namespace bemfft

@@ -1,4 +1,7 @@
 // Measured choices the shape of a problem does not fix by itself:
+//   - the launch shapes of the apply that are runtime choices: the cells per
+//     load batch of the 2D fused cell walks (2 or 4; both kernels are built)
+//     and the lines per CTA of the 3D z pass;
 //   - the number of forked capture streams of a batch graph (how many of the
 //     geometries' applies run side by side);
 //   - the block size of the block-Jacobi preconditioner (fewer GMRES
@@ -59,11 +62,92 @@ static bem_status batch_set_streams(bem_batch_s* b, int S) {
   return batch_capture(b);
 }
 
+// the plan whose kernels take the shape: the inner node plan of an
+// accuracy-mode plan, else the plan itself
+static bem_plan_s* shape_owner(bem_plan_s* p) { return p->pf ? p->pf->inner : p; }
+
+// candidate values of the plan's runtime launch shape (empty: none)
+static std::vector<int> shape_candidates(const bem_plan_s* q) {
+  if (q->dim == 2 && q->v2 && q->prec == BEM_F32) return {2, 4};  // FP32 and tensor-core fused walks
+  if (q->dim == 3) return {1, 2, 4, 8, 16};
+  return {};
+}
+
+static void set_shape(bem_plan_s* p, int v) {
+  bem_plan_s* q = shape_owner(p);
+  if (q->dim == 2) q->cell_batch = v;
+  else q->zpass_lines = v;
+  // captured graphs hold the old launches
+  ++q->op_version;
+  ++p->op_version;
+  ++p->pc_version;
+}
+
 }  // namespace bemfft
 
 using namespace bemfft;
 
 extern "C" {
+
+bem_status bem_tune_shapes(bem_plan_t p, int reps, void* stream, int* chosen, double* best_ms_out) {
+  if (!p || reps < 1) {
+    set_error("bem_tune_shapes: need a plan and reps >= 1");
+    return BEM_ERR_ARG;
+  }
+  if (bem_status dc = check_device(p, "bem_tune_shapes"); dc != BEM_OK) return dc;
+  const std::vector<int> cand = shape_candidates(shape_owner(p));
+  if (chosen) *chosen = 0;
+  if (best_ms_out) *best_ms_out = 0.0;
+  if (cand.empty()) return BEM_OK;
+  const bem_layer layer = p->have_bc ? BEM_SYSTEM : BEM_SINGLE;
+  const std::string key = "shape:" + plan_shape(p) + ":" + std::to_string(p->pf != nullptr) + ":" +
+                          std::to_string((int)layer);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int best = 0;
+  float best_ms = 0.0f;
+  if (!tune_lookup(key, &best)) {
+    // device vectors and events for the timing, released on every path
+    struct Timing {
+      void* in = nullptr;
+      void* out = nullptr;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      ~Timing() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(in);
+        cudaFree(out);
+      }
+    } tm;
+    const size_t bytes = (size_t)p->nb * p->ncomp * prec_bytes(p);
+    BEM_CUDA_TRY(cudaMalloc(&tm.in, bytes));
+    BEM_CUDA_TRY(cudaMalloc(&tm.out, bytes));
+    BEM_CUDA_TRY(cudaMemsetAsync(tm.in, 0, bytes, st));
+    BEM_CUDA_TRY(cudaEventCreate(&tm.e0));
+    BEM_CUDA_TRY(cudaEventCreate(&tm.e1));
+    for (int v : cand) {
+      set_shape(p, v);
+      bem_status rc = apply_operator(p, layer, tm.in, tm.out, st);  // warm-up
+      if (rc != BEM_OK) return rc;
+      BEM_CUDA_TRY(cudaEventRecord(tm.e0, st));
+      for (int i = 0; i < reps; ++i)
+        if ((rc = apply_operator(p, layer, tm.in, tm.out, st)) != BEM_OK) return rc;
+      BEM_CUDA_TRY(cudaEventRecord(tm.e1, st));
+      BEM_CUDA_TRY(cudaEventSynchronize(tm.e1));
+      float ms = 0.0f;
+      BEM_CUDA_TRY(cudaEventElapsedTime(&ms, tm.e0, tm.e1));
+      ms /= (float)reps;
+      if (best == 0 || ms < best_ms) {
+        best = v;
+        best_ms = ms;
+      }
+    }
+    tune_store(key, best);
+  }
+  set_shape(p, best);
+  if (chosen) *chosen = best;
+  if (best_ms_out) *best_ms_out = best_ms;
+  return BEM_OK;
+}
 
 bem_status bem_tune_batch(bem_batch_t b, int reps, int* streams_out) {
   if (!b || reps < 1) {
