@@ -103,6 +103,9 @@ typedef struct {
   double seconds;            /* wall time of the solve (host clock) */
   int applies;               /* all operator applies, right-hand side and final check included */
   int refine_steps;          /* outer steps of mixed-precision refinement (0 without it) */
+  double rel_residual_fp64;  /* rel_residual when its operator is accurate to FP64 level (an FP64 plan, or the
+                                double-float / FP64 companion of a refined solve), else NaN: a plain FP32 or
+                                tensor-core solve has no FP64-accurate residual to report */
 } bem_solve_info;
 
 typedef struct {

@@ -51,7 +51,7 @@ class BemError(RuntimeError):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("rel_residual_est", ctypes.c_double), ("seconds", ctypes.c_double), ("applies", ctypes.c_int),
-                ("refine_steps", ctypes.c_int)]
+                ("refine_steps", ctypes.c_int), ("rel_residual_fp64", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

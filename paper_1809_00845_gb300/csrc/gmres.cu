@@ -147,6 +147,10 @@ static inline double rel_norm(double r, double b) {
   return b > 0 ? r / b : 0.0;
 }
 
+// whether residuals formed with plan r are accurate to FP64 level (FP64 or
+// double-float arithmetic)
+static inline bool fp64_residual(const bem_plan_s* r) { return r->prec == BEM_F64 || r->prec == BEM_F32X2; }
+
 static inline double inner_tolerance(double tol, double rel) {
   return std::min(std::max(1e-5, 0.3 * tol / std::max(rel, 1e-300)), 0.1);
 }
@@ -492,6 +496,7 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     info->iters = tot.iters;
     info->restarts = tot.restarts;
     info->rel_residual = rel;
+    info->rel_residual_fp64 = fp64_residual(R) ? rel : NAN;
     info->rel_residual_est = rel_est;
     info->applies = applies;
     info->refine_steps = refine_steps;
@@ -1124,6 +1129,7 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
       info[s].iters = cnt.iters;
       info[s].restarts = cnt.restarts;
       info[s].rel_residual = rel[s];
+      info[s].rel_residual_fp64 = fp64_residual(refine ? bt->plans[s]->companion : bt->plans[s]) ? rel[s] : NAN;
       info[s].rel_residual_est = rel[s];
       info[s].seconds = secs;
       info[s].applies = cnt.applies;

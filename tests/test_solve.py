@@ -52,6 +52,11 @@ def test_star_mixed_bc_residual(torch_cuda, oracle_mod, prec, tol, bound):
     rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, u * (bc == 0), q * (bc == 1))
     r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
     assert np.linalg.norm(r) / np.linalg.norm(rhs) <= bound
+    # the FP64-level residual is reported only where the residual operator has that accuracy
+    if prec == "f32":
+        assert np.isnan(info["rel_residual_fp64"])
+    else:
+        assert info["rel_residual_fp64"] == info["rel_residual"]
     # known entries are passed through
     assert np.array_equal(u_out[bc == 0], u[bc == 0]) and np.array_equal(q_out[bc == 1], q[bc == 1])
 
@@ -103,6 +108,7 @@ def test_fp32_refinement_reaches_fp64_tolerance(torch_cuda, oracle_mod):
     plan.enable_refinement(True)
     u_out, q_out, info = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=1500)
     assert info["status"] == 0 and info["refine_steps"] >= 1, info
+    assert info["rel_residual_fp64"] == info["rel_residual"] <= 1e-8  # the double-float companion's residual
     x = np.where(bc == 0, q_out, u_out)
     rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, u * (bc == 0), q * (bc == 1))
     r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
