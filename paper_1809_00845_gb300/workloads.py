@@ -6,6 +6,7 @@ isolation (``ncu`` captures a named kernel of this process).
 
 Workloads (seeded synthetic inputs, the bench's geometry recipes):
   star       2D Laplace, r = 0.3 (1 + 0.3 cos 5 theta), mixed boundary conditions
+  panels     the same star as flat panels (accuracy mode, order 3, near radius 5), mixed conditions
   circle     2D Laplace, radius 0.35
   ellipsoid  3D Laplace, semi-axes (0.4, 0.3, 0.2)
   cube       3D Kelvin (nu = 0.3, mu = 1), side 0.5 on node planes
@@ -36,6 +37,10 @@ def make_plan(workload: str, n: int, precision: str, flags: int = 0):
         b = I.circle_boundary(n, 0.35)
         p = Plan.from_boundary(b, "laplace2d", precision, flags=flags)
         p.set_bc(I.mixed_bc_theta(b), 0.5)
+    elif workload == "panels":
+        b = I.curve_panels(n, I.star_curve(0.3, 0.3, 5))
+        p = Plan.from_panel_boundary(b, precision, 3, 5)
+        p.set_bc((np.asarray(b.param) >= np.pi).astype(np.uint8), 0.5)
     elif workload == "ellipsoid":
         b = I.ellipsoid_boundary(n)
         p = Plan.from_boundary(b, "laplace3d", precision, flags=flags)
@@ -51,7 +56,7 @@ def make_plan(workload: str, n: int, precision: str, flags: int = 0):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("workload", choices=["star", "circle", "ellipsoid", "cube"])
+    ap.add_argument("workload", choices=["star", "panels", "circle", "ellipsoid", "cube"])
     ap.add_argument("--n", type=int, default=None, help="grid cells per axis (default: the bench's size)")
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--layer", default="single", choices=["single", "double", "system"])
@@ -61,7 +66,7 @@ def main(argv=None):
     import torch
     from paper_1809_00845_gb300 import build
     build.build()
-    n = args.n or {"star": 4096, "circle": 128, "ellipsoid": 256, "cube": 128}[args.workload]
+    n = args.n or {"star": 4096, "panels": 4096, "circle": 128, "ellipsoid": 256, "cube": 128}[args.workload]
     from paper_1809_00845_gb300.bem import BEM_PLAN_THREE_PASS
     b, p = make_plan(args.workload, n, args.precision, BEM_PLAN_THREE_PASS if args.three_pass else 0)
     dt = torch.float32 if args.precision in ("f32", "tc_bf16x3", "tc_f16x3") else torch.float64
