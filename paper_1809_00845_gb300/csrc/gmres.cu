@@ -529,6 +529,8 @@ struct BatchSolveWs {
   int64_t* off = nullptr;
   int32_t* sys = nullptr;
   int* h_active = nullptr;  // pinned
+  int C = 1;                 // chunks per system segment of the dot products
+  double* dpart = nullptr;   // K * (m + 1) * C partial dot products (C > 1)
   cudaStream_t st = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -559,26 +561,46 @@ __global__ void k_b_copy_vj(const double* __restrict__ V, int64_t Mt, const int*
   if (i < Mt) dst[i] = V[(int64_t)(*jdev) * Mt + i];
 }
 
-// out[s*ldo + k] = <V_k, w> over the segment of system s, for k < nvec
-// (nvec = *jdev + 1, or nfix when jdev is null); one block per (k, s)
+// <V_k, w> over chunk c of the segment of system s, for k < nvec (nvec =
+// *jdev + 1, or nfix when jdev is null); one block per (k, s, c), the segment
+// cut into gridDim.z equal chunks.  With one chunk the result goes to
+// out[s*ldo + k], else to part[(s*ldo + k)*C + c] for k_b_dots_final.
 __global__ void k_b_dots(const double* __restrict__ V, int64_t ldv, const int* __restrict__ jdev, int nfix,
                          const double* __restrict__ w, const int64_t* __restrict__ off, double* __restrict__ out,
-                         int ldo) {
+                         int ldo, double* __restrict__ part) {
   __shared__ double red[kDotThreads / 32];
-  const int k = blockIdx.x, s = blockIdx.y;
+  const int k = blockIdx.x, s = blockIdx.y, c = blockIdx.z, C = gridDim.z;
   const int nvec = jdev ? *jdev + 1 : nfix;
   if (k >= nvec) return;
   const double* a = V + (int64_t)k * ldv;
+  const int64_t a0 = off[s], len = off[s + 1] - a0;
+  const int64_t i0 = a0 + len * c / C, i1 = a0 + len * (c + 1) / C;
   double acc = 0.0;
-  for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += kDotThreads) acc += a[i] * w[i];
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kDotThreads) acc += a[i] * w[i];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
     acc = threadIdx.x < kDotThreads / 32 ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) out[(int64_t)s * ldo + k] = acc;
+    if (threadIdx.x == 0) {
+      if (C == 1) out[(int64_t)s * ldo + k] = acc;
+      else part[((int64_t)s * ldo + k) * C + c] = acc;
+    }
   }
+}
+
+// out[s*ldo + k] = sum over the C chunks in order, for k < nvec
+__global__ void k_b_dots_final(const int* __restrict__ jdev, int nfix, int K, int C,
+                               const double* __restrict__ part, double* __restrict__ out, int ldo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // s * ldo + k
+  if (i >= K * ldo) return;
+  const int k = i % ldo;
+  const int nvec = jdev ? *jdev + 1 : nfix;
+  if (k >= nvec) return;
+  double acc = 0.0;
+  for (int c = 0; c < C; ++c) acc += part[(int64_t)i * C + c];
+  out[i] = acc;
 }
 
 // w[i] -= sum_{k <= *j} V[k][i] h[sys(i)][k]
@@ -744,10 +766,19 @@ bem_status batch_apply_f64(bem_batch_s* bt, const double* v, double* w, cudaStre
   return BEM_OK;
 }
 
+// out[s*ldo + k] = <V_k, w>_s for k < nvec (gx >= nvec blocks per system),
+// each segment in W.C chunks summed in a fixed order
+void b_dots(const BatchSolveWs& W, const double* V, int64_t ldv, const int* jdev, int nfix, const double* w,
+            double* out, int ldo, int gx, cudaStream_t st) {
+  k_b_dots<<<dim3(gx, W.K, W.C), kDotThreads, 0, st>>>(V, ldv, jdev, nfix, w, W.off, out, ldo, W.dpart);
+  if (W.C > 1)
+    k_b_dots_final<<<blocks_for((int64_t)W.K * ldo, 128), 128, 0, st>>>(jdev, nfix, W.K, W.C, W.dpart, out, ldo);
+}
+
 // per-system squared norms of v into W.nrm (device) and `out` (host)
 bem_status seg_norms(BatchSolveWs& W, const double* v, std::vector<double>& out) {
   cudaStream_t st = W.st;
-  k_b_dots<<<dim3(1, W.K), kDotThreads, 0, st>>>(v, W.Mt, nullptr, 1, v, W.off, W.nrm, 1);
+  b_dots(W, v, W.Mt, nullptr, 1, v, W.nrm, 1, 1, st);
   out.resize(W.K);
   BEM_CUDA_TRY(cudaMemcpyAsync(out.data(), W.nrm, W.K * sizeof(double), cudaMemcpyDeviceToHost, st));
   BEM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -772,12 +803,11 @@ bem_status capture_arnoldi(bem_batch_s* bt, BatchSolveWs& W) {
   batch_precond(bt, W.vin, W.zz, cs);
   bem_status rc = batch_apply_f64(bt, W.zz, W.w, cs, false);
   if (rc == BEM_OK) {
-    const dim3 gd(m + 1, K);
-    k_b_dots<<<gd, kDotThreads, 0, cs>>>(W.V, Mt, W.jdev, 0, W.w, W.off, W.h1, ldh);
+    b_dots(W, W.V, Mt, W.jdev, 0, W.w, W.h1, ldh, m + 1, cs);
     k_b_sub<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.V, Mt, W.jdev, W.sys, W.h1, ldh, W.w, Mt);
-    k_b_dots<<<gd, kDotThreads, 0, cs>>>(W.V, Mt, W.jdev, 0, W.w, W.off, W.h2, ldh);
+    b_dots(W, W.V, Mt, W.jdev, 0, W.w, W.h2, ldh, m + 1, cs);
     k_b_sub<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.V, Mt, W.jdev, W.sys, W.h2, ldh, W.w, Mt);
-    k_b_dots<<<dim3(1, K), kDotThreads, 0, cs>>>(W.w, Mt, nullptr, 1, W.w, W.off, W.nrm, 1);
+    b_dots(W, W.w, Mt, nullptr, 1, W.w, W.nrm, 1, 1, cs);
     k_b_next<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.w, W.nrm, W.sys, W.V, Mt, W.jdev, m, Mt);
     k_b_givens<<<1, ((K + 31) / 32) * 32, 0, cs>>>(K, m, W.jdev, W.h1, W.h2, ldh, W.nrm, W.H, W.cs, W.sn, W.g,
                                                    W.bnorm, W.tolv, W.jstop, W.relest, W.active);
@@ -976,6 +1006,11 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     ok = ok && dalloc(*W, &W->jdev, 1) == BEM_OK && dalloc(*W, &W->jstop, K) == BEM_OK &&
          dalloc(*W, &W->active, 1) == BEM_OK;
     ok = ok && dalloc(*W, &W->off, K + 1) == BEM_OK && dalloc(*W, &W->sys, Mt) == BEM_OK;
+    // dot-product chunks: about 8192 elements each (32 blocks at most per vector and system)
+    int64_t maxseg = 0;
+    for (int s = 0; s < K; ++s) maxseg = std::max<int64_t>(maxseg, (int64_t)(bt->offset[s + 1] - bt->offset[s]));
+    W->C = (int)std::min<int64_t>(32, std::max<int64_t>(1, maxseg / 8192));
+    if (W->C > 1) ok = ok && dalloc(*W, &W->dpart, (size_t)K * (m + 1) * W->C) == BEM_OK;
     if (!ok) {
       batch_solve_free(bt);
       return BEM_ERR_OOM;
