@@ -811,8 +811,10 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
 }
 
 // Grouped launch: the plans of a batch that share the grid (same N and thread
-// count) in one persistent launch.  The P (n + 1) columns of the group are
-// split into gridDim.x contiguous ranges, one per CTA; a CTA walks the plans
+// count) in one persistent launch, with the fused cell walks of k_col2d_v2
+// (each CTA gathers the last column of a plan's range before it flushes).
+// The P (n + 1) columns of the group are split into gridDim.x contiguous
+// ranges, one per CTA; a CTA walks the plans
 // its range touches, for each one zeroing its accumulators, running its
 // columns and flushing them into the plan's partial sums at row
 // blockIdx.x - c0[plan] (c0: the first CTA whose range reaches the plan, so
@@ -841,7 +843,6 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
                          (T)(6.283185307179586476925 / (double)N)};
   FourStep<T, 0> fs;
   fs.init(t, TT, sA, ftab);
-  const ColSmem<T> sm{sA, sF, sS, carry, nullptr};
   const int64_t C = (int64_t)nplans * (n + 1);
   const int64_t lo = (int64_t)blockIdx.x * C / gridDim.x, hi = ((int64_t)blockIdx.x + 1) * C / gridDim.x;
   for (int64_t c = lo; c < hi;) {
@@ -854,11 +855,26 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
     cplx<T>* twc = p.twc ? p.twc + (size_t)slot * p.npos : nullptr;
     const int qs = p.acc_rows;
     const int cnt = __ldg(p.chunk + t + 1) - __ldg(p.chunk + t);
-    __syncthreads();  // the previous plan's accumulators have been flushed
+    // per-column twiddles of the fused walks, after this plan's accumulator rows
+    cplx<T>* stw = reinterpret_cast<cplx<T>*>(sacc + (size_t)qs * TT);
+    const ColSmem<T> sm{sA, sF, sS, carry, stw};
+    __syncthreads();  // the previous plan's accumulators have been flushed and its tables read
     for (int i = 0; i < cnt; ++i) *acc_at(sacc, gacc, qs, i, TT, t) = T(0);
+    if constexpr (ACCREG) column_twiddles(g, k0, tw, stw);
+    int kxp = -1;  // the column whose gather is pending (fused walks)
     for (int kx = k0; kx < k1; ++kx) {
       __syncthreads();
-      col2d_column<T, NF, ACCREG, TTC, 0>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc);
+      col2d_column<T, NF, ACCREG, TTC, 0, false, ACCREG>(p, g, kx, fs, tw, sm, sacc, gacc, qs, twc,
+                                                         cplx<T>{T(1), T(0)}, kxp);
+      if constexpr (ACCREG) column_twiddles(g, kx + 1, tw, stw);
+      kxp = kx;
+    }
+    if constexpr (ACCREG) {
+      if (kxp >= 0) {
+        __syncthreads();
+        walk_cells<T, NF, TTC, false, false, true, CB>(p, g, kxp, cnt, nullptr, nullptr, nullptr, sA, sacc, gacc, qs,
+                                                      tw, stw, twc, cplx<T>{T(0), T(0)});
+      }
     }
     __syncthreads();
     for (int i = 0; i < cnt && i < qs; ++i) gacc[(size_t)i * TT + t] = sacc[(size_t)i * TT + t];
