@@ -588,6 +588,12 @@ def secondary_configs(dev):
                                  "double_apply_ms": _time_applies(p, "double", x, 5),
                                  "plan_s": p.info()["plan_seconds"], "zpass_lines_tuned": zl}
     p.close()
+    # the refinement companion of 3D FP32 plans: double-float passes, against FP64
+    x64 = x.double()
+    for prec in ("f32x2", "f64"):
+        p = Plan.from_boundary(b, "laplace3d", prec)
+        out["ellipsoid_n256_f32"][f"{prec}_single_apply_ms"] = _time_applies(p, "single", x64, 3)
+        p.close()
     # batched: 64 random stars on uneven grids, one CUDA graph per batched apply
     from paper_1809_00845_gb300.bem import Batch
     rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 4))

@@ -71,7 +71,8 @@ typedef enum { BEM_LAPLACE_2D = 0, BEM_LAPLACE_3D = 1, BEM_KELVIN_3D = 2 } bem_k
  * 48-bit significand) on the FP32 pipes, double I/O; about 1e-13 relative
  * accuracy at several times the speed of FP64 on GPUs with reduced FP64
  * throughput.  BEM_F32X2 is available for 2D plans with n >= 256 (the
- * four-step column kernel) and returns BEM_ERR_UNSUPPORTED otherwise.
+ * four-step column kernel) and for 3D plans, and returns BEM_ERR_UNSUPPORTED
+ * for 2D plans with n < 256.
  * BEM_TC_BF16X3, BEM_TC_F16X3: FP32 I/O and arithmetic except the radix-16
  * DFT stages of the column transforms (Eq. 16), which run on the tensor cores
  * as DFT-matrix products with every FP32 operand split into a 16-bit hi and
@@ -272,8 +273,8 @@ bem_status bem_solve(bem_plan_t plan, const uint8_t* bc, const double* data, dou
 bem_status bem_set_preconditioner(bem_plan_t plan, int kind, int block_size);
 
 /* Mixed-precision iterative refinement for BEM_F32 plans: with enable != 0
- * the plan builds a companion plan of the same geometry in BEM_F32X2 (2D,
- * n >= 256) or BEM_F64 (otherwise); bem_solve then forms the right-hand side
+ * the plan builds a companion plan of the same geometry in BEM_F32X2 (3D, and
+ * 2D with n >= 256) or BEM_F64 (2D, n < 256); bem_solve then forms the right-hand side
  * and every residual with the companion operator and solves
  * for the corrections with the preconditioned FP32 GMRES, so that tolerances
  * below the FP32 operator's own accuracy (plain FP32 GMRES stalls at a

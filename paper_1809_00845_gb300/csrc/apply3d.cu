@@ -18,6 +18,7 @@
 // values per field.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "bem_internal.h"
@@ -41,22 +42,24 @@ struct Tw2 {
 
 // ------------------------------------------------------------------ kernels
 
-template <typename T>
-__global__ void k3_prep(int nb, int ncomp, const int32_t* __restrict__ perm, const T* __restrict__ in,
+// T: arithmetic type of the passes; TIO: type of the caller's vectors (FP64
+// for double-float plans, else T)
+template <typename T, typename TIO>
+__global__ void k3_prep(int nb, int ncomp, const int32_t* __restrict__ perm, const TIO* __restrict__ in,
                         const Field3D* __restrict__ fields, T* __restrict__ val) {
   const int f = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const Field3D fd = fields[f];
-  val[(size_t)f * nb + j] = static_cast<const T*>(fd.coef)[j] * in[(size_t)perm[j] * ncomp + fd.comp];
+  val[(size_t)f * nb + j] = static_cast<const T*>(fd.coef)[j] * T(in[(size_t)perm[j] * ncomp + fd.comp]);
 }
 
 // out[perm[j]*ncomp + o] = sum_kx c_kx Re(X_o[kx][z][y] e^{+2 pi i kx x/N}) + diag * in
-template <typename T>
+template <typename T, typename TIO>
 __global__ void k3_gather(int n, int log2N, int nb, int ncomp, const int32_t* __restrict__ perm,
                           const uint16_t* __restrict__ xs, const uint32_t* __restrict__ yz,
-                          const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ tw2, const T* __restrict__ diag,
-                          const T* __restrict__ in, T* __restrict__ out) {
+                          const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ tw2,
+                          const TIO* __restrict__ diag, const TIO* __restrict__ in, TIO* __restrict__ out) {
   __shared__ cplx<T> stw[2048 / 64 + 64 + 64];
   const int N = 1 << log2N;
   const int nhi = N >= 64 ? N >> 6 : 1;
@@ -71,22 +74,26 @@ __global__ void k3_gather(int n, int log2N, int nb, int ncomp, const int32_t* __
   const int y = (int)(p & 0xffffu), z = (int)(p >> 16);
   const int64_t plane = (int64_t)n * n;
   const cplx<T>* src = X + (size_t)o * (n + 1) * plane + (size_t)z * n + y;
-  // compensated FP32 sum (FP64 plans: plain FP64 sum)
-  T s = 0, comp = 0;
+  // compensated FP32 sum (FP64 and double-float plans: plain sum)
+  T s = T(0), comp = T(0);
   for (int kx = 0; kx <= n; ++kx) {
     const cplx<T> Y = src[(size_t)kx * plane];
     const cplx<T> w = tw.template get<+1>((kx * x) & (N - 1));
     const T ck = (kx == 0 || kx == n) ? T(1) : T(2);
-    const T term = ck * (Y.x * w.x - Y.y * w.y) - comp;
-    const T ns = s + term;
-    comp = (ns - s) - term;
-    s = ns;
+    if constexpr (std::is_same<T, float>::value) {
+      const T term = ck * (Y.x * w.x - Y.y * w.y) - comp;
+      const T ns = s + term;
+      comp = (ns - s) - term;
+      s = ns;
+    } else {
+      s = s + ck * (Y.x * w.x - Y.y * w.y);
+    }
   }
   const int u = perm[j];
   const size_t oi = (size_t)u * ncomp + o;
   double r = (double)s;
   if (diag) r += (double)diag[oi] * (double)in[oi];
-  out[oi] = (T)r;
+  out[oi] = (TIO)r;
 }
 
 // ------------------------------------------------------------------ host
@@ -116,13 +123,14 @@ struct Passes3D {
   }
 };
 
-template <typename T>
+template <typename T, typename TIO = T>
 static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in, void* out, void* val, void* X,
                              void* B, bool timed, cudaStream_t st) {
   const int n = (int)p->n, nb = (int)p->nb;
   const int tb = 256;
-  k3_prep<T><<<dim3((nb + tb - 1) / tb, op.nf), tb, 0, st>>>(nb, p->ncomp, p->d_perm, static_cast<const T*>(in),
-                                                              op.d_fields, static_cast<T*>(val));
+  k3_prep<T, TIO><<<dim3((nb + tb - 1) / tb, op.nf), tb, 0, st>>>(nb, p->ncomp, p->d_perm,
+                                                                   static_cast<const TIO*>(in), op.d_fields,
+                                                                   static_cast<T*>(val));
   cudaEvent_t e1 = nullptr;
   if (timed) {
     if (p->ev_used + 2 > (int)p->ev_pool.size())
@@ -143,10 +151,10 @@ static bem_status launch3d_t(bem_plan_s* p, const Operator3D& op, const void* in
     return 0;
   });
   if (timed) BEM_CUDA_TRY(cudaEventRecord(e1, st));
-  k3_gather<T><<<dim3((nb + tb - 1) / tb, op.no), tb, 0, st>>>(
+  k3_gather<T, TIO><<<dim3((nb + tb - 1) / tb, op.no), tb, 0, st>>>(
       n, p->log2N, nb, p->ncomp, p->d_perm, p->d_x3, p->d_yz3, static_cast<const cplx<T>*>(X),
-      static_cast<const cplx<T>*>(p->d_tw2), static_cast<const T*>(op.diag), static_cast<const T*>(in),
-      static_cast<T*>(out));
+      static_cast<const cplx<T>*>(p->d_tw2), static_cast<const TIO*>(op.diag), static_cast<const TIO*>(in),
+      static_cast<TIO*>(out));
   BEM_CUDA_TRY(cudaGetLastError());
   return BEM_OK;
 }
@@ -183,12 +191,31 @@ int zpass_lpc(const bem_plan_s* p, int nf) {
   return lpc;
 }
 
+// complex table (FP64 values) in the plan's arithmetic type, rounded once
+template <typename T>
+static bem_status upload_table3_t(const std::vector<double>& re, const std::vector<double>& im, void** dst) {
+  std::vector<cplx<T>> t(re.size());
+  for (size_t i = 0; i < re.size(); ++i) t[i] = {T(re[i]), T(im[i])};
+  BEM_CUDA_TRY(cudaMalloc(dst, t.size() * sizeof(t[0])));
+  BEM_CUDA_TRY(cudaMemcpy(*dst, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice));
+  return BEM_OK;
+}
+
+static bem_status upload_table3(const bem_plan_s* p, const std::vector<double>& re, const std::vector<double>& im,
+                                void** dst) {
+  if (p->prec == BEM_F64) return upload_table3_t<double>(re, im, dst);
+  if (p->prec == BEM_F32X2) return upload_table3_t<f32x2>(re, im, dst);
+  return upload_table3_t<float>(re, im, dst);
+}
+
 bem_status setup_apply_3d(bem_plan_s* p, int maxnf) {
   if (p->log2N < 5 || p->log2N > 10) {
     set_error("3D grids need 16 <= n <= 512, n a power of two");
     return BEM_ERR_UNSUPPORTED;
   }
-  bem_status rc = p->prec == BEM_F64 ? configure3d_t<double>(p) : configure3d_t<float>(p);
+  bem_status rc = p->prec == BEM_F64     ? configure3d_t<double>(p)
+                  : p->prec == BEM_F32X2 ? configure3d_t<f32x2>(p)
+                                         : configure3d_t<float>(p);
   if (rc != BEM_OK) return rc;
   // 2-level twiddles e^{2 pi i m / N}
   const int64_t N = p->N;
@@ -216,31 +243,11 @@ bem_status setup_apply_3d(bem_plan_s* p, int maxnf) {
           pim.push_back(std::sin(2 * PI * (double)(k * r) / (double)(Ns * R)));
         }
     }
-    const size_t np = std::max<size_t>(pre.size(), 1);
-    if (p->prec == BEM_F64) {
-      std::vector<cplx<double>> t(np);
-      for (size_t i = 0; i < pre.size(); ++i) t[i] = {pre[i], pim[i]};
-      BEM_CUDA_TRY(cudaMalloc(&p->d_ptab3, np * sizeof(t[0])));
-      BEM_CUDA_TRY(cudaMemcpy(p->d_ptab3, t.data(), np * sizeof(t[0]), cudaMemcpyHostToDevice));
-    } else {
-      std::vector<cplx<float>> t(np);
-      for (size_t i = 0; i < pre.size(); ++i) t[i] = {(float)pre[i], (float)pim[i]};
-      BEM_CUDA_TRY(cudaMalloc(&p->d_ptab3, np * sizeof(t[0])));
-      BEM_CUDA_TRY(cudaMemcpy(p->d_ptab3, t.data(), np * sizeof(t[0]), cudaMemcpyHostToDevice));
-    }
+    pre.resize(std::max<size_t>(pre.size(), 1), 0.0);
+    pim.resize(pre.size(), 0.0);
+    if ((rc = upload_table3(p, pre, pim, &p->d_ptab3)) != BEM_OK) return rc;
   }
-  const size_t m = re.size();
-  if (p->prec == BEM_F64) {
-    std::vector<cplx<double>> t(m);
-    for (size_t i = 0; i < m; ++i) t[i] = {re[i], im[i]};
-    BEM_CUDA_TRY(cudaMalloc(&p->d_tw2, m * sizeof(t[0])));
-    BEM_CUDA_TRY(cudaMemcpy(p->d_tw2, t.data(), m * sizeof(t[0]), cudaMemcpyHostToDevice));
-  } else {
-    std::vector<cplx<float>> t(m);
-    for (size_t i = 0; i < m; ++i) t[i] = {(float)re[i], (float)im[i]};
-    BEM_CUDA_TRY(cudaMalloc(&p->d_tw2, m * sizeof(t[0])));
-    BEM_CUDA_TRY(cudaMemcpy(p->d_tw2, t.data(), m * sizeof(t[0]), cudaMemcpyHostToDevice));
-  }
+  if ((rc = upload_table3(p, re, im, &p->d_tw2)) != BEM_OK) return rc;
   // buffers sized for the widest operator
   const size_t tb = prec_bytes(p);
   BEM_CUDA_TRY(cudaMalloc(&p->d_val3, (size_t)maxnf * p->nb * tb));
@@ -261,8 +268,9 @@ bem_status launch_apply_3d(bem_plan_s* p, const Operator3D& op, const void* in, 
     set_error("3D operator wider than the plan's buffers");
     return BEM_ERR_UNSUPPORTED;
   }
-  return p->prec == BEM_F64 ? launch3d_t<double>(p, op, in, out, val, X, B, p->timing, st)
-                            : launch3d_t<float>(p, op, in, out, val, X, B, p->timing, st);
+  if (p->prec == BEM_F64) return launch3d_t<double>(p, op, in, out, val, X, B, p->timing, st);
+  if (p->prec == BEM_F32X2) return launch3d_t<f32x2, double>(p, op, in, out, val, X, B, p->timing, st);
+  return launch3d_t<float>(p, op, in, out, val, X, B, p->timing, st);
 }
 
 }  // namespace bemfft

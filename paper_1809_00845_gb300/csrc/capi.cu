@@ -265,8 +265,8 @@ static bem_status plan_impl(bem_plan_t* out, int dim, const int64_t* n, double h
     set_error("bem_plan: unknown precision");
     return BEM_ERR_ARG;
   }
-  if (prec == BEM_F32X2 && (dim != 2 || n[0] < 256)) {
-    set_error("bem_plan: BEM_F32X2 needs a 2D grid with n >= 256");
+  if (prec == BEM_F32X2 && dim == 2 && n[0] < 256) {
+    set_error("bem_plan: BEM_F32X2 needs n >= 256 in 2D");
     return BEM_ERR_UNSUPPORTED;
   }
   // tensor-core DFT stages: an FP32 plan whose column kernel runs its
@@ -730,7 +730,7 @@ bem_status bem_enable_refinement(bem_plan_t p, int enable) {
   }
   bem_status rc = plan_impl(&c, p->dim, n, p->h, p->nb, p->h_cell_user.data(), p->h_w_user.data(),
                             p->h_normal_user.data(), (bem_kernel)p->kernel, p->nu, p->mu,
-                            p->dim == 2 && p->n >= 256 ? BEM_F32X2 : BEM_F64, 0, nullptr);
+                            p->dim == 3 || p->n >= 256 ? BEM_F32X2 : BEM_F64, 0, nullptr);
   if (rc != BEM_OK) return rc;
   c->pc.kind = 0;
   p->companion = c;

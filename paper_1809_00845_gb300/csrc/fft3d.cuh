@@ -19,6 +19,8 @@
 // Included only by the translation units that instantiate Fft3DKernels.
 #pragma once
 
+#include <type_traits>
+
 #include "bem_internal.h"
 #include "fft3d.h"
 #include "fft4step.cuh"
@@ -38,6 +40,14 @@ struct Tw64 {
     return z;
   }
 };
+
+// read-only load of one value of the working type (the read-only cache path
+// for float and double; a double-float pair is read as a plain struct)
+template <typename T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) return __ldg(p);
+  else return *p;
+}
 
 template <int LOG2N>
 struct Line3D {
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
     cplx<T> sum = {T(0), T(0)};
     for (int j = j0[m]; j < j1[m]; ++j) {
       const cplx<T> w = t64.template get<-1>((kx * (int)__ldg(xs + j)) & (N - 1));
-      const T r = __ldg(vf + j);
+      const T r = ld_ro(vf + j);
       sum.x += r * w.x;
       sum.y += r * w.y;
     }
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(512) k3_zpass(int nf, int no, int LPC, const i
     for (int m = 0; m < 16; ++m) {
       const int kz = t + m * TT;
       const bool hiz = kz > n;
-      const T a = __ldg(S + (hiz ? N - kz : kz));
+      const T a = ld_ro(S + (hiz ? N - kz : kz));
       sv[m] = (negy != (hiz && sp.oddz)) ? -a : a;
     }
   };

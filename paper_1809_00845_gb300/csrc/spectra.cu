@@ -311,6 +311,8 @@ bem_status compute_spectra_3d(bem_plan_s* p, cudaStream_t st) {
     }
     if (p->prec == BEM_F64)
       k_compress3d<double><<<152 * 16, 256, 0, st>>>(buf, n, N, q, scale, static_cast<double*>(d));
+    else if (p->prec == BEM_F32X2)
+      k_compress3d<f32x2><<<152 * 16, 256, 0, st>>>(buf, n, N, q, scale, static_cast<f32x2*>(d));
     else
       k_compress3d<float><<<152 * 16, 256, 0, st>>>(buf, n, N, q, scale, static_cast<float*>(d));
     sp.data = d;

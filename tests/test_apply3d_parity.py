@@ -1,5 +1,6 @@
 """Parity of the 3D CUDA apply (3D Laplace, Kelvin) with the CPU FP64 oracle
-(GPU).  Relative L2 <= 1e-12 (FP64) / 2e-6 (FP32) on random N(0,1) densities."""
+(GPU).  Relative L2 <= 1e-12 (FP64 and double-float) / 2e-6 (FP32) on random
+N(0,1) densities."""
 import numpy as np
 import pytest
 
@@ -7,7 +8,7 @@ from paper_1809_00845_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 2e-6}
+TOL = {"f64": 1e-12, "f32x2": 1e-12, "f32": 2e-6}
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +39,7 @@ def _plan(b, kernel, prec, nu=0.3, mu=1.0):
     return Plan.from_boundary(b, kernel, prec, nu=nu, mu=mu)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 @pytest.mark.parametrize("n,nb", [(16, 60), (32, 400), (64, 1500)])
 def test_laplace3d_random_cells(torch_cuda, oracle_mod, prec, n, nb):
     rng = np.random.default_rng(300 + n)
@@ -54,7 +55,7 @@ def test_laplace3d_random_cells(torch_cuda, oracle_mod, prec, n, nb):
     assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 @pytest.mark.parametrize("n,nb", [(16, 50), (32, 300)])
 def test_kelvin_random_cells(torch_cuda, oracle_mod, prec, n, nb):
     rng = np.random.default_rng(700 + n)
@@ -70,7 +71,7 @@ def test_kelvin_random_cells(torch_cuda, oracle_mod, prec, n, nb):
     assert rel_l2(gpu_apply(torch_cuda, plan, "system", x), ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 def test_system_operator_uniform_bc_3d(torch_cuda, oracle_mod, prec):
     """All-Dirichlet and all-Neumann data in 3D (Laplace and Kelvin, the
     latter also with one component Neumann everywhere): the system operator
@@ -106,7 +107,7 @@ def test_kelvin_other_material(torch_cuda, oracle_mod):
         assert rel_l2(gpu_apply(torch_cuda, plan, layer, x), ref) <= 1e-12
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 def test_ellipsoid_n64(torch_cuda, oracle_mod, prec):
     b = I.ellipsoid_boundary(64)
     rng = np.random.default_rng(8)
@@ -142,7 +143,7 @@ def test_cube_kelvin_n128_full_size_sampled_rows(torch_cuda, oracle_mod):
         assert rel_l2(out[1000:1128], ref) <= TOL["f32"], layer
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "f32x2"])
 def test_largest_3d_grid_sampled_rows(torch_cuda, oracle_mod, prec):
     """The largest supported 3D grid, n = 512 (padded 1024^3: line FFTs span
     two warps, 8 planes per y-pass block), a small ellipsoid of 46k cells,
