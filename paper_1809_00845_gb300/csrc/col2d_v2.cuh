@@ -267,7 +267,7 @@ template <typename T, int NB>
 struct CellBatch {
   uint32_t m[NB];
   cplx<T> v[NB], w[NB];
-  T c[NB];
+  T c[NB], a[NB];
 };
 
 // One walk over the thread's cells that serves two columns (kernels with the
@@ -304,6 +304,17 @@ __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColD
         if (twc) B.w[i] = twc[pos + i * TT];
       }
     }
+    // accumulator rows kept in the partial sums (not in shared memory) are
+    // read with the batch, so their L2 round trip overlaps the batch before.
+    // Only in the edge-flow kernels (the accuracy mode's node plans, whose
+    // ~100 nodes a thread overflow shared memory): it costs the paper-form
+    // star kernel, whose rows all fit, 5 us in register allocation.
+    if constexpr (GATHER && EDGE) {
+      if (base + NB > qs) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) B.a[i] = base + i >= qs ? gacc[(size_t)(base + i) * TT + t] : T(0);
+      }
+    }
   };
   auto process = [&](CellBatch<T, NB>& B, int i0) {
     if constexpr (GATHER) {
@@ -319,6 +330,14 @@ __device__ __forceinline__ void walk_cells(const Col2Dv2Params<T>& p, const ColD
 #pragma unroll
         for (int i = 0; i < NB; ++i)
           if (i0 + i < cnt) acc[i * TT] += Y[i].x * wp[i].x - Y[i].y * wp[i].y;
+      } else if constexpr (EDGE) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i0 + i >= cnt) continue;
+          const T term = Y[i].x * wp[i].x - Y[i].y * wp[i].y;
+          if (i0 + i < qs) sacc[(size_t)(i0 + i) * TT + t] += term;
+          else gacc[(size_t)(i0 + i) * TT + t] = B.a[i] + term;
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < NB; ++i)
