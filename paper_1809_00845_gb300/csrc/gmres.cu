@@ -120,6 +120,12 @@ static inline dim3 block_apply_grid(int nblocks, int bs) {
   return dim3((unsigned)nblocks, (unsigned)((bs + kBlockApplyRows - 1) / kBlockApplyRows));
 }
 
+// z = M^-1 v on one plan's segment (m unknowns per block)
+static void block_apply(const bem_plan_s* p, int m, int64_t M, const double* v, double* z, cudaStream_t st) {
+  k_block_apply<<<block_apply_grid(p->pc.nblocks, m), 32 * kBlockApplyRows, m * sizeof(double), st>>>(p->pc.d_inv, m,
+                                                                                                   M, v, z);
+}
+
 // masked copies: um = data * (1 - bc), qm = data * bc
 __global__ void k_split_known(const double* __restrict__ data, const uint8_t* __restrict__ bc, double* __restrict__ um,
                               double* __restrict__ qm, int64_t M) {
@@ -178,8 +184,7 @@ struct Gm {
       cudaMemcpyAsync(z, v, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
     } else {
       const int m = p->pc.bs * p->ncomp;
-      k_block_apply<<<block_apply_grid(p->pc.nblocks, m), 32 * kBlockApplyRows, m * sizeof(double), st>>>(
-          p->pc.d_inv, m, M, v, z);
+      block_apply(p, m, M, v, z, st);
     }
   }
   // out[0..nvec) = V[0..nvec) . w   (device)
@@ -628,53 +633,84 @@ __global__ void k_b_next(const double* __restrict__ w, const double* __restrict_
   V[(int64_t)(j + 1) * ldv + i] = (s > 0.0 && isfinite(s)) ? w[i] / s : 0.0;
 }
 
-// Per system (one thread each): the new Hessenberg column from the two
-// Gram-Schmidt sweeps and the norm, the earlier rotations, a new rotation,
-// the residual estimate and the stop test; then j advances.
+// Per system (one warp each, WPB systems side by side, more in turn): the new
+// Hessenberg column from the two Gram-Schmidt sweeps and the norm, the earlier
+// rotations, a new rotation, the residual estimate and the stop test; then j
+// advances.  The warp stages the column and the rotations in shared memory
+// (all loads in flight), lane 0 runs the rotations there, the warp writes the
+// rotated column back.  One block; dynamic shared memory WPB * (3m + 1) doubles.
 __global__ void k_b_givens(int K, int m, int* __restrict__ jdev, const double* __restrict__ h1,
                            const double* __restrict__ h2, int ldh, const double* __restrict__ nrm2,
                            double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                            double* __restrict__ g, const double* __restrict__ bnorm, const double* __restrict__ tolv,
                            int* __restrict__ jstop, double* __restrict__ relest, int* __restrict__ active) {
-  const int s = threadIdx.x;
+  extern __shared__ double gsm[];
+  __shared__ int n_live;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, WPB = blockDim.x >> 5;
   const int j = *jdev;
+  if (threadIdx.x == 0) n_live = 0;
+  __syncthreads();
+  double* hb = gsm + (size_t)wp * (3 * m + 1);  // j + 1 column entries, then the rotated ones
+  double* cc = hb + (m + 1);
+  double* ss = cc + m;
   int live = 0;
-  if (s < K && j < m && jstop[s] < 0) {
+  for (int s = wp; s < K; s += WPB) {
+    if (!(j < m && jstop[s] < 0)) continue;  // warp-uniform
     double* col = H + ((int64_t)s * m + j) * (m + 1);
     double* c = cs + (int64_t)s * m;
     double* sv = sn + (int64_t)s * m;
-    double* gv = g + (int64_t)s * (m + 1);
-    // the earlier rotations down the new column: entry i + 1 enters rotation
-    // i unrotated, entry i leaves it final, so only the running entry is
-    // carried from one rotation to the next (the loads do not wait on it)
     const double* h1s = h1 + (int64_t)s * ldh;
     const double* h2s = h2 + (int64_t)s * ldh;
-    const double hn = sqrt(nrm2[s]);
-    double run = h1s[0] + h2s[0];
-#pragma unroll 4
-    for (int i = 0; i < j; ++i) {
-      const double bb = h1s[i + 1] + h2s[i + 1];
-      col[i] = c[i] * run + sv[i] * bb;
-      run = -sv[i] * run + c[i] * bb;
+    for (int i = lane; i <= j; i += 32) hb[i] = h1s[i] + h2s[i];
+    for (int i = lane; i < j; i += 32) {
+      cc[i] = c[i];
+      ss[i] = sv[i];
     }
-    const double a = run, bb = hn;
-    const double r = hypot(a, bb);
-    c[j] = r > 0 ? a / r : 1.0;
-    sv[j] = r > 0 ? bb / r : 0.0;
-    col[j] = r;
-    col[j + 1] = 0.0;
-    gv[j + 1] = -sv[j] * gv[j];
-    gv[j] = c[j] * gv[j];
-    const double rel = bnorm[s] > 0 ? fabs(gv[j + 1]) / bnorm[s] : 0.0;
-    relest[s] = rel;
-    if (!(rel > tolv[s]) || !(hn > 1e-14 * bnorm[s]) || j + 1 == m) jstop[s] = j + 1;
-    else live = 1;
+    __syncwarp();
+    if (lane == 0) {
+      // the earlier rotations down the new column: entry i + 1 enters rotation
+      // i unrotated, entry i leaves it final
+      double* gv = g + (int64_t)s * (m + 1);
+      const double hn = sqrt(nrm2[s]);
+      double run = hb[0];
+      for (int i = 0; i < j; ++i) {
+        const double bb = hb[i + 1];
+        hb[i] = cc[i] * run + ss[i] * bb;
+        run = -ss[i] * run + cc[i] * bb;
+      }
+      const double a = run, bb = hn;
+      const double r = hypot(a, bb);
+      c[j] = r > 0 ? a / r : 1.0;
+      sv[j] = r > 0 ? bb / r : 0.0;
+      col[j] = r;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sv[j] * gv[j];
+      gv[j] = c[j] * gv[j];
+      const double rel = bnorm[s] > 0 ? fabs(gv[j + 1]) / bnorm[s] : 0.0;
+      relest[s] = rel;
+      if (!(rel > tolv[s]) || !(hn > 1e-14 * bnorm[s]) || j + 1 == m) jstop[s] = j + 1;
+      else ++live;
+    }
+    __syncwarp();
+    for (int i = lane; i < j; i += 32) col[i] = hb[i];
+    __syncwarp();  // the warp's staging buffers are free for its next system
   }
-  const int n_live = __syncthreads_count(live);
-  if (s == 0) {
+  if (live) atomicAdd(&n_live, live);
+  __syncthreads();
+  if (threadIdx.x == 0) {
     *active = n_live;
     if (j < m) *jdev = j + 1;
   }
+}
+
+// launch shape of k_b_givens: systems side by side (warps) and the dynamic
+// shared memory they stage in
+static void givens_shape(int K, int m, int* warps, size_t* smem) {
+  const size_t per = (size_t)(3 * m + 1) * sizeof(double);
+  int wpb = std::min(K, 32);
+  while (wpb > 1 && (size_t)wpb * per > (size_t)200 * 1024) wpb >>= 1;
+  *warps = std::max(1, wpb);
+  *smem = (size_t)*warps * per;
 }
 
 // y_s = H_s^{-1} g_s over the system's own number of columns
@@ -740,8 +776,7 @@ void batch_precond(bem_batch_s* bt, const double* v, double* z, cudaStream_t st)
       cudaMemcpyAsync(z + o, v + o, M * sizeof(double), cudaMemcpyDeviceToDevice, st);
     } else {
       const int mb = p->pc.bs * p->ncomp;
-      k_block_apply<<<block_apply_grid(p->pc.nblocks, mb), 32 * kBlockApplyRows, mb * sizeof(double), st>>>(
-          p->pc.d_inv, mb, M, v + o, z + o);
+      block_apply(p, mb, M, v + o, z + o, st);
     }
   }
 }
@@ -809,7 +844,11 @@ bem_status capture_arnoldi(bem_batch_s* bt, BatchSolveWs& W) {
     k_b_sub<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.V, Mt, W.jdev, W.sys, W.h2, ldh, W.w, Mt);
     b_dots(W, W.w, Mt, nullptr, 1, W.w, W.nrm, 1, 1, cs);
     k_b_next<<<blocks_for(Mt, 256), 256, 0, cs>>>(W.w, W.nrm, W.sys, W.V, Mt, W.jdev, m, Mt);
-    k_b_givens<<<1, ((K + 31) / 32) * 32, 0, cs>>>(K, m, W.jdev, W.h1, W.h2, ldh, W.nrm, W.H, W.cs, W.sn, W.g,
+    int gw = 1;
+    size_t gsmem = 0;
+    givens_shape(K, m, &gw, &gsmem);
+    if (gsmem > 48 * 1024) cudaFuncSetAttribute(k_b_givens, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+    k_b_givens<<<1, 32 * gw, gsmem, cs>>>(K, m, W.jdev, W.h1, W.h2, ldh, W.nrm, W.H, W.cs, W.sn, W.g,
                                                    W.bnorm, W.tolv, W.jstop, W.relest, W.active);
     cudaMemcpyAsync(W.h_active, W.active, sizeof(int), cudaMemcpyDeviceToHost, cs);
   }
@@ -1006,10 +1045,10 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     ok = ok && dalloc(*W, &W->jdev, 1) == BEM_OK && dalloc(*W, &W->jstop, K) == BEM_OK &&
          dalloc(*W, &W->active, 1) == BEM_OK;
     ok = ok && dalloc(*W, &W->off, K + 1) == BEM_OK && dalloc(*W, &W->sys, Mt) == BEM_OK;
-    // dot-product chunks: about 8192 elements each (32 blocks at most per vector and system)
+    // dot-product chunks: about 2048 elements each (32 blocks at most per vector and system)
     int64_t maxseg = 0;
     for (int s = 0; s < K; ++s) maxseg = std::max<int64_t>(maxseg, (int64_t)(bt->offset[s + 1] - bt->offset[s]));
-    W->C = (int)std::min<int64_t>(32, std::max<int64_t>(1, maxseg / 8192));
+    W->C = (int)std::min<int64_t>(32, std::max<int64_t>(1, maxseg / 2048));
     if (W->C > 1) ok = ok && dalloc(*W, &W->dpart, (size_t)K * (m + 1) * W->C) == BEM_OK;
     if (!ok) {
       batch_solve_free(bt);
