@@ -27,6 +27,8 @@
 // but the DFT matrices and synchronises only its own warpgroup.
 #pragma once
 
+#include <type_traits>
+
 #include "fft_reg.cuh"
 #include "tc_dft.cuh"
 
@@ -43,7 +45,7 @@ constexpr int kTcStages = COL2D_TC_STAGES;
 template <int DIR, typename T>
 __device__ __forceinline__ void dft4_lowhalf(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
   const cplx<T> b1 = mul_i<DIR>(a1);
-  const cplx<T> x0 = a0 + a1, x2 = a0 - a1, x1 = a0 + b1, x3 = a0 - b1;
+  const cplx<T> x0 = padd(a0, a1), x2 = psub(a0, a1), x1 = a0 + b1, x3 = a0 - b1;
   a0 = x0;
   a1 = x1;
   a2 = x2;
@@ -72,6 +74,21 @@ __device__ __forceinline__ void dft16_lowhalf(cplx<T> (&a)[16]) {
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) a[i] = o[i];
+}
+
+// Radix-2 combine across a lane pair: mine + other on the even lane (h = 0),
+// other - mine on the odd one.  For FP32 one packed fused multiply-add with
+// the lane's sign (exact: a product by +-1 rounds nothing) replaces both sums
+// and the select.
+template <typename T>
+__device__ __forceinline__ cplx<T> s8_combine(cplx<T> mine, cplx<T> other, int h) {
+  if constexpr (std::is_same_v<T, float>) {
+    const float sg = h ? -1.0f : 1.0f;
+    const float2 r = __ffma2_rn(make_float2(mine.x, mine.y), make_float2(sg, sg), make_float2(other.x, other.y));
+    return {r.x, r.y};
+  } else {
+    return h ? other - mine : mine + other;
+  }
 }
 
 // Twiddle tables of the four-step engine (forward direction e^{+2 pi i ...},
@@ -204,7 +221,7 @@ struct FourStep {
       cplx<T> other;
       other.x = shfl_xor(mine.x, 1);
       other.y = shfl_xor(mine.y, 1);
-      v[k] = h ? other - mine : mine + other;
+      v[k] = s8_combine(mine, other, h);
     }
   }
   // frequency held by register k after forward(): freq0() + 16 * J * k
@@ -223,7 +240,8 @@ struct FourStep {
       cplx<T> other;
       other.x = shfl_xor(v[k].x, 1);
       other.y = shfl_xor(v[k].y, 1);
-      v[k] = h ? twc<32, +1>(other - v[k], k) : v[k] + other;
+      const cplx<T> s = s8_combine(v[k], other, h);
+      v[k] = h ? twc<32, +1>(s, k) : s;
     }
     if constexpr (TCK > 0 && (kTcStages & 8)) tc.template run<+1, false>(v, 0);
     else dft<16, +1>(v);

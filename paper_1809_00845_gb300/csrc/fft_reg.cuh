@@ -52,6 +52,23 @@ __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
 template <typename T>
 __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
 
+// Complex add and subtract.  For FP32 both parts go through one packed
+// FP32-pair instruction (sm_100 and later), the same IEEE round-to-nearest
+// sums as two scalar adds in half the issue slots; the butterflies below use
+// them wherever both parts take the same operation.
+__device__ __forceinline__ cplx<float> padd(cplx<float> a, cplx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  return {r.x, r.y};
+}
+__device__ __forceinline__ cplx<float> psub(cplx<float> a, cplx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
+  return {r.x, r.y};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> padd(cplx<T> a, cplx<T> b) { return a + b; }
+template <typename T>
+__device__ __forceinline__ cplx<T> psub(cplx<T> a, cplx<T> b) { return a - b; }
+
 // multiply by e^{DIR i pi/2} = DIR * i
 template <int DIR, typename T>
 __device__ __forceinline__ cplx<T> mul_i(cplx<T> a) {
@@ -106,17 +123,24 @@ __device__ __forceinline__ cplx<T> twc(cplx<T> a, int m) {
 template <int DIR, typename T>
 __device__ __forceinline__ void dft2(cplx<T>& a, cplx<T>& b) {
   cplx<T> t = a;
-  a = t + b;
-  b = t - b;
+  a = padd(t, b);
+  b = psub(t, b);
 }
 
 template <int DIR, typename T>
 __device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
-  cplx<T> s0 = a0 + a2, d0 = a0 - a2, s1 = a1 + a3, d1 = mul_i<DIR>(a1 - a3);
-  a0 = s0 + s1;
-  a2 = s0 - s1;
-  a1 = d0 + d1;
-  a3 = d0 - d1;
+  const cplx<T> s0 = padd(a0, a2), d0 = psub(a0, a2), s1 = padd(a1, a3), e1 = psub(a1, a3);
+  a0 = padd(s0, s1);
+  a2 = psub(s0, s1);
+  // a1 = d0 + DIR i e1, a3 = d0 - DIR i e1: the rotation swaps e1's parts, so
+  // these four sums stay scalar
+  if constexpr (DIR > 0) {
+    a1 = {d0.x - e1.y, d0.y + e1.x};
+    a3 = {d0.x + e1.y, d0.y - e1.x};
+  } else {
+    a1 = {d0.x + e1.y, d0.y - e1.x};
+    a3 = {d0.x - e1.y, d0.y + e1.x};
+  }
 }
 
 // In-place DFT of R registers: a[k] <- sum_r a[r] e^{DIR 2 pi i r k / R}.
