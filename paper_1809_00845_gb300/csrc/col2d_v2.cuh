@@ -494,8 +494,7 @@ __device__ __forceinline__ void walk_field(const Col2Dv2Params<T>& p, const ColD
           const bool ty = (mt[i] >> 31) != 0;
           const T a = vv[i].x, b = vv[i].y;
           const T c = FSEL <= 0 ? (ty ? T(0) : a) : (FSEL == 1 ? (ty ? a : b) : (ty ? b : T(0)));
-          s0.x += c * w[i].x;
-          s0.y += c * w[i].y;
+          s0 = cmacr(s0, c, w[i]);
           if (mt[i] & kMetaFlush) {
             const int row = meta_slot(mt[i]);
             const bool car = (mt[i] & kMetaCarry) != 0;
@@ -599,8 +598,7 @@ __device__ __forceinline__ void spectral_multiply(const T* sS, const SpecAddr& a
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const T sv = s[k * a.step] * (k == 0 ? sg0 : sg);
-      const cplx<T> term = {v[k].x * sv, v[k].y * sv};
-      y[k] = ACC ? y[k] + term : term;
+      y[k] = ACC ? cmacc(y[k], v[k], sv) : cscale(v[k], sv);
     }
   }
 }

@@ -168,8 +168,7 @@ __global__ void __launch_bounds__(512) k3_yfwd(int nb, const int32_t* __restrict
     for (int j = j0[m]; j < j1[m]; ++j) {
       const cplx<T> w = t64.template get<-1>((kx * (int)__ldg(xs + j)) & (N - 1));
       const T r = ld_ro(vf + j);
-      sum.x += r * w.x;
-      sum.y += r * w.y;
+      sum = cmacr(sum, r, w);
     }
     v[m] = sum;
   }

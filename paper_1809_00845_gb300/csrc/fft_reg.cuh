@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ff.cuh"
+
 namespace bemfft {
 
 template <typename T>
@@ -64,10 +66,83 @@ __device__ __forceinline__ cplx<float> psub(cplx<float> a, cplx<float> b) {
   const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
   return {r.x, r.y};
 }
+// Complex double-float add and subtract with the real and imaginary parts'
+// FP32 steps paired into packed instructions: each part sees the scalar
+// double-float add's operations in the same order (bitwise the same result)
+// in half the issue slots.
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ cplx<f32x2> ffc_add(float2 ah, float2 al, float2 bh, float2 bl) {
+  const float2 s = f2add(ah, bh), bb = f2sub(s, ah);
+  float2 e = f2add(f2sub(ah, f2sub(s, bb)), f2sub(bh, bb));
+  e = f2add(e, f2add(al, bl));
+  const float2 rh = f2add(s, e), rl = f2sub(e, f2sub(rh, s));
+  return {f32x2(rh.x, rl.x), f32x2(rh.y, rl.y)};
+}
+__device__ __forceinline__ cplx<f32x2> padd(cplx<f32x2> a, cplx<f32x2> b) {
+  return ffc_add(make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo), make_float2(b.x.hi, b.y.hi),
+                 make_float2(b.x.lo, b.y.lo));
+}
+__device__ __forceinline__ cplx<f32x2> psub(cplx<f32x2> a, cplx<f32x2> b) {
+  return ffc_add(make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo), make_float2(-b.x.hi, -b.y.hi),
+                 make_float2(-b.x.lo, -b.y.lo));
+}
+// Packed double-float product, lane by lane a * b (Dekker's product: the
+// scalar double-float multiply's steps in the same order), and the complex
+// double-float products built on it.  (For FP32 the packed complex product
+// was measured slower than four scalar operations: its operands need
+// broadcast and swapped register pairs.)
+__device__ __forceinline__ void ffp_mul(float2 ah, float2 al, float2 bh, float2 bl, float2& rh, float2& rl) {
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  rh = f2add(p, e);
+  rl = f2sub(e, f2sub(rh, p));
+}
+__device__ __forceinline__ cplx<f32x2> cmul(cplx<f32x2> a, cplx<f32x2> b) {
+  float2 ph, pl, qh, ql;
+  ffp_mul(make_float2(a.x.hi, a.x.hi), make_float2(a.x.lo, a.x.lo), make_float2(b.x.hi, b.y.hi),
+          make_float2(b.x.lo, b.y.lo), ph, pl);
+  ffp_mul(make_float2(a.y.hi, a.y.hi), make_float2(a.y.lo, a.y.lo), make_float2(-b.y.hi, b.x.hi),
+          make_float2(-b.y.lo, b.x.lo), qh, ql);
+  return ffc_add(ph, pl, qh, ql);
+}
+__device__ __forceinline__ cplx<f32x2> cscale(cplx<f32x2> a, f32x2 s) {
+  float2 rh, rl;
+  ffp_mul(make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo), make_float2(s.hi, s.hi), make_float2(s.lo, s.lo),
+          rh, rl);
+  return {f32x2(rh.x, rl.x), f32x2(rh.y, rl.y)};
+}
+// s + a * w (real a first: the x-DFT row sums)
+__device__ __forceinline__ cplx<f32x2> cmacr(cplx<f32x2> s, f32x2 a, cplx<f32x2> w) {
+  float2 rh, rl;
+  ffp_mul(make_float2(a.hi, a.hi), make_float2(a.lo, a.lo), make_float2(w.x.hi, w.y.hi), make_float2(w.x.lo, w.y.lo),
+          rh, rl);
+  return ffc_add(make_float2(s.x.hi, s.y.hi), make_float2(s.x.lo, s.y.lo), rh, rl);
+}
+// y + v * s (complex v first: the spectral multiply)
+__device__ __forceinline__ cplx<f32x2> cmacc(cplx<f32x2> y, cplx<f32x2> v, f32x2 s) {
+  float2 rh, rl;
+  ffp_mul(make_float2(v.x.hi, v.y.hi), make_float2(v.x.lo, v.y.lo), make_float2(s.hi, s.hi), make_float2(s.lo, s.lo),
+          rh, rl);
+  return ffc_add(make_float2(y.x.hi, y.y.hi), make_float2(y.x.lo, y.y.lo), rh, rl);
+}
 template <typename T>
 __device__ __forceinline__ cplx<T> padd(cplx<T> a, cplx<T> b) { return a + b; }
 template <typename T>
 __device__ __forceinline__ cplx<T> psub(cplx<T> a, cplx<T> b) { return a - b; }
+
+// s + a * w and y + v * s for complex s, w, y, v and real a, s (the packed
+// double-float forms above keep these operand orders)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmacr(cplx<T> s, T a, cplx<T> w) {
+  return {s.x + a * w.x, s.y + a * w.y};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cmacc(cplx<T> y, cplx<T> v, T s) {
+  return {y.x + v.x * s, y.y + v.y * s};
+}
 
 // multiply by e^{DIR i pi/2} = DIR * i
 template <int DIR, typename T>
