@@ -167,6 +167,10 @@ struct bem_plan_s {
   std::vector<double> h_w_user, h_normal_user;
   bemfft::Operator op_single, op_double, op_system;
   bool have_bc = false;
+  // the BC-split operator of the complementary mask (built on first use by
+  // apply_complement; dropped when the conditions change)
+  bemfft::Operator op_comp;
+  bool have_comp = false;
   std::vector<uint8_t> h_bc;
   bemfft::BlockPrecond pc;
   // four-step column kernel: per-thread equal cell ranges
@@ -347,6 +351,13 @@ bem_status solve_graph(bem_plan_s* p, const uint8_t* bc, const double* data, dou
                        int restart, const double* x0, double* u_out, double* q_out, bem_solve_info* info,
                        cudaStream_t st);
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st);
+// Right-hand side of the mixed problem in one apply: with data d (u on the
+// Dirichlet cells, q on the Neumann cells) the right-hand side c u_D - D u_D -
+// S q_N equals -(A' d), A' the BC-split system operator of the complementary
+// mask.  has_complement: the plan can do this (2D four-step plans with both
+// condition types set); apply_complement writes A' d (plan-precision I/O).
+bool has_complement(const bem_plan_s* p);
+bem_status apply_complement(bem_plan_s* p, const void* in, void* out, cudaStream_t st);
 // argument checks of the entry points (capi.cu)
 bem_status check_device(const bem_plan_s* p, const char* who);
 bem_status check_buffer_device(const bem_plan_s* p, const void* ptr, const char* who);

@@ -481,6 +481,36 @@ bem_status bem_plan_panels(bem_plan_t* out, int64_t n, double h, int64_t nb, con
   return panel_plan_impl(out, n, h, nb, panels, order, near_radius, prec, static_cast<cudaStream_t>(stream));
 }
 
+// BC-split system operator of a 2D four-step plan, A x = S(x m_D) + D(x m_N)
+// - c x m_N (Eq. 15 with the BC split), for the mask bc or (complement) its
+// complement: per sorted cell a type and two coefficients, type 0
+// (Dirichlet): (w, 0) -> fields (U, -); type 1 (Neumann): (w n_x, w n_y) ->
+// (Q_x, Q_y); all-Neumann: type 0 with (w n_x, w n_y) -> fields (Q_x, Q_y).
+// Fields that no cell feeds are left out (exact: they would add zeros).
+static bem_status build_system_v2(bem_plan_s* p, const uint8_t* bc, double c, bool complement, Operator& s) {
+  const int64_t nb = p->nb;
+  auto neu_of = [&](int64_t i) { return (bc[i] != 0) != complement; };
+  int64_t nneu = 0;
+  for (int64_t i = 0; i < nb; ++i) nneu += neu_of(i) ? 1 : 0;
+  const bool all_d = nneu == 0, all_n = nneu == nb;
+  std::vector<double> ca(nb), cb(nb), dg(nb);
+  std::vector<uint8_t> ty(nb);
+  for (int64_t j = 0; j < nb; ++j) {
+    const bool neu = neu_of(p->h_perm[j]);
+    ty[j] = neu && !all_n ? 1 : 0;
+    ca[j] = neu ? p->h_w[j] * p->h_normal[2 * j] : p->h_w[j];
+    cb[j] = neu ? p->h_w[j] * p->h_normal[2 * j + 1] : 0.0;
+  }
+  for (int64_t i = 0; i < nb; ++i) dg[i] = neu_of(i) ? -c : 0.0;  // user order
+  s.nf = all_d ? 1 : (all_n ? 2 : 3);
+  s.f[0] = {nullptr, 0, all_n ? 1 : 0, 0, nullptr, nullptr};
+  s.f[1] = {nullptr, 0, all_n ? 2 : 1, 0, nullptr, nullptr};
+  s.f[2] = {nullptr, 0, 2, 0, nullptr, nullptr};
+  bem_status rc;
+  if ((rc = build_op_v2(p, s, ca, cb, ty)) != BEM_OK) return rc;
+  return upload_coef(p, s, dg, &s.diag, true);
+}
+
 bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
   if (!p || !bc) {
     set_error("bem_set_bc: null pointer argument");
@@ -503,6 +533,8 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
   }
   if (p->have_bc && c == p->c && std::equal(p->h_bc.begin(), p->h_bc.end(), bc)) return BEM_OK;
   free_operator(p->op_system);
+  free_operator(p->op_comp);
+  p->have_comp = false;
   ++p->op_version;
   p->h_bc.assign(bc, bc + nb * p->ncomp);
   p->c = c;
@@ -525,22 +557,7 @@ bem_status bem_set_bc(bem_plan_t p, const uint8_t* bc, double c) {
     for (int64_t i = 0; i < nb; ++i) nneu += bc[i] ? 1 : 0;
     const bool all_d = nneu == 0, all_n = nneu == nb;
     if (p->v2) {
-      // type 0 (Dirichlet): (w, 0) -> fields (U, -); type 1 (Neumann): (w n_x, w n_y) -> (Q_x, Q_y);
-      // all-Neumann: type 0 with (w n_x, w n_y) -> fields (Q_x, Q_y)
-      std::vector<double> ca(nb), cb(nb);
-      std::vector<uint8_t> ty(nb);
-      for (int64_t j = 0; j < nb; ++j) {
-        const bool neu = bc[p->h_perm[j]] != 0;
-        ty[j] = neu && !all_n ? 1 : 0;
-        ca[j] = neu ? p->h_w[j] * p->h_normal[2 * j] : p->h_w[j];
-        cb[j] = neu ? p->h_w[j] * p->h_normal[2 * j + 1] : 0.0;
-      }
-      s.nf = all_d ? 1 : (all_n ? 2 : 3);
-      s.f[0] = {nullptr, 0, all_n ? 1 : 0, 0, nullptr, nullptr};
-      s.f[1] = {nullptr, 0, all_n ? 2 : 1, 0, nullptr, nullptr};
-      s.f[2] = {nullptr, 0, 2, 0, nullptr, nullptr};
-      if ((rc = build_op_v2(p, s, ca, cb, ty)) != BEM_OK) return rc;
-      if ((rc = upload_coef(p, s, dg, &s.diag, true)) != BEM_OK) return rc;
+      if ((rc = build_system_v2(p, bc, c, false, s)) != BEM_OK) return rc;
       p->have_bc = true;
       p->pc.valid = false;
       return BEM_OK;
@@ -840,6 +857,7 @@ bem_status bem_destroy(bem_plan_t p) {
   free_operator(p->op_single);
   free_operator(p->op_double);
   free_operator(p->op_system);
+  free_operator(p->op_comp);
   free_slot_set(&p->all_set);
   cudaFree(p->d_tinfo);
   cudaFree(p->d_perm_il);
@@ -901,6 +919,29 @@ const char* bem_last_error(void) { return g_last_error.c_str(); }
 }  // extern "C"
 
 namespace bemfft {
+
+bool has_complement(const bem_plan_s* p) {
+  if (!p->have_bc || p->pf || p->dim != 2 || !p->v2 || p->kernel != BEM_LAPLACE_2D) return false;
+  bool d = false, n = false;
+  for (uint8_t b : p->h_bc) (b ? n : d) = true;
+  return d && n;
+}
+
+bem_status apply_complement(bem_plan_s* p, const void* in, void* out, cudaStream_t st) {
+  if (!has_complement(p)) {
+    set_error("apply_complement: needs a 2D four-step plan with both condition types set");
+    return BEM_ERR_UNSUPPORTED;
+  }
+  if (!p->have_comp) {
+    bem_status rc = build_system_v2(p, p->h_bc.data(), p->c, true, p->op_comp);
+    if (rc != BEM_OK) {
+      free_operator(p->op_comp);
+      return rc;
+    }
+    p->have_comp = true;
+  }
+  return launch_apply_2d(p, p->op_comp, in, out, st);
+}
 
 bem_status apply_operator(bem_plan_s* p, bem_layer layer, const void* in, void* out, cudaStream_t st) {
   if (p->pf) return launch_apply_panels(p, layer, in, out, st);

@@ -178,6 +178,15 @@ struct Gm {
     k_convert<float, double><<<blocks_for(M, 256), 256, 0, st>>>(static_cast<const float*>(p->d_tout), w, M);
     return BEM_OK;
   }
+  // w (FP64) = A' x with the complementary mask's operator (apply_complement)
+  bem_status apply_comp(const double* x, double* w) {
+    if (fp64) return apply_complement(p, x, w, st);
+    k_convert<double, float><<<blocks_for(M, 256), 256, 0, st>>>(x, static_cast<float*>(p->d_tin), M);
+    bem_status rc = apply_complement(p, p->d_tin, p->d_tout, st);
+    if (rc != BEM_OK) return rc;
+    k_convert<float, double><<<blocks_for(M, 256), 256, 0, st>>>(static_cast<const float*>(p->d_tout), w, M);
+    return BEM_OK;
+  }
   // z = M^-1 v (or a copy when unpreconditioned)
   void precond(const double* v, double* z) {
     if (p->pc.kind == 0) {
@@ -215,8 +224,13 @@ struct GmresOut {
 // apply of g.p; stops when ||b - A x|| <= tol * bnorm (recomputed at every
 // restart with the same apply), after max_iter iterations, or when the
 // recomputed residual stagnates for three restarts.  x is updated in place.
+// x_zero: x is zero on entry, so the first residual is b (no apply).
+// trust_estimate: a correction solve inside refinement, whose caller forms
+// the residual of the updated x with its own operator next; the solve ends
+// when the Arnoldi estimate meets tol (or at max_iter) without recomputing
+// the residual with the low-precision apply.
 static bem_status gmres_core(Gm& g, const GmresWs& ws, const double* d_b, double bnorm, double* d_x, double tol,
-                             int max_iter, GmresOut* out) {
+                             int max_iter, GmresOut* out, bool x_zero = false, bool trust_estimate = false) {
   const int64_t M = g.M;
   const int m = ws.m;
   cudaStream_t st = g.st;
@@ -226,12 +240,16 @@ static bem_status gmres_core(Gm& g, const GmresWs& ws, const double* d_b, double
   double best_rel = INFINITY;
   int stagnant = 0;
   out->status = BEM_ERR_NOT_CONVERGED;
+  bool first = true;
   while (true) {
     // r = b - A x  -> V[0]
-    if ((rc = g.apply(BEM_SYSTEM, d_x, ws.w)) != BEM_OK) return rc;
-    ++out->applies;
     BEM_CUDA_TRY(cudaMemcpyAsync(V, d_b, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, ws.w, 1.0, V, M);
+    if (!(first && x_zero)) {
+      if ((rc = g.apply(BEM_SYSTEM, d_x, ws.w)) != BEM_OK) return rc;
+      ++out->applies;
+      k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, ws.w, 1.0, V, M);
+    }
+    first = false;
     double beta2 = 0.0;
     g.dots(V, M, 1, V, ws.h, false);
     BEM_CUDA_TRY(cudaMemcpyAsync(&beta2, ws.h, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -262,6 +280,7 @@ static bem_status gmres_core(Gm& g, const GmresWs& ws, const double* d_b, double
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int j = 0;
+    bool est_done = false;
     for (; j < m && out->iters < max_iter; ++j) {
       double* vj = V + (int64_t)j * M;
       double* vn = V + (int64_t)(j + 1) * M;
@@ -303,6 +322,7 @@ static bem_status gmres_core(Gm& g, const GmresWs& ws, const double* d_b, double
       out->rel_est = bnorm > 0 ? std::fabs(gv[j + 1]) / bnorm : 0.0;
       if (out->rel_est <= tol || std::sqrt(hbuf[j + 1]) <= 1e-14 * bnorm) {
         ++j;
+        est_done = true;
         break;
       }
     }
@@ -320,6 +340,11 @@ static bem_status gmres_core(Gm& g, const GmresWs& ws, const double* d_b, double
       k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(1.0, ws.z, 1.0, d_x, M);
     }
     ++out->restarts;
+    if (trust_estimate && (est_done || out->iters >= max_iter)) {
+      out->rel = out->rel_est;
+      if (est_done) out->status = BEM_OK;
+      return BEM_OK;
+    }
   }
 }
 
@@ -383,23 +408,35 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
   k_split_known<<<blocks_for(M, 256), 256, 0, st>>>(d_data, d_bc, d_um, d_qm, M);
   // b = c um - sigma K2 um - K1 qm,  sigma K2 = +D (Laplace) or -T (Kelvin)
   const double sigma = p->kernel == BEM_KELVIN_3D ? -1.0 : 1.0;
-  // an apply of an all-zero density (no Dirichlet or no Neumann entries) is skipped
+  // an apply of an all-zero density (no Dirichlet or no Neumann entries) is
+  // skipped; with both kinds an FP64-accurate residual operator gives b in
+  // one apply where it has the complementary mask's operator (b = -(A'
+  // data)).  An FP32 operator keeps the two layer applies and adds c um in
+  // FP64: with b from one FP32 apply, plain FP32 GMRES on the 4096^2 star
+  // stalled at 6.2e-6 instead of 2.3e-6.
   int64_t nneu = 0;
   for (int64_t i = 0; i < M; ++i) nneu += bc[i] != 0;
-  if (nneu < M) {
-    if ((rc = gr.apply(BEM_DOUBLE, d_um, d_b)) != BEM_OK) return rc;
+  if (fp64_residual(R) && has_complement(R)) {
+    if ((rc = gr.apply_comp(d_data, d_w)) != BEM_OK) return rc;
     ++applies;
-  } else {
     BEM_CUDA_TRY(cudaMemsetAsync(d_b, 0, M * sizeof(double), st));
-  }
-  if (nneu > 0) {
-    if ((rc = gr.apply(BEM_SINGLE, d_qm, d_w)) != BEM_OK) return rc;
-    ++applies;
+    k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, 0.0, d_b, M);
   } else {
-    BEM_CUDA_TRY(cudaMemsetAsync(d_w, 0, M * sizeof(double), st));
+    if (nneu < M) {
+      if ((rc = gr.apply(BEM_DOUBLE, d_um, d_b)) != BEM_OK) return rc;
+      ++applies;
+    } else {
+      BEM_CUDA_TRY(cudaMemsetAsync(d_b, 0, M * sizeof(double), st));
+    }
+    if (nneu > 0) {
+      if ((rc = gr.apply(BEM_SINGLE, d_qm, d_w)) != BEM_OK) return rc;
+      ++applies;
+    } else {
+      BEM_CUDA_TRY(cudaMemsetAsync(d_w, 0, M * sizeof(double), st));
+    }
+    k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, -sigma, d_b, M);  // b = -sigma K2 um - K1 qm
+    k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(c, d_um, 1.0, d_b, M);       // b += c um
   }
-  k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(-1.0, d_w, -sigma, d_b, M);  // b = -sigma K2 um - K1 qm
-  k_axpby<<<blocks_for(M, 256), 256, 0, st>>>(c, d_um, 1.0, d_b, M);       // b += c um
   if (x0)
     BEM_CUDA_TRY(cudaMemcpyAsync(d_x, x0, M * sizeof(double), cudaMemcpyHostToDevice, st));
   else
@@ -420,7 +457,7 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
   bem_status result = BEM_ERR_NOT_CONVERGED;
   double rel = 1.0, rel_est = 1.0;
   if (R == p) {
-    if ((rc = gmres_core(g, ws, d_b, bnorm, d_x, tol, max_iter, &tot)) != BEM_OK) return rc;
+    if ((rc = gmres_core(g, ws, d_b, bnorm, d_x, tol, max_iter, &tot, x0 == nullptr)) != BEM_OK) return rc;
     result = tot.status;
     rel = tot.rel;
     rel_est = tot.rel_est;
@@ -433,7 +470,9 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
     if (x0) {
       // first step from the initial guess: low-precision GMRES from x0 on A x = b
       GmresOut in;
-      if ((rc = gmres_core(g, ws, d_b, bnorm, d_x, inner_tolerance(tol, 1.0), max_iter, &in)) != BEM_OK) return rc;
+      if ((rc = gmres_core(g, ws, d_b, bnorm, d_x, inner_tolerance(tol, 1.0), max_iter, &in, false, true)) !=
+          BEM_OK)
+        return rc;
       tot.iters += in.iters;
       tot.restarts += in.restarts;
       tot.applies += in.applies;
@@ -476,7 +515,8 @@ bem_status solve_gmres(bem_plan_s* p, const uint8_t* bc, const double* data, dou
       // inner solve A d = r to a modest relative accuracy
       BEM_CUDA_TRY(cudaMemsetAsync(d_d, 0, M * sizeof(double), st));
       GmresOut in;
-      if ((rc = gmres_core(g, ws, d_r, rn, d_d, inner_tolerance(tol, rel), max_iter - tot.iters, &in)) != BEM_OK)
+      if ((rc = gmres_core(g, ws, d_r, rn, d_d, inner_tolerance(tol, rel), max_iter - tot.iters, &in, true, true)) !=
+          BEM_OK)
         return rc;
       tot.iters += in.iters;
       tot.restarts += in.restarts;
@@ -882,10 +922,13 @@ struct BatchCounters {
 
 // Lockstep GMRES(m) on A x = rhs (per system: stop when |rhs - A x| <=
 // tol_s * rn_s, recomputed with A at every restart).  x is updated in place;
-// rel[s] holds the last recomputed relative residual.
+// rel[s] holds the last recomputed relative residual.  x_zero and
+// trust_estimate as in gmres_core: a zero start takes rhs as its first
+// residual, and a correction solve inside refinement ends on the Arnoldi
+// estimates (every system stopped, or max_iter) without a closing apply.
 bem_status batch_gmres(bem_batch_s* bt, BatchSolveWs& W, const double* rhs, const std::vector<double>& rn,
                        double* x, const std::vector<double>& tols, int max_iter, BatchCounters* cnt,
-                       std::vector<double>& rel) {
+                       std::vector<double>& rel, bool x_zero = false, bool trust_estimate = false) {
   const int K = W.K, m = W.m;
   const int64_t Mt = W.Mt;
   cudaStream_t st = W.st;
@@ -898,15 +941,18 @@ bem_status batch_gmres(bem_batch_s* bt, BatchSolveWs& W, const double* rhs, cons
   std::vector<int> stagnant(K, 0);
   rel.assign(K, 1.0);
   const int iters0 = cnt->iters;
+  bool first = true;
   for (;;) {
-    bem_status rc = batch_apply_f64(bt, x, W.w, st, true);
-    if (rc != BEM_OK) return rc;
-    ++cnt->applies;
+    bem_status rc;
     // r = rhs - A x, per-system norms
     BEM_CUDA_TRY(cudaMemcpyAsync(W.r, rhs, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(-1.0, W.w, 1.0, W.r, Mt);
+    if (!(first && x_zero)) {
+      if ((rc = batch_apply_f64(bt, x, W.w, st, true)) != BEM_OK) return rc;
+      ++cnt->applies;
+      k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(-1.0, W.w, 1.0, W.r, Mt);
+    }
     if ((rc = seg_norms(W, W.r, beta2)) != BEM_OK) return rc;
-    if (cnt->iters == iters0) {
+    if (cnt->iters == iters0 && !(first && x_zero)) {
       // a starting point worse than zero (an initial guess) is replaced by zero
       bool any = false;
       for (int s = 0; s < K; ++s)
@@ -943,18 +989,24 @@ bem_status batch_gmres(bem_batch_s* bt, BatchSolveWs& W, const double* rhs, cons
     // V0 = r / beta (W.r already holds rhs - A x; pass a zero w)
     BEM_CUDA_TRY(cudaMemsetAsync(W.w, 0, Mt * sizeof(double), st));
     k_b_start<<<blocks_for(Mt, 256), 256, 0, st>>>(W.r, W.w, W.nrm, W.jstop, W.sys, W.V, Mt);
+    first = false;
+    bool stopped = false;
     for (int j = 0; j < m && cnt->iters < max_iter; ++j) {
       BEM_CUDA_TRY(cudaGraphLaunch(W.exec, st));
       BEM_CUDA_TRY(cudaStreamSynchronize(st));
       ++cnt->iters;
       ++cnt->applies;
-      if (*W.h_active == 0) break;
+      if (*W.h_active == 0) {
+        stopped = true;
+        break;
+      }
     }
     k_b_backsolve<<<blocks_for(K, 64), 64, 0, st>>>(K, m, W.jdev, W.jstop, W.H, W.g, W.y);
     k_b_combine<<<blocks_for(Mt, 256), 256, 0, st>>>(W.V, Mt, W.jdev, W.jstop, W.sys, W.y, m, W.d, Mt);
     batch_precond(bt, W.d, W.zz, st);
     k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(1.0, W.zz, 1.0, x, Mt);
     ++cnt->restarts;
+    if (trust_estimate && (stopped || cnt->iters >= max_iter)) return BEM_OK;
   }
 }
 
@@ -1082,8 +1134,12 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
   }
   BEM_CUDA_TRY(cudaMemcpyAsync(W->vin, um.data(), Mt * sizeof(double), cudaMemcpyHostToDevice, st));
   BEM_CUDA_TRY(cudaMemcpyAsync(W->zz, qm.data(), Mt * sizeof(double), cudaMemcpyHostToDevice, st));
+  BEM_CUDA_TRY(cudaMemcpyAsync(W->rhs, data, Mt * sizeof(double), cudaMemcpyHostToDevice, st));
   // per plan on the batch's side streams (fork from st, join back); an apply
-  // of an all-zero density is skipped
+  // of an all-zero density is skipped, and a plan with both condition types
+  // that has the complementary mask's operator forms its part in one apply
+  // (w = A' data, with its um zeroed so that the sum below gives -(A' data);
+  // FP64-accurate residual operators only, as in bem_solve)
   BEM_CUDA_TRY(cudaMemsetAsync(W->b, 0, Mt * sizeof(double), st));
   BEM_CUDA_TRY(cudaMemsetAsync(W->w, 0, Mt * sizeof(double), st));
   const int S = bt->nstreams;
@@ -1098,6 +1154,12 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
     if (!R->d_tin) {
       BEM_CUDA_TRY(cudaMalloc(&R->d_tin, (size_t)M * prec_bytes(R)));
       BEM_CUDA_TRY(cudaMalloc(&R->d_tout, (size_t)M * prec_bytes(R)));
+    }
+    if (fp64_residual(R) && has_complement(R)) {
+      if ((rc = gr.apply_comp(W->rhs + o, W->w + o)) != BEM_OK) return rc;
+      BEM_CUDA_TRY(cudaMemsetAsync(W->vin + o, 0, M * sizeof(double), ss));
+      ++rhs_applies;
+      continue;
     }
     int64_t nneu = 0;
     for (int64_t i = 0; i < M; ++i) nneu += bc[o + i] != 0;
@@ -1131,7 +1193,8 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
   std::vector<double> rel(K, 1.0);
   int refine_steps = 0;
   if (!refine) {
-    if ((rc = batch_gmres(bt, *W, W->b, bnorm, W->x, std::vector<double>(K, tol), max_iter, &cnt, rel)) != BEM_OK)
+    if ((rc = batch_gmres(bt, *W, W->b, bnorm, W->x, std::vector<double>(K, tol), max_iter, &cnt, rel,
+                          x0 == nullptr)) != BEM_OK)
       return rc;
   } else {
     // residuals with the companions' operator, corrections from the lockstep
@@ -1147,7 +1210,8 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
       // residual with the companion operator
       std::vector<double> first_tol(K, inner_tolerance(tol, 1.0));
       std::vector<double> rin;
-      if ((rc = batch_gmres(bt, *W, W->b, bnorm, W->x, first_tol, max_iter, &cnt, rin)) != BEM_OK) return rc;
+      if ((rc = batch_gmres(bt, *W, W->b, bnorm, W->x, first_tol, max_iter, &cnt, rin, false, true)) != BEM_OK)
+        return rc;
       ++refine_steps;
     }
     for (;;) {
@@ -1179,7 +1243,8 @@ extern "C" bem_status bem_batch_solve(bem_batch_t bt, const uint8_t* bc, const d
       BEM_CUDA_TRY(cudaMemcpyAsync(W->rhs, W->r, Mt * sizeof(double), cudaMemcpyDeviceToDevice, st));
       BEM_CUDA_TRY(cudaMemsetAsync(W->e, 0, Mt * sizeof(double), st));
       std::vector<double> rin;
-      if ((rc = batch_gmres(bt, *W, W->rhs, rn, W->e, inner_tol, max_iter, &cnt, rin)) != BEM_OK) return rc;
+      if ((rc = batch_gmres(bt, *W, W->rhs, rn, W->e, inner_tol, max_iter, &cnt, rin, true, true)) != BEM_OK)
+        return rc;
       k_axpby<<<blocks_for(Mt, 256), 256, 0, st>>>(1.0, W->e, 1.0, W->x, Mt);
       ++refine_steps;
     }

@@ -109,6 +109,11 @@ def test_fp32_refinement_reaches_fp64_tolerance(torch_cuda, oracle_mod):
     u_out, q_out, info = plan.solve(bc, data, tol=1e-8, restart=100, max_iter=1500)
     assert info["status"] == 0 and info["refine_steps"] >= 1, info
     assert info["rel_residual_fp64"] == info["rel_residual"] <= 1e-8  # the double-float companion's residual
+    # one apply for the right-hand side (the complementary mask's operator),
+    # one per Arnoldi step and one per cycle's closing residual: a correction
+    # solve starts from zero without an apply and ends on its estimate, the
+    # residual of the updated iterate coming from the companion
+    assert info["applies"] == info["iters"] + 1 + info["restarts"], info
     x = np.where(bc == 0, q_out, u_out)
     rhs = oracle_mod.system_rhs("laplace2d", b.cell, b.h, b.w, b.normal, bc, u * (bc == 0), q * (bc == 1))
     r = rhs - oracle_mod.system_apply("laplace2d", b.cell, b.h, b.w, b.normal, bc, x)
