@@ -639,7 +639,7 @@ struct ColSmem {
 // rows in sA: the caller gathers the CTA's last column after its loop.
 template <typename T, int NF, bool ACCREG, int TTC, int TCK, bool EDGE = false, bool FUSED = false, int NB = CB>
 __device__ __forceinline__ void col2d_column(const Col2Dv2Params<T>& p, const ColDims<TTC>& g, int kx,
-                                             FourStep<T, TCK>& fs, const Twiddles2L<T>& tw, const ColSmem<T>& sm,
+                                             FourStep<T, TCK, !EDGE>& fs, const Twiddles2L<T>& tw, const ColSmem<T>& sm,
                                              T* sacc, T* gacc, int qs, cplx<T>* twc,
                                              cplx<T> half = {T(1), T(0)}, int kxp = -1) {
   static_assert(!EDGE || NF == 2, "edge-flow form: two fields");
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(ColBounds<TTC>::threads, ColBounds<TTC>::block
   const FourStepTables<T> ftab{stab, stab + 512, stab + 512 + W * 16};
   const Twiddles2L<T> tw{stab + 1024 + W * 16, stab + 1024 + W * 16 + 128, g.log2N - 7,
                          (T)(6.283185307179586476925 / (double)N)};
-  FourStep<T, TCK> fs;
+  FourStep<T, TCK, !EDGE> fs;  // the edge-flow kernels keep the plain butterfly adds
   fs.init(t, TT, sA, ftab);
   if constexpr (TCK > 0) {
     const uint32_t tm = tc_setup(smem_raw, p.tcmat, 2 * kTcMatBytes, TTC / 128 * kTcGroupCols);

@@ -42,10 +42,10 @@ namespace bemfft {
 constexpr int kTcStages = COL2D_TC_STAGES;
 
 // a0..a3 with the upper half (a2, a3) known to be zero
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = true>
 __device__ __forceinline__ void dft4_lowhalf(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
   const cplx<T> b1 = mul_i<DIR>(a1);
-  const cplx<T> x0 = padd(a0, a1), x2 = psub(a0, a1), x1 = a0 + b1, x3 = a0 - b1;
+  const cplx<T> x0 = badd<PK>(a0, a1), x2 = bsub<PK>(a0, a1), x1 = a0 + b1, x3 = a0 - b1;
   a0 = x0;
   a1 = x1;
   a2 = x2;
@@ -53,11 +53,11 @@ __device__ __forceinline__ void dft4_lowhalf(cplx<T>& a0, cplx<T>& a1, cplx<T>& 
 }
 
 // 16-point DFT in registers whose inputs 8..15 are zero.
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = true>
 __device__ __forceinline__ void dft16_lowhalf(cplx<T> (&a)[16]) {
   // R1 = 4 over stride-4 subsequences: elements r2 + 4 r1, r1 = 2, 3 are zero
 #pragma unroll
-  for (int r2 = 0; r2 < 4; ++r2) dft4_lowhalf<DIR>(a[r2], a[r2 + 4], a[r2 + 8], a[r2 + 12]);
+  for (int r2 = 0; r2 < 4; ++r2) dft4_lowhalf<DIR, T, PK>(a[r2], a[r2 + 4], a[r2 + 8], a[r2 + 12]);
 #pragma unroll
   for (int r2 = 1; r2 < 4; ++r2)
 #pragma unroll
@@ -66,7 +66,7 @@ __device__ __forceinline__ void dft16_lowhalf(cplx<T> (&a)[16]) {
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
     cplx<T> t0 = a[4 * k1], t1 = a[4 * k1 + 1], t2 = a[4 * k1 + 2], t3 = a[4 * k1 + 3];
-    dft4<DIR>(t0, t1, t2, t3);
+    dft4<DIR, T, PK>(t0, t1, t2, t3);
     o[k1] = t0;
     o[k1 + 4] = t1;
     o[k1 + 8] = t2;
@@ -80,9 +80,9 @@ __device__ __forceinline__ void dft16_lowhalf(cplx<T> (&a)[16]) {
 // other - mine on the odd one.  For FP32 one packed fused multiply-add with
 // the lane's sign (exact: a product by +-1 rounds nothing) replaces both sums
 // and the select.
-template <typename T>
+template <bool PK, typename T>
 __device__ __forceinline__ cplx<T> s8_combine(cplx<T> mine, cplx<T> other, int h) {
-  if constexpr (std::is_same_v<T, float>) {
+  if constexpr (PK && std::is_same_v<T, float>) {
     const float sg = h ? -1.0f : 1.0f;
     const float2 r = __ffma2_rn(make_float2(mine.x, mine.y), make_float2(sg, sg), make_float2(other.x, other.y));
     return {r.x, r.y};
@@ -104,7 +104,8 @@ struct FourStepTables {
   const cplx<T>* t5;
 };
 
-template <typename T, int TCK = 0>
+// PK: the butterflies' packed FP32-pair adds (fft_reg.cuh badd / bsub)
+template <typename T, int TCK = 0, bool PK = true>
 struct FourStep {
   int t, TT;
   int w, l;             // warp, lane
@@ -163,23 +164,23 @@ struct FourStep {
   template <int DIR>
   __device__ __forceinline__ void dftJ(cplx<T> (&u)[16]) const {
     if (J == 16) {
-      dft<16, DIR>(u);
+      dft<16, DIR, T, PK>(u);
     } else if (J == 8) {
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         cplx<T> q[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) q[j] = u[a * 8 + j];
-        dft<8, DIR>(q);
+        dft<8, DIR, T, PK>(q);
 #pragma unroll
         for (int j = 0; j < 8; ++j) u[a * 8 + j] = q[j];
       }
     } else if (J == 4) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) dft4<DIR>(u[a * 4], u[a * 4 + 1], u[a * 4 + 2], u[a * 4 + 3]);
+      for (int a = 0; a < 4; ++a) dft4<DIR, T, PK>(u[a * 4], u[a * 4 + 1], u[a * 4 + 2], u[a * 4 + 3]);
     } else if (J == 2) {
 #pragma unroll
-      for (int a = 0; a < 8; ++a) dft2<DIR>(u[a * 2], u[a * 2 + 1]);
+      for (int a = 0; a < 8; ++a) dft2<DIR, T, PK>(u[a * 2], u[a * 2 + 1]);
     }
   }
   // shared-memory index of register a in the transposed (line) layout
@@ -192,8 +193,8 @@ struct FourStep {
   template <bool LOWHALF>
   __device__ __forceinline__ void forward(cplx<T> (&v)[16]) {
     if constexpr (TCK > 0 && (kTcStages & 1)) tc.template run<-1, LOWHALF>(v, 0);
-    else if constexpr (LOWHALF) dft16_lowhalf<-1>(v);
-    else dft<16, -1>(v);
+    else if constexpr (LOWHALF) dft16_lowhalf<-1, T, PK>(v);
+    else dft<16, -1, T, PK>(v);
     twiddleT2<-1>(v);
 #pragma unroll
     for (int k = 0; k < 16; ++k) sA[k * TT + t] = v[k];
@@ -213,7 +214,7 @@ struct FourStep {
     for (int i = 0; i < 16; ++i) v[i] = sB[d * 34 + 2 * i + h];
     __syncwarp();
     if constexpr (TCK > 0 && (kTcStages & 4)) tc.template run<-1, false>(v, 0);
-    else dft<16, -1>(v);
+    else dft<16, -1, T, PK>(v);
     // S8: X[k] = E0[k] + w32^k E1[k], X[k+16] = E0[k] - w32^k E1[k]
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -221,7 +222,7 @@ struct FourStep {
       cplx<T> other;
       other.x = shfl_xor(mine.x, 1);
       other.y = shfl_xor(mine.y, 1);
-      v[k] = s8_combine(mine, other, h);
+      v[k] = s8_combine<PK>(mine, other, h);
     }
   }
   // frequency held by register k after forward(): freq0() + 16 * J * k
@@ -240,11 +241,11 @@ struct FourStep {
       cplx<T> other;
       other.x = shfl_xor(v[k].x, 1);
       other.y = shfl_xor(v[k].y, 1);
-      const cplx<T> s = s8_combine(v[k], other, h);
+      const cplx<T> s = s8_combine<PK>(v[k], other, h);
       v[k] = h ? twc<32, +1>(s, k) : s;
     }
     if constexpr (TCK > 0 && (kTcStages & 8)) tc.template run<+1, false>(v, 0);
-    else dft<16, +1>(v);
+    else dft<16, +1, T, PK>(v);
     cplx<T>* sB = sA + w * (16 * 34);
 #pragma unroll
     for (int i = 0; i < 16; ++i) sB[d * 34 + 2 * i + h] = v[i];
@@ -263,7 +264,7 @@ struct FourStep {
     cta_sync();
     twiddleT2<+1>(v);
     if constexpr (TCK > 0 && (kTcStages & 32)) tc.template run<+1, false>(v, 0);
-    else dft<16, +1>(v);
+    else dft<16, +1, T, PK>(v);
   }
 };
 

@@ -133,6 +133,20 @@ __device__ __forceinline__ cplx<T> padd(cplx<T> a, cplx<T> b) { return a + b; }
 template <typename T>
 __device__ __forceinline__ cplx<T> psub(cplx<T> a, cplx<T> b) { return a - b; }
 
+// Butterfly add / subtract: packed (PK) or the plain complex operators.  The
+// kernels pick the form per instantiation (the packed adds cost the
+// accuracy mode's edge-flow column kernel 2% while they speed up the others).
+template <bool PK, typename T>
+__device__ __forceinline__ cplx<T> badd(cplx<T> a, cplx<T> b) {
+  if constexpr (PK) return padd(a, b);
+  else return a + b;
+}
+template <bool PK, typename T>
+__device__ __forceinline__ cplx<T> bsub(cplx<T> a, cplx<T> b) {
+  if constexpr (PK) return psub(a, b);
+  else return a - b;
+}
+
 // s + a * w and y + v * s for complex s, w, y, v and real a, s (the packed
 // double-float forms above keep these operand orders)
 template <typename T>
@@ -195,18 +209,18 @@ __device__ __forceinline__ cplx<T> twc(cplx<T> a, int m) {
   return cmul(a, w);
 }
 
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = true>
 __device__ __forceinline__ void dft2(cplx<T>& a, cplx<T>& b) {
   cplx<T> t = a;
-  a = padd(t, b);
-  b = psub(t, b);
+  a = badd<PK>(t, b);
+  b = bsub<PK>(t, b);
 }
 
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = true>
 __device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
-  const cplx<T> s0 = padd(a0, a2), d0 = psub(a0, a2), s1 = padd(a1, a3), e1 = psub(a1, a3);
-  a0 = padd(s0, s1);
-  a2 = psub(s0, s1);
+  const cplx<T> s0 = badd<PK>(a0, a2), d0 = bsub<PK>(a0, a2), s1 = badd<PK>(a1, a3), e1 = bsub<PK>(a1, a3);
+  a0 = badd<PK>(s0, s1);
+  a2 = bsub<PK>(s0, s1);
   // a1 = d0 + DIR i e1, a3 = d0 - DIR i e1: the rotation swaps e1's parts, so
   // these four sums stay scalar
   if constexpr (DIR > 0) {
@@ -221,13 +235,13 @@ __device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx
 // In-place DFT of R registers: a[k] <- sum_r a[r] e^{DIR 2 pi i r k / R}.
 // R = R1 * R2 split: R1-point DFTs on stride-R2 subsequences, twiddles,
 // R2-point DFTs, transposed read-out (register renaming after unrolling).
-template <int R, int DIR, typename T>
+template <int R, int DIR, typename T, bool PK = true>
 __device__ __forceinline__ void dft(cplx<T> (&a)[R]) {
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
-    dft2<DIR>(a[0], a[1]);
+    dft2<DIR, T, PK>(a[0], a[1]);
   } else if constexpr (R == 4) {
-    dft4<DIR>(a[0], a[1], a[2], a[3]);
+    dft4<DIR, T, PK>(a[0], a[1], a[2], a[3]);
   } else {
     constexpr int R1 = 4;
     constexpr int R2 = R / R1;
@@ -236,7 +250,7 @@ __device__ __forceinline__ void dft(cplx<T> (&a)[R]) {
       cplx<T> t[R1];
 #pragma unroll
       for (int r1 = 0; r1 < R1; ++r1) t[r1] = a[r2 + R2 * r1];
-      dft<R1, DIR>(t);
+      dft<R1, DIR, T, PK>(t);
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) a[r2 + R2 * k1] = t[k1];
     }
@@ -250,7 +264,7 @@ __device__ __forceinline__ void dft(cplx<T> (&a)[R]) {
       cplx<T> t[R2];
 #pragma unroll
       for (int r2 = 0; r2 < R2; ++r2) t[r2] = a[r2 + R2 * k1];
-      dft<R2, DIR>(t);
+      dft<R2, DIR, T, PK>(t);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = t[k2];
     }
