@@ -81,12 +81,12 @@ __global__ void k3_gather(int n, int log2N, int nb, int ncomp, const int32_t* __
     const cplx<T> w = tw.template get<+1>((kx * x) & (N - 1));
     const T ck = (kx == 0 || kx == n) ? T(1) : T(2);
     if constexpr (std::is_same<T, float>::value) {
-      const T term = ck * (Y.x * w.x - Y.y * w.y) - comp;
+      const T term = ck * cdot_re(Y, w) - comp;
       const T ns = s + term;
       comp = (ns - s) - term;
       s = ns;
     } else {
-      s = s + ck * (Y.x * w.x - Y.y * w.y);
+      s = s + ck * cdot_re(Y, w);
     }
   }
   const int u = perm[j];

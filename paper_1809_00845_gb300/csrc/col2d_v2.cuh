@@ -243,7 +243,7 @@ __device__ __forceinline__ void gather_cells(const Col2Dv2Params<T>& p, const Co
     }
 #pragma unroll
     for (int i = 0; i < CB; ++i)
-      if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += ckx * (Y[i].x * w[i].x - Y[i].y * w[i].y);
+      if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += ckx * cdot_re(Y[i], w[i]);
   }
 }
 
@@ -468,7 +468,7 @@ __device__ __forceinline__ void walk_field(const Col2Dv2Params<T>& p, const ColD
       for (int i = 0; i < CB; ++i) Y[i] = rows[meta_slot(mt[i])];
 #pragma unroll
       for (int i = 0; i < CB; ++i)
-        if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += Y[i].x * w[i].x + Y[i].y * w[i].y;
+        if (i0 + i < cnt) *acc_at(sacc, gacc, qs, i0 + i, TT, t) += cdot_rc(Y[i], w[i]);
     }
     if constexpr (SPARSE) {
 #pragma unroll

@@ -128,6 +128,20 @@ __device__ __forceinline__ cplx<f32x2> cmacc(cplx<f32x2> y, cplx<f32x2> v, f32x2
           rh, rl);
   return ffc_add(make_float2(y.x.hi, y.y.hi), make_float2(y.x.lo, y.y.lo), rh, rl);
 }
+// Re(a b) and Re(a conj(b)) (the gathers' output-pruned inverse DFT terms),
+// with the two products paired
+__device__ __forceinline__ f32x2 cdot_re(cplx<f32x2> a, cplx<f32x2> b) {
+  float2 rh, rl;
+  ffp_mul(make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo), make_float2(b.x.hi, b.y.hi),
+          make_float2(b.x.lo, b.y.lo), rh, rl);
+  return f32x2(rh.x, rl.x) - f32x2(rh.y, rl.y);
+}
+__device__ __forceinline__ f32x2 cdot_rc(cplx<f32x2> a, cplx<f32x2> b) {
+  float2 rh, rl;
+  ffp_mul(make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo), make_float2(b.x.hi, b.y.hi),
+          make_float2(b.x.lo, b.y.lo), rh, rl);
+  return f32x2(rh.x, rl.x) + f32x2(rh.y, rl.y);
+}
 template <typename T>
 __device__ __forceinline__ cplx<T> padd(cplx<T> a, cplx<T> b) { return a + b; }
 template <typename T>
@@ -156,6 +170,14 @@ __device__ __forceinline__ cplx<T> cmacr(cplx<T> s, T a, cplx<T> w) {
 template <typename T>
 __device__ __forceinline__ cplx<T> cmacc(cplx<T> y, cplx<T> v, T s) {
   return {y.x + v.x * s, y.y + v.y * s};
+}
+template <typename T>
+__device__ __forceinline__ T cdot_re(cplx<T> a, cplx<T> b) {
+  return a.x * b.x - a.y * b.y;
+}
+template <typename T>
+__device__ __forceinline__ T cdot_rc(cplx<T> a, cplx<T> b) {
+  return a.x * b.x + a.y * b.y;
 }
 
 // multiply by e^{DIR i pi/2} = DIR * i
