@@ -543,11 +543,13 @@ def ellipsoid_solve(dev, n=256):
     bc = np.zeros(b.nb, np.uint8)
     p = Plan.from_boundary(b, "laplace3d", "f32")
     p.enable_refinement(True)
+    pc_block = p.tune_preconditioner(bc, u, tol=1e-6, restart=100, max_iter=1000)
     p.solve(bc, u, tol=1e-6, restart=100, max_iter=1000)
     torch.cuda.synchronize()
     _, q_out, info = p.solve(bc, u, tol=1e-6, restart=100, max_iter=1000)
     p.close()
     return {"nb": b.nb, "seconds": info["seconds"], "iters": info["iters"], "status": info["status"],
+            "preconditioner_block_tuned": pc_block,
             "rel_residual": info["rel_residual"], "refine_steps": info["refine_steps"],
             "q_rel_l2_vs_analytic": float(np.linalg.norm(q_out - q) / np.linalg.norm(q))}
 

@@ -264,6 +264,30 @@ def test_split_system_is_the_unsplit_equation(oracle_mod, kernel):
         assert np.allclose(y, residual, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("kernel", ["laplace2d", "laplace3d", "kelvin3d"])
+def test_right_hand_side_is_the_complementary_split_applied_to_the_data(oracle_mod, kernel):
+    """The reading behind the one-apply right-hand side of the GPU solves: with
+    data d (u on the Dirichlet entries, q on the Neumann entries), the known
+    terms b of the split equation are minus the split operator of the
+    complementary mask applied to d, since swapping the mask swaps which layer
+    each entry feeds and moves the c u term onto the Dirichlet entries
+    (Eq. 15 with the BC split; Eq. 8 for Navier)."""
+    rng = np.random.default_rng(23)
+    dim = 2 if kernel == "laplace2d" else 3
+    b = I.random_cells(16, 30, rng, dim=dim)
+    nc = 3 if kernel == "kelvin3d" else 1
+    args = (b.cell, b.h, b.w, b.normal)
+    for trial in range(3):
+        u = rng.standard_normal(b.nb * nc)
+        q = rng.standard_normal(b.nb * nc)
+        bc = (rng.uniform(size=b.nb * nc) < 0.5).astype(np.uint8)
+        c = 0.5 if trial else 0.25
+        d = np.where(bc == 0, u, q)
+        rhs = oracle_mod.system_rhs(kernel, *args, bc, u, q, c=c)
+        comp = oracle_mod.system_apply(kernel, *args, 1 - bc, d, c=c)
+        assert np.allclose(-comp, rhs, rtol=1e-12, atol=1e-12 * np.abs(rhs).max())
+
+
 def _double_layer_at_targets(oracle_mod, kernel, b, targets, u):
     """The oracle's assembled double layer of the constant density u, read at
     extra zero-weight target cells (they add no source)."""
